@@ -1,0 +1,402 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix.
+
+Each test ties one oracle function to something other than itself: values
+printed in the paper (tests/golden), a hand-derived byte image of the stream
+layout, closed forms, exact rational arithmetic, library routines (numpy,
+scipy) and brute force on tiny arrays.  No GPU is used.
+"""
+import math
+import struct
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import read_golden_table, GOLDEN
+
+SIZES_S = (1, 2, 3, 4, 7, 16, 31, 32, 33, 64, 100, 128)
+
+
+# --------------------------------------------------------------- quantization
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_worked_example_codes(orc, dtype):
+    """Section IV worked example: Y with eps = 0.1 quantizes to the printed Y_q."""
+    g = read_golden_table("worked_example.txt")
+    eps = float(g["eps"][0])
+    Y = np.array([float(v) for v in g["Y"]], dtype).reshape(2, 4)
+    Yq = np.array([int(v) for v in g["Yq"]], np.int32).reshape(2, 4)
+    np.testing.assert_array_equal(orc.quantize(Y, eps), Yq)
+
+
+def test_round_half_up_on_exact_halves(orc):
+    """round(t) = floor(t + 1/2): exact half-integers go up (-12.5 -> -12, 12.5 -> 13)."""
+    eps = 0.25  # 2 eps = 0.5 is exact, so x / (2 eps) is exact
+    k = np.arange(-40, 41)
+    x = ((k + 0.5) * 0.5).astype(np.float64)
+    np.testing.assert_array_equal(orc.quantize(x, eps), (k + 1).astype(np.int32))
+    x2 = (k * 0.5).astype(np.float64)
+    np.testing.assert_array_equal(orc.quantize(x2, eps), k.astype(np.int32))
+
+
+def _err_bound_exact(x, q, eps, sample):
+    """max over a sample of |x - 2 eps q| / eps in exact rational arithmetic."""
+    e = Fraction(eps)
+    worst = Fraction(0)
+    for i in sample:
+        d = abs(Fraction(float(x.flat[i])) - 2 * e * int(q.flat[i]))
+        worst = max(worst, d / e)
+    return worst
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("eb,rel", [(1e-2, True), (1e-3, True), (1e-4, True), (0.37, False), (1e-6, True)])
+def test_error_bound_every_element(orc, rng, dtype, eb, rel):
+    """|d - d'| <= eps for every point (Section III-A and IV), d' = 2 eps q.
+
+    The division x / (2 eps) is rounded once, so the bound holds up to one
+    rounding of a double near a half-integer (relative 2^-52)."""
+    x = (rng.standard_normal(20000) * 3.0 + rng.uniform(-5, 5)).astype(dtype)
+    eps = orc.eps_for(x, eb, rel)
+    if rel:
+        assert eps == eb * (float(x.max()) - float(x.min()))
+    else:
+        assert eps == eb
+    q = orc.quantize(x, eps)
+    err = np.abs(x.astype(np.float64) - q.astype(np.float64) * (2 * eps))
+    assert np.all(err <= eps * (1 + 1e-9) + 4 * np.spacing(np.abs(x.astype(np.float64))))
+    sample = rng.choice(x.size, 300, replace=False)
+    assert _err_bound_exact(x, q, eps, sample) <= 1 + Fraction(1, 2**40)
+
+
+def test_error_bound_float_field_after_dequantize(orc, rng):
+    """The float32 reconstruction stays within eps plus the float32 rounding of d'."""
+    x = rng.uniform(-1, 1, 50000).astype(np.float32)
+    s, eps = orc.compress(x, 1e-3, True, 32)
+    f = orc.decode(s, "f")
+    err = np.abs(f.astype(np.float64) - x.astype(np.float64))
+    assert np.all(err <= eps + 2 * np.spacing(np.abs(f)).astype(np.float64))
+
+
+def test_range_and_argument_errors(orc):
+    with pytest.raises(orc.OracleError) as e:
+        orc.quantize(np.array([1.0, 2.0**31], np.float64), 0.5)
+    assert e.value.status == 2
+    with pytest.raises(orc.OracleError) as e:
+        orc.quantize(np.array([np.nan], np.float64), 0.5)
+    assert e.value.status == 2
+    with pytest.raises(orc.OracleError) as e:
+        orc.compress(np.ones(8, np.float32), -1.0, False, 4)
+    assert e.value.status == 1
+    # constant field with a relative bound: eps falls back to eb
+    assert orc.eps_for(np.full(10, 3.0, np.float32), 1e-3, True) == 1e-3
+
+
+# ---------------------------------------------------------------- the stream
+def _golden_stream_bytes():
+    out = None
+    items = []
+    with open(f"{GOLDEN}/stream_s4.txt") as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            parts = line.split()
+            if parts[0] == "total":
+                out = bytearray(int(parts[1]))
+                continue
+            items.append((int(parts[0]), parts[1], parts[2]))
+    fmt = {"u8": "<B", "u16": "<H", "u32": "<I", "i32": "<i", "u64": "<Q", "f64": "<d"}
+    for off, ty, val in items:
+        v = float(val) if ty == "f64" else int(val, 0)
+        b = struct.pack(fmt[ty], v)
+        out[off:off + len(b)] = b
+    return bytes(out)
+
+
+def test_stream_matches_hand_derived_bytes(orc):
+    """The oracle writes exactly the documented layout (hand-derived S = 4 example)."""
+    q = np.array([5, 3, 4, 4, -1, -1, -1, -1, 7, 9], np.int32)
+    x = q.astype(np.float32)  # eps = 0.5 -> 2 eps = 1 -> codes are the values
+    s, eps = orc.compress(x, 0.5, False, 4)
+    assert eps == 0.5
+    assert bytes(s) == _golden_stream_bytes()
+    np.testing.assert_array_equal(orc.decode(s, "q"), q)
+    np.testing.assert_array_equal(orc.decode(s, "m"), [5, -1, 7])
+    np.testing.assert_array_equal(orc.decode(s, "p"), [5, -2, 1, 0, -1, 0, 0, 0, 7, 2])
+
+
+def _py_decode(stream):
+    """Independent reader of the layout (numpy, not the oracle's C loops)."""
+    s = np.asarray(stream, np.uint8)
+    u32 = lambda o: int(s[o:o + 4].view("<u4")[0])
+    u64 = lambda o: int(s[o:o + 8].view("<u8")[0])
+    S = u32(32)
+    N = u64(64)
+    nb = u64(72)
+    ow, oh, oc, op = u64(96), u64(104), u64(112), u64(120)
+    widths = s[ow:ow + nb].astype(np.int64)
+    heads = s[oh:oh + 4 * nb].view("<i4").astype(np.int64)
+    nsw = (S + 31) // 32
+    words = np.where(widths > 0, nsw + (S * widths + 31) // 32, 0)
+    offs = np.concatenate([[0], np.cumsum(words)])
+    pw = u64(88)
+    payload = s[op:op + 4 * pw].view("<u4").astype(np.uint64)
+    bits = ((payload[:, None] >> np.arange(32, dtype=np.uint64)) & 1).reshape(-1)
+    q = np.empty(N, np.int64)
+    for b in range(nb):
+        first = b * S
+        Sb = min(S, N - first)
+        w = int(widths[b])
+        if w == 0:
+            q[first:first + Sb] = heads[b]
+            continue
+        base = int(offs[b]) * 32
+        k = np.arange(S)
+        sign = bits[base + k]
+        mb = base + nsw * 32 + (k[:, None] * w + np.arange(w)[None, :])
+        mag = (bits[mb] << np.arange(w, dtype=np.uint64)).sum(axis=1).astype(np.int64)
+        p = np.where(sign == 1, -mag, mag)
+        assert p[0] == 0 and np.all(p[Sb:] == 0)
+        q[first:first + Sb] = heads[b] + np.cumsum(p[:Sb])
+    chunk_g = max(1, 4096 // S)
+    chunks = s[oc:oc + 8 * (-(-nb // chunk_g) + 1)].view("<u8").astype(np.int64)
+    np.testing.assert_array_equal(chunks, offs[::chunk_g].tolist() + ([offs[-1]] if nb % chunk_g else []))
+    return q, widths
+
+
+@pytest.mark.parametrize("S", SIZES_S)
+def test_roundtrip_and_independent_reader(orc, rng, S):
+    """c -> D_q recovers the quantized codes exactly; an independent numpy reader of
+    the layout agrees; every width is the bit length of the block's max |p|."""
+    n = int(rng.integers(1, 700))
+    x = np.cumsum(rng.standard_normal(n)).astype(np.float32)
+    if n > 5:
+        x[rng.integers(0, n, 3)] += 50.0
+    s, eps = orc.compress(x, 1e-2, True, S)
+    q_ref = orc.quantize(x, eps)
+    np.testing.assert_array_equal(orc.decode(s, "q"), q_ref)
+    q_py, widths = _py_decode(s)
+    np.testing.assert_array_equal(q_py, q_ref)
+    for b in range(widths.size):
+        blk = q_ref[b * S:(b + 1) * S].astype(np.int64)
+        m = int(np.abs(np.diff(blk)).max()) if blk.size > 1 else 0
+        assert widths[b] == m.bit_length()
+    h = orc.read_header(s)
+    assert h["qmax"] == int(np.abs(q_ref).max())
+    assert h["wmax"] == int(widths.max())
+
+
+@pytest.mark.parametrize("S", SIZES_S)
+def test_stage_chain(orc, rng, S):
+    """c -> D_p -> D_q -> D_f: the in-block inclusive prefix sum of D_p is D_q, and
+    D_f = 2 eps q in the field's arithmetic; encoding the codes again is the identity."""
+    shape = (3, 5, int(rng.integers(1, 40)))
+    x = rng.normal(size=shape).astype(np.float64)
+    s, eps = orc.compress(x, 1e-3, True, S)
+    dp = orc.decode(s, "p").reshape(-1).astype(np.int64)
+    dq = orc.decode(s, "q").reshape(-1)
+    n = dq.size
+    q_from_p = np.empty(n, np.int64)
+    for first in range(0, n, S):
+        q_from_p[first:first + S] = np.cumsum(dp[first:first + S])
+    np.testing.assert_array_equal(q_from_p, dq)
+    np.testing.assert_array_equal(orc.decode(s, "m"), dq[::S])
+    f = orc.decode(s, "f").reshape(-1)
+    np.testing.assert_array_equal(f, dq.astype(np.float64) * (2 * eps))
+    s2 = orc.compress_codes(dq.reshape(shape), eps, S, np.float64, eb=1e-3, rel=True)
+    assert bytes(s2) == bytes(s)
+
+
+def test_float32_dequantize_rule(orc):
+    """float32 reconstruction is (float)q * (float)(2 eps) in float32 arithmetic."""
+    q = np.array([0, 1, -1, 3, 12345, -(2**29), 2**29 + 7, 16777217], np.int32)
+    eps = 0.1234567
+    f = orc.dequantize(q, eps, np.float32)
+    expect = q.astype(np.float32) * np.float32(2 * eps)
+    np.testing.assert_array_equal(f, expect)
+
+
+def test_corrupt_streams_are_rejected(orc, rng):
+    x = rng.normal(size=1000).astype(np.float32)
+    s, _ = orc.compress(x, 1e-3, True, 32)
+    bad = s.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(orc.OracleError) as e:
+        orc.decode(bad, "q")
+    assert e.value.status == 3
+    with pytest.raises(orc.OracleError):
+        orc.decode(s[: s.size // 2], "q")
+    h = orc.read_header(s)
+    bad = s.copy()
+    bad[256] = 40  # width > 31
+    with pytest.raises(orc.OracleError):
+        orc.decode(bad, "q")
+    bad = s.copy()
+    bad[256] = (int(bad[256]) + 1) % 32  # width changed: payload walk no longer matches
+    with pytest.raises(orc.OracleError):
+        orc.decode(bad, "q")
+    assert h["N"] == 1000
+
+
+# ------------------------------------------------------------------- statistics
+def test_worked_example_std_eq_var_q(orc):
+    """Eq. var_q on the printed Y_q: sigma = sqrt((740 - 18^2/8)/7) * 0.2 = 1.99928..."""
+    g = read_golden_table("worked_example.txt")
+    Yq = np.array([int(v) for v in g["Yq"]], np.int32)
+    s1, s2 = orc.sums_q(Yq)
+    assert (s1, s2) == (18, 740)
+    mean, var, sd = orc.finalize(8, s1, s2, 0.1)
+    exact_var = (Fraction(740) - Fraction(18 * 18, 8)) / 7 * Fraction(0.2) ** 2
+    assert abs(var - float(exact_var)) <= 1e-15 * float(exact_var)
+    assert abs(sd - 1.9992855) < 1e-6
+    assert abs(mean - 18 / 8 * 0.2) < 1e-15
+    # the HSZx stage-2 value of Section V-A uses the rounded integer mean 2:
+    mu_t = round(Fraction(18, 8))
+    alt = math.sqrt(sum((int(v) - mu_t) ** 2 for v in Yq) / 7) * 0.2
+    assert abs(alt - float(g["sigma_p_hszx"][0])) < 5e-4
+
+
+def test_stage2_weighted_mean_brute_force(orc, rng):
+    """Section V-A: sum_i q_i = sum_i (S_b - i + 1) p_i inside each block (pure Python)."""
+    for S in (1, 2, 3, 5, 8):
+        n = int(rng.integers(1, 30))
+        q = rng.integers(-50, 50, n).astype(np.int32)
+        dp = []
+        for first in range(0, n, S):
+            blk = [int(v) for v in q[first:first + S]]
+            dp += [blk[0]] + [blk[k] - blk[k - 1] for k in range(1, len(blk))]
+        dp = np.array(dp, np.int32)
+        assert orc.mean_p_sum(dp, S) == sum(int(v) for v in q)
+        s1, s2 = orc.var_p_sums(dp, S)
+        assert s1 == sum(int(v) for v in q)
+        assert s2 == sum(int(v) ** 2 for v in q)
+
+
+def test_exact_sums_wide_codes(orc, rng):
+    """Sums of q^2 past 2^64 stay exact (128-bit), checked with Python integers."""
+    q = rng.integers(-(2**30) + 1, 2**30, 5000).astype(np.int32)
+    s1, s2 = orc.sums_q(q)
+    assert s1 == sum(int(v) for v in q)
+    assert s2 == sum(int(v) ** 2 for v in q)
+    assert s2 > 2**64
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 1000])
+def test_variance_exact_rational(orc, rng, n):
+    """finalize() equals the sample variance of d' = 2 eps q in exact arithmetic."""
+    q = rng.integers(-3000, 3000, n).astype(np.int32)
+    eps = 0.0123
+    s1, s2 = orc.sums_q(q)
+    mean, var, sd = orc.finalize(n, s1, s2, eps)
+    e2 = Fraction(2 * eps)
+    d = [e2 * int(v) for v in q]
+    mu = sum(d) / n
+    v_exact = sum((t - mu) ** 2 for t in d) / (n - 1)
+    assert abs(var - float(v_exact)) <= 1e-14 * float(v_exact)
+    assert abs(mean - float(mu)) <= 1e-14 * max(abs(float(mu)), float(e2))
+    assert sd == math.sqrt(var)
+
+
+def test_variance_single_element_is_nan(orc):
+    mean, var, sd = orc.finalize(1, 5, 25, 0.5)
+    assert mean == 5.0 and math.isnan(var) and math.isnan(sd)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_generic_flow_stats_vs_numpy(orc, rng, dtype):
+    x = (rng.standard_normal(100000) + 7.0).astype(dtype)
+    m, v = orc.stats_f(x)
+    xd = x.astype(np.float64)
+    assert abs(m - xd.mean()) <= 1e-13 * abs(xd.mean())
+    assert abs(v - xd.var(ddof=1)) <= 1e-12 * xd.var(ddof=1)
+
+
+@pytest.mark.parametrize("dtype,rtol", [(np.float64, 1e-12), (np.float32, 1e-6)])
+def test_homomorphic_stats_equal_generic_flow(orc, rng, dtype, rtol):
+    """Section V-D: stage-2/3 mean and std equal the D_f result up to float rounding."""
+    import synth
+
+    x = synth.sinusoid_field((24, 20, 18), dtype=dtype)
+    s, eps = orc.compress(x, 1e-3, True, 32)
+    q = orc.decode(s, "q")
+    mean, var, _ = orc.finalize(q.size, *orc.sums_q(q), eps)
+    mf, vf = orc.stats_f(orc.decode(s, "f"))
+    assert abs(mean - mf) <= rtol * abs(mf)
+    assert abs(var - vf) <= rtol * vf
+
+
+# --------------------------------------------------------------------- stencils
+def _gradient(d, axis):
+    if d.shape[axis] < 2:
+        return np.zeros_like(d)
+    return np.gradient(d, axis=axis, edge_order=1)
+
+
+@pytest.mark.parametrize("shape", [(7,), (2,), (5, 1), (6, 9), (1, 4, 5), (4, 5, 6), (3, 2, 8)])
+def test_stencils_generic_flow_vs_library(orc, rng, shape):
+    """Eq. derivatives / Eq. laplacian on D_f equal numpy.gradient(edge_order=1) and
+    scipy.ndimage.laplace(mode='nearest')."""
+    from scipy import ndimage
+
+    f = rng.standard_normal(shape)
+    for ax in range(len(shape)):
+        np.testing.assert_allclose(orc.stencil_f(f, orc.KIND_DERIV, ax), _gradient(f, ax), rtol=1e-14, atol=1e-14)
+    gm = np.sqrt(sum(_gradient(f, ax) ** 2 for ax in range(len(shape))))
+    np.testing.assert_allclose(orc.stencil_f(f, orc.KIND_GRADMAG), gm, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(orc.stencil_f(f, orc.KIND_LAPLACIAN), ndimage.laplace(f, mode="nearest"),
+                               rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [(9,), (6, 9), (4, 5, 6), (2, 3, 1)])
+def test_integer_stencils_match_library_on_codes(orc, rng, shape):
+    """eps * D and 2 eps * L from integer numerators equal the library stencils of 2 eps q."""
+    from scipy import ndimage
+
+    q = rng.integers(-1000, 1000, shape).astype(np.int32)
+    eps = 0.05
+    d = q.astype(np.float64) * (2 * eps)
+    for ax in range(len(shape)):
+        np.testing.assert_allclose(orc.deriv_q(q, ax) * eps, _gradient(d, ax), rtol=1e-13, atol=1e-12)
+        np.testing.assert_allclose(orc.stencil_q(q, orc.KIND_DERIV, eps, ax), _gradient(d, ax), rtol=1e-13,
+                                   atol=1e-12)
+    np.testing.assert_allclose(orc.lap_q(q) * 2 * eps, ndimage.laplace(d, mode="nearest"), rtol=1e-13, atol=1e-12)
+    gm = np.sqrt(sum(_gradient(d, ax) ** 2 for ax in range(len(shape))))
+    np.testing.assert_allclose(orc.stencil_q(q, orc.KIND_GRADMAG, eps), gm, rtol=1e-13, atol=1e-12)
+
+
+def test_stencil_closed_forms(orc):
+    """Linear ramp: constant derivative 2a along its axis, 0 elsewhere, Laplacian 0
+    inside; quadratic i^2: interior Laplacian numerator 2; constant field: all zero."""
+    n0, n1, n2 = 5, 6, 7
+    i0, i1, i2 = np.meshgrid(np.arange(n0), np.arange(n1), np.arange(n2), indexing="ij")
+    a = 3
+    ramp = (a * i1).astype(np.int32)
+    np.testing.assert_array_equal(orc.deriv_q(ramp, 1), np.full(ramp.shape, 2 * a))
+    np.testing.assert_array_equal(orc.deriv_q(ramp, 0), 0)
+    np.testing.assert_array_equal(orc.deriv_q(ramp, 2), 0)
+    L = orc.lap_q(ramp)
+    np.testing.assert_array_equal(L[:, 1:-1, :], 0)
+    quad = (i2 ** 2).astype(np.int32)
+    np.testing.assert_array_equal(orc.lap_q(quad)[:, :, 1:-1], 2)
+    const = np.full((4, 4, 4), 17, np.int32)
+    assert not orc.lap_q(const).any()
+    assert not orc.deriv_q(const, 2).any()
+    # a one-sided edge is twice the forward difference: D = 2 (q1 - q0)
+    line = np.array([0, 5, 6, 20], np.int32)
+    np.testing.assert_array_equal(orc.deriv_q(line, 0), [10, 6, 15, 28])
+
+
+@pytest.mark.parametrize("shape,S", [((13, 17, 19), 32), ((40, 33), 16), ((200,), 7), ((5, 6, 70), 64)])
+def test_homomorphic_stencils_equal_generic_flow(orc, rng, shape, S):
+    """Section V-D: derivative/Laplacian from codes equal the D_f result up to rounding."""
+    import synth
+
+    x = synth.sinusoid_field(shape, dtype=np.float64)
+    s, eps = orc.compress(x, 1e-3, True, S)
+    q = orc.decode(s, "q")
+    f = orc.decode(s, "f")
+    for kind in (orc.KIND_DERIV, orc.KIND_GRADMAG, orc.KIND_LAPLACIAN):
+        for ax in range(len(shape) if kind == orc.KIND_DERIV else 1):
+            hq = orc.stencil_q(q, kind, eps, ax)
+            hf = orc.stencil_f(f, kind, ax)
+            np.testing.assert_allclose(hq, hf, rtol=1e-12, atol=1e-12 * eps)
