@@ -1,0 +1,541 @@
+"""Benchmark: homomorphic operations on compressed paper-like fields, GB300.
+
+One step = every homomorphic operation of the hot path on every field of the
+paper-like workload, each field resident in HBM in compressed form:
+  mean (fused, stage 2 weights), variance (fused, stage 3), the derivative
+  along every axis, the gradient magnitude and the Laplacian (fused, stage 3),
+for five float32 fields shaped like the paper's datasets (k^-3 Gaussian random
+field + 5% spikes, value-range-relative eb = 1e-3, block 32).
+
+value   = original bytes of the fields x operations / step time (GB/s of
+          original data, the paper's throughput definition) on the device
+          with the compressed inputs already resident;
+e2e     = the same through the C ABI from pinned host memory: the compressed
+          streams are copied in and every result copied out inside the
+          timed region;
+plain   = full decompression to float32 followed by the same operations on
+          the same GPU (the "generic flow"), for the speedup;
+roofline: the dominant kernel's algorithmic bytes (compressed input + output
+          field) over its CUDA-event time, against the measured HBM copy
+          bandwidth.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference].
+With torchrun (WORLD_SIZE > 1) every rank runs its own copy of the workload
+on its own GPU (independent problems, weak scaling, no data-path collective);
+the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "homomorphic-op GB/s of original data & speedup vs full decompress+op; %HBM peak"
+UNIT = "GB/s"
+EB = 1e-3
+BLOCK = 32
+WORKLOAD = ("paper-like scale: five float32 fields 100x500x500, 512x512x512, 256x384x384, 98x1200x1200, "
+            "1800x3600 (2-D); seeded k^-3 Gaussian random fields + 5% spikes normalised to [0,1]; "
+            "value-range-relative eb=1e-3; block 32; every homomorphic op (mean@2, variance@3, "
+            "derivative per axis@3, gradient magnitude@3, Laplacian@3) fused on the compressed stream")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max of a per-rank float over the process group (identity when world == 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# -------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smi_index(local: int) -> str:
+    """nvidia-smi -i argument for this rank's GPU (honours CUDA_VISIBLE_DEVICES)."""
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    if local < len(vis):
+        return vis[local]
+    return str(local)
+
+
+# ------------------------------------------------------------------ workload
+def make_fields():
+    import synth
+
+    return [(shape, synth.grf_field(shape, 1000 + i)) for i, shape in enumerate(synth.PAPER_SHAPES)]
+
+
+def op_list(ndim):
+    return [("mean", None), ("variance", None)] + [("derivative", a) for a in range(ndim)] + \
+        [("gradmag", None), ("laplacian", None)]
+
+
+class Workload:
+    """Compressed fields resident on the device plus preallocated outputs."""
+
+    def __init__(self, hc, torch, dev, fields, eb=EB, S=BLOCK):
+        self.hc, self.torch, self.dev = hc, torch, dev
+        self.items = []
+        for shape, x in fields:
+            xd = torch.from_numpy(x).to(dev)
+            c = hc.compress(xd, eb, rel=True, S=S)
+            # keep only the stream bytes resident (the compressor's bound-sized buffer is freed)
+            stream = c.stream[: c.nbytes].clone()
+            c = hc.Compressed(stream, c.header, c.nbytes)
+            del xd
+            out = torch.empty(shape, dtype=torch.float32, device=dev)
+            scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
+            self.items.append({"shape": shape, "c": c, "out": out, "scal": scal, "n": int(np.prod(shape))})
+        torch.cuda.synchronize()
+
+    @property
+    def orig_bytes_per_step(self):
+        return sum(it["n"] * 4 * len(op_list(len(it["shape"]))) for it in self.items)
+
+    @property
+    def launches_per_step(self):
+        return sum(len(op_list(len(it["shape"]))) for it in self.items)
+
+    def run_op(self, it, op, ax, src=None, level_q="q"):
+        hc = self.hc
+        inp = it["c"] if src is None else src
+        if op == "mean":
+            hc.mean(inp, level="p", out=it["scal"])
+        elif op == "variance":
+            hc.variance(inp, level=level_q, out=it["scal"])
+        elif op == "derivative":
+            hc.derivative(inp, ax, out=it["out"])
+        elif op == "gradmag":
+            hc.gradmag(inp, out=it["out"])
+        else:
+            hc.laplacian(inp, out=it["out"])
+
+    def step(self, events=None):
+        for fi, it in enumerate(self.items):
+            for op, ax in op_list(len(it["shape"])):
+                if events is not None:
+                    e0 = self.torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                self.run_op(it, op, ax)
+                if events is not None:
+                    e1 = self.torch.cuda.Event(enable_timing=True)
+                    e1.record()
+                    events.append((fi, op, e0, e1))
+
+
+def flush_l2(torch, dev, buf=[]):
+    if not buf:
+        buf.append(torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev))
+    buf[0].fill_(1.0)
+
+
+def time_call(torch, dev, fn, reps=5):
+    """Median CUDA-event time (ms) of fn() with an L2 flush before each rep."""
+    ts = []
+    for _ in range(reps):
+        flush_l2(torch, dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def per_op_table(hc, torch, dev, wl):
+    """Every op at every stage vs the plain path, per field (Tab. 4 style split)."""
+    rows = []
+    for it in wl.items:
+        c = it["c"]
+        n = it["n"]
+        dq = hc.decompress(c, "q")
+        dp = hc.decompress(c, "p")
+        df = hc.decompress(c, "f")
+        t_dec = {s: time_call(torch, dev, lambda s=s, o=o: hc.decompress(c, s, out=o))
+                 for s, o in (("p", dp), ("q", dq), ("f", df))}
+        sp, sq, sf = hc.as_stage(c, "p", dp), hc.as_stage(c, "q", dq), hc.as_stage(c, "f", df)
+        for op, ax in op_list(len(it["shape"])):
+            r = {"field": "x".join(map(str, it["shape"])), "op": op + ("" if ax is None else str(ax))}
+            r["fused_ms"] = time_call(torch, dev, lambda: wl.run_op(it, op, ax))
+            if op in ("mean", "variance"):
+                r["fused_p_ms"] = time_call(torch, dev, lambda: wl.run_op(it, op, ax, level_q="p"))
+                r["unfused_p_ms"] = t_dec["p"] + time_call(torch, dev, lambda: wl.run_op(it, op, ax, src=sp))
+            r["unfused_q_ms"] = t_dec["q"] + time_call(torch, dev, lambda: wl.run_op(it, op, ax, src=sq))
+            r["plain_decompress_ms"] = t_dec["f"]
+            r["plain_op_ms"] = time_call(torch, dev, lambda: wl.run_op(it, op, ax, src=sf))
+            r["plain_ms"] = r["plain_decompress_ms"] + r["plain_op_ms"]
+            r["speedup_vs_plain"] = r["plain_ms"] / r["fused_ms"]
+            r["fused_gbs_orig"] = n * 4 / r["fused_ms"] / 1e6
+            rows.append(r)
+        del dq, dp, df
+    return rows
+
+
+# ---------------------------------------------------------------- roofline
+def read_profile_traffic(kernel_tag: str):
+    """dram bytes per launch recorded in profiles/<kernel_tag>.md, if the
+    CUDA sources are unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", kernel_tag + ".md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    h = re.search(r"csrc_sha256:\s*([0-9a-f]{16,64})", text)
+    if not m or not h or h.group(1) != csrc_hash()[: len(h.group(1))]:
+        return None
+    return float(m.group(1))
+
+
+def csrc_hash():
+    d = hashlib.sha256()
+    for sub in ("paper_2603_25206_gb300/csrc", "include"):
+        base = os.path.join(ROOT, sub)
+        for fn in sorted(os.listdir(base)):
+            d.update(fn.encode())
+            d.update(open(os.path.join(base, fn), "rb").read())
+    return d.hexdigest()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- CPU baseline
+def cpu_sample_run(field, shape, planes):
+    """The oracle, as it stands, on the first `planes` planes of a field: decode the
+    compressed sample and run every operation.  Returns (seconds, original bytes x ops)."""
+    import oracle
+
+    sub = np.ascontiguousarray(field[:planes])
+    s, eps = oracle.compress(sub, EB, True, BLOCK)
+    t0 = time.perf_counter()
+    dp = oracle.decode(s, "p")
+    oracle.mean_p_sum(dp, BLOCK)
+    q = oracle.decode(s, "q")
+    s1, s2 = oracle.sums_q(q)
+    oracle.finalize(q.size, s1, s2, eps)
+    for ax in range(sub.ndim):
+        oracle.stencil_q(q, oracle.KIND_DERIV, eps, ax)
+    oracle.stencil_q(q, oracle.KIND_GRADMAG, eps)
+    oracle.stencil_q(q, oracle.KIND_LAPLACIAN, eps)
+    dt = time.perf_counter() - t0
+    return dt, sub.size * 4 * len(op_list(sub.ndim))
+
+
+def cpu_baseline(fields, target_s=12.0):
+    shape, x = fields[1]  # the 512^3 field
+    planes = 8
+    dt, b = cpu_sample_run(x, shape, planes)
+    planes = int(max(8, min(shape[0], planes * target_s / max(dt, 1e-3))))
+    dt, b = cpu_sample_run(x, shape, planes)
+    return {"value": b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {planes} planes of the 512x512x512 field ({planes * 512 * 512} elements), "
+                      f"oracle decode to D_p and D_q + mean, variance, 3 derivatives, gradient magnitude, "
+                      f"Laplacian, single thread, {dt:.1f} s"}
+
+
+# -------------------------------------------------------------------- arms
+def run_reference(args):
+    """The oracle as the reference arm: K timed steps on a bounded sample."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+
+    shape = synth.PAPER_SHAPES[1]
+    x = synth.grf_field(shape, 1001)
+    planes = 16
+    for _ in range(args.warmup):
+        cpu_sample_run(x, shape, planes)
+    tot_t, tot_b = 0.0, 0
+    for _ in range(args.steps):
+        dt, b = cpu_sample_run(x, shape, planes)
+        tot_t += dt
+        tot_b += b
+    value = tot_b / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"first {planes} planes of 512^3"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {planes} planes of the 512x512x512 field per step, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    hc.lib()
+    fields = make_fields()
+    wl = Workload(hc, torch, dev, fields)
+    bytes_step = wl.orig_bytes_per_step
+    comp_bytes = sum(it["c"].nbytes for it in wl.items)
+
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    sampler = ClockSampler(smi_index(local))
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    events = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        wl.step(events)
+    t1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    ms = reduce_max(ms, world)
+    value = bytes_step * world / (ms * 1e-3) / 1e9
+
+    # per-kernel durations inside the timed region
+    per = {}
+    for fi, op, a, b in events:
+        d = per.setdefault(op, {"ms": 0.0, "bytes": 0.0, "launches": 0})
+        it = wl.items[fi]
+        d["ms"] += a.elapsed_time(b)
+        d["bytes"] += it["c"].nbytes + (it["n"] * 4 if op in ("derivative", "gradmag", "laplacian") else 64)
+        d["launches"] += 1
+    dom = max(per, key=lambda k: per[k]["ms"])
+    peak, peak_src = measured_peaks()
+    achieved = per[dom]["bytes"] / (per[dom]["ms"] * 1e-3) / 1e9
+    tag = f"stencil_{dom}_paper5" if dom != "mean" and dom != "variance" else f"reduce_{dom}_paper5"
+    traffic = read_profile_traffic(tag)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": per[dom]["bytes"] / per[dom]["launches"],
+                "avg_launch_ms": per[dom]["ms"] / per[dom]["launches"]}
+    share = {k: v["ms"] / sum(x["ms"] for x in per.values()) for k, v in per.items()}
+
+    # ---- plain path (full decompression to float32, then the same ops), same step structure
+    plain_ms = None
+    if not args.skip_plain:
+        df = {}
+        for fi, it in enumerate(wl.items):
+            df[fi] = torch.empty(it["shape"], dtype=torch.float32, device=dev)
+
+        def plain_step():
+            for fi, it in enumerate(wl.items):
+                hc.decompress(it["c"], "f", out=df[fi])
+                st = hc.as_stage(it["c"], "f", df[fi])
+                for op, ax in op_list(len(it["shape"])):
+                    wl.run_op(it, op, ax, src=st)
+
+        for _ in range(max(1, args.warmup)):
+            plain_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            plain_step()
+        b.record()
+        torch.cuda.synchronize()
+        plain_ms = reduce_max(a.elapsed_time(b) / args.steps, world)
+        del df
+
+    # ---- end to end through the ABI from pinned host memory
+    host_streams = [it["c"].stream.cpu().pin_memory() for it in wl.items]
+    dev_streams = [torch.empty_like(it["c"].stream) for it in wl.items]
+    e2e_items = [hc.Compressed(ds, it["c"].header, it["c"].nbytes) for ds, it in zip(dev_streams, wl.items)]
+    host_out = [torch.empty(it["shape"], dtype=torch.float32).pin_memory() for it in wl.items]
+    host_scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8).pin_memory()
+    d2h = 0
+
+    def e2e_step():
+        nonlocal d2h
+        d2h = 0
+        for fi, it in enumerate(wl.items):
+            dev_streams[fi].copy_(host_streams[fi], non_blocking=True)
+            for op, ax in op_list(len(it["shape"])):
+                if op == "mean":
+                    hc.mean(e2e_items[fi], level="p", out=it["scal"])
+                elif op == "variance":
+                    hc.variance(e2e_items[fi], level="q", out=it["scal"])
+                elif op == "derivative":
+                    hc.derivative(e2e_items[fi], ax, out=it["out"])
+                elif op == "gradmag":
+                    hc.gradmag(e2e_items[fi], out=it["out"])
+                else:
+                    hc.laplacian(e2e_items[fi], out=it["out"])
+                if op in ("mean", "variance"):
+                    host_scal.copy_(it["scal"], non_blocking=True)
+                    d2h += hc.SCALAR_BYTES
+                else:
+                    host_out[fi].copy_(it["out"], non_blocking=True)
+                    d2h += it["n"] * 4
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        e2e_step()
+    b.record()
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(a.elapsed_time(b) / args.steps, world)
+    e2e = {"value": bytes_step * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": comp_bytes,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    per_op = None
+    if args.per_op and rank == 0:
+        per_op = per_op_table(hc, torch, dev, wl)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "fields": ["x".join(map(str, it["shape"])) for it in wl.items],
+                           "eb_rel": EB, "block": BLOCK, "compressed_bytes": comp_bytes,
+                           "original_bytes_per_op_pass": sum(it["n"] * 4 for it in wl.items),
+                           "l2": "no flush: every step streams 5 compressed fields and writes ~6.9 GB of output "
+                                 "fields, far larger than the 129 MB L2",
+                           "parallelism": f"replicas x{world} (independent fields per GPU)"},
+                "plain": None if plain_ms is None else {
+                    "ms_per_step": plain_ms, "value": bytes_step * world / (plain_ms * 1e-3) / 1e9,
+                    "speedup_homomorphic_vs_plain": plain_ms / ms},
+                "e2e": e2e, "gpu_launches": wl.launches_per_step * args.steps,
+                "roofline": roofline, "kernel_time_share": share, "clocks": clocks}
+        if args.cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(fields)
+        if per_op is not None:
+            line["per_op"] = per_op
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--per-op", action="store_true", help="also time every op at every stage per field")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * hc.h -- C ABI of libhc.so: HSZp-style error-bounded compression with
+ * multi-stage partial decompression and homomorphic analytical operations on
+ * the intermediate stages, for one NVIDIA GB300 (sm_103a) GPU.
+ *
+ * Paper: "HSZ" (arXiv 2603.25206).  Problem statement, Section III-A: a
+ * compressor C, decompression stages D_1..D_m and operations Q_i run on the
+ * intermediate representation d^(i) = D_i(...D_1(c)).  Stages follow Table 1:
+ *   1 = D_m (block metadata), 2 = D_p (decorrelated integers),
+ *   3 = D_q (quantization integers), 4 = D_f (decompressed floats).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; all
+ *    other pointers are host pointers.  The library never allocates or frees
+ *    device memory: callers pass outputs and a workspace sized by the
+ *    *_workspace_bytes queries.  Device buffers must be 16-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls marked ASYNC only enqueue kernels on it and return; their
+ *    results are valid once the stream has been synchronised.  Calls marked
+ *    SYNC wait for the stream before returning.
+ *  - Return value: HC_OK, or an error code with a message readable through
+ *    hc_last_error() (thread-local).  Argument errors are detected on the
+ *    host before anything is enqueued.  A corrupt stream found by a kernel is
+ *    reported through a device status word: the `status` field of an
+ *    hc_scalar result, or the first int32 of the workspace for field results
+ *    (read it with hc_workspace_status).  Kernels never read outside the
+ *    stream, whatever its content.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef HC_H
+#define HC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HC_API __attribute__((visibility("default")))
+#else
+#define HC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HC_OK = 0,
+  HC_ERR_INVALID_ARG = 1,  /* bad pointer, size, shape, dtype, or mismatch with the stream header */
+  HC_ERR_RANGE = 2,        /* a code |q| >= 2^30, or a non-finite input value */
+  HC_ERR_CORRUPT = 3,      /* the stream violates its layout */
+  HC_ERR_UNSUPPORTED = 4,  /* operation not defined at this stage (Section V-B) */
+  HC_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+  HC_ERR_NOMEM = 6,        /* the caller's buffer or workspace is too small */
+  HC_ERR_TIMEOUT = 7       /* a bounded wait ran out */
+} hc_status;
+
+typedef enum { HC_F32 = 0, HC_F64 = 1, HC_I32 = 2, HC_I64 = 3 } hc_dtype;
+typedef enum { HC_EB_ABS = 0, HC_EB_REL = 1 } hc_eb_mode;
+typedef enum {
+  HC_STAGE_COMPRESSED = 0, /* the stream itself (operations fuse decoding in) */
+  HC_STAGE_M = 1,          /* D_m: heads int32[nb] */
+  HC_STAGE_P = 2,          /* D_p: int32[N], block head in each block's first slot */
+  HC_STAGE_Q = 3,          /* D_q: int32[N] */
+  HC_STAGE_F = 4           /* D_f: float32 or float64 [N] */
+} hc_stage_kind;
+
+/* Host copy of a stream header (layout: 256-byte little-endian header followed
+ * by widths u8[nb], heads i32[nb], chunk index u64[nchunks+1] and payload
+ * u32 words, each section 16-byte aligned; see the stream layout notes in the
+ * library source).  Filled by hc_read_header. */
+typedef struct hc_header {
+  int32_t dtype;     /* HC_F32 or HC_F64: the type of the original field */
+  int32_t ndim;      /* 1..3 */
+  int64_t dims[3];   /* (n0, n1, n2) row-major, n2 fastest, leading ones for ndim < 3 */
+  int32_t S;         /* block size, 1..4096 */
+  int32_t G;         /* blocks per chunk = max(1, 4096 / S) */
+  double eps;        /* absolute error bound used by the quantizer */
+  double eb;         /* error bound as given */
+  int32_t eb_mode;   /* HC_EB_ABS or HC_EB_REL */
+  uint32_t qmax;     /* max |q| over the field */
+  int64_t N, nb, nchunks, payload_words;
+  int64_t off_widths, off_heads, off_chunks, off_payload, total_bytes;
+  uint32_t wmax;     /* largest block width */
+  uint32_t reserved;
+} hc_header;
+
+/* An input of an operation: the stream (fused decode + operation) or a
+ * materialized stage array. */
+typedef struct hc_stage {
+  int32_t kind;          /* hc_stage_kind */
+  int32_t level;         /* COMPRESSED only: the stage the fused kernel works at,
+                            HC_STAGE_P (Section V, "Operation with D_p") or
+                            HC_STAGE_Q ("Operation with D_q") */
+  const void* d_data;    /* stream bytes, or the stage array */
+  const hc_header* hdr;  /* COMPRESSED: header of d_data (from hc_read_header) */
+  int32_t dtype;         /* F: HC_F32 / HC_F64 */
+  int32_t S;             /* P: block size of the stream the array came from */
+  int64_t n;             /* P / Q / F: element count */
+  uint32_t qmax;         /* P / Q: an upper bound on |q|, 0 if unknown */
+  uint32_t reserved;
+} hc_stage;
+
+/* Device-resident result of a statistic.  Integer stages carry the exact
+ * sums; the float stage (plain path) carries zeros there and exact = 0. */
+typedef struct hc_scalar {
+  double mean;       /* (sum q / N) * 2 eps                         (Section V-A) */
+  double variance;   /* (N s2 - s1^2) / (N (N-1)) * (2 eps)^2        (Eq. var_q) */
+  double std;        /* sqrt(variance)                               (Eq. var)   */
+  int64_t n;         /* N */
+  int64_t s1;        /* sum q, exact */
+  uint64_t s2_lo;    /* sum q^2, exact, low 64 bits  (variance only) */
+  uint64_t s2_hi;    /* sum q^2, high 64 bits */
+  int32_t status;    /* HC_OK or the error a kernel found */
+  int32_t exact;     /* 1 when s1 / s2 are exact integer sums */
+} hc_scalar;
+
+/* ----------------------------------------------------------- diagnostics */
+HC_API const char* hc_status_str(int status);
+HC_API const char* hc_last_error(void);
+HC_API int hc_version(void);
+
+/* ------------------------------------------------------------ sizing (host) */
+/* Upper bound of the stream size for N elements at block size S (every block
+ * at width 31).  Returns 0 for invalid arguments. */
+HC_API size_t hc_compress_bound(int64_t n, int S);
+/* Workspace of hc_compress for N elements at block size S. */
+HC_API size_t hc_compress_workspace_bytes(int64_t n, int S);
+/* Workspace of any hc_decompress_to_stage / hc_op_* call (one size fits all). */
+HC_API size_t hc_workspace_bytes(void);
+/* Bytes of a materialized stage (M, P, Q or F; F in the header's dtype). */
+HC_API size_t hc_stage_bytes(const hc_header* hdr, int kind);
+
+/* ------------------------------------------------------------ compression */
+/* C (Algorithm 1, Section IV): quantize q = floor(x / (2 eps) + 0.5) (IEEE
+ * double), partition into blocks of S, keep each block's first code as
+ * metadata, delta-code inside the block, and encode every block at the bit
+ * width of its largest |p| with the sign bits first.
+ *   d_x: float32 or float64 field (dtype), row-major dims[0..ndim).
+ *   eb, eb_mode: absolute bound, or eb * (max - min) (Section VI-B); a
+ *     constant field with a relative bound uses eps = eb.
+ *   d_stream, cap: output buffer of at least hc_compress_bound(N, S) bytes.
+ *   d_ws, ws_bytes: hc_compress_workspace_bytes(N, S) bytes of scratch.
+ *   out_bytes, hdr_out (host, hdr_out may be NULL): stream size and header.
+ * SYNC.  HC_ERR_RANGE if a code would not fit in (-2^30, 2^30). */
+HC_API int hc_compress(const void* d_x, int dtype, int ndim, const int64_t* dims, double eb, int eb_mode, int S,
+                void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
+                hc_header* hdr_out, void* stream);
+
+/* Encoder on given codes (the steps of Algorithm 1 after quantization):
+ * d_q int32[N] with |q| < 2^30; eps/eb/eb_mode/dtype are recorded in the
+ * header.  SYNC.  Produces the same bytes as hc_compress on the field. */
+HC_API int hc_compress_codes(const int32_t* d_q, int dtype, int ndim, const int64_t* dims, double eps, double eb,
+                      int eb_mode, int S, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
+                      size_t* out_bytes, hc_header* hdr_out, void* stream);
+
+/* Copy the 256-byte header of a device-resident stream to the host and
+ * validate it (magic, version, shape, section offsets, total size against
+ * `bytes`).  SYNC. */
+HC_API int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out, void* stream);
+
+/* ---------------------------------------------------------- decompression */
+/* D_i ... D_1 (Algorithm 2): decode the whole stream to stage `kind`:
+ *   HC_STAGE_M -> int32 heads[nb]; HC_STAGE_P -> int32[N] (head in each
+ *   block's first slot, so q is the in-block prefix sum); HC_STAGE_Q ->
+ *   int32[N]; HC_STAGE_F -> out_dtype HC_F32 ((float)q * (float)(2 eps)) or
+ *   HC_F64 ((double)q * 2 eps).
+ * d_out holds hc_stage_bytes(hdr, kind) bytes (8 per element for F64).
+ * ASYNC; corruption is reported in the workspace status word. */
+HC_API int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, int kind, void* d_out, int out_dtype,
+                           void* d_ws, size_t ws_bytes, void* stream);
+
+/* Status word a kernel left in a workspace (HC_OK when clean); resets it.  SYNC. */
+HC_API int hc_workspace_status(void* d_ws, void* stream);
+
+/* ------------------------------------------------------------- operations */
+/* Statistics (Section V-A).  `in`: the stream (fused; level P uses the
+ * block-weighted sum sum_i (S_b - i + 1) p_i without a prefix sum, level Q
+ * sums q) or a materialized P, Q or F array.  eps and dims must match the
+ * stream header for the fused form.  d_out: one hc_scalar in device memory.
+ * hc_op_mean fills mean (and s1); hc_op_variance and hc_op_std fill every
+ * field.  ASYNC. */
+HC_API int hc_op_mean(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
+               size_t ws_bytes, void* stream);
+HC_API int hc_op_variance(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
+                   size_t ws_bytes, void* stream);
+HC_API int hc_op_std(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
+              size_t ws_bytes, void* stream);
+
+/* Numerical differentiation (Section V-B, "Operation with D_q").  Inputs: the
+ * stream (fused, level Q), or a materialized Q or F array.  A stage-P input
+ * returns HC_ERR_UNSUPPORTED: a 1-D block partition does not keep the
+ * multidimensional layout (Section V-B).  `axis` is a user axis in
+ * [0, ndim), 0 the slowest.  d_out: N elements of out_dtype:
+ *   HC_F32 / HC_F64  the scaled value (eps * D, eps * |grad|, 2 eps * L),
+ *   HC_I64           the exact integer numerator (D or L; integer inputs).
+ * Interior derivative D = q[i+1] - q[i-1]; at a domain edge D = 2 (q[1] -
+ * q[0]) (one-sided); an axis of length 1 gives 0.  The Laplacian replicates
+ * edge values.  ASYNC. */
+HC_API int hc_op_derivative(const hc_stage* in, double eps, int ndim, const int64_t* dims, int axis, void* d_out,
+                     int out_dtype, void* d_ws, size_t ws_bytes, void* stream);
+HC_API int hc_op_gradmag(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+                  void* d_ws, size_t ws_bytes, void* stream);
+HC_API int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+                    void* d_ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HC_H */

@@ -69,10 +69,11 @@ def lib():
         L.orc_lap_q.argtypes = [vp, vp, vp]
         L.orc_stencil_q.argtypes = [vp, vp, i32, i32, dbl, vp]
         L.orc_stencil_f.argtypes = [vp, i32, vp, i32, i32, vp]
+        L.orc_stencil_at.argtypes = [vp, vp, i32, i32, dbl, vp, i64, vp, vp]
         for f in (L.orc_eps, L.orc_quantize, L.orc_compress, L.orc_compress_codes, L.orc_read_header,
                   L.orc_decode_p, L.orc_decode_q, L.orc_decode_m, L.orc_decode_f, L.orc_dequantize,
                   L.orc_sums_q, L.orc_mean_p_sum, L.orc_var_p_sums, L.orc_finalize, L.orc_stats_f,
-                  L.orc_deriv_q, L.orc_lap_q, L.orc_stencil_q, L.orc_stencil_f):
+                  L.orc_deriv_q, L.orc_lap_q, L.orc_stencil_q, L.orc_stencil_f, L.orc_stencil_at):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -270,3 +271,15 @@ def stencil_f(f: np.ndarray, kind: int, axis: int = 0) -> np.ndarray:
     _check(lib().orc_stencil_f(_ptr(f), _dtype_code(f), _ptr(d), kind, axis + 3 - f.ndim, _ptr(out)),
            "stencil_f")
     return out
+
+
+def stencil_at(q: np.ndarray, kind: int, eps: float, idx, axis: int = 0):
+    """(integer numerators, scaled values) at flat indices idx only."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    d = dims3(q.shape)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    num = np.empty(idx.size, np.int64)
+    val = np.empty(idx.size, np.float64)
+    _check(lib().orc_stencil_at(_ptr(q), _ptr(d), kind, axis + 3 - q.ndim, eps, _ptr(idx), idx.size, _ptr(num),
+                                _ptr(val)), "stencil_at")
+    return num, val

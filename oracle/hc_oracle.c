@@ -724,22 +724,57 @@ int orc_deriv_q(const int32_t *q, const int64_t *dims3, int axis, int64_t *D) {
   return ORC_OK;
 }
 
+/* integer Laplacian numerator at one point (replicated edges) */
+static int64_t lap_num(const int32_t *q, const int64_t *d, int64_t i0, int64_t i1, int64_t i2) {
+  int64_t c[3] = {i0, i1, i2};
+  int64_t center = q[idx3(d, i0, i1, i2)];
+  int64_t acc = 0;
+  for (int a = 0; a < 3; a++) {
+    int64_t m[3] = {i0, i1, i2}, p[3] = {i0, i1, i2};
+    m[a] = c[a] > 0 ? c[a] - 1 : 0;
+    p[a] = c[a] < d[a] - 1 ? c[a] + 1 : d[a] - 1;
+    acc += (int64_t)q[idx3(d, m[0], m[1], m[2])] + q[idx3(d, p[0], p[1], p[2])] - 2 * center;
+  }
+  return acc;
+}
+
 /* integer Laplacian numerators L */
 int orc_lap_q(const int32_t *q, const int64_t *d, int64_t *L) {
   for (int64_t i0 = 0; i0 < d[0]; i0++)
     for (int64_t i1 = 0; i1 < d[1]; i1++)
-      for (int64_t i2 = 0; i2 < d[2]; i2++) {
-        int64_t c[3] = {i0, i1, i2};
-        int64_t center = q[idx3(d, i0, i1, i2)];
-        int64_t acc = 0;
-        for (int a = 0; a < 3; a++) {
-          int64_t m[3] = {i0, i1, i2}, p[3] = {i0, i1, i2};
-          m[a] = c[a] > 0 ? c[a] - 1 : 0;
-          p[a] = c[a] < d[a] - 1 ? c[a] + 1 : d[a] - 1;
-          acc += (int64_t)q[idx3(d, m[0], m[1], m[2])] + q[idx3(d, p[0], p[1], p[2])] - 2 * center;
-        }
-        L[idx3(d, i0, i1, i2)] = acc;
+      for (int64_t i2 = 0; i2 < d[2]; i2++) L[idx3(d, i0, i1, i2)] = lap_num(q, d, i0, i1, i2);
+  return ORC_OK;
+}
+
+/* The same numerators and scaled values at m flat indices only (sampled
+ * checks of fields too large to evaluate whole):
+ *   kind 0: num = D along axis, val = eps * D
+ *   kind 1: num = 0,            val = eps * sqrt(sum_a D_a^2)
+ *   kind 2: num = L,            val = 2 eps * L */
+int orc_stencil_at(const int32_t *q, const int64_t *d, int kind, int axis, double eps, const int64_t *idx,
+                   int64_t m, int64_t *num, double *val) {
+  if (kind < 0 || kind > 2 || axis < 0 || axis > 2) return ORC_ERR_INVALID_ARG;
+  for (int64_t k = 0; k < m; k++) {
+    int64_t i = idx[k];
+    if (i < 0 || i >= d[0] * d[1] * d[2]) return ORC_ERR_INVALID_ARG;
+    int64_t i2 = i % d[2], i1 = (i / d[2]) % d[1], i0 = i / (d[1] * d[2]);
+    if (kind == 0) {
+      num[k] = deriv_num(q, d, i0, i1, i2, axis);
+      val[k] = (double)num[k] * eps;
+    } else if (kind == 1) {
+      u128 acc = 0;
+      for (int a = 0; a < 3; a++) {
+        int64_t t = deriv_num(q, d, i0, i1, i2, a);
+        uint64_t u = (uint64_t)(t < 0 ? -t : t);
+        acc += (u128)u * u;
       }
+      num[k] = 0;
+      val[k] = sqrt((double)acc) * eps;
+    } else {
+      num[k] = lap_num(q, d, i0, i1, i2);
+      val[k] = (double)num[k] * (2.0 * eps);
+    }
+  }
   return ORC_OK;
 }
 

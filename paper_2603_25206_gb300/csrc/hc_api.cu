@@ -1,0 +1,346 @@
+// hc_api.cu -- the extern "C" entry points of libhc.so (declared in
+// include/hc.h): argument checking, header parsing, dispatch to the kernels.
+// Nothing here allocates device memory.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "hc_internal.cuh"
+#include "hc_launch.h"
+
+namespace hc {
+
+static thread_local char g_last_error[512] = "";
+
+int fail(int code, const char* msg) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg ? msg : "");
+  return code;
+}
+
+static int64_t align16(int64_t x) { return (x + 15) & ~(int64_t)15; }
+
+int make_layout(int ndim, const int64_t* dims, int S, Layout* L) {
+  if (ndim < 1 || ndim > 3 || !dims) return fail(HC_ERR_INVALID_ARG, "ndim must be 1..3 with dims given");
+  if (S < 1 || S > kMaxS) return fail(HC_ERR_INVALID_ARG, "block size S must be in 1..4096");
+  L->dims[0] = L->dims[1] = L->dims[2] = 1;
+  int64_t n = 1;
+  for (int a = 0; a < ndim; ++a) {
+    if (dims[a] < 1) return fail(HC_ERR_INVALID_ARG, "every dimension must be >= 1");
+    if (n > ((int64_t)1 << 40) / dims[a]) return fail(HC_ERR_INVALID_ARG, "field too large");
+    n *= dims[a];
+    L->dims[3 - ndim + a] = dims[a];
+  }
+  L->N = n;
+  L->S = S;
+  L->nb = (n + S - 1) / S;
+  L->G = std::max(1, kChunkElems / S);
+  L->nchunks = (L->nb + L->G - 1) / L->G;
+  L->off_widths = kHeaderBytes;
+  L->off_heads = align16(L->off_widths + L->nb);
+  L->off_chunks = align16(L->off_heads + 4 * L->nb);
+  L->off_payload = align16(L->off_chunks + 8 * (L->nchunks + 1));
+  const int64_t nseg = (S + 31) / 32;
+  const int64_t wmax_words = nseg + ((int64_t)S * 31 + 31) / 32;
+  L->bound = (size_t)align16(L->off_payload + 4 * L->nb * wmax_words + 16);
+  return HC_OK;
+}
+
+size_t compress_ws_bytes(const Layout& L) { return 64 + 8 * (size_t)(L.nchunks + 1); }
+
+int device_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!sms[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = v > 0 ? v : 148;
+  }
+  return sms[dev];
+}
+
+int check_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    char buf[400];
+    std::snprintf(buf, sizeof(buf), "%s: kernel launch failed: %s", what, cudaGetErrorString(e));
+    return fail(HC_ERR_CUDA, buf);
+  }
+  return HC_OK;
+}
+
+int ensure_smem(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<std::pair<const void*, int>, int>> done;  // (kernel, device) -> largest size set
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (bytes <= 48 * 1024) return HC_OK;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(std::make_pair(kernel, dev), bytes);
+  if (done.count(key)) return HC_OK;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (bytes > optin) return fail(HC_ERR_UNSUPPORTED, "kernel needs more shared memory than the device offers");
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  done.insert(key);
+  return HC_OK;
+}
+
+static uint64_t le(const uint8_t* b, int off, int n) {
+  uint64_t v = 0;
+  for (int i = 0; i < n; ++i) v |= (uint64_t)b[off + i] << (8 * i);
+  return v;
+}
+
+int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st) {
+  if (!d_stream || !out) return fail(HC_ERR_INVALID_ARG, "null pointer");
+  if (bytes < (size_t)kHeaderBytes) return fail(HC_ERR_CORRUPT, "stream shorter than its header");
+  uint8_t b[kHeaderBytes];
+  if (cudaMemcpyAsync(b, d_stream, kHeaderBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  if (le(b, 0, 4) != kMagic || le(b, 4, 2) != (uint64_t)kVersion) return fail(HC_ERR_CORRUPT, "bad magic or version");
+  hc_header h;
+  std::memset(&h, 0, sizeof h);
+  h.dtype = (int32_t)le(b, 6, 1);
+  h.ndim = (int32_t)le(b, 7, 1);
+  for (int a = 0; a < 3; ++a) h.dims[a] = (int64_t)le(b, 8 + 8 * a, 8);
+  h.S = (int32_t)le(b, 32, 4);
+  h.G = (int32_t)le(b, 36, 4);
+  const uint64_t eps_bits = le(b, 40, 8), eb_bits = le(b, 48, 8);
+  std::memcpy(&h.eps, &eps_bits, 8);
+  std::memcpy(&h.eb, &eb_bits, 8);
+  h.eb_mode = (int32_t)le(b, 56, 4);
+  h.qmax = (uint32_t)le(b, 60, 4);
+  h.N = (int64_t)le(b, 64, 8);
+  h.nb = (int64_t)le(b, 72, 8);
+  h.nchunks = (int64_t)le(b, 80, 8);
+  h.payload_words = (int64_t)le(b, 88, 8);
+  h.off_widths = (int64_t)le(b, 96, 8);
+  h.off_heads = (int64_t)le(b, 104, 8);
+  h.off_chunks = (int64_t)le(b, 112, 8);
+  h.off_payload = (int64_t)le(b, 120, 8);
+  h.total_bytes = (int64_t)le(b, 128, 8);
+  h.wmax = (uint32_t)le(b, 136, 4);
+  if (h.dtype != HC_F32 && h.dtype != HC_F64) return fail(HC_ERR_CORRUPT, "bad dtype");
+  if (h.ndim < 1 || h.ndim > 3) return fail(HC_ERR_CORRUPT, "bad ndim");
+  for (int a = 0; a < 3 - h.ndim; ++a)
+    if (h.dims[a] != 1) return fail(HC_ERR_CORRUPT, "leading dims must be 1");
+  Layout L;
+  int64_t d[3];
+  for (int a = 0; a < h.ndim; ++a) d[a] = h.dims[3 - h.ndim + a];
+  if (make_layout(h.ndim, d, h.S, &L) != HC_OK) return fail(HC_ERR_CORRUPT, "bad shape or block size");
+  if (L.N != h.N || L.nb != h.nb || L.G != h.G || L.nchunks != h.nchunks || L.off_widths != h.off_widths ||
+      L.off_heads != h.off_heads || L.off_chunks != h.off_chunks || L.off_payload != h.off_payload)
+    return fail(HC_ERR_CORRUPT, "section offsets do not follow from the shape");
+  if (h.payload_words < 0 || h.total_bytes != align16(h.off_payload + 4 * h.payload_words + 16))
+    return fail(HC_ERR_CORRUPT, "payload size and total size disagree");
+  if ((size_t)h.total_bytes > bytes) return fail(HC_ERR_CORRUPT, "stream truncated");
+  if ((size_t)h.total_bytes > L.bound) return fail(HC_ERR_CORRUPT, "payload larger than any valid stream");
+  if (h.wmax > 31) return fail(HC_ERR_CORRUPT, "max width above 31");
+  if (!(h.eps > 0.0) || !std::isfinite(h.eps)) return fail(HC_ERR_CORRUPT, "bad eps");
+  if (h.qmax >= (1u << 30)) return fail(HC_ERR_CORRUPT, "max |q| out of range");
+  *out = h;
+  return HC_OK;
+}
+
+}  // namespace hc
+
+using namespace hc;
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Checks shared by every operation: workspace, shape and the stage view.
+static int check_op(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_ws, size_t ws_bytes,
+                    int64_t dims3[3]) {
+  if (!in || !in->d_data) return fail(HC_ERR_INVALID_ARG, "null stage");
+  if (!d_ws || ws_bytes < kOpWsBytes) return fail(HC_ERR_NOMEM, "workspace smaller than hc_workspace_bytes()");
+  if (!aligned16(d_ws) || !aligned16(in->d_data)) return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
+  Layout L;
+  int rc = make_layout(ndim, dims, 1, &L);
+  if (rc) return rc;
+  for (int a = 0; a < 3; ++a) dims3[a] = L.dims[a];
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HC_ERR_INVALID_ARG, "eps must be positive");
+  if (in->kind == HC_STAGE_COMPRESSED) {
+    const hc_header* h = in->hdr;
+    if (!h) return fail(HC_ERR_INVALID_ARG, "a stream input needs its header (hc_read_header)");
+    if (h->ndim != ndim || h->eps != eps) return fail(HC_ERR_INVALID_ARG, "eps / ndim differ from the stream header");
+    for (int a = 0; a < 3; ++a)
+      if (h->dims[a] != dims3[a]) return fail(HC_ERR_INVALID_ARG, "dims differ from the stream header");
+    if (in->level != HC_STAGE_P && in->level != HC_STAGE_Q)
+      return fail(HC_ERR_INVALID_ARG, "fused level must be HC_STAGE_P or HC_STAGE_Q");
+    return HC_OK;
+  }
+  if (in->n != L.N) return fail(HC_ERR_INVALID_ARG, "stage length differs from prod(dims)");
+  if (in->kind == HC_STAGE_P && (in->S < 1 || in->S > kMaxS)) return fail(HC_ERR_INVALID_ARG, "P input needs S");
+  if (in->kind == HC_STAGE_F && in->dtype != HC_F32 && in->dtype != HC_F64)
+    return fail(HC_ERR_INVALID_ARG, "F input dtype");
+  if (in->kind == HC_STAGE_M) return fail(HC_ERR_UNSUPPORTED, "HSZp-style metadata supports no operation (Section V)");
+  if (in->kind < HC_STAGE_M || in->kind > HC_STAGE_F) return fail(HC_ERR_INVALID_ARG, "unknown stage kind");
+  return HC_OK;
+}
+
+extern "C" {
+
+const char* hc_status_str(int status) {
+  switch (status) {
+    case HC_OK:
+      return "ok";
+    case HC_ERR_INVALID_ARG:
+      return "invalid argument";
+    case HC_ERR_RANGE:
+      return "value out of range";
+    case HC_ERR_CORRUPT:
+      return "corrupt stream";
+    case HC_ERR_UNSUPPORTED:
+      return "unsupported";
+    case HC_ERR_CUDA:
+      return "CUDA error";
+    case HC_ERR_NOMEM:
+      return "buffer too small";
+    case HC_ERR_TIMEOUT:
+      return "timeout";
+    default:
+      return "unknown status";
+  }
+}
+
+const char* hc_last_error(void) { return g_last_error; }
+
+int hc_version(void) { return kVersion; }
+
+size_t hc_compress_bound(int64_t n, int S) {
+  Layout L;
+  if (make_layout(1, &n, S, &L) != HC_OK) return 0;
+  return L.bound;
+}
+
+size_t hc_compress_workspace_bytes(int64_t n, int S) {
+  Layout L;
+  if (make_layout(1, &n, S, &L) != HC_OK) return 0;
+  return compress_ws_bytes(L);
+}
+
+size_t hc_workspace_bytes(void) { return kOpWsBytes; }
+
+size_t hc_stage_bytes(const hc_header* hdr, int kind) {
+  if (!hdr) return 0;
+  switch (kind) {
+    case HC_STAGE_COMPRESSED:
+      return (size_t)hdr->total_bytes;
+    case HC_STAGE_M:
+      return 4 * (size_t)hdr->nb;
+    case HC_STAGE_P:
+    case HC_STAGE_Q:
+      return 4 * (size_t)hdr->N;
+    case HC_STAGE_F:
+      return (hdr->dtype == HC_F64 ? 8 : 4) * (size_t)hdr->N;
+    default:
+      return 0;
+  }
+}
+
+int hc_compress(const void* d_x, int dtype, int ndim, const int64_t* dims, double eb, int eb_mode, int S,
+                void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out,
+                void* stream) {
+  return compress_impl(d_x, dtype == HC_F64 ? 1 : 0, dtype, ndim, dims, eb, 0.0, eb_mode, S, d_stream, cap, d_ws,
+                       ws_bytes, out_bytes, hdr_out, as_stream(stream));
+}
+
+int hc_compress_codes(const int32_t* d_q, int dtype, int ndim, const int64_t* dims, double eps, double eb,
+                      int eb_mode, int S, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
+                      hc_header* hdr_out, void* stream) {
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HC_ERR_INVALID_ARG, "eps must be positive and finite");
+  return compress_impl(d_q, 2, dtype, ndim, dims, eb, eps, eb_mode, S, d_stream, cap, d_ws, ws_bytes, out_bytes,
+                       hdr_out, as_stream(stream));
+}
+
+int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out, void* stream) {
+  return read_header_impl(d_stream, bytes, hdr_out, as_stream(stream));
+}
+
+int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, int kind, void* d_out, int out_dtype,
+                           void* d_ws, size_t ws_bytes, void* stream) {
+  if (!hdr || !d_stream || !d_out) return fail(HC_ERR_INVALID_ARG, "null pointer");
+  if (!d_ws || ws_bytes < kOpWsBytes) return fail(HC_ERR_NOMEM, "workspace smaller than hc_workspace_bytes()");
+  if (!aligned16(d_stream) || !aligned16(d_out) || !aligned16(d_ws))
+    return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
+  if (kind < HC_STAGE_M || kind > HC_STAGE_F) return fail(HC_ERR_INVALID_ARG, "kind must be M, P, Q or F");
+  if (kind == HC_STAGE_F && out_dtype != HC_F32 && out_dtype != HC_F64)
+    return fail(HC_ERR_INVALID_ARG, "F output is HC_F32 or HC_F64");
+  return decode_impl(hdr, d_stream, kind, d_out, out_dtype, d_ws, as_stream(stream));
+}
+
+int hc_workspace_status(void* d_ws, void* stream) {
+  if (!d_ws) return fail(HC_ERR_INVALID_ARG, "null workspace");
+  int v = 0, zero = 0;
+  cudaStream_t st = as_stream(stream);
+  if (cudaMemcpyAsync(&v, d_ws, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_ws, &zero, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  return v;
+}
+
+static int stats(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
+                 size_t ws_bytes, void* stream, int what) {
+  int64_t dims3[3];
+  int rc = check_op(in, eps, ndim, dims, d_ws, ws_bytes, dims3);
+  if (rc) return rc;
+  if (!d_out) return fail(HC_ERR_INVALID_ARG, "null output");
+  if (in->kind == HC_STAGE_COMPRESSED)
+    return reduce_stream_impl(in->hdr, in->d_data, in->level, what, d_out, d_ws, as_stream(stream));
+  return reduce_array_impl(in, eps, what, d_out, d_ws, as_stream(stream));
+}
+
+int hc_op_mean(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
+               size_t ws_bytes, void* stream) {
+  return stats(in, eps, ndim, dims, d_out, d_ws, ws_bytes, stream, RED_MEAN);
+}
+
+int hc_op_variance(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
+                   size_t ws_bytes, void* stream) {
+  return stats(in, eps, ndim, dims, d_out, d_ws, ws_bytes, stream, RED_VAR);
+}
+
+int hc_op_std(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
+              size_t ws_bytes, void* stream) {
+  return stats(in, eps, ndim, dims, d_out, d_ws, ws_bytes, stream, RED_VAR);
+}
+
+static int stencil(const hc_stage* in, double eps, int ndim, const int64_t* dims, int op, int axis, void* d_out,
+                   int out_dtype, void* d_ws, size_t ws_bytes, void* stream) {
+  int64_t dims3[3];
+  int rc = check_op(in, eps, ndim, dims, d_ws, ws_bytes, dims3);
+  if (rc) return rc;
+  if (!d_out || !aligned16(d_out)) return fail(HC_ERR_INVALID_ARG, "output must be a 16-byte aligned device buffer");
+  if (op == ST_DERIV && (axis < 0 || axis >= ndim)) return fail(HC_ERR_INVALID_ARG, "axis out of range");
+  const int axis3 = axis + 3 - ndim;
+  if (in->kind == HC_STAGE_COMPRESSED) {
+    if (in->level == HC_STAGE_P)
+      return fail(HC_ERR_UNSUPPORTED,
+                  "stage-2 differentiation is not defined for a 1-D block partition (Section V-B)");
+    return stencil_stream_impl(in->hdr, in->d_data, op, axis3, d_out, out_dtype, d_ws, as_stream(stream));
+  }
+  return stencil_array_impl(in, dims3, eps, op, axis3, d_out, out_dtype, d_ws, as_stream(stream));
+}
+
+int hc_op_derivative(const hc_stage* in, double eps, int ndim, const int64_t* dims, int axis, void* d_out,
+                     int out_dtype, void* d_ws, size_t ws_bytes, void* stream) {
+  return stencil(in, eps, ndim, dims, ST_DERIV, axis, d_out, out_dtype, d_ws, ws_bytes, stream);
+}
+
+int hc_op_gradmag(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+                  void* d_ws, size_t ws_bytes, void* stream) {
+  return stencil(in, eps, ndim, dims, ST_GRADMAG, 0, d_out, out_dtype, d_ws, ws_bytes, stream);
+}
+
+int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+                    void* d_ws, size_t ws_bytes, void* stream) {
+  return stencil(in, eps, ndim, dims, ST_LAPLACIAN, 0, d_out, out_dtype, d_ws, ws_bytes, stream);
+}
+
+}  // extern "C"

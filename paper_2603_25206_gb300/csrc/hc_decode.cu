@@ -1,0 +1,206 @@
+// hc_decode.cu -- multi-stage partial decompression (Algorithm 2) of a whole
+// stream to a materialized stage: D_m (heads), D_p, D_q or D_f.
+//
+// A persistent grid walks the stream two chunks (about 8192 elements) at a
+// time.  Per tile the CTA stages the widths, scans them into word offsets and
+// copies the tile's payload into shared memory with 16-byte loads; each thread
+// then decodes one 32-element segment serially (bit unpack, sign, in-block
+// prefix sum) into a padded shared tile, which is written out with coalesced
+// 16-byte stores.
+#include <cstdint>
+
+#include "hc_internal.cuh"
+#include "hc_launch.h"
+
+namespace hc {
+
+__device__ __forceinline__ int pidx(int r) { return r + (r >> 5); }
+// padded output tile: 33 words per 32 elements (conflict-free serial writes)
+__host__ __device__ inline int decode_out_words(int tb, int S) { return round4(((tb * S + 31) / 32) * 33 + 4); }
+
+template <class OutT>
+struct Conv;
+template <>
+struct Conv<int32_t> {
+  __device__ static int32_t f(int32_t q, float, double) { return q; }
+};
+template <>
+struct Conv<float> {
+  // float32 reconstruction: (float)q * (float)(2 eps) in float32 arithmetic
+  __device__ static float f(int32_t q, float te, double) { return __fmul_rn(__int2float_rn(q), te); }
+};
+template <>
+struct Conv<double> {
+  __device__ static double f(int32_t q, float, double te) { return __dmul_rn((double)q, te); }
+};
+
+// KIND: HC_STAGE_P, HC_STAGE_Q or HC_STAGE_F.  SMALL: S <= 32 (one segment per block).
+template <int KIND, class OutT, bool SMALL>
+__global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restrict__ out, float te_f, double te_d,
+                                                      int64_t ntiles, int stage_words, int* err) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_warp[32];
+  __shared__ int s_flag;
+  const int tb = kTileChunks * s.G;  // blocks per tile
+  const int out_words = decode_out_words(tb, s.S);
+  const TileSmem L = tile_smem(tb, 0, s.S, s.wmax, out_words + (SMALL ? 0 : tb * s.nseg));
+  uint32_t* s_stage = smem;
+  uint32_t* s_off = smem + L.off;
+  int32_t* s_out = reinterpret_cast<int32_t*>(smem + L.extra);
+  int32_t* s_tot = s_out + out_words;
+  uint8_t* s_w = reinterpret_cast<uint8_t*>(smem + L.w);
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b0 = t * tb;
+    const int nblk = (int)min((int64_t)tb, s.nb - b0);
+    const int64_t e0 = b0 * s.S;
+    const int elems = (int)min((int64_t)nblk * s.S, s.N - e0);
+    TileView tv;
+    if (!load_blocks(s, b0, nblk, s_w, s_off, s_stage, stage_words, s_warp, &s_flag, err, tv)) continue;
+
+    const int nsegs = SMALL ? nblk : nblk * s.nseg;
+    for (int seg = tid; seg < nsegs; seg += nt) {
+      const int bl = SMALL ? seg : seg / s.nseg;
+      const int j = SMALL ? 0 : seg - bl * s.nseg;
+      const int64_t b = b0 + bl;
+      const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
+      const int cnt = min(32, Sb - 32 * j);
+      if (cnt <= 0) continue;
+      const uint32_t w = tv.w[bl];
+      const int32_t head = __ldg(s.heads + b);
+      const int r0 = bl * s.S + 32 * j;
+      int32_t acc = (KIND == HC_STAGE_P) ? 0 : (SMALL ? head : 0);
+      if (w == 0) {
+        for (int i = 0; i < cnt; ++i)
+          s_out[pidx(r0 + i)] = (KIND == HC_STAGE_P) ? ((j == 0 && i == 0) ? head : 0) : acc;
+      } else {
+        const uint32_t* blk = tv.words + tv.off[bl];
+        const uint32_t sw = blk[j];
+        unpack_any(blk + s.nseg + j * w, sw, w, cnt, [&](int i, int32_t p) {
+          if (KIND == HC_STAGE_P) {
+            s_out[pidx(r0 + i)] = (j == 0 && i == 0) ? head : p;
+          } else {
+            acc += p;
+            s_out[pidx(r0 + i)] = acc;
+          }
+        });
+      }
+      if (!SMALL && KIND != HC_STAGE_P) s_tot[seg] = acc;
+    }
+    __syncthreads();
+    if (!SMALL && KIND != HC_STAGE_P) {
+      // carry of segment j: head + totals of the block's earlier segments
+      for (int seg = tid; seg < nsegs; seg += nt) {
+        const int bl = seg / s.nseg, j = seg - bl * s.nseg;
+        const int64_t b = b0 + bl;
+        const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
+        const int cnt = min(32, Sb - 32 * j);
+        if (cnt <= 0) continue;
+        int32_t c = __ldg(s.heads + b);
+        for (int jj = 0; jj < j; ++jj) c += s_tot[bl * s.nseg + jj];
+        const int r0 = bl * s.S + 32 * j;
+        for (int i = 0; i < cnt; ++i) s_out[pidx(r0 + i)] += c;
+      }
+      __syncthreads();
+    }
+    // coalesced write-out
+    OutT* dst = out + e0;
+    constexpr int V = 16 / sizeof(OutT);
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+      const int nv = elems / V;
+      for (int v = tid; v < nv; v += nt) {
+        union {
+          uint4 u;
+          OutT e[V];
+        } pk;
+#pragma unroll
+        for (int k = 0; k < V; ++k) pk.e[k] = Conv<OutT>::f(s_out[pidx(v * V + k)], te_f, te_d);
+        reinterpret_cast<uint4*>(dst)[v] = pk.u;
+      }
+      done = nv * V;
+    }
+    for (int i = done + tid; i < elems; i += nt) dst[i] = Conv<OutT>::f(s_out[pidx(i)], te_f, te_d);
+    __syncthreads();
+  }
+}
+
+__global__ void k_copy_heads(const int32_t* __restrict__ heads, int32_t* __restrict__ out, int64_t nb) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __ldg(heads + i);
+}
+
+DevStream dev_stream(const hc_header* h, const void* d_stream) {
+  const uint8_t* b = reinterpret_cast<const uint8_t*>(d_stream);
+  DevStream s;
+  s.widths = b + h->off_widths;
+  s.heads = reinterpret_cast<const int32_t*>(b + h->off_heads);
+  s.chunks = reinterpret_cast<const uint64_t*>(b + h->off_chunks);
+  s.payload = reinterpret_cast<const uint32_t*>(b + h->off_payload);
+  s.N = h->N;
+  s.nb = h->nb;
+  s.nchunks = h->nchunks;
+  s.payload_words = h->payload_words;
+  s.S = h->S;
+  s.G = h->G;
+  s.nseg = (h->S + 31) / 32;
+  s.wmax = (int)h->wmax;
+  return s;
+}
+
+static TileSmem decode_layout(const hc_header* h, bool small) {
+  const int tb = kTileChunks * h->G;
+  const int nseg = (h->S + 31) / 32;
+  return tile_smem(tb, 0, h->S, (int)h->wmax, decode_out_words(tb, h->S) + (small ? 0 : tb * nseg));
+}
+
+template <int KIND, class OutT, bool SMALL>
+static int launch_decode(const hc_header* h, const void* d_stream, void* d_out, int* err, cudaStream_t st) {
+  const DevStream s = dev_stream(h, d_stream);
+  const TileSmem L = decode_layout(h, SMALL);
+  const int smem = 4 * L.words;
+  auto kern = k_decode<KIND, OutT, SMALL>;
+  int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  if (rc) return rc;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  per_sm = std::max(per_sm, 1);
+  const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm);
+  const double te = 2.0 * h->eps;
+  kern<<<grid, kThreads, smem, st>>>(s, reinterpret_cast<OutT*>(d_out), (float)te, te, ntiles, L.stage_words,
+                                     err);
+  return check_launch("decompress_to_stage");
+}
+
+template <int KIND, class OutT>
+static int launch_decode_s(const hc_header* h, const void* d_stream, void* d_out, int* err, cudaStream_t st) {
+  if (h->S <= 32) return launch_decode<KIND, OutT, true>(h, d_stream, d_out, err, st);
+  return launch_decode<KIND, OutT, false>(h, d_stream, d_out, err, st);
+}
+
+int decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,
+                cudaStream_t st) {
+  int* err = &reinterpret_cast<OpWs*>(d_ws)->status;
+  switch (kind) {
+    case HC_STAGE_M: {
+      const uint8_t* b = reinterpret_cast<const uint8_t*>(d_stream);
+      const int grid = (int)std::min<int64_t>(ceil_div(h->nb, kThreads), 4096);
+      k_copy_heads<<<grid, kThreads, 0, st>>>(reinterpret_cast<const int32_t*>(b + h->off_heads),
+                                              reinterpret_cast<int32_t*>(d_out), h->nb);
+      return check_launch("decompress_to_stage(M)");
+    }
+    case HC_STAGE_P:
+      return launch_decode_s<HC_STAGE_P, int32_t>(h, d_stream, d_out, err, st);
+    case HC_STAGE_Q:
+      return launch_decode_s<HC_STAGE_Q, int32_t>(h, d_stream, d_out, err, st);
+    case HC_STAGE_F:
+      if (out_dtype == HC_F64) return launch_decode_s<HC_STAGE_F, double>(h, d_stream, d_out, err, st);
+      return launch_decode_s<HC_STAGE_F, float>(h, d_stream, d_out, err, st);
+    default:
+      return fail(HC_ERR_INVALID_ARG, "unknown stage");
+  }
+}
+
+}  // namespace hc

@@ -1,0 +1,79 @@
+// hc_launch.h -- host-side declarations shared by the translation units of
+// libhc.so (argument checking, layout arithmetic, launch helpers and the
+// per-file entry points the C ABI dispatches to).
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hc.h"
+
+namespace hc {
+
+// Geometry of a stream for a given shape and block size.
+struct Layout {
+  int64_t dims[3];  // padded to 3 axes with leading ones
+  int64_t N, nb, nchunks;
+  int S, G;
+  int64_t off_widths, off_heads, off_chunks, off_payload;
+  size_t bound;  // stream bytes with every block at width 31
+};
+
+// Record a failure message (thread-local) and return `code`.
+int fail(int code, const char* msg);
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int make_layout(int ndim, const int64_t* dims, int S, Layout* L);
+size_t compress_ws_bytes(const Layout& L);
+
+int device_sms();
+int check_launch(const char* what);
+// Raise a kernel's dynamic shared-memory limit once per (kernel, size).
+int ensure_smem(const void* kernel, int bytes);
+
+int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st);
+
+int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int64_t* dims, double eb,
+                  double eps_given, int eb_mode, int S, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
+                  size_t* out_bytes, hc_header* hdr_out, cudaStream_t st);
+
+// Workspace of decompression and operations: a status word, the
+// last-block ticket of the reductions and the per-CTA partial results.
+struct Partial {
+  long long s1;
+  unsigned long long s2_lo, s2_hi;
+  int err;
+  int pad;
+};
+struct OpWs {
+  int status;
+  unsigned int ticket;
+  int pad[14];
+};
+constexpr int kMaxGrid = 4096;
+constexpr size_t kOpWsBytes = sizeof(OpWs) + sizeof(Partial) * kMaxGrid;
+
+inline Partial* ws_partials(void* d_ws) {
+  return reinterpret_cast<Partial*>(reinterpret_cast<char*>(d_ws) + sizeof(OpWs));
+}
+
+// Per-file entry points (inputs already validated by the ABI layer).
+int decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,
+                cudaStream_t st);
+
+enum ReduceWhat { RED_MEAN = 0, RED_VAR = 1 };
+int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out,
+                       void* d_ws, cudaStream_t st);
+int reduce_array_impl(const hc_stage* in, double eps, int what, hc_scalar* d_out, void* d_ws, cudaStream_t st);
+
+enum StencilOp { ST_DERIV = 0, ST_GRADMAG = 1, ST_LAPLACIAN = 2 };
+int stencil_stream_impl(const hc_header* h, const void* d_stream, int op, int axis3, void* d_out, int out_dtype,
+                        void* d_ws, cudaStream_t st);
+int stencil_array_impl(const hc_stage* in, const int64_t* dims3, double eps, int op, int axis3, void* d_out,
+                       int out_dtype, void* d_ws, cudaStream_t st);
+
+}  // namespace hc

@@ -1,0 +1,648 @@
+// hc_reduce.cu -- homomorphic statistics (Section V-A): mean, variance and
+// standard deviation.
+//
+// Fused forms read the compressed stream and never materialize a stage:
+//   level 2 (Operation with D_p):  sum q = sum_b sum_i (S_b - i + 1) p_i,
+//                                  the block-weighted sum, no prefix sum;
+//   level 3 (Operation with D_q):  q rebuilt in registers (the eta
+//                                  accumulator of Section V-A), s1 = sum q,
+//                                  s2 = sum q^2.
+// Array forms read a materialized D_p, D_q or D_f (the unfused and the plain
+// "decompress, then operate" paths).
+//
+// Integer sums are exact: int64 for s1, 128-bit for s2.  Each CTA writes one
+// partial; the last CTA to finish (ticket counter in the workspace, reset by
+// that CTA) adds the partials and applies the final scaling of Eq. var_q:
+//   mean = (s1 / N) * 2 eps,
+//   var  = ((N s2 - s1^2) / (N (N - 1))) * (2 eps)^2   (exact 128-bit numerator).
+#include <cstdint>
+#include <type_traits>
+
+#include "hc_internal.cuh"
+#include "hc_launch.h"
+
+namespace hc {
+
+DevStream dev_stream(const hc_header* h, const void* d_stream);
+
+__device__ __forceinline__ int pidx(int r) { return r + (r >> 5); }
+
+// words of the per-segment moment arrays: totals (int32), sums (int64) and,
+// for the variance, sums of squares (128-bit)
+__host__ __device__ inline int seg_moment_words(int nsegmax, bool var) {
+  return round4(nsegmax) + round4(2 * nsegmax) + (var ? 4 * nsegmax : 0);
+}
+// padded value tile (33 words per 32 elements)
+__host__ __device__ inline int padded_words(int elems) { return round4(((elems + 31) / 32) * 33 + 4); }
+
+// ---------------------------------------------------------------- finishing
+__device__ inline void finalize_int(hc_scalar* out, int64_t n, long long s1, u128 s2, bool var, double two_eps,
+                                    int err) {
+  out->n = n;
+  out->s1 = s1;
+  out->s2_lo = var ? (unsigned long long)s2 : 0ull;
+  out->s2_hi = var ? (unsigned long long)(s2 >> 64) : 0ull;
+  out->status = err;
+  out->exact = 1;
+  out->mean = (__ll2double_rn(s1) / (double)n) * two_eps;
+  double v = __longlong_as_double(0x7ff8000000000000ll);  // NaN: not computed / undefined
+  if (var && n >= 2) {
+    const i128 num = (i128)n * (i128)s2 - (i128)s1 * (i128)s1;
+    const double den = (double)n * (double)(n - 1);
+    v = (i128_to_double(num) / den) * (two_eps * two_eps);
+  }
+  out->variance = v;
+  out->std = sqrt(v);
+}
+
+// CTA sum of (s1, s2, err), one partial per CTA, and the last CTA's finish.
+template <class Fin>
+__device__ inline void reduce_and_finish(long long s1, u128 s2, int err, Partial* parts, unsigned* ticket,
+                                         Fin&& fin) {
+  __shared__ long long r_s1[32];
+  __shared__ u128 r_s2[32];
+  __shared__ int r_err[32];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += shfl_down_u128(s2, o);
+    err |= __shfl_down_sync(0xffffffffu, err, o);
+  }
+  if (lane == 0) {
+    r_s1[wid] = s1;
+    r_s2[wid] = s2;
+    r_err[wid] = err;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    long long a = 0;
+    u128 b = 0;
+    int e = 0;
+    for (int i = 0; i < nw; ++i) {
+      a += r_s1[i];
+      b += r_s2[i];
+      e |= r_err[i];
+    }
+    Partial p;
+    p.s1 = a;
+    p.s2_lo = (unsigned long long)b;
+    p.s2_hi = (unsigned long long)(b >> 64);
+    p.err = e;
+    p.pad = 0;
+    parts[blockIdx.x] = p;
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  long long a = 0;
+  u128 b = 0;
+  int e = 0;
+  for (int i = tid; i < (int)gridDim.x; i += blockDim.x) {
+    a += __ldcg(&parts[i].s1);
+    b += ((u128)__ldcg(&parts[i].s2_hi) << 64) | (u128)__ldcg(&parts[i].s2_lo);
+    e |= __ldcg(&parts[i].err);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += shfl_down_u128(b, o);
+    e |= __shfl_down_sync(0xffffffffu, e, o);
+  }
+  if (lane == 0) {
+    r_s1[wid] = a;
+    r_s2[wid] = b;
+    r_err[wid] = e;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    long long ta = 0;
+    u128 tb = 0;
+    int te = 0;
+    for (int i = 0; i < nw; ++i) {
+      ta += r_s1[i];
+      tb += r_s2[i];
+      te |= r_err[i];
+    }
+    fin(ta, tb, te);
+    *ticket = 0;
+  }
+}
+
+// ------------------------------------------------------- fused, from stream
+// ACC: 0 narrow (max |q| < 2^12: 32-bit per-segment sums), 1 mid (< 2^26:
+// 64-bit per-segment sums), 2 wide (128-bit per element).
+template <int LEVEL, int ACC, bool VAR, bool SMALL>
+__global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t ntiles, int stage_words,
+                                                             Partial* parts, unsigned* ticket, hc_scalar* out,
+                                                             double two_eps) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_warp[32];
+  __shared__ int s_flag;
+  __shared__ int s_err;
+  const int tb = kTileChunks * s.G;
+  const int nsegmax = SMALL ? tb : tb * s.nseg;
+  constexpr bool seg_arrays = (!SMALL && LEVEL == 3);
+  const TileSmem L = tile_smem(tb, 0, s.S, s.wmax, seg_arrays ? seg_moment_words(nsegmax, VAR) : 0);
+  uint32_t* s_stage = smem;
+  uint32_t* s_off = smem + L.off;
+  // per-segment local moments for S > 32 at level 3
+  int32_t* s_T = reinterpret_cast<int32_t*>(smem + L.extra);
+  long long* s_a1 = reinterpret_cast<long long*>(smem + L.extra + round4(nsegmax));
+  u128* s_a2 = reinterpret_cast<u128*>(smem + L.extra + round4(nsegmax) + round4(2 * nsegmax));
+  uint8_t* s_w = reinterpret_cast<uint8_t*>(smem + L.w);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) s_err = 0;
+  long long S1 = 0;
+  u128 S2 = 0;
+  unsigned long long S2n = 0;  // narrow: 64-bit per-thread sum of q^2
+
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b0 = t * tb;
+    const int nblk = (int)min((int64_t)tb, s.nb - b0);
+    TileView tv;
+    if (!load_blocks(s, b0, nblk, s_w, s_off, s_stage, stage_words, s_warp, &s_flag, &s_err, tv)) continue;
+    const int nsegs = SMALL ? nblk : nblk * s.nseg;
+    for (int seg = tid; seg < nsegs; seg += nt) {
+      const int bl = SMALL ? seg : seg / s.nseg;
+      const int j = SMALL ? 0 : seg - bl * s.nseg;
+      const int64_t b = b0 + bl;
+      const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
+      const int cnt = min(32, Sb - 32 * j);
+      if (cnt <= 0) {
+        if (seg_arrays) {
+          s_T[seg] = 0;
+          s_a1[seg] = 0;
+          if (VAR) s_a2[seg] = 0;
+        }
+        continue;
+      }
+      const uint32_t w = tv.w[bl];
+      const int32_t head = __ldg(s.heads + b);
+      const uint32_t* blk = tv.words + tv.off[bl];
+      if constexpr (LEVEL == 2) {
+        // Section V-A, stage 2: sum_k (S_b - k) p_k with the head as p_0
+        using A = typename std::conditional<ACC == 0, int32_t, long long>::type;
+        A sa = 0, sb = 0;
+        if (w) unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
+            sa += p;
+            sb += (A)i * p;
+          });
+        long long c = (long long)(Sb - 32 * j) * (long long)sa - (long long)sb;
+        if (j == 0) c += (long long)Sb * head;
+        S1 += c;
+      } else if constexpr (SMALL) {
+        // Section V-A, stage 3 / eta accumulator: q rebuilt from the head
+        if constexpr (ACC == 0) {
+          int32_t q = head, a1 = 0;
+          uint32_t a2 = 0;
+          if (w) {
+            unpack_any(blk + s.nseg, blk[0], w, cnt, [&](int i, int32_t p) {
+              q += p;
+              a1 += q;
+              if (VAR) a2 += (uint32_t)(q * q);
+            });
+          } else {
+            a1 = cnt * head;
+            if (VAR) a2 = (uint32_t)cnt * (uint32_t)(head * head);
+          }
+          S1 += a1;
+          if (VAR) S2n += a2;
+        } else if constexpr (ACC == 1) {
+          int32_t q = head;
+          long long a1 = 0;
+          unsigned long long a2 = 0;
+          if (w) {
+            unpack_any(blk + s.nseg, blk[0], w, cnt, [&](int i, int32_t p) {
+              q += p;
+              a1 += q;
+              if (VAR) a2 += (unsigned long long)((long long)q * q);
+            });
+          } else {
+            a1 = (long long)cnt * head;
+            if (VAR) a2 = (unsigned long long)cnt * (unsigned long long)((long long)head * head);
+          }
+          S1 += a1;
+          if (VAR) S2 += a2;
+        } else {
+          int32_t q = head;
+          long long a1 = 0;
+          u128 a2 = 0;
+          if (w) {
+            unpack_any(blk + s.nseg, blk[0], w, cnt, [&](int i, int32_t p) {
+              q += p;
+              a1 += q;
+              if (VAR) a2 += (u128)(unsigned long long)((long long)q * q);
+            });
+          } else {
+            a1 = (long long)cnt * head;
+            if (VAR) a2 = (u128)cnt * (u128)(unsigned long long)((long long)head * head);
+          }
+          S1 += a1;
+          if (VAR) S2 += a2;
+        }
+      } else {
+        // S > 32: local prefix P (relative to the segment's carry), its sums
+        // and the segment total; the carry is added once all totals are known.
+        int32_t P = 0;
+        long long a1 = 0;
+        u128 a2 = 0;
+        if (w) {
+          if constexpr (ACC == 0) {
+            int32_t l1 = 0;
+            uint32_t l2 = 0;
+            unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
+              P += p;
+              l1 += P;
+              if (VAR) l2 += (uint32_t)(P * P);
+            });
+            a1 = l1;
+            a2 = l2;
+          } else if constexpr (ACC == 1) {
+            unsigned long long l2 = 0;
+            unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
+              P += p;
+              a1 += P;
+              if (VAR) l2 += (unsigned long long)((long long)P * P);
+            });
+            a2 = l2;
+          } else {
+            unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
+              P += p;
+              a1 += P;
+              if (VAR) a2 += (u128)(unsigned long long)((long long)P * P);
+            });
+          }
+        }
+        s_T[seg] = P;
+        s_a1[seg] = a1;
+        if (VAR) s_a2[seg] = a2;
+      }
+    }
+    if constexpr (!SMALL && LEVEL == 3) {
+      __syncthreads();
+      for (int seg = tid; seg < nsegs; seg += nt) {
+        const int bl = seg / s.nseg, j = seg - bl * s.nseg;
+        const int64_t b = b0 + bl;
+        const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
+        const int cnt = min(32, Sb - 32 * j);
+        if (cnt <= 0) continue;
+        long long c = __ldg(s.heads + b);
+        for (int jj = 0; jj < j; ++jj) c += s_T[bl * s.nseg + jj];
+        const long long a1 = s_a1[seg];
+        S1 += (long long)cnt * c + a1;
+        if (VAR) {
+          const i128 v = (i128)cnt * c * c + (i128)2 * c * a1 + (i128)s_a2[seg];
+          S2 += (u128)v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (ACC == 0 && VAR) S2 += S2n;
+  __syncthreads();
+  const int err = s_err;
+  reduce_and_finish(S1, S2, err, parts, ticket, [&](long long a, u128 b, int e) {
+    finalize_int(out, s.N, a, b, VAR, two_eps, e);
+  });
+}
+
+// ------------------------------------------------------- materialized D_q
+template <bool VAR>
+__global__ void __launch_bounds__(kThreads) k_reduce_q_array(const int32_t* __restrict__ q, int64_t n,
+                                                              Partial* parts, unsigned* ticket, hc_scalar* out,
+                                                              double two_eps) {
+  long long S1 = 0;
+  u128 S2 = 0;
+  const int64_t nv = ((reinterpret_cast<uintptr_t>(q) & 15u) == 0) ? n / 4 : 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const int4 x = __ldg(reinterpret_cast<const int4*>(q) + v);
+    S1 += (long long)x.x + x.y + x.z + x.w;
+    if (VAR)
+      S2 += (u128)((unsigned long long)((long long)x.x * x.x) + (unsigned long long)((long long)x.y * x.y)) +
+            (u128)((unsigned long long)((long long)x.z * x.z) + (unsigned long long)((long long)x.w * x.w));
+  }
+  for (int64_t i = nv * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long x = __ldg(q + i);
+    S1 += x;
+    if (VAR) S2 += (u128)(unsigned long long)(x * x);
+  }
+  reduce_and_finish(S1, S2, 0, parts, ticket, [&](long long a, u128 b, int e) {
+    finalize_int(out, n, a, b, VAR, two_eps, e);
+  });
+}
+
+// ------------------------------------------------------- materialized D_p
+// Tile of 2 chunks' worth of blocks staged into shared memory; one thread per
+// 32-element segment applies the stage-2 weights (mean) or rebuilds q with
+// the running accumulator (variance).
+template <bool VAR, bool SMALL>
+__global__ void __launch_bounds__(kThreads) k_reduce_p_array(const int32_t* __restrict__ dp, int64_t n, int S,
+                                                              int tb, Partial* parts, unsigned* ticket,
+                                                              hc_scalar* out, double two_eps) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int nseg = (S + 31) / 32;
+  const int nsegmax = SMALL ? tb : tb * nseg;
+  int32_t* s_v = reinterpret_cast<int32_t*>(smem);
+  const int vwords = padded_words(tb * S);
+  int32_t* s_T = s_v + vwords;
+  long long* s_a1 = reinterpret_cast<long long*>(smem + vwords + round4(nsegmax));
+  u128* s_a2 = reinterpret_cast<u128*>(smem + vwords + round4(nsegmax) + round4(2 * nsegmax));
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t nb = (n + S - 1) / S;
+  const int64_t ntiles = (nb + tb - 1) / tb;
+  long long S1 = 0;
+  u128 S2 = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t b0 = t * tb;
+    const int nblk = (int)min((int64_t)tb, nb - b0);
+    const int64_t e0 = b0 * S;
+    const int elems = (int)min((int64_t)nblk * S, n - e0);
+    for (int i = tid; i < elems; i += nt) s_v[pidx(i)] = __ldg(dp + e0 + i);
+    __syncthreads();
+    const int nsegs = SMALL ? nblk : nblk * nseg;
+    for (int seg = tid; seg < nsegs; seg += nt) {
+      const int bl = SMALL ? seg : seg / nseg;
+      const int j = SMALL ? 0 : seg - bl * nseg;
+      const int Sb = (int)min((int64_t)S, n - (b0 + bl) * S);
+      const int cnt = min(32, Sb - 32 * j);
+      const int r0 = bl * S + 32 * j;
+      if (!VAR) {
+        long long c = 0;
+        for (int i = 0; i < cnt; ++i) c += (long long)(Sb - 32 * j - i) * s_v[pidx(r0 + i)];
+        S1 += c;
+        continue;
+      }
+      long long P = 0, a1 = 0;
+      u128 a2 = 0;
+      for (int i = 0; i < cnt; ++i) {
+        P += s_v[pidx(r0 + i)];
+        a1 += P;
+        a2 += (u128)(unsigned long long)(P * P);
+      }
+      if (SMALL) {
+        S1 += a1;
+        S2 += a2;
+      } else {
+        s_T[seg] = cnt > 0 ? (int32_t)P : 0;
+        s_a1[seg] = cnt > 0 ? a1 : 0;
+        s_a2[seg] = cnt > 0 ? a2 : 0;
+      }
+    }
+    if (VAR && !SMALL) {
+      __syncthreads();
+      for (int seg = tid; seg < nsegs; seg += nt) {
+        const int bl = seg / nseg, j = seg - bl * nseg;
+        const int Sb = (int)min((int64_t)S, n - (b0 + bl) * S);
+        const int cnt = min(32, Sb - 32 * j);
+        if (cnt <= 0) continue;
+        long long c = 0;
+        for (int jj = 0; jj < j; ++jj) c += s_T[bl * nseg + jj];
+        const long long a1 = s_a1[seg];
+        S1 += (long long)cnt * c + a1;
+        S2 += (u128)((i128)cnt * c * c + (i128)2 * c * a1 + (i128)s_a2[seg]);
+      }
+    }
+    __syncthreads();
+  }
+  reduce_and_finish(S1, S2, 0, parts, ticket, [&](long long a, u128 b, int e) {
+    finalize_int(out, n, a, b, VAR, two_eps, e);
+  });
+}
+
+// ------------------------------------------------------- materialized D_f
+// The plain path: statistics of a float array.  Each thread keeps compensated
+// float32 sums of (x - c) and (x - c)^2 around its first element c; the
+// per-thread (count, mean, M2) triples are merged in double with the
+// pairwise update of Chan et al.  No integer information is used.
+template <class T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
+  const T y = v - c;
+  const T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+struct Moments {
+  double n, mean, m2;
+};
+__device__ __forceinline__ Moments merge(Moments a, Moments b) {
+  if (a.n == 0) return b;
+  if (b.n == 0) return a;
+  Moments r;
+  r.n = a.n + b.n;
+  const double d = b.mean - a.mean;
+  r.mean = a.mean + d * (b.n / r.n);
+  r.m2 = a.m2 + b.m2 + d * d * (a.n * b.n / r.n);
+  return r;
+}
+__device__ __forceinline__ Moments shfl_down_m(Moments m, int o) {
+  Moments r;
+  r.n = __shfl_down_sync(0xffffffffu, m.n, o);
+  r.mean = __shfl_down_sync(0xffffffffu, m.mean, o);
+  r.m2 = __shfl_down_sync(0xffffffffu, m.m2, o);
+  return r;
+}
+
+template <class T, bool VAR>
+__global__ void __launch_bounds__(kThreads) k_reduce_f_array(const T* __restrict__ f, int64_t n, Partial* parts,
+                                                              unsigned* ticket, hc_scalar* out) {
+  __shared__ Moments r_m[32];
+  __shared__ int s_last;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T s = 0, cs = 0, s2 = 0, c2 = 0;
+  const T c = i0 < n ? f[i0] : T(0);
+  double cnt = 0;
+  for (int64_t i = i0; i < n; i += stride) {
+    const T d = f[i] - c;
+    kahan_add(s, cs, d);
+    if (VAR) kahan_add(s2, c2, d * d);
+    cnt += 1.0;
+  }
+  Moments m;
+  m.n = cnt;
+  m.mean = cnt > 0 ? (double)c + (double)s / cnt : 0.0;
+  m.m2 = cnt > 0 ? (double)s2 - (double)s * (double)s / cnt : 0.0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = merge(m, shfl_down_m(m, o));
+  if (lane == 0) r_m[wid] = m;
+  __syncthreads();
+  if (tid == 0) {
+    Moments a = r_m[0];
+    for (int k = 1; k < nw; ++k) a = merge(a, r_m[k]);
+    Partial p;
+    p.s1 = __double_as_longlong(a.n);
+    p.s2_lo = (unsigned long long)__double_as_longlong(a.mean);
+    p.s2_hi = (unsigned long long)__double_as_longlong(a.m2);
+    p.err = 0;
+    p.pad = 0;
+    parts[blockIdx.x] = p;
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || tid != 0) return;
+  __threadfence();
+  Moments a{0, 0, 0};
+  for (int k = 0; k < (int)gridDim.x; ++k) {
+    Moments b;
+    b.n = __longlong_as_double(__ldcg(&parts[k].s1));
+    b.mean = __longlong_as_double((long long)__ldcg(&parts[k].s2_lo));
+    b.m2 = __longlong_as_double((long long)__ldcg(&parts[k].s2_hi));
+    a = merge(a, b);
+  }
+  out->n = n;
+  out->s1 = 0;
+  out->s2_lo = 0;
+  out->s2_hi = 0;
+  out->status = 0;
+  out->exact = 0;
+  out->mean = a.mean;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  out->variance = (VAR && n >= 2) ? a.m2 / (double)(n - 1) : nan;
+  out->std = sqrt(out->variance);
+  *ticket = 0;
+}
+
+// --------------------------------------------------------------------- host
+static int acc_class(uint32_t qmax) {
+  if (qmax == 0) return 2;  // unknown bound: widest accumulators
+  if (qmax < (1u << 12)) return 0;
+  if (qmax < (1u << 26)) return 1;
+  return 2;
+}
+
+template <int LEVEL, int ACC, bool VAR, bool SMALL>
+static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st) {
+  const DevStream s = dev_stream(h, d_stream);
+  const int tb = kTileChunks * h->G;
+  const int nseg = (h->S + 31) / 32;
+  const int nsegmax = SMALL ? tb : tb * nseg;
+  const TileSmem L = tile_smem(tb, 0, h->S, (int)h->wmax, (!SMALL && LEVEL == 3) ? seg_moment_words(nsegmax, VAR) : 0);
+  const int bytes = 4 * L.words;
+  const int stage = L.stage_words;
+  auto kern = k_reduce_stream<LEVEL, ACC, VAR, SMALL>;
+  int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
+  if (rc) return rc;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, bytes);
+  per_sm = std::max(per_sm, 1);
+  const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm), kMaxGrid);
+  OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
+  kern<<<grid, kThreads, bytes, st>>>(s, ntiles, stage, ws_partials(d_ws), &ws->ticket, d_out, 2.0 * h->eps);
+  return check_launch("reduce (fused)");
+}
+
+template <int LEVEL, bool VAR, bool SMALL>
+static int launch_stream_acc(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st) {
+  switch (acc_class(h->qmax)) {
+    case 0:
+      return launch_stream<LEVEL, 0, VAR, SMALL>(h, d_stream, d_out, d_ws, st);
+    case 1:
+      return launch_stream<LEVEL, (LEVEL == 2 ? 2 : 1), VAR, SMALL>(h, d_stream, d_out, d_ws, st);
+    default:
+      return launch_stream<LEVEL, 2, VAR, SMALL>(h, d_stream, d_out, d_ws, st);
+  }
+}
+
+int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, void* d_ws,
+                       cudaStream_t st) {
+  const bool small = h->S <= 32;
+  if (level == HC_STAGE_P && what == RED_MEAN)
+    return small ? launch_stream_acc<2, false, true>(h, d_stream, d_out, d_ws, st)
+                 : launch_stream_acc<2, false, false>(h, d_stream, d_out, d_ws, st);
+  // the stage-2 standard deviation of Section V-A rebuilds q with the eta
+  // accumulator: the same arithmetic as stage 3
+  if (what == RED_MEAN)
+    return small ? launch_stream_acc<3, false, true>(h, d_stream, d_out, d_ws, st)
+                 : launch_stream_acc<3, false, false>(h, d_stream, d_out, d_ws, st);
+  return small ? launch_stream_acc<3, true, true>(h, d_stream, d_out, d_ws, st)
+               : launch_stream_acc<3, true, false>(h, d_stream, d_out, d_ws, st);
+}
+
+template <class K>
+static int persistent_grid(K kern, int smem, int64_t work) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  per_sm = std::max(per_sm, 1);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(work, (int64_t)device_sms() * per_sm), kMaxGrid));
+}
+
+int reduce_array_impl(const hc_stage* in, double eps, int what, hc_scalar* d_out, void* d_ws, cudaStream_t st) {
+  OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
+  Partial* parts = ws_partials(d_ws);
+  const int64_t n = in->n;
+  const bool var = what == RED_VAR;
+  if (in->kind == HC_STAGE_Q) {
+    const int32_t* q = reinterpret_cast<const int32_t*>(in->d_data);
+    if (var) {
+      const int grid = persistent_grid(k_reduce_q_array<true>, 0, ceil_div(n, kThreads * 4));
+      k_reduce_q_array<true><<<grid, kThreads, 0, st>>>(q, n, parts, &ws->ticket, d_out, 2.0 * eps);
+    } else {
+      const int grid = persistent_grid(k_reduce_q_array<false>, 0, ceil_div(n, kThreads * 4));
+      k_reduce_q_array<false><<<grid, kThreads, 0, st>>>(q, n, parts, &ws->ticket, d_out, 2.0 * eps);
+    }
+    return check_launch("reduce (D_q)");
+  }
+  if (in->kind == HC_STAGE_P) {
+    const int S = in->S;
+    const int G = std::max(1, kChunkElems / S);
+    const int tb = kTileChunks * G;
+    const int nseg = (S + 31) / 32;
+    const bool small = S <= 32;
+    const int nsegmax = small ? tb : tb * nseg;
+    const int bytes = 4 * (padded_words(tb * S) + ((var && !small) ? seg_moment_words(nsegmax, true) : 0));
+    const int32_t* dp = reinterpret_cast<const int32_t*>(in->d_data);
+    const int64_t ntiles = ceil_div(ceil_div(n, S), tb);
+    const void* kern;
+    int rc;
+#define HC_LAUNCH_P(VAR, SMALL)                                                                          \
+  {                                                                                                      \
+    kern = reinterpret_cast<const void*>(k_reduce_p_array<VAR, SMALL>);                                  \
+    rc = ensure_smem(kern, bytes);                                                                       \
+    if (rc) return rc;                                                                                   \
+    const int grid = persistent_grid(k_reduce_p_array<VAR, SMALL>, bytes, ntiles);                       \
+    k_reduce_p_array<VAR, SMALL><<<grid, kThreads, bytes, st>>>(dp, n, S, tb, parts, &ws->ticket, d_out, \
+                                                                 2.0 * eps);                             \
+  }
+    if (var && small) HC_LAUNCH_P(true, true)
+    else if (var) HC_LAUNCH_P(true, false)
+    else if (small) HC_LAUNCH_P(false, true)
+    else HC_LAUNCH_P(false, false)
+#undef HC_LAUNCH_P
+    return check_launch("reduce (D_p)");
+  }
+  if (in->kind == HC_STAGE_F) {
+    if (in->dtype == HC_F64) {
+      const double* f = reinterpret_cast<const double*>(in->d_data);
+      if (var) {
+        const int grid = persistent_grid(k_reduce_f_array<double, true>, 0, ceil_div(n, kThreads));
+        k_reduce_f_array<double, true><<<grid, kThreads, 0, st>>>(f, n, parts, &ws->ticket, d_out);
+      } else {
+        const int grid = persistent_grid(k_reduce_f_array<double, false>, 0, ceil_div(n, kThreads));
+        k_reduce_f_array<double, false><<<grid, kThreads, 0, st>>>(f, n, parts, &ws->ticket, d_out);
+      }
+    } else {
+      const float* f = reinterpret_cast<const float*>(in->d_data);
+      if (var) {
+        const int grid = persistent_grid(k_reduce_f_array<float, true>, 0, ceil_div(n, kThreads));
+        k_reduce_f_array<float, true><<<grid, kThreads, 0, st>>>(f, n, parts, &ws->ticket, d_out);
+      } else {
+        const int grid = persistent_grid(k_reduce_f_array<float, false>, 0, ceil_div(n, kThreads));
+        k_reduce_f_array<float, false><<<grid, kThreads, 0, st>>>(f, n, parts, &ws->ticket, d_out);
+      }
+    }
+    return check_launch("reduce (D_f)");
+  }
+  return fail(HC_ERR_INVALID_ARG, "statistics take a stream or a P, Q or F array");
+}
+
+}  // namespace hc

@@ -1,0 +1,365 @@
+"""ctypes binding of libhc.so (include/hc.h).
+
+Argument marshalling only: torch provides device memory and the current CUDA
+stream; every step of compression, decompression and the homomorphic
+operations runs in the library's CUDA kernels.  There is no fallback: if the
+library or a GPU is missing, loading fails with an error.
+
+Two layers:
+* ``lib()`` returns the raw ctypes functions named exactly as in hc.h
+  (``hc_compress``, ``hc_decompress_to_stage``, ``hc_op_mean`` ...).
+* ``compress`` / ``decompress`` / ``mean`` / ``variance`` / ``derivative`` /
+  ``gradmag`` / ``laplacian`` allocate outputs with torch and call them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhc.so")
+
+HC_OK, HC_ERR_INVALID_ARG, HC_ERR_RANGE, HC_ERR_CORRUPT, HC_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+HC_ERR_CUDA, HC_ERR_NOMEM, HC_ERR_TIMEOUT = 5, 6, 7
+HC_F32, HC_F64, HC_I32, HC_I64 = 0, 1, 2, 3
+HC_EB_ABS, HC_EB_REL = 0, 1
+HC_STAGE_COMPRESSED, HC_STAGE_M, HC_STAGE_P, HC_STAGE_Q, HC_STAGE_F = 0, 1, 2, 3, 4
+
+STAGES = {"m": HC_STAGE_M, "p": HC_STAGE_P, "q": HC_STAGE_Q, "f": HC_STAGE_F}
+
+# Names of every function declared in include/hc.h (checked by the tests).
+ABI_FUNCTIONS = (
+    "hc_status_str", "hc_last_error", "hc_version", "hc_compress_bound", "hc_compress_workspace_bytes",
+    "hc_workspace_bytes", "hc_stage_bytes", "hc_compress", "hc_compress_codes", "hc_read_header",
+    "hc_decompress_to_stage", "hc_workspace_status", "hc_op_mean", "hc_op_variance", "hc_op_std",
+    "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian",
+)
+
+
+class HcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libhc status {status}: {msg}")
+        self.status = status
+
+
+class HcHeader(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("ndim", ctypes.c_int32), ("dims", ctypes.c_int64 * 3),
+                ("S", ctypes.c_int32), ("G", ctypes.c_int32), ("eps", ctypes.c_double), ("eb", ctypes.c_double),
+                ("eb_mode", ctypes.c_int32), ("qmax", ctypes.c_uint32), ("N", ctypes.c_int64),
+                ("nb", ctypes.c_int64), ("nchunks", ctypes.c_int64), ("payload_words", ctypes.c_int64),
+                ("off_widths", ctypes.c_int64), ("off_heads", ctypes.c_int64), ("off_chunks", ctypes.c_int64),
+                ("off_payload", ctypes.c_int64), ("total_bytes", ctypes.c_int64), ("wmax", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    @property
+    def shape(self):
+        return tuple(int(d) for d in self.dims)[3 - self.ndim:]
+
+
+class HcStage(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("d_data", ctypes.c_void_p),
+                ("hdr", ctypes.POINTER(HcHeader)), ("dtype", ctypes.c_int32), ("S", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("qmax", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+SCALAR_BYTES = 64
+_SCALAR_DTYPE = np.dtype([("mean", "<f8"), ("variance", "<f8"), ("std", "<f8"), ("n", "<i8"), ("s1", "<i8"),
+                          ("s2_lo", "<u8"), ("s2_hi", "<u8"), ("status", "<i4"), ("exact", "<i4")])
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libhc.so (build it first with paper_2603_25206_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, sz, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "hc_status_str": ([i32], ctypes.c_char_p),
+            "hc_last_error": ([], ctypes.c_char_p),
+            "hc_version": ([], i32),
+            "hc_compress_bound": ([i64, i32], sz),
+            "hc_compress_workspace_bytes": ([i64, i32], sz),
+            "hc_workspace_bytes": ([], sz),
+            "hc_stage_bytes": ([P(HcHeader), i32], sz),
+            "hc_compress": ([vp, i32, i32, P(ctypes.c_int64), dbl, i32, i32, vp, sz, vp, sz, P(sz), P(HcHeader), vp],
+                            i32),
+            "hc_compress_codes": ([vp, i32, i32, P(ctypes.c_int64), dbl, dbl, i32, i32, vp, sz, vp, sz, P(sz),
+                                   P(HcHeader), vp], i32),
+            "hc_read_header": ([vp, sz, P(HcHeader), vp], i32),
+            "hc_decompress_to_stage": ([P(HcHeader), vp, i32, vp, i32, vp, sz, vp], i32),
+            "hc_workspace_status": ([vp, vp], i32),
+            "hc_op_mean": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, vp, sz, vp], i32),
+            "hc_op_variance": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, vp, sz, vp], i32),
+            "hc_op_std": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, vp, sz, vp], i32),
+            "hc_op_derivative": ([P(HcStage), dbl, i32, P(ctypes.c_int64), i32, vp, i32, vp, sz, vp], i32),
+            "hc_op_gradmag": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
+            "hc_op_laplacian": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != HC_OK:
+        raise HcError(rc, lib().hc_last_error().decode())
+
+
+# ------------------------------------------------------------ torch plumbing
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dims(shape):
+    arr = (ctypes.c_int64 * 3)()
+    for i, d in enumerate(shape):
+        arr[i] = int(d)
+    return arr
+
+
+_ws_cache: dict = {}
+
+
+def workspace(device=None, stream=None):
+    """Zero-initialised operation workspace, one per (device, stream)."""
+    torch = _torch()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    key = (dev.index, s.cuda_stream)
+    ws = _ws_cache.get(key)
+    if ws is None:
+        ws = torch.zeros(int(lib().hc_workspace_bytes()), dtype=torch.uint8, device=dev)
+        _ws_cache[key] = ws
+    return ws
+
+
+@dataclass
+class Compressed:
+    """A device-resident stream with its host-side header."""
+    stream: "object"  # torch.uint8 tensor (possibly larger than nbytes)
+    header: HcHeader
+    nbytes: int
+
+    @property
+    def shape(self):
+        return self.header.shape
+
+    @property
+    def eps(self):
+        return self.header.eps
+
+    @property
+    def dtype(self):
+        return "float64" if self.header.dtype == HC_F64 else "float32"
+
+    def stage(self, level: str = "q") -> HcStage:
+        st = HcStage()
+        st.kind = HC_STAGE_COMPRESSED
+        st.level = STAGES[level]
+        st.d_data = self.stream.data_ptr()
+        st.hdr = ctypes.pointer(self.header)
+        return st
+
+
+@dataclass
+class StageArray:
+    """A materialized stage: kind 'p', 'q' or 'f' (torch tensor on the GPU)."""
+    kind: str
+    data: "object"
+    shape: tuple
+    eps: float
+    S: int = 0
+    qmax: int = 0
+
+    def stage(self) -> HcStage:
+        torch = _torch()
+        st = HcStage()
+        st.kind = STAGES[self.kind]
+        st.d_data = self.data.data_ptr()
+        st.dtype = HC_F64 if self.data.dtype == torch.float64 else HC_F32
+        st.S = self.S
+        st.n = int(np.prod(self.shape))
+        st.qmax = self.qmax
+        return st
+
+
+def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None) -> Compressed:
+    """C (Algorithm 1) of a float32/float64 CUDA tensor."""
+    torch = _torch()
+    if not x.is_cuda:
+        raise ValueError("compress expects a CUDA tensor")
+    x = x.contiguous()
+    dtype = HC_F64 if x.dtype == torch.float64 else HC_F32
+    if x.dtype not in (torch.float32, torch.float64):
+        raise TypeError("fields are float32 or float64")
+    L = lib()
+    cap = int(L.hc_compress_bound(x.numel(), S))
+    out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    ws = torch.empty(int(L.hc_compress_workspace_bytes(x.numel(), S)), dtype=torch.uint8, device=x.device)
+    nbytes = ctypes.c_size_t()
+    hdr = HcHeader()
+    _check(L.hc_compress(ctypes.c_void_p(x.data_ptr()), dtype, x.dim(), _dims(x.shape), eb,
+                         HC_EB_REL if rel else HC_EB_ABS, S, ctypes.c_void_p(out.data_ptr()), cap,
+                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(nbytes), ctypes.byref(hdr),
+                         _stream_ptr(stream)))
+    return Compressed(out, hdr, nbytes.value)
+
+
+def compress_codes(q, eps: float, S: int = 32, dtype: str = "float32", eb=None, rel=False, stream=None) -> Compressed:
+    """Encode given int32 codes (CUDA tensor)."""
+    torch = _torch()
+    q = q.contiguous()
+    L = lib()
+    cap = int(L.hc_compress_bound(q.numel(), S))
+    out = torch.empty(cap, dtype=torch.uint8, device=q.device)
+    ws = torch.empty(int(L.hc_compress_workspace_bytes(q.numel(), S)), dtype=torch.uint8, device=q.device)
+    nbytes = ctypes.c_size_t()
+    hdr = HcHeader()
+    _check(L.hc_compress_codes(ctypes.c_void_p(q.data_ptr()), HC_F64 if dtype == "float64" else HC_F32, q.dim(),
+                               _dims(q.shape), eps, eps if eb is None else eb, HC_EB_REL if rel else HC_EB_ABS, S,
+                               ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                               ctypes.byref(nbytes), ctypes.byref(hdr), _stream_ptr(stream)))
+    return Compressed(out, hdr, nbytes.value)
+
+
+def from_stream(stream_tensor, stream=None) -> Compressed:
+    """Wrap a device-resident stream (uint8 tensor): reads and checks its header."""
+    hdr = HcHeader()
+    _check(lib().hc_read_header(ctypes.c_void_p(stream_tensor.data_ptr()), stream_tensor.numel(),
+                                ctypes.byref(hdr), _stream_ptr(stream)))
+    return Compressed(stream_tensor, hdr, int(hdr.total_bytes))
+
+
+def decompress(c: Compressed, stage: str = "f", out=None, out_dtype=None, stream=None):
+    """D_i..D_1 (Algorithm 2) to stage 'm', 'p', 'q' or 'f'."""
+    torch = _torch()
+    kind = STAGES[stage]
+    if stage == "m":
+        shape, tdt = (c.header.nb,), torch.int32
+    elif stage in ("p", "q"):
+        shape, tdt = c.shape, torch.int32
+    else:
+        f64 = (out_dtype == "float64") if out_dtype else (c.header.dtype == HC_F64)
+        shape, tdt = c.shape, (torch.float64 if f64 else torch.float32)
+    if out is None:
+        out = torch.empty(shape, dtype=tdt, device=c.stream.device)
+    odt = HC_F64 if out.dtype == torch.float64 else HC_F32
+    ws = workspace(c.stream.device, stream)
+    _check(lib().hc_decompress_to_stage(ctypes.byref(c.header), ctypes.c_void_p(c.stream.data_ptr()), kind,
+                                        ctypes.c_void_p(out.data_ptr()), odt, ctypes.c_void_p(ws.data_ptr()),
+                                        ws.numel(), _stream_ptr(stream)))
+    return out
+
+
+def as_stage(c: Compressed, stage: str, data) -> StageArray:
+    """Describe a materialized stage of c for the operations."""
+    return StageArray(stage, data, c.shape, c.eps, c.header.S, int(c.header.qmax))
+
+
+def _input(inp, level):
+    if isinstance(inp, Compressed):
+        return inp.stage(level), inp.eps, inp.shape, inp.stream.device
+    return inp.stage(), inp.eps, inp.shape, inp.data.device
+
+
+def parse_scalar(buf) -> dict:
+    """hc_scalar (64 bytes, any tensor/bytes) -> dict with exact s2 as a Python int."""
+    raw = np.frombuffer(bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf),
+                        dtype=_SCALAR_DTYPE, count=1)[0]
+    d = {k: raw[k].item() for k in _SCALAR_DTYPE.names}
+    d["s2"] = (int(d.pop("s2_hi")) << 64) | int(d.pop("s2_lo"))
+    return d
+
+
+def _stat(fn_name, inp, level, out, stream):
+    torch = _torch()
+    st, eps, shape, dev = _input(inp, level)
+    if out is None:
+        out = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=dev)
+    ws = workspace(dev, stream)
+    _check(getattr(lib(), fn_name)(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return out
+
+
+def mean(inp, level: str = "p", out=None, stream=None):
+    """Homomorphic mean; returns the 64-byte device hc_scalar (see parse_scalar)."""
+    return _stat("hc_op_mean", inp, level, out, stream)
+
+
+def variance(inp, level: str = "q", out=None, stream=None):
+    return _stat("hc_op_variance", inp, level, out, stream)
+
+
+def std(inp, level: str = "q", out=None, stream=None):
+    return _stat("hc_op_std", inp, level, out, stream)
+
+
+_OUT = {"float32": HC_F32, "float64": HC_F64, "int64": HC_I64}
+
+
+def _field_out(shape, out_dtype, dev, out):
+    torch = _torch()
+    if out is None:
+        tdt = {"float32": torch.float32, "float64": torch.float64, "int64": torch.int64}[out_dtype]
+        out = torch.empty(shape, dtype=tdt, device=dev)
+    return out
+
+
+def derivative(inp, axis: int, out_dtype: str = "float32", out=None, level: str = "q", stream=None):
+    st, eps, shape, dev = _input(inp, level)
+    out = _field_out(shape, out_dtype, dev, out)
+    ws = workspace(dev, stream)
+    _check(lib().hc_op_derivative(ctypes.byref(st), eps, len(shape), _dims(shape), axis,
+                                  ctypes.c_void_p(out.data_ptr()), _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()),
+                                  ws.numel(), _stream_ptr(stream)))
+    return out
+
+
+def gradmag(inp, out_dtype: str = "float32", out=None, level: str = "q", stream=None):
+    st, eps, shape, dev = _input(inp, level)
+    out = _field_out(shape, out_dtype, dev, out)
+    ws = workspace(dev, stream)
+    _check(lib().hc_op_gradmag(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
+                               _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return out
+
+
+def laplacian(inp, out_dtype: str = "float32", out=None, level: str = "q", stream=None):
+    st, eps, shape, dev = _input(inp, level)
+    out = _field_out(shape, out_dtype, dev, out)
+    ws = workspace(dev, stream)
+    _check(lib().hc_op_laplacian(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
+                                 _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return out
+
+
+def workspace_status(stream=None) -> int:
+    ws = workspace(None, stream)
+    return int(lib().hc_workspace_status(ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))

@@ -1,0 +1,137 @@
+"""Host-side checks of the C ABI (no GPU needed, no kernel is launched).
+
+* libhc.so loads and exports every function include/hc.h declares, and the
+  Python binding names exactly those functions.
+* The structs of hc.h have the sizes and field offsets the binding assumes
+  (checked against a C program compiled with gcc from hc.h).
+* Sizing queries agree with the oracle's layout arithmetic.
+* Argument errors are caught on the host before any CUDA call.
+"""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from conftest import ROOT
+
+HC_H = os.path.join(ROOT, "include", "hc.h")
+
+
+def _declared():
+    return re.findall(r"HC_API [^(]*?(hc_\w+)\(", open(HC_H).read())
+
+
+@pytest.fixture(scope="module")
+def hc():
+    import __graft_entry__
+
+    from paper_2603_25206_gb300 import build as b
+
+    b.build()
+    from paper_2603_25206_gb300 import hc as mod
+
+    mod.lib()
+    return mod
+
+
+def test_exports_every_declared_symbol(hc):
+    names = _declared()
+    assert len(names) >= 18
+    lib = ctypes.CDLL(hc.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(names) == sorted(hc.ABI_FUNCTIONS)
+
+
+def test_struct_layout_matches_c(hc):
+    src = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "hc.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(hc_header), sizeof(hc_stage), sizeof(hc_scalar));
+  printf("%zu %zu %zu %zu\n", offsetof(hc_header, eps), offsetof(hc_header, N), offsetof(hc_header, wmax),
+         offsetof(hc_header, total_bytes));
+  printf("%zu %zu %zu %zu\n", offsetof(hc_stage, d_data), offsetof(hc_stage, hdr), offsetof(hc_stage, n),
+         offsetof(hc_stage, qmax));
+  printf("%zu %zu %zu\n", offsetof(hc_scalar, s1), offsetof(hc_scalar, status), offsetof(hc_scalar, exact));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c11", "-I", os.path.dirname(HC_H), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    vals = [int(v) for v in out]
+    H, St = hc.HcHeader, hc.HcStage
+    assert vals[:3] == [ctypes.sizeof(H), ctypes.sizeof(St), hc.SCALAR_BYTES]
+    assert vals[3:7] == [H.eps.offset, H.N.offset, H.wmax.offset, H.total_bytes.offset]
+    assert vals[7:11] == [St.d_data.offset, St.hdr.offset, St.n.offset, St.qmax.offset]
+    assert vals[11:14] == [hc._SCALAR_DTYPE.fields["s1"][1], hc._SCALAR_DTYPE.fields["status"][1],
+                           hc._SCALAR_DTYPE.fields["exact"][1]]
+
+
+@pytest.mark.parametrize("S", [1, 2, 3, 16, 32, 33, 64, 100, 128, 4096])
+def test_compress_bound_matches_oracle_layout(hc, orc, S):
+    for n in (1, 7, 31, 32, 33, 1000, 4096 * 3 + 5, 10**6 + 3):
+        assert int(hc.lib().hc_compress_bound(n, S)) == orc.compress_bound(n, S)
+
+
+def test_status_strings_and_version(hc):
+    L = hc.lib()
+    assert L.hc_status_str(0) == b"ok"
+    assert L.hc_status_str(3) == b"corrupt stream"
+    assert L.hc_version() == 1
+    assert L.hc_workspace_bytes() >= 64
+    assert L.hc_compress_bound(0, 32) == 0
+    assert L.hc_compress_bound(10, 0) == 0
+    assert L.hc_compress_bound(10, 4097) == 0
+
+
+def test_argument_errors_before_any_cuda_call(hc):
+    L = hc.lib()
+    dims = (ctypes.c_int64 * 3)(10, 1, 1)
+    n = ctypes.c_size_t()
+    # S out of range -> rejected by the layout check on the host
+    rc = L.hc_compress(ctypes.c_void_p(16), 0, 1, dims, 1e-3, 1, 0, ctypes.c_void_p(16), 10**6,
+                       ctypes.c_void_p(16), 10**6, ctypes.byref(n), None, None)
+    assert rc == hc.HC_ERR_INVALID_ARG
+    assert b"block size" in L.hc_last_error()
+    # null stage
+    rc = L.hc_op_mean(None, 1e-3, 1, dims, ctypes.c_void_p(16), ctypes.c_void_p(16), 10**6, None)
+    assert rc == hc.HC_ERR_INVALID_ARG
+    # workspace too small
+    st = hc.HcStage()
+    st.kind = hc.HC_STAGE_Q
+    st.d_data = 16
+    st.n = 10
+    rc = L.hc_op_variance(ctypes.byref(st), 1e-3, 1, dims, ctypes.c_void_p(16), ctypes.c_void_p(16), 8, None)
+    assert rc == hc.HC_ERR_NOMEM
+    # stage-2 differentiation of a 1-D block partition is not defined (Section V-B)
+    st.kind = hc.HC_STAGE_P
+    st.S = 32
+    rc = L.hc_op_laplacian(ctypes.byref(st), 1e-3, 1, dims, ctypes.c_void_p(16), 0, ctypes.c_void_p(16),
+                           L.hc_workspace_bytes(), None)
+    assert rc == hc.HC_ERR_UNSUPPORTED
+    # metadata of an HSZp-style stream supports no operation
+    st.kind = hc.HC_STAGE_M
+    rc = L.hc_op_mean(ctypes.byref(st), 1e-3, 1, dims, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                      L.hc_workspace_bytes(), None)
+    assert rc == hc.HC_ERR_UNSUPPORTED
+    # axis out of range
+    st.kind = hc.HC_STAGE_Q
+    rc = L.hc_op_derivative(ctypes.byref(st), 1e-3, 1, dims, 1, ctypes.c_void_p(16), 0, ctypes.c_void_p(16),
+                            L.hc_workspace_bytes(), None)
+    assert rc == hc.HC_ERR_INVALID_ARG
+
+
+def test_binding_fails_loudly_without_library(hc, monkeypatch, tmp_path):
+    monkeypatch.setattr(hc, "_lib", None)
+    monkeypatch.setattr(hc, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        hc.lib()

@@ -1,0 +1,80 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (needs a GPU).
+
+The five paper-like float32 fields (k^-3 Gaussian random field plus 5% spikes,
+value-range-relative eb = 1e-3, block 32): the whole stream is compared bit
+for bit with the oracle's, the exact sums of the fused statistics are
+compared with the oracle's, and the fused stencil outputs are compared at
+sampled points (edges, corners and random interior points) that the oracle
+evaluates one by one.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    hc.lib()
+    return hc, torch, torch.device("cuda:0")
+
+
+def _sample_indices(shape, rng, m=4000):
+    dims = (1,) * (3 - len(shape)) + tuple(shape)
+    n = int(np.prod(dims))
+    corners = []
+    for i0 in (0, dims[0] - 1):
+        for i1 in (0, 1, dims[1] // 2, dims[1] - 2, dims[1] - 1):
+            for i2 in (0, 1, 31, 32, dims[2] - 2, dims[2] - 1):
+                if 0 <= i1 < dims[1] and 0 <= i2 < dims[2]:
+                    corners.append((i0 * dims[1] + i1) * dims[2] + i2)
+    idx = np.concatenate([np.array(corners, np.int64), rng.integers(0, n, m)])
+    return np.unique(idx)
+
+
+@pytest.mark.parametrize("fi", range(5))
+def test_paper_like_field_full_size(env, orc, fi):
+    import synth
+
+    hc, torch, dev = env
+    shape = synth.PAPER_SHAPES[fi]
+    x = synth.grf_field(shape, 1000 + fi)
+    ref, eps = orc.compress(x, 1e-3, True, 32)
+    c = hc.compress(torch.from_numpy(x).to(dev), 1e-3, rel=True, S=32)
+    del x
+    assert c.nbytes == ref.size
+    assert np.array_equal(c.stream[: c.nbytes].cpu().numpy(), ref)
+    q = orc.decode(ref, "q")
+    del ref
+    s1, s2 = orc.sums_q(q)
+    rm = hc.parse_scalar(hc.mean(c, level="p"))
+    rv = hc.parse_scalar(hc.variance(c, level="q"))
+    assert rm["s1"] == s1
+    assert (rv["s1"], rv["s2"]) == (s1, s2)
+    m_ref, v_ref, _ = orc.finalize(q.size, s1, s2, eps)
+    assert abs(rv["variance"] - v_ref) <= 1e-12 * v_ref
+    assert abs(rm["mean"] - m_ref) <= 1e-12 * abs(m_ref)
+
+    rng = np.random.default_rng(fi)
+    idx = _sample_indices(shape, rng)
+    for ax in range(len(shape)):
+        d = hc.derivative(c, ax, out_dtype="float32").reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+        num, val = orc.stencil_at(q, orc.KIND_DERIV, eps, idx, ax)
+        assert np.all(np.abs(d - val) <= 1e-6 * np.maximum(np.abs(val), eps))
+    g = hc.gradmag(c).reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    _, val = orc.stencil_at(q, orc.KIND_GRADMAG, eps, idx)
+    assert np.all(np.abs(g - val) <= 1e-6 * np.maximum(np.abs(val), eps))
+    lap_i = hc.laplacian(c, out_dtype="int64").reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    num, val = orc.stencil_at(q, orc.KIND_LAPLACIAN, eps, idx)
+    assert np.array_equal(lap_i, num)
+    lap = hc.laplacian(c).reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    assert np.all(np.abs(lap - val) <= 1e-6 * np.maximum(np.abs(val), 2 * eps))
+    assert hc.workspace_status() == 0

@@ -400,3 +400,18 @@ def test_homomorphic_stencils_equal_generic_flow(orc, rng, shape, S):
             hq = orc.stencil_q(q, kind, eps, ax)
             hf = orc.stencil_f(f, kind, ax)
             np.testing.assert_allclose(hq, hf, rtol=1e-12, atol=1e-12 * eps)
+
+
+def test_sampled_stencils_equal_whole_field(orc, rng):
+    """stencil_at evaluates the same numerators and values as the whole-field routines."""
+    q = rng.integers(-500, 500, (6, 7, 9)).astype(np.int32)
+    idx = np.concatenate([[0, q.size - 1], rng.integers(0, q.size, 50)])
+    eps = 0.01
+    for ax in range(3):
+        num, val = orc.stencil_at(q, orc.KIND_DERIV, eps, idx, ax)
+        np.testing.assert_array_equal(num, orc.deriv_q(q, ax).reshape(-1)[idx])
+        np.testing.assert_array_equal(val, orc.stencil_q(q, orc.KIND_DERIV, eps, ax).reshape(-1)[idx])
+    num, val = orc.stencil_at(q, orc.KIND_LAPLACIAN, eps, idx)
+    np.testing.assert_array_equal(num, orc.lap_q(q).reshape(-1)[idx])
+    _, val = orc.stencil_at(q, orc.KIND_GRADMAG, eps, idx)
+    np.testing.assert_array_equal(val, orc.stencil_q(q, orc.KIND_GRADMAG, eps).reshape(-1)[idx])
