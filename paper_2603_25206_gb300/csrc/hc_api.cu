@@ -4,7 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
-#include <set>
+#include <map>
 #include <utility>
 
 #include "hc_internal.cuh"
@@ -71,21 +71,45 @@ int check_launch(const char* what) {
   return HC_OK;
 }
 
+int check_launch_cfg(const char* what, const void* kernel, long long grid, int smem) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFuncAttributes fa;
+    std::memset(&fa, 0, sizeof fa);
+    cudaFuncGetAttributes(&fa, kernel);
+    cudaGetLastError();
+    char buf[480];
+    std::snprintf(buf, sizeof(buf),
+                  "%s: kernel launch failed: %s (grid %lld, block %d, dynamic smem %d, static smem %zu, "
+                  "max dynamic smem %d, regs %d)",
+                  what, cudaGetErrorString(e), grid, kThreads, smem, fa.sharedSizeBytes,
+                  fa.maxDynamicSharedSizeBytes, fa.numRegs);
+    return fail(HC_ERR_CUDA, buf);
+  }
+  return HC_OK;
+}
+
 int ensure_smem(const void* kernel, int bytes) {
+  // Per (kernel, device): the largest dynamic shared-memory size set so far.
+  // The limit is only ever raised, so launches of the same kernel with
+  // smaller tiles stay valid.
   static std::mutex mu;
-  static std::set<std::pair<std::pair<const void*, int>, int>> done;  // (kernel, device) -> largest size set
+  static std::map<std::pair<const void*, int>, int> limit;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (bytes <= 48 * 1024) return HC_OK;
   std::lock_guard<std::mutex> lock(mu);
-  auto key = std::make_pair(std::make_pair(kernel, dev), bytes);
-  if (done.count(key)) return HC_OK;
+  const auto key = std::make_pair(kernel, dev);
+  auto it = limit.find(key);
+  if (it != limit.end() && it->second >= bytes) return HC_OK;
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (bytes > optin) return fail(HC_ERR_UNSUPPORTED, "kernel needs more shared memory than the device offers");
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  if ((size_t)bytes + fa.sharedSizeBytes > (size_t)optin)
+    return fail(HC_ERR_UNSUPPORTED, "kernel needs more shared memory than the device offers");
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
     return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
-  done.insert(key);
+  limit[key] = bytes;
   return HC_OK;
 }
 

@@ -171,7 +171,7 @@ static int launch_decode(const hc_header* h, const void* d_stream, void* d_out, 
   const double te = 2.0 * h->eps;
   kern<<<grid, kThreads, smem, st>>>(s, reinterpret_cast<OutT*>(d_out), (float)te, te, ntiles, L.stage_words,
                                      err);
-  return check_launch("decompress_to_stage");
+  return check_launch_cfg("decompress_to_stage", reinterpret_cast<const void*>(kern), grid, smem);
 }
 
 template <int KIND, class OutT>

@@ -32,7 +32,9 @@ size_t compress_ws_bytes(const Layout& L);
 
 int device_sms();
 int check_launch(const char* what);
-// Raise a kernel's dynamic shared-memory limit once per (kernel, size).
+// Like check_launch, with the launch configuration in the error message.
+int check_launch_cfg(const char* what, const void* kernel, long long grid, int smem);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it).
 int ensure_smem(const void* kernel, int bytes);
 
 int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st);

@@ -538,7 +538,7 @@ static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_
   const int grid = (int)std::min<int64_t>(std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm), kMaxGrid);
   OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
   kern<<<grid, kThreads, bytes, st>>>(s, ntiles, stage, ws_partials(d_ws), &ws->ticket, d_out, 2.0 * h->eps);
-  return check_launch("reduce (fused)");
+  return check_launch_cfg("reduce (fused)", reinterpret_cast<const void*>(kern), grid, bytes);
 }
 
 template <int LEVEL, bool VAR, bool SMALL>

@@ -142,6 +142,131 @@ __device__ inline int64_t decode_range(const DevStream& s, int64_t e0, int64_t e
   return b0 * s.S;
 }
 
+__device__ __forceinline__ int ring_slot(const Geo& g, int64_t z) { return g.nslot == 3 ? (int)(z % 3) : 0; }
+
+// Decode plane z of the CTA's slab (rows [ylo, yhi), x range [xlo, xhi) when
+// rows are split) into its ring slot.
+template <bool SMALL>
+__device__ inline void load_slab(const DevStream& s, const Geo& g, int64_t z, int64_t ylo, int64_t yhi, int64_t xlo,
+                                 int64_t xhi, bool whole, int32_t* ring, int range_words, long long (*s_base)[66],
+                                 uint8_t* s_w, uint32_t* s_off, uint32_t* s_stage, int stage_words, int32_t* s_tot,
+                                 uint32_t* s_warp, int* s_flag, int* err) {
+  const int slot = ring_slot(g, z);
+  int32_t* dst = ring + slot * g.slot_words;
+  if (whole) {
+    const int64_t e0 = (z * g.n1 + ylo) * g.n2, e1 = (z * g.n1 + yhi) * g.n2;
+    const int64_t base = decode_range<SMALL>(s, e0, e1, dst, s_w, s_off, s_stage, stage_words, s_tot, s_warp,
+                                             s_flag, err);
+    if (threadIdx.x == 0) s_base[slot][0] = base;
+  } else {
+    for (int64_t y = ylo; y < yhi; ++y) {
+      const int ri = (int)(y - ylo);
+      const int64_t row = (z * g.n1 + y) * g.n2;
+      const int64_t base = decode_range<SMALL>(s, row + xlo, row + xhi, dst + ri * range_words, s_w, s_off,
+                                               s_stage, stage_words, s_tot, s_warp, s_flag, err);
+      if (threadIdx.x == 0) s_base[slot][ri] = base;
+    }
+  }
+  __syncthreads();
+}
+
+// Integer stencil of one output point from its neighbours (clamped indices
+// already applied by the caller) and its scaled output.
+template <int OP, int OUT>
+__device__ __forceinline__ typename OutType<OUT>::T point(const Geo& g, int32_t c, int32_t zm, int32_t zp,
+                                                          int32_t ym, int32_t yp, int32_t xm, int32_t xp, int ez,
+                                                          int ey, int ex) {
+  if constexpr (OP == ST_LAPLACIAN) {
+    const long long sum = (long long)zm + zp + ym + yp + xm + xp - 6ll * c;
+    return emit<OP, OUT>(sum, 0, 0, g);
+  } else {
+    // one-sided differences at an edge are doubled: (q1 - q0) * 2
+    const long long d0 = (long long)(zp - zm) * ez;
+    const long long d1 = (long long)(yp - ym) * ey;
+    const long long d2 = (long long)(xp - xm) * ex;
+    if constexpr (OP == ST_DERIV)
+      return emit<OP, OUT>(g.axis == 0 ? d0 : (g.axis == 1 ? d1 : d2), 0, 0, g);
+    else
+      return emit<OP, OUT>(d0, d1, d2, g);
+  }
+}
+
+// Whole rows: every slot holds one contiguous decoded range; all offsets
+// are 32-bit element offsets into the padded slot.
+template <int OP, int OUT>
+__device__ inline void stencil_plane_whole(const Geo& g, int64_t z, int64_t y0, int64_t y1, const int32_t* ring,
+                                           long long (*s_base)[66], typename OutType<OUT>::T* out) {
+  const int64_t zm = z > 0 ? z - 1 : 0, zp = z + 1 < g.n0 ? z + 1 : z;
+  const int sc = ring_slot(g, z), sm = ring_slot(g, zm), sp = ring_slot(g, zp);
+  const int32_t* pc = ring + sc * g.slot_words;
+  const int32_t* pm = ring + sm * g.slot_words;
+  const int32_t* pp = ring + sp * g.slot_words;
+  const int n2 = (int)g.n2;
+  const int ez = (z == 0 || z == g.n0 - 1) ? 2 : 1;
+  for (int64_t y = y0; y < y1; ++y) {
+    const int64_t erow = (z * g.n1 + y) * g.n2;
+    const int rc = (int)(erow - s_base[sc][0]);
+    const int rzm = (int)((zm * g.n1 + y) * g.n2 - s_base[sm][0]);
+    const int rzp = (int)((zp * g.n1 + y) * g.n2 - s_base[sp][0]);
+    const int rym = y > 0 ? rc - n2 : rc;
+    const int ryp = y + 1 < g.n1 ? rc + n2 : rc;
+    const int ey = (y == 0 || y == g.n1 - 1) ? 2 : 1;
+    typename OutType<OUT>::T* orow = out + erow;
+    for (int x = threadIdx.x; x < n2; x += blockDim.x) {
+      const int xm = x > 0 ? x - 1 : 0, xp = x + 1 < n2 ? x + 1 : x;
+      const int ex = (x == 0 || x == n2 - 1) ? 2 : 1;
+      const int32_t c = pc[pidx(rc + x)];
+      int32_t vzm = 0, vzp = 0, vym = 0, vyp = 0, vxm = 0, vxp = 0;
+      if (OP != ST_DERIV || g.axis == 0) {
+        vzm = pm[pidx(rzm + x)];
+        vzp = pp[pidx(rzp + x)];
+      }
+      if (OP != ST_DERIV || g.axis == 1) {
+        vym = pc[pidx(rym + x)];
+        vyp = pc[pidx(ryp + x)];
+      }
+      if (OP != ST_DERIV || g.axis == 2) {
+        vxm = pc[pidx(rc + xm)];
+        vxp = pc[pidx(rc + xp)];
+      }
+      orow[x] = point<OP, OUT>(g, c, vzm, vzp, vym, vyp, vxm, vxp, ez, ey, ex);
+    }
+  }
+}
+
+// Rows split along x: every row of a slot is its own decoded range.
+template <int OP, int OUT>
+__device__ inline void stencil_plane_tiled(const Geo& g, int64_t z, int64_t y0, int64_t y1, int64_t x0, int64_t x1,
+                                           int64_t ylo, const int32_t* ring, int range_words, long long (*s_base)[66],
+                                           typename OutType<OUT>::T* out) {
+  const int64_t zm = z > 0 ? z - 1 : 0, zp = z + 1 < g.n0 ? z + 1 : z;
+  const int sc = ring_slot(g, z), sm = ring_slot(g, zm), sp = ring_slot(g, zp);
+  const int ez = (z == 0 || z == g.n0 - 1) ? 2 : 1;
+  for (int64_t y = y0; y < y1; ++y) {
+    const int64_t ym = y > 0 ? y - 1 : 0, yp = y + 1 < g.n1 ? y + 1 : y;
+    const int ey = (y == 0 || y == g.n1 - 1) ? 2 : 1;
+    auto row = [&](int slot, int64_t zz, int64_t yy) -> const int32_t* {
+      const int ri = (int)(yy - ylo);
+      return ring + slot * g.slot_words + ri * range_words;
+    };
+    auto rel = [&](int slot, int64_t zz, int64_t yy) -> int64_t {
+      return (zz * g.n1 + yy) * g.n2 - s_base[slot][(int)(yy - ylo)];
+    };
+    const int32_t *pc = row(sc, z, y), *pym = row(sc, z, ym), *pyp = row(sc, z, yp);
+    const int32_t *pzm = row(sm, zm, y), *pzp = row(sp, zp, y);
+    const int64_t rc = rel(sc, z, y), rym = rel(sc, z, ym), ryp = rel(sc, z, yp), rzm = rel(sm, zm, y),
+                  rzp = rel(sp, zp, y);
+    typename OutType<OUT>::T* orow = out + (z * g.n1 + y) * g.n2;
+    for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+      const int64_t xm = x > 0 ? x - 1 : 0, xp = x + 1 < g.n2 ? x + 1 : x;
+      const int ex = (x == 0 || x == g.n2 - 1) ? 2 : 1;
+      orow[x] = point<OP, OUT>(g, pc[pidx((int)(rc + x))], pzm[pidx((int)(rzm + x))], pzp[pidx((int)(rzp + x))],
+                               pym[pidx((int)(rym + x))], pyp[pidx((int)(ryp + x))], pc[pidx((int)(rc + xm))],
+                               pc[pidx((int)(rc + xp))], ez, ey, ex);
+    }
+  }
+}
+
 template <int OP, int OUT, bool SMALL>
 __global__ void __launch_bounds__(kThreads) k_stencil_stream(DevStream s, Geo g, typename OutType<OUT>::T* out,
                                                               int* err) {
@@ -173,67 +298,20 @@ __global__ void __launch_bounds__(kThreads) k_stencil_stream(DevStream s, Geo g,
   const int64_t xlo = max(x0 - 1, (int64_t)0), xhi = min(x1 + 1, g.n2);
   const bool whole = (g.ranges == 1);
 
-  // decode plane z into its ring slot
-  auto load_plane = [&](int64_t z) {
-    const int slot = g.nslot == 3 ? (int)(z % 3) : 0;
-    int32_t* dst = ring + slot * g.slot_words;
-    if (whole) {
-      const int64_t e0 = (z * g.n1 + ylo) * g.n2, e1 = (z * g.n1 + yhi) * g.n2;
-      const int64_t base =
-          decode_range<SMALL>(s, e0, e1, dst, s_w, s_off, s_stage, L.stage_words, s_tot, s_warp, &s_flag, err);
-      if (threadIdx.x == 0) s_base[slot][0] = base;
-    } else {
-      for (int64_t y = ylo; y < yhi; ++y) {
-        const int ri = (int)(y - ylo);
-        const int64_t row = (z * g.n1 + y) * g.n2;
-        const int64_t base = decode_range<SMALL>(s, row + xlo, row + xhi, dst + ri * range_words, s_w, s_off, s_stage,
-                                                 L.stage_words, s_tot, s_warp, &s_flag, err);
-        if (threadIdx.x == 0) s_base[slot][ri] = base;
-      }
-    }
-    __syncthreads();
-  };
-  // value of q at (z, y, x), all inside the decoded window
-  auto V = [&](int64_t z, int64_t y, int64_t x) -> int32_t {
-    const int slot = g.nslot == 3 ? (int)(z % 3) : 0;
-    const int32_t* src = ring + slot * g.slot_words;
-    const int64_t e = (z * g.n1 + y) * g.n2 + x;
-    if (whole) return src[pidx((int)(e - s_base[slot][0]))];
-    const int ri = (int)(y - ylo);
-    return src[ri * range_words + pidx((int)(e - s_base[slot][ri]))];
-  };
-
-  if (z0 > 0) load_plane(z0 - 1);
-  load_plane(z0);
+  // prime the ring with planes z0 - 1 and z0, then march: load z + 1, compute z
+  if (z0 > 0)
+    load_slab<SMALL>(s, g, z0 - 1, ylo, yhi, xlo, xhi, whole, ring, range_words, s_base, s_w, s_off, s_stage,
+                     L.stage_words, s_tot, s_warp, &s_flag, err);
+  load_slab<SMALL>(s, g, z0, ylo, yhi, xlo, xhi, whole, ring, range_words, s_base, s_w, s_off, s_stage,
+                   L.stage_words, s_tot, s_warp, &s_flag, err);
   for (int64_t z = z0; z < z1; ++z) {
-    if (z + 1 < g.n0) load_plane(z + 1);
-    const int64_t zm = z > 0 ? z - 1 : 0, zp = z + 1 < g.n0 ? z + 1 : z;
-    for (int64_t y = y0; y < y1; ++y) {
-      const int64_t ym = y > 0 ? y - 1 : 0, yp = y + 1 < g.n1 ? y + 1 : y;
-      T* orow = out + (z * g.n1 + y) * g.n2;
-      for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
-        const int64_t xm = x > 0 ? x - 1 : 0, xp = x + 1 < g.n2 ? x + 1 : x;
-        if constexpr (OP == ST_LAPLACIAN) {
-          const long long c = V(z, y, x);
-          const long long sum = (long long)V(zm, y, x) + V(zp, y, x) + V(z, ym, x) + V(z, yp, x) + V(z, y, xm) +
-                                V(z, y, xp);
-          orow[x] = emit<OP, OUT>(sum - 6 * c, 0, 0, g);
-        } else {
-          // one-sided differences at an edge are doubled: (q1 - q0) * 2
-          long long d[3] = {0, 0, 0};
-          if (OP == ST_GRADMAG || g.axis == 0)
-            d[0] = (long long)(V(zp, y, x) - V(zm, y, x)) * ((z == 0 || z == g.n0 - 1) ? 2 : 1);
-          if (OP == ST_GRADMAG || g.axis == 1)
-            d[1] = (long long)(V(z, yp, x) - V(z, ym, x)) * ((y == 0 || y == g.n1 - 1) ? 2 : 1);
-          if (OP == ST_GRADMAG || g.axis == 2)
-            d[2] = (long long)(V(z, y, xp) - V(z, y, xm)) * ((x == 0 || x == g.n2 - 1) ? 2 : 1);
-          if constexpr (OP == ST_DERIV)
-            orow[x] = emit<OP, OUT>(d[g.axis], 0, 0, g);
-          else
-            orow[x] = emit<OP, OUT>(d[0], d[1], d[2], g);
-        }
-      }
-    }
+    if (z + 1 < g.n0)
+      load_slab<SMALL>(s, g, z + 1, ylo, yhi, xlo, xhi, whole, ring, range_words, s_base, s_w, s_off, s_stage,
+                       L.stage_words, s_tot, s_warp, &s_flag, err);
+    if (whole)
+      stencil_plane_whole<OP, OUT>(g, z, y0, y1, ring, s_base, out);
+    else
+      stencil_plane_tiled<OP, OUT>(g, z, y0, y1, x0, x1, ylo, ring, range_words, s_base, out);
     __syncthreads();
   }
 }
@@ -269,17 +347,14 @@ __global__ void __launch_bounds__(kThreads) k_stencil_array(const In* __restrict
                                 __ldg(a + i + yp) + __ldg(a + i + zm) + __ldg(a + i + zp) - 6ll * __ldg(a + i);
           out[i] = emit<OP, OUT>(sum, 0, 0, g);
         } else {
-          long long d[3] = {0, 0, 0};
-          if (OP == ST_GRADMAG || g.axis == 0)
-            d[0] = ((long long)__ldg(a + i + zp) - __ldg(a + i + zm)) * (zedge ? 2 : 1);
-          if (OP == ST_GRADMAG || g.axis == 1)
-            d[1] = ((long long)__ldg(a + i + yp) - __ldg(a + i + ym)) * (yedge ? 2 : 1);
-          if (OP == ST_GRADMAG || g.axis == 2)
-            d[2] = ((long long)__ldg(a + i + xp) - __ldg(a + i + xm)) * (xedge ? 2 : 1);
+          long long d0 = 0, d1 = 0, d2 = 0;
+          if (OP == ST_GRADMAG || g.axis == 0) d0 = ((long long)__ldg(a + i + zp) - __ldg(a + i + zm)) * (zedge ? 2 : 1);
+          if (OP == ST_GRADMAG || g.axis == 1) d1 = ((long long)__ldg(a + i + yp) - __ldg(a + i + ym)) * (yedge ? 2 : 1);
+          if (OP == ST_GRADMAG || g.axis == 2) d2 = ((long long)__ldg(a + i + xp) - __ldg(a + i + xm)) * (xedge ? 2 : 1);
           if constexpr (OP == ST_DERIV)
-            out[i] = emit<OP, OUT>(d[g.axis], 0, 0, g);
+            out[i] = emit<OP, OUT>(g.axis == 0 ? d0 : (g.axis == 1 ? d1 : d2), 0, 0, g);
           else
-            out[i] = emit<OP, OUT>(d[0], d[1], d[2], g);
+            out[i] = emit<OP, OUT>(d0, d1, d2, g);
         }
       } else {
         using R = typename OutType<OUT>::T;
@@ -295,14 +370,14 @@ __global__ void __launch_bounds__(kThreads) k_stencil_array(const In* __restrict
                        ((__ldg(a + i + xm) + __ldg(a + i + xp)) - In(2) * c);
           out[i] = (R)v;
         } else {
-          In d[3] = {0, 0, 0};
-          if (OP == ST_GRADMAG || g.axis == 0) d[0] = g.n0 > 1 ? der(zm, zp, zedge) : In(0);
-          if (OP == ST_GRADMAG || g.axis == 1) d[1] = g.n1 > 1 ? der(ym, yp, yedge) : In(0);
-          if (OP == ST_GRADMAG || g.axis == 2) d[2] = g.n2 > 1 ? der(xm, xp, xedge) : In(0);
+          In d0 = 0, d1 = 0, d2 = 0;
+          if (OP == ST_GRADMAG || g.axis == 0) d0 = g.n0 > 1 ? der(zm, zp, zedge) : In(0);
+          if (OP == ST_GRADMAG || g.axis == 1) d1 = g.n1 > 1 ? der(ym, yp, yedge) : In(0);
+          if (OP == ST_GRADMAG || g.axis == 2) d2 = g.n2 > 1 ? der(xm, xp, xedge) : In(0);
           if constexpr (OP == ST_DERIV)
-            out[i] = (R)d[g.axis];
+            out[i] = (R)(g.axis == 0 ? d0 : (g.axis == 1 ? d1 : d2));
           else
-            out[i] = (R)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            out[i] = (R)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
         }
       }
     }
@@ -396,7 +471,7 @@ static int launch_stream_st(const hc_header* h, const void* d_stream, Geo g, voi
   if (grid > 0x7fffffff) return fail(HC_ERR_UNSUPPORTED, "field too large");
   kern<<<(unsigned)grid, kThreads, smem, st>>>(dev_stream(h, d_stream), g,
                                                 reinterpret_cast<typename OutType<OUT>::T*>(d_out), err);
-  return check_launch("stencil (fused)");
+  return check_launch_cfg("stencil (fused)", reinterpret_cast<const void*>(kern), grid, smem);
 }
 
 template <int OP, int OUT>

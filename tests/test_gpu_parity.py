@@ -240,3 +240,20 @@ def test_repeat_calls_deterministic(env):
     for fn in (lambda: hc.variance(a), lambda: hc.mean(a), lambda: hc.gradmag(a), lambda: hc.laplacian(a),
                lambda: hc.decompress(a, "f")):
         assert torch.equal(fn(), fn())
+
+
+def test_kernel_reuse_across_tile_sizes(env, orc):
+    """One kernel launched with large, small, then large shared-memory tiles
+    (fields of different row lengths) stays valid and exact."""
+    hc, torch, dev = env
+    import synth
+
+    fields = [synth.grf_field((4, 300, 900), 21), synth.grf_field((6, 20, 40), 22), synth.grf_field((3, 280, 1100), 23)]
+    for x in fields + fields[::-1]:
+        ref, eps = orc.compress(x, 1e-3, True, 32)
+        c = hc.compress(torch.from_numpy(x).to(dev), 1e-3)
+        q = orc.decode(ref, "q")
+        assert np.array_equal(hc.laplacian(c, out_dtype="int64").cpu().numpy(), orc.lap_q(q))
+        assert np.array_equal(hc.decompress(c, "q").cpu().numpy(), q)
+        r = hc.parse_scalar(hc.variance(c))
+        assert (r["s1"], r["s2"]) == orc.sums_q(q)
