@@ -186,6 +186,27 @@ HC_API int hc_op_variance(const hc_stage* in, double eps, int ndim, const int64_
 HC_API int hc_op_std(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
               size_t ws_bytes, void* stream);
 
+/* Allocation-free fused variance (the paper has no counterpart: this is an
+ * interface for callers, not a method step).  For callers that cannot
+ * allocate device memory when they need the statistic -- code inside a CUDA
+ * graph capture, allocation-free real-time loops, plugins handed only a stream
+ * and pointers by a host application that owns all memory -- it computes what
+ * hc_op_variance computes for a compressed-stream input (level P or Q), but
+ * takes no workspace: its scratch is a static device array inside libhc.so of
+ * 64 KiB + 256 bytes (one ticket counter and 2048 per-CTA partial sums), held
+ * by every GPU that loads the library until the process exits.
+ *   in: a HC_STAGE_COMPRESSED stage (other kinds: HC_ERR_UNSUPPORTED);
+ *   d_out: one hc_scalar in device memory (every field filled, as
+ *   hc_op_variance does).  A launch that would need more than 2048 partial
+ *   slots is refused with HC_ERR_NOMEM.
+ * It calls no allocating routine.  The first call on each device looks up the
+ * device address of the static array (with that device current); make that
+ * first call before any stream capture.  Every call clears the ticket it needs
+ * and reuses the same array, so calls whose kernels overlap on the GPU (for
+ * example on two concurrent streams) race and must not be issued.  ASYNC. */
+HC_API int hc_op_variance_noalloc(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out,
+                                  void* stream);
+
 /* Numerical differentiation (Section V-B, "Operation with D_q").  Inputs: the
  * stream (fused, level Q), or a materialized Q or F array.  A stage-P input
  * returns HC_ERR_UNSUPPORTED: a 1-D block partition does not keep the

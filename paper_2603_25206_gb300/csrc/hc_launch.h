@@ -71,6 +71,9 @@ enum ReduceWhat { RED_MEAN = 0, RED_VAR = 1 };
 int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out,
                        void* d_ws, cudaStream_t st);
 int reduce_array_impl(const hc_stage* in, double eps, int what, hc_scalar* d_out, void* d_ws, cudaStream_t st);
+// Fused stage-3 variance with its scratch (per-CTA partials + ticket) at given device addresses.
+int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
+                                 unsigned* ticket, int max_parts, cudaStream_t st);
 
 enum StencilOp { ST_DERIV = 0, ST_GRADMAG = 1, ST_LAPLACIAN = 2 };
 int stencil_stream_impl(const hc_header* h, const void* d_stream, int op, int axis3, void* d_out, int out_dtype,

@@ -646,3 +646,50 @@ int reduce_array_impl(const hc_stage* in, double eps, int what, hc_scalar* d_out
 }
 
 }  // namespace hc
+
+namespace hc {
+
+// ------------------------------------------- fused variance, scratch given
+// The fused stage-3 variance kernel above, launched with its per-CTA
+// partials and last-block ticket at caller-given device addresses instead of
+// the workspace.  Fails with HC_ERR_NOMEM when the launch would need more than
+// max_parts partial slots.
+template <int ACC, bool SMALL>
+static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
+                              unsigned* ticket, int max_parts, cudaStream_t st) {
+  const DevStream s = dev_stream(h, d_stream);
+  const int tb = kTileChunks * h->G;
+  const int nseg = (h->S + 31) / 32;
+  const int nsegmax = SMALL ? tb : tb * nseg;
+  const TileSmem L = tile_smem(tb, 0, h->S, (int)h->wmax, !SMALL ? seg_moment_words(nsegmax, true) : 0);
+  const int bytes = 4 * L.words;
+  auto kern = k_reduce_stream<3, ACC, true, SMALL>;
+  int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
+  if (rc) return rc;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, bytes);
+  per_sm = std::max(per_sm, 1);
+  const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm);
+  if (grid > max_parts) return fail(HC_ERR_NOMEM, "the static scratch of hc_op_variance_noalloc has too few partial slots for this GPU");
+  kern<<<(unsigned)grid, kThreads, bytes, st>>>(s, ntiles, L.stage_words, parts, ticket, d_out, 2.0 * h->eps);
+  return check_launch_cfg("variance (static scratch)", reinterpret_cast<const void*>(kern), grid, bytes);
+}
+
+int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
+                                 unsigned* ticket, int max_parts, cudaStream_t st) {
+  const bool small = h->S <= 32;
+  switch (acc_class(h->qmax)) {
+    case 0:
+      return small ? launch_var_scratch<0, true>(h, d_stream, d_out, parts, ticket, max_parts, st)
+                   : launch_var_scratch<0, false>(h, d_stream, d_out, parts, ticket, max_parts, st);
+    case 1:
+      return small ? launch_var_scratch<1, true>(h, d_stream, d_out, parts, ticket, max_parts, st)
+                   : launch_var_scratch<1, false>(h, d_stream, d_out, parts, ticket, max_parts, st);
+    default:
+      return small ? launch_var_scratch<2, true>(h, d_stream, d_out, parts, ticket, max_parts, st)
+                   : launch_var_scratch<2, false>(h, d_stream, d_out, parts, ticket, max_parts, st);
+  }
+}
+
+}  // namespace hc

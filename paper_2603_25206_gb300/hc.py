@@ -36,7 +36,7 @@ ABI_FUNCTIONS = (
     "hc_status_str", "hc_last_error", "hc_version", "hc_compress_bound", "hc_compress_workspace_bytes",
     "hc_workspace_bytes", "hc_stage_bytes", "hc_compress", "hc_compress_codes", "hc_read_header",
     "hc_decompress_to_stage", "hc_workspace_status", "hc_op_mean", "hc_op_variance", "hc_op_std",
-    "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian",
+    "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc",
 )
 
 
@@ -106,6 +106,7 @@ def lib():
             "hc_op_mean": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, vp, sz, vp], i32),
             "hc_op_variance": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, vp, sz, vp], i32),
             "hc_op_std": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, vp, sz, vp], i32),
+            "hc_op_variance_noalloc": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, vp], i32),
             "hc_op_derivative": ([P(HcStage), dbl, i32, P(ctypes.c_int64), i32, vp, i32, vp, sz, vp], i32),
             "hc_op_gradmag": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_op_laplacian": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
@@ -319,6 +320,17 @@ def variance(inp, level: str = "q", out=None, stream=None):
 
 def std(inp, level: str = "q", out=None, stream=None):
     return _stat("hc_op_std", inp, level, out, stream)
+
+
+def variance_noalloc(c: Compressed, level: str = "q", out=None, stream=None):
+    """Fused variance without a workspace (static scratch inside libhc.so)."""
+    torch = _torch()
+    st = c.stage(level)
+    if out is None:
+        out = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=c.stream.device)
+    _check(lib().hc_op_variance_noalloc(ctypes.byref(st), c.eps, len(c.shape), _dims(c.shape),
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 _OUT = {"float32": HC_F32, "float64": HC_F64, "int64": HC_I64}
