@@ -55,6 +55,7 @@ typedef enum {
 } hc_status;
 
 typedef enum { HC_F32 = 0, HC_F64 = 1, HC_I32 = 2, HC_I64 = 3 } hc_dtype;
+typedef enum { HC_OP_MEAN = 0, HC_OP_VARIANCE = 1, HC_OP_DERIVATIVE = 2, HC_OP_GRADMAG = 3, HC_OP_LAPLACIAN = 4 } hc_op;
 typedef enum { HC_EB_ABS = 0, HC_EB_REL = 1 } hc_eb_mode;
 typedef enum {
   HC_STAGE_COMPRESSED = 0, /* the stream itself (operations fuse decoding in) */
@@ -223,6 +224,19 @@ HC_API int hc_op_gradmag(const hc_stage* in, double eps, int ndim, const int64_t
                   void* d_ws, size_t ws_bytes, void* stream);
 HC_API int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
                     void* d_ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- tuning */
+/* Autotuner of the fused stencil kernel (no counterpart in the paper: a GPU
+ * tiling choice).  For a compressed-stream input and op (HC_OP_DERIVATIVE,
+ * HC_OP_GRADMAG or HC_OP_LAPLACIAN) and output type, times every tile height
+ * the kernel can use on this field (each 1 warm-up + 3 runs, writing d_out,
+ * which must hold the op's output) and keeps the fastest for all later calls
+ * on fields of the same shape, max width, op and output type in this
+ * process.  *chosen receives the tile height (0: the general kernel applies
+ * and nothing was tuned; statistics ops have nothing to tune).  SYNC: call it
+ * before capturing work in a CUDA graph. */
+HC_API int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_ws, size_t ws_bytes,
+                       void* stream, int* chosen);
 
 #ifdef __cplusplus
 }

@@ -367,4 +367,33 @@ int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64_t* dim
   return stencil(in, eps, ndim, dims, ST_LAPLACIAN, 0, d_out, out_dtype, d_ws, ws_bytes, stream);
 }
 
+int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_ws, size_t ws_bytes, void* stream,
+                int* chosen) {
+  if (!in || !chosen) return fail(HC_ERR_INVALID_ARG, "null argument");
+  *chosen = 0;
+  if (in->kind != HC_STAGE_COMPRESSED || !in->hdr || !in->d_data)
+    return fail(HC_ERR_INVALID_ARG, "hc_autotune takes a compressed stream with its header");
+  if (!d_ws || ws_bytes < kOpWsBytes) return fail(HC_ERR_NOMEM, "workspace smaller than hc_workspace_bytes()");
+  if (!d_out || !aligned16(d_out) || !aligned16(in->d_data) || !aligned16(d_ws))
+    return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
+  int sop;
+  switch (op) {
+    case HC_OP_DERIVATIVE:
+      sop = ST_DERIV;
+      break;
+    case HC_OP_GRADMAG:
+      sop = ST_GRADMAG;
+      break;
+    case HC_OP_LAPLACIAN:
+      sop = ST_LAPLACIAN;
+      break;
+    default:
+      return HC_OK;  // statistics have no tunable tile
+  }
+  if (out_dtype != HC_F32 && out_dtype != HC_F64 && out_dtype != HC_I64) return fail(HC_ERR_INVALID_ARG, "out_dtype");
+  int64_t d3[3];
+  stencil_walk_dims(in->hdr, d3, nullptr);
+  return stencil_pipe_autotune(in->hdr, in->d_data, d3, sop, d_out, out_dtype, d_ws, as_stream(stream), chosen);
+}
+
 }  // extern "C"

@@ -43,24 +43,60 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
   __shared__ int s_flag;
   const int tb = kTileChunks * s.G;  // blocks per tile
   const int out_words = decode_out_words(tb, s.S);
-  const TileSmem L = tile_smem(tb, 0, s.S, s.wmax, out_words + (SMALL ? 0 : tb * s.nseg));
-  uint32_t* s_stage = smem;
+  const int nsegmax = SMALL ? tb : tb * s.nseg;
+  const PipeTileSmem L =
+      pipe_tile_smem(tb, stage_words, out_words + (SMALL ? 0 : nsegmax) + (kWidthSpecialize ? round4((nsegmax + 32 * 32 + 1) / 2) : 0));
   uint32_t* s_off = smem + L.off;
   int32_t* s_out = reinterpret_cast<int32_t*>(smem + L.extra);
   int32_t* s_tot = s_out + out_words;
-  uint8_t* s_w = reinterpret_cast<uint8_t*>(smem + L.w);
+  uint16_t* s_order = reinterpret_cast<uint16_t*>(s_tot + (SMALL ? 0 : nsegmax));
+  __shared__ int s_hist[64];
   const int tid = threadIdx.x, nt = blockDim.x;
 
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t b0 = t * tb;
-    const int nblk = (int)min((int64_t)tb, s.nb - b0);
+  // two tile buffers: tile t is decoded while tile t + gridDim.x is copied in
+  int64_t t = blockIdx.x;
+  int bi = 0;
+  TileCopy cur{}, nxt{};
+  bool cur_ok = false, have_nxt = false;
+  if (t < ntiles) {
+    cur = tile_bounds(s, t, tb);
+    cur_ok = tile_issue(s, cur, stage_words, L.w(smem, 0), L.h(smem, 0), L.words(smem, 0));
+  }
+  if (t + gridDim.x < ntiles) {
+    nxt = tile_bounds(s, t + gridDim.x, tb);
+    have_nxt = true;
+  }
+  for (; t < ntiles; t += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();
+    bool nxt_ok = false;
+    if (have_nxt) nxt_ok = tile_issue(s, nxt, stage_words, L.w(smem, bi ^ 1), L.h(smem, bi ^ 1), L.words(smem, bi ^ 1));
+    TileCopy nn{};
+    const bool have_nn = t + 2 * (int64_t)gridDim.x < ntiles;
+    if (have_nn) nn = tile_bounds(s, t + 2 * (int64_t)gridDim.x, tb);
+    const int64_t b0 = cur.b0;
+    const int nblk = cur.nblk;
     const int64_t e0 = b0 * s.S;
     const int elems = (int)min((int64_t)nblk * s.S, s.N - e0);
+    const int32_t* hb = L.h(smem, bi) + (int)(b0 & 3);
     TileView tv;
-    if (!load_blocks(s, b0, nblk, s_w, s_off, s_stage, stage_words, s_warp, &s_flag, err, tv)) continue;
+    const bool ok = tile_ready(s, cur, cur_ok, L.w(smem, bi), s_off, L.words(smem, bi), s_warp, &s_flag, err, tv);
+    cur = nxt;
+    cur_ok = nxt_ok;
+    nxt = nn;
+    have_nxt = have_nn;
+    bi ^= 1;
+    if (!ok) continue;
 
     const int nsegs = SMALL ? nblk : nblk * s.nseg;
-    for (int seg = tid; seg < nsegs; seg += nt) {
+    // group segments of equal width so each warp runs one specialised unpacker
+    const bool sorted = kWidthSpecialize && s.S >= 32;
+    const int nwork =
+        sorted ? cta_sort_by_width([&](int i) { return (int)tv.w[SMALL ? i : i / s.nseg]; }, nsegs, s_order, s_hist)
+               : nsegs;
+    for (int u = tid; u < nwork; u += nt) {
+      const int seg = sorted ? (int)s_order[u] : u;
+      if (seg == 0xFFFF) continue;
       const int bl = SMALL ? seg : seg / s.nseg;
       const int j = SMALL ? 0 : seg - bl * s.nseg;
       const int64_t b = b0 + bl;
@@ -68,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
       const int cnt = min(32, Sb - 32 * j);
       if (cnt <= 0) continue;
       const uint32_t w = tv.w[bl];
-      const int32_t head = __ldg(s.heads + b);
+      const int32_t head = hb[bl];
       const int r0 = bl * s.S + 32 * j;
       int32_t acc = (KIND == HC_STAGE_P) ? 0 : (SMALL ? head : 0);
       if (w == 0) {
@@ -97,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
         const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
         const int cnt = min(32, Sb - 32 * j);
         if (cnt <= 0) continue;
-        int32_t c = __ldg(s.heads + b);
+        int32_t c = hb[bl];
         for (int jj = 0; jj < j; ++jj) c += s_tot[bl * s.nseg + jj];
         const int r0 = bl * s.S + 32 * j;
         for (int i = 0; i < cnt; ++i) s_out[pidx(r0 + i)] += c;
@@ -122,8 +158,8 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
       done = nv * V;
     }
     for (int i = done + tid; i < elems; i += nt) dst[i] = Conv<OutT>::f(s_out[pidx(i)], te_f, te_d);
-    __syncthreads();
   }
+  cp_async_wait_all();
 }
 
 __global__ void k_copy_heads(const int32_t* __restrict__ heads, int32_t* __restrict__ out, int64_t nb) {
@@ -146,20 +182,23 @@ DevStream dev_stream(const hc_header* h, const void* d_stream) {
   s.G = h->G;
   s.nseg = (h->S + 31) / 32;
   s.wmax = (int)h->wmax;
+  s.gshift = (h->G & (h->G - 1)) == 0 ? __builtin_ctz((unsigned)h->G) : -1;
   return s;
 }
 
-static TileSmem decode_layout(const hc_header* h, bool small) {
+static PipeTileSmem decode_layout(const hc_header* h, bool small, int stage) {
   const int tb = kTileChunks * h->G;
   const int nseg = (h->S + 31) / 32;
-  return tile_smem(tb, 0, h->S, (int)h->wmax, decode_out_words(tb, h->S) + (small ? 0 : tb * nseg));
+  const int nsegmax = small ? tb : tb * nseg;
+  return pipe_tile_smem(tb, stage, decode_out_words(tb, h->S) + (small ? 0 : nsegmax) + (kWidthSpecialize ? round4((nsegmax + 32 * 32 + 1) / 2) : 0));
 }
 
 template <int KIND, class OutT, bool SMALL>
 static int launch_decode(const hc_header* h, const void* d_stream, void* d_out, int* err, cudaStream_t st) {
   const DevStream s = dev_stream(h, d_stream);
-  const TileSmem L = decode_layout(h, SMALL);
-  const int smem = 4 * L.words;
+  const int stage = stage_words_for(kTileChunks * h->G, h->S, (int)h->wmax);
+  const PipeTileSmem L = decode_layout(h, SMALL, stage);
+  const int smem = 4 * L.total;
   auto kern = k_decode<KIND, OutT, SMALL>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (rc) return rc;
@@ -169,8 +208,7 @@ static int launch_decode(const hc_header* h, const void* d_stream, void* d_out, 
   const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm);
   const double te = 2.0 * h->eps;
-  kern<<<grid, kThreads, smem, st>>>(s, reinterpret_cast<OutT*>(d_out), (float)te, te, ntiles, L.stage_words,
-                                     err);
+  kern<<<grid, kThreads, smem, st>>>(s, reinterpret_cast<OutT*>(d_out), (float)te, te, ntiles, stage, err);
   return check_launch_cfg("decompress_to_stage", reinterpret_cast<const void*>(kern), grid, smem);
 }
 

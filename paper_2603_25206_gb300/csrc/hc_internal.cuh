@@ -43,7 +43,16 @@ struct DevStream {
   int64_t N, nb, nchunks, payload_words;
   int S, G, nseg;  // nseg = ceil(S/32): sign words and segments per block
   int wmax;        // largest block width recorded in the header (sizes the staging buffers)
+  int gshift;      // log2(G) when G is a power of two, else -1
 };
+
+// First block of the chunk that holds block b (a shift when G is a power of two).
+__device__ __forceinline__ int64_t chunk_start(const DevStream& s, int64_t b) {
+  return s.gshift >= 0 ? (b >> s.gshift) << s.gshift : (b / s.G) * s.G;
+}
+__device__ __forceinline__ int64_t chunk_of(const DevStream& s, int64_t b) {
+  return s.gshift >= 0 ? (b >> s.gshift) : b / s.G;
+}
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -127,10 +136,100 @@ __device__ __forceinline__ void unpack_segment(const uint32_t* __restrict__ mw, 
   }
 }
 
+
+
+// Width-specialised unpack of one full 32-element segment of width W: the W
+// magnitude words are read into registers once and every value is cut out
+// with compile-time shifts.  f(i, p) is called for i = 0..31 in order.
+template <int W, class F>
+__device__ __forceinline__ void unpack_w(const uint32_t* __restrict__ mw, uint32_t sw, F&& f) {
+  uint32_t r[W + 1];
+#pragma unroll
+  for (int j = 0; j < W; ++j) r[j] = mw[j];
+  r[W] = 0u;
+  constexpr uint32_t mask = (1u << W) - 1u;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int b = i * W, j = b >> 5, sh = b & 31;
+    uint32_t m;
+    if (sh + W <= 32)
+      m = (r[j] >> sh) & mask;
+    else
+      m = __funnelshift_r(r[j], r[j + 1], sh) & mask;
+    const int32_t neg = (int32_t)(sw << (31 - i)) >> 31;
+    f(i, ((int32_t)m ^ neg) - neg);
+  }
+}
+
+// Widest width with a specialised unpacker; wider segments take the
+// sliding-window unpacker (unpack_segment).
+constexpr int kMaxSpecialW = 12;
+
+// Width-specialised unpacking removes the sliding window's per-code checks,
+// but measured on GB300 it was slower in every kernel: warps must first be
+// given segments of one width (a per-tile sort whose padding leaves lanes idle
+// and adds barriers), and the specialised code strains the instruction cache.
+// It is kept switchable; the sliding-window unpacker is the one in use.
+constexpr bool kWidthSpecialize = false;
+
+// Full 32-element segment of any width 1..31 (width 0 is handled by callers).
+template <class F>
+__device__ __forceinline__ void unpack_full(const uint32_t* mw, uint32_t sw, uint32_t w, F&& f) {
+  if constexpr (!kWidthSpecialize) {
+    unpack_segment<true>(mw, sw, w, 32, f);
+    return;
+  }
+  switch (w) {
+#define HC_UNPACK_CASE(W) \
+  case W:                 \
+    unpack_w<W>(mw, sw, f); \
+    break;
+    HC_UNPACK_CASE(1) HC_UNPACK_CASE(2) HC_UNPACK_CASE(3) HC_UNPACK_CASE(4) HC_UNPACK_CASE(5) HC_UNPACK_CASE(6)
+    HC_UNPACK_CASE(7) HC_UNPACK_CASE(8) HC_UNPACK_CASE(9) HC_UNPACK_CASE(10) HC_UNPACK_CASE(11) HC_UNPACK_CASE(12)
+#undef HC_UNPACK_CASE
+    default:
+      unpack_segment<true>(mw, sw, w, 32, f);
+  }
+}
+
+// Counting sort of n (< 65536) items by a key in 0..31 (key(i), read from
+// shared memory) into order[], with every key's run padded to a multiple of
+// 32 entries (holes hold 0xFFFF): a warp taking 32 consecutive entries sees
+// one width, so it runs one specialised unpacker without divergence.
+// Returns the padded length (<= n + 31 * 32).  s_hist: 64 ints of shared
+// scratch.  Every thread of the CTA must call it.
+template <class K>
+__device__ inline int cta_sort_by_width(K&& key, int n, uint16_t* order, int* s_hist) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < 64) s_hist[tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) atomicAdd(&s_hist[key(i) & 31], 1);
+  __syncthreads();
+  if (tid < 32) {
+    const int c = (s_hist[tid] + 31) & ~31;
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (tid >= o) x += y;
+    }
+    s_hist[32 + tid] = x - c;  // start of each padded bin
+    if (tid == 31) s_hist[0] = x;  // padded length (counts are no longer needed)
+  }
+  __syncthreads();
+  const int padded = s_hist[0];
+  for (int i = tid; i < padded; i += nt) order[i] = 0xFFFFu;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) order[atomicAdd(&s_hist[32 + (key(i) & 31)], 1)] = (uint16_t)i;
+  __syncthreads();
+  return padded;
+}
+
+// Any segment: full ones take the width-specialised path.
 template <class F>
 __device__ __forceinline__ void unpack_any(const uint32_t* mw, uint32_t sw, uint32_t w, int count, F&& f) {
   if (count == 32)
-    unpack_segment<true>(mw, sw, w, 32, f);
+    unpack_full(mw, sw, w, f);
   else
     unpack_segment<false>(mw, sw, w, count, f);
 }
@@ -159,7 +258,7 @@ __device__ inline bool load_blocks(const DevStream& s, int64_t b0, int nblk, uin
                                    uint32_t* s_stage, int stage_words, uint32_t* s_warp, int* s_flag,
                                    int* err, TileView& tv) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t cs = (b0 / s.G) * s.G;
+  const int64_t cs = chunk_start(s, b0);
   const int npre = (int)(b0 - cs);
   const int n = npre + nblk;
   if (tid == 0) *s_flag = 0;
@@ -175,15 +274,15 @@ __device__ inline bool load_blocks(const DevStream& s, int64_t b0, int nblk, uin
   }
   __syncthreads();
   cta_exclusive_scan(s_off, n, s_warp);
-  const uint64_t base = s.chunks[cs / s.G] + s_off[npre];
+  const uint64_t base = s.chunks[chunk_of(s, cs)] + s_off[npre];
   const uint32_t first = s_off[npre];
   const uint32_t words = s_off[n] - first;
   if (tid == 0) {
     // every chunk start inside the run (and the run's end, when it is one)
     // must agree with the chunk index
-    const uint64_t c0 = s.chunks[cs / s.G];
+    const uint64_t c0 = s.chunks[chunk_of(s, cs)];
     for (int64_t cb = cs + s.G; cb <= b0 + nblk; cb += s.G) {
-      const uint64_t expect = (cb >= s.nb) ? (uint64_t)s.payload_words : s.chunks[cb / s.G];
+      const uint64_t expect = (cb >= s.nb) ? (uint64_t)s.payload_words : s.chunks[chunk_of(s, cb)];
       if (c0 + s_off[cb - cs] != expect) *s_flag = 1;
     }
     if (b0 + nblk == s.nb && c0 + s_off[n] != (uint64_t)s.payload_words) *s_flag = 1;
@@ -217,6 +316,16 @@ __device__ inline bool load_blocks(const DevStream& s, int64_t b0, int nblk, uin
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
+// cp.async 16-byte global -> shared copies (the caller waits with
+// cp_async_wait_all; both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+
+
 // Size in words of the staging buffer for up to nblk blocks of width at most
 // wmax (a multiple of 4).  A block wider than the header's wmax makes the
 // loader report HC_ERR_CORRUPT instead of overflowing the buffer.
@@ -244,6 +353,109 @@ __host__ __device__ inline TileSmem tile_smem(int nblk_max, int npre_max, int S,
   t.w = t.extra + round4(extra_words);
   t.words = t.w + round4((npre_max + nblk_max + 3) / 4 + 1);
   return t;
+}
+
+// ----------------------------------------------------- chunk-aligned tiles
+// Reductions and whole-stream decoding walk tiles of kTileChunks chunks.  A
+// tile's payload range comes straight from the chunk index, so the next
+// tile's widths, heads and payload are copied into shared memory with
+// cp.async while the current tile is decoded.
+struct TileCopy {
+  int64_t b0;      // first block
+  int nblk;        // blocks
+  uint64_t p0, p1;  // payload words [p0, p1)
+};
+
+__device__ __forceinline__ TileCopy tile_bounds(const DevStream& s, int64_t t, int tb) {
+  TileCopy c;
+  c.b0 = t * tb;
+  c.nblk = (int)min((int64_t)tb, s.nb - c.b0);
+  const int64_t c0 = t * kTileChunks;
+  c.p0 = __ldg(s.chunks + c0);
+  c.p1 = __ldg(s.chunks + min(c0 + kTileChunks, s.nchunks));
+  return c;
+}
+
+// Issue the copies of one tile (every thread of the CTA takes a share).
+// Buffers: w (tb + 32 bytes), h (tb + 8 ints), words (stage_words).  Returns
+// false when the chunk index is inconsistent (nothing is copied then).
+__device__ inline bool tile_issue(const DevStream& s, const TileCopy& c, int stage_words, uint8_t* w, int32_t* h,
+                                  uint32_t* words) {
+  if (c.p1 < c.p0 || c.p1 > (uint64_t)s.payload_words || (int64_t)(c.p1 - c.p0) + 8 > stage_words) return false;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // widths: bytes [b0, b0 + nblk), from a 16-byte aligned start
+  const int64_t w0 = c.b0 & ~(int64_t)15;
+  const int nw = (int)((c.b0 + c.nblk - w0 + 15) >> 4);
+  for (int i = tid; i < nw; i += nt) cp_async16(w + 16 * i, s.widths + w0 + 16 * i);
+  // heads: ints [b0, b0 + nblk)
+  const int64_t h0 = c.b0 & ~(int64_t)3;
+  const int nh = (int)((c.b0 + c.nblk - h0 + 3) >> 2);
+  for (int i = tid; i < nh; i += nt) cp_async16(h + 4 * i, s.heads + h0 + 4 * i);
+  // payload: words [p0, p1] (one word past the end for the unpacker)
+  const uint64_t a0 = c.p0 & ~(uint64_t)3;
+  const int np = (int)((c.p1 + 1 - a0 + 3) >> 2);
+  for (int i = tid; i < np; i += nt) cp_async16(words + 4 * i, s.payload + a0 + 4 * i);
+  return true;
+}
+
+// After the copies of tile c have landed: scan its widths into staging offsets.
+// Fills tv (widths, offsets, payload views into the staged buffers).  Returns
+// false (and records HC_ERR_CORRUPT) if the widths disagree with the chunk
+// index.  Every thread of the CTA must call it.
+__device__ inline bool tile_ready(const DevStream& s, const TileCopy& c, bool issued, const uint8_t* w,
+                                  uint32_t* s_off, const uint32_t* words, uint32_t* s_warp, int* s_flag, int* err,
+                                  TileView& tv) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int wlead = (int)(c.b0 & 15);
+  if (tid == 0) *s_flag = issued ? 0 : 1;
+  __syncthreads();
+  for (int i = tid; i < c.nblk; i += nt) {
+    uint32_t wi = w[wlead + i];
+    if (wi > (uint32_t)s.wmax) {
+      atomicOr(s_flag, 1);
+      wi = 0;
+    }
+    s_off[i] = block_words(s.S, s.nseg, wi);
+  }
+  __syncthreads();
+  const uint32_t total = cta_exclusive_scan(s_off, c.nblk, s_warp);
+  const bool bad = (*s_flag != 0) || (uint64_t)total != c.p1 - c.p0;
+  if (bad) {
+    __syncthreads();
+    if (tid == 0) set_error(err, HC_ERR_CORRUPT);
+    return false;
+  }
+  const int lead = (int)(c.p0 & 3);
+  for (int i = tid; i < c.nblk; i += nt) s_off[i] += lead;
+  __syncthreads();
+  tv.w = w + wlead;
+  tv.off = s_off;
+  tv.words = words;
+  tv.b0 = c.b0;
+  tv.nblk = c.nblk;
+  return true;
+}
+
+// Shared-memory layout (32-bit word offsets) of a kernel walking
+// chunk-aligned tiles with two copy buffers, each [widths | heads | payload],
+// followed by the block offsets and `extra` words of the kernel's own.
+struct PipeTileSmem {
+  int wbuf, hbuf, pbuf, buf;  // offsets inside one buffer; buffer size
+  int off, extra, total;
+  __device__ uint8_t* w(uint32_t* sm, int b) const { return reinterpret_cast<uint8_t*>(sm + b * buf + wbuf); }
+  __device__ int32_t* h(uint32_t* sm, int b) const { return reinterpret_cast<int32_t*>(sm + b * buf + hbuf); }
+  __device__ uint32_t* words(uint32_t* sm, int b) const { return sm + b * buf + pbuf; }
+};
+__host__ __device__ inline PipeTileSmem pipe_tile_smem(int tb, int stage_words, int extra_words) {
+  PipeTileSmem p;
+  p.wbuf = 0;
+  p.hbuf = round4((tb + 32 + 3) / 4);
+  p.pbuf = p.hbuf + round4(tb + 8);
+  p.buf = p.pbuf + round4(stage_words);
+  p.off = 2 * p.buf;
+  p.extra = p.off + round4(tb + 1);
+  p.total = p.extra + round4(extra_words);
+  return p;
 }
 
 // 128-bit helpers ------------------------------------------------------

@@ -78,6 +78,15 @@ int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_sc
 enum StencilOp { ST_DERIV = 0, ST_GRADMAG = 1, ST_LAPLACIAN = 2 };
 int stencil_stream_impl(const hc_header* h, const void* d_stream, int op, int axis3, void* d_out, int out_dtype,
                         void* d_ws, cudaStream_t st);
+// Pipelined fused stencil (block size 32, rows of a multiple of 8, |q| < 2^15);
+// HC_ERR_UNSUPPORTED when it does not apply.  d3 is the (possibly remapped) shape.
+int stencil_pipe_impl(const hc_header* h, const void* d_stream, const int64_t* d3, int op, int axis3, void* d_out,
+                      int out_dtype, void* d_ws, cudaStream_t st);
+// Shape the fused stencils walk: a 2-D field (1, n1, n2) is walked as (n1, 1, n2).
+void stencil_walk_dims(const hc_header* h, int64_t d3[3], int* axis3);
+// Time the pipelined kernel's tile heights for this field/op and cache the best.
+int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_t* d3, int op, void* d_out,
+                          int out_dtype, void* d_ws, cudaStream_t st, int* chosen);
 int stencil_array_impl(const hc_stage* in, const int64_t* dims3, double eps, int op, int axis3, void* d_out,
                        int out_dtype, void* d_ws, cudaStream_t st);
 

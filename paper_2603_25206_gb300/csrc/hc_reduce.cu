@@ -32,6 +32,8 @@ __device__ __forceinline__ int pidx(int r) { return r + (r >> 5); }
 __host__ __device__ inline int seg_moment_words(int nsegmax, bool var) {
   return round4(nsegmax) + round4(2 * nsegmax) + (var ? 4 * nsegmax : 0);
 }
+// words of a uint16 segment-order array
+__host__ __device__ inline int order_words(int nsegmax) { return kWidthSpecialize ? round4((nsegmax + 32 * 32 + 1) / 2) : 0; }
 // padded value tile (33 words per 32 elements)
 __host__ __device__ inline int padded_words(int elems) { return round4(((elems + 31) / 32) * 33 + 4); }
 
@@ -147,27 +149,62 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
   const int tb = kTileChunks * s.G;
   const int nsegmax = SMALL ? tb : tb * s.nseg;
   constexpr bool seg_arrays = (!SMALL && LEVEL == 3);
-  const TileSmem L = tile_smem(tb, 0, s.S, s.wmax, seg_arrays ? seg_moment_words(nsegmax, VAR) : 0);
-  uint32_t* s_stage = smem;
+  const int segw = seg_arrays ? seg_moment_words(nsegmax, VAR) : 0;
+  const PipeTileSmem L = pipe_tile_smem(tb, stage_words, segw + order_words(nsegmax));
   uint32_t* s_off = smem + L.off;
   // per-segment local moments for S > 32 at level 3
   int32_t* s_T = reinterpret_cast<int32_t*>(smem + L.extra);
   long long* s_a1 = reinterpret_cast<long long*>(smem + L.extra + round4(nsegmax));
   u128* s_a2 = reinterpret_cast<u128*>(smem + L.extra + round4(nsegmax) + round4(2 * nsegmax));
-  uint8_t* s_w = reinterpret_cast<uint8_t*>(smem + L.w);
+  uint16_t* s_order = reinterpret_cast<uint16_t*>(smem + L.extra + segw);
+  __shared__ int s_hist[64];
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) s_err = 0;
   long long S1 = 0;
   u128 S2 = 0;
   unsigned long long S2n = 0;  // narrow: 64-bit per-thread sum of q^2
 
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t b0 = t * tb;
-    const int nblk = (int)min((int64_t)tb, s.nb - b0);
+  // two tile buffers: tile t is decoded while tile t + gridDim.x is copied in
+  int64_t t = blockIdx.x;
+  int bi = 0;
+  TileCopy cur{}, nxt{};
+  bool cur_ok = false, have_nxt = false;
+  if (t < ntiles) {
+    cur = tile_bounds(s, t, tb);
+    cur_ok = tile_issue(s, cur, stage_words, L.w(smem, 0), L.h(smem, 0), L.words(smem, 0));
+  }
+  if (t + gridDim.x < ntiles) {
+    nxt = tile_bounds(s, t + gridDim.x, tb);
+    have_nxt = true;
+  }
+  for (; t < ntiles; t += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();
+    bool nxt_ok = false;
+    if (have_nxt) nxt_ok = tile_issue(s, nxt, stage_words, L.w(smem, bi ^ 1), L.h(smem, bi ^ 1), L.words(smem, bi ^ 1));
+    TileCopy nn{};
+    const bool have_nn = t + 2 * (int64_t)gridDim.x < ntiles;
+    if (have_nn) nn = tile_bounds(s, t + 2 * (int64_t)gridDim.x, tb);
+    const int64_t b0 = cur.b0;
+    const int nblk = cur.nblk;
+    const int32_t* hb = L.h(smem, bi) + (int)(b0 & 3);
     TileView tv;
-    if (!load_blocks(s, b0, nblk, s_w, s_off, s_stage, stage_words, s_warp, &s_flag, &s_err, tv)) continue;
+    const bool ok = tile_ready(s, cur, cur_ok, L.w(smem, bi), s_off, L.words(smem, bi), s_warp, &s_flag, &s_err, tv);
+    cur = nxt;
+    cur_ok = nxt_ok;
+    nxt = nn;
+    have_nxt = have_nn;
+    bi ^= 1;
+    if (!ok) continue;
     const int nsegs = SMALL ? nblk : nblk * s.nseg;
-    for (int seg = tid; seg < nsegs; seg += nt) {
+    // group segments of equal width so each warp runs one specialised unpacker
+    const bool sorted = kWidthSpecialize && s.S >= 32;
+    const int nwork =
+        sorted ? cta_sort_by_width([&](int i) { return (int)tv.w[SMALL ? i : i / s.nseg]; }, nsegs, s_order, s_hist)
+               : nsegs;
+    for (int u = tid; u < nwork; u += nt) {
+      const int seg = sorted ? (int)s_order[u] : u;
+      if (seg == 0xFFFF) continue;
       const int bl = SMALL ? seg : seg / s.nseg;
       const int j = SMALL ? 0 : seg - bl * s.nseg;
       const int64_t b = b0 + bl;
@@ -182,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
         continue;
       }
       const uint32_t w = tv.w[bl];
-      const int32_t head = __ldg(s.heads + b);
+      const int32_t head = hb[bl];
       const uint32_t* blk = tv.words + tv.off[bl];
       if constexpr (LEVEL == 2) {
         // Section V-A, stage 2: sum_k (S_b - k) p_k with the head as p_0
@@ -291,7 +328,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
         const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
         const int cnt = min(32, Sb - 32 * j);
         if (cnt <= 0) continue;
-        long long c = __ldg(s.heads + b);
+        long long c = hb[bl];
         for (int jj = 0; jj < j; ++jj) c += s_T[bl * s.nseg + jj];
         const long long a1 = s_a1[seg];
         S1 += (long long)cnt * c + a1;
@@ -301,8 +338,8 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
         }
       }
     }
-    __syncthreads();
   }
+  cp_async_wait_all();
   if (ACC == 0 && VAR) S2 += S2n;
   __syncthreads();
   const int err = s_err;
@@ -416,10 +453,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce_p_array(const int32_t* __re
 }
 
 // ------------------------------------------------------- materialized D_f
-// The plain path: statistics of a float array.  Each thread keeps compensated
-// float32 sums of (x - c) and (x - c)^2 around its first element c; the
-// per-thread (count, mean, M2) triples are merged in double with the
-// pairwise update of Chan et al.  No integer information is used.
+// The plain path: statistics of a float array in its own precision.  All
+// threads use one shift c (the array's first value): each keeps compensated
+// sums of d = x - c and d^2, warps add them in the array's type, CTAs in
+// double, and the last CTA adds the per-CTA partials in parallel:
+//   mean = c + S1 / N,   variance = (S2 - S1^2 / N) / (N - 1).
+// No integer information is used.
 template <class T>
 __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
   const T y = v - c;
@@ -428,59 +467,55 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
   s = t;
 }
 
-struct Moments {
-  double n, mean, m2;
-};
-__device__ __forceinline__ Moments merge(Moments a, Moments b) {
-  if (a.n == 0) return b;
-  if (b.n == 0) return a;
-  Moments r;
-  r.n = a.n + b.n;
-  const double d = b.mean - a.mean;
-  r.mean = a.mean + d * (b.n / r.n);
-  r.m2 = a.m2 + b.m2 + d * d * (a.n * b.n / r.n);
-  return r;
-}
-__device__ __forceinline__ Moments shfl_down_m(Moments m, int o) {
-  Moments r;
-  r.n = __shfl_down_sync(0xffffffffu, m.n, o);
-  r.mean = __shfl_down_sync(0xffffffffu, m.mean, o);
-  r.m2 = __shfl_down_sync(0xffffffffu, m.m2, o);
-  return r;
-}
-
 template <class T, bool VAR>
 __global__ void __launch_bounds__(kThreads) k_reduce_f_array(const T* __restrict__ f, int64_t n, Partial* parts,
                                                               unsigned* ticket, hc_scalar* out) {
-  __shared__ Moments r_m[32];
+  __shared__ double r1[32], r2[32];
   __shared__ int s_last;
+  constexpr int V = 16 / sizeof(T);
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int64_t nv = ((reinterpret_cast<uintptr_t>(f) & 15u) == 0) ? n / V : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const T c = f[0];
   T s = 0, cs = 0, s2 = 0, c2 = 0;
-  const T c = i0 < n ? f[i0] : T(0);
-  double cnt = 0;
-  for (int64_t i = i0; i < n; i += stride) {
+  for (int64_t v = i0; v < nv; v += stride) {
+    const Vec x = reinterpret_cast<const Vec*>(f)[v];
+    const T* xe = reinterpret_cast<const T*>(&x);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const T d = xe[k] - c;
+      kahan_add(s, cs, d);
+      if (VAR) kahan_add(s2, c2, d * d);
+    }
+  }
+  for (int64_t i = nv * V + i0; i < n; i += stride) {
     const T d = f[i] - c;
     kahan_add(s, cs, d);
     if (VAR) kahan_add(s2, c2, d * d);
-    cnt += 1.0;
   }
-  Moments m;
-  m.n = cnt;
-  m.mean = cnt > 0 ? (double)c + (double)s / cnt : 0.0;
-  m.m2 = cnt > 0 ? (double)s2 - (double)s * (double)s / cnt : 0.0;
+  T a = s - cs, b = s2 - c2;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = merge(m, shfl_down_m(m, o));
-  if (lane == 0) r_m[wid] = m;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    r1[wid] = (double)a;
+    r2[wid] = (double)b;
+  }
   __syncthreads();
   if (tid == 0) {
-    Moments a = r_m[0];
-    for (int k = 1; k < nw; ++k) a = merge(a, r_m[k]);
+    double A = 0, B = 0;
+    for (int k = 0; k < nw; ++k) {
+      A += r1[k];
+      B += r2[k];
+    }
     Partial p;
-    p.s1 = __double_as_longlong(a.n);
-    p.s2_lo = (unsigned long long)__double_as_longlong(a.mean);
-    p.s2_hi = (unsigned long long)__double_as_longlong(a.m2);
+    p.s1 = __double_as_longlong(A);
+    p.s2_lo = (unsigned long long)__double_as_longlong(B);
+    p.s2_hi = 0;
     p.err = 0;
     p.pad = 0;
     parts[blockIdx.x] = p;
@@ -488,25 +523,41 @@ __global__ void __launch_bounds__(kThreads) k_reduce_f_array(const T* __restrict
     s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || tid != 0) return;
+  if (!s_last) return;
   __threadfence();
-  Moments a{0, 0, 0};
-  for (int k = 0; k < (int)gridDim.x; ++k) {
-    Moments b;
-    b.n = __longlong_as_double(__ldcg(&parts[k].s1));
-    b.mean = __longlong_as_double((long long)__ldcg(&parts[k].s2_lo));
-    b.m2 = __longlong_as_double((long long)__ldcg(&parts[k].s2_hi));
-    a = merge(a, b);
+  double A = 0, B = 0;
+  for (int k = tid; k < (int)gridDim.x; k += blockDim.x) {
+    A += __longlong_as_double(__ldcg(&parts[k].s1));
+    B += __longlong_as_double((long long)__ldcg(&parts[k].s2_lo));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    A += __shfl_down_sync(0xffffffffu, A, o);
+    B += __shfl_down_sync(0xffffffffu, B, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    r1[wid] = A;
+    r2[wid] = B;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  A = 0;
+  B = 0;
+  for (int k = 0; k < nw; ++k) {
+    A += r1[k];
+    B += r2[k];
+  }
+  const double nd = (double)n;
   out->n = n;
   out->s1 = 0;
   out->s2_lo = 0;
   out->s2_hi = 0;
   out->status = 0;
   out->exact = 0;
-  out->mean = a.mean;
+  out->mean = (double)c + A / nd;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
-  out->variance = (VAR && n >= 2) ? a.m2 / (double)(n - 1) : nan;
+  out->variance = (VAR && n >= 2) ? (B - A * A / nd) / (nd - 1.0) : nan;
   out->std = sqrt(out->variance);
   *ticket = 0;
 }
@@ -525,9 +576,10 @@ static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_
   const int tb = kTileChunks * h->G;
   const int nseg = (h->S + 31) / 32;
   const int nsegmax = SMALL ? tb : tb * nseg;
-  const TileSmem L = tile_smem(tb, 0, h->S, (int)h->wmax, (!SMALL && LEVEL == 3) ? seg_moment_words(nsegmax, VAR) : 0);
-  const int bytes = 4 * L.words;
-  const int stage = L.stage_words;
+  const int stage = stage_words_for(tb, h->S, (int)h->wmax);
+  const PipeTileSmem L =
+      pipe_tile_smem(tb, stage, ((!SMALL && LEVEL == 3) ? seg_moment_words(nsegmax, VAR) : 0) + order_words(nsegmax));
+  const int bytes = 4 * L.total;
   auto kern = k_reduce_stream<LEVEL, ACC, VAR, SMALL>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
   if (rc) return rc;
@@ -661,8 +713,10 @@ static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scala
   const int tb = kTileChunks * h->G;
   const int nseg = (h->S + 31) / 32;
   const int nsegmax = SMALL ? tb : tb * nseg;
-  const TileSmem L = tile_smem(tb, 0, h->S, (int)h->wmax, !SMALL ? seg_moment_words(nsegmax, true) : 0);
-  const int bytes = 4 * L.words;
+  const int stage = stage_words_for(tb, h->S, (int)h->wmax);
+  const PipeTileSmem L =
+      pipe_tile_smem(tb, stage, (!SMALL ? seg_moment_words(nsegmax, true) : 0) + order_words(nsegmax));
+  const int bytes = 4 * L.total;
   auto kern = k_reduce_stream<3, ACC, true, SMALL>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
   if (rc) return rc;
@@ -672,7 +726,7 @@ static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scala
   const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm);
   if (grid > max_parts) return fail(HC_ERR_NOMEM, "the static scratch of hc_op_variance_noalloc has too few partial slots for this GPU");
-  kern<<<(unsigned)grid, kThreads, bytes, st>>>(s, ntiles, L.stage_words, parts, ticket, d_out, 2.0 * h->eps);
+  kern<<<(unsigned)grid, kThreads, bytes, st>>>(s, ntiles, stage, parts, ticket, d_out, 2.0 * h->eps);
   return check_launch_cfg("variance (static scratch)", reinterpret_cast<const void*>(kern), grid, bytes);
 }
 

@@ -24,6 +24,7 @@
 // Array form: the same stencils on a materialized D_q (exact) or D_f (the
 // plain path, in the field's floating-point type).
 #include <cstdint>
+#include <cstdlib>
 #include <type_traits>
 
 #include "hc_internal.cuh"
@@ -116,8 +117,10 @@ __device__ inline int64_t decode_range(const DevStream& s, int64_t e0, int64_t e
     if (w == 0) {
       for (int i = 0; i < cnt; ++i) dst[pidx(r0 + i)] = acc;
     } else {
+      // the general kernel keeps the compact sliding-window unpacker (the
+      // pipelined kernel carries the width-specialised one)
       const uint32_t* blk = tv.words + tv.off[bl];
-      unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
+      unpack_segment<false>(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
         acc += p;
         dst[pidx(r0 + i)] = acc;
       });
@@ -384,6 +387,64 @@ __global__ void __launch_bounds__(kThreads) k_stencil_array(const In* __restrict
   }
 }
 
+// Plain path, 4 outputs per thread (rows a multiple of 4, 16-byte aligned
+// arrays): the same formulas as k_stencil_array with vector loads and stores.
+template <int OP, int OUT, class In>
+__global__ void __launch_bounds__(kThreads) k_stencil_array4(const In* __restrict__ a, Geo g,
+                                                              typename OutType<OUT>::T* __restrict__ out) {
+  using R = typename OutType<OUT>::T;
+  using V4 = typename std::conditional<sizeof(In) == 4, int4, longlong4>::type;
+  const int64_t rows = g.n0 * g.n1, pl = g.n1 * g.n2;
+  const int nq = (int)(g.n2 / 4);
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int64_t z = r / g.n1, y = r - z * g.n1;
+    const int64_t rb = r * g.n2;
+    const int64_t ym = y > 0 ? -g.n2 : 0, yp = y + 1 < g.n1 ? g.n2 : 0;
+    const int64_t zm = z > 0 ? -pl : 0, zp = z + 1 < g.n0 ? pl : 0;
+    const bool yedge = (y == 0 || y == g.n1 - 1), zedge = (z == 0 || z == g.n0 - 1);
+    for (int xq = threadIdx.x; xq < nq; xq += blockDim.x) {
+      const int64_t i = rb + 4 * xq;
+      In c[4], vym[4], vyp[4], vzm[4], vzp[4];
+      *reinterpret_cast<V4*>(c) = *reinterpret_cast<const V4*>(a + i);
+      *reinterpret_cast<V4*>(vym) = *reinterpret_cast<const V4*>(a + i + ym);
+      *reinterpret_cast<V4*>(vyp) = *reinterpret_cast<const V4*>(a + i + yp);
+      *reinterpret_cast<V4*>(vzm) = *reinterpret_cast<const V4*>(a + i + zm);
+      *reinterpret_cast<V4*>(vzp) = *reinterpret_cast<const V4*>(a + i + zp);
+      const In xl = xq > 0 ? __ldg(a + i - 1) : c[0];
+      const In xr = 4 * xq + 4 < g.n2 ? __ldg(a + i + 4) : c[3];
+      R res[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t x = 4 * xq + k;
+        const In cm = k == 0 ? xl : c[k - 1];
+        const In cp = k == 3 ? xr : c[k + 1];
+        const bool xedge = (x == 0 || x == g.n2 - 1);
+        if constexpr (OP == ST_LAPLACIAN) {
+          const In v = ((vzm[k] + vzp[k]) - In(2) * c[k]) + ((vym[k] + vyp[k]) - In(2) * c[k]) +
+                       ((cm + cp) - In(2) * c[k]);
+          res[k] = (R)v;
+        } else {
+          auto der = [&](In m, In p, bool edge) -> In {
+            const In v = p - m;
+            return edge ? v : v * In(0.5);
+          };
+          In d0 = 0, d1 = 0, d2 = 0;
+          if (OP == ST_GRADMAG || g.axis == 0) d0 = g.n0 > 1 ? der(vzm[k], vzp[k], zedge) : In(0);
+          if (OP == ST_GRADMAG || g.axis == 1) d1 = g.n1 > 1 ? der(vym[k], vyp[k], yedge) : In(0);
+          if (OP == ST_GRADMAG || g.axis == 2) d2 = g.n2 > 1 ? der(cm, cp, xedge) : In(0);
+          if constexpr (OP == ST_DERIV)
+            res[k] = (R)(g.axis == 0 ? d0 : (g.axis == 1 ? d1 : d2));
+          else
+            res[k] = (R)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        }
+      }
+      R* o = out + i;
+#pragma unroll
+      for (int v = 0; v < (int)(4 * sizeof(R) / 16); ++v) reinterpret_cast<uint4*>(o)[v] = reinterpret_cast<const uint4*>(res)[v];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host
 static Geo base_geo(const int64_t* dims3, double eps, int axis3) {
   Geo g{};
@@ -500,12 +561,15 @@ static int launch_stream_o(const hc_header* h, const void* d_stream, const Geo& 
 int stencil_stream_impl(const hc_header* h, const void* d_stream, int op, int axis3, void* d_out, int out_dtype,
                         void* d_ws, cudaStream_t st) {
   int* err = &reinterpret_cast<OpWs*>(d_ws)->status;
-  int64_t d3[3] = {h->dims[0], h->dims[1], h->dims[2]};
-  if (d3[0] == 1 && d3[1] > 1) {
-    // a 2-D field marches along its rows: (1, n1, n2) is walked as (n1, 1, n2)
-    d3[0] = d3[1];
-    d3[1] = 1;
-    if (axis3 == 1) axis3 = 0;
+  // a 2-D field marches along its rows: (1, n1, n2) is walked as (n1, 1, n2)
+  int64_t d3[3];
+  stencil_walk_dims(h, d3, &axis3);
+  // the pipelined kernel covers block size 32 with rows of a multiple of 8
+  // codes and |q| < 2^15; everything else takes the general kernel below
+  static const bool force_general = std::getenv("HC_FORCE_GENERAL_STENCIL") != nullptr;
+  if (!force_general) {
+    const int rc = stencil_pipe_impl(h, d_stream, d3, op, axis3, d_out, out_dtype, d_ws, st);
+    if (rc != HC_ERR_UNSUPPORTED) return rc;
   }
   const Geo g = base_geo(d3, h->eps, axis3);
   switch (op) {
@@ -522,6 +586,13 @@ template <int OP, int OUT, class In>
 static int launch_array(const void* d_in, const Geo& g, void* d_out, cudaStream_t st) {
   const int64_t rows = g.n0 * g.n1;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(rows, (int64_t)device_sms() * 16));
+  if constexpr (!std::is_integral<In>::value) {
+    if (g.n2 % 4 == 0 && aligned16(d_in) && aligned16(d_out)) {
+      k_stencil_array4<OP, OUT, In><<<grid, kThreads, 0, st>>>(reinterpret_cast<const In*>(d_in), g,
+                                                               reinterpret_cast<typename OutType<OUT>::T*>(d_out));
+      return check_launch("stencil (array, 4-wide)");
+    }
+  }
   k_stencil_array<OP, OUT, In><<<grid, kThreads, 0, st>>>(reinterpret_cast<const In*>(d_in), g,
                                                           reinterpret_cast<typename OutType<OUT>::T*>(d_out));
   return check_launch("stencil (array)");
@@ -570,4 +641,18 @@ int stencil_array_impl(const hc_stage* in, const int64_t* dims3, double eps, int
   return fail(HC_ERR_INVALID_ARG, "stencils take a stream or a Q or F array");
 }
 
+}  // namespace hc
+
+namespace hc {
+// The (possibly remapped) 3-D shape the fused stencil kernels walk.
+void stencil_walk_dims(const hc_header* h, int64_t d3[3], int* axis3) {
+  d3[0] = h->dims[0];
+  d3[1] = h->dims[1];
+  d3[2] = h->dims[2];
+  if (d3[0] == 1 && d3[1] > 1) {
+    d3[0] = d3[1];
+    d3[1] = 1;
+    if (axis3 && *axis3 == 1) *axis3 = 0;
+  }
+}
 }  // namespace hc

@@ -28,6 +28,9 @@ HC_ERR_CUDA, HC_ERR_NOMEM, HC_ERR_TIMEOUT = 5, 6, 7
 HC_F32, HC_F64, HC_I32, HC_I64 = 0, 1, 2, 3
 HC_EB_ABS, HC_EB_REL = 0, 1
 HC_STAGE_COMPRESSED, HC_STAGE_M, HC_STAGE_P, HC_STAGE_Q, HC_STAGE_F = 0, 1, 2, 3, 4
+HC_OP_MEAN, HC_OP_VARIANCE, HC_OP_DERIVATIVE, HC_OP_GRADMAG, HC_OP_LAPLACIAN = 0, 1, 2, 3, 4
+OPS = {"mean": HC_OP_MEAN, "variance": HC_OP_VARIANCE, "derivative": HC_OP_DERIVATIVE, "gradmag": HC_OP_GRADMAG,
+       "laplacian": HC_OP_LAPLACIAN}
 
 STAGES = {"m": HC_STAGE_M, "p": HC_STAGE_P, "q": HC_STAGE_Q, "f": HC_STAGE_F}
 
@@ -36,7 +39,7 @@ ABI_FUNCTIONS = (
     "hc_status_str", "hc_last_error", "hc_version", "hc_compress_bound", "hc_compress_workspace_bytes",
     "hc_workspace_bytes", "hc_stage_bytes", "hc_compress", "hc_compress_codes", "hc_read_header",
     "hc_decompress_to_stage", "hc_workspace_status", "hc_op_mean", "hc_op_variance", "hc_op_std",
-    "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc",
+    "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc", "hc_autotune",
 )
 
 
@@ -110,6 +113,7 @@ def lib():
             "hc_op_derivative": ([P(HcStage), dbl, i32, P(ctypes.c_int64), i32, vp, i32, vp, sz, vp], i32),
             "hc_op_gradmag": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_op_laplacian": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
+            "hc_autotune": ([P(HcStage), i32, i32, vp, vp, sz, vp, P(ctypes.c_int)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -375,3 +379,15 @@ def laplacian(inp, out_dtype: str = "float32", out=None, level: str = "q", strea
 def workspace_status(stream=None) -> int:
     ws = workspace(None, stream)
     return int(lib().hc_workspace_status(ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
+
+
+def autotune(c: Compressed, op: str, out_dtype: str = "float32", out=None, stream=None) -> int:
+    """Time the fused stencil's tile heights for this field and op; later calls use the fastest."""
+    torch = _torch()
+    st = c.stage("q")
+    out = _field_out(c.shape, out_dtype, c.stream.device, out)
+    ws = workspace(c.stream.device, stream)
+    chosen = ctypes.c_int()
+    _check(lib().hc_autotune(ctypes.byref(st), OPS[op], _OUT[out_dtype], ctypes.c_void_p(out.data_ptr()),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), ctypes.byref(chosen)))
+    return chosen.value

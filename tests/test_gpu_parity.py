@@ -54,6 +54,11 @@ def _cases():
     yield "single", np.array([0.25], np.float32), 1e-3, False, 32
     yield "constant", np.full((8, 9, 10), 3.5, np.float32), 1e-3, True, 32
     yield "two_point_axis", synth.grf_field((2, 3, 40), 19), 1e-3, True, 32
+    # shapes the pipelined stencil kernel takes (S = 32, rows of a multiple of 8)
+    yield "pipe_ragged_3d", synth.grf_field((7, 13, 40), 24), 1e-3, True, 32
+    yield "pipe_2d", synth.grf_field((33, 24), 25), 1e-3, True, 32
+    yield "pipe_2planes", synth.grf_field((2, 9, 16), 26), 1e-4, True, 32
+    yield "pipe_tall", synth.grf_field((40, 70, 8), 27), 1e-2, True, 32
     yield "wide_f64", synth.wide_field((8, 16, 64), 20), 1e-6, True, 64
     x = r.standard_normal((6, 7, 8)).astype(np.float64)
     rng_ = float(x.max() - x.min())
@@ -257,3 +262,21 @@ def test_kernel_reuse_across_tile_sizes(env, orc):
         assert np.array_equal(hc.decompress(c, "q").cpu().numpy(), q)
         r = hc.parse_scalar(hc.variance(c))
         assert (r["s1"], r["s2"]) == orc.sums_q(q)
+
+
+def test_autotune_keeps_results_exact(env, orc):
+    """hc_autotune times the fused stencil's tile heights; whatever it keeps,
+    the outputs stay bit-exact (integer) and within tolerance (float)."""
+    hc, torch, dev = env
+    import synth
+
+    x = synth.grf_field((6, 40, 96), 31)
+    ref, eps = orc.compress(x, 1e-3, True, 32)
+    q = orc.decode(ref, "q")
+    c = hc.compress(torch.from_numpy(x).to(dev), 1e-3)
+    assert hc.autotune(c, "laplacian", "int64") in (1, 2, 4, 8, 16)
+    assert np.array_equal(hc.laplacian(c, out_dtype="int64").cpu().numpy(), orc.lap_q(q))
+    assert hc.autotune(c, "derivative", "float32") in (1, 2, 4, 8, 16)
+    for ax in range(3):
+        _close(hc.derivative(c, ax).cpu().numpy(), orc.stencil_q(q, orc.KIND_DERIV, eps, ax), RTOL_F32, eps)
+    assert hc.autotune(c, "mean") == 0  # statistics have no tile to tune
