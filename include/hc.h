@@ -225,6 +225,84 @@ HC_API int hc_op_gradmag(const hc_stage* in, double eps, int ndim, const int64_t
 HC_API int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
                     void* d_ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------- batched fused launch */
+/* Many compressed fields, each with its own operations, decoded and operated
+ * on by ONE persistent kernel: decoding and operation fused, no stage
+ * materialized (Section V's homomorphic operations, batched; the batching
+ * itself has no counterpart in the paper).  Statistics are taken at stage Q
+ * ("Operation with D_q", Section V-A: exact s1 = sum q, s2 = sum q^2 and the
+ * final scaling of Eq. var_q); stencils follow Section V-B exactly as
+ * hc_op_derivative / hc_op_gradmag / hc_op_laplacian do on a stream.  A field
+ * with both a stencil and statistics is read once: the stencil pass also
+ * accumulates the sums.
+ *
+ * Use: hc_batch_plan (host only) writes a plan into caller host memory; the
+ * caller copies those plan bytes unchanged into a 16-byte aligned device
+ * buffer; hc_batch_run launches the kernel (ASYNC, capturable in a CUDA
+ * graph), or hc_batch_graph_create captures it once and hc_batch_graph_launch
+ * replays it.  The device plan, the streams and the outputs must stay valid
+ * while launches that use them run.
+ *
+ * Workspace (hc_batch_workspace_bytes(n), 16-byte aligned, device): must be
+ * zero-filled before its first use; every launch leaves it zeroed again
+ * except the status word.  One workspace serves one launch at a time:
+ * concurrent launches need separate workspaces.  Errors found by the kernel
+ * (a corrupt stream) go to the field's hc_scalar.status and to the status
+ * word read by hc_batch_status. */
+typedef enum {
+  HC_BATCH_MEAN = 1,        /* d_scalar: mean; exact s1 */
+  HC_BATCH_VARIANCE = 2,    /* d_scalar: mean, variance, std; exact s1, s2 */
+  HC_BATCH_DERIVATIVE = 4,  /* d_field: derivative along `axis` */
+  HC_BATCH_GRADMAG = 8,     /* d_field: gradient magnitude */
+  HC_BATCH_LAPLACIAN = 16   /* d_field: Laplacian */
+} hc_batch_op;
+
+typedef struct hc_batch_item {
+  const void* d_stream;  /* device: the compressed stream, 16-byte aligned */
+  hc_header hdr;         /* host copy of its header (hc_read_header / hc_compress) */
+  uint32_t ops;          /* OR of hc_batch_op, with at most one field operation */
+  int32_t axis;          /* HC_BATCH_DERIVATIVE: user axis in [0, ndim) */
+  hc_scalar* d_scalar;   /* device: statistics result, or NULL without MEAN / VARIANCE */
+  void* d_field;         /* device: N outputs of field_dtype, or NULL without a field op */
+  int32_t field_dtype;   /* HC_F32, HC_F64, or HC_I64 (exact numerators; not GRADMAG) */
+  int32_t reserved;
+} hc_batch_item;
+
+/* Launch shape of the batch kernel (GPU tiling choices, no counterpart in
+ * the paper).  Zero fields take the defaults. */
+typedef struct hc_batch_tune {
+  int32_t threads;      /* threads per CTA: 128, 256 (default) or 512 */
+  int32_t ty;           /* largest stencil tile height in rows (16, 8, 4, 2 or 1); 0: largest that fits */
+  int64_t unit_elems;   /* output points per stencil work unit; 0: about six units per CTA */
+  int32_t ctas_per_sm;  /* upper limit on resident CTAs per SM; 0: occupancy limit */
+  int32_t reserved;
+} hc_batch_tune;
+
+/* Bytes of a plan / of the workspace for n items (0 for n < 1). */
+HC_API size_t hc_batch_plan_bytes(int n_items);
+HC_API size_t hc_batch_workspace_bytes(int n_items);
+/* Validate the items and build the plan in h_plan (host memory, cap bytes);
+ * *used receives its size.  Host only, but it queries the current device's
+ * occupancy and sets the kernel's shared-memory limit.  Errors:
+ * HC_ERR_INVALID_ARG (bad item or tune), HC_ERR_CORRUPT (inconsistent
+ * header), HC_ERR_NOMEM (cap too small), HC_ERR_UNSUPPORTED (a tile does not
+ * fit in shared memory, or GRADMAG with HC_I64). */
+HC_API int hc_batch_plan(const hc_batch_item* items, int n_items, const hc_batch_tune* tune, void* h_plan,
+                         size_t cap, size_t* used);
+/* Launch the batch on `stream`.  h_plan: the host plan; d_plan: its device
+ * copy.  ASYNC. */
+HC_API int hc_batch_run(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_bytes, void* stream);
+/* Capture one hc_batch_run into an instantiated CUDA graph (*graph_exec,
+ * owned by the caller: hc_batch_graph_destroy), replayed by
+ * hc_batch_graph_launch on any stream.  SYNC for the capture itself. */
+HC_API int hc_batch_graph_create(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_bytes,
+                                 void** graph_exec);
+HC_API int hc_batch_graph_launch(void* graph_exec, void* stream);
+HC_API int hc_batch_graph_destroy(void* graph_exec);
+/* Read and clear the batch workspace's status word (first error of any
+ * launch since the last call).  SYNC on `stream`. */
+HC_API int hc_batch_status(void* d_ws, void* stream);
+
 /* ---------------------------------------------------------------- tuning */
 /* Autotuner of the fused stencil kernel (no counterpart in the paper: a GPU
  * tiling choice).  For a compressed-stream input and op (HC_OP_DERIVATIVE,

@@ -119,6 +119,29 @@ static uint64_t le(const uint8_t* b, int off, int n) {
   return v;
 }
 
+// Consistency of a header's fields with one another (the checks that need no
+// device access).
+int check_header(const hc_header& h) {
+  if (h.dtype != HC_F32 && h.dtype != HC_F64) return fail(HC_ERR_CORRUPT, "bad dtype");
+  if (h.ndim < 1 || h.ndim > 3) return fail(HC_ERR_CORRUPT, "bad ndim");
+  for (int a = 0; a < 3 - h.ndim; ++a)
+    if (h.dims[a] != 1) return fail(HC_ERR_CORRUPT, "leading dims must be 1");
+  Layout L;
+  int64_t d[3];
+  for (int a = 0; a < h.ndim; ++a) d[a] = h.dims[3 - h.ndim + a];
+  if (make_layout(h.ndim, d, h.S, &L) != HC_OK) return fail(HC_ERR_CORRUPT, "bad shape or block size");
+  if (L.N != h.N || L.nb != h.nb || L.G != h.G || L.nchunks != h.nchunks || L.off_widths != h.off_widths ||
+      L.off_heads != h.off_heads || L.off_chunks != h.off_chunks || L.off_payload != h.off_payload)
+    return fail(HC_ERR_CORRUPT, "section offsets do not follow from the shape");
+  if (h.payload_words < 0 || h.total_bytes != align16(h.off_payload + 4 * h.payload_words + 16))
+    return fail(HC_ERR_CORRUPT, "payload size and total size disagree");
+  if ((size_t)h.total_bytes > L.bound) return fail(HC_ERR_CORRUPT, "payload larger than any valid stream");
+  if (h.wmax > 31) return fail(HC_ERR_CORRUPT, "max width above 31");
+  if (!(h.eps > 0.0) || !std::isfinite(h.eps)) return fail(HC_ERR_CORRUPT, "bad eps");
+  if (h.qmax >= (1u << 30)) return fail(HC_ERR_CORRUPT, "max |q| out of range");
+  return HC_OK;
+}
+
 int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st) {
   if (!d_stream || !out) return fail(HC_ERR_INVALID_ARG, "null pointer");
   if (bytes < (size_t)kHeaderBytes) return fail(HC_ERR_CORRUPT, "stream shorter than its header");
@@ -149,24 +172,9 @@ int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStr
   h.off_payload = (int64_t)le(b, 120, 8);
   h.total_bytes = (int64_t)le(b, 128, 8);
   h.wmax = (uint32_t)le(b, 136, 4);
-  if (h.dtype != HC_F32 && h.dtype != HC_F64) return fail(HC_ERR_CORRUPT, "bad dtype");
-  if (h.ndim < 1 || h.ndim > 3) return fail(HC_ERR_CORRUPT, "bad ndim");
-  for (int a = 0; a < 3 - h.ndim; ++a)
-    if (h.dims[a] != 1) return fail(HC_ERR_CORRUPT, "leading dims must be 1");
-  Layout L;
-  int64_t d[3];
-  for (int a = 0; a < h.ndim; ++a) d[a] = h.dims[3 - h.ndim + a];
-  if (make_layout(h.ndim, d, h.S, &L) != HC_OK) return fail(HC_ERR_CORRUPT, "bad shape or block size");
-  if (L.N != h.N || L.nb != h.nb || L.G != h.G || L.nchunks != h.nchunks || L.off_widths != h.off_widths ||
-      L.off_heads != h.off_heads || L.off_chunks != h.off_chunks || L.off_payload != h.off_payload)
-    return fail(HC_ERR_CORRUPT, "section offsets do not follow from the shape");
-  if (h.payload_words < 0 || h.total_bytes != align16(h.off_payload + 4 * h.payload_words + 16))
-    return fail(HC_ERR_CORRUPT, "payload size and total size disagree");
+  int rc = check_header(h);
+  if (rc) return rc;
   if ((size_t)h.total_bytes > bytes) return fail(HC_ERR_CORRUPT, "stream truncated");
-  if ((size_t)h.total_bytes > L.bound) return fail(HC_ERR_CORRUPT, "payload larger than any valid stream");
-  if (h.wmax > 31) return fail(HC_ERR_CORRUPT, "max width above 31");
-  if (!(h.eps > 0.0) || !std::isfinite(h.eps)) return fail(HC_ERR_CORRUPT, "bad eps");
-  if (h.qmax >= (1u << 30)) return fail(HC_ERR_CORRUPT, "max |q| out of range");
   *out = h;
   return HC_OK;
 }
@@ -395,5 +403,23 @@ int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_
   stencil_walk_dims(in->hdr, d3, nullptr);
   return stencil_pipe_autotune(in->hdr, in->d_data, d3, sop, d_out, out_dtype, d_ws, as_stream(stream), chosen);
 }
+
+size_t hc_batch_plan_bytes(int n_items) { return (size_t)batch_plan_bytes(n_items); }
+size_t hc_batch_workspace_bytes(int n_items) { return (size_t)batch_ws_bytes(n_items); }
+int hc_batch_plan(const hc_batch_item* items, int n_items, const hc_batch_tune* tune, void* h_plan, size_t cap,
+                  size_t* used) {
+  return batch_plan_impl(items, n_items, tune, h_plan, cap, used);
+}
+int hc_batch_run(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_bytes, void* stream) {
+  return batch_run_impl(h_plan, d_plan, d_ws, ws_bytes, as_stream(stream));
+}
+int hc_batch_graph_create(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_bytes, void** graph_exec) {
+  return batch_graph_impl(h_plan, d_plan, d_ws, ws_bytes, graph_exec);
+}
+int hc_batch_graph_launch(void* graph_exec, void* stream) {
+  return batch_graph_launch_impl(graph_exec, as_stream(stream));
+}
+int hc_batch_graph_destroy(void* graph_exec) { return batch_graph_destroy_impl(graph_exec); }
+int hc_batch_status(void* d_ws, void* stream) { return batch_status_impl(d_ws, as_stream(stream)); }
 
 }  // extern "C"

@@ -489,4 +489,26 @@ __device__ inline double i128_to_double(i128 x) {
   return neg ? -r : r;
 }
 
+// Final scaling of exact sums into a statistic result (Section V-A, Eq. var_q):
+//   mean = (s1 / N) * 2 eps,
+//   var  = ((N s2 - s1^2) / (N (N - 1))) * (2 eps)^2   (exact 128-bit numerator).
+__device__ inline void finalize_int(hc_scalar* out, int64_t n, long long s1, u128 s2, bool var, double two_eps,
+                                    int err) {
+  out->n = n;
+  out->s1 = s1;
+  out->s2_lo = var ? (unsigned long long)s2 : 0ull;
+  out->s2_hi = var ? (unsigned long long)(s2 >> 64) : 0ull;
+  out->status = err;
+  out->exact = 1;
+  out->mean = (__ll2double_rn(s1) / (double)n) * two_eps;
+  double v = __longlong_as_double(0x7ff8000000000000ll);  // NaN: not computed / undefined
+  if (var && n >= 2) {
+    const i128 num = (i128)n * (i128)s2 - (i128)s1 * (i128)s1;
+    const double den = (double)n * (double)(n - 1);
+    v = (i128_to_double(num) / den) * (two_eps * two_eps);
+  }
+  out->variance = v;
+  out->std = sqrt(v);
+}
+
 }  // namespace hc

@@ -37,6 +37,8 @@ int check_launch_cfg(const char* what, const void* kernel, long long grid, int s
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it).
 int ensure_smem(const void* kernel, int bytes);
 
+// Consistency checks of a header (no device access).
+int check_header(const hc_header& h);
 int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st);
 
 int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int64_t* dims, double eb,
@@ -89,5 +91,16 @@ int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_
                           int out_dtype, void* d_ws, cudaStream_t st, int* chosen);
 int stencil_array_impl(const hc_stage* in, const int64_t* dims3, double eps, int op, int axis3, void* d_out,
                        int out_dtype, void* d_ws, cudaStream_t st);
+
+// Batched fused launch (hc_batch.cu).
+int64_t batch_plan_bytes(int n);
+int64_t batch_ws_bytes(int n);
+int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune, void* h_plan, size_t cap,
+                    size_t* used);
+int batch_run_impl(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_bytes, cudaStream_t st);
+int batch_graph_impl(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_bytes, void** out);
+int batch_graph_launch_impl(void* graph, cudaStream_t st);
+int batch_graph_destroy_impl(void* graph);
+int batch_status_impl(void* d_ws, cudaStream_t st);
 
 }  // namespace hc

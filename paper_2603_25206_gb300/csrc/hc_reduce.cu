@@ -38,25 +38,6 @@ __host__ __device__ inline int order_words(int nsegmax) { return kWidthSpecializ
 __host__ __device__ inline int padded_words(int elems) { return round4(((elems + 31) / 32) * 33 + 4); }
 
 // ---------------------------------------------------------------- finishing
-__device__ inline void finalize_int(hc_scalar* out, int64_t n, long long s1, u128 s2, bool var, double two_eps,
-                                    int err) {
-  out->n = n;
-  out->s1 = s1;
-  out->s2_lo = var ? (unsigned long long)s2 : 0ull;
-  out->s2_hi = var ? (unsigned long long)(s2 >> 64) : 0ull;
-  out->status = err;
-  out->exact = 1;
-  out->mean = (__ll2double_rn(s1) / (double)n) * two_eps;
-  double v = __longlong_as_double(0x7ff8000000000000ll);  // NaN: not computed / undefined
-  if (var && n >= 2) {
-    const i128 num = (i128)n * (i128)s2 - (i128)s1 * (i128)s1;
-    const double den = (double)n * (double)(n - 1);
-    v = (i128_to_double(num) / den) * (two_eps * two_eps);
-  }
-  out->variance = v;
-  out->std = sqrt(v);
-}
-
 // CTA sum of (s1, s2, err), one partial per CTA, and the last CTA's finish.
 template <class Fin>
 __device__ inline void reduce_and_finish(long long s1, u128 s2, int err, Partial* parts, unsigned* ticket,

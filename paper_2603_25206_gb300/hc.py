@@ -40,7 +40,12 @@ ABI_FUNCTIONS = (
     "hc_workspace_bytes", "hc_stage_bytes", "hc_compress", "hc_compress_codes", "hc_read_header",
     "hc_decompress_to_stage", "hc_workspace_status", "hc_op_mean", "hc_op_variance", "hc_op_std",
     "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc", "hc_autotune",
+    "hc_batch_plan_bytes", "hc_batch_workspace_bytes", "hc_batch_plan", "hc_batch_run", "hc_batch_graph_create",
+    "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status",
 )
+HC_BATCH_MEAN, HC_BATCH_VARIANCE, HC_BATCH_DERIVATIVE, HC_BATCH_GRADMAG, HC_BATCH_LAPLACIAN = 1, 2, 4, 8, 16
+BATCH_OPS = {"mean": HC_BATCH_MEAN, "variance": HC_BATCH_VARIANCE, "derivative": HC_BATCH_DERIVATIVE,
+             "gradmag": HC_BATCH_GRADMAG, "laplacian": HC_BATCH_LAPLACIAN}
 
 
 class HcError(RuntimeError):
@@ -67,6 +72,17 @@ class HcStage(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("d_data", ctypes.c_void_p),
                 ("hdr", ctypes.POINTER(HcHeader)), ("dtype", ctypes.c_int32), ("S", ctypes.c_int32),
                 ("n", ctypes.c_int64), ("qmax", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class HcBatchItem(ctypes.Structure):
+    _fields_ = [("d_stream", ctypes.c_void_p), ("hdr", HcHeader), ("ops", ctypes.c_uint32), ("axis", ctypes.c_int32),
+                ("d_scalar", ctypes.c_void_p), ("d_field", ctypes.c_void_p), ("field_dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class HcBatchTune(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ty", ctypes.c_int32), ("unit_elems", ctypes.c_int64),
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 SCALAR_BYTES = 64
@@ -114,6 +130,14 @@ def lib():
             "hc_op_gradmag": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_op_laplacian": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_autotune": ([P(HcStage), i32, i32, vp, vp, sz, vp, P(ctypes.c_int)], i32),
+            "hc_batch_plan_bytes": ([i32], sz),
+            "hc_batch_workspace_bytes": ([i32], sz),
+            "hc_batch_plan": ([P(HcBatchItem), i32, P(HcBatchTune), vp, sz, P(sz)], i32),
+            "hc_batch_run": ([vp, vp, vp, sz, vp], i32),
+            "hc_batch_graph_create": ([vp, vp, vp, sz, P(vp)], i32),
+            "hc_batch_graph_launch": ([vp, vp], i32),
+            "hc_batch_graph_destroy": ([vp], i32),
+            "hc_batch_status": ([vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -391,3 +415,110 @@ def autotune(c: Compressed, op: str, out_dtype: str = "float32", out=None, strea
     _check(lib().hc_autotune(ctypes.byref(st), OPS[op], _OUT[out_dtype], ctypes.c_void_p(out.data_ptr()),
                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), ctypes.byref(chosen)))
     return chosen.value
+
+
+# ------------------------------------------------------------ batched launch
+class Batch:
+    """Many compressed fields and their operations in one persistent fused
+    launch (hc_batch_*).
+
+    ``items``: a list of (Compressed, ops) where ops is a string such as
+    "mean|variance|laplacian" (at most one of derivative / gradmag /
+    laplacian).  Field outputs are allocated here (``field_dtype``); the
+    statistics land in one 64-byte hc_scalar per item.  ``run()`` launches
+    the kernel; ``capture()`` records it in a CUDA graph that ``replay()``
+    relaunches.  The plan is built once (host) and copied to the device; the
+    workspace is zeroed once and left zeroed by every launch.
+    """
+
+    def __init__(self, items, field_dtype: str = "float32", axis: int = 0, threads: int = 0, ty: int = 0,
+                 unit_elems: int = 0, ctas_per_sm: int = 0, device=None):
+        torch = _torch()
+        if not items:
+            raise ValueError("empty batch")
+        L = lib()
+        self.comps = [c for c, _ in items]
+        dev = device if device is not None else self.comps[0].stream.device
+        n = len(items)
+        self.n = n
+        self.scalars = torch.zeros((n, SCALAR_BYTES), dtype=torch.uint8, device=dev)
+        self.fields = [None] * n
+        arr = (HcBatchItem * n)()
+        for i, (c, ops) in enumerate(items):
+            mask = 0
+            for name in ops.split("|"):
+                mask |= BATCH_OPS[name.strip()]
+            it = arr[i]
+            it.d_stream = c.stream.data_ptr()
+            it.hdr = c.header
+            it.ops = mask
+            it.axis = axis
+            if mask & (HC_BATCH_MEAN | HC_BATCH_VARIANCE):
+                it.d_scalar = self.scalars[i].data_ptr()
+            if mask & (HC_BATCH_DERIVATIVE | HC_BATCH_GRADMAG | HC_BATCH_LAPLACIAN):
+                f = _field_out(c.shape, field_dtype, dev, None)
+                self.fields[i] = f
+                it.d_field = f.data_ptr()
+                it.field_dtype = _OUT[field_dtype]
+        self._items = arr
+        tune = HcBatchTune(threads, ty, unit_elems, ctas_per_sm, 0)
+        cap = int(L.hc_batch_plan_bytes(n))
+        self.h_plan = torch.empty(cap, dtype=torch.uint8).pin_memory()
+        used = ctypes.c_size_t()
+        _check(L.hc_batch_plan(arr, n, ctypes.byref(tune), ctypes.c_void_p(self.h_plan.data_ptr()), cap,
+                               ctypes.byref(used)))
+        self.d_plan = self.h_plan.to(dev, non_blocking=False)
+        self.ws = torch.zeros(int(L.hc_batch_workspace_bytes(n)), dtype=torch.uint8, device=dev)
+        self.graph = None
+        self.plan_info = np.frombuffer(self.h_plan[:24].numpy().tobytes(), dtype=np.int32).tolist()
+
+    @property
+    def threads(self):
+        return self.plan_info[2]
+
+    @property
+    def grid(self):
+        return self.plan_info[3]
+
+    @property
+    def smem(self):
+        return self.plan_info[4]
+
+    def run(self, stream=None):
+        _check(lib().hc_batch_run(ctypes.c_void_p(self.h_plan.data_ptr()), ctypes.c_void_p(self.d_plan.data_ptr()),
+                                  ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), _stream_ptr(stream)))
+
+    def capture(self):
+        if self.graph is None:
+            g = ctypes.c_void_p()
+            _check(lib().hc_batch_graph_create(ctypes.c_void_p(self.h_plan.data_ptr()),
+                                               ctypes.c_void_p(self.d_plan.data_ptr()),
+                                               ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), ctypes.byref(g)))
+            self.graph = g
+        return self.graph
+
+    def replay(self, stream=None):
+        _check(lib().hc_batch_graph_launch(self.capture(), _stream_ptr(stream)))
+
+    def status(self, stream=None) -> int:
+        return int(lib().hc_batch_status(ctypes.c_void_p(self.ws.data_ptr()), _stream_ptr(stream)))
+
+    def results(self):
+        """Per item: the parsed hc_scalar (or None) and the field tensor (or None)."""
+        raw = self.scalars.cpu().numpy()
+        out = []
+        for i in range(self.n):
+            sc = parse_scalar(raw[i].tobytes()) if self._items[i].d_scalar else None
+            out.append((sc, self.fields[i]))
+        return out
+
+    def close(self):
+        if self.graph is not None:
+            lib().hc_batch_graph_destroy(self.graph)
+            self.graph = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -58,6 +58,9 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(hc_stage, d_data), offsetof(hc_stage, hdr), offsetof(hc_stage, n),
          offsetof(hc_stage, qmax));
   printf("%zu %zu %zu\n", offsetof(hc_scalar, s1), offsetof(hc_scalar, status), offsetof(hc_scalar, exact));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(hc_batch_item), offsetof(hc_batch_item, hdr), offsetof(hc_batch_item, ops),
+         offsetof(hc_batch_item, d_scalar), offsetof(hc_batch_item, field_dtype));
+  printf("%zu %zu %zu\n", sizeof(hc_batch_tune), offsetof(hc_batch_tune, unit_elems), offsetof(hc_batch_tune, ctas_per_sm));
   return 0;
 }
 """
@@ -74,6 +77,9 @@ int main(void) {
     assert vals[7:11] == [St.d_data.offset, St.hdr.offset, St.n.offset, St.qmax.offset]
     assert vals[11:14] == [hc._SCALAR_DTYPE.fields["s1"][1], hc._SCALAR_DTYPE.fields["status"][1],
                            hc._SCALAR_DTYPE.fields["exact"][1]]
+    B, T = hc.HcBatchItem, hc.HcBatchTune
+    assert vals[14:19] == [ctypes.sizeof(B), B.hdr.offset, B.ops.offset, B.d_scalar.offset, B.field_dtype.offset]
+    assert vals[19:22] == [ctypes.sizeof(T), T.unit_elems.offset, T.ctas_per_sm.offset]
 
 
 @pytest.mark.parametrize("S", [1, 2, 3, 16, 32, 33, 64, 100, 128, 4096])
@@ -135,3 +141,57 @@ def test_binding_fails_loudly_without_library(hc, monkeypatch, tmp_path):
     monkeypatch.setattr(hc, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         hc.lib()
+
+
+def test_batch_argument_errors_before_any_cuda_call(hc):
+    L = hc.lib()
+    assert L.hc_batch_plan_bytes(0) == 0 and L.hc_batch_workspace_bytes(0) == 0
+    assert L.hc_batch_plan_bytes(4) > L.hc_batch_plan_bytes(1) > 0
+    assert L.hc_batch_workspace_bytes(3) == 64 + 3 * 32
+    cap = L.hc_batch_plan_bytes(1)
+    buf = ctypes.create_string_buffer(cap)
+    used = ctypes.c_size_t()
+    items = (hc.HcBatchItem * 1)()
+    # empty batch / null items
+    assert L.hc_batch_plan(items, 0, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    assert L.hc_batch_plan(None, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    # plan buffer too small
+    assert L.hc_batch_plan(items, 1, None, buf, cap - 1, ctypes.byref(used)) == hc.HC_ERR_NOMEM
+    # a zero header is inconsistent
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_CORRUPT
+    # a consistent header (block 32, 1-D, 100 elements) with bad ops / pointers
+    h = items[0].hdr
+    h.dtype, h.ndim, h.S, h.G = hc.HC_F32, 1, 32, 128
+    h.dims[0], h.dims[1], h.dims[2] = 1, 1, 100
+    h.eps, h.eb, h.eb_mode, h.qmax = 1e-3, 1e-3, hc.HC_EB_ABS, 10
+    h.N, h.nb, h.nchunks, h.payload_words, h.wmax = 100, 4, 1, 0, 0
+    h.off_widths = 256
+    h.off_heads = 256 + 16
+    h.off_chunks = h.off_heads + 16
+    h.off_payload = h.off_chunks + 16
+    h.total_bytes = h.off_payload + 16
+    items[0].d_stream = 16
+    items[0].ops = 0
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    assert b"ops" in L.hc_last_error()
+    items[0].ops = hc.HC_BATCH_LAPLACIAN | hc.HC_BATCH_GRADMAG
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    items[0].ops = hc.HC_BATCH_VARIANCE  # statistics without an output pointer
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    items[0].ops = hc.HC_BATCH_GRADMAG
+    items[0].d_field = 16
+    items[0].field_dtype = hc.HC_I64
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_UNSUPPORTED
+    items[0].ops = hc.HC_BATCH_DERIVATIVE
+    items[0].axis = 1
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    tune = hc.HcBatchTune(100, 0, 0, 0, 0)
+    items[0].axis = 0
+    assert L.hc_batch_plan(items, 1, ctypes.byref(tune), buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    # run / graph with something that is not a plan
+    ws = ctypes.c_void_p(16)
+    assert L.hc_batch_run(buf, ctypes.c_void_p(16), ws, 1 << 20, None) == hc.HC_ERR_INVALID_ARG
+    g = ctypes.c_void_p()
+    assert L.hc_batch_graph_create(buf, ctypes.c_void_p(16), ws, 1 << 20, ctypes.byref(g)) == hc.HC_ERR_INVALID_ARG
+    assert L.hc_batch_graph_launch(None, None) == hc.HC_ERR_INVALID_ARG
+    assert L.hc_batch_graph_destroy(None) == hc.HC_OK

@@ -78,3 +78,61 @@ def test_paper_like_field_full_size(env, orc, fi):
     lap = hc.laplacian(c).reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy()
     assert np.all(np.abs(lap - val) <= 1e-6 * np.maximum(np.abs(val), 2 * eps))
     assert hc.workspace_status() == 0
+
+
+def _width_hist(orc, stream):
+    h = orc.read_header(stream)
+    off = int(np.frombuffer(stream[96:104].tobytes(), np.int64)[0])  # widths section offset (header word 96)
+    w = stream[off: off + h["nb"]]
+    return np.bincount(w, minlength=32)
+
+
+@pytest.mark.parametrize("mode", ["rel_1e-6", "abs_2^-31"])
+def test_wide_code_full_size(env, orc, mode):
+    """Wide-code stress: one float64 512 x 512 x 1024 field (k^-3 field times 1e4
+    plus a linear trend), block 64, exact 64/128-bit sums, derivative fields in
+    float32 and float64.  The ABS companion centres the field on its mid-range
+    and takes eps = range / 2^31, so |q| <= 2^29 and block widths reach the
+    upper 20s (value-range-relative 1e-6 alone keeps |p| below 2^19)."""
+    import synth
+
+    hc, torch, dev = env
+    shape = (512, 512, 1024)
+    x = synth.wide_field(shape, 3000)
+    if mode == "rel_1e-6":
+        eb, rel = 1e-6, True
+    else:
+        x = np.ascontiguousarray(x - (x.max() + x.min()) / 2)
+        eb, rel = float(x.max() - x.min()) / 2**31, False
+    ref, eps = orc.compress(x, eb, rel, 64)
+    c = hc.compress(torch.from_numpy(x).to(dev), eb, rel=rel, S=64)
+    del x
+    assert c.nbytes == ref.size
+    assert np.array_equal(c.stream[: c.nbytes].cpu().numpy(), ref)
+    hist = _width_hist(orc, ref)
+    print(f"{mode}: widths {np.nonzero(hist)[0].min()}..{np.nonzero(hist)[0].max()}, qmax {orc.read_header(ref)['qmax']}")
+    if mode != "rel_1e-6":
+        assert np.nonzero(hist)[0].max() >= 24
+    q = orc.decode(ref, "q")
+    del ref
+    s1, s2 = orc.sums_q(q)
+    rm = hc.parse_scalar(hc.mean(c, level="p"))
+    rv = hc.parse_scalar(hc.variance(c, level="q"))
+    assert rm["s1"] == s1
+    assert (rv["s1"], rv["s2"]) == (s1, s2)
+    m_ref, v_ref, _ = orc.finalize(q.size, s1, s2, eps)
+    assert abs(rv["variance"] - v_ref) <= 1e-12 * v_ref
+    assert abs(rm["mean"] - m_ref) <= 1e-12 * max(abs(m_ref), eps)
+
+    rng = np.random.default_rng(7)
+    idx = _sample_indices(shape, rng)
+    tidx = torch.from_numpy(idx).to(dev)
+    for ax in range(3):
+        num, val = orc.stencil_at(q, orc.KIND_DERIV, eps, idx, ax)
+        d64 = hc.derivative(c, ax, out_dtype="float64").reshape(-1)[tidx].cpu().numpy()
+        assert np.all(np.abs(d64 - val) <= 1e-12 * np.maximum(np.abs(val), eps))
+        d32 = hc.derivative(c, ax, out_dtype="float32").reshape(-1)[tidx].cpu().numpy()
+        assert np.all(np.abs(d32 - val) <= 1e-6 * np.maximum(np.abs(val), eps))
+        dn = hc.derivative(c, ax, out_dtype="int64").reshape(-1)[tidx].cpu().numpy()
+        assert np.array_equal(dn, num)
+    assert hc.workspace_status() == 0
