@@ -383,6 +383,8 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
       int sm = 0;
       rc = stencil_plan(&items[i].hdr, b.g, &sm, ty_force, unit_elems);
       if (rc) return rc;
+      // the planes per tile do not change the tile's shared memory
+      if (sm > smem) return fail(HC_ERR_UNSUPPORTED, "batch: inconsistent tile plan");
       b.units = (int64_t)b.g.nxt * b.g.nyt * b.g.nzt;
     }
     if (b.units >= (int64_t)0xffffffffu) return fail(HC_ERR_UNSUPPORTED, "batch: field too large");
