@@ -522,3 +522,61 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _trim(c: Compressed) -> Compressed:
+    """Keep only the stream bytes resident (drop the bound-sized buffer)."""
+    return Compressed(c.stream[: c.nbytes].clone(), c.header, c.nbytes)
+
+
+def time_batch(b: Batch, reps: int = 5, flush=None) -> float:
+    """Median CUDA-event time (ms) of a graph replay of the batch."""
+    torch = _torch()
+    b.replay()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.replay()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def batch_autotune(fields, eb: float, rel: bool = True, ops: str = "mean|variance|laplacian",
+                   S_list=(16, 32, 64, 128), threads_list=(128, 256, 512), ty_list=(16, 8, 4),
+                   field_dtype: str = "float32", reps: int = 5, flush=None):
+    """Autotuner of the batched launch: block size S, threads per CTA and
+    stencil tile height.
+
+    For every S the fields (CUDA tensors) are compressed at that block size;
+    for every (threads, tile height) the batch is planned, captured in a CUDA
+    graph and timed (median of `reps` replays).  Returns (best, table): best
+    is a dict with the chosen S, threads, ty, the compressed fields at that S
+    and the planned Batch; table lists every (S, threads, ty, ms, compressed
+    bytes).
+    The block size changes the stream (and its compression ratio), not the
+    results: the codes q, and so every integer result, are the same for all S.
+    """
+    table = []
+    best = None
+    for S in S_list:
+        comps = [_trim(compress(x, eb, rel=rel, S=S)) for x in fields]
+        cbytes = sum(c.nbytes for c in comps)
+        for th in threads_list:
+            for ty in ty_list:
+                b = Batch([(c, ops) for c in comps], field_dtype=field_dtype, threads=th, ty=ty)
+                ms = time_batch(b, reps=reps, flush=flush)
+                table.append({"S": S, "threads": th, "ty": ty, "ms": ms, "compressed_bytes": cbytes,
+                              "grid": b.grid, "smem": b.smem})
+                if best is None or ms < best["ms"]:
+                    if best is not None:
+                        best["batch"].close()
+                    best = {"S": S, "threads": th, "ty": ty, "ms": ms, "comps": comps, "batch": b}
+                else:
+                    b.close()
+    return best, table

@@ -16,6 +16,10 @@ Recipes
   min-max normalised to [0, 1].
 * ``wide_field``: the k^-3 field times 1e4 plus a linear trend 1e4 * i0/n0
   along the slowest axis, in float64.
+* ``grf_field_device``: the ``grf_field`` recipe drawn on a CUDA device with
+  torch's seeded CUDA generator (for workloads too large to draw on the host,
+  such as the 200-field serving set); the same spectrum and spikes, but not
+  the same numbers as the host generator.
 """
 from __future__ import annotations
 
@@ -23,7 +27,7 @@ import math
 
 import numpy as np
 
-__all__ = ["sinusoid_field", "grf_field", "wide_field", "log_uniform_shapes", "PAPER_SHAPES"]
+__all__ = ["sinusoid_field", "grf_field", "grf_field_device", "wide_field", "log_uniform_shapes", "PAPER_SHAPES"]
 
 # Shapes of the paper-like workload: Hurricane-like, NYX-like, Miranda-like,
 # a 98 x 1200 x 1200 volume and a 1800 x 3600 (2-D) ocean-like slice.
@@ -92,6 +96,43 @@ def grf_field(shape, seed: int, spikes: float = 0.05, dtype=np.float32) -> np.nd
         amp = rng.uniform(3.0, 10.0, size=int(mask.sum())) * rng.choice((-1.0, 1.0), size=int(mask.sum()))
         field[mask] += amp
     return np.ascontiguousarray(_minmax(field).astype(dtype))
+
+
+def grf_field_device(shape, seed: int, device, spikes: float = 0.05):
+    """k^-3 Gaussian random field (+ spikes) as a float32 CUDA tensor in [0, 1]."""
+    import torch
+
+    shape = tuple(int(s) for s in shape)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    white = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+    spec = torch.fft.rfftn(white)
+    del white
+    k2 = None
+    for ax, n in enumerate(shape):
+        f = (torch.fft.rfftfreq(n, d=1.0 / n) if ax == len(shape) - 1 else torch.fft.fftfreq(n, d=1.0 / n))
+        view = [1] * len(shape)
+        view[ax] = -1
+        f2 = (f.to(device=device, dtype=torch.float32) ** 2).reshape(view)
+        k2 = f2 if k2 is None else k2 + f2
+    spec *= torch.where(k2 > 0, k2.clamp_min(1e-12) ** -0.75, torch.zeros((), device=device))
+    del k2
+    field = torch.fft.irfftn(spec, s=shape).to(torch.float64)
+    del spec
+    field -= field.mean()
+    sd = field.std()
+    if sd > 0:
+        field /= sd
+    if spikes > 0:
+        mask = torch.rand(shape, generator=g, device=device) < spikes
+        amp = torch.rand(shape, generator=g, device=device, dtype=torch.float64) * 7.0 + 3.0
+        sign = torch.where(torch.rand(shape, generator=g, device=device) < 0.5, -1.0, 1.0).to(torch.float64)
+        field += torch.where(mask, amp * sign, torch.zeros((), device=device, dtype=torch.float64))
+        del mask, amp, sign
+    lo, hi = field.min(), field.max()
+    if hi > lo:
+        field = (field - lo) / (hi - lo)
+    return field.to(torch.float32).contiguous()
 
 
 def wide_field(shape, seed: int) -> np.ndarray:
