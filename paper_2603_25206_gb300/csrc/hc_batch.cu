@@ -3,8 +3,10 @@
 //
 // Work is cut into units.  A field with a stencil operation (derivative,
 // gradient magnitude, Laplacian; Section V-B) contributes one unit per output
-// tile of the general fused stencil (TY rows x the row length x TZ planes,
-// decoded with halos into a shared-memory ring); a field with statistics only
+// tile (TY rows x the row length x TZ planes, decoded with halos into a
+// shared-memory ring): a tile of the pipelined stencil (block size 32, |q| <
+// 2^15, 256 threads per CTA: a loader warp prefetches the next slabs while
+// seven warps decode and compute) or else of the general one; a field with statistics only
 // (Section V-A) contributes one unit per two chunks of blocks, decoded to
 // D_q in shared memory and summed.  Statistics are taken at stage 3 (the codes
 // q): s1 = sum q (64-bit) and s2 = sum q^2 (128-bit), exact.  When a field has
@@ -24,6 +26,7 @@
 
 #include "hc_internal.cuh"
 #include "hc_launch.h"
+#include "hc_stencil_pipe.cuh"
 #include "hc_stencil_tile.cuh"
 
 namespace hc {
@@ -37,9 +40,12 @@ constexpr uint32_t kPlanMagic = 0x4E4C5042u;  // "BPLN"
 enum { STATS_NONE = 0, STATS_MEAN = 1, STATS_VAR = 2 };
 
 // One field of the batch as the kernel sees it.
+enum { KIND_TILE = 0, KIND_PIPE = 1, KIND_STATS = 2 };
+
 struct BItem {
   DevStream s;
-  Geo g;               // stencil geometry (fop >= 0)
+  Geo g;               // general stencil geometry (KIND_TILE)
+  PGeo pg;             // pipelined stencil geometry (KIND_PIPE)
   void* field;         // stencil output
   hc_scalar* scalar;   // statistics output
   int64_t units;       // work units of this field
@@ -49,6 +55,8 @@ struct BItem {
   int out;             // hc_dtype of the stencil output
   int stats;           // STATS_*
   int rwords;          // statistics unit: words of the decoded D_q tile
+  int kind;            // KIND_*
+  int vec;             // KIND_PIPE: outputs per work item (8, 4 or 1)
 };
 
 struct BPlan {
@@ -116,6 +124,12 @@ __device__ __noinline__ void stencil_unit(const BItem& it, int64_t lu, int* err,
   stencil_tile<ST_RUNTIME, ST_RUNTIME, SMALL, true>(it.s, it.g, lu, it.field, err, smem, s_warp, s_flag, s_base, mo);
 }
 
+template <int V>
+__device__ __noinline__ void pipe_unit(const BItem& it, int64_t lu, int* err, unsigned char* smem, Moments& mo) {
+  pipe_tile<ST_RUNTIME, ST_RUNTIME, V, true>(it.s, it.pg, (int)(lu % it.pg.nyt), (int)(lu / it.pg.nyt), it.field,
+                                            err, smem, mo);
+}
+
 // CTA sum of the unit's moments into the field accumulator; the field's last
 // unit finishes the statistic and zeroes the accumulator.
 template <int THREADS>
@@ -169,7 +183,7 @@ __device__ void publish(const BItem& it, const Moments& mo, BAcc* a, int* status
 }
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_batch(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
+__global__ void __launch_bounds__(THREADS, THREADS == 512 ? 1 : 768 / THREADS) k_batch(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_warp[32];
   __shared__ int s_flag;
@@ -216,7 +230,17 @@ __global__ void __launch_bounds__(THREADS) k_batch(const uint8_t* __restrict__ p
     const int64_t lu = s_unit;
     int* err = &acc[it].err;
     Moments mo;
-    if (s_it.fop >= 0) {
+    if (s_it.kind == KIND_PIPE) {
+      if constexpr (THREADS == kThreads) {
+        unsigned char* sm = reinterpret_cast<unsigned char*>(smem);
+        if (s_it.vec == 8)
+          pipe_unit<8>(s_it, lu, err, sm, mo);
+        else if (s_it.vec == 4)
+          pipe_unit<4>(s_it, lu, err, sm, mo);
+        else
+          pipe_unit<1>(s_it, lu, err, sm, mo);
+      }
+    } else if (s_it.fop >= 0) {
       if (s_it.s.S <= 32)
         stencil_unit<true>(s_it, lu, err, smem, s_warp, &s_flag, s_base, mo);
       else
@@ -341,16 +365,35 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
       }
       int64_t d3[3];
       stencil_walk_dims(&h, d3, &axis3);
-      b.g = stencil_base_geo(d3, h.eps, axis3);
-      b.g.op = b.fop;
-      b.g.out = b.out;
       int sm = 0;
-      rc = stencil_plan(&h, b.g, &sm, ty_force, 1);
-      if (rc) return rc;
+      // the pipelined tile when it applies (it needs kThreads threads per CTA)
+      b.kind = KIND_TILE;
+      if (threads == kThreads && aligned16(x.d_field) && d3[1] * d3[2] < ((int64_t)1 << 31) &&
+          plan_pipe_geometry(&h, d3, b.pg, &sm, ty_force, ty_force ? 200 * 1024 : 74 * 1024)) {
+        b.vec = d3[2] % 8 == 0 ? 8 : (d3[2] % 4 == 0 ? 4 : 1);
+        if (plan_pipe_items(b.pg, b.vec)) {
+          b.kind = KIND_PIPE;
+          b.pg.axis = axis3;
+          b.pg.op = b.fop;
+          b.pg.out = b.out;
+          b.pg.eps = h.eps;
+          b.pg.te = 2.0 * h.eps;
+          b.pg.eps_f = (float)h.eps;
+          b.pg.te_f = (float)(2.0 * h.eps);
+        }
+      }
+      if (b.kind == KIND_TILE) {
+        b.g = stencil_base_geo(d3, h.eps, axis3);
+        b.g.op = b.fop;
+        b.g.out = b.out;
+        rc = stencil_plan(&h, b.g, &sm, ty_force, 1);
+        if (rc) return rc;
+      }
       smem = std::max(smem, sm);
       field_points += h.N;
     } else {
       b.fop = -1;
+      b.kind = KIND_STATS;
       b.rblocks = (int64_t)kTileChunks * h.G;
       const bool small = h.S <= 32;
       const int nseg = (h.S + 31) / 32;
@@ -379,13 +422,20 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
   int64_t total = 0;
   for (int i = 0; i < n; ++i) {
     BItem& b = it[i];
-    if (b.fop >= 0) {
+    if (b.kind == KIND_TILE) {
       int sm = 0;
       rc = stencil_plan(&items[i].hdr, b.g, &sm, ty_force, unit_elems);
       if (rc) return rc;
       // the planes per tile do not change the tile's shared memory
       if (sm > smem) return fail(HC_ERR_UNSUPPORTED, "batch: inconsistent tile plan");
       b.units = (int64_t)b.g.nxt * b.g.nyt * b.g.nzt;
+    } else if (b.kind == KIND_PIPE) {
+      // at least four planes per unit: a pipelined tile primes three slabs
+      const int64_t plane = (int64_t)b.pg.ty * b.pg.n2;
+      const int64_t tz = std::max<int64_t>(4, ceil_div(unit_elems, plane));
+      b.pg.tz = (int)std::min<int64_t>(b.pg.n0, tz);
+      b.pg.nzt = (int)ceil_div(b.pg.n0, b.pg.tz);
+      b.units = (int64_t)b.pg.nyt * b.pg.nzt;
     }
     if (b.units >= (int64_t)0xffffffffu) return fail(HC_ERR_UNSUPPORTED, "batch: field too large");
     prefix[i] = total;

@@ -1,0 +1,459 @@
+// hc_stencil_pipe.cuh -- the pipelined fused stream -> stencil tile for the
+// common case: block size 32 and codes |q| < 2^15 (the header's max |q| says
+// so).  Same results as the general tile (Section V-B, "Operation with D_q").
+// Shared by the one-field kernel and the batched persistent kernel.
+//
+// One CTA owns TY whole rows for a range of planes and marches along the
+// slowest axis (the sliding window of Algorithm 3, one plane slab per step).
+// Warp 0 is a loader; warps 1..7 decode and compute:
+//   step k:  loader   wait for the copies issued in step k-1, scan the widths
+//                     of slab k+2, cp.async its payload and the widths + heads
+//                     of slab k+3 (so every copy has a whole step to land);
+//            workers  decode slab k into ring slot k % 4 and compute every
+//                     output plane whose three slabs are ready (normally the
+//                     plane of slab k-2);
+//            one __syncthreads.
+// Buffers: 4 ring slots, 3 payload stages, 4 metadata buffers.  A work item
+// is V = 8 (rows a multiple of 8), V = 4 (a multiple of 4) or V = 1 (any row
+// length) consecutive outputs of one row.
+// Decoded codes are stored as int16, a 32-code segment as 64 contiguous
+// bytes: a decoding thread writes its segment with four 16-byte stores and a
+// stencil thread reads V consecutive codes of a row with one load
+// (consecutive threads read consecutive bytes: no bank conflicts).
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "hc_internal.cuh"
+#include "hc_launch.h"
+#include "hc_stencil_tile.cuh"
+
+namespace hc {
+
+constexpr int kWorkers = kThreads - 32;
+constexpr int kSlots = 4;
+constexpr int kWorkerWarps = kWorkers / 32;
+constexpr int kSegCost = 4;  // decoding one 32-code segment ~ this many output items
+
+
+struct PGeo {
+  int64_t n0, n1, n2;
+  int ty, tz, nyt, nzt;
+  int nblk_max;     // blocks of one slab
+  int pre_max;      // widths bytes staged per slab (G - 1 + nblk_max, rounded to 16)
+  int heads_max;    // heads staged per slab (nblk_max + 4, rounded to 4)
+  int stage_words;  // payload words per stage buffer
+  int slot_bytes;   // nblk_max * 64
+  int axis;
+  int op, out;        // operation and output type for the ST_RUNTIME instantiation
+  unsigned nq_magic;  // ceil(2^32 / nq) for the row/item split (unused when nq == 1)
+  int nq;             // items per row: n2 / V
+  float eps_f, te_f;
+  double eps, te;
+};
+
+template <int OUT>
+struct OT;
+template <>
+struct OT<ST_RUNTIME> {
+  using T = void;
+};
+template <>
+struct OT<HC_F32> {
+  using T = float;
+};
+template <>
+struct OT<HC_F64> {
+  using T = double;
+};
+template <>
+struct OT<HC_I64> {
+  using T = long long;
+};
+
+template <int OP, int OUT>
+__device__ __forceinline__ typename OT<OUT>::T emit1(int a, int b, int c, const PGeo& g) {
+  if constexpr (OP == ST_DERIV) {
+    if constexpr (OUT == HC_F32) return __fmul_rn(__int2float_rn(a), g.eps_f);
+    if constexpr (OUT == HC_F64) return __dmul_rn((double)a, g.eps);
+    if constexpr (OUT == HC_I64) return (long long)a;
+  } else if constexpr (OP == ST_LAPLACIAN) {
+    if constexpr (OUT == HC_F32) return __fmul_rn(__int2float_rn(a), g.te_f);
+    if constexpr (OUT == HC_F64) return __dmul_rn((double)a, g.te);
+    if constexpr (OUT == HC_I64) return (long long)a;
+  } else {
+    if constexpr (OUT == HC_F32) {
+      const float x = __int2float_rn(a), y = __int2float_rn(b), z = __int2float_rn(c);
+      return __fmul_rn(__fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z))), g.eps_f);
+    } else {
+      const double x = (double)a, y = (double)b, z = (double)c;
+      return sqrt(x * x + y * y + z * z) * g.eps;
+    }
+  }
+  return 0;
+}
+
+// Shared-memory carve-up (byte offsets), computed identically on both sides.
+struct PSmem {
+  int ring, stage, meta, total;
+  int meta_bytes;  // one meta buffer: widths | heads | offsets
+};
+__host__ __device__ inline PSmem psmem(const PGeo& g) {
+  PSmem p;
+  p.ring = 0;
+  p.stage = p.ring + kSlots * g.slot_bytes;
+  p.meta = p.stage + 3 * 4 * g.stage_words;
+  p.meta_bytes = g.pre_max + 4 * g.heads_max + 4 * (g.nblk_max + 4) + (kWidthSpecialize ? 2 * (g.nblk_max + 32 * 32 + 8) : 0);
+  p.meta_bytes = (p.meta_bytes + 15) & ~15;
+  p.total = p.meta + 4 * p.meta_bytes;
+  return p;
+}
+
+struct SlabDesc {
+  int64_t b0;   // first block
+  int nblk;     // blocks
+  int npre;     // widths before b0 in its chunk
+  int64_t cs;   // chunk start block
+};
+
+__device__ __forceinline__ SlabDesc slab_desc(const DevStream& s, const PGeo& g, int64_t z, int64_t ylo,
+                                              int64_t yhi) {
+  SlabDesc d;
+  const int64_t e0 = (z * g.n1 + ylo) * g.n2, e1 = (z * g.n1 + yhi) * g.n2;
+  d.b0 = e0 >> 5;
+  d.nblk = (int)(((e1 - 1) >> 5) - d.b0 + 1);
+  d.cs = d.b0 & ~(int64_t)127;  // G = 128 blocks per chunk at S = 32
+  d.npre = (int)(d.b0 - d.cs);
+  return d;
+}
+
+// The V outputs of one work item from their neighbourhoods (compile-time
+// operation O and output type D), written with vector stores when they fill
+// 16 bytes.  cm / cp are the x neighbours of the first / last point.
+template <int O, int D, int V>
+__device__ __forceinline__ void emit_items(const PGeo& g, typename OT<D>::T* o, const short* c, const short* a,
+                                           const short* b, const short* zmv, const short* zpv, int xl, int xr,
+                                           int ex0, int exn, int ez, int ey) {
+  using T = typename OT<D>::T;
+  T res[V];
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+    const int cm = i == 0 ? xl : c[i - 1];
+    const int cp = i == V - 1 ? xr : c[i + 1];
+    if constexpr (O == ST_LAPLACIAN) {
+      const int l = (int)zmv[i] + zpv[i] + a[i] + b[i] + cm + cp - 6 * (int)c[i];
+      res[i] = emit1<O, D>(l, 0, 0, g);
+    } else {
+      int ex = 1;
+      if (i == 0) ex = ex0;
+      if (i == V - 1) ex = ex * exn;
+      int d0 = 0, d1 = 0, d2 = 0;
+      if (O == ST_GRADMAG || g.axis == 0) d0 = ((int)zpv[i] - zmv[i]) * ez;
+      if (O == ST_GRADMAG || g.axis == 1) d1 = ((int)b[i] - a[i]) * ey;
+      if (O == ST_GRADMAG || g.axis == 2) d2 = (cp - cm) * ex;
+      if constexpr (O == ST_DERIV)
+        res[i] = emit1<O, D>(g.axis == 0 ? d0 : (g.axis == 1 ? d1 : d2), 0, 0, g);
+      else
+        res[i] = emit1<O, D>(d0, d1, d2, g);
+    }
+  }
+  if constexpr (V * sizeof(T) >= 16) {
+#pragma unroll
+    for (int v = 0; v < (int)(V * sizeof(T) / 16); ++v)
+      reinterpret_cast<uint4*>(o)[v] = reinterpret_cast<const uint4*>(res)[v];
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; ++i) o[i] = res[i];
+  }
+}
+
+// Compile-time operation and type, or (ST_RUNTIME) the run-time switch over
+// both; out + i0 is the item's first output.
+template <int OP, int OUT, int V>
+__device__ __forceinline__ void store_items(const PGeo& g, typename OT<OUT>::T* out, int64_t i0, const short* c,
+                                            const short* a, const short* b, const short* zmv, const short* zpv,
+                                            int xl, int xr, int ex0, int exn, int ez, int ey) {
+  if constexpr (OP == ST_RUNTIME) {
+#define HC_PIPE_RT(O, D)                                                                                            \
+  case O * 4 + D:                                                                                                   \
+    emit_items<O, D, V>(g, reinterpret_cast<typename OT<D>::T*>(out) + i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, \
+                        ey);                                                                                        \
+    break;
+    switch (g.op * 4 + g.out) {
+      HC_PIPE_RT(ST_DERIV, HC_F32)
+      HC_PIPE_RT(ST_DERIV, HC_F64)
+      HC_PIPE_RT(ST_DERIV, HC_I64)
+      HC_PIPE_RT(ST_GRADMAG, HC_F32)
+      HC_PIPE_RT(ST_GRADMAG, HC_F64)
+      HC_PIPE_RT(ST_LAPLACIAN, HC_F32)
+      HC_PIPE_RT(ST_LAPLACIAN, HC_F64)
+      HC_PIPE_RT(ST_LAPLACIAN, HC_I64)
+      default:
+        break;
+    }
+#undef HC_PIPE_RT
+  } else {
+    emit_items<OP, OUT, V>(g, out + i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
+  }
+}
+
+// One tile (row tile yt, plane range zt) of the pipelined stencil; needs
+// blockDim.x == kThreads.  sm: the dynamic shared memory (psmem(g).total
+// bytes).  With STATS the codes of the points the tile owns are added to mo.
+// OP = OUT = ST_RUNTIME takes the operation and output type from g.
+template <int OP, int OUT, int V, bool STATS>
+__device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int zt, typename OT<OUT>::T* out, int* err,
+                                 unsigned char* sm, Moments& mo) {
+  using T = typename OT<OUT>::T;
+  const PSmem L = psmem(g);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  const int64_t y0 = (int64_t)yt * g.ty, y1 = min(y0 + g.ty, g.n1);
+  const int64_t z0 = (int64_t)zt * g.tz, z1 = min(z0 + g.tz, g.n0);
+  const int64_t ylo = max(y0 - 1, (int64_t)0), yhi = min(y1 + 1, g.n1);
+  const int64_t zs = max(z0 - 1, (int64_t)0), ze = min(z1 + 1, g.n0);  // slabs [zs, ze)
+  const int nslab = (int)(ze - zs);
+
+  auto meta_w = [&](int j) { return sm + L.meta + (j & 3) * L.meta_bytes; };
+  auto meta_h = [&](int j) { return reinterpret_cast<int32_t*>(sm + L.meta + (j & 3) * L.meta_bytes + g.pre_max); };
+  auto meta_o = [&](int j) {
+    return reinterpret_cast<uint32_t*>(sm + L.meta + (j & 3) * L.meta_bytes + g.pre_max + 4 * g.heads_max);
+  };
+  auto meta_ord = [&](int j) {
+    return reinterpret_cast<uint16_t*>(sm + L.meta + (j & 3) * L.meta_bytes + g.pre_max + 4 * g.heads_max +
+                                       4 * (g.nblk_max + 4));
+  };
+  auto stage = [&](int j) { return reinterpret_cast<uint32_t*>(sm + L.stage + (j % 3) * 4 * g.stage_words); };
+  __shared__ int s_whist[64];
+  __shared__ int s_npad[4];  // padded order length per metadata buffer
+  auto slot = [&](int64_t z) { return sm + L.ring + (int)(z & 3) * g.slot_bytes; };
+
+  // loader: copy widths [cs, b0 + nblk) and heads [b0, b0 + nblk) of slab j
+  auto load_meta = [&](int j) {
+    const SlabDesc d = slab_desc(s, g, zs + j, ylo, yhi);
+    const int nw = (d.npre + d.nblk + 15) & ~15;
+    const uint8_t* wsrc = s.widths + d.cs;  // cs is a multiple of G = 128: 16-byte aligned
+    uint8_t* wdst = meta_w(j);
+    for (int i = lane * 16; i < nw; i += 32 * 16) cp_async16(wdst + i, wsrc + i);
+    const int64_t h0 = d.b0 & ~(int64_t)3;
+    const int nh = (int)((d.b0 + d.nblk - h0 + 3) & ~3);
+    int32_t* hdst = meta_h(j);
+    for (int i = lane * 4; i < nh; i += 32 * 4) cp_async16(hdst + i, s.heads + h0 + i);
+  };
+  // loader: offsets of slab j from its widths, then cp.async of its payload
+  auto scan_and_load_payload = [&](int j) {
+    const SlabDesc d = slab_desc(s, g, zs + j, ylo, yhi);
+    const uint8_t* w = meta_w(j);
+    uint32_t* off = meta_o(j);
+    uint32_t carry = 0;
+    const int n = d.npre + d.nblk;
+    int bad = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      uint32_t wi = i < n ? w[i] : 0u;
+      if (wi > (uint32_t)s.wmax) {
+        bad = 1;
+        wi = 0;
+      }
+      const uint32_t words = wi ? 1u + wi : 0u;  // S = 32: one sign word + w magnitude words
+      uint32_t x = words;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (i >= d.npre && i < n) off[i - d.npre] = carry + x - words;  // exclusive, relative to chunk start
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    // payload words [chunk base + off[0], chunk base + carry) plus one word
+    __syncwarp();
+    const uint32_t first = off[0];
+    const uint64_t base = s.chunks[d.cs >> 7] + first;
+    const uint32_t words = carry - first;
+    bad |= (base + words > (uint64_t)s.payload_words) || ((int)words + 8 > g.stage_words);
+    bad = __any_sync(0xffffffffu, bad);
+    const uint64_t a0 = base & ~(uint64_t)3;
+    const int lead = (int)(base - a0);
+    if (!bad) {
+      uint32_t* dst = stage(j);
+      const int nvec = (lead + (int)words + 1 + 3) >> 2;
+      for (int v = lane; v < nvec; v += 32) cp_async16(dst + 4 * v, s.payload + a0 + 4 * v);
+    }
+    __syncwarp();
+    // offsets relative to the staging buffer (or all zero for a bad slab)
+    for (int i = lane; i < d.nblk; i += 32) off[i] = bad ? 0u : off[i] - first + lead;
+    if (bad && lane == 0) set_error(err, HC_ERR_CORRUPT);
+    // counting sort of the slab's blocks by width: workers taking consecutive
+    // entries run one width-specialised unpacker per warp
+    uint16_t* ord = meta_ord(j);
+    if (!kWidthSpecialize) return;
+    s_whist[lane] = 0;
+    __syncwarp();
+    for (int i = lane; i < d.nblk; i += 32) atomicAdd(&s_whist[min((int)w[d.npre + i], 31)], 1);
+    __syncwarp();
+    {
+      const int c = (s_whist[lane] + 31) & ~31;  // runs padded to whole warps
+      int x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      s_whist[32 + lane] = x - c;
+      const int padded = __shfl_sync(0xffffffffu, x, 31);
+      if (lane == 0) s_npad[j & 3] = padded;
+      for (int i = lane; i < padded; i += 32) ord[i] = 0xFFFFu;
+    }
+    __syncwarp();
+    for (int i = lane; i < d.nblk; i += 32) ord[atomicAdd(&s_whist[32 + min((int)w[d.npre + i], 31)], 1)] = (uint16_t)i;
+    __syncwarp();
+  };
+
+  // ---- prologue: metadata of slabs 0..2, payload of slabs 0 and 1
+  if (warp == 0) {
+    load_meta(0);
+    if (nslab > 1) load_meta(1);
+    cp_async_wait_all();
+    __syncwarp();
+    scan_and_load_payload(0);
+    if (nslab > 1) scan_and_load_payload(1);
+    if (nslab > 2) load_meta(2);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+
+  int64_t znext = z0;  // next output plane
+  for (int k = 0; k <= nslab; ++k) {
+    if (warp == 0) {
+      // copies issued in the previous step (payload k+1, metadata k+2) land here
+      cp_async_wait_all();
+      __syncwarp();
+      if (k + 2 < nslab) scan_and_load_payload(k + 2);
+      if (k + 3 < nslab) load_meta(k + 3);
+    } else {
+      // Split the 7 worker warps between decoding slab k and computing the
+      // planes that are ready, in proportion to the estimated work (a segment
+      // costs about kSegCost items); a warp has one role, so no divergence.
+      const int ww = warp - 1;
+      const int64_t ready = zs + k - 1;  // last slab decoded in an earlier step
+      int64_t zc1 = znext;
+      while (zc1 < z1 && min(zc1 + 1, g.n0 - 1) <= ready) ++zc1;
+      const int nplanes = (int)(zc1 - znext);
+      const int nseg_k = k < nslab ? slab_desc(s, g, zs + k, ylo, yhi).nblk : 0;
+      const int items = (int)(y1 - y0) * g.nq;
+      const int dec_cost = kSegCost * nseg_k, comp_cost = nplanes * items;
+      int ndw = kWorkerWarps;
+      if (comp_cost == 0)
+        ndw = kWorkerWarps;
+      else if (dec_cost == 0)
+        ndw = 0;
+      else
+        ndw = min(kWorkerWarps - 1, max(1, (kWorkerWarps * dec_cost + (dec_cost + comp_cost) / 2) / (dec_cost + comp_cost)));
+      const bool decoder = ww < ndw;
+      const int wt = decoder ? ww * 32 + lane : (ww - ndw) * 32 + lane;
+      const int wstride = decoder ? ndw * 32 : (kWorkerWarps - ndw) * 32;
+      // decode slab k into its slot
+      if (decoder && k < nslab) {
+        const int64_t z = zs + k;
+        const SlabDesc d = slab_desc(s, g, z, ylo, yhi);
+        const uint8_t* w = meta_w(k) + d.npre;
+        const int32_t* hd = meta_h(k) + (int)(d.b0 & 3);
+        const uint32_t* off = meta_o(k);
+        const uint32_t* stg = stage(k);
+        unsigned char* dst = slot(z);
+        const uint16_t* ord = meta_ord(k);
+        const int nwork = kWidthSpecialize ? s_npad[k & 3] : d.nblk;
+        for (int t = wt; t < nwork; t += wstride) {
+          const int seg = kWidthSpecialize ? (int)ord[t] : t;
+          if (seg == 0xFFFF) continue;
+          const uint32_t wi = min((uint32_t)w[seg], (uint32_t)s.wmax);
+          int32_t q = hd[seg];
+          short v[32];
+          if (wi == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = (short)q;
+          } else {
+            const uint32_t* blk = stg + off[seg];
+            unpack_full(blk + 1, blk[0], wi, [&](int i, int32_t p) {
+              q += p;
+              v[i] = (short)q;
+            });
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint4 pk;
+            pk.x = (uint32_t)(uint16_t)v[8 * j + 0] | ((uint32_t)(uint16_t)v[8 * j + 1] << 16);
+            pk.y = (uint32_t)(uint16_t)v[8 * j + 2] | ((uint32_t)(uint16_t)v[8 * j + 3] << 16);
+            pk.z = (uint32_t)(uint16_t)v[8 * j + 4] | ((uint32_t)(uint16_t)v[8 * j + 5] << 16);
+            pk.w = (uint32_t)(uint16_t)v[8 * j + 6] | ((uint32_t)(uint16_t)v[8 * j + 7] << 16);
+            *reinterpret_cast<uint4*>(dst + (seg << 6) + (j << 4)) = pk;
+          }
+        }
+      }
+      // compute every output plane whose slabs are all decoded before this step
+      for (; znext < zc1; ++znext) {
+        if (decoder) continue;
+        const int64_t z = znext, zm = z > 0 ? z - 1 : 0, zp = z + 1 < g.n0 ? z + 1 : z;
+        const short* pc = reinterpret_cast<const short*>(slot(z));
+        const short* pm = reinterpret_cast<const short*>(slot(zm));
+        const short* pp = reinterpret_cast<const short*>(slot(zp));
+        // element offsets (inside each slot) of row y0 of planes z, z-1, z+1
+        const int64_t row0 = (z * g.n1 + y0) * g.n2;
+        const int rc0 = (int)(row0 - (slab_desc(s, g, z, ylo, yhi).b0 << 5));
+        const int rm0 = (int)((zm * g.n1 + y0) * g.n2 - (slab_desc(s, g, zm, ylo, yhi).b0 << 5));
+        const int rp0 = (int)((zp * g.n1 + y0) * g.n2 - (slab_desc(s, g, zp, ylo, yhi).b0 << 5));
+        const int n2 = (int)g.n2;
+        const int ez = (z == 0 || z == g.n0 - 1) ? 2 : 1;
+        using Vec = typename std::conditional<V == 8, uint4,
+                                              typename std::conditional<V == 4, uint2, unsigned short>::type>::type;
+        for (int it = wt; it < items; it += wstride) {
+          const int yr = g.nq == 1 ? it : (int)__umulhi((unsigned)it, g.nq_magic);
+          const int x = (it - yr * g.nq) * V;
+          const int roff = yr * n2 + x;
+          const int rc = rc0 + roff;
+          const int64_t y = y0 + yr;
+          const int ey = (y == 0 || y == g.n1 - 1) ? 2 : 1;
+          short c[V], a[V], b[V], zmv[V], zpv[V];
+          *reinterpret_cast<Vec*>(c) = *reinterpret_cast<const Vec*>(pc + rc);
+          if (OP == ST_RUNTIME || OP != ST_DERIV || g.axis == 1) {
+            *reinterpret_cast<Vec*>(a) = *reinterpret_cast<const Vec*>(pc + (y > 0 ? rc - n2 : rc));
+            *reinterpret_cast<Vec*>(b) = *reinterpret_cast<const Vec*>(pc + (y + 1 < g.n1 ? rc + n2 : rc));
+          }
+          if (OP == ST_RUNTIME || OP != ST_DERIV || g.axis == 0) {
+            *reinterpret_cast<Vec*>(zmv) = *reinterpret_cast<const Vec*>(pm + rm0 + roff);
+            *reinterpret_cast<Vec*>(zpv) = *reinterpret_cast<const Vec*>(pp + rp0 + roff);
+          }
+          int xl = c[0], xr = c[V - 1];
+          if (OP == ST_RUNTIME || OP != ST_DERIV || g.axis == 2) {
+            if (x > 0) xl = pc[rc - 1];
+            if (x + V < n2) xr = pc[rc + V];
+          }
+          // one-sided differences at the row ends are doubled
+          const int ex0 = x == 0 ? 2 : 1, exn = x + V == n2 ? 2 : 1;
+          if (STATS) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) mo.add((int32_t)c[i]);
+          }
+          store_items<OP, OUT, V>(g, out, row0 + roff, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (warp == 0) cp_async_wait_all();
+}
+
+// Tile heights tried by the autotuner (and, without tuning, the first that
+// fits the shared-memory budget).
+constexpr int kPipeTileHeights[] = {16, 8, 4, 2, 1};
+
+// Geometry of the pipelined tile for a field walked as d3 (host).  False when
+// the tile does not apply: S != 32, |q| >= 2^15, or no tile height fits.
+// budget: shared-memory bytes a CTA may use (force_ty > 0 takes that height).
+bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* smem_out, int force_ty, int budget);
+// Items per row and the magic divisor of the row/item split; false when
+// the 32-bit magic division would not be exact for this tile.
+bool plan_pipe_items(PGeo& g, int V);
+
+}  // namespace hc

@@ -116,18 +116,25 @@ def test_batch_equals_single_field_calls(env, orc):
 
 def test_other_field_ops(env, orc):
     hc, torch, dev = env
-    specs = [((20, 30, 40), 32, "gradmag|variance", 1e-3, True, 31), ((50, 70), 64, "gradmag", 1e-3, True, 32)]
+    # block 32 rows of 40 (8 outputs per item), 36 (4) and 30 (1) codes take
+    # the pipelined tile; block 64 the general one
+    specs = [((20, 30, 40), 32, "gradmag|variance", 1e-3, True, 31), ((50, 70), 64, "gradmag", 1e-3, True, 32),
+             ((10, 12, 36), 32, "gradmag|mean", 1e-3, True, 35), ((14, 22, 30), 32, "gradmag", 1e-3, True, 36)]
     b, refs = _make(env, orc, specs, field_dtype="float64")
     b.run()
     for (sc, f), (q, eps, ops) in zip(b.results(), refs):
         val = orc.stencil_q(q, orc.KIND_GRADMAG, eps)
         assert np.all(np.abs(f.cpu().numpy() - val) <= 1e-12 * np.maximum(np.abs(val), eps))
     for ax in range(3):
-        specs = [((20, 30, 40), 32, "derivative|mean", 1e-3, True, 33), ((12, 9, 300), 16, "derivative", 1e-3, True, 34)]
+        specs = [((20, 30, 40), 32, "derivative|mean", 1e-3, True, 33), ((12, 9, 300), 16, "derivative", 1e-3, True, 34),
+                 ((10, 12, 36), 32, "derivative|variance", 1e-3, True, 37), ((14, 22, 30), 32, "derivative", 1e-3, True, 38)]
         b, refs = _make(env, orc, specs, field_dtype="int64", axis=ax)
         b.run()
         for (sc, f), (q, eps, ops) in zip(b.results(), refs):
             assert np.array_equal(f.cpu().numpy(), orc.deriv_q(q, ax))
+            if sc is not None:
+                assert (sc["s1"], sc["s2"] if "variance" in ops else 0) == \
+                    (orc.sums_q(q)[0], orc.sums_q(q)[1] if "variance" in ops else 0)
 
 
 def test_graph_replay_and_launch_shapes_identical(env, orc):
