@@ -1,28 +1,36 @@
 """Benchmark: homomorphic operations on compressed paper-like fields, GB300.
 
 One step = every homomorphic operation of the hot path on every field of the
-paper-like workload, each field resident in HBM in compressed form:
-  mean (fused, stage 2 weights), variance (fused, stage 3), the derivative
-  along every axis, the gradient magnitude and the Laplacian (fused, stage 3),
-for five float32 fields shaped like the paper's datasets (k^-3 Gaussian random
-field + 5% spikes, value-range-relative eb = 1e-3, block 32).
+paper-like workload, each field resident in HBM in compressed form: the
+derivative along every axis, the gradient magnitude, the Laplacian and the
+exact mean / variance, for five float32 fields shaped like the paper's
+datasets (k^-3 Gaussian random field + 5% spikes, value-range-relative
+eb = 1e-3, block 32).  The step runs one pass per field (hc_op_multi: the
+stream is decoded once and every operation is written from the same
+neighbourhood, "decompress once, many ops").
 
-value   = original bytes of the fields x operations / step time (GB/s of
-          original data, the paper's throughput definition) on the device
-          with the compressed inputs already resident;
-e2e     = the same through the C ABI from pinned host memory: the compressed
-          streams are copied in and every result copied out inside the
-          timed region;
-plain   = full decompression to float32 followed by the same operations on
-          the same GPU (the "generic flow"), for the speedup;
-roofline: the dominant kernel's algorithmic bytes (compressed input + output
-          field) over its CUDA-event time, against the measured HBM copy
-          bandwidth.
+value    = original bytes of the fields x operations / step time (GB/s of
+           original data, the paper's throughput definition) on the device
+           with the compressed inputs already resident;
+per_op_launches = the same operations as one fused kernel per operation
+           (the paper's per-operation form: mean at stage 2, the rest at
+           stage 3), with that form's own roofline and kernel shares;
+e2e      = the one-pass step through the C ABI from pinned host memory: the
+           compressed streams are copied in and every output field and the
+           statistics copied out inside the timed region;
+plain    = full decompression to float32 followed by the same operations on
+           the same GPU (the "generic flow"), once per field or once per
+           operation, for the speedups;
+roofline = the one-pass kernel's algorithmic bytes (compressed input +
+           output fields) over its CUDA-event time, against the measured HBM
+           copy bandwidth.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference].
 With torchrun (WORLD_SIZE > 1) every rank runs its own copy of the workload
 on its own GPU (independent problems, weak scaling, no data-path collective);
-the step time is the maximum over ranks.
+the step time is the maximum over ranks.  Other modes: --batched (64 uneven
+fields in one launch), --serving (query stream), --profile-small /
+--profile-batch (small ncu cases).
 """
 from __future__ import annotations
 
@@ -48,8 +56,9 @@ EB = 1e-3
 BLOCK = 32
 WORKLOAD = ("paper-like scale: five float32 fields 100x500x500, 512x512x512, 256x384x384, 98x1200x1200, "
             "1800x3600 (2-D); seeded k^-3 Gaussian random fields + 5% spikes normalised to [0,1]; "
-            "value-range-relative eb=1e-3; block 32; every homomorphic op (mean@2, variance@3, "
-            "derivative per axis@3, gradient magnitude@3, Laplacian@3) fused on the compressed stream")
+            "value-range-relative eb=1e-3; block 32; every homomorphic op (derivative per axis, gradient "
+            "magnitude, Laplacian, exact mean and variance, all at stage 3) fused on the compressed stream, "
+            "one pass per field")
 
 
 def dist_env():
@@ -72,6 +81,18 @@ def reduce_max(value: float, world: int) -> float:
     return float(t.item())
 
 
+def weak_value(bytes_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job GB/s: every rank processes bytes_per_rank in its step, the
+    job's step time is the slowest rank's (ms_max)."""
+    return bytes_per_rank * world / (ms_max * 1e-3) / 1e9
+
+
+def timed_max(local_ms: float, world: int) -> float:
+    """The step time the job reports: the max over ranks, after a barrier."""
+    barrier(world)
+    return reduce_max(local_ms, world)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -81,7 +102,11 @@ def barrier(world: int):
 
 # -------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    """nvidia-smi clock / throttle-reason samples (every 50 ms) around the
+    timed region.  Started before the warm-up so that sampling is running when
+    the timed region begins; mark() brackets the region and stop() keeps the
+    samples that arrived inside it (or the one nearest to it when the region
+    is shorter than the sampling period)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -90,34 +115,53 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, line)
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, wait_first: float = 3.0):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t = time.monotonic()
+        while not self.lines and time.monotonic() - t < wait_first:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self):
+        if self.t0 is None:
+            self.t0 = time.monotonic()
+        else:
+            self.t1 = time.monotonic()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        if self.t1 is None:
+            self.mark()
+        time.sleep(0.06)  # let the sample that covers the region's end arrive
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        t0 = self.t0 if self.t0 is not None else -1e30
+        inside = [ln for t, ln in self.lines if t0 <= t <= self.t1 + 0.05]
+        if not inside and self.lines:
+            mid = (t0 + self.t1) / 2
+            inside = [min(self.lines, key=lambda tl: abs(tl[0] - mid))[1]]
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -130,7 +174,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "period_ms": 50}
 
 
 def smi_index(local: int) -> str:
@@ -381,53 +425,103 @@ def run_ours(args):
         for op in ("derivative", "gradmag", "laplacian"):
             tiles["x".join(map(str, it["shape"])) + ":" + op] = hc.autotune(it["c"], op, "float32", out=it["out"])
 
-    for _ in range(args.warmup):
-        wl.step()
-    torch.cuda.synchronize()
+    peak, peak_src = measured_peaks()
+    # outputs of the one-pass step: every derivative, the gradient magnitude,
+    # the Laplacian and the statistics of each field
+    mouts = []
+    for it in wl.items:
+        nd = len(it["shape"])
+        mouts.append({"derivative": [torch.empty(it["shape"], dtype=torch.float32, device=dev) for _ in range(nd)],
+                      "gradmag": torch.empty(it["shape"], dtype=torch.float32, device=dev),
+                      "laplacian": it["out"], "stats": it["scal"]})
 
-    # ---- device-resident timed region
+    def one_pass_step(evs=None, items=None):
+        for fi, it in enumerate(wl.items):
+            if evs is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+            hc.multi(it["c"] if items is None else items[fi], outs=mouts[fi])
+            if evs is not None:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record()
+                evs.append((fi, e0, e1))
+
     sampler = ClockSampler(smi_index(local))
     sampler.start()
+    for _ in range(args.warmup):
+        one_pass_step()
+    torch.cuda.synchronize()
+
+    # ---- headline, device-resident: one pass per field computes every
+    # operation from one decode (hc_op_multi)
     barrier(world)
     torch.cuda.synchronize()
-    events = []
+    sampler.mark()
+    mev = []
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(args.steps):
-        wl.step(events)
+        one_pass_step(mev)
     t1.record()
     torch.cuda.synchronize()
+    sampler.mark()
     barrier(world)
     clocks = sampler.stop()
-    ms = t0.elapsed_time(t1) / args.steps
-    ms = reduce_max(ms, world)
-    value = bytes_step * world / (ms * 1e-3) / 1e9
+    ms = reduce_max(t0.elapsed_time(t1) / args.steps, world)
+    value = weak_value(bytes_step, world, ms)
+    m_ms = sum(x.elapsed_time(y) for _, x, y in mev)
+    m_bytes = sum(wl.items[fi]["c"].nbytes + (len(wl.items[fi]["shape"]) + 2) * 4 * wl.items[fi]["n"] + 64
+                  for fi, _, _ in mev)
+    achieved = m_bytes / (m_ms * 1e-3) / 1e9
+    per_elem = read_profile_traffic("stencil_multi_256x384x384")
+    m_elems = sum(wl.items[fi]["n"] for fi, _, _ in mev) / max(1, len(mev))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": per_elem * m_elems if per_elem is not None else None,
+                "kernel": "k_stencil_multi", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": m_bytes / len(mev), "avg_launch_ms": m_ms / len(mev),
+                "algorithmic_bytes": "compressed stream + (ndim + 2) float32 output fields + 64 B of statistics"}
 
-    # per-kernel durations inside the timed region
+    # ---- the same operations as one fused kernel per operation (the paper's
+    # per-operation form), device-resident
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    barrier(world)
+    events = []
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        wl.step(events)
+    b.record()
+    torch.cuda.synchronize()
+    op_ms = reduce_max(a.elapsed_time(b) / args.steps, world)
     per = {}
-    for fi, op, a, b in events:
+    for fi, op, x, y in events:
         d = per.setdefault(op, {"ms": 0.0, "bytes": 0.0, "launches": 0})
         it = wl.items[fi]
-        d["ms"] += a.elapsed_time(b)
+        d["ms"] += x.elapsed_time(y)
         d["bytes"] += it["c"].nbytes + (it["n"] * 4 if op in ("derivative", "gradmag", "laplacian") else 64)
         d["launches"] += 1
     dom = max(per, key=lambda k: per[k]["ms"])
-    peak, peak_src = measured_peaks()
-    achieved = per[dom]["bytes"] / (per[dom]["ms"] * 1e-3) / 1e9
+    op_ach = per[dom]["bytes"] / (per[dom]["ms"] * 1e-3) / 1e9
     # DRAM traffic: the dominant kernel's bytes per element from its committed
     # ncu capture on the 256x384x384 case, scaled to this launch's elements
     tag = {"derivative": "stencil_pipe_derivative_256x384x384", "gradmag": "stencil_pipe_gradmag_256x384x384",
            "laplacian": "stencil_pipe_laplacian_256x384x384",
            "variance": "reduce_stream_variance_256x384x384"}.get(dom, "")
-    per_elem = read_profile_traffic(tag) if tag else None
+    op_pe = read_profile_traffic(tag) if tag else None
     elems = sum(wl.items[fi]["n"] for fi, op, _, _ in events if op == dom) / max(1, per[dom]["launches"])
-    traffic = per_elem * elems if per_elem is not None else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": per[dom]["bytes"] / per[dom]["launches"],
-                "avg_launch_ms": per[dom]["ms"] / per[dom]["launches"]}
-    share = {k: v["ms"] / sum(x["ms"] for x in per.values()) for k, v in per.items()}
+    per_op_launches = {
+        "what": "one fused kernel per operation (mean at stage 2, the rest at stage 3), 35 launches per step",
+        "ms_per_step": op_ms, "value": weak_value(bytes_step, world, op_ms),
+        "one_pass_speedup": op_ms / ms,
+        "roofline": {"bound": "hbm", "achieved": op_ach, "peak": peak, "unit": "GB/s", "frac": op_ach / peak,
+                     "traffic": op_pe * elems if op_pe is not None else None, "kernel": dom,
+                     "algorithmic_bytes_per_launch": per[dom]["bytes"] / per[dom]["launches"],
+                     "avg_launch_ms": per[dom]["ms"] / per[dom]["launches"]},
+        "kernel_time_share": {k: v["ms"] / sum(x["ms"] for x in per.values()) for k, v in per.items()}}
 
     # ---- plain path: every op on a full decompression to float32 (the
     # paper's "decompress, then operate" per operation), and, for reference,
@@ -463,12 +557,15 @@ def run_ours(args):
         plain_once_ms = timed(lambda: plain_step(True))
         del df
 
-    # ---- end to end through the ABI from pinned host memory
+    # ---- end to end through the ABI from pinned host memory: every step
+    # copies the compressed streams in, runs the one-pass step and copies
+    # every output field and the statistics out
     host_streams = [it["c"].stream.cpu().pin_memory() for it in wl.items]
     dev_streams = [torch.empty_like(it["c"].stream) for it in wl.items]
     e2e_items = [hc.Compressed(ds, it["c"].header, it["c"].nbytes) for ds, it in zip(dev_streams, wl.items)]
-    host_out = [torch.empty(it["shape"], dtype=torch.float32).pin_memory() for it in wl.items]
-    host_scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8).pin_memory()
+    host_out = [[torch.empty(it["shape"], dtype=torch.float32).pin_memory() for _ in range(len(it["shape"]) + 2)]
+                for it in wl.items]
+    host_scal = [torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8).pin_memory() for _ in wl.items]
     d2h = 0
 
     def e2e_step():
@@ -476,23 +573,14 @@ def run_ours(args):
         d2h = 0
         for fi, it in enumerate(wl.items):
             dev_streams[fi].copy_(host_streams[fi], non_blocking=True)
-            for op, ax in op_list(len(it["shape"])):
-                if op == "mean":
-                    hc.mean(e2e_items[fi], level="p", out=it["scal"])
-                elif op == "variance":
-                    hc.variance(e2e_items[fi], level="q", out=it["scal"])
-                elif op == "derivative":
-                    hc.derivative(e2e_items[fi], ax, out=it["out"])
-                elif op == "gradmag":
-                    hc.gradmag(e2e_items[fi], out=it["out"])
-                else:
-                    hc.laplacian(e2e_items[fi], out=it["out"])
-                if op in ("mean", "variance"):
-                    host_scal.copy_(it["scal"], non_blocking=True)
-                    d2h += hc.SCALAR_BYTES
-                else:
-                    host_out[fi].copy_(it["out"], non_blocking=True)
-                    d2h += it["n"] * 4
+        one_pass_step(items=e2e_items)
+        for fi, it in enumerate(wl.items):
+            mo = mouts[fi]
+            for dst, src in zip(host_out[fi], mo["derivative"] + [mo["gradmag"], mo["laplacian"]]):
+                dst.copy_(src, non_blocking=True)
+                d2h += it["n"] * 4
+            host_scal[fi].copy_(mo["stats"], non_blocking=True)
+            d2h += hc.SCALAR_BYTES
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
@@ -506,7 +594,7 @@ def run_ours(args):
     b.record()
     torch.cuda.synchronize()
     e2e_ms = reduce_max(a.elapsed_time(b) / args.steps, world)
-    e2e = {"value": bytes_step * world / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": comp_bytes,
+    e2e = {"value": weak_value(bytes_step, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": comp_bytes,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
     per_op = None
@@ -524,15 +612,20 @@ def run_ours(args):
                                  "fields, far larger than the 129 MB L2",
                            "parallelism": f"replicas x{world} (independent fields per GPU)",
                            "autotuned_tile_rows": tiles},
+                "step": "one pass per field: hc_op_multi decodes the stream once and writes the derivative "
+                        "along every axis, the gradient magnitude, the Laplacian and the exact stage-3 "
+                        "mean / variance (5 launches per step)",
                 "plain": None if plain_ms is None else {
-                    "what": "per op: decompress to float32, then the op on the GPU",
-                    "ms_per_step": plain_ms, "value": bytes_step * world / (plain_ms * 1e-3) / 1e9,
-                    "speedup_homomorphic_vs_plain": plain_ms / ms,
+                    "what": "decompress to float32 on the GPU, then the same operations on the floats",
                     "decompress_once_ms_per_step": plain_once_ms,
-                    "decompress_once_value": bytes_step * world / (plain_once_ms * 1e-3) / 1e9,
-                    "speedup_homomorphic_vs_decompress_once": plain_once_ms / ms},
-                "e2e": e2e, "gpu_launches": wl.launches_per_step * args.steps,
-                "roofline": roofline, "kernel_time_share": share, "clocks": clocks}
+                    "decompress_once_value": weak_value(bytes_step, world, plain_once_ms),
+                    "speedup_vs_decompress_once": plain_once_ms / ms,
+                    "decompress_per_op_ms_per_step": plain_ms,
+                    "decompress_per_op_value": weak_value(bytes_step, world, plain_ms),
+                    "speedup_vs_decompress_per_op": plain_ms / ms},
+                "per_op_launches": per_op_launches,
+                "e2e": e2e, "gpu_launches": len(wl.items) * args.steps,
+                "roofline": roofline, "clocks": clocks}
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(fields)
         if per_op is not None:
@@ -572,11 +665,12 @@ def run_batched(args):
     del raw
     b, comps = best["batch"], best["comps"]
     comp_bytes = sum(c.nbytes for c in comps)
+    sampler = ClockSampler(smi_index(0))
+    sampler.start()
     for _ in range(args.warmup):
         b.replay()
     torch.cuda.synchronize()
-    sampler = ClockSampler(smi_index(0))
-    sampler.start()
+    sampler.mark()
     ev = []
     for _ in range(args.steps):
         flush()
@@ -587,6 +681,7 @@ def run_batched(args):
         e1.record()
         ev.append((e0, e1))
     torch.cuda.synchronize()
+    sampler.mark()
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(z) for a, z in ev) / args.steps
     assert b.status() == 0
@@ -703,7 +798,8 @@ def run_serving(args):
 
 def run_profile_small():
     """Small case for ncu captures: one 256x384x384 float32 field (compressed
-    ~44 MB, float32 outputs 151 MB: larger than L2), each operation 3 times."""
+    ~44 MB, float32 outputs 151 MB each: larger than L2), each operation 3
+    times, then the one-pass call (5 output fields + statistics)."""
     import torch
 
     import __graft_entry__
@@ -715,6 +811,8 @@ def run_profile_small():
     x = synth.grf_field((256, 384, 384), 1002)
     c = hc.compress(torch.from_numpy(x).cuda(), EB, rel=True, S=BLOCK)
     out = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+    mouts = {"derivative": [torch.empty(x.shape, dtype=torch.float32, device="cuda") for _ in range(3)],
+             "gradmag": torch.empty(x.shape, dtype=torch.float32, device="cuda"), "laplacian": out}
     for _ in range(3):
         hc.derivative(c, 2, out=out)
         hc.gradmag(c, out=out)
@@ -722,8 +820,38 @@ def run_profile_small():
         hc.variance(c, level="q")
         hc.mean(c, level="p")
         hc.decompress(c, "f", out=out)
+        hc.multi(c, outs=mouts)
     torch.cuda.synchronize()
     print(json.dumps({"profile_small": "ok", "compressed_bytes": c.nbytes, "wmax": int(c.header.wmax)}))
+    return 0
+
+
+def run_profile_batch():
+    """Small case for an ncu capture of the batched kernel: the 64-field
+    batched workload at block 32, 256 threads, tile height 16 (the tuned
+    choice), launched 3 times without the autotuner."""
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    shapes = synth.log_uniform_shapes(64, 32, 384, 3)
+    comps = []
+    for j, sh in enumerate(shapes):
+        x = torch.from_numpy(synth.grf_field(sh, 3000 + j)).to(dev)
+        comps.append(hc._trim(hc.compress(x, EB, rel=True, S=BLOCK)))
+        del x
+    b = hc.Batch([(c, "mean|variance|laplacian") for c in comps], threads=256, ty=16)
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    print(json.dumps({"profile_batch": "ok", "compressed_bytes": sum(c.nbytes for c in comps),
+                      "elements": sum(int(np.prod(c.shape)) for c in comps), "grid": b.grid, "smem": b.smem}))
     return 0
 
 
@@ -738,6 +866,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-small", action="store_true", help="run the small ncu case and exit")
     ap.add_argument("--batched", action="store_true", help="the batched form (64 uneven fields, one launch)")
+    ap.add_argument("--profile-batch", action="store_true", help="run the small batched ncu case and exit")
     ap.add_argument("--serving", action="store_true", help="the serving form (200 resident fields, Poisson queries)")
     ap.add_argument("--fields", type=int, default=200)
     ap.add_argument("--qps", type=float, default=2000.0)
@@ -745,6 +874,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.profile_small:
         return run_profile_small()
+    if args.profile_batch:
+        return run_profile_batch()
     if args.serving:
         return run_serving(args)
     if args.batched:

@@ -225,6 +225,28 @@ HC_API int hc_op_gradmag(const hc_stage* in, double eps, int ndim, const int64_t
 HC_API int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
                     void* d_ws, size_t ws_bytes, void* stream);
 
+/* All operations of one field in one pass ("decompress once, many ops",
+ * Section VI's remark that a decompressed representation serves several
+ * analyses).  Fused on a stream input (level Q): the codes are decoded once
+ * and every wanted output is written from the same neighbourhood -- the
+ * derivative along each user axis, the gradient magnitude, the Laplacian
+ * (values exactly as hc_op_derivative / hc_op_gradmag / hc_op_laplacian
+ * produce them) and the stage-Q statistics (as hc_op_variance at level Q:
+ * exact s1, s2, mean, variance, std).  Where the one-pass kernel does not
+ * apply (block size other than 32, |q| >= 2^15, rows not a multiple of 4
+ * codes, unaligned outputs) and for array inputs, the same results come from
+ * the one-operation entry points in turn.  ASYNC. */
+typedef struct hc_multi_out {
+  void* d_derivative[3];  /* per user axis (the first ndim used): N outputs, or NULL */
+  void* d_gradmag;        /* N outputs, or NULL */
+  void* d_laplacian;      /* N outputs, or NULL */
+  hc_scalar* d_stats;     /* or NULL */
+  int32_t out_dtype;      /* HC_F32 or HC_F64 for every field output */
+  int32_t reserved;
+} hc_multi_out;
+HC_API int hc_op_multi(const hc_stage* in, double eps, int ndim, const int64_t* dims, const hc_multi_out* out,
+                       void* d_ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------- batched fused launch */
 /* Many compressed fields, each with its own operations, decoded and operated
  * on by ONE persistent kernel: decoding and operation fused, no stage

@@ -404,6 +404,52 @@ int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_
   return stencil_pipe_autotune(in->hdr, in->d_data, d3, sop, d_out, out_dtype, d_ws, as_stream(stream), chosen);
 }
 
+int hc_op_multi(const hc_stage* in, double eps, int ndim, const int64_t* dims, const hc_multi_out* out, void* d_ws,
+                size_t ws_bytes, void* stream) {
+  int64_t dims3[3];
+  int rc = check_op(in, eps, ndim, dims, d_ws, ws_bytes, dims3);
+  if (rc) return rc;
+  if (!out) return fail(HC_ERR_INVALID_ARG, "null output set");
+  if (out->out_dtype != HC_F32 && out->out_dtype != HC_F64) return fail(HC_ERR_INVALID_ARG, "out_dtype must be F32 or F64");
+  void* fields[5] = {out->d_derivative[0], out->d_derivative[1], out->d_derivative[2], out->d_gradmag,
+                     out->d_laplacian};
+  for (int a = ndim; a < 3; ++a)
+    if (out->d_derivative[a]) return fail(HC_ERR_INVALID_ARG, "derivative output for an axis >= ndim");
+  for (void* f : fields)
+    if (f && !aligned16(f)) return fail(HC_ERR_INVALID_ARG, "outputs must be 16-byte aligned device buffers");
+  if (in->kind == HC_STAGE_COMPRESSED) {
+    if (in->level == HC_STAGE_P && (out->d_derivative[0] || out->d_derivative[1] || out->d_derivative[2] ||
+                                    out->d_gradmag || out->d_laplacian))
+      return fail(HC_ERR_UNSUPPORTED, "stage-2 differentiation is not defined for a 1-D block partition (Section V-B)");
+    if (in->level == HC_STAGE_Q) {
+      // the user's derivative axes in the shape the kernel walks
+      void* deriv3[3] = {nullptr, nullptr, nullptr};
+      for (int a = 0; a < ndim; ++a) {
+        int axis3 = a + 3 - ndim;
+        int64_t d3[3];
+        stencil_walk_dims(in->hdr, d3, &axis3);
+        deriv3[axis3] = out->d_derivative[a];
+      }
+      rc = stencil_multi_impl(in->hdr, in->d_data, deriv3, out->d_gradmag, out->d_laplacian, out->d_stats,
+                              out->out_dtype, d_ws, as_stream(stream));
+      if (rc != HC_ERR_UNSUPPORTED) return rc;
+    }
+  }
+  // one operation at a time
+  for (int a = 0; a < ndim; ++a)
+    if (out->d_derivative[a] &&
+        (rc = stencil(in, eps, ndim, dims, ST_DERIV, a, out->d_derivative[a], out->out_dtype, d_ws, ws_bytes, stream)))
+      return rc;
+  if (out->d_gradmag &&
+      (rc = stencil(in, eps, ndim, dims, ST_GRADMAG, 0, out->d_gradmag, out->out_dtype, d_ws, ws_bytes, stream)))
+    return rc;
+  if (out->d_laplacian &&
+      (rc = stencil(in, eps, ndim, dims, ST_LAPLACIAN, 0, out->d_laplacian, out->out_dtype, d_ws, ws_bytes, stream)))
+    return rc;
+  if (out->d_stats) return stats(in, eps, ndim, dims, out->d_stats, d_ws, ws_bytes, stream, RED_VAR);
+  return HC_OK;
+}
+
 size_t hc_batch_plan_bytes(int n_items) { return (size_t)batch_plan_bytes(n_items); }
 size_t hc_batch_workspace_bytes(int n_items) { return (size_t)batch_ws_bytes(n_items); }
 int hc_batch_plan(const hc_batch_item* items, int n_items, const hc_batch_tune* tune, void* h_plan, size_t cap,

@@ -77,13 +77,19 @@ int reduce_array_impl(const hc_stage* in, double eps, int what, hc_scalar* d_out
 int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
                                  unsigned* ticket, int max_parts, cudaStream_t st);
 
-enum StencilOp { ST_DERIV = 0, ST_GRADMAG = 1, ST_LAPLACIAN = 2 };
+enum StencilOp { ST_DERIV = 0, ST_GRADMAG = 1, ST_LAPLACIAN = 2, ST_MULTI = 3 };
 int stencil_stream_impl(const hc_header* h, const void* d_stream, int op, int axis3, void* d_out, int out_dtype,
                         void* d_ws, cudaStream_t st);
 // Pipelined fused stencil (block size 32, rows of a multiple of 8, |q| < 2^15);
 // HC_ERR_UNSUPPORTED when it does not apply.  d3 is the (possibly remapped) shape.
 int stencil_pipe_impl(const hc_header* h, const void* d_stream, const int64_t* d3, int op, int axis3, void* d_out,
                       int out_dtype, void* d_ws, cudaStream_t st);
+// All operations of one field in one pass (pipelined tile, ST_MULTI):
+// outputs by internal axis, NULL where not wanted; d_stats (exact stage-3
+// statistics) or NULL.  HC_ERR_UNSUPPORTED when the pipelined tile does not
+// apply (nothing recorded).
+int stencil_multi_impl(const hc_header* h, const void* d_stream, void* const deriv3[3], void* d_grad, void* d_lap,
+                       hc_scalar* d_stats, int out_dtype, void* d_ws, cudaStream_t st);
 // Shape the fused stencils walk: a 2-D field (1, n1, n2) is walked as (n1, 1, n2).
 void stencil_walk_dims(const hc_header* h, int64_t d3[3], int* axis3);
 // Time the pipelined kernel's tile heights for this field/op and cache the best.

@@ -8,6 +8,7 @@
 #include <tuple>
 #include <type_traits>
 
+#include "hc_finish.cuh"
 #include "hc_internal.cuh"
 #include "hc_launch.h"
 #include "hc_stencil_pipe.cuh"
@@ -22,6 +23,29 @@ __global__ void __launch_bounds__(kThreads) k_stencil_pipe(DevStream s, PGeo g, 
   extern __shared__ __align__(16) unsigned char sm[];
   Moments mo;
   pipe_tile<OP, OUT, V, false>(s, g, (int)(blockIdx.x % g.nyt), (int)(blockIdx.x / g.nyt), out, err, sm, mo);
+}
+
+// All operations of one field from one decode (ST_MULTI); with STATS the
+// exact sums of the codes go through the per-CTA partials and the last CTA
+// finishes the stage-3 statistics.
+template <int OUT, int V, bool STATS>
+__global__ void __launch_bounds__(kThreads) k_stencil_multi(DevStream s, PGeo g, int* err, Partial* parts,
+                                                             unsigned* ticket, hc_scalar* stats, double two_eps) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int s_err;
+  if (threadIdx.x == 0) s_err = 0;
+  __syncthreads();
+  Moments mo;
+  pipe_tile<ST_MULTI, OUT, V, STATS>(s, g, (int)(blockIdx.x % g.nyt), (int)(blockIdx.x / g.nyt), nullptr, &s_err, sm,
+                                     mo);
+  __syncthreads();
+  const int e = s_err;
+  if (threadIdx.x == 0 && e) set_error(err, e);
+  if constexpr (STATS) {
+    const u128 s2 = ((u128)mo.hi << 64) | (u128)mo.lo;
+    reduce_and_finish(mo.s1, s2, e, parts, ticket,
+                      [&](long long a, u128 b, int ee) { finalize_int(stats, s.N, a, b, true, two_eps, ee); });
+  }
 }
 
 // ------------------------------------------------------------------ host
@@ -211,6 +235,71 @@ static int stencil_pipe_launch(const hc_header* h, const void* d_stream, const i
     HC_PIPE_OUT(ST_LAPLACIAN)
   }
 #undef HC_PIPE_OUT
+}
+
+template <int OUT, int V, bool STATS>
+static int launch_multi(const hc_header* h, const void* d_stream, PGeo g, int smem, hc_scalar* d_stats, void* d_ws,
+                        cudaStream_t st) {
+  auto kern = k_stencil_multi<OUT, V, STATS>;
+  if (!plan_pipe_items(g, V)) return HC_ERR_UNSUPPORTED;
+  int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  if (rc) return rc;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  plan_pipe_grid(g, per_sm);
+  if (STATS && (int64_t)g.nyt * g.nzt > kMaxGrid) {
+    // one partial per CTA: fewer, taller plane ranges
+    if (g.nyt > kMaxGrid) return HC_ERR_UNSUPPORTED;
+    const int64_t nzt = std::max<int64_t>(1, kMaxGrid / g.nyt);
+    g.tz = (int)ceil_div(g.n0, nzt);
+    g.nzt = (int)ceil_div(g.n0, g.tz);
+  }
+  const int64_t grid = (int64_t)g.nyt * g.nzt;
+  OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(dev_stream(h, d_stream), g, &ws->status, ws_partials(d_ws),
+                                                &ws->ticket, d_stats, 2.0 * h->eps);
+  return check_launch_cfg("stencil (all operations)", reinterpret_cast<const void*>(kern), grid, smem);
+}
+
+int stencil_multi_impl(const hc_header* h, const void* d_stream, void* const deriv3[3], void* d_grad, void* d_lap,
+                       hc_scalar* d_stats, int out_dtype, void* d_ws, cudaStream_t st) {
+  if (out_dtype != HC_F32 && out_dtype != HC_F64) return HC_ERR_UNSUPPORTED;
+  void* outs[5] = {deriv3[0], deriv3[1], deriv3[2], d_grad, d_lap};
+  for (void* o : outs)
+    if (o && !aligned16(o)) return HC_ERR_UNSUPPORTED;
+  int64_t d3[3];
+  stencil_walk_dims(h, d3, nullptr);
+  PGeo g{};
+  int smem = 0;
+  if (!plan_pipe_geometry(h, d3, g, &smem, 0, 74 * 1024)) return HC_ERR_UNSUPPORTED;
+  if (g.n1 * g.n2 >= ((int64_t)1 << 31)) return HC_ERR_UNSUPPORTED;
+  g.axis = 0;
+  g.op = ST_MULTI;
+  g.out = out_dtype;
+  for (int k = 0; k < 5; ++k) g.mout[k] = outs[k];
+  g.eps = h->eps;
+  g.te = 2.0 * h->eps;
+  g.eps_f = (float)h->eps;
+  g.te_f = (float)(2.0 * h->eps);
+  const int v = g.n2 % 8 == 0 ? 8 : (g.n2 % 4 == 0 ? 4 : 0);
+  if (!v) return HC_ERR_UNSUPPORTED;
+#define HC_MULTI(OUTT, VV)                                                                                  \
+  return d_stats ? launch_multi<OUTT, VV, true>(h, d_stream, g, smem, d_stats, d_ws, st)                    \
+                 : launch_multi<OUTT, VV, false>(h, d_stream, g, smem, d_stats, d_ws, st);
+  if (out_dtype == HC_F32) {
+    if (v == 8) {
+      HC_MULTI(HC_F32, 8)
+    } else {
+      HC_MULTI(HC_F32, 4)
+    }
+  } else {
+    if (v == 8) {
+      HC_MULTI(HC_F64, 8)
+    } else {
+      HC_MULTI(HC_F64, 4)
+    }
+  }
+#undef HC_MULTI
 }
 
 }  // namespace hc

@@ -47,6 +47,8 @@ struct PGeo {
   int slot_bytes;   // nblk_max * 64
   int axis;
   int op, out;        // operation and output type for the ST_RUNTIME instantiation
+  void* mout[5];      // ST_MULTI outputs (NULL: not wanted): the derivative along
+                      // internal axes 0, 1, 2, the gradient magnitude, the Laplacian
   unsigned nq_magic;  // ceil(2^32 / nq) for the row/item split (unused when nq == 1)
   int nq;             // items per row: n2 / V
   float eps_f, te_f;
@@ -168,6 +170,46 @@ __device__ __forceinline__ void emit_items(const PGeo& g, typename OT<D>::T* o, 
   }
 }
 
+// ST_MULTI: every wanted output of the V points from one neighbourhood (one
+// decode serves all operations), output by output so that only V results are
+// live at a time.
+template <int D, int V>
+__device__ __forceinline__ void emit_multi(const PGeo& g, int64_t i0, const short* c, const short* a,
+                                           const short* b, const short* zmv, const short* zpv, int xl, int xr,
+                                           int ex0, int exn, int ez, int ey) {
+  using T = typename OT<D>::T;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    T* o = reinterpret_cast<T*>(g.mout[k]);
+    if (o == nullptr) continue;
+    T res[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      const int cm = i == 0 ? xl : c[i - 1];
+      const int cp = i == V - 1 ? xr : c[i + 1];
+      int ex = 1;
+      if (i == 0) ex = ex0;
+      if (i == V - 1) ex = ex * exn;
+      const int d0 = ((int)zpv[i] - zmv[i]) * ez, d1 = ((int)b[i] - a[i]) * ey, d2 = (cp - cm) * ex;
+      if (k == 0) res[i] = emit1<ST_DERIV, D>(d0, 0, 0, g);
+      if (k == 1) res[i] = emit1<ST_DERIV, D>(d1, 0, 0, g);
+      if (k == 2) res[i] = emit1<ST_DERIV, D>(d2, 0, 0, g);
+      if (k == 3) res[i] = emit1<ST_GRADMAG, D>(d0, d1, d2, g);
+      if (k == 4)
+        res[i] = emit1<ST_LAPLACIAN, D>((int)zmv[i] + zpv[i] + a[i] + b[i] + cm + cp - 6 * (int)c[i], 0, 0, g);
+    }
+    o += i0;
+    if constexpr (V * sizeof(T) >= 16) {
+#pragma unroll
+      for (int v = 0; v < (int)(V * sizeof(T) / 16); ++v)
+        reinterpret_cast<uint4*>(o)[v] = reinterpret_cast<const uint4*>(res)[v];
+    } else {
+#pragma unroll
+      for (int i = 0; i < V; ++i) o[i] = res[i];
+    }
+  }
+}
+
 // Compile-time operation and type, or (ST_RUNTIME) the run-time switch over
 // both; out + i0 is the item's first output.
 template <int OP, int OUT, int V>
@@ -193,6 +235,8 @@ __device__ __forceinline__ void store_items(const PGeo& g, typename OT<OUT>::T* 
         break;
     }
 #undef HC_PIPE_RT
+  } else if constexpr (OP == ST_MULTI) {
+    emit_multi<OUT, V>(g, i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
   } else {
     emit_items<OP, OUT, V>(g, out + i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
   }
@@ -201,7 +245,8 @@ __device__ __forceinline__ void store_items(const PGeo& g, typename OT<OUT>::T* 
 // One tile (row tile yt, plane range zt) of the pipelined stencil; needs
 // blockDim.x == kThreads.  sm: the dynamic shared memory (psmem(g).total
 // bytes).  With STATS the codes of the points the tile owns are added to mo.
-// OP = OUT = ST_RUNTIME takes the operation and output type from g.
+// OP = OUT = ST_RUNTIME takes the operation and output type from g; OP =
+// ST_MULTI writes every output of g.mout that is set (out is unused).
 template <int OP, int OUT, int V, bool STATS>
 __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int zt, typename OT<OUT>::T* out, int* err,
                                  unsigned char* sm, Moments& mo) {

@@ -41,7 +41,7 @@ ABI_FUNCTIONS = (
     "hc_decompress_to_stage", "hc_workspace_status", "hc_op_mean", "hc_op_variance", "hc_op_std",
     "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc", "hc_autotune",
     "hc_batch_plan_bytes", "hc_batch_workspace_bytes", "hc_batch_plan", "hc_batch_run", "hc_batch_graph_create",
-    "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status",
+    "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi",
 )
 HC_BATCH_MEAN, HC_BATCH_VARIANCE, HC_BATCH_DERIVATIVE, HC_BATCH_GRADMAG, HC_BATCH_LAPLACIAN = 1, 2, 4, 8, 16
 BATCH_OPS = {"mean": HC_BATCH_MEAN, "variance": HC_BATCH_VARIANCE, "derivative": HC_BATCH_DERIVATIVE,
@@ -77,6 +77,12 @@ class HcStage(ctypes.Structure):
 class HcBatchItem(ctypes.Structure):
     _fields_ = [("d_stream", ctypes.c_void_p), ("hdr", HcHeader), ("ops", ctypes.c_uint32), ("axis", ctypes.c_int32),
                 ("d_scalar", ctypes.c_void_p), ("d_field", ctypes.c_void_p), ("field_dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class HcMultiOut(ctypes.Structure):
+    _fields_ = [("d_derivative", ctypes.c_void_p * 3), ("d_gradmag", ctypes.c_void_p),
+                ("d_laplacian", ctypes.c_void_p), ("d_stats", ctypes.c_void_p), ("out_dtype", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -130,6 +136,7 @@ def lib():
             "hc_op_gradmag": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_op_laplacian": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_autotune": ([P(HcStage), i32, i32, vp, vp, sz, vp, P(ctypes.c_int)], i32),
+            "hc_op_multi": ([P(HcStage), dbl, i32, P(ctypes.c_int64), P(HcMultiOut), vp, sz, vp], i32),
             "hc_batch_plan_bytes": ([i32], sz),
             "hc_batch_workspace_bytes": ([i32], sz),
             "hc_batch_plan": ([P(HcBatchItem), i32, P(HcBatchTune), vp, sz, P(sz)], i32),
@@ -398,6 +405,40 @@ def laplacian(inp, out_dtype: str = "float32", out=None, level: str = "q", strea
     _check(lib().hc_op_laplacian(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
                                  _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return out
+
+
+def multi(inp, derivative=True, gradmag=True, laplacian=True, stats=True, out_dtype: str = "float32",
+          outs=None, level: str = "q", stream=None) -> dict:
+    """Every operation of one field from one decode (hc_op_multi).  Returns a
+    dict with "derivative" (list per axis), "gradmag", "laplacian" (tensors)
+    and "stats" (the 64-byte hc_scalar), each present when requested.
+    `outs` may hold preallocated tensors under the same keys."""
+    torch = _torch()
+    st, eps, shape, dev = _input(inp, level)
+    outs = dict(outs or {})
+    mo = HcMultiOut()
+    mo.out_dtype = _OUT[out_dtype]
+    if derivative:
+        ds = outs.get("derivative") or [None] * len(shape)
+        ds = [_field_out(shape, out_dtype, dev, d) for d in ds]
+        outs["derivative"] = ds
+        for a, d in enumerate(ds):
+            mo.d_derivative[a] = d.data_ptr()
+    for key, flag in (("gradmag", gradmag), ("laplacian", laplacian)):
+        if flag:
+            t = _field_out(shape, out_dtype, dev, outs.get(key))
+            outs[key] = t
+            setattr(mo, "d_" + key, t.data_ptr())
+    if stats:
+        t = outs.get("stats")
+        if t is None:
+            t = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=dev)
+        outs["stats"] = t
+        mo.d_stats = t.data_ptr()
+    ws = workspace(dev, stream)
+    _check(lib().hc_op_multi(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.byref(mo),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return outs
 
 
 def workspace_status(stream=None) -> int:

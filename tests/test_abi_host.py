@@ -61,6 +61,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(hc_batch_item), offsetof(hc_batch_item, hdr), offsetof(hc_batch_item, ops),
          offsetof(hc_batch_item, d_scalar), offsetof(hc_batch_item, field_dtype));
   printf("%zu %zu %zu\n", sizeof(hc_batch_tune), offsetof(hc_batch_tune, unit_elems), offsetof(hc_batch_tune, ctas_per_sm));
+  printf("%zu %zu %zu\n", sizeof(hc_multi_out), offsetof(hc_multi_out, d_stats), offsetof(hc_multi_out, out_dtype));
   return 0;
 }
 """
@@ -80,6 +81,8 @@ int main(void) {
     B, T = hc.HcBatchItem, hc.HcBatchTune
     assert vals[14:19] == [ctypes.sizeof(B), B.hdr.offset, B.ops.offset, B.d_scalar.offset, B.field_dtype.offset]
     assert vals[19:22] == [ctypes.sizeof(T), T.unit_elems.offset, T.ctas_per_sm.offset]
+    M = hc.HcMultiOut
+    assert vals[22:25] == [ctypes.sizeof(M), M.d_stats.offset, M.out_dtype.offset]
 
 
 @pytest.mark.parametrize("S", [1, 2, 3, 16, 32, 33, 64, 100, 128, 4096])
@@ -195,3 +198,27 @@ def test_batch_argument_errors_before_any_cuda_call(hc):
     assert L.hc_batch_graph_create(buf, ctypes.c_void_p(16), ws, 1 << 20, ctypes.byref(g)) == hc.HC_ERR_INVALID_ARG
     assert L.hc_batch_graph_launch(None, None) == hc.HC_ERR_INVALID_ARG
     assert L.hc_batch_graph_destroy(None) == hc.HC_OK
+
+
+def test_multi_argument_errors_before_any_cuda_call(hc):
+    L = hc.lib()
+    dims = (ctypes.c_int64 * 3)(10, 1, 1)
+    st = hc.HcStage()
+    st.kind = hc.HC_STAGE_Q
+    st.d_data = 16
+    st.n = 10
+    mo = hc.HcMultiOut()
+    mo.out_dtype = hc.HC_F32
+    ws = ctypes.c_void_p(16)
+    assert L.hc_op_multi(ctypes.byref(st), 1e-3, 1, dims, None, ws, L.hc_workspace_bytes(), None) == hc.HC_ERR_INVALID_ARG
+    mo.out_dtype = hc.HC_I64
+    assert L.hc_op_multi(ctypes.byref(st), 1e-3, 1, dims, ctypes.byref(mo), ws, L.hc_workspace_bytes(),
+                         None) == hc.HC_ERR_INVALID_ARG
+    mo.out_dtype = hc.HC_F32
+    mo.d_derivative[1] = 16  # axis 1 of a 1-D field
+    assert L.hc_op_multi(ctypes.byref(st), 1e-3, 1, dims, ctypes.byref(mo), ws, L.hc_workspace_bytes(),
+                         None) == hc.HC_ERR_INVALID_ARG
+    mo.d_derivative[1] = None
+    mo.d_laplacian = 20  # unaligned
+    assert L.hc_op_multi(ctypes.byref(st), 1e-3, 1, dims, ctypes.byref(mo), ws, L.hc_workspace_bytes(),
+                         None) == hc.HC_ERR_INVALID_ARG
