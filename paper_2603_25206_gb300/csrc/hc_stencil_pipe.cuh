@@ -34,7 +34,12 @@ namespace hc {
 constexpr int kWorkers = kThreads - 32;
 constexpr int kSlots = 4;
 constexpr int kWorkerWarps = kWorkers / 32;
-constexpr int kSegCost = 4;  // decoding one 32-code segment ~ this many output items
+// Estimated thread instructions per decoded code and per output point (from
+// ncu instruction counts of the kernels): decoding costs about 25 per code,
+// a point about as much for one operation and about 100 for all of them.
+constexpr int kDecodeCost = 25;
+constexpr int kPointCost = 25;
+constexpr int kPointCostMulti = 100;
 
 
 struct PGeo {
@@ -379,7 +384,7 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
     } else {
       // Split the 7 worker warps between decoding slab k and computing the
       // planes that are ready, in proportion to the estimated work (a segment
-      // costs about kSegCost items); a warp has one role, so no divergence.
+      // kDecodeCost / kPointCost above); a warp has one role, so no divergence.
       const int ww = warp - 1;
       const int64_t ready = zs + k - 1;  // last slab decoded in an earlier step
       int64_t zc1 = znext;
@@ -387,14 +392,16 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
       const int nplanes = (int)(zc1 - znext);
       const int nseg_k = k < nslab ? slab_desc(s, g, zs + k, ylo, yhi).nblk : 0;
       const int items = (int)(y1 - y0) * g.nq;
-      const int dec_cost = kSegCost * nseg_k, comp_cost = nplanes * items;
+      const long long dec_cost = (long long)kDecodeCost * 32 * nseg_k;
+      const long long comp_cost = (long long)(OP == ST_MULTI ? kPointCostMulti : kPointCost) * V * nplanes * items;
       int ndw = kWorkerWarps;
       if (comp_cost == 0)
         ndw = kWorkerWarps;
       else if (dec_cost == 0)
         ndw = 0;
       else
-        ndw = min(kWorkerWarps - 1, max(1, (kWorkerWarps * dec_cost + (dec_cost + comp_cost) / 2) / (dec_cost + comp_cost)));
+        ndw = min(kWorkerWarps - 1,
+                  max(1, (int)((kWorkerWarps * dec_cost + (dec_cost + comp_cost) / 2) / (dec_cost + comp_cost))));
       const bool decoder = ww < ndw;
       const int wt = decoder ? ww * 32 + lane : (ww - ndw) * 32 + lane;
       const int wstride = decoder ? ndw * 32 : (kWorkerWarps - ndw) * 32;
