@@ -56,6 +56,11 @@ def lib():
         L.orc_compress_bound.restype = i64
         L.orc_compress.argtypes = [vp, i32, i32, vp, dbl, i32, i32, vp, i64, P(i64), P(dbl)]
         L.orc_compress_codes.argtypes = [vp, i32, i32, vp, dbl, dbl, i32, i32, vp, i64, P(i64)]
+        L.orc_compress_pred.argtypes = [vp, i32, i32, vp, dbl, i32, i32, i32, vp, i64, P(i64), P(dbl)]
+        L.orc_compress_codes_pred.argtypes = [vp, i32, i32, vp, dbl, dbl, i32, i32, i32, vp, i64, P(i64)]
+        L.orc_mean_m_sum.argtypes = [vp, i64, i32, i64, P(i64)]
+        L.orc_mean_p_sum_x.argtypes = [vp, vp, i64, i32, P(i64)]
+        L.orc_std_p_x.argtypes = [vp, vp, i64, i32, dbl, P(i64), P(ctypes.c_uint64), P(ctypes.c_uint64), P(dbl)]
         L.orc_read_header.argtypes = [vp, i64, vp, vp]
         for name in ("orc_decode_p", "orc_decode_q", "orc_decode_m", "orc_decode_f"):
             getattr(L, name).argtypes = [vp, i64, vp]
@@ -73,7 +78,9 @@ def lib():
         for f in (L.orc_eps, L.orc_quantize, L.orc_compress, L.orc_compress_codes, L.orc_read_header,
                   L.orc_decode_p, L.orc_decode_q, L.orc_decode_m, L.orc_decode_f, L.orc_dequantize,
                   L.orc_sums_q, L.orc_mean_p_sum, L.orc_var_p_sums, L.orc_finalize, L.orc_stats_f,
-                  L.orc_deriv_q, L.orc_lap_q, L.orc_stencil_q, L.orc_stencil_f, L.orc_stencil_at):
+                  L.orc_deriv_q, L.orc_lap_q, L.orc_stencil_q, L.orc_stencil_f, L.orc_stencil_at,
+                  L.orc_compress_pred, L.orc_compress_codes_pred, L.orc_mean_m_sum, L.orc_mean_p_sum_x,
+                  L.orc_std_p_x):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -121,8 +128,9 @@ def compress_bound(n: int, S: int) -> int:
     return int(lib().orc_compress_bound(n, S))
 
 
-def compress(x: np.ndarray, eb: float, rel: bool = True, S: int = 32):
-    """Algorithm 1 on a float32/float64 array -> (stream bytes as uint8 array, eps)."""
+def compress(x: np.ndarray, eb: float, rel: bool = True, S: int = 32, pred: int = 0):
+    """Algorithm 1 on a float32/float64 array -> (stream bytes as uint8 array, eps).
+    pred 0: delta inside each block (HSZp, block heads); 1: block means (HSZx)."""
     x = np.ascontiguousarray(x)
     d = np.array(x.shape, np.int64)
     cap = compress_bound(x.size, S)
@@ -131,12 +139,12 @@ def compress(x: np.ndarray, eb: float, rel: bool = True, S: int = 32):
     out = np.zeros(cap, np.uint8)
     nbytes = ctypes.c_int64()
     eps = ctypes.c_double()
-    _check(lib().orc_compress(_ptr(x), _dtype_code(x), x.ndim, _ptr(d), eb, int(rel), S, _ptr(out),
-                              cap, ctypes.byref(nbytes), ctypes.byref(eps)), "compress")
+    _check(lib().orc_compress_pred(_ptr(x), _dtype_code(x), x.ndim, _ptr(d), eb, int(rel), S, pred, _ptr(out),
+                                   cap, ctypes.byref(nbytes), ctypes.byref(eps)), "compress")
     return out[: nbytes.value].copy(), eps.value
 
 
-def compress_codes(q: np.ndarray, eps: float, S: int = 32, dtype=np.float32, eb=None, rel=False):
+def compress_codes(q: np.ndarray, eps: float, S: int = 32, dtype=np.float32, eb=None, rel=False, pred: int = 0):
     """Encode given integer codes (the steps of Algorithm 1 after quantization)."""
     q = np.ascontiguousarray(q, dtype=np.int32)
     d = np.array(q.shape, np.int64)
@@ -144,18 +152,19 @@ def compress_codes(q: np.ndarray, eps: float, S: int = 32, dtype=np.float32, eb=
     out = np.zeros(cap, np.uint8)
     nbytes = ctypes.c_int64()
     code = 0 if np.dtype(dtype) == np.float32 else 1
-    _check(lib().orc_compress_codes(_ptr(q), code, q.ndim, _ptr(d), eps, eps if eb is None else eb,
-                                    int(rel), S, _ptr(out), cap, ctypes.byref(nbytes)), "compress_codes")
+    _check(lib().orc_compress_codes_pred(_ptr(q), code, q.ndim, _ptr(d), eps, eps if eb is None else eb,
+                                         int(rel), S, pred, _ptr(out), cap, ctypes.byref(nbytes)),
+           "compress_codes")
     return out[: nbytes.value].copy()
 
 
 HEADER_KEYS = ("dtype", "ndim", "n0", "n1", "n2", "S", "G", "eb_mode", "qmax", "N", "nb", "nchunks",
-               "payload_words", "total_bytes", "wmax", "off_payload")
+               "payload_words", "total_bytes", "wmax", "off_payload", "pred")
 
 
 def read_header(stream: np.ndarray) -> dict:
     s = np.ascontiguousarray(stream, dtype=np.uint8)
-    ints = np.zeros(16, np.int64)
+    ints = np.zeros(17, np.int64)
     dbls = np.zeros(2, np.float64)
     _check(lib().orc_read_header(_ptr(s), s.size, _ptr(ints), _ptr(dbls)), "read_header")
     h = {k: int(v) for k, v in zip(HEADER_KEYS, ints)}
@@ -217,6 +226,34 @@ def var_p_sums(dp: np.ndarray, S: int):
     _check(lib().orc_var_p_sums(_ptr(dp), dp.size, S, ctypes.byref(s1), ctypes.byref(lo),
                                 ctypes.byref(hi)), "var_p_sums")
     return s1.value, (hi.value << 64) | lo.value
+
+
+def mean_m_sum(M: np.ndarray, S: int, n: int) -> int:
+    """Stage-1 sum of the HSZx block means weighted by the true block sizes (Eq. mean_m)."""
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    t = ctypes.c_int64()
+    _check(lib().orc_mean_m_sum(_ptr(M), M.size, S, n, ctypes.byref(t)), "mean_m_sum")
+    return t.value
+
+
+def mean_p_sum_x(dp: np.ndarray, M: np.ndarray, S: int) -> int:
+    """Stage-2 HSZx sum of q: sum p + M_b S_b."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    s1 = ctypes.c_int64()
+    _check(lib().orc_mean_p_sum_x(_ptr(dp), _ptr(M), dp.size, S, ctypes.byref(s1)), "mean_p_sum_x")
+    return s1.value
+
+
+def std_p_x(dp: np.ndarray, M: np.ndarray, S: int, eps: float):
+    """Stage-2 HSZx standard deviation about the integer mean mu~:
+    (mu~, exact sum (p + M_b - mu~)^2, sigma)."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    mt, lo, hi, sg = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().orc_std_p_x(_ptr(dp), _ptr(M), dp.size, S, eps, ctypes.byref(mt), ctypes.byref(lo),
+                             ctypes.byref(hi), ctypes.byref(sg)), "std_p_x")
+    return mt.value, (hi.value << 64) | lo.value, sg.value
 
 
 def finalize(n: int, s1: int, s2: int, eps: float):

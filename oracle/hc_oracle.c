@@ -21,7 +21,9 @@
  *    56 u32 eb mode (0 abs, 1 rel)     60 u32 max |q|
  *    64 i64 N  72 i64 nb  80 i64 nchunks  88 i64 payload words
  *    96 i64 off widths  104 i64 off heads  112 i64 off chunks
- *   120 i64 off payload 128 i64 total bytes  136 u32 max width; rest zero
+ *   120 i64 off payload 128 i64 total bytes  136 u32 max width
+ *   140 u32 predictor: 0 = delta inside the block (HSZp with SZp-style block
+ *       heads), 1 = block mean (HSZx); rest zero
  *   widths u8[nb] at 256; heads i32[nb], chunk index u64[nchunks + 1] and
  *   payload u32 words each start on the next 16-byte boundary; the stream
  *   ends 16..31 zero bytes after the payload (total rounded to 16).
@@ -29,9 +31,12 @@
  *   payload words.  A block of width w > 0 holds ceil(S/32) sign words (bit
  *   k%32 of word k/32 set iff p_k < 0) followed by ceil(S*w/32) magnitude
  *   words in which |p_k| occupies bits [k*w, (k+1)*w) of the word sequence
- *   read least-significant bit first.  p_0 = 0 (the head is metadata) and the
- *   padding slots of a short last block are 0.  A block of width 0 has no
- *   payload words.
+ *   read least-significant bit first.  Predictor 0: heads[b] is the block's
+ *   first code, p_k = q_k - q_{k-1} and p_0 = 0.  Predictor 1: heads[b] is
+ *   the block mean M_b (the integer nearest to the block's code sum over its
+ *   true size, ties toward zero) and p_k = q_k - M_b for every k.  The padding
+ *   slots of a short last block are 0.  A block of width 0 has no payload
+ *   words.
  *
  * Integers: codes q are int32 with |q| < 2^30; sums of q are int64; sums of
  * q^2 and the variance numerator are 128-bit (__int128).  Floating point is
@@ -121,6 +126,7 @@ typedef struct {
   int64_t N, nb, nchunks, payload_words;
   int64_t off_widths, off_heads, off_chunks, off_payload, total_bytes;
   int wmax;
+  int pred; /* 0 delta inside the block (HSZp), 1 block mean (HSZx) */
 } orc_header;
 
 static int64_t chunk_blocks(int S) {
@@ -219,10 +225,21 @@ int64_t orc_compress_bound(int64_t n, int S) {
 /* "Encoding": per block the signs are gathered first, then the         */
 /* magnitudes in order at the width set by the largest magnitude.       */
 /* ------------------------------------------------------------------ */
-int orc_compress_codes(const int32_t *q, int dtype, int ndim, const int64_t *dims_in, double eps,
-                       double eb, int eb_mode, int S, uint8_t *out, int64_t cap,
-                       int64_t *out_bytes) {
+/* Integer mean of HSZx: the integer nearest to a / d (d > 0), ties toward
+ * zero.  Reading: Section V-D bounds the rounding error of the block means by
+ * 1/2 (so: nearest), and the worked example of Section IV rounds 22/4 = 5.5
+ * to 5 (so: the tie goes toward zero). */
+static int64_t nearest_ratio(int64_t a, int64_t d) {
+  i128 m = a < 0 ? -(i128)a : (i128)a;
+  i128 r = (2 * m + d - 1) / (2 * (i128)d);
+  return (int64_t)(a < 0 ? -r : r);
+}
+
+int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t *dims_in, double eps,
+                            double eb, int eb_mode, int S, int pred, uint8_t *out, int64_t cap,
+                            int64_t *out_bytes) {
   if (ndim < 1 || ndim > 3 || S < 1 || S > ORC_MAX_S || !(eps > 0.0)) return ORC_ERR_INVALID_ARG;
+  if (pred != 0 && pred != 1) return ORC_ERR_INVALID_ARG;
   if (dtype != 0 && dtype != 1) return ORC_ERR_INVALID_ARG;
   orc_header h;
   memset(&h, 0, sizeof h);
@@ -252,21 +269,39 @@ int orc_compress_codes(const int32_t *q, int dtype, int ndim, const int64_t *dim
     int64_t first = b * S;
     int64_t Sb = (first + S <= n) ? S : n - first; /* true size of the last block */
     if (b % h.G == 0) put_u64(out, h.off_chunks + 8 * (b / h.G), (uint64_t)word);
-    /* metadata: the first code of the block */
-    int32_t head = q[first];
-    put_u32(out, h.off_heads + 4 * b, (uint32_t)head);
-    /* decorrelation inside the block: p_k = q_k - q_{k-1}, p_0 = 0; the
-     * padding slots k >= Sb of a short last block are zero */
+    int32_t head;
     uint32_t maxmag = 0;
-    for (int64_t k = 0; k < S; k++) {
-      if (k == 0 || k >= Sb) {
-        p[k] = 0;
-      } else {
-        p[k] = q[first + k] - q[first + k - 1];
-        uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
-        if (m > maxmag) maxmag = m;
+    if (pred == 0) {
+      /* metadata: the first code of the block; decorrelation inside the
+       * block: p_k = q_k - q_{k-1}, p_0 = 0 */
+      head = q[first];
+      for (int64_t k = 0; k < S; k++) {
+        if (k == 0 || k >= Sb) {
+          p[k] = 0;
+        } else {
+          p[k] = q[first + k] - q[first + k - 1];
+          uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
+          if (m > maxmag) maxmag = m;
+        }
+      }
+    } else {
+      /* HSZx (Section IV, "HSZx"): metadata M_b = mean of the block's codes
+       * as an integer; decorrelation p_k = q_k - M_b */
+      int64_t sum = 0;
+      for (int64_t k = 0; k < Sb; k++) sum += q[first + k];
+      head = (int32_t)nearest_ratio(sum, Sb);
+      for (int64_t k = 0; k < S; k++) {
+        if (k >= Sb) {
+          p[k] = 0;
+        } else {
+          p[k] = q[first + k] - head;
+          uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
+          if (m > maxmag) maxmag = m;
+        }
       }
     }
+    put_u32(out, h.off_heads + 4 * b, (uint32_t)head);
+    /* the padding slots k >= Sb of a short last block are zero */
     for (int64_t k = 0; k < Sb; k++) {
       int64_t a = q[first + k] < 0 ? -(int64_t)q[first + k] : q[first + k];
       if (a > qmax) qmax = a;
@@ -332,12 +367,19 @@ int orc_compress_codes(const int32_t *q, int dtype, int ndim, const int64_t *dim
   put_u64(out, 120, (uint64_t)h.off_payload);
   put_u64(out, 128, (uint64_t)h.total_bytes);
   put_u32(out, 136, (uint32_t)wmax);
+  put_u32(out, 140, (uint32_t)pred);
   *out_bytes = h.total_bytes;
   return ORC_OK;
 }
 
-int orc_compress(const void *x, int dtype, int ndim, const int64_t *dims, double eb, int eb_mode,
-                 int S, uint8_t *out, int64_t cap, int64_t *out_bytes, double *eps_out) {
+int orc_compress_codes(const int32_t *q, int dtype, int ndim, const int64_t *dims_in, double eps,
+                       double eb, int eb_mode, int S, uint8_t *out, int64_t cap,
+                       int64_t *out_bytes) {
+  return orc_compress_codes_pred(q, dtype, ndim, dims_in, eps, eb, eb_mode, S, 0, out, cap, out_bytes);
+}
+
+int orc_compress_pred(const void *x, int dtype, int ndim, const int64_t *dims, double eb, int eb_mode,
+                      int S, int pred, uint8_t *out, int64_t cap, int64_t *out_bytes, double *eps_out) {
   if (ndim < 1 || ndim > 3) return ORC_ERR_INVALID_ARG;
   int64_t n = 1;
   for (int a = 0; a < ndim; a++) {
@@ -350,10 +392,15 @@ int orc_compress(const void *x, int dtype, int ndim, const int64_t *dims, double
   int32_t *q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
   if (!q) return ORC_ERR_INVALID_ARG;
   st = orc_quantize(x, dtype, n, eps, q);
-  if (!st) st = orc_compress_codes(q, dtype, ndim, dims, eps, eb, eb_mode, S, out, cap, out_bytes);
+  if (!st) st = orc_compress_codes_pred(q, dtype, ndim, dims, eps, eb, eb_mode, S, pred, out, cap, out_bytes);
   free(q);
   if (eps_out) *eps_out = eps;
   return st;
+}
+
+int orc_compress(const void *x, int dtype, int ndim, const int64_t *dims, double eb, int eb_mode,
+                 int S, uint8_t *out, int64_t cap, int64_t *out_bytes, double *eps_out) {
+  return orc_compress_pred(x, dtype, ndim, dims, eb, eb_mode, S, 0, out, cap, out_bytes, eps_out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -392,13 +439,15 @@ static int parse(const uint8_t *s, int64_t bytes, orc_header *h) {
   h->payload_words = (int64_t)get_u64(s, 88);
   h->total_bytes = (int64_t)get_u64(s, 128);
   h->wmax = (int)get_u32(s, 136);
+  h->pred = (int)get_u32(s, 140);
+  if (h->pred != 0 && h->pred != 1) return ORC_ERR_CORRUPT;
   if (h->total_bytes != align16(h->off_payload + 4 * h->payload_words + 16)) return ORC_ERR_CORRUPT;
   if (h->total_bytes > bytes) return ORC_ERR_CORRUPT;
   if (!(h->eps > 0.0)) return ORC_ERR_CORRUPT;
   return ORC_OK;
 }
 
-/* exported view of the header: 16 int64 fields + 2 doubles */
+/* exported view of the header: 17 int64 fields + 2 doubles */
 int orc_read_header(const uint8_t *s, int64_t bytes, int64_t *ints, double *dbls) {
   orc_header h;
   int st = parse(s, bytes, &h);
@@ -419,6 +468,7 @@ int orc_read_header(const uint8_t *s, int64_t bytes, int64_t *ints, double *dbls
   ints[13] = h.total_bytes;
   ints[14] = h.wmax;
   ints[15] = h.off_payload;
+  ints[16] = h.pred;
   dbls[0] = h.eps;
   dbls[1] = h.eb;
   return ORC_OK;
@@ -457,7 +507,7 @@ static int decode_block(const uint8_t *s, const orc_header *h, int64_t b, int64_
 /* Walk all blocks; per block call back with (b, first index, Sb, head, p).
  * The payload word offset of each block is the running sum of block sizes,
  * checked against the stored chunk index at every chunk start. */
-typedef void (*block_fn)(void *ctx, int64_t b, int64_t first, int64_t Sb, int32_t head,
+typedef void (*block_fn)(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int32_t head,
                          const int32_t *p);
 
 static int walk(const uint8_t *s, int64_t bytes, block_fn fn, void *ctx, orc_header *hout) {
@@ -480,7 +530,7 @@ static int walk(const uint8_t *s, int64_t bytes, block_fn fn, void *ctx, orc_hea
     int64_t first = b * h.S;
     int64_t Sb = (first + h.S <= h.N) ? h.S : h.N - first;
     int32_t head = (int32_t)get_u32(s, h.off_heads + 4 * b);
-    fn(ctx, b, first, Sb, head, p);
+    fn(ctx, h.pred, b, first, Sb, head, p);
     word += block_words(h.S, w);
   }
   free(p);
@@ -491,13 +541,19 @@ static int walk(const uint8_t *s, int64_t bytes, block_fn fn, void *ctx, orc_hea
   return ORC_OK;
 }
 
-/* Stage 2 (D_p).  Reading: the materialized D_p carries the block's head in
- * the slot of its first element, so that q is the inclusive prefix sum of
- * D_p inside every block (the form q_i = sum_{t<=i} p_t of Section V-A). */
-static void put_p(void *ctx, int64_t b, int64_t first, int64_t Sb, int32_t head,
+/* Stage 2 (D_p).  Predictor 0 -- reading: the materialized D_p carries the
+ * block's head in the slot of its first element, so that q is the inclusive
+ * prefix sum of D_p inside every block (the form q_i = sum_{t<=i} p_t of
+ * Section V-A).  Predictor 1: D_p = q - M_b in every slot (Section IV,
+ * "HSZx"). */
+static void put_p(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int32_t head,
                   const int32_t *p) {
   (void)b;
   int32_t *dp = (int32_t *)ctx;
+  if (pred == 1) {
+    for (int64_t k = 0; k < Sb; k++) dp[first + k] = p[k];
+    return;
+  }
   dp[first] = head;
   for (int64_t k = 1; k < Sb; k++) dp[first + k] = p[k];
 }
@@ -505,11 +561,16 @@ int orc_decode_p(const uint8_t *s, int64_t bytes, int32_t *dp) {
   return walk(s, bytes, put_p, dp, NULL);
 }
 
-/* Stage 3 (D_q): recorrelate q_k = q_{k-1} + p_k, starting from the head. */
-static void put_q(void *ctx, int64_t b, int64_t first, int64_t Sb, int32_t head,
+/* Stage 3 (D_q).  Predictor 0: recorrelate q_k = q_{k-1} + p_k from the
+ * head.  Predictor 1: q_k = M_b + p_k. */
+static void put_q(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int32_t head,
                   const int32_t *p) {
   (void)b;
   int32_t *dq = (int32_t *)ctx;
+  if (pred == 1) {
+    for (int64_t k = 0; k < Sb; k++) dq[first + k] = head + p[k];
+    return;
+  }
   int32_t q = head;
   dq[first] = q;
   for (int64_t k = 1; k < Sb; k++) {
@@ -521,9 +582,10 @@ int orc_decode_q(const uint8_t *s, int64_t bytes, int32_t *dq) {
   return walk(s, bytes, put_q, dq, NULL);
 }
 
-/* Stage 1 (D_m): the block metadata (heads) and widths. */
-static void put_m(void *ctx, int64_t b, int64_t first, int64_t Sb, int32_t head,
+/* Stage 1 (D_m): the block metadata (heads, or the block means of HSZx). */
+static void put_m(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int32_t head,
                   const int32_t *p) {
+  (void)pred;
   (void)first;
   (void)Sb;
   (void)p;
@@ -617,6 +679,59 @@ int orc_var_p_sums(const int32_t *dp, int64_t n, int S, int64_t *s1, uint64_t *s
   *s1 = a;
   *s2_lo = (uint64_t)b;
   *s2_hi = (uint64_t)(b >> 64);
+  return ORC_OK;
+}
+
+/* Stage 1 mean of HSZx (Eq. mean_m): T = sum_b M_b * S_b from the block
+ * means alone; mu = (T / N) * 2 eps.  S_b is the true size of block b. */
+int orc_mean_m_sum(const int32_t *M, int64_t nb, int S, int64_t n, int64_t *T) {
+  int64_t t = 0;
+  for (int64_t b = 0; b < nb; b++) {
+    int64_t first = b * S;
+    int64_t Sb = (first + S <= n) ? S : n - first;
+    t += (int64_t)M[b] * Sb;
+  }
+  *T = t;
+  return ORC_OK;
+}
+
+/* Stage 2 mean of HSZx (Section V-A, "Operation with D_p"): the block sum of
+ * q is sum_{p in block} p + M_b S_b. */
+int orc_mean_p_sum_x(const int32_t *dp, const int32_t *M, int64_t n, int S, int64_t *s1) {
+  int64_t total = 0;
+  for (int64_t first = 0, b = 0; first < n; first += S, b++) {
+    int64_t Sb = (first + S <= n) ? S : n - first;
+    for (int64_t k = 0; k < Sb; k++) total += dp[first + k];
+    total += (int64_t)M[b] * Sb;
+  }
+  *s1 = total;
+  return ORC_OK;
+}
+
+/* Stage 2 standard deviation of HSZx (Section V-A): with the integer mean
+ * mu~ = round(T / N) (T as in orc_mean_m_sum; the same rounding as the block
+ * means: nearest, ties toward zero, in exact integer arithmetic), each
+ * deviation is split
+ * as (q - M_b) + (M_b - mu~) = p + M_b - mu~, and
+ *   sigma = sqrt(sum (p + M_b - mu~)^2 / (N - 1)) * 2 eps.
+ * Returns mu~, the exact 128-bit sum of squares and sigma (NaN for N = 1). */
+int orc_std_p_x(const int32_t *dp, const int32_t *M, int64_t n, int S, double eps, int64_t *mu_tilde,
+                uint64_t *ss_lo, uint64_t *ss_hi, double *sigma) {
+  int64_t nb = (n + S - 1) / S, T;
+  orc_mean_m_sum(M, nb, S, n, &T);
+  int64_t mt = nearest_ratio(T, n);
+  u128 ss = 0;
+  for (int64_t first = 0, b = 0; first < n; first += S, b++) {
+    int64_t Sb = (first + S <= n) ? S : n - first;
+    for (int64_t k = 0; k < Sb; k++) {
+      int64_t d = (int64_t)dp[first + k] + M[b] - mt;
+      ss += (u128)((i128)d * d);
+    }
+  }
+  *mu_tilde = mt;
+  *ss_lo = (uint64_t)ss;
+  *ss_hi = (uint64_t)(ss >> 64);
+  *sigma = n < 2 ? NAN : sqrt((double)ss / (double)(n - 1)) * (2.0 * eps);
   return ORC_OK;
 }
 

@@ -133,6 +133,7 @@ def _py_decode(stream):
     S = u32(32)
     N = u64(64)
     nb = u64(72)
+    pred = u32(140)
     ow, oh, oc, op = u64(96), u64(104), u64(112), u64(120)
     widths = s[ow:ow + nb].astype(np.int64)
     heads = s[oh:oh + 4 * nb].view("<i4").astype(np.int64)
@@ -147,7 +148,7 @@ def _py_decode(stream):
         first = b * S
         Sb = min(S, N - first)
         w = int(widths[b])
-        if w == 0:
+        if w == 0:  # every p is 0: q = head (delta) or q = M_b (block mean)
             q[first:first + Sb] = heads[b]
             continue
         base = int(offs[b]) * 32
@@ -156,8 +157,12 @@ def _py_decode(stream):
         mb = base + nsw * 32 + (k[:, None] * w + np.arange(w)[None, :])
         mag = (bits[mb] << np.arange(w, dtype=np.uint64)).sum(axis=1).astype(np.int64)
         p = np.where(sign == 1, -mag, mag)
-        assert p[0] == 0 and np.all(p[Sb:] == 0)
-        q[first:first + Sb] = heads[b] + np.cumsum(p[:Sb])
+        assert np.all(p[Sb:] == 0)
+        if pred == 1:  # block mean: q = M_b + p
+            q[first:first + Sb] = heads[b] + p[:Sb]
+        else:  # delta inside the block: q = head + prefix sum, p_0 = 0
+            assert p[0] == 0
+            q[first:first + Sb] = heads[b] + np.cumsum(p[:Sb])
     chunk_g = max(1, 4096 // S)
     chunks = s[oc:oc + 8 * (-(-nb // chunk_g) + 1)].view("<u8").astype(np.int64)
     np.testing.assert_array_equal(chunks, offs[::chunk_g].tolist() + ([offs[-1]] if nb % chunk_g else []))
@@ -415,3 +420,105 @@ def test_sampled_stencils_equal_whole_field(orc, rng):
     np.testing.assert_array_equal(num, orc.lap_q(q).reshape(-1)[idx])
     _, val = orc.stencil_at(q, orc.KIND_GRADMAG, eps, idx)
     np.testing.assert_array_equal(val, orc.stencil_q(q, orc.KIND_GRADMAG, eps).reshape(-1)[idx])
+
+
+# ------------------------------------------------------------ HSZx (block mean)
+def _nearest_tie_zero(a, d):
+    """Integer nearest to a / d, ties toward zero (Python integers)."""
+    f = Fraction(a, d)
+    r = math.floor(abs(f) + Fraction(1, 2))
+    if abs(f) - math.floor(abs(f)) == Fraction(1, 2):
+        r = math.floor(abs(f))
+    return r if a >= 0 else -r
+
+
+def test_hszx_worked_example(orc):
+    """Section IV's HSZx example: 2x2 blocks of the printed Y_q give the block
+    means M = 5, -1 and the printed Y_p; Section V-A's stage-2 standard
+    deviation about the integer mean round(16/8) = 2 is 2.000.  The two 2x2
+    blocks, taken in block order, are blocks of 4 consecutive codes."""
+    g = read_golden_table("worked_example.txt")
+    Yq = np.array([int(v) for v in g["Yq"]], np.int64).reshape(2, 4)
+    Yp = np.array([int(v) for v in g["Yp"]], np.int64).reshape(2, 4)
+    M = [int(v) for v in g["M"]]
+    blocks = lambda a: np.concatenate([a[:, 0:2].reshape(-1), a[:, 2:4].reshape(-1)])  # noqa: E731
+    qb = blocks(Yq).astype(np.int32)
+    s = orc.compress_codes(qb, 0.1, 4, np.float64, pred=1)
+    assert orc.read_header(s)["pred"] == 1
+    np.testing.assert_array_equal(orc.decode(s, "m"), M)
+    np.testing.assert_array_equal(orc.decode(s, "p"), blocks(Yp))
+    np.testing.assert_array_equal(orc.decode(s, "q"), qb)
+    dp = orc.decode(s, "p")
+    # stage 1 (Eq. mean_m) and stage 2 means
+    assert orc.mean_m_sum(np.array(M, np.int32), 4, 8) == 5 * 4 + (-1) * 4
+    assert orc.mean_p_sum_x(dp, np.array(M, np.int32), 4) == int(Yq.sum()) == 18
+    mt, ss, sigma = orc.std_p_x(dp, np.array(M, np.int32), 4, 0.1)
+    assert mt == 2 and ss == 700  # sum (q - 2)^2 over the printed codes
+    assert abs(sigma - 2.0) < 1e-15
+    assert f"{sigma:.3f}" == g["sigma_p_hszx"][0]
+
+
+def test_hszx_block_mean_rounding(orc):
+    """Block means: nearest integer, ties toward zero, over the true block size
+    (a short last block uses its own size)."""
+    q = np.array([-1, -1, -1, -2,   3, 3, 3, 4,   2, 3, 2, 3,   -2, -3, -2, -3,   1, 2], np.int32)
+    s = orc.compress_codes(q, 1.0, 4, np.float32, pred=1)
+    M = orc.decode(s, "m")
+    # -5/4 -> -1; 13/4 -> 3; 10/4 = 2.5 -> 2; -10/4 = -2.5 -> -2; 3/2 = 1.5 -> 1
+    np.testing.assert_array_equal(M, [-1, 3, 2, -2, 1])
+    for b, (lo, hi) in enumerate([(0, 4), (4, 8), (8, 12), (12, 16), (16, 18)]):
+        assert M[b] == _nearest_tie_zero(int(q[lo:hi].astype(np.int64).sum()), hi - lo)
+    np.testing.assert_array_equal(orc.decode(s, "p"), q - np.repeat(M, [4, 4, 4, 4, 2]))
+
+
+@pytest.mark.parametrize("S", SIZES_S)
+def test_hszx_roundtrip_and_independent_reader(orc, rng, S):
+    """HSZx streams: D_q is the codes exactly, the independent reader agrees,
+    M_b follows the rounding rule and the width is the bit length of
+    max |q - M_b|; encoding the decoded codes again is the identity."""
+    n = int(rng.integers(1, 700))
+    x = np.cumsum(rng.standard_normal(n)).astype(np.float32)
+    if n > 5:
+        x[rng.integers(0, n, 3)] += 50.0
+    s, eps = orc.compress(x, 1e-2, True, S, pred=1)
+    q_ref = orc.quantize(x, eps)
+    np.testing.assert_array_equal(orc.decode(s, "q"), q_ref)
+    q_py, widths = _py_decode(s)
+    np.testing.assert_array_equal(q_py, q_ref)
+    M = orc.decode(s, "m")
+    for b in range(widths.size):
+        blk = q_ref[b * S:(b + 1) * S].astype(np.int64)
+        assert M[b] == _nearest_tie_zero(int(blk.sum()), blk.size)
+        assert widths[b] == int(np.abs(blk - M[b]).max()).bit_length()
+    s2 = orc.compress_codes(q_ref, eps, S, np.float32, eb=1e-2, rel=True, pred=1)
+    assert bytes(s2) == bytes(s)
+    # the same codes under the delta predictor: same header except byte 140
+    s0, _ = orc.compress(x, 1e-2, True, S)
+    assert orc.read_header(s0)["pred"] == 0
+
+
+@pytest.mark.parametrize("S", [1, 4, 32, 100])
+def test_hszx_statistics_stage_forms(orc, rng, S):
+    """Stage 2 mean = exact sum q; stage 1 mean within eps of it (Section V-D:
+    |r_b| <= 1/2 per block); stage 2 sigma about mu~ equals the exact rational
+    value sum (q - mu~)^2 / (N - 1) and stays within the Section V-D bound
+    of the exact sample standard deviation."""
+    n = int(rng.integers(2, 3000))
+    x = (np.cumsum(rng.standard_normal(n)) * 3).astype(np.float64)
+    s, eps = orc.compress(x, 1e-3, True, S, pred=1)
+    q = orc.decode(s, "q").astype(np.int64)
+    dp = orc.decode(s, "p")
+    M = orc.decode(s, "m")
+    s1 = int(q.sum())
+    assert orc.mean_p_sum_x(dp, M, S) == s1
+    T = orc.mean_m_sum(M, S, n)
+    assert abs(Fraction(T, n) - Fraction(s1, n)) <= Fraction(1, 2)
+    mu1 = T / n * 2 * eps
+    assert abs(mu1 - s1 / n * 2 * eps) <= eps * (1 + 1e-12)
+    mt, ss, sigma = orc.std_p_x(dp, M, S, eps)
+    assert mt == _nearest_tie_zero(T, n)
+    assert ss == int(((q - mt) ** 2).sum())
+    assert abs(sigma - math.sqrt(ss / (n - 1)) * 2 * eps) <= 1e-12 * sigma + 1e-300
+    s2 = int((q * q).sum())
+    _, var, sd = orc.finalize(n, s1, s2, eps)
+    assert abs(sigma - sd) <= 2 * eps * (math.sqrt(n / (n - 1)) * 0.5 + 0.5) + 1e-12
