@@ -57,6 +57,11 @@ typedef enum {
 typedef enum { HC_F32 = 0, HC_F64 = 1, HC_I32 = 2, HC_I64 = 3 } hc_dtype;
 typedef enum { HC_OP_MEAN = 0, HC_OP_VARIANCE = 1, HC_OP_DERIVATIVE = 2, HC_OP_GRADMAG = 3, HC_OP_LAPLACIAN = 4 } hc_op;
 typedef enum { HC_EB_ABS = 0, HC_EB_REL = 1 } hc_eb_mode;
+/* Decorrelation inside a block (Section IV).  DELTA: the block's first code is
+ * metadata and p_k = q_k - q_{k-1} (HSZp with SZp-style block heads).  MEAN:
+ * the block mean M_b (nearest integer to the code sum over the block size,
+ * ties toward zero) is metadata and p_k = q_k - M_b (HSZx). */
+typedef enum { HC_PRED_DELTA = 0, HC_PRED_MEAN = 1 } hc_predictor;
 typedef enum {
   HC_STAGE_COMPRESSED = 0, /* the stream itself (operations fuse decoding in) */
   HC_STAGE_M = 1,          /* D_m: heads int32[nb] */
@@ -82,7 +87,7 @@ typedef struct hc_header {
   int64_t N, nb, nchunks, payload_words;
   int64_t off_widths, off_heads, off_chunks, off_payload, total_bytes;
   uint32_t wmax;     /* largest block width */
-  uint32_t reserved;
+  uint32_t pred;     /* hc_predictor the stream was written with */
 } hc_header;
 
 /* An input of an operation: the stream (fused decode + operation) or a
@@ -98,7 +103,7 @@ typedef struct hc_stage {
   int32_t S;             /* P: block size of the stream the array came from */
   int64_t n;             /* P / Q / F: element count */
   uint32_t qmax;         /* P / Q: an upper bound on |q|, 0 if unknown */
-  uint32_t reserved;
+  uint32_t pred;         /* M / P arrays: hc_predictor of the stream they came from */
 } hc_stage;
 
 /* Device-resident result of a statistic.  Integer stages carry the exact
@@ -154,6 +159,17 @@ HC_API int hc_compress_codes(const int32_t* d_q, int dtype, int ndim, const int6
                       int eb_mode, int S, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
                       size_t* out_bytes, hc_header* hdr_out, void* stream);
 
+/* hc_compress / hc_compress_codes with a choice of decorrelation
+ * (hc_predictor): HC_PRED_DELTA gives the same bytes as hc_compress,
+ * HC_PRED_MEAN writes an HSZx stream (block means as metadata, p = q - M_b;
+ * Section IV, "HSZx").  SYNC. */
+HC_API int hc_compress_ex(const void* d_x, int dtype, int ndim, const int64_t* dims, double eb, int eb_mode, int S,
+                          int predictor, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
+                          hc_header* hdr_out, void* stream);
+HC_API int hc_compress_codes_ex(const int32_t* d_q, int dtype, int ndim, const int64_t* dims, double eps, double eb,
+                                int eb_mode, int S, int predictor, void* d_stream, size_t cap, void* d_ws,
+                                size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, void* stream);
+
 /* Copy the 256-byte header of a device-resident stream to the host and
  * validate it (magic, version, shape, section offsets, total size against
  * `bytes`).  SYNC. */
@@ -161,8 +177,9 @@ HC_API int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out
 
 /* ---------------------------------------------------------- decompression */
 /* D_i ... D_1 (Algorithm 2): decode the whole stream to stage `kind`:
- *   HC_STAGE_M -> int32 heads[nb]; HC_STAGE_P -> int32[N] (head in each
- *   block's first slot, so q is the in-block prefix sum); HC_STAGE_Q ->
+ *   HC_STAGE_M -> int32 heads[nb] (HC_PRED_MEAN: the block means);
+ *   HC_STAGE_P -> int32[N] (HC_PRED_DELTA: head in each block's first slot,
+ *   so q is the in-block prefix sum; HC_PRED_MEAN: p = q - M_b); HC_STAGE_Q ->
  *   int32[N]; HC_STAGE_F -> out_dtype HC_F32 ((float)q * (float)(2 eps)) or
  *   HC_F64 ((double)q * 2 eps).
  * d_out holds hc_stage_bytes(hdr, kind) bytes (8 per element for F64).
@@ -174,12 +191,25 @@ HC_API int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, in
 HC_API int hc_workspace_status(void* d_ws, void* stream);
 
 /* ------------------------------------------------------------- operations */
-/* Statistics (Section V-A).  `in`: the stream (fused; level P uses the
- * block-weighted sum sum_i (S_b - i + 1) p_i without a prefix sum, level Q
- * sums q) or a materialized P, Q or F array.  eps and dims must match the
- * stream header for the fused form.  d_out: one hc_scalar in device memory.
- * hc_op_mean fills mean (and s1); hc_op_variance and hc_op_std fill every
- * field.  ASYNC. */
+/* Statistics (Section V-A).  `in`: the stream (fused) at a level, or a
+ * materialized M, P, Q or F array.  eps and dims must match the stream header
+ * for the fused form.  d_out: one hc_scalar in device memory.  hc_op_mean
+ * fills mean (and s1); hc_op_variance and hc_op_std fill every field.
+ *   level Q: exact s1 = sum q, s2 = sum q^2, Eq. var_q.
+ *   level P, HC_PRED_DELTA: the mean from the block-weighted sum
+ *     sum_i (S_b - i + 1) p_i (no prefix sum); the variance through the eta
+ *     accumulator (exact, as level Q).
+ *   level P, HC_PRED_MEAN: the mean from sum p + M_b S_b (exact); the
+ *     variance of Section V-A about the integer mean mu~ = round(T / N),
+ *     T = sum_b M_b S_b (nearest, ties toward zero):
+ *     variance = sum (p + M_b - mu~)^2 / (N - 1) * (2 eps)^2, std its root;
+ *     s1 = sum q exact and s2 = sum (q - mu~)^2 exact; exact = 0 because
+ *     this variance is the paper's approximation, not Eq. var_q.
+ *   level M (HC_PRED_MEAN streams, or an M array with pred = HC_PRED_MEAN,
+ *     S and n set): the mean of Eq. mean_m, (T / N) 2 eps, from the block
+ *     means alone; s1 = T, exact = 0; mean only (the variance needs the codes).
+ *     HC_PRED_DELTA heads support no statistic (HC_ERR_UNSUPPORTED).
+ * ASYNC. */
 HC_API int hc_op_mean(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
                size_t ws_bytes, void* stream);
 HC_API int hc_op_variance(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,

@@ -137,6 +137,7 @@ int check_header(const hc_header& h) {
     return fail(HC_ERR_CORRUPT, "payload size and total size disagree");
   if ((size_t)h.total_bytes > L.bound) return fail(HC_ERR_CORRUPT, "payload larger than any valid stream");
   if (h.wmax > 31) return fail(HC_ERR_CORRUPT, "max width above 31");
+  if (h.pred != HC_PRED_DELTA && h.pred != HC_PRED_MEAN) return fail(HC_ERR_CORRUPT, "unknown predictor");
   if (!(h.eps > 0.0) || !std::isfinite(h.eps)) return fail(HC_ERR_CORRUPT, "bad eps");
   if (h.qmax >= (1u << 30)) return fail(HC_ERR_CORRUPT, "max |q| out of range");
   return HC_OK;
@@ -172,6 +173,7 @@ int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStr
   h.off_payload = (int64_t)le(b, 120, 8);
   h.total_bytes = (int64_t)le(b, 128, 8);
   h.wmax = (uint32_t)le(b, 136, 4);
+  h.pred = (uint32_t)le(b, 140, 4);
   int rc = check_header(h);
   if (rc) return rc;
   if ((size_t)h.total_bytes > bytes) return fail(HC_ERR_CORRUPT, "stream truncated");
@@ -202,15 +204,19 @@ static int check_op(const hc_stage* in, double eps, int ndim, const int64_t* dim
     if (h->ndim != ndim || h->eps != eps) return fail(HC_ERR_INVALID_ARG, "eps / ndim differ from the stream header");
     for (int a = 0; a < 3; ++a)
       if (h->dims[a] != dims3[a]) return fail(HC_ERR_INVALID_ARG, "dims differ from the stream header");
-    if (in->level != HC_STAGE_P && in->level != HC_STAGE_Q)
-      return fail(HC_ERR_INVALID_ARG, "fused level must be HC_STAGE_P or HC_STAGE_Q");
+    if (in->level != HC_STAGE_M && in->level != HC_STAGE_P && in->level != HC_STAGE_Q)
+      return fail(HC_ERR_INVALID_ARG, "fused level must be HC_STAGE_M, HC_STAGE_P or HC_STAGE_Q");
     return HC_OK;
   }
   if (in->n != L.N) return fail(HC_ERR_INVALID_ARG, "stage length differs from prod(dims)");
-  if (in->kind == HC_STAGE_P && (in->S < 1 || in->S > kMaxS)) return fail(HC_ERR_INVALID_ARG, "P input needs S");
+  if ((in->kind == HC_STAGE_P || in->kind == HC_STAGE_M) && (in->S < 1 || in->S > kMaxS))
+    return fail(HC_ERR_INVALID_ARG, "M / P input needs S");
   if (in->kind == HC_STAGE_F && in->dtype != HC_F32 && in->dtype != HC_F64)
     return fail(HC_ERR_INVALID_ARG, "F input dtype");
-  if (in->kind == HC_STAGE_M) return fail(HC_ERR_UNSUPPORTED, "HSZp-style metadata supports no operation (Section V)");
+  if (in->kind == HC_STAGE_M && in->pred != HC_PRED_MEAN)
+    return fail(HC_ERR_UNSUPPORTED, "HSZp-style metadata supports no operation (Section V)");
+  if (in->kind == HC_STAGE_P && in->pred == HC_PRED_MEAN)
+    return fail(HC_ERR_UNSUPPORTED, "a block-mean D_p array needs its block means: operate on the stream");
   if (in->kind < HC_STAGE_M || in->kind > HC_STAGE_F) return fail(HC_ERR_INVALID_ARG, "unknown stage kind");
   return HC_OK;
 }
@@ -275,19 +281,33 @@ size_t hc_stage_bytes(const hc_header* hdr, int kind) {
   }
 }
 
+int hc_compress_ex(const void* d_x, int dtype, int ndim, const int64_t* dims, double eb, int eb_mode, int S,
+                   int predictor, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
+                   hc_header* hdr_out, void* stream) {
+  return compress_impl(d_x, dtype == HC_F64 ? 1 : 0, dtype, ndim, dims, eb, 0.0, eb_mode, S, predictor, d_stream,
+                       cap, d_ws, ws_bytes, out_bytes, hdr_out, as_stream(stream));
+}
+
 int hc_compress(const void* d_x, int dtype, int ndim, const int64_t* dims, double eb, int eb_mode, int S,
                 void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out,
                 void* stream) {
-  return compress_impl(d_x, dtype == HC_F64 ? 1 : 0, dtype, ndim, dims, eb, 0.0, eb_mode, S, d_stream, cap, d_ws,
-                       ws_bytes, out_bytes, hdr_out, as_stream(stream));
+  return hc_compress_ex(d_x, dtype, ndim, dims, eb, eb_mode, S, HC_PRED_DELTA, d_stream, cap, d_ws, ws_bytes,
+                        out_bytes, hdr_out, stream);
+}
+
+int hc_compress_codes_ex(const int32_t* d_q, int dtype, int ndim, const int64_t* dims, double eps, double eb,
+                         int eb_mode, int S, int predictor, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
+                         size_t* out_bytes, hc_header* hdr_out, void* stream) {
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HC_ERR_INVALID_ARG, "eps must be positive and finite");
+  return compress_impl(d_q, 2, dtype, ndim, dims, eb, eps, eb_mode, S, predictor, d_stream, cap, d_ws, ws_bytes,
+                       out_bytes, hdr_out, as_stream(stream));
 }
 
 int hc_compress_codes(const int32_t* d_q, int dtype, int ndim, const int64_t* dims, double eps, double eb,
                       int eb_mode, int S, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
                       hc_header* hdr_out, void* stream) {
-  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HC_ERR_INVALID_ARG, "eps must be positive and finite");
-  return compress_impl(d_q, 2, dtype, ndim, dims, eb, eps, eb_mode, S, d_stream, cap, d_ws, ws_bytes, out_bytes,
-                       hdr_out, as_stream(stream));
+  return hc_compress_codes_ex(d_q, dtype, ndim, dims, eps, eb, eb_mode, S, HC_PRED_DELTA, d_stream, cap, d_ws,
+                              ws_bytes, out_bytes, hdr_out, stream);
 }
 
 int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out, void* stream) {
@@ -325,6 +345,12 @@ static int stats(const hc_stage* in, double eps, int ndim, const int64_t* dims, 
   if (!d_out) return fail(HC_ERR_INVALID_ARG, "null output");
   if (in->kind == HC_STAGE_COMPRESSED)
     return reduce_stream_impl(in->hdr, in->d_data, in->level, what, d_out, d_ws, as_stream(stream));
+  if (in->kind == HC_STAGE_M) {
+    // block means of an HSZx stream (Eq. mean_m): the mean only
+    if (what != RED_MEAN) return fail(HC_ERR_UNSUPPORTED, "stage 1 gives the mean only (Eq. mean_m)");
+    return mean_m_array_impl(reinterpret_cast<const int32_t*>(in->d_data), ceil_div(in->n, in->S), in->S, in->n, eps,
+                             d_out, d_ws, as_stream(stream));
+  }
   return reduce_array_impl(in, eps, what, d_out, d_ws, as_stream(stream));
 }
 
@@ -352,6 +378,7 @@ static int stencil(const hc_stage* in, double eps, int ndim, const int64_t* dims
   if (op == ST_DERIV && (axis < 0 || axis >= ndim)) return fail(HC_ERR_INVALID_ARG, "axis out of range");
   const int axis3 = axis + 3 - ndim;
   if (in->kind == HC_STAGE_COMPRESSED) {
+    if (in->level == HC_STAGE_M) return fail(HC_ERR_UNSUPPORTED, "stage 1 holds no point values to differentiate");
     if (in->level == HC_STAGE_P)
       return fail(HC_ERR_UNSUPPORTED,
                   "stage-2 differentiation is not defined for a 1-D block partition (Section V-B)");

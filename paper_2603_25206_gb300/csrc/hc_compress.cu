@@ -5,8 +5,9 @@
 //   k_ws_init      clear the workspace accumulators
 //   k_minmax       value range of the field (value-range-relative bound)
 //   k_eps          eps = eb or eb * (max - min)
-//   k_blocks       quantize, delta inside each block, block width, heads,
-//                  words per chunk, max |q|, max width          (one thread / block)
+//   k_blocks       quantize, block metadata (first code, or the block mean
+//                  for HSZx), block width, words per chunk, max |q|,
+//                  max width                                     (one thread / block)
 //   k_chunk_scan   exclusive scan of the words per chunk -> chunk index
 //   k_pack         sign words + w-bit magnitudes of every block  (one thread / block)
 //   k_header       header and the zero padding between sections
@@ -151,7 +152,17 @@ struct OutStream {
   uint32_t* payload;
   int64_t N, nb, nchunks;
   int S, G, nseg;
+  int pred;  // hc_predictor
 };
+
+// Integer block mean of HSZx: the integer nearest to a / d (d > 0), ties
+// toward zero (Section V-D bounds the rounding by 1/2; the worked example of
+// Section IV rounds 5.5 down to 5).
+__device__ __forceinline__ int32_t nearest_ratio(long long a, long long d) {
+  const unsigned long long m = (unsigned long long)(a < 0 ? -a : a);
+  const long long r = (long long)((2ull * m + (unsigned long long)d - 1ull) / (2ull * (unsigned long long)d));
+  return (int32_t)(a < 0 ? -r : r);
+}
 
 // One thread per block: codes, deltas, width, head; per-chunk word counts.
 template <class Src>
@@ -176,18 +187,37 @@ __global__ void __launch_bounds__(kThreads) k_blocks(Src src, OutStream o, CompW
     int32_t prev = 0, q;
     uint32_t maxmag = 0, qm = 0;
     bool ok = true;
-    for (int64_t k = 0; k < Sb; ++k) {
-      ok &= quantize_at(src, first + k, two_eps, q);
-      if (k == 0) {
-        o.heads[b] = q;
-      } else {
-        const int32_t p = q - prev;
+    if (o.pred == HC_PRED_MEAN) {
+      // HSZx: M_b from the block's code sum, then the widest |q - M_b|
+      long long sum = 0;
+      for (int64_t k = 0; k < Sb; ++k) {
+        ok &= quantize_at(src, first + k, two_eps, q);
+        sum += q;
+        const uint32_t aq = (uint32_t)(q < 0 ? -q : q);
+        qm = aq > qm ? aq : qm;
+      }
+      const int32_t mb = ok ? nearest_ratio(sum, Sb) : 0;
+      o.heads[b] = mb;
+      for (int64_t k = 0; k < Sb && ok; ++k) {
+        quantize_at(src, first + k, two_eps, q);
+        const int32_t p = q - mb;
         const uint32_t m = (uint32_t)(p < 0 ? -p : p);
         maxmag = m > maxmag ? m : maxmag;
       }
-      const uint32_t aq = (uint32_t)(q < 0 ? -q : q);
-      qm = aq > qm ? aq : qm;
-      prev = q;
+    } else {
+      for (int64_t k = 0; k < Sb; ++k) {
+        ok &= quantize_at(src, first + k, two_eps, q);
+        if (k == 0) {
+          o.heads[b] = q;
+        } else {
+          const int32_t p = q - prev;
+          const uint32_t m = (uint32_t)(p < 0 ? -p : p);
+          maxmag = m > maxmag ? m : maxmag;
+        }
+        const uint32_t aq = (uint32_t)(q < 0 ? -q : q);
+        qm = aq > qm ? aq : qm;
+        prev = q;
+      }
     }
     const uint32_t w = maxmag ? 32u - (uint32_t)__clz(maxmag) : 0u;
     o.widths[b] = (uint8_t)w;
@@ -277,11 +307,13 @@ __global__ void __launch_bounds__(kThreads) k_pack(Src src, OutStream o, CompWs*
     unsigned long long acc = 0;
     uint32_t nbits = 0;
     int32_t prev = 0, q;
+    const bool mean_pred = o.pred == HC_PRED_MEAN;
+    const int32_t mb = mean_pred ? o.heads[b] : 0;
     for (int64_t k = 0; k < o.S; ++k) {
       int32_t p = 0;
       if (k < Sb) {
         quantize_at(src, first + k, two_eps, q);
-        p = (k == 0) ? 0 : q - prev;
+        p = mean_pred ? q - mb : ((k == 0) ? 0 : q - prev);
         prev = q;
       }
       if (p < 0) sign |= 1u << (k & 31);
@@ -303,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) k_pack(Src src, OutStream o, CompWs*
 }
 
 struct HeaderArgs {
-  int dtype, ndim, S, G, eb_mode;
+  int dtype, ndim, S, G, eb_mode, pred;
   int64_t dims[3];
   double eb;
   int64_t N, nb, nchunks, off_widths, off_heads, off_chunks, off_payload;
@@ -340,6 +372,7 @@ __global__ void k_header(HeaderArgs a, uint8_t* stream, CompWs* ws) {
   put_le(stream, 120, (unsigned long long)a.off_payload, 8);
   put_le(stream, 128, (unsigned long long)total, 8);
   put_le(stream, 136, ws->wmax, 4);
+  put_le(stream, 140, (unsigned long long)a.pred, 4);
   for (int64_t i = a.off_widths + a.nb; i < a.off_heads; ++i) stream[i] = 0;
   for (int64_t i = a.off_heads + 4 * a.nb; i < a.off_chunks; ++i) stream[i] = 0;
   for (int64_t i = a.off_chunks + 8 * (a.nchunks + 1); i < a.off_payload; ++i) stream[i] = 0;
@@ -348,8 +381,8 @@ __global__ void k_header(HeaderArgs a, uint8_t* stream, CompWs* ws) {
 
 // ------------------------------------------------------------------ host
 int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int64_t* dims, double eb,
-                  double eps_given, int eb_mode, int S, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
-                  size_t* out_bytes, hc_header* hdr_out, cudaStream_t st) {
+                  double eps_given, int eb_mode, int S, int pred, void* d_stream, size_t cap, void* d_ws,
+                  size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, cudaStream_t st) {
   Layout L;
   int rc = make_layout(ndim, dims, S, &L);
   if (rc) return rc;
@@ -357,6 +390,7 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   if (!aligned16(d_stream) || !aligned16(d_ws) || !aligned16(d_x)) return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
   if (dtype != HC_F32 && dtype != HC_F64) return fail(HC_ERR_INVALID_ARG, "dtype must be HC_F32 or HC_F64");
   if (eb_mode != HC_EB_ABS && eb_mode != HC_EB_REL) return fail(HC_ERR_INVALID_ARG, "eb_mode");
+  if (pred != HC_PRED_DELTA && pred != HC_PRED_MEAN) return fail(HC_ERR_INVALID_ARG, "predictor");
   if (!(eb > 0.0) || !std::isfinite(eb)) return fail(HC_ERR_INVALID_ARG, "eb must be positive and finite");
   if (cap < L.bound) return fail(HC_ERR_NOMEM, "stream buffer smaller than hc_compress_bound");
   if (ws_bytes < compress_ws_bytes(L)) return fail(HC_ERR_NOMEM, "workspace smaller than hc_compress_workspace_bytes");
@@ -375,6 +409,7 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   o.S = S;
   o.G = L.G;
   o.nseg = (S + 31) / 32;
+  o.pred = pred;
 
   const int sms = device_sms();
   k_ws_init<<<(unsigned)std::min<int64_t>(ceil_div(L.nchunks, kThreads) + 1, 4096), kThreads, 0, st>>>(ws, L.nchunks);
@@ -410,6 +445,7 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   a.S = S;
   a.G = L.G;
   a.eb_mode = eb_mode;
+  a.pred = pred;
   for (int d = 0; d < 3; ++d) a.dims[d] = L.dims[d];
   a.eb = eb;
   a.N = L.N;

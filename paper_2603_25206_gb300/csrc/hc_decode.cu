@@ -5,7 +5,8 @@
 // time.  Per tile the CTA stages the widths, scans them into word offsets and
 // copies the tile's payload into shared memory with 16-byte loads; each thread
 // then decodes one 32-element segment serially (bit unpack, sign, in-block
-// prefix sum) into a padded shared tile, which is written out with coalesced
+// prefix sum -- or, for block-mean (HSZx) streams, the block mean added to
+// each value) into a padded shared tile, which is written out with coalesced
 // 16-byte stores.
 #include <cstdint>
 
@@ -106,6 +107,18 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
       const uint32_t w = tv.w[bl];
       const int32_t head = hb[bl];
       const int r0 = bl * s.S + 32 * j;
+      if (s.pred == HC_PRED_MEAN) {
+        // HSZx: q = M_b + p in every slot, no prefix sum (D_p holds p)
+        const int32_t base = (KIND == HC_STAGE_P) ? 0 : head;
+        if (w == 0) {
+          for (int i = 0; i < cnt; ++i) s_out[pidx(r0 + i)] = base;
+        } else {
+          const uint32_t* blk = tv.words + tv.off[bl];
+          unpack_any(blk + s.nseg + j * w, blk[j], w, cnt,
+                     [&](int i, int32_t p) { s_out[pidx(r0 + i)] = base + p; });
+        }
+        continue;
+      }
       int32_t acc = (KIND == HC_STAGE_P) ? 0 : (SMALL ? head : 0);
       if (w == 0) {
         for (int i = 0; i < cnt; ++i)
@@ -125,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
       if (!SMALL && KIND != HC_STAGE_P) s_tot[seg] = acc;
     }
     __syncthreads();
-    if (!SMALL && KIND != HC_STAGE_P) {
+    if (!SMALL && KIND != HC_STAGE_P && s.pred != HC_PRED_MEAN) {
       // carry of segment j: head + totals of the block's earlier segments
       for (int seg = tid; seg < nsegs; seg += nt) {
         const int bl = seg / s.nseg, j = seg - bl * s.nseg;
@@ -183,6 +196,7 @@ DevStream dev_stream(const hc_header* h, const void* d_stream) {
   s.nseg = (h->S + 31) / 32;
   s.wmax = (int)h->wmax;
   s.gshift = (h->G & (h->G - 1)) == 0 ? __builtin_ctz((unsigned)h->G) : -1;
+  s.pred = (int)h->pred;
   return s;
 }
 

@@ -9,8 +9,10 @@
 //   payload word of its first block.  A block of width w > 0 holds
 //   ceil(S/32) sign words (bit k%32 of word k/32 set iff p_k < 0) and then
 //   ceil(S*w/32) magnitude words with |p_k| at bits [k*w, (k+1)*w),
-//   least-significant bit first.  p_0 = 0: the block's first code (head) is
-//   metadata (Section IV, SZp-style metadata).  Width-0 blocks have no words.
+//   least-significant bit first.  Width-0 blocks have no words.  Header byte
+//   140 names the predictor: delta (heads[b] = the block's first code, p_k =
+//   q_k - q_{k-1}, p_0 = 0: Section IV, SZp-style metadata) or block mean
+//   (HSZx: heads[b] = M_b, p_k = q_k - M_b for every k).
 //
 // Decoding works on 32-element "segments": segment j of a block covers
 // elements [32j, 32j+32).  Its signs are sign word j and its magnitudes start
@@ -44,6 +46,7 @@ struct DevStream {
   int S, G, nseg;  // nseg = ceil(S/32): sign words and segments per block
   int wmax;        // largest block width recorded in the header (sizes the staging buffers)
   int gshift;      // log2(G) when G is a power of two, else -1
+  int pred;        // hc_predictor: heads are first codes (delta) or block means (HSZx)
 };
 
 // First block of the chunk that holds block b (a shift when G is a power of two).
@@ -507,6 +510,25 @@ __device__ inline void finalize_int(hc_scalar* out, int64_t n, long long s1, u12
     const double den = (double)n * (double)(n - 1);
     v = (i128_to_double(num) / den) * (two_eps * two_eps);
   }
+  out->variance = v;
+  out->std = sqrt(v);
+}
+
+// Stage-2 standard deviation of HSZx (Section V-A): s2 is the exact sum of
+// squared deviations from the integer mean mu~; variance = s2 / (N - 1) *
+// (2 eps)^2 (the paper's form, not Eq. var_q), mean from the exact s1.
+__device__ inline void finalize_about(hc_scalar* out, int64_t n, long long s1, u128 s2, long long mu, double two_eps,
+                                      int err) {
+  (void)mu;
+  out->n = n;
+  out->s1 = s1;
+  out->s2_lo = (unsigned long long)s2;
+  out->s2_hi = (unsigned long long)(s2 >> 64);
+  out->status = err;
+  out->exact = 0;
+  out->mean = (__ll2double_rn(s1) / (double)n) * two_eps;
+  double v = __longlong_as_double(0x7ff8000000000000ll);
+  if (n >= 2) v = (i128_to_double((i128)s2) / (double)(n - 1)) * (two_eps * two_eps);
   out->variance = v;
   out->std = sqrt(v);
 }

@@ -42,8 +42,8 @@ int check_header(const hc_header& h);
 int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st);
 
 int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int64_t* dims, double eb,
-                  double eps_given, int eb_mode, int S, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
-                  size_t* out_bytes, hc_header* hdr_out, cudaStream_t st);
+                  double eps_given, int eb_mode, int S, int pred, void* d_stream, size_t cap, void* d_ws,
+                  size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, cudaStream_t st);
 
 // Workspace of decompression and operations: a status word, the
 // last-block ticket of the reductions and the per-CTA partial results.
@@ -56,7 +56,7 @@ struct Partial {
 struct OpWs {
   int status;
   unsigned int ticket;
-  int pad[14];
+  int pad[14];  // pad[0..1]: the integer mean of a stage-2 HSZx deviation (8-byte aligned)
 };
 constexpr int kMaxGrid = 4096;
 constexpr size_t kOpWsBytes = sizeof(OpWs) + sizeof(Partial) * kMaxGrid;
@@ -73,6 +73,9 @@ enum ReduceWhat { RED_MEAN = 0, RED_VAR = 1 };
 int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out,
                        void* d_ws, cudaStream_t st);
 int reduce_array_impl(const hc_stage* in, double eps, int what, hc_scalar* d_out, void* d_ws, cudaStream_t st);
+// Stage-1 mean of HSZx from a block-means array (Eq. mean_m).
+int mean_m_array_impl(const int32_t* means, int64_t nb, int S, int64_t n, double eps, hc_scalar* d_out, void* d_ws,
+                      cudaStream_t st);
 // Fused stage-3 variance with its scratch (per-CTA partials + ticket) at given device addresses.
 int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
                                  unsigned* ticket, int max_parts, cudaStream_t st);

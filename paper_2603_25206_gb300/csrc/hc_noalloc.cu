@@ -58,6 +58,8 @@ extern "C" HC_API int hc_op_variance_noalloc(const hc_stage* in, double eps, int
   if (!in->d_data || !in->hdr) return fail(HC_ERR_INVALID_ARG, "a stream input needs its data and header");
   if (in->level != HC_STAGE_P && in->level != HC_STAGE_Q)
     return fail(HC_ERR_INVALID_ARG, "fused level must be HC_STAGE_P or HC_STAGE_Q");
+  if (in->hdr && in->hdr->pred == HC_PRED_MEAN && in->level == HC_STAGE_P)
+    return fail(HC_ERR_UNSUPPORTED, "the stage-2 block-mean deviation needs a workspace: use hc_op_variance");
   if (!aligned16(in->d_data)) return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
   const hc_header* h = in->hdr;
   Layout L;

@@ -42,11 +42,17 @@ __host__ __device__ inline int padded_words(int elems) { return round4(((elems +
 // ------------------------------------------------------- fused, from stream
 // ACC: 0 narrow (max |q| < 2^12: 32-bit per-segment sums), 1 mid (< 2^26:
 // 64-bit per-segment sums), 2 wide (128-bit per element).
+// Block-mean (HSZx) streams take one branch per segment: q = M_b + p, so the
+// segment's sums follow from sum p and sum p^2 (no prefix sum): s1 += cnt M_b
+// + sum p, and, about a shift c0 (0, or the integer mean mu~ of the stage-2
+// form), s2 += cnt c^2 + 2 c sum p + sum p^2 with c = M_b - c0.  `shift`
+// points at c0 in device memory (NULL: no shift).
 template <int LEVEL, int ACC, bool VAR, bool SMALL>
 __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t ntiles, int stage_words,
                                                              Partial* parts, unsigned* ticket, hc_scalar* out,
-                                                             double two_eps) {
+                                                             double two_eps, const long long* shift) {
   extern __shared__ __align__(16) uint32_t smem[];
+  const long long c0 = shift ? __ldcg(shift) : 0ll;
   __shared__ uint32_t s_warp[32];
   __shared__ int s_flag;
   __shared__ int s_err;
@@ -125,6 +131,28 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
       const uint32_t w = tv.w[bl];
       const int32_t head = hb[bl];
       const uint32_t* blk = tv.words + tv.off[bl];
+      if (s.pred == HC_PRED_MEAN) {
+        // HSZx (Section V-A): stage 2 mean sum p + M_b S_b, stage 3 / the
+        // stage-2 deviation sums from sum p and sum p^2
+        using P2 = typename std::conditional<ACC == 2, u128, unsigned long long>::type;
+        long long sp = 0;
+        P2 sp2 = 0;
+        if (w) unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
+            sp += p;
+            if (VAR) sp2 += (P2)(unsigned long long)((long long)p * p);
+          });
+        S1 += (long long)cnt * head + sp;
+        if (VAR) {
+          const long long c = (long long)head - c0;
+          S2 += (u128)((i128)cnt * c * c + (i128)2 * c * sp + (i128)sp2);
+        }
+        if constexpr (!SMALL && LEVEL == 3) {
+          s_T[seg] = 0;
+          s_a1[seg] = 0;
+          if (VAR) s_a2[seg] = 0;
+        }
+        continue;
+      }
       if constexpr (LEVEL == 2) {
         // Section V-A, stage 2: sum_k (S_b - k) p_k with the head as p_0
         using A = typename std::conditional<ACC == 0, int32_t, long long>::type;
@@ -226,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
     }
     if constexpr (!SMALL && LEVEL == 3) {
       __syncthreads();
-      for (int seg = tid; seg < nsegs; seg += nt) {
+      for (int seg = tid; seg < nsegs && s.pred != HC_PRED_MEAN; seg += nt) {
         const int bl = seg / s.nseg, j = seg - bl * s.nseg;
         const int64_t b = b0 + bl;
         const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
@@ -248,7 +276,40 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
   __syncthreads();
   const int err = s_err;
   reduce_and_finish(S1, S2, err, parts, ticket, [&](long long a, u128 b, int e) {
-    finalize_int(out, s.N, a, b, VAR, two_eps, e);
+    if (shift)
+      finalize_about(out, s.N, a, b, c0, two_eps, e);
+    else
+      finalize_int(out, s.N, a, b, VAR, two_eps, e);
+  });
+}
+
+// ------------------------------------------------------ stage 1 (HSZx)
+// Eq. mean_m: T = sum_b M_b S_b from the block means alone; mean = (T / N)
+// 2 eps.  With mu != NULL the integer mean mu~ = round(T / N) (nearest, ties
+// toward zero) is also stored for the stage-2 standard deviation.
+__global__ void __launch_bounds__(kThreads) k_mean_m(const int32_t* __restrict__ means, int64_t nb, int S, int64_t n,
+                                                      Partial* parts, unsigned* ticket, hc_scalar* out,
+                                                      double two_eps, long long* mu) {
+  long long t = 0;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    const long long Sb = min((long long)S, (long long)(n - b * S));
+    t += (long long)__ldg(means + b) * Sb;
+  }
+  reduce_and_finish(t, (u128)0, 0, parts, ticket, [&](long long a, u128, int e) {
+    out->n = n;
+    out->s1 = a;
+    out->s2_lo = 0;
+    out->s2_hi = 0;
+    out->status = e;
+    out->exact = 0;
+    out->mean = (__ll2double_rn(a) / (double)n) * two_eps;
+    out->variance = __longlong_as_double(0x7ff8000000000000ll);
+    out->std = out->variance;
+    if (mu) {
+      const unsigned long long m = (unsigned long long)(a < 0 ? -a : a);
+      const long long r = (long long)((2ull * m + (unsigned long long)n - 1ull) / (2ull * (unsigned long long)n));
+      *mu = a < 0 ? -r : r;
+    }
   });
 }
 
@@ -475,7 +536,8 @@ static int acc_class(uint32_t qmax) {
 }
 
 template <int LEVEL, int ACC, bool VAR, bool SMALL>
-static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st) {
+static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st,
+                         const long long* shift = nullptr) {
   const DevStream s = dev_stream(h, d_stream);
   const int tb = kTileChunks * h->G;
   const int nseg = (h->S + 31) / 32;
@@ -493,25 +555,57 @@ static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_
   const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
   const int grid = (int)std::min<int64_t>(std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm), kMaxGrid);
   OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
-  kern<<<grid, kThreads, bytes, st>>>(s, ntiles, stage, ws_partials(d_ws), &ws->ticket, d_out, 2.0 * h->eps);
+  kern<<<grid, kThreads, bytes, st>>>(s, ntiles, stage, ws_partials(d_ws), &ws->ticket, d_out, 2.0 * h->eps, shift);
   return check_launch_cfg("reduce (fused)", reinterpret_cast<const void*>(kern), grid, bytes);
 }
 
 template <int LEVEL, bool VAR, bool SMALL>
-static int launch_stream_acc(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st) {
+static int launch_stream_acc(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st,
+                             const long long* shift = nullptr) {
   switch (acc_class(h->qmax)) {
     case 0:
-      return launch_stream<LEVEL, 0, VAR, SMALL>(h, d_stream, d_out, d_ws, st);
+      return launch_stream<LEVEL, 0, VAR, SMALL>(h, d_stream, d_out, d_ws, st, shift);
     case 1:
-      return launch_stream<LEVEL, (LEVEL == 2 ? 2 : 1), VAR, SMALL>(h, d_stream, d_out, d_ws, st);
+      return launch_stream<LEVEL, (LEVEL == 2 ? 2 : 1), VAR, SMALL>(h, d_stream, d_out, d_ws, st, shift);
     default:
-      return launch_stream<LEVEL, 2, VAR, SMALL>(h, d_stream, d_out, d_ws, st);
+      return launch_stream<LEVEL, 2, VAR, SMALL>(h, d_stream, d_out, d_ws, st, shift);
   }
+}
+
+// Stage 1 of HSZx: the block means alone (Eq. mean_m).
+static int launch_mean_m(const int32_t* means, int64_t nb, int S, int64_t n, double eps, hc_scalar* d_out,
+                         void* d_ws, long long* mu, cudaStream_t st) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ceil_div(nb, kThreads),
+                                                                                   (int64_t)device_sms() * 4),
+                                                                 kMaxGrid));
+  OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
+  k_mean_m<<<grid, kThreads, 0, st>>>(means, nb, S, n, ws_partials(d_ws), &ws->ticket, d_out, 2.0 * eps, mu);
+  return check_launch("mean (stage 1)");
+}
+
+int mean_m_array_impl(const int32_t* means, int64_t nb, int S, int64_t n, double eps, hc_scalar* d_out, void* d_ws,
+                      cudaStream_t st) {
+  return launch_mean_m(means, nb, S, n, eps, d_out, d_ws, nullptr, st);
 }
 
 int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, void* d_ws,
                        cudaStream_t st) {
   const bool small = h->S <= 32;
+  const bool hszx = h->pred == HC_PRED_MEAN;
+  const int32_t* means = reinterpret_cast<const int32_t*>(reinterpret_cast<const uint8_t*>(d_stream) + h->off_heads);
+  if (level == HC_STAGE_M) {
+    if (!hszx) return fail(HC_ERR_UNSUPPORTED, "block heads of a delta-coded stream support no statistic");
+    if (what != RED_MEAN) return fail(HC_ERR_UNSUPPORTED, "stage 1 gives the mean only (Eq. mean_m)");
+    return launch_mean_m(means, h->nb, h->S, h->N, h->eps, d_out, d_ws, nullptr, st);
+  }
+  if (hszx && level == HC_STAGE_P && what == RED_VAR) {
+    // Section V-A: the deviations about the integer mean mu~ of stage 1
+    long long* mu = reinterpret_cast<long long*>(&reinterpret_cast<OpWs*>(d_ws)->pad[0]);
+    int rc = launch_mean_m(means, h->nb, h->S, h->N, h->eps, d_out, d_ws, mu, st);
+    if (rc) return rc;
+    return small ? launch_stream_acc<3, true, true>(h, d_stream, d_out, d_ws, st, mu)
+                 : launch_stream_acc<3, true, false>(h, d_stream, d_out, d_ws, st, mu);
+  }
   if (level == HC_STAGE_P && what == RED_MEAN)
     return small ? launch_stream_acc<2, false, true>(h, d_stream, d_out, d_ws, st)
                  : launch_stream_acc<2, false, false>(h, d_stream, d_out, d_ws, st);
@@ -630,7 +724,7 @@ static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scala
   const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm);
   if (grid > max_parts) return fail(HC_ERR_NOMEM, "the static scratch of hc_op_variance_noalloc has too few partial slots for this GPU");
-  kern<<<(unsigned)grid, kThreads, bytes, st>>>(s, ntiles, stage, parts, ticket, d_out, 2.0 * h->eps);
+  kern<<<(unsigned)grid, kThreads, bytes, st>>>(s, ntiles, stage, parts, ticket, d_out, 2.0 * h->eps, nullptr);
   return check_launch_cfg("variance (static scratch)", reinterpret_cast<const void*>(kern), grid, bytes);
 }
 

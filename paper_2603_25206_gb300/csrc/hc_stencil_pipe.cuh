@@ -258,6 +258,7 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
   using T = typename OT<OUT>::T;
   const PSmem L = psmem(g);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool mean_pred = s.pred == HC_PRED_MEAN;
 
   const int64_t y0 = (int64_t)yt * g.ty, y1 = min(y0 + g.ty, g.n1);
   const int64_t z0 = (int64_t)zt * g.tz, z1 = min(z0 + g.tz, g.n0);
@@ -425,6 +426,10 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
           if (wi == 0) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = (short)q;
+          } else if (mean_pred) {
+            // block mean (HSZx): q = M_b + p
+            const uint32_t* blk = stg + off[seg];
+            unpack_full(blk + 1, blk[0], wi, [&](int i, int32_t p) { v[i] = (short)(q + p); });
           } else {
             const uint32_t* blk = stg + off[seg];
             unpack_full(blk + 1, blk[0], wi, [&](int i, int32_t p) {

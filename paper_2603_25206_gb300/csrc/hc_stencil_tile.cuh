@@ -108,6 +108,17 @@ __device__ inline int64_t decode_range(const DevStream& s, int64_t e0, int64_t e
     const uint32_t w = tv.w[bl];
     const int32_t head = __ldg(s.heads + b);
     const int r0 = bl * s.S + 32 * j;
+    if (s.pred == HC_PRED_MEAN) {
+      // block mean (HSZx): q = M_b + p, no prefix sum and no carry
+      if (w == 0) {
+        for (int i = 0; i < cnt; ++i) dst[pidx(r0 + i)] = head;
+      } else {
+        const uint32_t* blk = tv.words + tv.off[bl];
+        unpack_segment<false>(blk + s.nseg + j * w, blk[j], w, cnt,
+                              [&](int i, int32_t p) { dst[pidx(r0 + i)] = head + p; });
+      }
+      continue;
+    }
     int32_t acc = SMALL ? head : 0;
     if (w == 0) {
       for (int i = 0; i < cnt; ++i) dst[pidx(r0 + i)] = acc;
@@ -123,7 +134,7 @@ __device__ inline int64_t decode_range(const DevStream& s, int64_t e0, int64_t e
     if (!SMALL) s_tot[seg] = acc;
   }
   __syncthreads();
-  if (!SMALL) {
+  if (!SMALL && s.pred != HC_PRED_MEAN) {
     for (int seg = tid; seg < nsegs; seg += nt) {
       const int bl = seg / s.nseg, j = seg - bl * s.nseg;
       const int64_t b = b0 + bl;

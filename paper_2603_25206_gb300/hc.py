@@ -41,8 +41,11 @@ ABI_FUNCTIONS = (
     "hc_decompress_to_stage", "hc_workspace_status", "hc_op_mean", "hc_op_variance", "hc_op_std",
     "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc", "hc_autotune",
     "hc_batch_plan_bytes", "hc_batch_workspace_bytes", "hc_batch_plan", "hc_batch_run", "hc_batch_graph_create",
-    "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi",
+    "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
+    "hc_compress_codes_ex",
 )
+HC_PRED_DELTA, HC_PRED_MEAN = 0, 1
+PREDICTORS = {"delta": HC_PRED_DELTA, "mean": HC_PRED_MEAN}
 HC_BATCH_MEAN, HC_BATCH_VARIANCE, HC_BATCH_DERIVATIVE, HC_BATCH_GRADMAG, HC_BATCH_LAPLACIAN = 1, 2, 4, 8, 16
 BATCH_OPS = {"mean": HC_BATCH_MEAN, "variance": HC_BATCH_VARIANCE, "derivative": HC_BATCH_DERIVATIVE,
              "gradmag": HC_BATCH_GRADMAG, "laplacian": HC_BATCH_LAPLACIAN}
@@ -61,7 +64,7 @@ class HcHeader(ctypes.Structure):
                 ("nb", ctypes.c_int64), ("nchunks", ctypes.c_int64), ("payload_words", ctypes.c_int64),
                 ("off_widths", ctypes.c_int64), ("off_heads", ctypes.c_int64), ("off_chunks", ctypes.c_int64),
                 ("off_payload", ctypes.c_int64), ("total_bytes", ctypes.c_int64), ("wmax", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("pred", ctypes.c_uint32)]
 
     @property
     def shape(self):
@@ -71,7 +74,7 @@ class HcHeader(ctypes.Structure):
 class HcStage(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("d_data", ctypes.c_void_p),
                 ("hdr", ctypes.POINTER(HcHeader)), ("dtype", ctypes.c_int32), ("S", ctypes.c_int32),
-                ("n", ctypes.c_int64), ("qmax", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("n", ctypes.c_int64), ("qmax", ctypes.c_uint32), ("pred", ctypes.c_uint32)]
 
 
 class HcBatchItem(ctypes.Structure):
@@ -125,6 +128,10 @@ def lib():
                             i32),
             "hc_compress_codes": ([vp, i32, i32, P(ctypes.c_int64), dbl, dbl, i32, i32, vp, sz, vp, sz, P(sz),
                                    P(HcHeader), vp], i32),
+            "hc_compress_ex": ([vp, i32, i32, P(ctypes.c_int64), dbl, i32, i32, i32, vp, sz, vp, sz, P(sz),
+                                P(HcHeader), vp], i32),
+            "hc_compress_codes_ex": ([vp, i32, i32, P(ctypes.c_int64), dbl, dbl, i32, i32, i32, vp, sz, vp, sz,
+                                      P(sz), P(HcHeader), vp], i32),
             "hc_read_header": ([vp, sz, P(HcHeader), vp], i32),
             "hc_decompress_to_stage": ([P(HcHeader), vp, i32, vp, i32, vp, sz, vp], i32),
             "hc_workspace_status": ([vp, vp], i32),
@@ -225,13 +232,14 @@ class Compressed:
 
 @dataclass
 class StageArray:
-    """A materialized stage: kind 'p', 'q' or 'f' (torch tensor on the GPU)."""
+    """A materialized stage: kind 'm', 'p', 'q' or 'f' (torch tensor on the GPU)."""
     kind: str
     data: "object"
     shape: tuple
     eps: float
     S: int = 0
     qmax: int = 0
+    pred: int = HC_PRED_DELTA
 
     def stage(self) -> HcStage:
         torch = _torch()
@@ -242,11 +250,13 @@ class StageArray:
         st.S = self.S
         st.n = int(np.prod(self.shape))
         st.qmax = self.qmax
+        st.pred = self.pred
         return st
 
 
-def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None) -> Compressed:
-    """C (Algorithm 1) of a float32/float64 CUDA tensor."""
+def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None, predictor: str = "delta") -> Compressed:
+    """C (Algorithm 1) of a float32/float64 CUDA tensor.  predictor "delta"
+    (HSZp with block heads) or "mean" (HSZx: block means)."""
     torch = _torch()
     if not x.is_cuda:
         raise ValueError("compress expects a CUDA tensor")
@@ -260,14 +270,15 @@ def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None) -> Compre
     ws = torch.empty(int(L.hc_compress_workspace_bytes(x.numel(), S)), dtype=torch.uint8, device=x.device)
     nbytes = ctypes.c_size_t()
     hdr = HcHeader()
-    _check(L.hc_compress(ctypes.c_void_p(x.data_ptr()), dtype, x.dim(), _dims(x.shape), eb,
-                         HC_EB_REL if rel else HC_EB_ABS, S, ctypes.c_void_p(out.data_ptr()), cap,
-                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(nbytes), ctypes.byref(hdr),
-                         _stream_ptr(stream)))
+    _check(L.hc_compress_ex(ctypes.c_void_p(x.data_ptr()), dtype, x.dim(), _dims(x.shape), eb,
+                            HC_EB_REL if rel else HC_EB_ABS, S, PREDICTORS[predictor],
+                            ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                            ctypes.byref(nbytes), ctypes.byref(hdr), _stream_ptr(stream)))
     return Compressed(out, hdr, nbytes.value)
 
 
-def compress_codes(q, eps: float, S: int = 32, dtype: str = "float32", eb=None, rel=False, stream=None) -> Compressed:
+def compress_codes(q, eps: float, S: int = 32, dtype: str = "float32", eb=None, rel=False, stream=None,
+                   predictor: str = "delta") -> Compressed:
     """Encode given int32 codes (CUDA tensor)."""
     torch = _torch()
     q = q.contiguous()
@@ -277,10 +288,11 @@ def compress_codes(q, eps: float, S: int = 32, dtype: str = "float32", eb=None, 
     ws = torch.empty(int(L.hc_compress_workspace_bytes(q.numel(), S)), dtype=torch.uint8, device=q.device)
     nbytes = ctypes.c_size_t()
     hdr = HcHeader()
-    _check(L.hc_compress_codes(ctypes.c_void_p(q.data_ptr()), HC_F64 if dtype == "float64" else HC_F32, q.dim(),
-                               _dims(q.shape), eps, eps if eb is None else eb, HC_EB_REL if rel else HC_EB_ABS, S,
-                               ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
-                               ctypes.byref(nbytes), ctypes.byref(hdr), _stream_ptr(stream)))
+    _check(L.hc_compress_codes_ex(ctypes.c_void_p(q.data_ptr()), HC_F64 if dtype == "float64" else HC_F32,
+                                  q.dim(), _dims(q.shape), eps, eps if eb is None else eb,
+                                  HC_EB_REL if rel else HC_EB_ABS, S, PREDICTORS[predictor],
+                                  ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                  ctypes.byref(nbytes), ctypes.byref(hdr), _stream_ptr(stream)))
     return Compressed(out, hdr, nbytes.value)
 
 
@@ -315,7 +327,7 @@ def decompress(c: Compressed, stage: str = "f", out=None, out_dtype=None, stream
 
 def as_stage(c: Compressed, stage: str, data) -> StageArray:
     """Describe a materialized stage of c for the operations."""
-    return StageArray(stage, data, c.shape, c.eps, c.header.S, int(c.header.qmax))
+    return StageArray(stage, data, c.shape, c.eps, c.header.S, int(c.header.qmax), int(c.header.pred))
 
 
 def _input(inp, level):
