@@ -796,6 +796,94 @@ def run_serving(args):
     return 0
 
 
+def run_hszx(args):
+    """The block-mean (HSZx) form of the paper-like workload: the same five
+    fields compressed with block means as metadata (block 32, eb 1e-3
+    value-range relative).  Per field and operation: the fused time at every
+    stage it is defined at (mean at stages 1, 2, 3; standard deviation at 2
+    and 3; all stencils in one pass at 3) and the plain path (decompress to
+    float32, then the operation), median CUDA-event time over 5 runs with an
+    L2 flush before each.  GB/s counts the field's original bytes."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = []
+    tot = {}
+    for shape, x in make_fields():
+        xd = torch.from_numpy(x).to(dev)
+        cx = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK, predictor="mean"))
+        cd = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK))
+        del xd
+        n = int(np.prod(shape))
+        scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
+        df = torch.empty(shape, dtype=torch.float32, device=dev)
+        nd = len(shape)
+        mo = {"derivative": [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(nd)],
+              "gradmag": torch.empty(shape, dtype=torch.float32, device=dev),
+              "laplacian": torch.empty(shape, dtype=torch.float32, device=dev), "stats": scal}
+        sf = hc.as_stage(cx, "f", df)
+
+        def plain_stat(fn):
+            hc.decompress(cx, "f", out=df)
+            fn(sf, out=scal)
+
+        def plain_all():
+            hc.decompress(cx, "f", out=df)
+            hc.mean(sf, out=scal)
+            hc.variance(sf, out=scal)
+            for a in range(nd):
+                hc.derivative(sf, a, out=mo["derivative"][a])
+            hc.gradmag(sf, out=mo["gradmag"])
+            hc.laplacian(sf, out=mo["laplacian"])
+
+        t = {
+            "mean_stage1": time_call(torch, dev, lambda: hc.mean(cx, level="m", out=scal)),
+            "mean_stage2": time_call(torch, dev, lambda: hc.mean(cx, level="p", out=scal)),
+            "mean_stage3": time_call(torch, dev, lambda: hc.mean(cx, level="q", out=scal)),
+            "mean_plain": time_call(torch, dev, lambda: plain_stat(hc.mean)),
+            "std_stage2": time_call(torch, dev, lambda: hc.variance(cx, level="p", out=scal)),
+            "std_stage3": time_call(torch, dev, lambda: hc.variance(cx, level="q", out=scal)),
+            "std_plain": time_call(torch, dev, lambda: plain_stat(hc.variance)),
+            "all_ops_one_pass_stage3": time_call(torch, dev, lambda: hc.multi(cx, outs=mo)),
+            "all_ops_plain_decompress_once": time_call(torch, dev, plain_all),
+        }
+        r = {"field": "x".join(map(str, shape)), "hszx_bytes": cx.nbytes, "delta_bytes": cd.nbytes,
+             "ms": {k: round(v, 4) for k, v in t.items()},
+             "gbs_orig": {k: round(n * 4 / v / 1e6, 1) for k, v in t.items()},
+             "speedup_vs_plain": {"mean_stage1": round(t["mean_plain"] / t["mean_stage1"], 2),
+                                  "mean_stage2": round(t["mean_plain"] / t["mean_stage2"], 2),
+                                  "mean_stage3": round(t["mean_plain"] / t["mean_stage3"], 2),
+                                  "std_stage2": round(t["std_plain"] / t["std_stage2"], 2),
+                                  "std_stage3": round(t["std_plain"] / t["std_stage3"], 2),
+                                  "all_ops_one_pass": round(t["all_ops_plain_decompress_once"] /
+                                                            t["all_ops_one_pass_stage3"], 2)}}
+        rows.append(r)
+        for k, v in t.items():
+            tot[k] = tot.get(k, 0.0) + v
+        del cx, cd, df, mo
+    orig = sum(int(np.prod(sh)) * 4 for sh in synth_shapes())
+    line = {"metric": "HSZx (block-mean) operations: GB/s of original data per stage, vs the plain path",
+            "unit": "GB/s", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("block 32;", "block 32, block-mean predictor (HSZx);"),
+                       "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
+            "totals_ms": {k: round(v, 4) for k, v in tot.items()},
+            "totals_gbs_orig": {k: round(orig / v / 1e6, 1) for k, v in tot.items()},
+            "per_field": rows}
+    print(json.dumps(line))
+    return 0
+
+
+def synth_shapes():
+    import synth
+
+    return synth.PAPER_SHAPES
+
+
 def run_profile_small():
     """Small case for ncu captures: one 256x384x384 float32 field (compressed
     ~44 MB, float32 outputs 151 MB each: larger than L2), each operation 3
@@ -868,6 +956,7 @@ def main(argv=None):
     ap.add_argument("--batched", action="store_true", help="the batched form (64 uneven fields, one launch)")
     ap.add_argument("--profile-batch", action="store_true", help="run the small batched ncu case and exit")
     ap.add_argument("--serving", action="store_true", help="the serving form (200 resident fields, Poisson queries)")
+    ap.add_argument("--hszx", action="store_true", help="the block-mean (HSZx) form of the paper-like workload")
     ap.add_argument("--fields", type=int, default=200)
     ap.add_argument("--qps", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=30.0)
@@ -878,6 +967,8 @@ def main(argv=None):
         return run_profile_batch()
     if args.serving:
         return run_serving(args)
+    if args.hszx:
+        return run_hszx(args)
     if args.batched:
         if args.warmup < 3:
             args.warmup = 3

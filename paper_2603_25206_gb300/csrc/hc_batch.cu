@@ -124,10 +124,18 @@ __device__ __noinline__ void stencil_unit(const BItem& it, int64_t lu, int* err,
   stencil_tile<ST_RUNTIME, ST_RUNTIME, SMALL, true>(it.s, it.g, lu, it.field, err, smem, s_warp, s_flag, s_base, mo);
 }
 
-template <int V>
+template <int V, int PRED>
 __device__ __noinline__ void pipe_unit(const BItem& it, int64_t lu, int* err, unsigned char* smem, Moments& mo) {
-  pipe_tile<ST_RUNTIME, ST_RUNTIME, V, true>(it.s, it.pg, (int)(lu % it.pg.nyt), (int)(lu / it.pg.nyt), it.field,
-                                            err, smem, mo);
+  pipe_tile<ST_RUNTIME, ST_RUNTIME, V, true, PRED>(it.s, it.pg, (int)(lu % it.pg.nyt), (int)(lu / it.pg.nyt),
+                                                  it.field, err, smem, mo);
+}
+
+template <int V>
+__device__ __forceinline__ void pipe_unit_p(const BItem& it, int64_t lu, int* err, unsigned char* smem, Moments& mo) {
+  if (it.s.pred == HC_PRED_MEAN)
+    pipe_unit<V, HC_PRED_MEAN>(it, lu, err, smem, mo);
+  else
+    pipe_unit<V, HC_PRED_DELTA>(it, lu, err, smem, mo);
 }
 
 // CTA sum of the unit's moments into the field accumulator; the field's last
@@ -234,11 +242,11 @@ __global__ void __launch_bounds__(THREADS, THREADS == 512 ? 1 : 768 / THREADS) k
       if constexpr (THREADS == kThreads) {
         unsigned char* sm = reinterpret_cast<unsigned char*>(smem);
         if (s_it.vec == 8)
-          pipe_unit<8>(s_it, lu, err, sm, mo);
+          pipe_unit_p<8>(s_it, lu, err, sm, mo);
         else if (s_it.vec == 4)
-          pipe_unit<4>(s_it, lu, err, sm, mo);
+          pipe_unit_p<4>(s_it, lu, err, sm, mo);
         else
-          pipe_unit<1>(s_it, lu, err, sm, mo);
+          pipe_unit_p<1>(s_it, lu, err, sm, mo);
       }
     } else if (s_it.fop >= 0) {
       if (s_it.s.S <= 32)

@@ -36,7 +36,7 @@ struct Conv<double> {
 };
 
 // KIND: HC_STAGE_P, HC_STAGE_Q or HC_STAGE_F.  SMALL: S <= 32 (one segment per block).
-template <int KIND, class OutT, bool SMALL>
+template <int KIND, class OutT, bool SMALL, int PRED>
 __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restrict__ out, float te_f, double te_d,
                                                       int64_t ntiles, int stage_words, int* err) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
       const uint32_t w = tv.w[bl];
       const int32_t head = hb[bl];
       const int r0 = bl * s.S + 32 * j;
-      if (s.pred == HC_PRED_MEAN) {
+      if constexpr (PRED == HC_PRED_MEAN) {
         // HSZx: q = M_b + p in every slot, no prefix sum (D_p holds p)
         const int32_t base = (KIND == HC_STAGE_P) ? 0 : head;
         if (w == 0) {
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
       if (!SMALL && KIND != HC_STAGE_P) s_tot[seg] = acc;
     }
     __syncthreads();
-    if (!SMALL && KIND != HC_STAGE_P && s.pred != HC_PRED_MEAN) {
+    if (!SMALL && KIND != HC_STAGE_P && PRED != HC_PRED_MEAN) {
       // carry of segment j: head + totals of the block's earlier segments
       for (int seg = tid; seg < nsegs; seg += nt) {
         const int bl = seg / s.nseg, j = seg - bl * s.nseg;
@@ -207,13 +207,13 @@ static PipeTileSmem decode_layout(const hc_header* h, bool small, int stage) {
   return pipe_tile_smem(tb, stage, decode_out_words(tb, h->S) + (small ? 0 : nsegmax) + (kWidthSpecialize ? round4((nsegmax + 32 * 32 + 1) / 2) : 0));
 }
 
-template <int KIND, class OutT, bool SMALL>
+template <int KIND, class OutT, bool SMALL, int PRED>
 static int launch_decode(const hc_header* h, const void* d_stream, void* d_out, int* err, cudaStream_t st) {
   const DevStream s = dev_stream(h, d_stream);
   const int stage = stage_words_for(kTileChunks * h->G, h->S, (int)h->wmax);
   const PipeTileSmem L = decode_layout(h, SMALL, stage);
   const int smem = 4 * L.total;
-  auto kern = k_decode<KIND, OutT, SMALL>;
+  auto kern = k_decode<KIND, OutT, SMALL, PRED>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (rc) return rc;
   int per_sm = 0;
@@ -226,10 +226,16 @@ static int launch_decode(const hc_header* h, const void* d_stream, void* d_out, 
   return check_launch_cfg("decompress_to_stage", reinterpret_cast<const void*>(kern), grid, smem);
 }
 
+template <int KIND, class OutT, int PRED>
+static int launch_decode_sp(const hc_header* h, const void* d_stream, void* d_out, int* err, cudaStream_t st) {
+  if (h->S <= 32) return launch_decode<KIND, OutT, true, PRED>(h, d_stream, d_out, err, st);
+  return launch_decode<KIND, OutT, false, PRED>(h, d_stream, d_out, err, st);
+}
+
 template <int KIND, class OutT>
 static int launch_decode_s(const hc_header* h, const void* d_stream, void* d_out, int* err, cudaStream_t st) {
-  if (h->S <= 32) return launch_decode<KIND, OutT, true>(h, d_stream, d_out, err, st);
-  return launch_decode<KIND, OutT, false>(h, d_stream, d_out, err, st);
+  if (h->pred == HC_PRED_MEAN) return launch_decode_sp<KIND, OutT, HC_PRED_MEAN>(h, d_stream, d_out, err, st);
+  return launch_decode_sp<KIND, OutT, HC_PRED_DELTA>(h, d_stream, d_out, err, st);
 }
 
 int decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,

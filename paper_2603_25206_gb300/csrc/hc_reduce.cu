@@ -42,12 +42,13 @@ __host__ __device__ inline int padded_words(int elems) { return round4(((elems +
 // ------------------------------------------------------- fused, from stream
 // ACC: 0 narrow (max |q| < 2^12: 32-bit per-segment sums), 1 mid (< 2^26:
 // 64-bit per-segment sums), 2 wide (128-bit per element).
-// Block-mean (HSZx) streams take one branch per segment: q = M_b + p, so the
+// Block-mean (HSZx) streams (PRED = HC_PRED_MEAN, its own instantiations):
+// q = M_b + p, so the
 // segment's sums follow from sum p and sum p^2 (no prefix sum): s1 += cnt M_b
 // + sum p, and, about a shift c0 (0, or the integer mean mu~ of the stage-2
 // form), s2 += cnt c^2 + 2 c sum p + sum p^2 with c = M_b - c0.  `shift`
 // points at c0 in device memory (NULL: no shift).
-template <int LEVEL, int ACC, bool VAR, bool SMALL>
+template <int LEVEL, int ACC, bool VAR, bool SMALL, int PRED>
 __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t ntiles, int stage_words,
                                                              Partial* parts, unsigned* ticket, hc_scalar* out,
                                                              double two_eps, const long long* shift) {
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
       const uint32_t w = tv.w[bl];
       const int32_t head = hb[bl];
       const uint32_t* blk = tv.words + tv.off[bl];
-      if (s.pred == HC_PRED_MEAN) {
+      if constexpr (PRED == HC_PRED_MEAN) {
         // HSZx (Section V-A): stage 2 mean sum p + M_b S_b, stage 3 / the
         // stage-2 deviation sums from sum p and sum p^2
         using P2 = typename std::conditional<ACC == 2, u128, unsigned long long>::type;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
     }
     if constexpr (!SMALL && LEVEL == 3) {
       __syncthreads();
-      for (int seg = tid; seg < nsegs && s.pred != HC_PRED_MEAN; seg += nt) {
+      for (int seg = tid; seg < nsegs && PRED != HC_PRED_MEAN; seg += nt) {
         const int bl = seg / s.nseg, j = seg - bl * s.nseg;
         const int64_t b = b0 + bl;
         const int Sb = (int)min((int64_t)s.S, s.N - b * s.S);
@@ -535,9 +536,9 @@ static int acc_class(uint32_t qmax) {
   return 2;
 }
 
-template <int LEVEL, int ACC, bool VAR, bool SMALL>
-static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st,
-                         const long long* shift = nullptr) {
+template <int LEVEL, int ACC, bool VAR, bool SMALL, int PRED>
+static int launch_stream_p(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st,
+                           const long long* shift) {
   const DevStream s = dev_stream(h, d_stream);
   const int tb = kTileChunks * h->G;
   const int nseg = (h->S + 31) / 32;
@@ -546,7 +547,7 @@ static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_
   const PipeTileSmem L =
       pipe_tile_smem(tb, stage, ((!SMALL && LEVEL == 3) ? seg_moment_words(nsegmax, VAR) : 0) + order_words(nsegmax));
   const int bytes = 4 * L.total;
-  auto kern = k_reduce_stream<LEVEL, ACC, VAR, SMALL>;
+  auto kern = k_reduce_stream<LEVEL, ACC, VAR, SMALL, PRED>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
   if (rc) return rc;
   int per_sm = 0;
@@ -557,6 +558,16 @@ static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_
   OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
   kern<<<grid, kThreads, bytes, st>>>(s, ntiles, stage, ws_partials(d_ws), &ws->ticket, d_out, 2.0 * h->eps, shift);
   return check_launch_cfg("reduce (fused)", reinterpret_cast<const void*>(kern), grid, bytes);
+}
+
+// Block-mean streams: the same sums at stages 2 and 3 (sum q = sum p + M_b
+// S_b), one accumulator class for codes below 2^26 and one above.
+template <int LEVEL, int ACC, bool VAR, bool SMALL>
+static int launch_stream(const hc_header* h, const void* d_stream, hc_scalar* d_out, void* d_ws, cudaStream_t st,
+                         const long long* shift = nullptr) {
+  if (h->pred == HC_PRED_MEAN)
+    return launch_stream_p<3, (ACC == 2 ? 2 : 1), VAR, SMALL, HC_PRED_MEAN>(h, d_stream, d_out, d_ws, st, shift);
+  return launch_stream_p<LEVEL, ACC, VAR, SMALL, HC_PRED_DELTA>(h, d_stream, d_out, d_ws, st, shift);
 }
 
 template <int LEVEL, bool VAR, bool SMALL>
@@ -704,9 +715,9 @@ namespace hc {
 // partials and last-block ticket at caller-given device addresses instead of
 // the workspace.  Fails with HC_ERR_NOMEM when the launch would need more than
 // max_parts partial slots.
-template <int ACC, bool SMALL>
-static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
-                              unsigned* ticket, int max_parts, cudaStream_t st) {
+template <int ACC, bool SMALL, int PRED>
+static int launch_var_scratch_p(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
+                                unsigned* ticket, int max_parts, cudaStream_t st) {
   const DevStream s = dev_stream(h, d_stream);
   const int tb = kTileChunks * h->G;
   const int nseg = (h->S + 31) / 32;
@@ -715,7 +726,7 @@ static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scala
   const PipeTileSmem L =
       pipe_tile_smem(tb, stage, (!SMALL ? seg_moment_words(nsegmax, true) : 0) + order_words(nsegmax));
   const int bytes = 4 * L.total;
-  auto kern = k_reduce_stream<3, ACC, true, SMALL>;
+  auto kern = k_reduce_stream<3, ACC, true, SMALL, PRED>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
   if (rc) return rc;
   int per_sm = 0;
@@ -726,6 +737,15 @@ static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scala
   if (grid > max_parts) return fail(HC_ERR_NOMEM, "the static scratch of hc_op_variance_noalloc has too few partial slots for this GPU");
   kern<<<(unsigned)grid, kThreads, bytes, st>>>(s, ntiles, stage, parts, ticket, d_out, 2.0 * h->eps, nullptr);
   return check_launch_cfg("variance (static scratch)", reinterpret_cast<const void*>(kern), grid, bytes);
+}
+
+template <int ACC, bool SMALL>
+static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
+                              unsigned* ticket, int max_parts, cudaStream_t st) {
+  if (h->pred == HC_PRED_MEAN)
+    return launch_var_scratch_p<(ACC == 2 ? 2 : 1), SMALL, HC_PRED_MEAN>(h, d_stream, d_out, parts, ticket,
+                                                                          max_parts, st);
+  return launch_var_scratch_p<ACC, SMALL, HC_PRED_DELTA>(h, d_stream, d_out, parts, ticket, max_parts, st);
 }
 
 int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,

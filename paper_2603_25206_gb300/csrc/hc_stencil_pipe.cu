@@ -17,18 +17,18 @@ namespace hc {
 
 DevStream dev_stream(const hc_header* h, const void* d_stream);
 
-template <int OP, int OUT, int V>
+template <int OP, int OUT, int V, int PRED>
 __global__ void __launch_bounds__(kThreads) k_stencil_pipe(DevStream s, PGeo g, typename OT<OUT>::T* __restrict__ out,
                                                             int* err) {
   extern __shared__ __align__(16) unsigned char sm[];
   Moments mo;
-  pipe_tile<OP, OUT, V, false>(s, g, (int)(blockIdx.x % g.nyt), (int)(blockIdx.x / g.nyt), out, err, sm, mo);
+  pipe_tile<OP, OUT, V, false, PRED>(s, g, (int)(blockIdx.x % g.nyt), (int)(blockIdx.x / g.nyt), out, err, sm, mo);
 }
 
 // All operations of one field from one decode (ST_MULTI); with STATS the
 // exact sums of the codes go through the per-CTA partials and the last CTA
 // finishes the stage-3 statistics.
-template <int OUT, int V, bool STATS>
+template <int OUT, int V, bool STATS, int PRED>
 __global__ void __launch_bounds__(kThreads) k_stencil_multi(DevStream s, PGeo g, int* err, Partial* parts,
                                                              unsigned* ticket, hc_scalar* stats, double two_eps) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(kThreads) k_stencil_multi(DevStream s, PGeo g,
   if (threadIdx.x == 0) s_err = 0;
   __syncthreads();
   Moments mo;
-  pipe_tile<ST_MULTI, OUT, V, STATS>(s, g, (int)(blockIdx.x % g.nyt), (int)(blockIdx.x / g.nyt), nullptr, &s_err, sm,
-                                     mo);
+  pipe_tile<ST_MULTI, OUT, V, STATS, PRED>(s, g, (int)(blockIdx.x % g.nyt), (int)(blockIdx.x / g.nyt), nullptr,
+                                           &s_err, sm, mo);
   __syncthreads();
   const int e = s_err;
   if (threadIdx.x == 0 && e) set_error(err, e);
@@ -110,10 +110,10 @@ static void plan_pipe_grid(PGeo& g, int per_sm) {
   g.nzt = (int)ceil_div(g.n0, g.tz);
 }
 
-template <int OP, int OUT, int V>
-static int launch_pipe_o(const hc_header* h, const void* d_stream, PGeo g, int smem, void* d_out, int* err,
+template <int OP, int OUT, int V, int PRED>
+static int launch_pipe_p(const hc_header* h, const void* d_stream, PGeo g, int smem, void* d_out, int* err,
                          cudaStream_t st) {
-  auto kern = k_stencil_pipe<OP, OUT, V>;
+  auto kern = k_stencil_pipe<OP, OUT, V, PRED>;
   if (!plan_pipe_items(g, V)) return HC_ERR_UNSUPPORTED;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (rc) return rc;
@@ -124,6 +124,13 @@ static int launch_pipe_o(const hc_header* h, const void* d_stream, PGeo g, int s
   kern<<<(unsigned)grid, kThreads, smem, st>>>(dev_stream(h, d_stream), g,
                                                 reinterpret_cast<typename OT<OUT>::T*>(d_out), err);
   return check_launch_cfg("stencil (pipelined)", reinterpret_cast<const void*>(kern), grid, smem);
+}
+
+template <int OP, int OUT, int V>
+static int launch_pipe_o(const hc_header* h, const void* d_stream, const PGeo& g, int smem, void* d_out, int* err,
+                         cudaStream_t st) {
+  if (h->pred == HC_PRED_MEAN) return launch_pipe_p<OP, OUT, V, HC_PRED_MEAN>(h, d_stream, g, smem, d_out, err, st);
+  return launch_pipe_p<OP, OUT, V, HC_PRED_DELTA>(h, d_stream, g, smem, d_out, err, st);
 }
 
 template <int OP, int OUT>
@@ -237,10 +244,10 @@ static int stencil_pipe_launch(const hc_header* h, const void* d_stream, const i
 #undef HC_PIPE_OUT
 }
 
-template <int OUT, int V, bool STATS>
-static int launch_multi(const hc_header* h, const void* d_stream, PGeo g, int smem, hc_scalar* d_stats, void* d_ws,
-                        cudaStream_t st) {
-  auto kern = k_stencil_multi<OUT, V, STATS>;
+template <int OUT, int V, bool STATS, int PRED>
+static int launch_multi_p(const hc_header* h, const void* d_stream, PGeo g, int smem, hc_scalar* d_stats, void* d_ws,
+                          cudaStream_t st) {
+  auto kern = k_stencil_multi<OUT, V, STATS, PRED>;
   if (!plan_pipe_items(g, V)) return HC_ERR_UNSUPPORTED;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (rc) return rc;
@@ -259,6 +266,13 @@ static int launch_multi(const hc_header* h, const void* d_stream, PGeo g, int sm
   kern<<<(unsigned)grid, kThreads, smem, st>>>(dev_stream(h, d_stream), g, &ws->status, ws_partials(d_ws),
                                                 &ws->ticket, d_stats, 2.0 * h->eps);
   return check_launch_cfg("stencil (all operations)", reinterpret_cast<const void*>(kern), grid, smem);
+}
+
+template <int OUT, int V, bool STATS>
+static int launch_multi(const hc_header* h, const void* d_stream, const PGeo& g, int smem, hc_scalar* d_stats,
+                        void* d_ws, cudaStream_t st) {
+  if (h->pred == HC_PRED_MEAN) return launch_multi_p<OUT, V, STATS, HC_PRED_MEAN>(h, d_stream, g, smem, d_stats, d_ws, st);
+  return launch_multi_p<OUT, V, STATS, HC_PRED_DELTA>(h, d_stream, g, smem, d_stats, d_ws, st);
 }
 
 int stencil_multi_impl(const hc_header* h, const void* d_stream, void* const deriv3[3], void* d_grad, void* d_lap,

@@ -251,14 +251,15 @@ __device__ __forceinline__ void store_items(const PGeo& g, typename OT<OUT>::T* 
 // blockDim.x == kThreads.  sm: the dynamic shared memory (psmem(g).total
 // bytes).  With STATS the codes of the points the tile owns are added to mo.
 // OP = OUT = ST_RUNTIME takes the operation and output type from g; OP =
-// ST_MULTI writes every output of g.mout that is set (out is unused).
-template <int OP, int OUT, int V, bool STATS>
+// ST_MULTI writes every output of g.mout that is set (out is unused).  PRED:
+// the stream's hc_predictor (s.pred), fixed at compile time so that each
+// decoding loop stays as small as it can be.
+template <int OP, int OUT, int V, bool STATS, int PRED>
 __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int zt, typename OT<OUT>::T* out, int* err,
                                  unsigned char* sm, Moments& mo) {
   using T = typename OT<OUT>::T;
   const PSmem L = psmem(g);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool mean_pred = s.pred == HC_PRED_MEAN;
 
   const int64_t y0 = (int64_t)yt * g.ty, y1 = min(y0 + g.ty, g.n1);
   const int64_t z0 = (int64_t)zt * g.tz, z1 = min(z0 + g.tz, g.n0);
@@ -426,7 +427,7 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
           if (wi == 0) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = (short)q;
-          } else if (mean_pred) {
+          } else if constexpr (PRED == HC_PRED_MEAN) {
             // block mean (HSZx): q = M_b + p
             const uint32_t* blk = stg + off[seg];
             unpack_full(blk + 1, blk[0], wi, [&](int i, int32_t p) { v[i] = (short)(q + p); });
