@@ -61,6 +61,8 @@ def lib():
         L.orc_mean_m_sum.argtypes = [vp, i64, i32, i64, P(i64)]
         L.orc_mean_p_sum_x.argtypes = [vp, vp, i64, i32, P(i64)]
         L.orc_std_p_x.argtypes = [vp, vp, i64, i32, dbl, P(i64), P(ctypes.c_uint64), P(ctypes.c_uint64), P(dbl)]
+        L.orc_divergence_q.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.orc_curl2_q.argtypes = [vp, vp, vp, i32, i32, dbl, dbl, vp, vp]
         L.orc_read_header.argtypes = [vp, i64, vp, vp]
         for name in ("orc_decode_p", "orc_decode_q", "orc_decode_m", "orc_decode_f"):
             getattr(L, name).argtypes = [vp, i64, vp]
@@ -80,7 +82,7 @@ def lib():
                   L.orc_sums_q, L.orc_mean_p_sum, L.orc_var_p_sums, L.orc_finalize, L.orc_stats_f,
                   L.orc_deriv_q, L.orc_lap_q, L.orc_stencil_q, L.orc_stencil_f, L.orc_stencil_at,
                   L.orc_compress_pred, L.orc_compress_codes_pred, L.orc_mean_m_sum, L.orc_mean_p_sum_x,
-                  L.orc_std_p_x):
+                  L.orc_std_p_x, L.orc_divergence_q, L.orc_curl2_q):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -298,6 +300,35 @@ def stencil_q(q: np.ndarray, kind: int, eps: float, axis: int = 0) -> np.ndarray
     out = np.empty(q.shape, np.float64)
     _check(lib().orc_stencil_q(_ptr(q), _ptr(d), kind, axis + 3 - q.ndim, eps, _ptr(out)), "stencil_q")
     return out
+
+
+def divergence_q(qs, eps):
+    """Divergence of the vector field whose components (same shape, ndim
+    components) are the code arrays qs, component c differentiated along user
+    axis c: (integer numerators, values)."""
+    qs = [np.ascontiguousarray(q, dtype=np.int32) for q in qs]
+    nd = qs[0].ndim
+    d = dims3(qs[0].shape)
+    axes = np.array([c + 3 - nd for c in range(len(qs))], np.int32)
+    ptrs = (ctypes.c_void_p * len(qs))(*[q.ctypes.data for q in qs])
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    num = np.empty(qs[0].shape, np.int64)
+    val = np.empty(qs[0].shape, np.float64)
+    _check(lib().orc_divergence_q(ptrs, len(qs), _ptr(d), _ptr(axes), _ptr(e), _ptr(num), _ptr(val)),
+           "divergence_q")
+    return num, val
+
+
+def curl2_q(qu, qv, eps_u, eps_v):
+    """Curl of a 2-D field (u, v): (integer numerators, values)."""
+    qu = np.ascontiguousarray(qu, dtype=np.int32)
+    qv = np.ascontiguousarray(qv, dtype=np.int32)
+    assert qu.ndim == 2 and qu.shape == qv.shape
+    d = dims3(qu.shape)
+    num = np.empty(qu.shape, np.int64)
+    val = np.empty(qu.shape, np.float64)
+    _check(lib().orc_curl2_q(_ptr(qu), _ptr(qv), _ptr(d), 1, 2, eps_u, eps_v, _ptr(num), _ptr(val)), "curl2_q")
+    return num, val
 
 
 def stencil_f(f: np.ndarray, kind: int, axis: int = 0) -> np.ndarray:

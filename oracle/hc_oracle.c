@@ -839,6 +839,51 @@ int orc_deriv_q(const int32_t *q, const int64_t *dims3, int axis, int64_t *D) {
   return ORC_OK;
 }
 
+/* Divergence of a vector field (Section V-C, "Multivariate Derivation",
+ * Eq. divergence on D_q): component c differentiated along internal axis
+ * axes[c] with the derivative numerators above; num = sum_c D_c.  The value
+ * is num * eps when every component has the same eps (the paper's form);
+ * otherwise (reading: components quantized with different bounds) each term
+ * carries its own eps, sum_c eps_c D_c in component order. */
+int orc_divergence_q(const int32_t *const *q, int ncomp, const int64_t *d, const int *axes, const double *eps,
+                     int64_t *num, double *val) {
+  if (ncomp < 1 || ncomp > 3) return ORC_ERR_INVALID_ARG;
+  int same = 1;
+  for (int c = 1; c < ncomp; c++) same &= eps[c] == eps[0];
+  for (int64_t i0 = 0; i0 < d[0]; i0++)
+    for (int64_t i1 = 0; i1 < d[1]; i1++)
+      for (int64_t i2 = 0; i2 < d[2]; i2++) {
+        int64_t n = 0;
+        double v = 0.0;
+        for (int c = 0; c < ncomp; c++) {
+          int64_t D = deriv_num(q[c], d, i0, i1, i2, axes[c]);
+          n += D;
+          v += (double)D * eps[c];
+        }
+        num[idx3(d, i0, i1, i2)] = n;
+        val[idx3(d, i0, i1, i2)] = same ? (double)n * eps[0] : v;
+      }
+  return ORC_OK;
+}
+
+/* Curl of a 2-D field F = (u, v) (Section V-C, Eq. curl on D_q): with i the
+ * first and j the second index, (q^u_{i,j+1} - q^u_{i,j-1}) - (q^v_{i+1,j} -
+ * q^v_{i-1,j}), times eps; axis_i / axis_j are the internal axes of i and j.
+ * The same edge rule and the same reading for different bounds as the
+ * divergence. */
+int orc_curl2_q(const int32_t *qu, const int32_t *qv, const int64_t *d, int axis_i, int axis_j, double eps_u,
+                double eps_v, int64_t *num, double *val) {
+  for (int64_t i0 = 0; i0 < d[0]; i0++)
+    for (int64_t i1 = 0; i1 < d[1]; i1++)
+      for (int64_t i2 = 0; i2 < d[2]; i2++) {
+        int64_t du = deriv_num(qu, d, i0, i1, i2, axis_j);
+        int64_t dv = deriv_num(qv, d, i0, i1, i2, axis_i);
+        num[idx3(d, i0, i1, i2)] = du - dv;
+        val[idx3(d, i0, i1, i2)] = eps_u == eps_v ? (double)(du - dv) * eps_u : (double)du * eps_u - (double)dv * eps_v;
+      }
+  return ORC_OK;
+}
+
 /* integer Laplacian numerator at one point (replicated edges) */
 static int64_t lap_num(const int32_t *q, const int64_t *d, int64_t i0, int64_t i1, int64_t i2) {
   int64_t c[3] = {i0, i1, i2};

@@ -522,3 +522,52 @@ def test_hszx_statistics_stage_forms(orc, rng, S):
     s2 = int((q * q).sum())
     _, var, sd = orc.finalize(n, s1, s2, eps)
     assert abs(sigma - sd) <= 2 * eps * (math.sqrt(n / (n - 1)) * 0.5 + 0.5) + 1e-12
+
+
+# ------------------------------------------------------- divergence and curl
+@pytest.mark.parametrize("shape", [(9, 11), (5, 6, 7), (2, 40), (1, 8, 3)])
+def test_divergence_equals_library_gradients(orc, rng, shape):
+    """Section V-C: the divergence is the sum of each component's derivative
+    along its own axis; on D_f = 2 eps q it equals numpy.gradient (first-order
+    edges) summed over the components, with a common or a per-component eps."""
+    qs = [rng.integers(-500, 500, size=shape).astype(np.int32) for _ in shape]
+    for eps in ([0.01] * len(shape), [0.01 * (c + 1) for c in range(len(shape))]):
+        num, val = orc.divergence_q(qs, eps)
+        ref = np.zeros(shape)
+        ref_num = np.zeros(shape, np.int64)
+        for c, q in enumerate(qs):
+            g = np.zeros(shape) if shape[c] < 2 else np.gradient(q.astype(np.float64) * 2 * eps[c], axis=c, edge_order=1)
+            ref += g
+            ref_num += orc.deriv_q(q, c)
+        np.testing.assert_array_equal(num, ref_num)
+        np.testing.assert_allclose(val, ref, rtol=1e-12, atol=1e-12)
+        if len(set(eps)) == 1:
+            np.testing.assert_array_equal(val, num.astype(np.float64) * eps[0])
+
+
+def test_divergence_and_curl_closed_forms(orc):
+    """u = a i, v = b j (codes): divergence 2 (a + b) eps everywhere (centred
+    and one-sided differences are exact on linear fields) and curl 0; u = c j,
+    v = d i: curl 2 (c - d) eps and divergence 0."""
+    n1, n2 = 7, 9
+    i = np.arange(n1)[:, None] * np.ones((1, n2), np.int64)
+    j = np.ones((n1, 1), np.int64) * np.arange(n2)[None, :]
+    a, b, c, d = 3, -5, 4, 7
+    num, val = orc.divergence_q([(a * i).astype(np.int32), (b * j).astype(np.int32)], [0.5, 0.5])
+    assert np.all(num == 2 * (a + b)) and np.all(val == 2 * (a + b) * 0.5)
+    num, val = orc.curl2_q((a * i).astype(np.int32), (b * j).astype(np.int32), 0.5, 0.5)
+    assert np.all(num == 0)
+    num, val = orc.curl2_q((c * j).astype(np.int32), (d * i).astype(np.int32), 0.5, 0.5)
+    assert np.all(num == 2 * (c - d)) and np.all(val == 2 * (c - d) * 0.5)
+    num, val = orc.divergence_q([(c * j).astype(np.int32), (d * i).astype(np.int32)], [0.5, 0.5])
+    assert np.all(num == 0)
+
+
+def test_curl_equals_library_gradients(orc, rng):
+    qu = rng.integers(-300, 300, size=(12, 10)).astype(np.int32)
+    qv = rng.integers(-300, 300, size=(12, 10)).astype(np.int32)
+    for eu, ev in ((0.02, 0.02), (0.02, 0.07)):
+        num, val = orc.curl2_q(qu, qv, eu, ev)
+        ref = np.gradient(qu * 2 * eu, axis=1, edge_order=1) - np.gradient(qv * 2 * ev, axis=0, edge_order=1)
+        np.testing.assert_allclose(val, ref, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(num, orc.deriv_q(qu, 1) - orc.deriv_q(qv, 0))
