@@ -255,6 +255,25 @@ HC_API int hc_op_gradmag(const hc_stage* in, double eps, int ndim, const int64_t
 HC_API int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64_t* dims, void* d_out, int out_dtype,
                     void* d_ws, size_t ws_bytes, void* stream);
 
+/* Divergence and curl of a vector field (Section V-C, "Multivariate
+ * Derivation"), stage Q, fused: one compressed stream per component, all of
+ * the same shape and block size, each read straight from its stream.
+ *   hc_op_divergence: ncomp == ndim components; component c is
+ *     differentiated along user axis c; value = (sum_c D_c) eps.
+ *   hc_op_curl: a 2-D field (u, v), ncomp == 2; with i the first and j the
+ *     second index, value = (D_u along j - D_v along i) eps.
+ * D is the derivative numerator of hc_op_derivative (one-sided and doubled at
+ * an edge).  Components quantized with different eps are scaled one by one,
+ * sum_c eps_c D_c in double (the paper assumes one eps); an HC_I64 output
+ * (the exact integer numerator) needs one eps for all components.
+ *   comps: ncomp HC_STAGE_COMPRESSED stages at level HC_STAGE_Q.
+ *   d_out: N outputs of out_dtype (HC_F32, HC_F64 or HC_I64), 16-byte aligned.
+ * Rows longer than about a million codes are HC_ERR_UNSUPPORTED.  ASYNC. */
+HC_API int hc_op_divergence(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out,
+                            int out_dtype, void* d_ws, size_t ws_bytes, void* stream);
+HC_API int hc_op_curl(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+                      void* d_ws, size_t ws_bytes, void* stream);
+
 /* All operations of one field in one pass ("decompress once, many ops",
  * Section VI's remark that a decompressed representation serves several
  * analyses).  Fused on a stream input (level Q): the codes are decoded once

@@ -477,6 +477,42 @@ int hc_op_multi(const hc_stage* in, double eps, int ndim, const int64_t* dims, c
   return HC_OK;
 }
 
+static int vector_op(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+                     void* d_ws, size_t ws_bytes, void* stream, int op) {
+  if (!comps || !d_out) return fail(HC_ERR_INVALID_ARG, "null pointer");
+  if (op == 0 && ncomp != ndim) return fail(HC_ERR_INVALID_ARG, "divergence takes ndim components");
+  if (op == 1 && (ndim != 2 || ncomp != 2)) return fail(HC_ERR_UNSUPPORTED, "curl is defined here for 2-D fields");
+  if (ncomp < 1 || ncomp > 3) return fail(HC_ERR_INVALID_ARG, "ncomp");
+  if (!aligned16(d_out)) return fail(HC_ERR_INVALID_ARG, "output must be a 16-byte aligned device buffer");
+  if (out_dtype != HC_F32 && out_dtype != HC_F64 && out_dtype != HC_I64) return fail(HC_ERR_INVALID_ARG, "out_dtype");
+  const hc_header* hs[3];
+  const void* ds[3];
+  for (int c = 0; c < ncomp; ++c) {
+    const hc_stage& in = comps[c];
+    if (in.kind != HC_STAGE_COMPRESSED || !in.hdr)
+      return fail(HC_ERR_UNSUPPORTED, "vector operations take compressed streams");
+    if (in.level != HC_STAGE_Q)
+      return fail(HC_ERR_UNSUPPORTED, "vector operations on a 1-D block partition run at stage Q (Section V-C)");
+    int64_t dims3[3];
+    int rc = check_op(&in, in.hdr->eps, ndim, dims, d_ws, ws_bytes, dims3);
+    if (rc) return rc;
+    if (in.hdr->S != comps[0].hdr->S) return fail(HC_ERR_UNSUPPORTED, "components must share the block size");
+    hs[c] = in.hdr;
+    ds[c] = in.d_data;
+  }
+  return vector_stream_impl(hs, ds, ncomp, op, d_out, out_dtype, d_ws, as_stream(stream));
+}
+
+int hc_op_divergence(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+                     void* d_ws, size_t ws_bytes, void* stream) {
+  return vector_op(comps, ncomp, ndim, dims, d_out, out_dtype, d_ws, ws_bytes, stream, 0);
+}
+
+int hc_op_curl(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out, int out_dtype,
+               void* d_ws, size_t ws_bytes, void* stream) {
+  return vector_op(comps, ncomp, ndim, dims, d_out, out_dtype, d_ws, ws_bytes, stream, 1);
+}
+
 size_t hc_batch_plan_bytes(int n_items) { return (size_t)batch_plan_bytes(n_items); }
 size_t hc_batch_workspace_bytes(int n_items) { return (size_t)batch_ws_bytes(n_items); }
 int hc_batch_plan(const hc_batch_item* items, int n_items, const hc_batch_tune* tune, void* h_plan, size_t cap,

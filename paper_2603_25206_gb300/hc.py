@@ -42,7 +42,7 @@ ABI_FUNCTIONS = (
     "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc", "hc_autotune",
     "hc_batch_plan_bytes", "hc_batch_workspace_bytes", "hc_batch_plan", "hc_batch_run", "hc_batch_graph_create",
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
-    "hc_compress_codes_ex",
+    "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl",
 )
 HC_PRED_DELTA, HC_PRED_MEAN = 0, 1
 PREDICTORS = {"delta": HC_PRED_DELTA, "mean": HC_PRED_MEAN}
@@ -144,6 +144,8 @@ def lib():
             "hc_op_laplacian": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_autotune": ([P(HcStage), i32, i32, vp, vp, sz, vp, P(ctypes.c_int)], i32),
             "hc_op_multi": ([P(HcStage), dbl, i32, P(ctypes.c_int64), P(HcMultiOut), vp, sz, vp], i32),
+            "hc_op_divergence": ([P(HcStage), i32, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
+            "hc_op_curl": ([P(HcStage), i32, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_batch_plan_bytes": ([i32], sz),
             "hc_batch_workspace_bytes": ([i32], sz),
             "hc_batch_plan": ([P(HcBatchItem), i32, P(HcBatchTune), vp, sz, P(sz)], i32),
@@ -451,6 +453,31 @@ def multi(inp, derivative=True, gradmag=True, laplacian=True, stats=True, out_dt
     _check(lib().hc_op_multi(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.byref(mo),
                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return outs
+
+
+def _vector(fn, comps, out_dtype, out, stream):
+    torch = _torch()
+    arr = (HcStage * len(comps))()
+    for k, c in enumerate(comps):
+        arr[k] = c.stage("q")
+    shape = comps[0].shape
+    dev = comps[0].stream.device
+    out = _field_out(shape, out_dtype, dev, out)
+    ws = workspace(dev, stream)
+    _check(getattr(lib(), fn)(arr, len(comps), len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
+                              _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return out
+
+
+def divergence(comps, out_dtype: str = "float32", out=None, stream=None):
+    """Divergence of the vector field whose components are the compressed
+    fields `comps` (one per axis, same shape and block size)."""
+    return _vector("hc_op_divergence", comps, out_dtype, out, stream)
+
+
+def curl(comps, out_dtype: str = "float32", out=None, stream=None):
+    """Curl of a 2-D vector field (u, v) given as two compressed fields."""
+    return _vector("hc_op_curl", comps, out_dtype, out, stream)
 
 
 def workspace_status(stream=None) -> int:

@@ -222,3 +222,20 @@ def test_multi_argument_errors_before_any_cuda_call(hc):
     mo.d_laplacian = 20  # unaligned
     assert L.hc_op_multi(ctypes.byref(st), 1e-3, 1, dims, ctypes.byref(mo), ws, L.hc_workspace_bytes(),
                          None) == hc.HC_ERR_INVALID_ARG
+
+
+def test_vector_argument_errors_before_any_cuda_call(hc):
+    L = hc.lib()
+    dims = (ctypes.c_int64 * 3)(10, 12, 1)
+    comps = (hc.HcStage * 2)()
+    ws = ctypes.c_void_p(16)
+    assert L.hc_op_divergence(None, 2, 2, dims, ctypes.c_void_p(16), hc.HC_F32, ws, L.hc_workspace_bytes(),
+                              None) == hc.HC_ERR_INVALID_ARG
+    assert L.hc_op_divergence(comps, 1, 2, dims, ctypes.c_void_p(16), hc.HC_F32, ws, L.hc_workspace_bytes(),
+                              None) == hc.HC_ERR_INVALID_ARG
+    assert L.hc_op_curl(comps, 2, 3, dims, ctypes.c_void_p(16), hc.HC_F32, ws, L.hc_workspace_bytes(),
+                        None) == hc.HC_ERR_UNSUPPORTED
+    # arrays instead of streams
+    comps[0].kind = comps[1].kind = hc.HC_STAGE_Q
+    assert L.hc_op_divergence(comps, 2, 2, dims, ctypes.c_void_p(16), hc.HC_F32, ws, L.hc_workspace_bytes(),
+                              None) == hc.HC_ERR_UNSUPPORTED
