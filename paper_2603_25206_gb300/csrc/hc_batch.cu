@@ -56,7 +56,7 @@ struct BItem {
   int stats;           // STATS_*
   int rwords;          // statistics unit: words of the decoded D_q tile
   int kind;            // KIND_*
-  int vec;             // KIND_PIPE: outputs per work item (8, 4 or 1)
+  int vec;             // KIND_PIPE: outputs per work item of the pipelined tile (8, 4 or 1)
 };
 
 struct BPlan {
@@ -130,12 +130,29 @@ __device__ __noinline__ void pipe_unit(const BItem& it, int64_t lu, int* err, un
                                                   it.field, err, smem, mo);
 }
 
+// The float32 Laplacian (the batched workload's field operation) with its
+// operation and type fixed at compile time; other operations take the
+// run-time switch of pipe_unit.
+template <int V, int PRED>
+__device__ __noinline__ void pipe_unit_lap(const BItem& it, int64_t lu, int* err, unsigned char* smem, Moments& mo) {
+  pipe_tile<ST_LAPLACIAN, HC_F32, V, true, PRED>(it.s, it.pg, (int)(lu % it.pg.nyt), (int)(lu / it.pg.nyt),
+                                                 reinterpret_cast<float*>(it.field), err, smem, mo);
+}
+
 template <int V>
 __device__ __forceinline__ void pipe_unit_p(const BItem& it, int64_t lu, int* err, unsigned char* smem, Moments& mo) {
-  if (it.s.pred == HC_PRED_MEAN)
-    pipe_unit<V, HC_PRED_MEAN>(it, lu, err, smem, mo);
-  else
-    pipe_unit<V, HC_PRED_DELTA>(it, lu, err, smem, mo);
+  const bool lap = it.pg.op == ST_LAPLACIAN && it.pg.out == HC_F32;
+  if (it.s.pred == HC_PRED_MEAN) {
+    if (lap)
+      pipe_unit_lap<V, HC_PRED_MEAN>(it, lu, err, smem, mo);
+    else
+      pipe_unit<V, HC_PRED_MEAN>(it, lu, err, smem, mo);
+  } else {
+    if (lap)
+      pipe_unit_lap<V, HC_PRED_DELTA>(it, lu, err, smem, mo);
+    else
+      pipe_unit<V, HC_PRED_DELTA>(it, lu, err, smem, mo);
+  }
 }
 
 // CTA sum of the unit's moments into the field accumulator; the field's last
@@ -190,8 +207,11 @@ __device__ void publish(const BItem& it, const Moments& mo, BAcc* a, int* status
   }
 }
 
+// Resident CTAs per SM assumed for the register budget: the tiles' shared
+// memory (tens of KB) allows about two 256-thread CTAs per SM, so more than
+// that would only force spills.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 512 ? 1 : 768 / THREADS) k_batch(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 ? 2 : 1)) k_batch(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_warp[32];
   __shared__ int s_flag;
@@ -378,6 +398,9 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
       b.kind = KIND_TILE;
       if (threads == kThreads && aligned16(x.d_field) && d3[1] * d3[2] < ((int64_t)1 << 31) &&
           plan_pipe_geometry(&h, d3, b.pg, &sm, ty_force, ty_force ? 200 * 1024 : 74 * 1024)) {
+        // rows of other lengths: one output per item (measured faster inside
+        // the batched kernel than the unaligned 8-wide items, whose code and
+        // registers the persistent kernel would carry for every unit)
         b.vec = d3[2] % 8 == 0 ? 8 : (d3[2] % 4 == 0 ? 4 : 1);
         if (plan_pipe_items(b.pg, b.vec)) {
           b.kind = KIND_PIPE;

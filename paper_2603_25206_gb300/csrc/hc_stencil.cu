@@ -295,8 +295,8 @@ int stencil_stream_impl(const hc_header* h, const void* d_stream, int op, int ax
   // a 2-D field marches along its rows: (1, n1, n2) is walked as (n1, 1, n2)
   int64_t d3[3];
   stencil_walk_dims(h, d3, &axis3);
-  // the pipelined kernel covers block size 32 with rows of a multiple of 8
-  // codes and |q| < 2^15; everything else takes the general kernel below
+  // the pipelined kernel covers block size 32 and |q| < 2^15 (rows of any
+  // length); everything else takes the general kernel below
   static const bool force_general = std::getenv("HC_FORCE_GENERAL_STENCIL") != nullptr;
   if (!force_general) {
     const int rc = stencil_pipe_impl(h, d_stream, d3, op, axis3, d_out, out_dtype, d_ws, st);

@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kThreads) k_stencil_multi(DevStream s, PGeo g,
 
 // ------------------------------------------------------------------ host
 // The fast path applies when: S = 32, |q| < 2^15, the output is 16-byte
-// aligned, and a tile of at least one row fits the shared-memory budget.  The
+// aligned, and a tile of at least one row fits the shared-memory budget (rows
+// of any length: 8-wide items, vector ones when the row length allows).  The
 // tile height is the largest that keeps at least three CTAs per SM; the plane
 // ranges are sized so that the grid fills whole waves of resident CTAs.
 bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* smem_out, int force_ty, int budget) {
@@ -85,8 +86,10 @@ bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* sme
 }
 
 bool plan_pipe_items(PGeo& g, int V) {
-  if (g.n2 % V != 0) return false;
-  g.nq = (int)(g.n2 / V);
+  // V = 0: items of 8 at any offset plus a scalar tail (rows of any length)
+  const int vw = V == 0 ? 8 : V;
+  if (V != 0 && g.n2 % V != 0) return false;
+  g.nq = (int)(g.n2 / vw);
   if (g.nq <= 1) {
     g.nq_magic = 0u;
     return true;
@@ -138,7 +141,7 @@ static int launch_pipe_v(const hc_header* h, const void* d_stream, const PGeo& g
                          cudaStream_t st) {
   if (g.n2 % 8 == 0) return launch_pipe_o<OP, OUT, 8>(h, d_stream, g, smem, d_out, err, st);
   if (g.n2 % 4 == 0) return launch_pipe_o<OP, OUT, 4>(h, d_stream, g, smem, d_out, err, st);
-  return HC_ERR_UNSUPPORTED;
+  return launch_pipe_o<OP, OUT, 0>(h, d_stream, g, smem, d_out, err, st);
 }
 
 // Returns HC_ERR_UNSUPPORTED (without recording an error) when the fast path
@@ -296,21 +299,24 @@ int stencil_multi_impl(const hc_header* h, const void* d_stream, void* const der
   g.eps_f = (float)h->eps;
   g.te_f = (float)(2.0 * h->eps);
   const int v = g.n2 % 8 == 0 ? 8 : (g.n2 % 4 == 0 ? 4 : 0);
-  if (!v) return HC_ERR_UNSUPPORTED;
 #define HC_MULTI(OUTT, VV)                                                                                  \
   return d_stats ? launch_multi<OUTT, VV, true>(h, d_stream, g, smem, d_stats, d_ws, st)                    \
                  : launch_multi<OUTT, VV, false>(h, d_stream, g, smem, d_stats, d_ws, st);
   if (out_dtype == HC_F32) {
     if (v == 8) {
       HC_MULTI(HC_F32, 8)
-    } else {
+    } else if (v == 4) {
       HC_MULTI(HC_F32, 4)
+    } else {
+      HC_MULTI(HC_F32, 0)
     }
   } else {
     if (v == 8) {
       HC_MULTI(HC_F64, 8)
-    } else {
+    } else if (v == 4) {
       HC_MULTI(HC_F64, 4)
+    } else {
+      HC_MULTI(HC_F64, 0)
     }
   }
 #undef HC_MULTI

@@ -14,8 +14,9 @@
 //                     plane of slab k-2);
 //            one __syncthreads.
 // Buffers: 4 ring slots, 3 payload stages, 4 metadata buffers.  A work item
-// is V = 8 (rows a multiple of 8), V = 4 (a multiple of 4) or V = 1 (any row
-// length) consecutive outputs of one row.
+// is V = 8 (rows a multiple of 8) or V = 4 (a multiple of 4) consecutive
+// outputs of one row, or for rows of any length (V = 0) 8 outputs at any
+// offset with unaligned loads, and the rows' last n2 % 8 outputs one by one.
 // Decoded codes are stored as int16, a 32-code segment as 64 contiguous
 // bytes: a decoding thread writes its segment with four 16-byte stores and a
 // stencil thread reads V consecutive codes of a row with one load
@@ -36,9 +37,12 @@ constexpr int kSlots = 4;
 constexpr int kWorkerWarps = kWorkers / 32;
 // Estimated thread instructions per decoded code and per output point (from
 // ncu instruction counts of the kernels): decoding costs about 25 per code,
-// a point about as much for one operation and about 100 for all of them.
+// a point about as much for one operation, about 40 with the run-time
+// operation dispatch and exact sums of the batched tiles, and about 100 for
+// all operations.
 constexpr int kDecodeCost = 25;
 constexpr int kPointCost = 25;
+constexpr int kPointCostRuntime = 40;  // run-time operation dispatch plus the exact sums (batched tiles)
 constexpr int kPointCostMulti = 100;
 
 
@@ -137,8 +141,9 @@ __device__ __forceinline__ SlabDesc slab_desc(const DevStream& s, const PGeo& g,
 
 // The V outputs of one work item from their neighbourhoods (compile-time
 // operation O and output type D), written with vector stores when they fill
-// 16 bytes.  cm / cp are the x neighbours of the first / last point.
-template <int O, int D, int V>
+// 16 bytes and AL (the item's first output is aligned to its size).  cm / cp
+// are the x neighbours of the first / last point.
+template <int O, int D, int V, bool AL>
 __device__ __forceinline__ void emit_items(const PGeo& g, typename OT<D>::T* o, const short* c, const short* a,
                                            const short* b, const short* zmv, const short* zpv, int xl, int xr,
                                            int ex0, int exn, int ez, int ey) {
@@ -165,7 +170,7 @@ __device__ __forceinline__ void emit_items(const PGeo& g, typename OT<D>::T* o, 
         res[i] = emit1<O, D>(d0, d1, d2, g);
     }
   }
-  if constexpr (V * sizeof(T) >= 16) {
+  if constexpr (AL && V * sizeof(T) >= 16) {
 #pragma unroll
     for (int v = 0; v < (int)(V * sizeof(T) / 16); ++v)
       reinterpret_cast<uint4*>(o)[v] = reinterpret_cast<const uint4*>(res)[v];
@@ -178,7 +183,7 @@ __device__ __forceinline__ void emit_items(const PGeo& g, typename OT<D>::T* o, 
 // ST_MULTI: every wanted output of the V points from one neighbourhood (one
 // decode serves all operations), output by output so that only V results are
 // live at a time.
-template <int D, int V>
+template <int D, int V, bool AL>
 __device__ __forceinline__ void emit_multi(const PGeo& g, int64_t i0, const short* c, const short* a,
                                            const short* b, const short* zmv, const short* zpv, int xl, int xr,
                                            int ex0, int exn, int ez, int ey) {
@@ -204,7 +209,7 @@ __device__ __forceinline__ void emit_multi(const PGeo& g, int64_t i0, const shor
         res[i] = emit1<ST_LAPLACIAN, D>((int)zmv[i] + zpv[i] + a[i] + b[i] + cm + cp - 6 * (int)c[i], 0, 0, g);
     }
     o += i0;
-    if constexpr (V * sizeof(T) >= 16) {
+    if constexpr (AL && V * sizeof(T) >= 16) {
 #pragma unroll
       for (int v = 0; v < (int)(V * sizeof(T) / 16); ++v)
         reinterpret_cast<uint4*>(o)[v] = reinterpret_cast<const uint4*>(res)[v];
@@ -217,15 +222,15 @@ __device__ __forceinline__ void emit_multi(const PGeo& g, int64_t i0, const shor
 
 // Compile-time operation and type, or (ST_RUNTIME) the run-time switch over
 // both; out + i0 is the item's first output.
-template <int OP, int OUT, int V>
+template <int OP, int OUT, int V, bool AL>
 __device__ __forceinline__ void store_items(const PGeo& g, typename OT<OUT>::T* out, int64_t i0, const short* c,
                                             const short* a, const short* b, const short* zmv, const short* zpv,
                                             int xl, int xr, int ex0, int exn, int ez, int ey) {
   if constexpr (OP == ST_RUNTIME) {
 #define HC_PIPE_RT(O, D)                                                                                            \
   case O * 4 + D:                                                                                                   \
-    emit_items<O, D, V>(g, reinterpret_cast<typename OT<D>::T*>(out) + i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, \
-                        ey);                                                                                        \
+    emit_items<O, D, V, AL>(g, reinterpret_cast<typename OT<D>::T*>(out) + i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, \
+                            ez, ey);                                                                                \
     break;
     switch (g.op * 4 + g.out) {
       HC_PIPE_RT(ST_DERIV, HC_F32)
@@ -241,10 +246,71 @@ __device__ __forceinline__ void store_items(const PGeo& g, typename OT<OUT>::T* 
     }
 #undef HC_PIPE_RT
   } else if constexpr (OP == ST_MULTI) {
-    emit_multi<OUT, V>(g, i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
+    emit_multi<OUT, V, AL>(g, i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
   } else {
-    emit_items<OP, OUT, V>(g, out + i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
+    emit_items<OP, OUT, V, AL>(g, out + i0, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
   }
+}
+
+// W consecutive int16 codes at element offset e of slot `base` (a 64-byte
+// aligned shared-memory slot): one vector load when AL (e a multiple of W),
+// else (W = 8, any e) five 32-bit loads from the word holding code e and a
+// byte permute per output word.  The address stays a shared-memory pointer
+// (base plus an offset), so the loads are shared-memory loads.  The reads may
+// reach 4 bytes past the codes; the ring is followed by the staging and
+// metadata buffers, so they stay inside the shared memory of the tile.
+template <int W, bool AL>
+__device__ __forceinline__ void load_codes(short* dst, const short* base, int e) {
+  if constexpr (AL) {
+    using Vec = typename std::conditional<W == 8, uint4, typename std::conditional<W == 4, uint2, unsigned short>::type>::type;
+    *reinterpret_cast<Vec*>(dst) = *reinterpret_cast<const Vec*>(base + e);
+  } else {
+    static_assert(W == 8, "unaligned items are 8 codes wide");
+    const uint32_t* wp = reinterpret_cast<const uint32_t*>(base) + (e >> 1);
+    const uint32_t sel = (e & 1) ? 0x5432u : 0x3210u;
+    uint32_t w[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = wp[k];
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k] = __byte_perm(w[k], w[k + 1], sel);
+  }
+}
+
+// One work item: the W outputs x .. x + W - 1 of row y0 + yr of plane z (slots
+// pc / pm / pp hold planes z, z - 1, z + 1; rc0 / rm0 / rp0 are the element
+// offsets of row y0 in them; row0 its element index in the field).
+template <int OP, int OUT, int W, bool AL, bool STATS>
+__device__ __forceinline__ void pipe_item(const PGeo& g, typename OT<OUT>::T* out, const short* pc, const short* pm,
+                                          const short* pp, int rc0, int rm0, int rp0, int64_t row0, int64_t y0,
+                                          int yr, int x, int n2, int ez, Moments& mo) {
+  const int roff = yr * n2 + x;
+  const int rc = rc0 + roff;
+  const int64_t y = y0 + yr;
+  const int ey = (y == 0 || y == g.n1 - 1) ? 2 : 1;
+  const int eop = OP == ST_RUNTIME ? g.op : OP;
+  short c[W], a[W], b[W], zmv[W], zpv[W];
+  load_codes<W, AL>(c, pc, rc);
+  if (eop != ST_DERIV || g.axis == 1) {
+    load_codes<W, AL>(a, pc, y > 0 ? rc - n2 : rc);
+    load_codes<W, AL>(b, pc, y + 1 < g.n1 ? rc + n2 : rc);
+  }
+  if (eop != ST_DERIV || g.axis == 0) {
+    load_codes<W, AL>(zmv, pm, rm0 + roff);
+    load_codes<W, AL>(zpv, pp, rp0 + roff);
+  }
+  int xl = c[0], xr = c[W - 1];
+  if (eop != ST_DERIV || g.axis == 2) {
+    if (x > 0) xl = pc[rc - 1];
+    if (x + W < n2) xr = pc[rc + W];
+  }
+  // one-sided differences at the row ends are doubled
+  const int ex0 = x == 0 ? 2 : 1, exn = x + W == n2 ? 2 : 1;
+  if (STATS) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) mo.add((int32_t)c[i]);
+  }
+  store_items<OP, OUT, W, AL>(g, out, row0 + roff, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
 }
 
 // One tile (row tile yt, plane range zt) of the pipelined stencil; needs
@@ -258,6 +324,9 @@ template <int OP, int OUT, int V, bool STATS, int PRED>
 __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int zt, typename OT<OUT>::T* out, int* err,
                                  unsigned char* sm, Moments& mo) {
   using T = typename OT<OUT>::T;
+  // V = 8 / 4: items of V outputs, rows a multiple of V; V = 0: items of 8
+  // outputs at any offset (unaligned loads, scalar stores) plus a scalar tail
+  constexpr int VW = V == 0 ? 8 : V;
   const PSmem L = psmem(g);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -393,9 +462,14 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
       while (zc1 < z1 && min(zc1 + 1, g.n0 - 1) <= ready) ++zc1;
       const int nplanes = (int)(zc1 - znext);
       const int nseg_k = k < nslab ? slab_desc(s, g, zs + k, ylo, yhi).nblk : 0;
-      const int items = (int)(y1 - y0) * g.nq;
+      // full items of VW outputs, then (V = 0: rows of any length) the
+      // n2 % 8 trailing outputs of every row one by one
+      const int nfull = (int)(y1 - y0) * g.nq;
+      const int tail = V == 0 ? (int)g.n2 - g.nq * VW : 0;
+      const int items = nfull + (int)(y1 - y0) * tail;
       const long long dec_cost = (long long)kDecodeCost * 32 * nseg_k;
-      const long long comp_cost = (long long)(OP == ST_MULTI ? kPointCostMulti : kPointCost) * V * nplanes * items;
+      const int point_cost = OP == ST_MULTI ? kPointCostMulti : (OP == ST_RUNTIME || STATS ? kPointCostRuntime : kPointCost);
+      const long long comp_cost = (long long)point_cost * nplanes * (int)(y1 - y0) * g.n2;
       int ndw = kWorkerWarps;
       if (comp_cost == 0)
         ndw = kWorkerWarps;
@@ -463,37 +537,18 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
         const int rp0 = (int)((zp * g.n1 + y0) * g.n2 - (slab_desc(s, g, zp, ylo, yhi).b0 << 5));
         const int n2 = (int)g.n2;
         const int ez = (z == 0 || z == g.n0 - 1) ? 2 : 1;
-        using Vec = typename std::conditional<V == 8, uint4,
-                                              typename std::conditional<V == 4, uint2, unsigned short>::type>::type;
         for (int it = wt; it < items; it += wstride) {
-          const int yr = g.nq == 1 ? it : (int)__umulhi((unsigned)it, g.nq_magic);
-          const int x = (it - yr * g.nq) * V;
-          const int roff = yr * n2 + x;
-          const int rc = rc0 + roff;
-          const int64_t y = y0 + yr;
-          const int ey = (y == 0 || y == g.n1 - 1) ? 2 : 1;
-          short c[V], a[V], b[V], zmv[V], zpv[V];
-          *reinterpret_cast<Vec*>(c) = *reinterpret_cast<const Vec*>(pc + rc);
-          if (OP == ST_RUNTIME || OP != ST_DERIV || g.axis == 1) {
-            *reinterpret_cast<Vec*>(a) = *reinterpret_cast<const Vec*>(pc + (y > 0 ? rc - n2 : rc));
-            *reinterpret_cast<Vec*>(b) = *reinterpret_cast<const Vec*>(pc + (y + 1 < g.n1 ? rc + n2 : rc));
+          if (V != 0 || it < nfull) {
+            const int yr = g.nq == 1 ? it : (int)__umulhi((unsigned)it, g.nq_magic);
+            const int x = (it - yr * g.nq) * VW;
+            pipe_item<OP, OUT, VW, (V != 0), STATS>(g, out, pc, pm, pp, rc0, rm0, rp0, row0, y0, yr, x, n2, ez, mo);
+          } else {
+            // the last n2 % 8 codes of every row, one at a time
+            const int t2 = it - nfull;
+            const int yr = t2 / tail;
+            const int x = g.nq * VW + (t2 - yr * tail);
+            pipe_item<OP, OUT, 1, true, STATS>(g, out, pc, pm, pp, rc0, rm0, rp0, row0, y0, yr, x, n2, ez, mo);
           }
-          if (OP == ST_RUNTIME || OP != ST_DERIV || g.axis == 0) {
-            *reinterpret_cast<Vec*>(zmv) = *reinterpret_cast<const Vec*>(pm + rm0 + roff);
-            *reinterpret_cast<Vec*>(zpv) = *reinterpret_cast<const Vec*>(pp + rp0 + roff);
-          }
-          int xl = c[0], xr = c[V - 1];
-          if (OP == ST_RUNTIME || OP != ST_DERIV || g.axis == 2) {
-            if (x > 0) xl = pc[rc - 1];
-            if (x + V < n2) xr = pc[rc + V];
-          }
-          // one-sided differences at the row ends are doubled
-          const int ex0 = x == 0 ? 2 : 1, exn = x + V == n2 ? 2 : 1;
-          if (STATS) {
-#pragma unroll
-            for (int i = 0; i < V; ++i) mo.add((int32_t)c[i]);
-          }
-          store_items<OP, OUT, V>(g, out, row0 + roff, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
         }
       }
     }
