@@ -422,8 +422,9 @@ def run_ours(args):
     # the library's autotuner picks the fused stencil's tile height per field and op
     tiles = {}
     for it in wl.items:
-        for op in ("derivative", "gradmag", "laplacian"):
-            tiles["x".join(map(str, it["shape"])) + ":" + op] = hc.autotune(it["c"], op, "float32", out=it["out"])
+        for op in ("derivative", "gradmag", "laplacian", "multi"):
+            tiles["x".join(map(str, it["shape"])) + ":" + op] = hc.autotune(
+                it["c"], op, "float32", out=None if op == "multi" else it["out"])
 
     peak, peak_src = measured_peaks()
     # outputs of the one-pass step: every derivative, the gradient magnitude,
@@ -568,19 +569,33 @@ def run_ours(args):
     host_scal = [torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8).pin_memory() for _ in wl.items]
     d2h = 0
 
+    # outputs go back on four copy streams: a field's copies overlap the next
+    # field's kernel and can use several copy engines
+    copy_streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
+
     def e2e_step():
         nonlocal d2h
         d2h = 0
+        main = torch.cuda.current_stream(dev)
         for fi, it in enumerate(wl.items):
             dev_streams[fi].copy_(host_streams[fi], non_blocking=True)
-        one_pass_step(items=e2e_items)
+        k = 0
         for fi, it in enumerate(wl.items):
+            hc.multi(e2e_items[fi], outs=mouts[fi])
+            done = torch.cuda.Event()
+            done.record(main)
             mo = mouts[fi]
-            for dst, src in zip(host_out[fi], mo["derivative"] + [mo["gradmag"], mo["laplacian"]]):
-                dst.copy_(src, non_blocking=True)
-                d2h += it["n"] * 4
-            host_scal[fi].copy_(mo["stats"], non_blocking=True)
-            d2h += hc.SCALAR_BYTES
+            pairs = list(zip(host_out[fi], mo["derivative"] + [mo["gradmag"], mo["laplacian"]]))
+            pairs.append((host_scal[fi], mo["stats"]))
+            for dst, src in pairs:
+                cs = copy_streams[k % len(copy_streams)]
+                k += 1
+                cs.wait_event(done)
+                with torch.cuda.stream(cs):
+                    dst.copy_(src, non_blocking=True)
+                d2h += src.numel() * src.element_size()
+        for cs in copy_streams:
+            main.wait_stream(cs)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()

@@ -55,7 +55,14 @@ typedef enum {
 } hc_status;
 
 typedef enum { HC_F32 = 0, HC_F64 = 1, HC_I32 = 2, HC_I64 = 3 } hc_dtype;
-typedef enum { HC_OP_MEAN = 0, HC_OP_VARIANCE = 1, HC_OP_DERIVATIVE = 2, HC_OP_GRADMAG = 3, HC_OP_LAPLACIAN = 4 } hc_op;
+typedef enum {
+  HC_OP_MEAN = 0,
+  HC_OP_VARIANCE = 1,
+  HC_OP_DERIVATIVE = 2,
+  HC_OP_GRADMAG = 3,
+  HC_OP_LAPLACIAN = 4,
+  HC_OP_MULTI = 5 /* every operation in one pass (hc_op_multi) */
+} hc_op;
 typedef enum { HC_EB_ABS = 0, HC_EB_REL = 1 } hc_eb_mode;
 /* Decorrelation inside a block (Section IV).  DELTA: the block's first code is
  * metadata and p_k = q_k - q_{k-1} (HSZp with SZp-style block heads).  MEAN:
@@ -382,8 +389,11 @@ HC_API int hc_batch_status(void* d_ws, void* stream);
  * which must hold the op's output) and keeps the fastest for all later calls
  * on fields of the same shape, max width, op and output type in this
  * process.  *chosen receives the tile height (0: the general kernel applies
- * and nothing was tuned; statistics ops have nothing to tune).  SYNC: call it
- * before capturing work in a CUDA graph. */
+ * and nothing was tuned; statistics ops have nothing to tune).  HC_OP_MULTI
+ * tunes hc_op_multi's one-pass kernel: d_out must then hold (ndim + 2) * N
+ * outputs (the derivative along each axis, the gradient magnitude and the
+ * Laplacian, one after the other).  SYNC: call it before capturing work in a
+ * CUDA graph. */
 HC_API int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_ws, size_t ws_bytes,
                        void* stream, int* chosen);
 

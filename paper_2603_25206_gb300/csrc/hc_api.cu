@@ -422,6 +422,10 @@ int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_
     case HC_OP_LAPLACIAN:
       sop = ST_LAPLACIAN;
       break;
+    case HC_OP_MULTI:
+      sop = ST_MULTI;
+      if (out_dtype == HC_I64) return fail(HC_ERR_INVALID_ARG, "out_dtype must be F32 or F64");
+      break;
     default:
       return HC_OK;  // statistics have no tunable tile
   }

@@ -173,6 +173,9 @@ int stencil_pipe_impl(const hc_header* h, const void* d_stream, const int64_t* d
   return stencil_pipe_launch(h, d_stream, d3, op, axis3, d_out, out_dtype, d_ws, st, tuned_ty(h, d3, op, out_dtype));
 }
 
+static int stencil_multi_launch(const hc_header* h, const void* d_stream, void* const outs[5], hc_scalar* d_stats,
+                                int out_dtype, void* d_ws, cudaStream_t st, int force_ty);
+
 // Time every tile height that fits on this field and remember the fastest.
 // Returns the chosen height (0 when the pipelined kernel does not apply).
 int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_t* d3, int op, void* d_out,
@@ -190,7 +193,26 @@ int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_
     int rc = HC_OK;
     for (int r = -1; r < 3 && rc == HC_OK; ++r) {
       cudaEventRecord(e0, st);
-      rc = stencil_pipe_launch(h, d_stream, d3, op, 0, d_out, out_dtype, d_ws, st, ty);
+      if (op == ST_MULTI) {
+        // the one-pass kernel: (ndim + 2) output fields one after the other
+        const size_t esz = out_dtype == HC_F64 ? 8 : 4;
+        const size_t nb = esz * (size_t)h->N;
+        char* o = reinterpret_cast<char*>(d_out);
+        void* outs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        int k = 0;
+        // derivative outputs for the user axes, in the walk's internal axes
+        for (int a = 0; a < h->ndim; ++a) {
+          int axis3 = a + 3 - h->ndim;
+          int64_t dd[3];
+          stencil_walk_dims(h, dd, &axis3);
+          outs[axis3] = o + (k++) * nb;
+        }
+        outs[3] = o + (k++) * nb;
+        outs[4] = o + (k++) * nb;
+        rc = stencil_multi_launch(h, d_stream, outs, nullptr, out_dtype, d_ws, st, ty);
+      } else {
+        rc = stencil_pipe_launch(h, d_stream, d3, op, 0, d_out, out_dtype, d_ws, st, ty);
+      }
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = HC_ERR_CUDA;
       if (r >= 0) cudaEventElapsedTime(&times[r], e0, e1);
@@ -280,15 +302,23 @@ static int launch_multi(const hc_header* h, const void* d_stream, const PGeo& g,
 
 int stencil_multi_impl(const hc_header* h, const void* d_stream, void* const deriv3[3], void* d_grad, void* d_lap,
                        hc_scalar* d_stats, int out_dtype, void* d_ws, cudaStream_t st) {
-  if (out_dtype != HC_F32 && out_dtype != HC_F64) return HC_ERR_UNSUPPORTED;
+  int64_t d3[3];
+  stencil_walk_dims(h, d3, nullptr);
   void* outs[5] = {deriv3[0], deriv3[1], deriv3[2], d_grad, d_lap};
+  return stencil_multi_launch(h, d_stream, outs, d_stats, out_dtype, d_ws, st, tuned_ty(h, d3, ST_MULTI, out_dtype));
+}
+
+static int stencil_multi_launch(const hc_header* h, const void* d_stream, void* const outs_in[5], hc_scalar* d_stats,
+                                int out_dtype, void* d_ws, cudaStream_t st, int force_ty) {
+  if (out_dtype != HC_F32 && out_dtype != HC_F64) return HC_ERR_UNSUPPORTED;
+  void* outs[5] = {outs_in[0], outs_in[1], outs_in[2], outs_in[3], outs_in[4]};
   for (void* o : outs)
     if (o && !aligned16(o)) return HC_ERR_UNSUPPORTED;
   int64_t d3[3];
   stencil_walk_dims(h, d3, nullptr);
   PGeo g{};
   int smem = 0;
-  if (!plan_pipe_geometry(h, d3, g, &smem, 0, 74 * 1024)) return HC_ERR_UNSUPPORTED;
+  if (!plan_pipe_geometry(h, d3, g, &smem, force_ty, force_ty ? 200 * 1024 : 74 * 1024)) return HC_ERR_UNSUPPORTED;
   if (g.n1 * g.n2 >= ((int64_t)1 << 31)) return HC_ERR_UNSUPPORTED;
   g.axis = 0;
   g.op = ST_MULTI;

@@ -29,7 +29,8 @@ HC_F32, HC_F64, HC_I32, HC_I64 = 0, 1, 2, 3
 HC_EB_ABS, HC_EB_REL = 0, 1
 HC_STAGE_COMPRESSED, HC_STAGE_M, HC_STAGE_P, HC_STAGE_Q, HC_STAGE_F = 0, 1, 2, 3, 4
 HC_OP_MEAN, HC_OP_VARIANCE, HC_OP_DERIVATIVE, HC_OP_GRADMAG, HC_OP_LAPLACIAN = 0, 1, 2, 3, 4
-OPS = {"mean": HC_OP_MEAN, "variance": HC_OP_VARIANCE, "derivative": HC_OP_DERIVATIVE, "gradmag": HC_OP_GRADMAG,
+HC_OP_MULTI = 5
+OPS = {"multi": HC_OP_MULTI, "mean": HC_OP_MEAN, "variance": HC_OP_VARIANCE, "derivative": HC_OP_DERIVATIVE, "gradmag": HC_OP_GRADMAG,
        "laplacian": HC_OP_LAPLACIAN}
 
 STAGES = {"m": HC_STAGE_M, "p": HC_STAGE_P, "q": HC_STAGE_Q, "f": HC_STAGE_F}
@@ -486,9 +487,13 @@ def workspace_status(stream=None) -> int:
 
 
 def autotune(c: Compressed, op: str, out_dtype: str = "float32", out=None, stream=None) -> int:
-    """Time the fused stencil's tile heights for this field and op; later calls use the fastest."""
+    """Time the fused stencil's tile heights for this field and op ("derivative",
+    "gradmag", "laplacian", or "multi" for hc_op_multi's one-pass kernel);
+    later calls use the fastest."""
     torch = _torch()
     st = c.stage("q")
+    if op == "multi" and out is None:
+        out = _field_out((len(c.shape) + 2,) + tuple(c.shape), out_dtype, c.stream.device, None)
     out = _field_out(c.shape, out_dtype, c.stream.device, out)
     ws = workspace(c.stream.device, stream)
     chosen = ctypes.c_int()

@@ -81,3 +81,20 @@ def test_multi_subsets_and_full_size(env, orc):
     s = hc.multi(c, derivative=False, gradmag=False, laplacian=False)
     assert hc.parse_scalar(s["stats"]) == hc.parse_scalar(full["stats"])
     assert hc.workspace_status() == 0
+
+
+def test_multi_autotune_keeps_results(env, orc):
+    """Tuning the one-pass kernel's tile height changes no output."""
+    import synth
+
+    hc, torch, dev = env
+    x = synth.grf_field((70, 96, 120), 7100)
+    c = hc.compress(torch.from_numpy(x).to(dev), 1e-3, rel=True, S=32)
+    before = hc.multi(c)
+    ty = hc.autotune(c, "multi")
+    assert ty in (1, 2, 4, 8, 16)
+    after = hc.multi(c)
+    for a in range(3):
+        assert torch.equal(before["derivative"][a], after["derivative"][a])
+    assert torch.equal(before["gradmag"], after["gradmag"]) and torch.equal(before["laplacian"], after["laplacian"])
+    assert hc.parse_scalar(before["stats"]) == hc.parse_scalar(after["stats"])
