@@ -181,13 +181,26 @@ __device__ __forceinline__ void emit_items(const PGeo& g, typename OT<D>::T* o, 
 }
 
 // ST_MULTI: every wanted output of the V points from one neighbourhood (one
-// decode serves all operations), output by output so that only V results are
-// live at a time.
+// decode serves all operations).  The integer numerators of the V points are
+// formed once; the outputs are then converted and stored one after the other.
 template <int D, int V, bool AL>
 __device__ __forceinline__ void emit_multi(const PGeo& g, int64_t i0, const short* c, const short* a,
                                            const short* b, const short* zmv, const short* zpv, int xl, int xr,
                                            int ex0, int exn, int ez, int ey) {
   using T = typename OT<D>::T;
+  int n[4][V];  // derivative along axes 0, 1, 2 and the Laplacian
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+    const int cm = i == 0 ? xl : c[i - 1];
+    const int cp = i == V - 1 ? xr : c[i + 1];
+    int ex = 1;
+    if (i == 0) ex = ex0;
+    if (i == V - 1) ex = ex * exn;
+    n[0][i] = ((int)zpv[i] - zmv[i]) * ez;
+    n[1][i] = ((int)b[i] - a[i]) * ey;
+    n[2][i] = (cp - cm) * ex;
+    n[3][i] = (int)zmv[i] + zpv[i] + a[i] + b[i] + cm + cp - 6 * (int)c[i];
+  }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     T* o = reinterpret_cast<T*>(g.mout[k]);
@@ -195,18 +208,9 @@ __device__ __forceinline__ void emit_multi(const PGeo& g, int64_t i0, const shor
     T res[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) {
-      const int cm = i == 0 ? xl : c[i - 1];
-      const int cp = i == V - 1 ? xr : c[i + 1];
-      int ex = 1;
-      if (i == 0) ex = ex0;
-      if (i == V - 1) ex = ex * exn;
-      const int d0 = ((int)zpv[i] - zmv[i]) * ez, d1 = ((int)b[i] - a[i]) * ey, d2 = (cp - cm) * ex;
-      if (k == 0) res[i] = emit1<ST_DERIV, D>(d0, 0, 0, g);
-      if (k == 1) res[i] = emit1<ST_DERIV, D>(d1, 0, 0, g);
-      if (k == 2) res[i] = emit1<ST_DERIV, D>(d2, 0, 0, g);
-      if (k == 3) res[i] = emit1<ST_GRADMAG, D>(d0, d1, d2, g);
-      if (k == 4)
-        res[i] = emit1<ST_LAPLACIAN, D>((int)zmv[i] + zpv[i] + a[i] + b[i] + cm + cp - 6 * (int)c[i], 0, 0, g);
+      if (k < 3) res[i] = emit1<ST_DERIV, D>(n[k][i], 0, 0, g);
+      if (k == 3) res[i] = emit1<ST_GRADMAG, D>(n[0][i], n[1][i], n[2][i], g);
+      if (k == 4) res[i] = emit1<ST_LAPLACIAN, D>(n[3][i], 0, 0, g);
     }
     o += i0;
     if constexpr (AL && V * sizeof(T) >= 16) {
