@@ -359,7 +359,7 @@ __host__ __device__ inline TileSmem tile_smem(int nblk_max, int npre_max, int S,
 }
 
 // ----------------------------------------------------- chunk-aligned tiles
-// Reductions and whole-stream decoding walk tiles of kTileChunks chunks.  A
+// Reductions and whole-stream decoding walk tiles of whole chunks.  A
 // tile's payload range comes straight from the chunk index, so the next
 // tile's widths, heads and payload are copied into shared memory with
 // cp.async while the current tile is decoded.
@@ -369,13 +369,15 @@ struct TileCopy {
   uint64_t p0, p1;  // payload words [p0, p1)
 };
 
+// tb: blocks per tile, a whole number of chunks (tb / G of them).
 __device__ __forceinline__ TileCopy tile_bounds(const DevStream& s, int64_t t, int tb) {
   TileCopy c;
   c.b0 = t * tb;
   c.nblk = (int)min((int64_t)tb, s.nb - c.b0);
-  const int64_t c0 = t * kTileChunks;
+  const int64_t nch = tb / s.G;
+  const int64_t c0 = t * nch;
   c.p0 = __ldg(s.chunks + c0);
-  c.p1 = __ldg(s.chunks + min(c0 + kTileChunks, s.nchunks));
+  c.p1 = __ldg(s.chunks + min(c0 + nch, s.nchunks));
   return c;
 }
 
