@@ -893,6 +893,68 @@ def run_hszx(args):
     return 0
 
 
+def run_wide(args):
+    """The wide-code configuration: one float64 512 x 512 x 1024 field (k^-3
+    field times 1e4 plus a linear trend), block 64, value-range-relative
+    eb 1e-6, and its ABS companion (eps = range / 2^31, block widths in the
+    upper 20s).  Per form and operation: fused time (mean, variance with exact
+    128-bit sums, derivative per axis into float32 and float64) against the
+    plain path (decompress to float64, then the operation), median of 5
+    CUDA-event runs with an L2 flush before each.  GB/s counts the field's
+    original bytes (8 per element)."""
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    shape = (512, 512, 1024)
+    x = synth.wide_field(shape, 3000)
+    forms = {}
+    for form in ("rel_1e-6", "abs_2^-31"):
+        if form == "rel_1e-6":
+            xd = torch.from_numpy(x).to(dev)
+            c = hc._trim(hc.compress(xd, 1e-6, rel=True, S=64))
+        else:
+            xc = np.ascontiguousarray(x - (x.max() + x.min()) / 2)
+            xd = torch.from_numpy(xc).to(dev)
+            c = hc._trim(hc.compress(xd, float(xc.max() - xc.min()) / 2**31, rel=False, S=64))
+            del xc
+        del xd
+        n = int(np.prod(shape))
+        scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
+        o32 = torch.empty(shape, dtype=torch.float32, device=dev)
+        o64 = torch.empty(shape, dtype=torch.float64, device=dev)
+        df = torch.empty(shape, dtype=torch.float64, device=dev)
+        sf = hc.as_stage(c, "f", df)
+
+        def plain(fn):
+            hc.decompress(c, "f", out=df)
+            fn()
+
+        t = {"mean_stage2": time_call(torch, dev, lambda: hc.mean(c, level="p", out=scal)),
+             "variance_stage3": time_call(torch, dev, lambda: hc.variance(c, level="q", out=scal)),
+             "variance_plain": time_call(torch, dev, lambda: plain(lambda: hc.variance(sf, out=scal)))}
+        for a in range(3):
+            t[f"derivative{a}_f32"] = time_call(torch, dev, lambda a=a: hc.derivative(c, a, out=o32))
+            t[f"derivative{a}_f64"] = time_call(torch, dev, lambda a=a: hc.derivative(c, a, out=o64))
+            t[f"derivative{a}_plain_f64"] = time_call(torch, dev, lambda a=a: plain(lambda: hc.derivative(sf, a, out=o64)))
+        forms[form] = {"compressed_bytes": c.nbytes, "wmax": int(c.header.wmax), "qmax": int(c.header.qmax),
+                       "ms": {k: round(v, 4) for k, v in t.items()},
+                       "gbs_orig": {k: round(n * 8 / v / 1e6, 1) for k, v in t.items()}}
+        del c, o32, o64, df, sf
+    print(json.dumps({"metric": "wide-code field: GB/s of original data per operation, fused vs plain",
+                      "unit": "GB/s", "data": "synthetic",
+                      "config": {"workload": "wide-code: float64 512x512x1024 k^-3 GRF x 1e4 + linear trend, block 64; "
+                                             "REL 1e-6 and ABS range/2^31",
+                                 "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
+                      "forms": forms}))
+    return 0
+
+
 def synth_shapes():
     import synth
 
@@ -972,6 +1034,7 @@ def main(argv=None):
     ap.add_argument("--profile-batch", action="store_true", help="run the small batched ncu case and exit")
     ap.add_argument("--serving", action="store_true", help="the serving form (200 resident fields, Poisson queries)")
     ap.add_argument("--hszx", action="store_true", help="the block-mean (HSZx) form of the paper-like workload")
+    ap.add_argument("--wide", action="store_true", help="the wide-code float64 configuration")
     ap.add_argument("--fields", type=int, default=200)
     ap.add_argument("--qps", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=30.0)
@@ -984,6 +1047,8 @@ def main(argv=None):
         return run_serving(args)
     if args.hszx:
         return run_hszx(args)
+    if args.wide:
+        return run_wide(args)
     if args.batched:
         if args.warmup < 3:
             args.warmup = 3

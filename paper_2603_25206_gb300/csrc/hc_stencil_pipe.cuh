@@ -311,8 +311,16 @@ __device__ __forceinline__ void pipe_item(const PGeo& g, typename OT<OUT>::T* ou
   // one-sided differences at the row ends are doubled
   const int ex0 = x == 0 ? 2 : 1, exn = x + W == n2 ? 2 : 1;
   if (STATS) {
+    // int16 codes: q^2 < 2^30, so an item's sums fit 32 / 64 bits and go
+    // into the 128-bit accumulator with one carry
+    int a1 = 0;
+    unsigned long long a2 = 0;
 #pragma unroll
-    for (int i = 0; i < W; ++i) mo.add((int32_t)c[i]);
+    for (int i = 0; i < W; ++i) {
+      a1 += c[i];
+      a2 += (unsigned long long)((int)c[i] * (int)c[i]);
+    }
+    mo.add_sums(a1, a2);
   }
   store_items<OP, OUT, W, AL>(g, out, row0 + roff, c, a, b, zmv, zpv, xl, xr, ex0, exn, ez, ey);
 }

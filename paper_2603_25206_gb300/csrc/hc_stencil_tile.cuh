@@ -239,6 +239,12 @@ struct Moments {
     lo += v;
     hi += (lo < v) ? 1ull : 0ull;
   }
+  // add a 64-bit partial sum of squares (and its sum) with one carry
+  __device__ __forceinline__ void add_sums(long long a1, unsigned long long a2) {
+    s1 += a1;
+    lo += a2;
+    hi += (lo < a2) ? 1ull : 0ull;
+  }
 };
 
 // Whole rows: every slot holds one contiguous decoded range; all offsets
