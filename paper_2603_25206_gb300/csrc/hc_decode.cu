@@ -46,12 +46,10 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
   const int out_words = decode_out_words(tb, s.S);
   const int nsegmax = SMALL ? tb : tb * s.nseg;
   const PipeTileSmem L =
-      pipe_tile_smem(tb, stage_words, out_words + (SMALL ? 0 : nsegmax) + (kWidthSpecialize ? round4((nsegmax + 32 * 32 + 1) / 2) : 0));
+      pipe_tile_smem(tb, stage_words, out_words + (SMALL ? 0 : nsegmax));
   uint32_t* s_off = smem + L.off;
   int32_t* s_out = reinterpret_cast<int32_t*>(smem + L.extra);
   int32_t* s_tot = s_out + out_words;
-  uint16_t* s_order = reinterpret_cast<uint16_t*>(s_tot + (SMALL ? 0 : nsegmax));
-  __shared__ int s_hist[64];
   const int tid = threadIdx.x, nt = blockDim.x;
 
   // two tile buffers: tile t is decoded while tile t + gridDim.x is copied in
@@ -90,14 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_decode(DevStream s, OutT* __restri
     if (!ok) continue;
 
     const int nsegs = SMALL ? nblk : nblk * s.nseg;
-    // group segments of equal width so each warp runs one specialised unpacker
-    const bool sorted = kWidthSpecialize && s.S >= 32;
-    const int nwork =
-        sorted ? cta_sort_by_width([&](int i) { return (int)tv.w[SMALL ? i : i / s.nseg]; }, nsegs, s_order, s_hist)
-               : nsegs;
-    for (int u = tid; u < nwork; u += nt) {
-      const int seg = sorted ? (int)s_order[u] : u;
-      if (seg == 0xFFFF) continue;
+    for (int seg = tid; seg < nsegs; seg += nt) {
       const int bl = SMALL ? seg : seg / s.nseg;
       const int j = SMALL ? 0 : seg - bl * s.nseg;
       const int64_t b = b0 + bl;
@@ -204,7 +195,7 @@ static PipeTileSmem decode_layout(const hc_header* h, bool small, int stage) {
   const int tb = kTileChunks * h->G;
   const int nseg = (h->S + 31) / 32;
   const int nsegmax = small ? tb : tb * nseg;
-  return pipe_tile_smem(tb, stage, decode_out_words(tb, h->S) + (small ? 0 : nsegmax) + (kWidthSpecialize ? round4((nsegmax + 32 * 32 + 1) / 2) : 0));
+  return pipe_tile_smem(tb, stage, decode_out_words(tb, h->S) + (small ? 0 : nsegmax));
 }
 
 template <int KIND, class OutT, bool SMALL, int PRED>

@@ -141,94 +141,18 @@ __device__ __forceinline__ void unpack_segment(const uint32_t* __restrict__ mw, 
 
 
 
-// Width-specialised unpack of one full 32-element segment of width W: the W
-// magnitude words are read into registers once and every value is cut out
-// with compile-time shifts.  f(i, p) is called for i = 0..31 in order.
-template <int W, class F>
-__device__ __forceinline__ void unpack_w(const uint32_t* __restrict__ mw, uint32_t sw, F&& f) {
-  uint32_t r[W + 1];
-#pragma unroll
-  for (int j = 0; j < W; ++j) r[j] = mw[j];
-  r[W] = 0u;
-  constexpr uint32_t mask = (1u << W) - 1u;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int b = i * W, j = b >> 5, sh = b & 31;
-    uint32_t m;
-    if (sh + W <= 32)
-      m = (r[j] >> sh) & mask;
-    else
-      m = __funnelshift_r(r[j], r[j + 1], sh) & mask;
-    const int32_t neg = (int32_t)(sw << (31 - i)) >> 31;
-    f(i, ((int32_t)m ^ neg) - neg);
-  }
-}
-
-// Widest width with a specialised unpacker; wider segments take the
-// sliding-window unpacker (unpack_segment).
-constexpr int kMaxSpecialW = 12;
-
-// Width-specialised unpacking removes the sliding window's per-code checks,
-// but measured on GB300 it was slower in every kernel: warps must first be
-// given segments of one width (a per-tile sort whose padding leaves lanes idle
-// and adds barriers), and the specialised code strains the instruction cache.
-// It is kept switchable; the sliding-window unpacker is the one in use.
-constexpr bool kWidthSpecialize = false;
-
 // Full 32-element segment of any width 1..31 (width 0 is handled by callers).
+// A width-specialised unpacker (compile-time shifts per width, with warps
+// handed segments of one width by a per-tile sort) was measured slower in
+// every kernel on GB300: the sort's padding idles lanes and adds barriers, and
+// the specialised code strains the instruction cache.  The sliding window is
+// the one unpacker.
 template <class F>
 __device__ __forceinline__ void unpack_full(const uint32_t* mw, uint32_t sw, uint32_t w, F&& f) {
-  if constexpr (!kWidthSpecialize) {
-    unpack_segment<true>(mw, sw, w, 32, f);
-    return;
-  }
-  switch (w) {
-#define HC_UNPACK_CASE(W) \
-  case W:                 \
-    unpack_w<W>(mw, sw, f); \
-    break;
-    HC_UNPACK_CASE(1) HC_UNPACK_CASE(2) HC_UNPACK_CASE(3) HC_UNPACK_CASE(4) HC_UNPACK_CASE(5) HC_UNPACK_CASE(6)
-    HC_UNPACK_CASE(7) HC_UNPACK_CASE(8) HC_UNPACK_CASE(9) HC_UNPACK_CASE(10) HC_UNPACK_CASE(11) HC_UNPACK_CASE(12)
-#undef HC_UNPACK_CASE
-    default:
-      unpack_segment<true>(mw, sw, w, 32, f);
-  }
+  unpack_segment<true>(mw, sw, w, 32, f);
 }
 
-// Counting sort of n (< 65536) items by a key in 0..31 (key(i), read from
-// shared memory) into order[], with every key's run padded to a multiple of
-// 32 entries (holes hold 0xFFFF): a warp taking 32 consecutive entries sees
-// one width, so it runs one specialised unpacker without divergence.
-// Returns the padded length (<= n + 31 * 32).  s_hist: 64 ints of shared
-// scratch.  Every thread of the CTA must call it.
-template <class K>
-__device__ inline int cta_sort_by_width(K&& key, int n, uint16_t* order, int* s_hist) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid < 64) s_hist[tid] = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) atomicAdd(&s_hist[key(i) & 31], 1);
-  __syncthreads();
-  if (tid < 32) {
-    const int c = (s_hist[tid] + 31) & ~31;
-    int x = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (tid >= o) x += y;
-    }
-    s_hist[32 + tid] = x - c;  // start of each padded bin
-    if (tid == 31) s_hist[0] = x;  // padded length (counts are no longer needed)
-  }
-  __syncthreads();
-  const int padded = s_hist[0];
-  for (int i = tid; i < padded; i += nt) order[i] = 0xFFFFu;
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) order[atomicAdd(&s_hist[32 + (key(i) & 31)], 1)] = (uint16_t)i;
-  __syncthreads();
-  return padded;
-}
-
-// Any segment: full ones take the width-specialised path.
+// Any segment: full ones skip the per-code count check.
 template <class F>
 __device__ __forceinline__ void unpack_any(const uint32_t* mw, uint32_t sw, uint32_t w, int count, F&& f) {
   if (count == 32)

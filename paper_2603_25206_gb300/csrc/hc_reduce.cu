@@ -38,8 +38,6 @@ __device__ __forceinline__ int pidx(int r) { return r + (r >> 5); }
 __host__ __device__ inline int seg_moment_words(int nsegmax, bool var) {
   return round4(nsegmax) + round4(2 * nsegmax) + (var ? 4 * nsegmax : 0);
 }
-// words of a uint16 segment-order array
-__host__ __device__ inline int order_words(int nsegmax) { return kWidthSpecialize ? round4((nsegmax + 32 * 32 + 1) / 2) : 0; }
 // padded value tile (33 words per 32 elements)
 __host__ __device__ inline int padded_words(int elems) { return round4(((elems + 31) / 32) * 33 + 4); }
 
@@ -66,14 +64,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
   const int nsegmax = SMALL ? tb : tb * s.nseg;
   constexpr bool seg_arrays = (!SMALL && LEVEL == 3);
   const int segw = seg_arrays ? seg_moment_words(nsegmax, VAR) : 0;
-  const PipeTileSmem L = pipe_tile_smem(tb, stage_words, segw + order_words(nsegmax));
+  const PipeTileSmem L = pipe_tile_smem(tb, stage_words, segw);
   uint32_t* s_off = smem + L.off;
   // per-segment local moments for S > 32 at level 3
   int32_t* s_T = reinterpret_cast<int32_t*>(smem + L.extra);
   long long* s_a1 = reinterpret_cast<long long*>(smem + L.extra + round4(nsegmax));
   u128* s_a2 = reinterpret_cast<u128*>(smem + L.extra + round4(nsegmax) + round4(2 * nsegmax));
-  uint16_t* s_order = reinterpret_cast<uint16_t*>(smem + L.extra + segw);
-  __shared__ int s_hist[64];
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) s_err = 0;
   long long S1 = 0;
@@ -113,14 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_stream(DevStream s, int64_t
     bi ^= 1;
     if (!ok) continue;
     const int nsegs = SMALL ? nblk : nblk * s.nseg;
-    // group segments of equal width so each warp runs one specialised unpacker
-    const bool sorted = kWidthSpecialize && s.S >= 32;
-    const int nwork =
-        sorted ? cta_sort_by_width([&](int i) { return (int)tv.w[SMALL ? i : i / s.nseg]; }, nsegs, s_order, s_hist)
-               : nsegs;
-    for (int u = tid; u < nwork; u += nt) {
-      const int seg = sorted ? (int)s_order[u] : u;
-      if (seg == 0xFFFF) continue;
+    for (int seg = tid; seg < nsegs; seg += nt) {
       const int bl = SMALL ? seg : seg / s.nseg;
       const int j = SMALL ? 0 : seg - bl * s.nseg;
       const int64_t b = b0 + bl;
@@ -550,7 +539,7 @@ static int launch_stream_p(const hc_header* h, const void* d_stream, hc_scalar* 
   const int nsegmax = SMALL ? tb : tb * nseg;
   const int stage = stage_words_for(tb, h->S, (int)h->wmax);
   const PipeTileSmem L =
-      pipe_tile_smem(tb, stage, ((!SMALL && LEVEL == 3) ? seg_moment_words(nsegmax, VAR) : 0) + order_words(nsegmax));
+      pipe_tile_smem(tb, stage, (!SMALL && LEVEL == 3) ? seg_moment_words(nsegmax, VAR) : 0);
   const int bytes = 4 * L.total;
   auto kern = k_reduce_stream<LEVEL, ACC, VAR, SMALL, PRED>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
@@ -729,7 +718,7 @@ static int launch_var_scratch_p(const hc_header* h, const void* d_stream, hc_sca
   const int nsegmax = SMALL ? tb : tb * nseg;
   const int stage = stage_words_for(tb, h->S, (int)h->wmax);
   const PipeTileSmem L =
-      pipe_tile_smem(tb, stage, (!SMALL ? seg_moment_words(nsegmax, true) : 0) + order_words(nsegmax));
+      pipe_tile_smem(tb, stage, !SMALL ? seg_moment_words(nsegmax, true) : 0);
   const int bytes = 4 * L.total;
   auto kern = k_reduce_stream<3, ACC, true, SMALL, PRED>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);

@@ -115,7 +115,7 @@ __host__ __device__ inline PSmem psmem(const PGeo& g) {
   p.ring = 0;
   p.stage = p.ring + kSlots * g.slot_bytes;
   p.meta = p.stage + 3 * 4 * g.stage_words;
-  p.meta_bytes = g.pre_max + 4 * g.heads_max + 4 * (g.nblk_max + 4) + (kWidthSpecialize ? 2 * (g.nblk_max + 32 * 32 + 8) : 0);
+  p.meta_bytes = g.pre_max + 4 * g.heads_max + 4 * (g.nblk_max + 4);
   p.meta_bytes = (p.meta_bytes + 15) & ~15;
   p.total = p.meta + 4 * p.meta_bytes;
   return p;
@@ -353,13 +353,7 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
   auto meta_o = [&](int j) {
     return reinterpret_cast<uint32_t*>(sm + L.meta + (j & 3) * L.meta_bytes + g.pre_max + 4 * g.heads_max);
   };
-  auto meta_ord = [&](int j) {
-    return reinterpret_cast<uint16_t*>(sm + L.meta + (j & 3) * L.meta_bytes + g.pre_max + 4 * g.heads_max +
-                                       4 * (g.nblk_max + 4));
-  };
   auto stage = [&](int j) { return reinterpret_cast<uint32_t*>(sm + L.stage + (j % 3) * 4 * g.stage_words); };
-  __shared__ int s_whist[64];
-  __shared__ int s_npad[4];  // padded order length per metadata buffer
   auto slot = [&](int64_t z) { return sm + L.ring + (int)(z & 3) * g.slot_bytes; };
 
   // loader: copy widths [cs, b0 + nblk) and heads [b0, b0 + nblk) of slab j
@@ -417,30 +411,6 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
     // offsets relative to the staging buffer (or all zero for a bad slab)
     for (int i = lane; i < d.nblk; i += 32) off[i] = bad ? 0u : off[i] - first + lead;
     if (bad && lane == 0) set_error(err, HC_ERR_CORRUPT);
-    // counting sort of the slab's blocks by width: workers taking consecutive
-    // entries run one width-specialised unpacker per warp
-    uint16_t* ord = meta_ord(j);
-    if (!kWidthSpecialize) return;
-    s_whist[lane] = 0;
-    __syncwarp();
-    for (int i = lane; i < d.nblk; i += 32) atomicAdd(&s_whist[min((int)w[d.npre + i], 31)], 1);
-    __syncwarp();
-    {
-      const int c = (s_whist[lane] + 31) & ~31;  // runs padded to whole warps
-      int x = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      s_whist[32 + lane] = x - c;
-      const int padded = __shfl_sync(0xffffffffu, x, 31);
-      if (lane == 0) s_npad[j & 3] = padded;
-      for (int i = lane; i < padded; i += 32) ord[i] = 0xFFFFu;
-    }
-    __syncwarp();
-    for (int i = lane; i < d.nblk; i += 32) ord[atomicAdd(&s_whist[32 + min((int)w[d.npre + i], 31)], 1)] = (uint16_t)i;
-    __syncwarp();
   };
 
   // ---- prologue: metadata of slabs 0..2, payload of slabs 0 and 1
@@ -502,11 +472,7 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
         const uint32_t* off = meta_o(k);
         const uint32_t* stg = stage(k);
         unsigned char* dst = slot(z);
-        const uint16_t* ord = meta_ord(k);
-        const int nwork = kWidthSpecialize ? s_npad[k & 3] : d.nblk;
-        for (int t = wt; t < nwork; t += wstride) {
-          const int seg = kWidthSpecialize ? (int)ord[t] : t;
-          if (seg == 0xFFFF) continue;
+        for (int seg = wt; seg < d.nblk; seg += wstride) {
           const uint32_t wi = min((uint32_t)w[seg], (uint32_t)s.wmax);
           int32_t q = hd[seg];
           short v[32];

@@ -123,8 +123,8 @@ __device__ inline int64_t decode_range(const DevStream& s, int64_t e0, int64_t e
     if (w == 0) {
       for (int i = 0; i < cnt; ++i) dst[pidx(r0 + i)] = acc;
     } else {
-      // the general kernel keeps the compact sliding-window unpacker (the
-      // pipelined kernel carries the width-specialised one)
+      // compact sliding-window unpacker: the general kernel is bound by its
+      // barriers, not by the unpack
       const uint32_t* blk = tv.words + tv.off[bl];
       unpack_segment<false>(blk + s.nseg + j * w, blk[j], w, cnt, [&](int i, int32_t p) {
         acc += p;
