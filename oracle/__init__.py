@@ -23,6 +23,10 @@ _SRC = os.path.join(_HERE, "hc_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 KIND_DERIV, KIND_GRADMAG, KIND_LAPLACIAN = 0, 1, 2
+# predictors: delta inside the block (HSZp with block heads), block mean
+# (HSZx), Lorenzo over the field's axes (HSZp-nd), delta across blocks over
+# the flattened field (HSZp)
+PRED_DELTA, PRED_MEAN, PRED_LORENZO, PRED_GLOBAL = 0, 1, 2, 3
 
 
 class OracleError(RuntimeError):
@@ -77,12 +81,17 @@ def lib():
         L.orc_stencil_q.argtypes = [vp, vp, i32, i32, dbl, vp]
         L.orc_stencil_f.argtypes = [vp, i32, vp, i32, i32, vp]
         L.orc_stencil_at.argtypes = [vp, vp, i32, i32, dbl, vp, i64, vp, vp]
+        L.orc_lorenzo_mean_p.argtypes = [vp, vp, P(i64)]
+        L.orc_lorenzo_var_p.argtypes = [vp, vp, P(i64), P(ctypes.c_uint64), P(ctypes.c_uint64)]
+        L.orc_lorenzo_deriv_p.argtypes = [vp, vp, i32, vp]
+        L.orc_lorenzo_lap_p.argtypes = [vp, vp, vp]
         for f in (L.orc_eps, L.orc_quantize, L.orc_compress, L.orc_compress_codes, L.orc_read_header,
                   L.orc_decode_p, L.orc_decode_q, L.orc_decode_m, L.orc_decode_f, L.orc_dequantize,
                   L.orc_sums_q, L.orc_mean_p_sum, L.orc_var_p_sums, L.orc_finalize, L.orc_stats_f,
                   L.orc_deriv_q, L.orc_lap_q, L.orc_stencil_q, L.orc_stencil_f, L.orc_stencil_at,
                   L.orc_compress_pred, L.orc_compress_codes_pred, L.orc_mean_m_sum, L.orc_mean_p_sum_x,
-                  L.orc_std_p_x, L.orc_divergence_q, L.orc_curl2_q):
+                  L.orc_std_p_x, L.orc_divergence_q, L.orc_curl2_q, L.orc_lorenzo_mean_p, L.orc_lorenzo_var_p,
+                  L.orc_lorenzo_deriv_p, L.orc_lorenzo_lap_p):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -132,7 +141,8 @@ def compress_bound(n: int, S: int) -> int:
 
 def compress(x: np.ndarray, eb: float, rel: bool = True, S: int = 32, pred: int = 0):
     """Algorithm 1 on a float32/float64 array -> (stream bytes as uint8 array, eps).
-    pred 0: delta inside each block (HSZp, block heads); 1: block means (HSZx)."""
+    pred 0: delta inside each block (HSZp, block heads); 1: block means (HSZx);
+    2: Lorenzo over the field's axes (HSZp-nd); 3: delta across blocks (HSZp)."""
     x = np.ascontiguousarray(x)
     d = np.array(x.shape, np.int64)
     cap = compress_bound(x.size, S)
@@ -351,3 +361,49 @@ def stencil_at(q: np.ndarray, kind: int, eps: float, idx, axis: int = 0):
     _check(lib().orc_stencil_at(_ptr(q), _ptr(d), kind, axis + 3 - q.ndim, eps, _ptr(idx), idx.size, _ptr(num),
                                 _ptr(val)), "stencil_at")
     return num, val
+
+
+# ------------------------------------------------- global predictors, stage 2
+def global_dims(shape, pred: int) -> np.ndarray:
+    """Prediction shape: the field's (n0, n1, n2) for HSZp-nd, (1, 1, N) for HSZp."""
+    d = dims3(shape)
+    if pred == PRED_GLOBAL:
+        return np.array((1, 1, int(np.prod(d))), np.int64)
+    return d
+
+
+def lorenzo_mean_p(dp: np.ndarray, pred: int) -> int:
+    """Stage-2 sum q of a global-predictor D_p: sum p (L0-z)(L1-y)(L2-x)."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    L = global_dims(dp.shape, pred)
+    s1 = ctypes.c_int64()
+    _check(lib().orc_lorenzo_mean_p(_ptr(dp), _ptr(L), ctypes.byref(s1)), "lorenzo_mean_p")
+    return s1.value
+
+
+def lorenzo_var_p(dp: np.ndarray, pred: int):
+    """Stage-2 (sum q, sum q^2) of a global-predictor D_p (Algorithm 4 extended)."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    L = global_dims(dp.shape, pred)
+    s1, lo, hi = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().orc_lorenzo_var_p(_ptr(dp), _ptr(L), ctypes.byref(s1), ctypes.byref(lo), ctypes.byref(hi)),
+           "lorenzo_var_p")
+    return s1.value, (hi.value << 64) | lo.value
+
+
+def lorenzo_deriv_p(dp: np.ndarray, axis: int) -> np.ndarray:
+    """Stage-2 derivative numerators of an HSZp-nd D_p along a user axis."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    d = dims3(dp.shape)
+    out = np.empty(dp.shape, np.int64)
+    _check(lib().orc_lorenzo_deriv_p(_ptr(dp), _ptr(d), axis + 3 - dp.ndim, _ptr(out)), "lorenzo_deriv_p")
+    return out
+
+
+def lorenzo_lap_p(dp: np.ndarray) -> np.ndarray:
+    """Stage-2 Laplacian numerators of an HSZp-nd D_p (replicated edges)."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    d = dims3(dp.shape)
+    out = np.empty(dp.shape, np.int64)
+    _check(lib().orc_lorenzo_lap_p(_ptr(dp), _ptr(d), _ptr(out)), "lorenzo_lap_p")
+    return out

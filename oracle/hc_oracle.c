@@ -23,7 +23,9 @@
  *    96 i64 off widths  104 i64 off heads  112 i64 off chunks
  *   120 i64 off payload 128 i64 total bytes  136 u32 max width
  *   140 u32 predictor: 0 = delta inside the block (HSZp with SZp-style block
- *       heads), 1 = block mean (HSZx); rest zero
+ *       heads), 1 = block mean (HSZx), 2 = Lorenzo over the field's axes
+ *       (HSZp-nd), 3 = delta across blocks over the flattened field (HSZp);
+ *       rest zero
  *   widths u8[nb] at 256; heads i32[nb], chunk index u64[nchunks + 1] and
  *   payload u32 words each start on the next 16-byte boundary; the stream
  *   ends 16..31 zero bytes after the payload (total rounded to 16).
@@ -34,7 +36,10 @@
  *   read least-significant bit first.  Predictor 0: heads[b] is the block's
  *   first code, p_k = q_k - q_{k-1} and p_0 = 0.  Predictor 1: heads[b] is
  *   the block mean M_b (the integer nearest to the block's code sum over its
- *   true size, ties toward zero) and p_k = q_k - M_b for every k.  The padding
+ *   true size, ties toward zero) and p_k = q_k - M_b for every k.
+ *   Predictors 2 and 3: heads[b] = 0 and every slot holds the residual of a
+ *   prediction that runs over the whole field (below, "global predictors").
+ *   The padding
  *   slots of a short last block are 0.  A block of width 0 has no payload
  *   words.
  *
@@ -235,11 +240,56 @@ static int64_t nearest_ratio(int64_t a, int64_t d) {
   return (int64_t)(a < 0 ? -r : r);
 }
 
+/* ------------------------------------------------------------------ */
+/* Global predictors (Section IV, "HSZp" and "HSZp-nd").                */
+/* The prediction runs over the whole field, across block boundaries;  */
+/* blocks only group residuals for the fixed-length encoder.  Codes     */
+/* outside the field count as 0, so the first residual is the code.     */
+/*   predictor 2 (HSZp-nd): the multidimensional Lorenzo residual over   */
+/*     the field's axes: 1-D p_i = q_i - q_{i-1}; 2-D p_{i,j} = q_{i,j} - */
+/*     q_{i,j-1} - q_{i-1,j} + q_{i-1,j-1}; 3-D the eight-term form.     */
+/*   predictor 3 (HSZp): p_i = q_i - q_{i-1} over the row-major          */
+/*     flattened field, whatever its ndim.                               */
+/* Both are the Lorenzo residual over "prediction dimensions" L: the    */
+/* field's (n0, n1, n2) for predictor 2, (1, 1, N) for predictor 3.      */
+/* Reading: the paper's HSZp-nd also partitions the field into          */
+/* multidimensional blocks for encoding; here the residuals are grouped */
+/* into 1-D blocks of S in row-major order like every other predictor   */
+/* (the grouping changes the widths, not any value of D_p or D_q).      */
+/* ------------------------------------------------------------------ */
+static void global_dims(const int64_t *dims3, int64_t n, int pred, int64_t *L) {
+  if (pred == 3) {
+    L[0] = 1;
+    L[1] = 1;
+    L[2] = n;
+  } else {
+    L[0] = dims3[0];
+    L[1] = dims3[1];
+    L[2] = dims3[2];
+  }
+}
+
+static int64_t code_at(const int32_t *q, const int64_t *L, int64_t z, int64_t y, int64_t x) {
+  if (z < 0 || y < 0 || x < 0) return 0;
+  return q[(z * L[1] + y) * L[2] + x];
+}
+
+/* Lorenzo residual at flat index i, written term by term as in Section IV
+ * (the 3-D form; with leading axes of length 1 the terms that reach before
+ * the field vanish and the 2-D and 1-D forms remain). */
+static int64_t lorenzo_residual(const int32_t *q, const int64_t *L, int64_t i) {
+  int64_t x = i % L[2], y = (i / L[2]) % L[1], z = i / (L[2] * L[1]);
+  int64_t v = code_at(q, L, z, y, x) - code_at(q, L, z, y, x - 1) - code_at(q, L, z, y - 1, x) -
+              code_at(q, L, z - 1, y, x) + code_at(q, L, z, y - 1, x - 1) + code_at(q, L, z - 1, y, x - 1) +
+              code_at(q, L, z - 1, y - 1, x) - code_at(q, L, z - 1, y - 1, x - 1);
+  return v;
+}
+
 int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t *dims_in, double eps,
                             double eb, int eb_mode, int S, int pred, uint8_t *out, int64_t cap,
                             int64_t *out_bytes) {
   if (ndim < 1 || ndim > 3 || S < 1 || S > ORC_MAX_S || !(eps > 0.0)) return ORC_ERR_INVALID_ARG;
-  if (pred != 0 && pred != 1) return ORC_ERR_INVALID_ARG;
+  if (pred < 0 || pred > 3) return ORC_ERR_INVALID_ARG;
   if (dtype != 0 && dtype != 1) return ORC_ERR_INVALID_ARG;
   orc_header h;
   memset(&h, 0, sizeof h);
@@ -262,6 +312,8 @@ int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t
 
   int32_t *p = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
   if (!p) return ORC_ERR_INVALID_ARG;
+  int64_t L[3];
+  global_dims(h.dims, n, pred, L);
   int64_t word = 0; /* running payload word index */
   int64_t qmax = 0;
   int wmax = 0;
@@ -280,6 +332,27 @@ int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t
           p[k] = 0;
         } else {
           p[k] = q[first + k] - q[first + k - 1];
+          uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
+          if (m > maxmag) maxmag = m;
+        }
+      }
+    } else if (pred >= 2) {
+      /* HSZp-nd / HSZp: no block metadata; each slot holds the residual of
+       * the prediction over the whole field */
+      head = 0;
+      for (int64_t k = 0; k < S; k++) {
+        if (k >= Sb) {
+          p[k] = 0;
+        } else {
+          /* reading: a residual must fit the 31-bit magnitude of the
+           * encoder (|p| < 2^31); a field whose residual does not is
+           * rejected like a code out of range */
+          int64_t v = lorenzo_residual(q, L, first + k);
+          if (v <= -((int64_t)1 << 31) || v >= ((int64_t)1 << 31)) {
+            free(p);
+            return ORC_ERR_RANGE;
+          }
+          p[k] = (int32_t)v;
           uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
           if (m > maxmag) maxmag = m;
         }
@@ -440,7 +513,7 @@ static int parse(const uint8_t *s, int64_t bytes, orc_header *h) {
   h->total_bytes = (int64_t)get_u64(s, 128);
   h->wmax = (int)get_u32(s, 136);
   h->pred = (int)get_u32(s, 140);
-  if (h->pred != 0 && h->pred != 1) return ORC_ERR_CORRUPT;
+  if (h->pred < 0 || h->pred > 3) return ORC_ERR_CORRUPT;
   if (h->total_bytes != align16(h->off_payload + 4 * h->payload_words + 16)) return ORC_ERR_CORRUPT;
   if (h->total_bytes > bytes) return ORC_ERR_CORRUPT;
   if (!(h->eps > 0.0)) return ORC_ERR_CORRUPT;
@@ -550,7 +623,7 @@ static void put_p(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int
                   const int32_t *p) {
   (void)b;
   int32_t *dp = (int32_t *)ctx;
-  if (pred == 1) {
+  if (pred != 0) { /* every slot holds a residual (HSZx and the global predictors) */
     for (int64_t k = 0; k < Sb; k++) dp[first + k] = p[k];
     return;
   }
@@ -578,8 +651,40 @@ static void put_q(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int
     dq[first + k] = q;
   }
 }
+/* Global predictors: q is the inclusive prefix sum of D_p over every
+ * prediction axis, rebuilt plane by plane with the row-wise recurrence of
+ * Algorithm 4 (HSZp-2d): a prefix sum runs along the row, a column buffer
+ * accumulates it down the plane (colSum), and, for a 3-D field, the plane
+ * below is added (q_{k,i,j} = q_{k-1,i,j} + colSum_j).  In place. */
+static void lorenzo_rebuild(int32_t *a, const int64_t *L) {
+  int64_t *col = (int64_t *)calloc((size_t)L[2], sizeof(int64_t));
+  for (int64_t z = 0; z < L[0]; z++) {
+    for (int64_t x = 0; x < L[2]; x++) col[x] = 0;
+    for (int64_t y = 0; y < L[1]; y++) {
+      int64_t pref = 0;
+      for (int64_t x = 0; x < L[2]; x++) {
+        int64_t i = (z * L[1] + y) * L[2] + x;
+        pref += a[i];
+        col[x] += pref;
+        int64_t below = z > 0 ? a[i - L[1] * L[2]] : 0;
+        a[i] = (int32_t)(below + col[x]);
+      }
+    }
+  }
+  free(col);
+}
+
 int orc_decode_q(const uint8_t *s, int64_t bytes, int32_t *dq) {
-  return walk(s, bytes, put_q, dq, NULL);
+  orc_header h;
+  int st = parse(s, bytes, &h);
+  if (st) return st;
+  if (h.pred < 2) return walk(s, bytes, put_q, dq, NULL);
+  st = walk(s, bytes, put_p, dq, NULL);
+  if (st) return st;
+  int64_t L[3];
+  global_dims(h.dims, h.N, h.pred, L);
+  lorenzo_rebuild(dq, L);
+  return ORC_OK;
 }
 
 /* Stage 1 (D_m): the block metadata (heads, or the block means of HSZx). */
@@ -592,6 +697,11 @@ static void put_m(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int
   ((int32_t *)ctx)[b] = head;
 }
 int orc_decode_m(const uint8_t *s, int64_t bytes, int32_t *heads) {
+  orc_header h;
+  int st = parse(s, bytes, &h);
+  if (st) return st;
+  /* the global predictors keep no block metadata (Table 2: stages 2-4) */
+  if (h.pred >= 2) return ORC_ERR_UNSUPPORTED;
   return walk(s, bytes, put_m, heads, NULL);
 }
 
@@ -791,6 +901,148 @@ int orc_stats_f(const void *f, int dtype, int64_t n, double *mean, double *var) 
     s = t;
   }
   *var = (s + c) / (double)(n - 1);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Stage 2 of the global predictors (predictors 2 and 3).  L is the      */
+/* prediction shape (L0, L1, L2): the field's (n0, n1, n2) for HSZp-nd,  */
+/* (1, 1, N) for HSZp.  q at (z, y, x) is the sum of D_p over the box    */
+/* [0..z] x [0..y] x [0..x].                                            */
+/* ------------------------------------------------------------------ */
+
+/* Mean (Section V-A, "Operation with D_p", the HSZp-2d weighted sum and the
+ * HSZp identity sum q_i = sum (S - i + 1) p_i with the prediction running
+ * over the whole field): every p is counted once for each code of the box
+ * that starts at it, so sum q = sum p (L0 - z)(L1 - y)(L2 - x). */
+int orc_lorenzo_mean_p(const int32_t *dp, const int64_t *L, int64_t *s1) {
+  i128 t = 0;
+  for (int64_t z = 0; z < L[0]; z++)
+    for (int64_t y = 0; y < L[1]; y++)
+      for (int64_t x = 0; x < L[2]; x++) {
+        int64_t i = (z * L[1] + y) * L[2] + x;
+        t += (i128)dp[i] * (L[0] - z) * (L[1] - y) * (L[2] - x);
+      }
+  *s1 = (int64_t)t;
+  return ORC_OK;
+}
+
+/* Standard deviation inputs (Section V-A): Algorithm 4's column buffer and
+ * row prefix rebuild each q in turn (for a 3-D field on top of the same
+ * position of the plane below, for HSZp the single row's running sum eta),
+ * and s1 += q, s2 += q^2 are accumulated without storing D_q. */
+int orc_lorenzo_var_p(const int32_t *dp, const int64_t *L, int64_t *s1, uint64_t *s2_lo, uint64_t *s2_hi) {
+  int64_t *col = (int64_t *)calloc((size_t)L[2], sizeof(int64_t));
+  int64_t *below = (int64_t *)calloc((size_t)(L[1] * L[2]), sizeof(int64_t));
+  if (!col || !below) {
+    free(col);
+    free(below);
+    return ORC_ERR_INVALID_ARG;
+  }
+  int64_t a = 0;
+  u128 b = 0;
+  for (int64_t z = 0; z < L[0]; z++) {
+    for (int64_t x = 0; x < L[2]; x++) col[x] = 0;
+    for (int64_t y = 0; y < L[1]; y++) {
+      int64_t pref = 0;
+      for (int64_t x = 0; x < L[2]; x++) {
+        pref += dp[(z * L[1] + y) * L[2] + x];
+        col[x] += pref;
+        int64_t qv = below[y * L[2] + x] + col[x];
+        below[y * L[2] + x] = qv;
+        a += qv;
+        b += (u128)(qv * qv);
+      }
+    }
+  }
+  free(col);
+  free(below);
+  *s1 = a;
+  *s2_lo = (uint64_t)b;
+  *s2_hi = (uint64_t)(b >> 64);
+  return ORC_OK;
+}
+
+/* inclusive prefix sum of a (int64, shape L) along internal axis ax */
+static void prefix_along(int64_t *a, const int64_t *L, int ax) {
+  int64_t st = ax == 2 ? 1 : (ax == 1 ? L[2] : L[1] * L[2]);
+  for (int64_t z = 0; z < L[0]; z++)
+    for (int64_t y = 0; y < L[1]; y++)
+      for (int64_t x = 0; x < L[2]; x++) {
+        int64_t c = ax == 0 ? z : (ax == 1 ? y : x);
+        if (c == 0) continue;
+        int64_t i = (z * L[1] + y) * L[2] + x;
+        a[i] += a[i - st];
+      }
+}
+
+static int64_t dp_at(const int32_t *dp, const int64_t *L, int64_t z, int64_t y, int64_t x) {
+  return dp[(z * L[1] + y) * L[2] + x];
+}
+
+/* Derivative numerators on D_p of HSZp-nd (Section V-B, Eq. derivative_Dp
+ * and the sum form above it): q[i+1] - q[i-1] along axis a is the box sum
+ * of p over the other axes, taken at the two slices a = i and a = i + 1,
+ * i.e. D_a = P_other(r) with r(i) = p(i) + p(i + e_a); the recursion of
+ * Eq. derivative_Dp is this prefix sum written incrementally (eta along the
+ * row, the column accumulators across rows).  Edges (the reading of the
+ * stage-3 operation): at a = 0, 2 (q_1 - q_0) = 2 P_other(p(i + e_a)); at
+ * the last slice, 2 (q_{n-1} - q_{n-2}) = 2 P_other(p(i)); an axis of
+ * length 1 gives 0.  dims3 = the field's (n0, n1, n2); axis internal. */
+int orc_lorenzo_deriv_p(const int32_t *dp, const int64_t *dims3, int axis, int64_t *D) {
+  const int64_t *L = dims3;
+  for (int64_t z = 0; z < L[0]; z++)
+    for (int64_t y = 0; y < L[1]; y++)
+      for (int64_t x = 0; x < L[2]; x++) {
+        int64_t c[3] = {z, y, x};
+        int64_t len = L[axis], k = c[axis];
+        int64_t nx[3] = {z, y, x};
+        nx[axis] = k + 1;
+        int64_t r;
+        if (len == 1)
+          r = 0;
+        else if (k == 0)
+          r = 2 * dp_at(dp, L, nx[0], nx[1], nx[2]);
+        else if (k == len - 1)
+          r = 2 * dp_at(dp, L, z, y, x);
+        else
+          r = dp_at(dp, L, z, y, x) + dp_at(dp, L, nx[0], nx[1], nx[2]);
+        D[(z * L[1] + y) * L[2] + x] = r;
+      }
+  for (int ax = 0; ax < 3; ax++)
+    if (ax != axis) prefix_along(D, L, ax);
+  return ORC_OK;
+}
+
+/* Laplacian numerators on D_p of HSZp-nd (Section V-B, Eq. laplacian_Dp):
+ * per axis, (q[i+1] - q[i]) - (q[i] - q[i-1]) is the difference of two box
+ * sums of p over the other axes (the xi prefix sums of the paper): with
+ * t_a(i) = [i_a < n_a - 1] p(i + e_a) - [i_a > 0] p(i) (a missing neighbour
+ * replicates the edge value, so its difference is 0), L = sum_a P_other(t_a).
+ * dims3 = the field's (n0, n1, n2). */
+int orc_lorenzo_lap_p(const int32_t *dp, const int64_t *dims3, int64_t *Lout) {
+  const int64_t *L = dims3;
+  int64_t n = L[0] * L[1] * L[2];
+  int64_t *t = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  if (!t) return ORC_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; i++) Lout[i] = 0;
+  for (int a = 0; a < 3; a++) {
+    for (int64_t z = 0; z < L[0]; z++)
+      for (int64_t y = 0; y < L[1]; y++)
+        for (int64_t x = 0; x < L[2]; x++) {
+          int64_t c[3] = {z, y, x};
+          int64_t nx[3] = {z, y, x};
+          nx[a] = c[a] + 1;
+          int64_t v = 0;
+          if (c[a] < L[a] - 1) v += dp_at(dp, L, nx[0], nx[1], nx[2]);
+          if (c[a] > 0) v -= dp_at(dp, L, z, y, x);
+          t[(z * L[1] + y) * L[2] + x] = v;
+        }
+    for (int ax = 0; ax < 3; ax++)
+      if (ax != a) prefix_along(t, L, ax);
+    for (int64_t i = 0; i < n; i++) Lout[i] += t[i];
+  }
+  free(t);
   return ORC_OK;
 }
 

@@ -151,6 +151,8 @@ def _py_decode(stream):
         if w == 0:  # every p is 0: q = head (delta) or q = M_b (block mean)
             q[first:first + Sb] = heads[b]
             continue
+        if pred >= 2:
+            assert heads[b] == 0
         base = int(offs[b]) * 32
         k = np.arange(S)
         sign = bits[base + k]
@@ -158,7 +160,9 @@ def _py_decode(stream):
         mag = (bits[mb] << np.arange(w, dtype=np.uint64)).sum(axis=1).astype(np.int64)
         p = np.where(sign == 1, -mag, mag)
         assert np.all(p[Sb:] == 0)
-        if pred == 1:  # block mean: q = M_b + p
+        if pred >= 2:  # global predictors: the slots hold residuals, no heads
+            q[first:first + Sb] = p[:Sb]
+        elif pred == 1:  # block mean: q = M_b + p
             q[first:first + Sb] = heads[b] + p[:Sb]
         else:  # delta inside the block: q = head + prefix sum, p_0 = 0
             assert p[0] == 0
@@ -166,6 +170,13 @@ def _py_decode(stream):
     chunk_g = max(1, 4096 // S)
     chunks = s[oc:oc + 8 * (-(-nb // chunk_g) + 1)].view("<u8").astype(np.int64)
     np.testing.assert_array_equal(chunks, offs[::chunk_g].tolist() + ([offs[-1]] if nb % chunk_g else []))
+    if pred == 3:  # HSZp: q is the running sum over the flattened field
+        q = np.cumsum(q)
+    elif pred == 2:  # HSZp-nd: q is the running sum along every axis
+        q = q.reshape(u64(8), u64(16), u64(24))
+        for a in range(3):
+            q = np.cumsum(q, axis=a)
+        q = q.reshape(-1)
     return q, widths
 
 
@@ -571,3 +582,138 @@ def test_curl_equals_library_gradients(orc, rng):
         ref = np.gradient(qu * 2 * eu, axis=1, edge_order=1) - np.gradient(qv * 2 * ev, axis=0, edge_order=1)
         np.testing.assert_allclose(val, ref, rtol=1e-12, atol=1e-12)
         np.testing.assert_array_equal(num, orc.deriv_q(qu, 1) - orc.deriv_q(qv, 0))
+
+
+# ------------------------------------------ global predictors (HSZp-nd, HSZp)
+GLOBAL_SHAPES = [(1,), (7,), (300,), (5, 9), (33, 40), (1, 6), (4, 6, 7), (1, 5, 3), (2, 1, 9), (3, 4, 1),
+                 (9, 10, 11)]
+
+
+def _residuals_numpy(q, pred):
+    """Backward differences with a zero before the field (numpy.diff): along
+    every axis for the Lorenzo predictor, over the flattened field for HSZp."""
+    r = q.astype(np.int64)
+    if pred == 3:
+        return np.diff(r.ravel(), prepend=0).reshape(q.shape)
+    for a in range(q.ndim):
+        r = np.diff(r, axis=a, prepend=0)
+    return r
+
+
+def _smooth_codes(rng, shape, scale=400):
+    x = rng.standard_normal(shape)
+    for a in range(len(shape)):
+        x = np.cumsum(x, axis=a)
+    return (x * scale / max(1.0, np.abs(x).max()) + rng.integers(-3, 4, size=shape)).astype(np.int32)
+
+
+@pytest.mark.parametrize("pred", [2, 3])
+@pytest.mark.parametrize("shape", GLOBAL_SHAPES)
+def test_global_predictor_residuals_and_roundtrip(orc, rng, pred, shape):
+    """Section IV, HSZp and HSZp-nd: D_p is the backward difference across
+    block boundaries (numpy.diff), D_q returns the codes, the independent
+    reader rebuilds them with numpy.cumsum, each width is the bit length of
+    the block's largest |p|, heads are zero and there is no stage 1."""
+    q = _smooth_codes(rng, shape)
+    for S in (32, 7, 64):
+        s = orc.compress_codes(q, 0.01, S, pred=pred)
+        assert orc.read_header(s)["pred"] == pred
+        p_ref = _residuals_numpy(q, pred)
+        np.testing.assert_array_equal(orc.decode(s, "p"), p_ref)
+        np.testing.assert_array_equal(orc.decode(s, "q"), q)
+        q_py, widths = _py_decode(s)
+        np.testing.assert_array_equal(q_py.reshape(shape), q)
+        flat = np.abs(p_ref.ravel())
+        for b in range(widths.size):
+            assert widths[b] == int(flat[b * S:(b + 1) * S].max()).bit_length()
+        with pytest.raises(orc.OracleError) as e:
+            orc.decode(s, "m")
+        assert e.value.status == 4
+
+
+def test_global_predictor_hand_example(orc):
+    """A 2x3 field worked by hand: the 2-D Lorenzo residuals are
+    [[1, 2, 3], [1, 1, 1]] (row 1: 2-1, 5-2-3+1, 9-5-6+3) and the flattened
+    HSZp residuals are [1, 2, 3, -4, 3, 4]."""
+    q = np.array([[1, 3, 6], [2, 5, 9]], np.int32)
+    s2 = orc.compress_codes(q, 0.5, 4, pred=2)
+    np.testing.assert_array_equal(orc.decode(s2, "p"), [[1, 2, 3], [1, 1, 1]])
+    s3 = orc.compress_codes(q, 0.5, 4, pred=3)
+    np.testing.assert_array_equal(orc.decode(s3, "p").ravel(), [1, 2, 3, -4, 3, 4])
+    # mean on D_p: weights (n1 - i)(n2 - j) = [[6, 4, 2], [3, 2, 1]] for the 2-D form
+    assert orc.lorenzo_mean_p(orc.decode(s2, "p"), 2) == 6 + 8 + 6 + 3 + 2 + 1 == int(q.sum())
+    assert orc.lorenzo_mean_p(orc.decode(s3, "p"), 3) == 6 * 1 + 5 * 2 + 4 * 3 - 3 * 4 + 2 * 3 + 1 * 4
+
+
+def test_global_predictor_residual_range(orc):
+    """A residual must fit the encoder's 31-bit magnitude: a checkerboard of
+    +-A codes has 3-D Lorenzo residuals of magnitude 8 A inside the field."""
+    z, y, x = np.meshgrid(np.arange(3), np.arange(3), np.arange(3), indexing="ij")
+    sign = 1 - 2 * ((x + y + z) % 2)
+    ok = (sign * (2**28 - 1)).astype(np.int32)
+    s = orc.compress_codes(ok, 1.0, 32, pred=2)
+    assert int(np.abs(orc.decode(s, "p")).max()) == 8 * (2**28 - 1)
+    np.testing.assert_array_equal(orc.decode(s, "q"), ok)
+    with pytest.raises(orc.OracleError) as e:
+        orc.compress_codes((sign * 2**28).astype(np.int32), 1.0, 32, pred=2)
+    assert e.value.status == 2
+
+
+def _box_weights(shape):
+    """Brute force: the number of codes whose box [0..i] contains position j."""
+    w = np.zeros(shape, np.int64)
+    for j in np.ndindex(*shape):
+        w[j] = int(np.prod([n - c for n, c in zip(shape, j)]))
+    return w
+
+
+@pytest.mark.parametrize("pred", [2, 3])
+@pytest.mark.parametrize("shape", [(1,), (17,), (5, 9), (4, 6, 7), (2, 1, 9), (9, 10, 11)])
+def test_global_predictor_stage2_statistics(orc, rng, pred, shape):
+    """Section V-A on D_p: the weighted sum equals sum q, the Algorithm 4
+    accumulators equal (sum q, sum q^2) exactly, and the weights are the
+    brute-force box counts."""
+    q = _smooth_codes(rng, shape, scale=3000)
+    s = orc.compress_codes(q, 0.01, 32, pred=pred)
+    dp = orc.decode(s, "p")
+    qi = [int(v) for v in q.ravel()]
+    assert orc.lorenzo_mean_p(dp, pred) == sum(qi)
+    s1, s2 = orc.lorenzo_var_p(dp, pred)
+    assert s1 == sum(qi) and s2 == sum(v * v for v in qi)
+    wshape = shape if pred == 2 else (q.size,)
+    w = _box_weights(wshape)
+    assert int((w.ravel() * dp.ravel().astype(np.int64)).sum()) == sum(qi)
+
+
+@pytest.mark.parametrize("shape", [(9,), (2,), (5, 9), (2, 7), (4, 6, 7), (1, 5, 3), (2, 1, 9), (3, 4, 2),
+                                   (8, 9, 10)])
+def test_lorenzo_stage2_derivative_equals_library_gradient(orc, rng, shape):
+    """Section V-B on D_p (Eq. derivative_Dp and its box-sum form): the
+    numerators equal 2 numpy.gradient of the codes (one-sided edges); an
+    axis of length 1 gives 0."""
+    q = _smooth_codes(rng, shape, scale=2000)
+    dp = orc.decode(orc.compress_codes(q, 0.01, 32, pred=2), "p")
+    for a in range(q.ndim):
+        D = orc.lorenzo_deriv_p(dp, a)
+        if shape[a] == 1:
+            assert not D.any()
+            continue
+        g = 2 * np.gradient(q.astype(np.float64), axis=a)
+        np.testing.assert_array_equal(D, g.astype(np.int64))
+        np.testing.assert_array_equal(D, orc.deriv_q(q, a))
+
+
+@pytest.mark.parametrize("shape", [(9,), (2,), (1,), (5, 9), (2, 7), (4, 6, 7), (1, 5, 3), (2, 1, 9),
+                                   (8, 9, 10)])
+def test_lorenzo_stage2_laplacian_equals_library(orc, rng, shape):
+    """Section V-B on D_p (Eq. laplacian_Dp, the xi prefix sums): the
+    numerators equal scipy.ndimage.laplace on the codes with replicated
+    edges."""
+    from scipy import ndimage
+
+    q = _smooth_codes(rng, shape, scale=2000)
+    dp = orc.decode(orc.compress_codes(q, 0.01, 32, pred=2), "p")
+    L = orc.lorenzo_lap_p(dp)
+    ref = ndimage.laplace(q.astype(np.float64), mode="nearest")
+    np.testing.assert_array_equal(L, ref.astype(np.int64))
+    np.testing.assert_array_equal(L, orc.lap_q(q))
