@@ -317,13 +317,18 @@ def read_profile_traffic(kernel_tag: str):
     return float(m.group(1)) / float(n.group(1))
 
 
+# device sources of the one-pass kernel (and of the tile helpers it shares with
+# the other profiled kernels): a profile's traffic is used only while these
+# are unchanged since its capture
+KERNEL_SOURCES = ("hc_stencil_pipe.cu", "hc_stencil_pipe.cuh", "hc_stencil_tile.cuh", "hc_internal.cuh",
+                  "hc_finish.cuh")
+
+
 def csrc_hash():
     d = hashlib.sha256()
-    for sub in ("paper_2603_25206_gb300/csrc", "include"):
-        base = os.path.join(ROOT, sub)
-        for fn in sorted(os.listdir(base)):
-            d.update(fn.encode())
-            d.update(open(os.path.join(base, fn), "rb").read())
+    for fn in KERNEL_SOURCES:
+        d.update(fn.encode())
+        d.update(open(os.path.join(ROOT, "paper_2603_25206_gb300", "csrc", fn), "rb").read())
     return d.hexdigest()
 
 
@@ -893,6 +898,120 @@ def run_hszx(args):
     return 0
 
 
+def run_lorenzo(args):
+    """The global predictors on the paper-like workload: the same five fields
+    compressed as HSZp-nd (Lorenzo over the field's axes) and as HSZp (delta
+    across blocks over the flattened field), block 32, eb 1e-3 value-range
+    relative.  Per field: the stream sizes beside the block-head stream; the
+    fused stage-2 mean (weighted sum), the statistics and the derivative along
+    the first axis and the Laplacian at stages 2 and 3, against the plain path
+    (decompress to float32, then the operation); decompression to D_q.
+    Median CUDA-event time over 5 runs with an L2 flush before each; GB/s
+    counts the field's original bytes.  The roofline line is the stage-2 mean
+    kernel (k_global_mean) at its algorithmic bytes, the compressed stream."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peak, peak_src = measured_peaks()
+    rows, tot = [], {}
+    mean_bytes = 0
+    for shape, x in make_fields():
+        xd = torch.from_numpy(x).to(dev)
+        cl = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK, predictor="lorenzo"))
+        cg = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK, predictor="global"))
+        cd = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK))
+        del xd
+        n = int(np.prod(shape))
+        scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
+        df = torch.empty(shape, dtype=torch.float32, device=dev)
+        dq = torch.empty(shape, dtype=torch.int32, device=dev)
+        fo = torch.empty(shape, dtype=torch.float32, device=dev)
+        sf = hc.as_stage(cl, "f", df)
+
+        def plain(op, c=cl):
+            hc.decompress(c, "f", out=df)
+            op()
+
+        t = {
+            "decompress_q": time_call(torch, dev, lambda: hc.decompress(cl, "q", out=dq)),
+            "mean_stage2": time_call(torch, dev, lambda: hc.mean(cl, level="p", out=scal)),
+            "mean_stage3": time_call(torch, dev, lambda: hc.mean(cl, level="q", out=scal)),
+            "mean_plain": time_call(torch, dev, lambda: plain(lambda: hc.mean(sf, out=scal))),
+            "std_stage2": time_call(torch, dev, lambda: hc.variance(cl, level="p", out=scal)),
+            "std_plain": time_call(torch, dev, lambda: plain(lambda: hc.variance(sf, out=scal))),
+            "deriv0_stage2": time_call(torch, dev, lambda: hc.derivative(cl, 0, level="p", out=fo)),
+            "deriv0_stage3": time_call(torch, dev, lambda: hc.derivative(cl, 0, level="q", out=fo)),
+            "deriv0_plain": time_call(torch, dev, lambda: plain(lambda: hc.derivative(sf, 0, out=fo))),
+            "lap_stage2": time_call(torch, dev, lambda: hc.laplacian(cl, level="p", out=fo)),
+            "lap_stage3": time_call(torch, dev, lambda: hc.laplacian(cl, level="q", out=fo)),
+            "lap_plain": time_call(torch, dev, lambda: plain(lambda: hc.laplacian(sf, out=fo))),
+            "hszp_mean_stage2": time_call(torch, dev, lambda: hc.mean(cg, level="p", out=scal)),
+            "hszp_mean_plain": time_call(torch, dev, lambda: plain(lambda: hc.mean(sf, out=scal), cg)),
+        }
+        mean_bytes += cl.nbytes + 64
+        sp = lambda a, b: round(t[a] / t[b], 2)
+        rows.append({"field": "x".join(map(str, shape)), "lorenzo_bytes": cl.nbytes, "hszp_bytes": cg.nbytes,
+                     "delta_bytes": cd.nbytes, "ms": {k: round(v, 4) for k, v in t.items()},
+                     "gbs_orig": {k: round(n * 4 / v / 1e6, 1) for k, v in t.items()},
+                     "speedup_vs_plain": {"mean_stage2": sp("mean_plain", "mean_stage2"),
+                                          "mean_stage3": sp("mean_plain", "mean_stage3"),
+                                          "std_stage2": sp("std_plain", "std_stage2"),
+                                          "deriv0_stage2": sp("deriv0_plain", "deriv0_stage2"),
+                                          "deriv0_stage3": sp("deriv0_plain", "deriv0_stage3"),
+                                          "lap_stage2": sp("lap_plain", "lap_stage2"),
+                                          "lap_stage3": sp("lap_plain", "lap_stage3"),
+                                          "hszp_mean_stage2": sp("hszp_mean_plain", "hszp_mean_stage2")}})
+        for k, v in t.items():
+            tot[k] = tot.get(k, 0.0) + v
+        del cl, cg, cd, df, dq, fo
+    orig = sum(int(np.prod(sh)) * 4 for sh in synth_shapes())
+    achieved = mean_bytes / (tot["mean_stage2"] * 1e-3) / 1e9
+    line = {"metric": "global predictors (HSZp-nd, HSZp): GB/s of original data per stage, vs the plain path",
+            "unit": "GB/s", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("block 32;", "block 32, Lorenzo predictor (HSZp-nd) and "
+                                                                 "delta across blocks (HSZp);"),
+                       "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
+            "roofline": {"kernel": "k_global_mean", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                         "algorithmic_bytes": "compressed stream + 64 B per field"},
+            "totals_ms": {k: round(v, 4) for k, v in tot.items()},
+            "totals_gbs_orig": {k: round(orig / v / 1e6, 1) for k, v in tot.items()},
+            "per_field": rows}
+    print(json.dumps(line))
+    return 0
+
+
+def run_profile_lorenzo():
+    """Small case for ncu captures of the global-predictor kernels: one
+    256x384x384 float32 field as HSZp-nd (compressed ~40 MB, D_q 151 MB), the
+    stage-2 mean three times, then decompression to D_q and the stage-2
+    derivative along the first axis."""
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    x = synth.grf_field((256, 384, 384), 1002)
+    c = hc.compress(torch.from_numpy(x).cuda(), EB, rel=True, S=BLOCK, predictor="lorenzo")
+    dq = torch.empty(x.shape, dtype=torch.int32, device="cuda")
+    out = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        hc.mean(c, level="p")
+    hc.decompress(c, "q", out=dq)
+    hc.derivative(c, 0, level="p", out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_lorenzo": "ok", "compressed_bytes": c.nbytes, "wmax": int(c.header.wmax)}))
+    return 0
+
+
 def run_wide(args):
     """The wide-code configuration: one float64 512 x 512 x 1024 field (k^-3
     field times 1e4 plus a linear trend), block 64, value-range-relative
@@ -1035,6 +1154,9 @@ def main(argv=None):
     ap.add_argument("--serving", action="store_true", help="the serving form (200 resident fields, Poisson queries)")
     ap.add_argument("--hszx", action="store_true", help="the block-mean (HSZx) form of the paper-like workload")
     ap.add_argument("--wide", action="store_true", help="the wide-code float64 configuration")
+    ap.add_argument("--lorenzo", action="store_true",
+                    help="the global predictors (HSZp-nd, HSZp) on the paper-like workload")
+    ap.add_argument("--profile-lorenzo", action="store_true", help="run the small global-predictor ncu case")
     ap.add_argument("--fields", type=int, default=200)
     ap.add_argument("--qps", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=30.0)
@@ -1049,6 +1171,10 @@ def main(argv=None):
         return run_hszx(args)
     if args.wide:
         return run_wide(args)
+    if args.lorenzo:
+        return run_lorenzo(args)
+    if args.profile_lorenzo:
+        return run_profile_lorenzo()
     if args.batched:
         if args.warmup < 3:
             args.warmup = 3

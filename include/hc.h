@@ -64,11 +64,27 @@ typedef enum {
   HC_OP_MULTI = 5 /* every operation in one pass (hc_op_multi) */
 } hc_op;
 typedef enum { HC_EB_ABS = 0, HC_EB_REL = 1 } hc_eb_mode;
-/* Decorrelation inside a block (Section IV).  DELTA: the block's first code is
- * metadata and p_k = q_k - q_{k-1} (HSZp with SZp-style block heads).  MEAN:
- * the block mean M_b (nearest integer to the code sum over the block size,
- * ties toward zero) is metadata and p_k = q_k - M_b (HSZx). */
-typedef enum { HC_PRED_DELTA = 0, HC_PRED_MEAN = 1 } hc_predictor;
+/* Decorrelation (Section IV).  DELTA: the block's first code is metadata and
+ * p_k = q_k - q_{k-1} inside the block (HSZp with SZp-style block heads).
+ * MEAN: the block mean M_b (nearest integer to the code sum over the block
+ * size, ties toward zero) is metadata and p_k = q_k - M_b (HSZx).
+ * The two global predictors keep no block metadata (heads are 0) and predict
+ * across block boundaries; blocks only group residuals for the encoder:
+ *   LORENZO (HSZp-nd): the multidimensional Lorenzo residual over the
+ *     field's axes -- 1-D p_i = q_i - q_{i-1}; 2-D p_{i,j} = q_{i,j} -
+ *     q_{i,j-1} - q_{i-1,j} + q_{i-1,j-1}; 3-D the eight-term form -- with
+ *     codes before the field taken as 0;
+ *   GLOBAL_DELTA (HSZp): p_i = q_i - q_{i-1} over the row-major flattened
+ *     field (p_0 = q_0), whatever its ndim.
+ * So q is the prefix sum of D_p over every prediction axis (the field's axes
+ * for LORENZO, the flattened field for GLOBAL_DELTA).  A global-predictor
+ * residual must satisfy |p| < 2^31 (else HC_ERR_RANGE at compression). */
+typedef enum {
+  HC_PRED_DELTA = 0,
+  HC_PRED_MEAN = 1,
+  HC_PRED_LORENZO = 2,
+  HC_PRED_GLOBAL_DELTA = 3
+} hc_predictor;
 typedef enum {
   HC_STAGE_COMPRESSED = 0, /* the stream itself (operations fuse decoding in) */
   HC_STAGE_M = 1,          /* D_m: heads int32[nb] */
@@ -138,8 +154,14 @@ HC_API int hc_version(void);
 HC_API size_t hc_compress_bound(int64_t n, int S);
 /* Workspace of hc_compress for N elements at block size S. */
 HC_API size_t hc_compress_workspace_bytes(int64_t n, int S);
-/* Workspace of any hc_decompress_to_stage / hc_op_* call (one size fits all). */
+/* Workspace of any hc_decompress_to_stage / hc_op_* call on a DELTA or MEAN
+ * stream or on a stage array (one size fits all). */
 HC_API size_t hc_workspace_bytes(void);
+/* Workspace of any call on the stream `hdr` describes: hc_workspace_bytes()
+ * for DELTA and MEAN streams; for the global predictors (LORENZO,
+ * GLOBAL_DELTA) hc_workspace_bytes() plus scratch for a rebuilt D_q and the
+ * prefix sums (about 12.3 bytes per element).  0 for a NULL header. */
+HC_API size_t hc_workspace_bytes_for(const hc_header* hdr);
 /* Bytes of a materialized stage (M, P, Q or F; F in the header's dtype). */
 HC_API size_t hc_stage_bytes(const hc_header* hdr, int kind);
 
@@ -184,12 +206,16 @@ HC_API int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out
 
 /* ---------------------------------------------------------- decompression */
 /* D_i ... D_1 (Algorithm 2): decode the whole stream to stage `kind`:
- *   HC_STAGE_M -> int32 heads[nb] (HC_PRED_MEAN: the block means);
+ *   HC_STAGE_M -> int32 heads[nb] (HC_PRED_MEAN: the block means; the
+ *   global predictors have no stage 1: HC_ERR_UNSUPPORTED);
  *   HC_STAGE_P -> int32[N] (HC_PRED_DELTA: head in each block's first slot,
- *   so q is the in-block prefix sum; HC_PRED_MEAN: p = q - M_b); HC_STAGE_Q ->
- *   int32[N]; HC_STAGE_F -> out_dtype HC_F32 ((float)q * (float)(2 eps)) or
- *   HC_F64 ((double)q * 2 eps).
+ *   so q is the in-block prefix sum; HC_PRED_MEAN: p = q - M_b; the global
+ *   predictors: their residuals); HC_STAGE_Q -> int32[N] (global
+ *   predictors: prefix sums of D_p along every prediction axis); HC_STAGE_F
+ *   -> out_dtype HC_F32 ((float)q * (float)(2 eps)) or HC_F64 ((double)q *
+ *   2 eps).
  * d_out holds hc_stage_bytes(hdr, kind) bytes (8 per element for F64).
+ * ws_bytes >= hc_workspace_bytes_for(hdr).
  * ASYNC; corruption is reported in the workspace status word. */
 HC_API int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, int kind, void* d_out, int out_dtype,
                            void* d_ws, size_t ws_bytes, void* stream);
@@ -216,6 +242,15 @@ HC_API int hc_workspace_status(void* d_ws, void* stream);
  *     S and n set): the mean of Eq. mean_m, (T / N) 2 eps, from the block
  *     means alone; s1 = T, exact = 0; mean only (the variance needs the codes).
  *     HC_PRED_DELTA heads support no statistic (HC_ERR_UNSUPPORTED).
+ *   Global predictors (stream inputs; ws_bytes >= hc_workspace_bytes_for):
+ *     level P mean: sum q = sum_i p_i (L0 - z)(L1 - y)(L2 - x), (z, y, x)
+ *     the position of p_i in the prediction shape L (the field's shape for
+ *     LORENZO, (1, 1, N) for GLOBAL_DELTA; Section V-A's HSZp-2d and HSZp
+ *     weighted sums), fused with the decode, no prefix sum, exact;
+ *     level P variance (Algorithm 4: q rebuilt by prefix sums, s1 and s2
+ *     accumulated) and level Q: D_q rebuilt in the workspace, then the
+ *     exact stage-3 sums.  Arrays of their D_p are refused (operate on the
+ *     stream); levels M are HC_ERR_UNSUPPORTED.
  * ASYNC. */
 HC_API int hc_op_mean(const hc_stage* in, double eps, int ndim, const int64_t* dims, hc_scalar* d_out, void* d_ws,
                size_t ws_bytes, void* stream);
@@ -248,7 +283,15 @@ HC_API int hc_op_variance_noalloc(const hc_stage* in, double eps, int ndim, cons
 /* Numerical differentiation (Section V-B, "Operation with D_q").  Inputs: the
  * stream (fused, level Q), or a materialized Q or F array.  A stage-P input
  * returns HC_ERR_UNSUPPORTED: a 1-D block partition does not keep the
- * multidimensional layout (Section V-B).  `axis` is a user axis in
+ * multidimensional layout (Section V-B) -- except for HC_PRED_LORENZO
+ * (HSZp-nd) streams at level P: the derivative along axis a is the box sum of
+ * D_p over the other axes at slices a = i and i + 1 (Eq. derivative_Dp and
+ * the sum form above it), the Laplacian the sum over axes of differences of
+ * such box sums (Eq. laplacian_Dp), computed from D_p by prefix sums over
+ * the other axes only, never forming D_q; the gradient magnitude is not
+ * offered there (HC_ERR_UNSUPPORTED).  Global-predictor streams at level Q
+ * rebuild D_q in the workspace and take the stage-3 operation on it
+ * (ws_bytes >= hc_workspace_bytes_for).  `axis` is a user axis in
  * [0, ndim), 0 the slowest.  d_out: N elements of out_dtype:
  *   HC_F32 / HC_F64  the scaled value (eps * D, eps * |grad|, 2 eps * L),
  *   HC_I64           the exact integer numerator (D or L; integer inputs).

@@ -137,7 +137,7 @@ int check_header(const hc_header& h) {
     return fail(HC_ERR_CORRUPT, "payload size and total size disagree");
   if ((size_t)h.total_bytes > L.bound) return fail(HC_ERR_CORRUPT, "payload larger than any valid stream");
   if (h.wmax > 31) return fail(HC_ERR_CORRUPT, "max width above 31");
-  if (h.pred != HC_PRED_DELTA && h.pred != HC_PRED_MEAN) return fail(HC_ERR_CORRUPT, "unknown predictor");
+  if (h.pred > HC_PRED_GLOBAL_DELTA) return fail(HC_ERR_CORRUPT, "unknown predictor");
   if (!(h.eps > 0.0) || !std::isfinite(h.eps)) return fail(HC_ERR_CORRUPT, "bad eps");
   if (h.qmax >= (1u << 30)) return fail(HC_ERR_CORRUPT, "max |q| out of range");
   return HC_OK;
@@ -217,6 +217,8 @@ static int check_op(const hc_stage* in, double eps, int ndim, const int64_t* dim
     return fail(HC_ERR_UNSUPPORTED, "HSZp-style metadata supports no operation (Section V)");
   if (in->kind == HC_STAGE_P && in->pred == HC_PRED_MEAN)
     return fail(HC_ERR_UNSUPPORTED, "a block-mean D_p array needs its block means: operate on the stream");
+  if ((in->kind == HC_STAGE_P || in->kind == HC_STAGE_M) && in->pred >= HC_PRED_LORENZO)
+    return fail(HC_ERR_UNSUPPORTED, "a global-predictor D_p array: operate on the stream");
   if (in->kind < HC_STAGE_M || in->kind > HC_STAGE_F) return fail(HC_ERR_INVALID_ARG, "unknown stage kind");
   return HC_OK;
 }
@@ -263,6 +265,11 @@ size_t hc_compress_workspace_bytes(int64_t n, int S) {
 }
 
 size_t hc_workspace_bytes(void) { return kOpWsBytes; }
+
+size_t hc_workspace_bytes_for(const hc_header* hdr) {
+  if (!hdr) return 0;
+  return global_workspace_bytes(hdr);
+}
 
 size_t hc_stage_bytes(const hc_header* hdr, int kind) {
   if (!hdr) return 0;
@@ -323,6 +330,8 @@ int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, int kind,
   if (kind < HC_STAGE_M || kind > HC_STAGE_F) return fail(HC_ERR_INVALID_ARG, "kind must be M, P, Q or F");
   if (kind == HC_STAGE_F && out_dtype != HC_F32 && out_dtype != HC_F64)
     return fail(HC_ERR_INVALID_ARG, "F output is HC_F32 or HC_F64");
+  if (hdr->pred >= HC_PRED_LORENZO)
+    return global_decode_impl(hdr, d_stream, kind, d_out, out_dtype, d_ws, ws_bytes, as_stream(stream));
   return decode_impl(hdr, d_stream, kind, d_out, out_dtype, d_ws, as_stream(stream));
 }
 
@@ -343,8 +352,11 @@ static int stats(const hc_stage* in, double eps, int ndim, const int64_t* dims, 
   int rc = check_op(in, eps, ndim, dims, d_ws, ws_bytes, dims3);
   if (rc) return rc;
   if (!d_out) return fail(HC_ERR_INVALID_ARG, "null output");
-  if (in->kind == HC_STAGE_COMPRESSED)
+  if (in->kind == HC_STAGE_COMPRESSED) {
+    if (in->hdr->pred >= HC_PRED_LORENZO)
+      return global_stats_impl(in->hdr, in->d_data, in->level, what, d_out, d_ws, ws_bytes, as_stream(stream));
     return reduce_stream_impl(in->hdr, in->d_data, in->level, what, d_out, d_ws, as_stream(stream));
+  }
   if (in->kind == HC_STAGE_M) {
     // block means of an HSZx stream (Eq. mean_m): the mean only
     if (what != RED_MEAN) return fail(HC_ERR_UNSUPPORTED, "stage 1 gives the mean only (Eq. mean_m)");
@@ -379,6 +391,9 @@ static int stencil(const hc_stage* in, double eps, int ndim, const int64_t* dims
   const int axis3 = axis + 3 - ndim;
   if (in->kind == HC_STAGE_COMPRESSED) {
     if (in->level == HC_STAGE_M) return fail(HC_ERR_UNSUPPORTED, "stage 1 holds no point values to differentiate");
+    if (in->hdr->pred >= HC_PRED_LORENZO)
+      return global_stencil_impl(in->hdr, in->d_data, in->level, op, axis3, d_out, out_dtype, d_ws, ws_bytes,
+                                 as_stream(stream));
     if (in->level == HC_STAGE_P)
       return fail(HC_ERR_UNSUPPORTED,
                   "stage-2 differentiation is not defined for a 1-D block partition (Section V-B)");
@@ -430,6 +445,7 @@ int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_
       return HC_OK;  // statistics have no tunable tile
   }
   if (out_dtype != HC_F32 && out_dtype != HC_F64 && out_dtype != HC_I64) return fail(HC_ERR_INVALID_ARG, "out_dtype");
+  if (in->hdr->pred >= HC_PRED_LORENZO) return HC_OK;  // global predictors: no tiled kernel to tune
   int64_t d3[3];
   stencil_walk_dims(in->hdr, d3, nullptr);
   return stencil_pipe_autotune(in->hdr, in->d_data, d3, sop, d_out, out_dtype, d_ws, as_stream(stream), chosen);
@@ -448,7 +464,7 @@ int hc_op_multi(const hc_stage* in, double eps, int ndim, const int64_t* dims, c
     if (out->d_derivative[a]) return fail(HC_ERR_INVALID_ARG, "derivative output for an axis >= ndim");
   for (void* f : fields)
     if (f && !aligned16(f)) return fail(HC_ERR_INVALID_ARG, "outputs must be 16-byte aligned device buffers");
-  if (in->kind == HC_STAGE_COMPRESSED) {
+  if (in->kind == HC_STAGE_COMPRESSED && in->hdr->pred < HC_PRED_LORENZO) {
     if (in->level == HC_STAGE_P && (out->d_derivative[0] || out->d_derivative[1] || out->d_derivative[2] ||
                                     out->d_gradmag || out->d_laplacian))
       return fail(HC_ERR_UNSUPPORTED, "stage-2 differentiation is not defined for a 1-D block partition (Section V-B)");
@@ -497,6 +513,8 @@ static int vector_op(const hc_stage* comps, int ncomp, int ndim, const int64_t* 
       return fail(HC_ERR_UNSUPPORTED, "vector operations take compressed streams");
     if (in.level != HC_STAGE_Q)
       return fail(HC_ERR_UNSUPPORTED, "vector operations on a 1-D block partition run at stage Q (Section V-C)");
+    if (in.hdr->pred >= HC_PRED_LORENZO)
+      return fail(HC_ERR_UNSUPPORTED, "vector operations take block-coded streams: decompress global ones to stage Q");
     int64_t dims3[3];
     int rc = check_op(&in, in.hdr->eps, ndim, dims, d_ws, ws_bytes, dims3);
     if (rc) return rc;

@@ -366,6 +366,8 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
     const hc_batch_item& x = items[i];
     const hc_header& h = x.hdr;
     int rc = check_header(h);
+    if (!rc && h.pred >= HC_PRED_LORENZO)
+      return fail(HC_ERR_UNSUPPORTED, "batch: global-predictor streams need hc_workspace_bytes_for scratch");
     if (rc) return rc;
     if (!x.d_stream || !aligned16(x.d_stream)) return fail(HC_ERR_INVALID_ARG, "batch: stream pointer");
     if (x.ops == 0 || (x.ops & ~(field_ops | HC_BATCH_MEAN | HC_BATCH_VARIANCE)))

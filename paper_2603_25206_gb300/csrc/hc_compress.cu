@@ -6,8 +6,8 @@
 //   k_minmax       value range of the field (value-range-relative bound)
 //   k_eps          eps = eb or eb * (max - min)
 //   k_blocks       quantize, block metadata (first code, or the block mean
-//                  for HSZx), block width, words per chunk, max |q|,
-//                  max width                                     (one thread / block)
+//                  for HSZx, or none for the global predictors), block
+//                  width, words per chunk, max |q|, max width    (one thread / block)
 //   k_chunk_scan   exclusive scan of the words per chunk -> chunk index
 //   k_pack         sign words + w-bit magnitudes of every block  (one thread / block)
 //   k_header       header and the zero padding between sections
@@ -152,8 +152,39 @@ struct OutStream {
   uint32_t* payload;
   int64_t N, nb, nchunks;
   int S, G, nseg;
-  int pred;  // hc_predictor
+  int pred;      // hc_predictor
+  int64_t L[3];  // prediction shape of the global predictors: (n0, n1, n2), or (1, 1, N) for HSZp
 };
+
+// Residual of the global predictors at flat index i (Section IV, HSZp and
+// HSZp-nd): the Lorenzo residual over the prediction shape L, with codes
+// outside the field taken as 0 -- sum over the corners d of {0,1}^3 of
+// (-1)^(d0+d1+d2) q(i - d).  With leading axes of length 1 it is the 2-D
+// four-term or the 1-D two-term form.  The neighbours are quantized again
+// here (the same rule, so the same codes).  Returns false when a code is out
+// of range or the residual does not fit the encoder's 31-bit magnitude.
+template <class Src>
+__device__ __forceinline__ bool global_residual(const Src& src, const OutStream& o, int64_t i, double two_eps,
+                                                int32_t& p) {
+  const int64_t x = i % o.L[2], r = i / o.L[2];
+  const int64_t y = r % o.L[1], z = r / o.L[1];
+  long long acc = 0;
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const int dz = d >> 2, dy = (d >> 1) & 1, dx = d & 1;
+    if ((dz && z == 0) || (dy && y == 0) || (dx && x == 0)) continue;
+    int32_t q;
+    ok &= quantize_at(src, i - dz * o.L[1] * o.L[2] - dy * o.L[2] - dx, two_eps, q);
+    acc += ((dz + dy + dx) & 1) ? -(long long)q : (long long)q;
+  }
+  if (!ok || acc <= -(1ll << 31) || acc >= (1ll << 31)) {
+    p = 0;
+    return false;
+  }
+  p = (int32_t)acc;
+  return true;
+}
 
 // Integer block mean of HSZx: the integer nearest to a / d (d > 0), ties
 // toward zero (Section V-D bounds the rounding by 1/2; the worked example of
@@ -187,7 +218,19 @@ __global__ void __launch_bounds__(kThreads) k_blocks(Src src, OutStream o, CompW
     int32_t prev = 0, q;
     uint32_t maxmag = 0, qm = 0;
     bool ok = true;
-    if (o.pred == HC_PRED_MEAN) {
+    if (o.pred >= HC_PRED_LORENZO) {
+      // global predictors: no block metadata, the widest residual
+      o.heads[b] = 0;
+      for (int64_t k = 0; k < Sb; ++k) {
+        ok &= quantize_at(src, first + k, two_eps, q);
+        const uint32_t aq = (uint32_t)(q < 0 ? -q : q);
+        qm = aq > qm ? aq : qm;
+        int32_t p;
+        ok &= global_residual(src, o, first + k, two_eps, p);
+        const uint32_t m = (uint32_t)(p < 0 ? -(long long)p : (long long)p);
+        maxmag = m > maxmag ? m : maxmag;
+      }
+    } else if (o.pred == HC_PRED_MEAN) {
       // HSZx: M_b from the block's code sum, then the widest |q - M_b|
       long long sum = 0;
       for (int64_t k = 0; k < Sb; ++k) {
@@ -308,20 +351,25 @@ __global__ void __launch_bounds__(kThreads) k_pack(Src src, OutStream o, CompWs*
     uint32_t nbits = 0;
     int32_t prev = 0, q;
     const bool mean_pred = o.pred == HC_PRED_MEAN;
+    const bool global_pred = o.pred >= HC_PRED_LORENZO;
     const int32_t mb = mean_pred ? o.heads[b] : 0;
     for (int64_t k = 0; k < o.S; ++k) {
       int32_t p = 0;
       if (k < Sb) {
-        quantize_at(src, first + k, two_eps, q);
-        p = mean_pred ? q - mb : ((k == 0) ? 0 : q - prev);
-        prev = q;
+        if (global_pred) {
+          global_residual(src, o, first + k, two_eps, p);
+        } else {
+          quantize_at(src, first + k, two_eps, q);
+          p = mean_pred ? q - mb : ((k == 0) ? 0 : q - prev);
+          prev = q;
+        }
       }
       if (p < 0) sign |= 1u << (k & 31);
       if ((k & 31) == 31 || k == o.S - 1) {
         out[k >> 5] = sign;
         sign = 0;
       }
-      const uint32_t m = (uint32_t)(p < 0 ? -p : p);
+      const uint32_t m = (uint32_t)(p < 0 ? -(long long)p : (long long)p);
       acc |= (unsigned long long)m << nbits;
       nbits += w;
       if (nbits >= 32) {
@@ -390,7 +438,7 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   if (!aligned16(d_stream) || !aligned16(d_ws) || !aligned16(d_x)) return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
   if (dtype != HC_F32 && dtype != HC_F64) return fail(HC_ERR_INVALID_ARG, "dtype must be HC_F32 or HC_F64");
   if (eb_mode != HC_EB_ABS && eb_mode != HC_EB_REL) return fail(HC_ERR_INVALID_ARG, "eb_mode");
-  if (pred != HC_PRED_DELTA && pred != HC_PRED_MEAN) return fail(HC_ERR_INVALID_ARG, "predictor");
+  if (pred < HC_PRED_DELTA || pred > HC_PRED_GLOBAL_DELTA) return fail(HC_ERR_INVALID_ARG, "predictor");
   if (!(eb > 0.0) || !std::isfinite(eb)) return fail(HC_ERR_INVALID_ARG, "eb must be positive and finite");
   if (cap < L.bound) return fail(HC_ERR_NOMEM, "stream buffer smaller than hc_compress_bound");
   if (ws_bytes < compress_ws_bytes(L)) return fail(HC_ERR_NOMEM, "workspace smaller than hc_compress_workspace_bytes");
@@ -410,6 +458,7 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   o.G = L.G;
   o.nseg = (S + 31) / 32;
   o.pred = pred;
+  for (int d = 0; d < 3; ++d) o.L[d] = pred == HC_PRED_GLOBAL_DELTA ? (d == 2 ? L.N : 1) : L.dims[d];
 
   const int sms = device_sms();
   k_ws_init<<<(unsigned)std::min<int64_t>(ceil_div(L.nchunks, kThreads) + 1, 4096), kThreads, 0, st>>>(ws, L.nchunks);
@@ -463,7 +512,8 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
-  if (h.status == HC_ERR_RANGE) return fail(HC_ERR_RANGE, "a code |q| >= 2^30 or a non-finite value");
+  if (h.status == HC_ERR_RANGE)
+    return fail(HC_ERR_RANGE, "a code |q| >= 2^30, a residual |p| >= 2^31 or a non-finite value");
   if (h.status) return fail(h.status, "compression failed on the device");
   const int64_t total = ((L.off_payload + 4 * (int64_t)h.total_words + 16) + 15) & ~(int64_t)15;
   *out_bytes = (size_t)total;

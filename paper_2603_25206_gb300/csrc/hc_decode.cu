@@ -229,8 +229,17 @@ static int launch_decode_s(const hc_header* h, const void* d_stream, void* d_out
   return launch_decode_sp<KIND, OutT, HC_PRED_DELTA>(h, d_stream, d_out, err, st);
 }
 
+// Every slot of a block-mean or global-predictor stream holds a residual, so
+// the block-mean decoder at stage P (which adds no base) writes D_p.
+int decode_residuals_impl(const hc_header* h, const void* d_stream, void* d_out, void* d_ws, cudaStream_t st) {
+  if (h->pred == HC_PRED_DELTA) return fail(HC_ERR_INVALID_ARG, "delta streams keep the head in the first slot");
+  int* err = &reinterpret_cast<OpWs*>(d_ws)->status;
+  return launch_decode_sp<HC_STAGE_P, int32_t, HC_PRED_MEAN>(h, d_stream, d_out, err, st);
+}
+
 int decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,
                 cudaStream_t st) {
+  if (h->pred >= HC_PRED_LORENZO) return fail(HC_ERR_INVALID_ARG, "global-predictor stream on the block decoder");
   int* err = &reinterpret_cast<OpWs*>(d_ws)->status;
   switch (kind) {
     case HC_STAGE_M: {

@@ -68,6 +68,19 @@ inline Partial* ws_partials(void* d_ws) {
 // Per-file entry points (inputs already validated by the ABI layer).
 int decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,
                 cudaStream_t st);
+// The residuals D_p of every slot (block-mean and global-predictor streams),
+// int32[N] into d_out (hc_decode.cu).
+int decode_residuals_impl(const hc_header* h, const void* d_stream, void* d_out, void* d_ws, cudaStream_t st);
+
+// Global-predictor streams (hc_global.cu): workspace they need (any call),
+// decompression, statistics and stencils at a level.
+size_t global_workspace_bytes(const hc_header* h);
+int global_decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,
+                       size_t ws_bytes, cudaStream_t st);
+int global_stats_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, void* d_ws,
+                      size_t ws_bytes, cudaStream_t st);
+int global_stencil_impl(const hc_header* h, const void* d_stream, int level, int op, int axis3, void* d_out,
+                        int out_dtype, void* d_ws, size_t ws_bytes, cudaStream_t st);
 
 enum ReduceWhat { RED_MEAN = 0, RED_VAR = 1 };
 int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out,

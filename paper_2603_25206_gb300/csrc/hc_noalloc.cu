@@ -60,6 +60,8 @@ extern "C" HC_API int hc_op_variance_noalloc(const hc_stage* in, double eps, int
     return fail(HC_ERR_INVALID_ARG, "fused level must be HC_STAGE_P or HC_STAGE_Q");
   if (in->hdr && in->hdr->pred == HC_PRED_MEAN && in->level == HC_STAGE_P)
     return fail(HC_ERR_UNSUPPORTED, "the stage-2 block-mean deviation needs a workspace: use hc_op_variance");
+  if (in->hdr && in->hdr->pred >= HC_PRED_LORENZO)
+    return fail(HC_ERR_UNSUPPORTED, "a global-predictor stream rebuilds D_q in a workspace: use hc_op_variance");
   if (!aligned16(in->d_data)) return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
   const hc_header* h = in->hdr;
   Layout L;

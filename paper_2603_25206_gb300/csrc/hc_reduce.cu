@@ -595,6 +595,7 @@ int mean_m_array_impl(const int32_t* means, int64_t nb, int S, int64_t n, double
 
 int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, void* d_ws,
                        cudaStream_t st) {
+  if (h->pred >= HC_PRED_LORENZO) return fail(HC_ERR_INVALID_ARG, "global-predictor stream on the block reducer");
   const bool small = h->S <= 32;
   const bool hszx = h->pred == HC_PRED_MEAN;
   const int32_t* means = reinterpret_cast<const int32_t*>(reinterpret_cast<const uint8_t*>(d_stream) + h->off_heads);
@@ -744,6 +745,7 @@ static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scala
 
 int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
                                  unsigned* ticket, int max_parts, cudaStream_t st) {
+  if (h->pred >= HC_PRED_LORENZO) return fail(HC_ERR_INVALID_ARG, "global-predictor stream on the block reducer");
   const bool small = h->S <= 32;
   switch (acc_class(h->qmax)) {
     case 0:

@@ -291,6 +291,7 @@ static int launch_stream_o(const hc_header* h, const void* d_stream, const Geo& 
 
 int stencil_stream_impl(const hc_header* h, const void* d_stream, int op, int axis3, void* d_out, int out_dtype,
                         void* d_ws, cudaStream_t st) {
+  if (h->pred >= HC_PRED_LORENZO) return fail(HC_ERR_INVALID_ARG, "global-predictor stream on the block stencil");
   int* err = &reinterpret_cast<OpWs*>(d_ws)->status;
   // a 2-D field marches along its rows: (1, n1, n2) is walked as (n1, 1, n2)
   int64_t d3[3];

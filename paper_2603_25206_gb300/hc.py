@@ -43,10 +43,13 @@ ABI_FUNCTIONS = (
     "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc", "hc_autotune",
     "hc_batch_plan_bytes", "hc_batch_workspace_bytes", "hc_batch_plan", "hc_batch_run", "hc_batch_graph_create",
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
-    "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl",
+    "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for",
 )
-HC_PRED_DELTA, HC_PRED_MEAN = 0, 1
-PREDICTORS = {"delta": HC_PRED_DELTA, "mean": HC_PRED_MEAN}
+HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA = 0, 1, 2, 3
+# "delta": HSZp with block heads; "mean": HSZx; "lorenzo": HSZp-nd (Lorenzo over
+# the field's axes); "global": HSZp (delta across blocks, flattened field)
+PREDICTORS = {"delta": HC_PRED_DELTA, "mean": HC_PRED_MEAN, "lorenzo": HC_PRED_LORENZO,
+              "global": HC_PRED_GLOBAL_DELTA}
 HC_BATCH_MEAN, HC_BATCH_VARIANCE, HC_BATCH_DERIVATIVE, HC_BATCH_GRADMAG, HC_BATCH_LAPLACIAN = 1, 2, 4, 8, 16
 BATCH_OPS = {"mean": HC_BATCH_MEAN, "variance": HC_BATCH_VARIANCE, "derivative": HC_BATCH_DERIVATIVE,
              "gradmag": HC_BATCH_GRADMAG, "laplacian": HC_BATCH_LAPLACIAN}
@@ -124,6 +127,7 @@ def lib():
             "hc_compress_bound": ([i64, i32], sz),
             "hc_compress_workspace_bytes": ([i64, i32], sz),
             "hc_workspace_bytes": ([], sz),
+            "hc_workspace_bytes_for": ([P(HcHeader)], sz),
             "hc_stage_bytes": ([P(HcHeader), i32], sz),
             "hc_compress": ([vp, i32, i32, P(ctypes.c_int64), dbl, i32, i32, vp, sz, vp, sz, P(sz), P(HcHeader), vp],
                             i32),
@@ -192,17 +196,28 @@ def _dims(shape):
 _ws_cache: dict = {}
 
 
-def workspace(device=None, stream=None):
-    """Zero-initialised operation workspace, one per (device, stream)."""
+def workspace(device=None, stream=None, nbytes: int = 0):
+    """Zero-initialised operation workspace, one per (device, stream), of at
+    least hc_workspace_bytes() and `nbytes` bytes (grown on demand)."""
     torch = _torch()
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     key = (dev.index, s.cuda_stream)
     ws = _ws_cache.get(key)
-    if ws is None:
-        ws = torch.zeros(int(lib().hc_workspace_bytes()), dtype=torch.uint8, device=dev)
+    need = max(int(lib().hc_workspace_bytes()), int(nbytes))
+    if ws is None or ws.numel() < need:
+        if ws is not None:
+            s.synchronize()  # the old buffer may still be in use by queued work
+        ws = torch.zeros(need, dtype=torch.uint8, device=dev)
         _ws_cache[key] = ws
     return ws
+
+
+def _workspace_for(inp, dev, stream):
+    """The workspace a call on `inp` needs (global-predictor streams need scratch)."""
+    if isinstance(inp, Compressed):
+        return workspace(dev, stream, int(lib().hc_workspace_bytes_for(ctypes.byref(inp.header))))
+    return workspace(dev, stream)
 
 
 @dataclass
@@ -259,7 +274,8 @@ class StageArray:
 
 def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None, predictor: str = "delta") -> Compressed:
     """C (Algorithm 1) of a float32/float64 CUDA tensor.  predictor "delta"
-    (HSZp with block heads) or "mean" (HSZx: block means)."""
+    (HSZp with block heads), "mean" (HSZx: block means), "lorenzo" (HSZp-nd)
+    or "global" (HSZp, delta across blocks)."""
     torch = _torch()
     if not x.is_cuda:
         raise ValueError("compress expects a CUDA tensor")
@@ -321,7 +337,7 @@ def decompress(c: Compressed, stage: str = "f", out=None, out_dtype=None, stream
     if out is None:
         out = torch.empty(shape, dtype=tdt, device=c.stream.device)
     odt = HC_F64 if out.dtype == torch.float64 else HC_F32
-    ws = workspace(c.stream.device, stream)
+    ws = _workspace_for(c, c.stream.device, stream)
     _check(lib().hc_decompress_to_stage(ctypes.byref(c.header), ctypes.c_void_p(c.stream.data_ptr()), kind,
                                         ctypes.c_void_p(out.data_ptr()), odt, ctypes.c_void_p(ws.data_ptr()),
                                         ws.numel(), _stream_ptr(stream)))
@@ -353,7 +369,7 @@ def _stat(fn_name, inp, level, out, stream):
     st, eps, shape, dev = _input(inp, level)
     if out is None:
         out = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=dev)
-    ws = workspace(dev, stream)
+    ws = _workspace_for(inp, dev, stream)
     _check(getattr(lib(), fn_name)(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return out
@@ -397,7 +413,7 @@ def _field_out(shape, out_dtype, dev, out):
 def derivative(inp, axis: int, out_dtype: str = "float32", out=None, level: str = "q", stream=None):
     st, eps, shape, dev = _input(inp, level)
     out = _field_out(shape, out_dtype, dev, out)
-    ws = workspace(dev, stream)
+    ws = _workspace_for(inp, dev, stream)
     _check(lib().hc_op_derivative(ctypes.byref(st), eps, len(shape), _dims(shape), axis,
                                   ctypes.c_void_p(out.data_ptr()), _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()),
                                   ws.numel(), _stream_ptr(stream)))
@@ -407,7 +423,7 @@ def derivative(inp, axis: int, out_dtype: str = "float32", out=None, level: str 
 def gradmag(inp, out_dtype: str = "float32", out=None, level: str = "q", stream=None):
     st, eps, shape, dev = _input(inp, level)
     out = _field_out(shape, out_dtype, dev, out)
-    ws = workspace(dev, stream)
+    ws = _workspace_for(inp, dev, stream)
     _check(lib().hc_op_gradmag(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
                                _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return out
@@ -416,7 +432,7 @@ def gradmag(inp, out_dtype: str = "float32", out=None, level: str = "q", stream=
 def laplacian(inp, out_dtype: str = "float32", out=None, level: str = "q", stream=None):
     st, eps, shape, dev = _input(inp, level)
     out = _field_out(shape, out_dtype, dev, out)
-    ws = workspace(dev, stream)
+    ws = _workspace_for(inp, dev, stream)
     _check(lib().hc_op_laplacian(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
                                  _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return out
@@ -450,7 +466,7 @@ def multi(inp, derivative=True, gradmag=True, laplacian=True, stats=True, out_dt
             t = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=dev)
         outs["stats"] = t
         mo.d_stats = t.data_ptr()
-    ws = workspace(dev, stream)
+    ws = _workspace_for(inp, dev, stream)
     _check(lib().hc_op_multi(ctypes.byref(st), eps, len(shape), _dims(shape), ctypes.byref(mo),
                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return outs
