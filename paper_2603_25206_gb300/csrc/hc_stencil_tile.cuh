@@ -354,7 +354,9 @@ __device__ inline void stencil_tile(const DevStream& s, const Geo& g, int64_t t,
   const int64_t z0 = (int64_t)zt * g.tz, z1 = min(z0 + g.tz, g.n0);
   const int64_t ylo = max(y0 - 1, (int64_t)0), yhi = min(y1 + 1, g.n1);
   const int64_t xlo = max(x0 - 1, (int64_t)0), xhi = min(x1 + 1, g.n2);
-  const bool whole = (g.ranges == 1);
+  // whole rows exactly when a tile spans the row (a slab of one row split
+  // along x also has one range per slot, but each range is the x window)
+  const bool whole = (g.tx == g.n2);
 
   // prime the ring with planes z0 - 1 and z0, then march: load z + 1, compute z
   if (z0 > 0)

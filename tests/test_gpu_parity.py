@@ -45,6 +45,10 @@ def _cases():
     yield "grf_ragged_3d", synth.grf_field((13, 17, 19), 11), 1e-3, True, 32
     yield "grf_2d_S16", synth.grf_field((40, 33), 12), 1e-2, True, 16
     yield "walk_1d_S7", np.cumsum(r.standard_normal(1000)).astype(np.float32), 1e-2, True, 7
+    # rows too long for a whole-row tile of the general kernel, one row per slab
+    # (a 1-D field; a 2-D field walked as (n1, 1, n2)): split along x
+    yield "walk_1d_long_S16", np.cumsum(r.standard_normal(60001)).astype(np.float32), 1e-3, True, 16
+    yield "rows_2d_long_S64", synth.grf_field((3, 70000), 28), 1e-3, True, 64
     yield "grf_S64", synth.grf_field((5, 6, 70), 13), 1e-4, True, 64
     yield "grf_S100", synth.grf_field((9, 10, 31), 14), 1e-3, True, 100
     yield "grf_S128_f64", synth.grf_field((7, 9, 40), 15, dtype=np.float64), 1e-3, True, 128
