@@ -376,7 +376,10 @@ int stencil_array_impl(const hc_stage* in, const int64_t* dims3, double eps, int
 }  // namespace hc
 
 namespace hc {
-// The (possibly remapped) 3-D shape the fused stencil kernels walk.
+// The (possibly remapped) 3-D shape the fused stencil kernels walk: a field
+// whose first axis has length 1, (1, n1, n2), is walked as (n1, 1, n2), so
+// internal axes 0 and 1 trade places (the derivative along the length-1 axis
+// stays 0, now along internal axis 1).
 void stencil_walk_dims(const hc_header* h, int64_t d3[3], int* axis3) {
   d3[0] = h->dims[0];
   d3[1] = h->dims[1];
@@ -384,7 +387,7 @@ void stencil_walk_dims(const hc_header* h, int64_t d3[3], int* axis3) {
   if (d3[0] == 1 && d3[1] > 1) {
     d3[0] = d3[1];
     d3[1] = 1;
-    if (axis3 && *axis3 == 1) *axis3 = 0;
+    if (axis3 && *axis3 < 2) *axis3 = 1 - *axis3;
   }
 }
 }  // namespace hc

@@ -98,8 +98,9 @@ __device__ __forceinline__ typename OT<OUT>::T emit1(int a, int b, int c, const 
       const float x = __int2float_rn(a), y = __int2float_rn(b), z = __int2float_rn(c);
       return __fmul_rn(__fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z))), g.eps_f);
     } else {
+      // explicit roundings: the same value from every kernel (no contraction)
       const double x = (double)a, y = (double)b, z = (double)c;
-      return sqrt(x * x + y * y + z * z) * g.eps;
+      return __dmul_rn(__dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z))), g.eps);
     }
   }
   return 0;

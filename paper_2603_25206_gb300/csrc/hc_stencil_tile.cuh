@@ -79,8 +79,9 @@ __device__ __forceinline__ typename OutType<OUT>::T emit(long long a, long long 
       const float x = __ll2float_rn(a), y = __ll2float_rn(b), z = __ll2float_rn(c);
       return __fmul_rn(__fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z))), g.eps_f);
     } else {
-      const double x = (double)a, y = (double)b, z = (double)c;
-      return sqrt(x * x + y * y + z * z) * g.eps;
+      // explicit roundings: the same value from every kernel (no contraction)
+      const double x = __ll2double_rn(a), y = __ll2double_rn(b), z = __ll2double_rn(c);
+      return __dmul_rn(__dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z))), g.eps);
     }
   }
   return 0;

@@ -31,6 +31,7 @@ CASES = [
     ((12, 16, 64), 64, "float32"),
     ((4096,), 32, "float32"),
     ((64, 64, 64), 16, "float64"),
+    ((1, 24, 40), 32, "float32"),  # first axis of length 1: walked as (24, 1, 40)
 ]
 
 
@@ -54,8 +55,11 @@ def test_multi_equals_one_operation_calls(env, orc, shape, S, dt):
     q = orc.decode(ref, "q")
     s1, s2 = orc.sums_q(q)
     assert (m["s1"], m["s2"], m["status"]) == (s1, s2, 0)
-    val = orc.stencil_q(q, orc.KIND_LAPLACIAN, eps)
     tol = 1e-6 if dt == "float32" else 1e-12
+    for a in range(len(shape)):
+        val = orc.stencil_q(q, orc.KIND_DERIV, eps, a)
+        assert np.all(np.abs(r["derivative"][a].cpu().numpy() - val) <= tol * np.maximum(np.abs(val), eps)), a
+    val = orc.stencil_q(q, orc.KIND_LAPLACIAN, eps)
     assert np.all(np.abs(r["laplacian"].cpu().numpy() - val) <= tol * np.maximum(np.abs(val), 2 * eps))
     assert hc.workspace_status() == 0
 

@@ -58,6 +58,9 @@ def _cases():
     yield "single", np.array([0.25], np.float32), 1e-3, False, 32
     yield "constant", np.full((8, 9, 10), 3.5, np.float32), 1e-3, True, 32
     yield "two_point_axis", synth.grf_field((2, 3, 40), 19), 1e-3, True, 32
+    # a 3-D field whose first axis has length 1 (walked as (n1, 1, n2))
+    yield "leading_len1_S32", synth.grf_field((1, 12, 40), 29), 1e-3, True, 32
+    yield "leading_len1_S16", synth.grf_field((1, 9, 30), 30), 1e-3, True, 16
     # shapes the pipelined stencil kernel takes (S = 32, rows of a multiple of 8)
     yield "pipe_ragged_3d", synth.grf_field((7, 13, 40), 24), 1e-3, True, 32
     yield "pipe_2d", synth.grf_field((33, 24), 25), 1e-3, True, 32
