@@ -173,7 +173,7 @@ def test_global_refusals(env, orc):
     L = hc.lib()
     need = int(L.hc_workspace_bytes_for(ctypes.byref(cl.header)))
     base = int(L.hc_workspace_bytes())
-    assert need > base + 12 * x.size
+    assert need >= base + 12 * x.size
     ws = torch.zeros(base, dtype=torch.uint8, device=dev)
     out = torch.empty(x.shape, dtype=torch.int32, device=dev)
     rc = L.hc_decompress_to_stage(ctypes.byref(cl.header), ctypes.c_void_p(cl.stream.data_ptr()), hc.HC_STAGE_Q,
