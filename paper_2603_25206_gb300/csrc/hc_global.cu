@@ -23,6 +23,7 @@
 // terms is exact modulo 2^32 whatever the intermediate sums are.
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "hc_finish.cuh"
 #include "hc_internal.cuh"
@@ -163,10 +164,14 @@ GlobalWs global_ws(const hc_header* h, void* d_ws) {
 
 // ------------------------------------------------------- stage-2 mean
 // Fused decode + weighted sum: tiles of two chunks, the next tile copied with
-// cp.async while this one is decoded; one thread per 32-code segment walks
-// its positions (z, y, x) in the prediction shape and adds
-// p (L0 - z)(L1 - y)(L2 - x) modulo 2^64 (the total, sum q, fits 63 bits).
-template <bool SMALL>
+// cp.async while this one is decoded; one thread per 32-code segment adds
+// p (L0 - z)(L1 - y)(L2 - x) over its positions (z, y, x) in the prediction
+// shape, modulo 2^64 (the total, sum q, fits 63 bits).  A segment inside one
+// row needs no per-code product: with P_j the running sums of its codes,
+// sum_k p_k (L2 - x0 - k) = (L2 - x0 - cnt) P_last + sum_j P_j, two additions
+// per code (32-bit when the widest block is at most 20 bits: |P| <= 2^25,
+// |sum P| <= 2^30).  A segment that crosses a row end walks its positions.
+template <bool SMALL, bool NARROW>
 __global__ void __launch_bounds__(kThreads) k_global_mean(DevStream s, int64_t L0, int64_t L1, int64_t L2,
                                                            int64_t ntiles, int stage_words, Partial* parts,
                                                            unsigned* ticket, hc_scalar* out, double two_eps) {
@@ -227,6 +232,17 @@ __global__ void __launch_bounds__(kThreads) k_global_mean(DevStream s, int64_t L
       int64_t y = r % L1, z = r / L1;
       unsigned long long wzy = (unsigned long long)(L0 - z) * (unsigned long long)(L1 - y);
       const uint32_t* blk = tv.words + tv.off[bl];
+      if (L2 - x >= cnt) {
+        using Acc = typename std::conditional<NARROW, int, long long>::type;
+        Acc P = 0, R = 0;
+        unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int, int32_t p) {
+          P += p;
+          R += P;
+        });
+        acc += wzy * ((unsigned long long)(L2 - x - cnt) * (unsigned long long)(long long)P +
+                      (unsigned long long)(long long)R);
+        continue;
+      }
       unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int, int32_t p) {
         acc += wzy * (unsigned long long)(L2 - x) * (unsigned long long)(long long)p;
         if (++x == L2) {
@@ -417,9 +433,11 @@ int global_stats_impl(const hc_header* h, const void* d_stream, int level, int w
     global_dims(h, L);
     const int stage = stage_words_for(kTileChunks * h->G, h->S, (int)h->wmax);
     const int smem = 4 * pipe_tile_smem(kTileChunks * h->G, stage, 0).total;
-    const bool small = h->S <= 32;
-    const void* kern = small ? reinterpret_cast<const void*>(k_global_mean<true>)
-                             : reinterpret_cast<const void*>(k_global_mean<false>);
+    const bool small = h->S <= 32, narrow = h->wmax <= 20;
+    const void* kern = small ? (narrow ? reinterpret_cast<const void*>(k_global_mean<true, true>)
+                                       : reinterpret_cast<const void*>(k_global_mean<true, false>))
+                             : (narrow ? reinterpret_cast<const void*>(k_global_mean<false, true>)
+                                       : reinterpret_cast<const void*>(k_global_mean<false, false>));
     int rc = ensure_smem(kern, smem);
     if (rc) return rc;
     int per_sm = 0;
@@ -428,12 +446,18 @@ int global_stats_impl(const hc_header* h, const void* d_stream, int level, int w
     const int64_t ntiles = ceil_div(h->nchunks, kTileChunks);
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm), kMaxGrid));
-    if (small)
-      k_global_mean<true><<<grid, kThreads, smem, st>>>(s, L[0], L[1], L[2], ntiles, stage, ws_partials(d_ws),
-                                                        &ws->ticket, d_out, 2.0 * h->eps);
+#define HC_GMEAN(SM, NA)                                                                                 \
+  k_global_mean<SM, NA><<<grid, kThreads, smem, st>>>(s, L[0], L[1], L[2], ntiles, stage, ws_partials(d_ws), \
+                                                      &ws->ticket, d_out, 2.0 * h->eps)
+    if (small && narrow)
+      HC_GMEAN(true, true);
+    else if (small)
+      HC_GMEAN(true, false);
+    else if (narrow)
+      HC_GMEAN(false, true);
     else
-      k_global_mean<false><<<grid, kThreads, smem, st>>>(s, L[0], L[1], L[2], ntiles, stage, ws_partials(d_ws),
-                                                         &ws->ticket, d_out, 2.0 * h->eps);
+      HC_GMEAN(false, false);
+#undef HC_GMEAN
     return check_launch_cfg("stage-2 mean (global predictor)", kern, grid, smem);
   }
   // Algorithm 4 (and level Q): q rebuilt by prefix sums, then exact s1, s2
