@@ -25,8 +25,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 KIND_DERIV, KIND_GRADMAG, KIND_LAPLACIAN = 0, 1, 2
 # predictors: delta inside the block (HSZp with block heads), block mean
 # (HSZx), Lorenzo over the field's axes (HSZp-nd), delta across blocks over
-# the flattened field (HSZp)
-PRED_DELTA, PRED_MEAN, PRED_LORENZO, PRED_GLOBAL = 0, 1, 2, 3
+# the flattened field (HSZp), block mean over multidimensional boxes (HSZx-nd)
+PRED_DELTA, PRED_MEAN, PRED_LORENZO, PRED_GLOBAL, PRED_MEAN_ND = 0, 1, 2, 3, 4
 
 
 class OracleError(RuntimeError):
@@ -82,6 +82,15 @@ def lib():
         L.orc_stencil_f.argtypes = [vp, i32, vp, i32, i32, vp]
         L.orc_stencil_at.argtypes = [vp, vp, i32, i32, dbl, vp, i64, vp, vp]
         L.orc_lorenzo_mean_p.argtypes = [vp, vp, P(i64)]
+        L.orc_compress_bound_nd.argtypes = [i32, vp, vp]
+        L.orc_compress_bound_nd.restype = i64
+        L.orc_compress_codes_nd.argtypes = [vp, i32, i32, vp, vp, dbl, dbl, i32, vp, i64, P(i64)]
+        L.orc_compress_nd.argtypes = [vp, i32, i32, vp, vp, dbl, i32, vp, i64, P(i64), P(dbl)]
+        L.orc_xnd_mean_m.argtypes = [vp, vp, vp, P(i64)]
+        L.orc_xnd_mean_p.argtypes = [vp, vp, vp, vp, P(i64)]
+        L.orc_xnd_std_p.argtypes = [vp, vp, vp, vp, dbl, P(i64), P(ctypes.c_uint64), P(ctypes.c_uint64), P(dbl)]
+        L.orc_xnd_deriv_p.argtypes = [vp, vp, vp, vp, i32, vp]
+        L.orc_xnd_lap_p.argtypes = [vp, vp, vp, vp, vp]
         L.orc_lorenzo_var_p.argtypes = [vp, vp, P(i64), P(ctypes.c_uint64), P(ctypes.c_uint64)]
         L.orc_lorenzo_deriv_p.argtypes = [vp, vp, i32, vp]
         L.orc_lorenzo_lap_p.argtypes = [vp, vp, vp]
@@ -91,7 +100,8 @@ def lib():
                   L.orc_deriv_q, L.orc_lap_q, L.orc_stencil_q, L.orc_stencil_f, L.orc_stencil_at,
                   L.orc_compress_pred, L.orc_compress_codes_pred, L.orc_mean_m_sum, L.orc_mean_p_sum_x,
                   L.orc_std_p_x, L.orc_divergence_q, L.orc_curl2_q, L.orc_lorenzo_mean_p, L.orc_lorenzo_var_p,
-                  L.orc_lorenzo_deriv_p, L.orc_lorenzo_lap_p):
+                  L.orc_lorenzo_deriv_p, L.orc_lorenzo_lap_p, L.orc_compress_codes_nd, L.orc_compress_nd,
+                  L.orc_xnd_mean_m, L.orc_xnd_mean_p, L.orc_xnd_std_p, L.orc_xnd_deriv_p, L.orc_xnd_lap_p):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -171,17 +181,18 @@ def compress_codes(q: np.ndarray, eps: float, S: int = 32, dtype=np.float32, eb=
 
 
 HEADER_KEYS = ("dtype", "ndim", "n0", "n1", "n2", "S", "G", "eb_mode", "qmax", "N", "nb", "nchunks",
-               "payload_words", "total_bytes", "wmax", "off_payload", "pred")
+               "payload_words", "total_bytes", "wmax", "off_payload", "pred", "b0", "b1", "b2")
 
 
 def read_header(stream: np.ndarray) -> dict:
     s = np.ascontiguousarray(stream, dtype=np.uint8)
-    ints = np.zeros(17, np.int64)
+    ints = np.zeros(20, np.int64)
     dbls = np.zeros(2, np.float64)
     _check(lib().orc_read_header(_ptr(s), s.size, _ptr(ints), _ptr(dbls)), "read_header")
     h = {k: int(v) for k, v in zip(HEADER_KEYS, ints)}
     h["eps"], h["eb"] = float(dbls[0]), float(dbls[1])
     h["shape"] = (h["n0"], h["n1"], h["n2"])[3 - h["ndim"]:]
+    h["block"] = (h["b0"], h["b1"], h["b2"])[3 - h["ndim"]:]
     return h
 
 
@@ -406,4 +417,91 @@ def lorenzo_lap_p(dp: np.ndarray) -> np.ndarray:
     d = dims3(dp.shape)
     out = np.empty(dp.shape, np.int64)
     _check(lib().orc_lorenzo_lap_p(_ptr(dp), _ptr(d), _ptr(out)), "lorenzo_lap_p")
+    return out
+
+
+# ------------------------------------------------------ HSZx-nd (boxes of codes)
+def compress_nd(x: np.ndarray, block, eb: float, rel: bool = True):
+    """Algorithm 1 with block means over boxes of `block` codes (HSZx-nd)."""
+    x = np.ascontiguousarray(x)
+    d = np.array(x.shape, np.int64)
+    b = np.array(block, np.int64)
+    cap = int(lib().orc_compress_bound_nd(x.ndim, _ptr(d), _ptr(b)))
+    if cap < 0:
+        raise OracleError(1, "compress_bound_nd")
+    out = np.zeros(cap, np.uint8)
+    nbytes, eps = ctypes.c_int64(), ctypes.c_double()
+    _check(lib().orc_compress_nd(_ptr(x), _dtype_code(x), x.ndim, _ptr(d), _ptr(b), eb, int(rel), _ptr(out), cap,
+                                 ctypes.byref(nbytes), ctypes.byref(eps)), "compress_nd")
+    return out[: nbytes.value].copy(), eps.value
+
+
+def compress_codes_nd(q: np.ndarray, block, eps: float, dtype=np.float32, eb=None, rel=False):
+    """Encode given codes with block means over boxes of `block` codes."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    d = np.array(q.shape, np.int64)
+    b = np.array(block, np.int64)
+    cap = int(lib().orc_compress_bound_nd(q.ndim, _ptr(d), _ptr(b)))
+    if cap < 0:
+        raise OracleError(1, "compress_bound_nd")
+    out = np.zeros(cap, np.uint8)
+    nbytes = ctypes.c_int64()
+    code = 0 if np.dtype(dtype) == np.float32 else 1
+    _check(lib().orc_compress_codes_nd(_ptr(q), code, q.ndim, _ptr(d), _ptr(b), eps, eps if eb is None else eb,
+                                       int(rel), _ptr(out), cap, ctypes.byref(nbytes)), "compress_codes_nd")
+    return out[: nbytes.value].copy()
+
+
+def _bd3(shape, block):
+    return dims3(shape), np.array((1,) * (3 - len(block)) + tuple(int(v) for v in block), np.int64)
+
+
+def xnd_mean_m(M: np.ndarray, shape, block) -> int:
+    """Stage-1 sum of the box means times the true box sizes (Eq. mean_m)."""
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    d, b = _bd3(shape, block)
+    t = ctypes.c_int64()
+    _check(lib().orc_xnd_mean_m(_ptr(M), _ptr(d), _ptr(b), ctypes.byref(t)), "xnd_mean_m")
+    return t.value
+
+
+def xnd_mean_p(dp: np.ndarray, M: np.ndarray, block) -> int:
+    """Stage-2 sum q of HSZx-nd: sum p + M_b S_b."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    d, b = _bd3(dp.shape, block)
+    s1 = ctypes.c_int64()
+    _check(lib().orc_xnd_mean_p(_ptr(dp), _ptr(M), _ptr(d), _ptr(b), ctypes.byref(s1)), "xnd_mean_p")
+    return s1.value
+
+
+def xnd_std_p(dp: np.ndarray, M: np.ndarray, block, eps: float):
+    """Stage-2 HSZx-nd standard deviation about mu~: (mu~, exact sum of squares, sigma)."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    d, b = _bd3(dp.shape, block)
+    mt, lo, hi, sg = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().orc_xnd_std_p(_ptr(dp), _ptr(M), _ptr(d), _ptr(b), eps, ctypes.byref(mt), ctypes.byref(lo),
+                               ctypes.byref(hi), ctypes.byref(sg)), "xnd_std_p")
+    return mt.value, (hi.value << 64) | lo.value, sg.value
+
+
+def xnd_deriv_p(dp: np.ndarray, M: np.ndarray, block, axis: int) -> np.ndarray:
+    """Stage-2 HSZx-nd derivative numerators along a user axis."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    d, b = _bd3(dp.shape, block)
+    out = np.empty(dp.shape, np.int64)
+    _check(lib().orc_xnd_deriv_p(_ptr(dp), _ptr(M), _ptr(d), _ptr(b), axis + 3 - dp.ndim, _ptr(out)),
+           "xnd_deriv_p")
+    return out
+
+
+def xnd_lap_p(dp: np.ndarray, M: np.ndarray, block) -> np.ndarray:
+    """Stage-2 HSZx-nd Laplacian numerators (replicated edges)."""
+    dp = np.ascontiguousarray(dp, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    d, b = _bd3(dp.shape, block)
+    out = np.empty(dp.shape, np.int64)
+    _check(lib().orc_xnd_lap_p(_ptr(dp), _ptr(M), _ptr(d), _ptr(b), _ptr(out)), "xnd_lap_p")
     return out

@@ -24,8 +24,10 @@
  *   120 i64 off payload 128 i64 total bytes  136 u32 max width
  *   140 u32 predictor: 0 = delta inside the block (HSZp with SZp-style block
  *       heads), 1 = block mean (HSZx), 2 = Lorenzo over the field's axes
- *       (HSZp-nd), 3 = delta across blocks over the flattened field (HSZp);
- *       rest zero
+ *       (HSZp-nd), 3 = delta across blocks over the flattened field (HSZp),
+ *       4 = block mean over multidimensional blocks (HSZx-nd)
+ *   144 u32[3] block extents (b0, b1, b2) along (n0, n1, n2) for predictor 4,
+ *       S = b0 b1 b2 (zero for the other predictors); rest zero
  *   widths u8[nb] at 256; heads i32[nb], chunk index u64[nchunks + 1] and
  *   payload u32 words each start on the next 16-byte boundary; the stream
  *   ends 16..31 zero bytes after the payload (total rounded to 16).
@@ -131,7 +133,8 @@ typedef struct {
   int64_t N, nb, nchunks, payload_words;
   int64_t off_widths, off_heads, off_chunks, off_payload, total_bytes;
   int wmax;
-  int pred; /* 0 delta inside the block (HSZp), 1 block mean (HSZx) */
+  int pred;      /* the predictor (header byte 140) */
+  int64_t bd[3]; /* predictor 4: block extents (b0, b1, b2); zero otherwise */
 } orc_header;
 
 static int64_t chunk_blocks(int S) {
@@ -139,9 +142,17 @@ static int64_t chunk_blocks(int S) {
   return g < 1 ? 1 : g;
 }
 
-/* Section offsets follow from (N, S) alone. */
+/* blocks of a multidimensional partition: the grid ceil(n_a / b_a) */
+static int64_t grid_blocks(const int64_t *dims, const int64_t *bd) {
+  int64_t nb = 1;
+  for (int a = 0; a < 3; a++) nb *= (dims[a] + bd[a] - 1) / bd[a];
+  return nb;
+}
+
+/* Section offsets follow from (N, S) alone, or from the block grid for
+ * predictor 4. */
 static void layout(orc_header *h) {
-  h->nb = (h->N + h->S - 1) / h->S;
+  h->nb = h->bd[0] > 0 ? grid_blocks(h->dims, h->bd) : (h->N + h->S - 1) / h->S;
   h->G = (int)chunk_blocks(h->S);
   h->nchunks = (h->nb + h->G - 1) / h->G;
   h->off_widths = ORC_HEADER_BYTES;
@@ -285,6 +296,9 @@ static int64_t lorenzo_residual(const int32_t *q, const int64_t *L, int64_t i) {
   return v;
 }
 
+static void encode_block(uint8_t *out, const orc_header *h, int64_t word, const int32_t *p, int w);
+static void finish_stream(uint8_t *out, orc_header *hp, int64_t word);
+
 int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t *dims_in, double eps,
                             double eb, int eb_mode, int S, int pred, uint8_t *out, int64_t cap,
                             int64_t *out_bytes) {
@@ -383,32 +397,10 @@ int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t
     if (w > wmax) wmax = w;
     put_u8(out, h.off_widths + b, (uint32_t)w);
     if (w == 0) continue;
-    /* encode: sign words, then magnitudes at w bits each, LSB first */
-    int64_t nsw = (S + 31) / 32;
-    for (int64_t k = 0; k < S; k++) {
-      if (p[k] < 0) {
-        int64_t byte = h.off_payload + 4 * (word + k / 32) + (k % 32) / 8;
-        out[byte] |= (uint8_t)(1u << (k % 8));
-      }
-    }
-    int64_t mword = word + nsw;
-    for (int64_t k = 0; k < S; k++) {
-      uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
-      for (int j = 0; j < w; j++) {
-        if ((m >> j) & 1u) {
-          int64_t bit = k * w + j; /* position in the magnitude bit string */
-          int64_t byte = h.off_payload + 4 * (mword + bit / 32) + (bit % 32) / 8;
-          out[byte] |= (uint8_t)(1u << (bit % 8));
-        }
-      }
-    }
+    encode_block(out, &h, word, p, w);
     word += block_words(S, w);
   }
   free(p);
-  h.nchunks = (h.nb + h.G - 1) / h.G;
-  put_u64(out, h.off_chunks + 8 * h.nchunks, (uint64_t)word);
-  h.payload_words = word;
-  h.total_bytes = align16(h.off_payload + 4 * word + 16);
   h.qmax = qmax;
   h.wmax = wmax;
   h.eps = eps;
@@ -416,6 +408,49 @@ int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t
   h.eb_mode = eb_mode;
   h.dtype = dtype;
   h.ndim = ndim;
+  h.pred = pred;
+  finish_stream(out, &h, word);
+  *out_bytes = h.total_bytes;
+  return ORC_OK;
+}
+
+/* Encoder (Section IV, "Encoding"): sign words, then the magnitudes at w bits
+ * each, least-significant bit first, for the S slots p[0..S) of one block
+ * whose payload starts at word `word`. */
+static void encode_block(uint8_t *out, const orc_header *h, int64_t word, const int32_t *p, int w) {
+  int S = h->S;
+  int64_t nsw = (S + 31) / 32;
+  for (int64_t k = 0; k < S; k++) {
+    if (p[k] < 0) {
+      int64_t byte = h->off_payload + 4 * (word + k / 32) + (k % 32) / 8;
+      out[byte] |= (uint8_t)(1u << (k % 8));
+    }
+  }
+  int64_t mword = word + nsw;
+  for (int64_t k = 0; k < S; k++) {
+    uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
+    for (int j = 0; j < w; j++) {
+      if ((m >> j) & 1u) {
+        int64_t bit = k * w + j; /* position in the magnitude bit string */
+        int64_t byte = h->off_payload + 4 * (mword + bit / 32) + (bit % 32) / 8;
+        out[byte] |= (uint8_t)(1u << (bit % 8));
+      }
+    }
+  }
+}
+
+/* The chunk index end, the totals and the 256-byte header of a stream whose
+ * payload holds `word` words. */
+static void finish_stream(uint8_t *out, orc_header *hp, int64_t word) {
+  orc_header h = *hp;
+  h.nchunks = (h.nb + h.G - 1) / h.G;
+  put_u64(out, h.off_chunks + 8 * h.nchunks, (uint64_t)word);
+  h.payload_words = word;
+  h.total_bytes = align16(h.off_payload + 4 * word + 16);
+  int S = h.S;
+  int dtype = h.dtype, ndim = h.ndim, eb_mode = h.eb_mode, pred = h.pred, wmax = h.wmax;
+  double eps = h.eps, eb = h.eb;
+  int64_t qmax = h.qmax;
 
   put_u32(out, 0, ORC_MAGIC);
   put_u16(out, 4, ORC_VERSION);
@@ -441,8 +476,170 @@ int orc_compress_codes_pred(const int32_t *q, int dtype, int ndim, const int64_t
   put_u64(out, 128, (uint64_t)h.total_bytes);
   put_u32(out, 136, (uint32_t)wmax);
   put_u32(out, 140, (uint32_t)pred);
+  for (int a = 0; a < 3; a++) put_u32(out, 144 + 4 * a, (uint32_t)h.bd[a]);
+  *hp = h;
+}
+
+/* ------------------------------------------------------------------ */
+/* HSZx-nd (Section IV, "HSZx-nd"): the field is partitioned into boxes  */
+/* of b0 x b1 x b2 codes (the multidimensional partition of HSZp-nd), and */
+/* each box is decorrelated by its own integer mean, p = q - M_b.        */
+/* Readings: boxes are stored in row-major order of the box grid          */
+/* ceil(n_a / b_a), the S = b0 b1 b2 slots of a box row-major inside it; */
+/* a box cut by the end of the field has its true size S_b (the product   */
+/* of its clipped extents) for the mean and zero in the slots outside    */
+/* the field; M_b is the nearest integer to the sum over S_b, ties toward */
+/* zero, as for HSZx.                                                     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int64_t g[3];  /* box grid */
+  int64_t k[3];  /* box coordinates of the current box */
+} nd_grid;
+
+static void nd_box(const int64_t *dims, const int64_t *bd, int64_t b, nd_grid *G) {
+  for (int a = 0; a < 3; a++) G->g[a] = (dims[a] + bd[a] - 1) / bd[a];
+  G->k[2] = b % G->g[2];
+  G->k[1] = (b / G->g[2]) % G->g[1];
+  G->k[0] = b / (G->g[2] * G->g[1]);
+}
+
+/* field index of slot s of the box, or -1 for a slot outside the field */
+static int64_t nd_slot_index(const int64_t *dims, const int64_t *bd, const nd_grid *G, int64_t s) {
+  int64_t c[3];
+  c[2] = s % bd[2];
+  c[1] = (s / bd[2]) % bd[1];
+  c[0] = s / (bd[2] * bd[1]);
+  for (int a = 0; a < 3; a++) {
+    c[a] += G->k[a] * bd[a];
+    if (c[a] >= dims[a]) return -1;
+  }
+  return (c[0] * dims[1] + c[1]) * dims[2] + c[2];
+}
+
+/* true size of box b */
+static int64_t nd_box_size(const int64_t *dims, const int64_t *bd, int64_t b) {
+  nd_grid G;
+  nd_box(dims, bd, b, &G);
+  int64_t n = 1;
+  for (int a = 0; a < 3; a++) {
+    int64_t rest = dims[a] - G.k[a] * bd[a];
+    n *= rest < bd[a] ? rest : bd[a];
+  }
+  return n;
+}
+
+/* box holding field position (z, y, x) */
+static int64_t nd_box_of(const int64_t *dims, const int64_t *bd, int64_t z, int64_t y, int64_t x) {
+  int64_t g1 = (dims[1] + bd[1] - 1) / bd[1], g2 = (dims[2] + bd[2] - 1) / bd[2];
+  return ((z / bd[0]) * g1 + y / bd[1]) * g2 + x / bd[2];
+}
+
+static int nd_setup(int ndim, const int64_t *dims_in, const int64_t *block_in, orc_header *h) {
+  if (ndim < 1 || ndim > 3) return ORC_ERR_INVALID_ARG;
+  memset(h, 0, sizeof *h);
+  int64_t n = 1, S = 1;
+  for (int a = 0; a < 3; a++) {
+    h->dims[a] = 1;
+    h->bd[a] = 1;
+  }
+  for (int a = 0; a < ndim; a++) {
+    if (dims_in[a] < 1 || block_in[a] < 1) return ORC_ERR_INVALID_ARG;
+    h->dims[3 - ndim + a] = dims_in[a];
+    h->bd[3 - ndim + a] = block_in[a];
+    n *= dims_in[a];
+    S *= block_in[a];
+  }
+  if (S > ORC_MAX_S) return ORC_ERR_INVALID_ARG;
+  h->N = n;
+  h->S = (int)S;
+  layout(h);
+  return ORC_OK;
+}
+
+int64_t orc_compress_bound_nd(int ndim, const int64_t *dims, const int64_t *block) {
+  orc_header h;
+  if (nd_setup(ndim, dims, block, &h)) return -1;
+  return align16(h.off_payload + 4 * h.nb * block_words(h.S, 31) + 16);
+}
+
+int orc_compress_codes_nd(const int32_t *q, int dtype, int ndim, const int64_t *dims_in, const int64_t *block_in,
+                          double eps, double eb, int eb_mode, uint8_t *out, int64_t cap, int64_t *out_bytes) {
+  if (!(eps > 0.0) || (dtype != 0 && dtype != 1)) return ORC_ERR_INVALID_ARG;
+  orc_header h;
+  int st = nd_setup(ndim, dims_in, block_in, &h);
+  if (st) return st;
+  int64_t bound = align16(h.off_payload + 4 * h.nb * block_words(h.S, 31) + 16);
+  if (cap < bound) return ORC_ERR_INVALID_ARG;
+  memset(out, 0, (size_t)bound);
+  for (int64_t i = 0; i < h.N; i++)
+    if (!(q[i] > -ORC_QLIMIT && q[i] < ORC_QLIMIT)) return ORC_ERR_RANGE;
+  int S = h.S;
+  int32_t *p = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
+  if (!p) return ORC_ERR_INVALID_ARG;
+  int64_t word = 0, qmax = 0;
+  int wmax = 0;
+  for (int64_t b = 0; b < h.nb; b++) {
+    if (b % h.G == 0) put_u64(out, h.off_chunks + 8 * (b / h.G), (uint64_t)word);
+    nd_grid G;
+    nd_box(h.dims, h.bd, b, &G);
+    /* metadata: the box mean over its true size */
+    int64_t sum = 0, Sb = 0;
+    for (int64_t k = 0; k < S; k++) {
+      int64_t i = nd_slot_index(h.dims, h.bd, &G, k);
+      if (i < 0) continue;
+      sum += q[i];
+      Sb++;
+      int64_t a = q[i] < 0 ? -(int64_t)q[i] : q[i];
+      if (a > qmax) qmax = a;
+    }
+    int32_t M = (int32_t)nearest_ratio(sum, Sb);
+    put_u32(out, h.off_heads + 4 * b, (uint32_t)M);
+    uint32_t maxmag = 0;
+    for (int64_t k = 0; k < S; k++) {
+      int64_t i = nd_slot_index(h.dims, h.bd, &G, k);
+      p[k] = i < 0 ? 0 : q[i] - M;
+      uint32_t m = (uint32_t)(p[k] < 0 ? -(int64_t)p[k] : p[k]);
+      if (m > maxmag) maxmag = m;
+    }
+    int w = bit_length(maxmag);
+    if (w > wmax) wmax = w;
+    put_u8(out, h.off_widths + b, (uint32_t)w);
+    if (w == 0) continue;
+    encode_block(out, &h, word, p, w);
+    word += block_words(S, w);
+  }
+  free(p);
+  h.qmax = qmax;
+  h.wmax = wmax;
+  h.eps = eps;
+  h.eb = eb;
+  h.eb_mode = eb_mode;
+  h.dtype = dtype;
+  h.ndim = ndim;
+  h.pred = 4;
+  finish_stream(out, &h, word);
   *out_bytes = h.total_bytes;
   return ORC_OK;
+}
+
+int orc_compress_nd(const void *x, int dtype, int ndim, const int64_t *dims, const int64_t *block, double eb,
+                    int eb_mode, uint8_t *out, int64_t cap, int64_t *out_bytes, double *eps_out) {
+  if (ndim < 1 || ndim > 3) return ORC_ERR_INVALID_ARG;
+  int64_t n = 1;
+  for (int a = 0; a < ndim; a++) {
+    if (dims[a] < 1) return ORC_ERR_INVALID_ARG;
+    n *= dims[a];
+  }
+  double eps;
+  int st = orc_eps(x, dtype, n, eb, eb_mode, &eps);
+  if (st) return st;
+  int32_t *q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  if (!q) return ORC_ERR_INVALID_ARG;
+  st = orc_quantize(x, dtype, n, eps, q);
+  if (!st) st = orc_compress_codes_nd(q, dtype, ndim, dims, block, eps, eb, eb_mode, out, cap, out_bytes);
+  free(q);
+  if (eps_out) *eps_out = eps;
+  return st;
 }
 
 int orc_compress_codes(const int32_t *q, int dtype, int ndim, const int64_t *dims_in, double eps,
@@ -495,6 +692,16 @@ static int parse(const uint8_t *s, int64_t bytes, orc_header *h) {
   if (h->dtype > 1 || h->ndim < 1 || h->ndim > 3 || h->S < 1 || h->S > ORC_MAX_S) return ORC_ERR_CORRUPT;
   if (h->dims[0] < 1 || h->dims[1] < 1 || h->dims[2] < 1) return ORC_ERR_CORRUPT;
   if (h->dims[0] * h->dims[1] * h->dims[2] != h->N) return ORC_ERR_CORRUPT;
+  int64_t bprod = 1;
+  for (int a = 0; a < 3; a++) {
+    h->bd[a] = (int64_t)get_u32(s, 144 + 4 * a);
+    bprod *= h->bd[a];
+  }
+  if ((int)get_u32(s, 140) == 4) {
+    if (bprod != h->S) return ORC_ERR_CORRUPT;
+  } else if (bprod != 0 || h->bd[0] || h->bd[1] || h->bd[2]) {
+    return ORC_ERR_CORRUPT;
+  }
   orc_header ref = *h;
   layout(&ref);
   h->nb = ref.nb;
@@ -513,14 +720,14 @@ static int parse(const uint8_t *s, int64_t bytes, orc_header *h) {
   h->total_bytes = (int64_t)get_u64(s, 128);
   h->wmax = (int)get_u32(s, 136);
   h->pred = (int)get_u32(s, 140);
-  if (h->pred < 0 || h->pred > 3) return ORC_ERR_CORRUPT;
+  if (h->pred < 0 || h->pred > 4) return ORC_ERR_CORRUPT;
   if (h->total_bytes != align16(h->off_payload + 4 * h->payload_words + 16)) return ORC_ERR_CORRUPT;
   if (h->total_bytes > bytes) return ORC_ERR_CORRUPT;
   if (!(h->eps > 0.0)) return ORC_ERR_CORRUPT;
   return ORC_OK;
 }
 
-/* exported view of the header: 17 int64 fields + 2 doubles */
+/* exported view of the header: 20 int64 fields + 2 doubles */
 int orc_read_header(const uint8_t *s, int64_t bytes, int64_t *ints, double *dbls) {
   orc_header h;
   int st = parse(s, bytes, &h);
@@ -542,6 +749,9 @@ int orc_read_header(const uint8_t *s, int64_t bytes, int64_t *ints, double *dbls
   ints[14] = h.wmax;
   ints[15] = h.off_payload;
   ints[16] = h.pred;
+  ints[17] = h.bd[0];
+  ints[18] = h.bd[1];
+  ints[19] = h.bd[2];
   dbls[0] = h.eps;
   dbls[1] = h.eb;
   return ORC_OK;
@@ -630,7 +840,38 @@ static void put_p(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int
   dp[first] = head;
   for (int64_t k = 1; k < Sb; k++) dp[first + k] = p[k];
 }
+/* HSZx-nd: the slots of box b go back to their field positions (slots
+ * outside the field are dropped); stage 2 holds p, stage 3 M_b + p. */
+typedef struct {
+  const orc_header *h;
+  int32_t *out;
+  int add_mean;
+} nd_ctx;
+static void put_nd(void *ctx, int pred, int64_t b, int64_t first, int64_t Sb, int32_t head, const int32_t *p) {
+  (void)pred;
+  (void)first;
+  (void)Sb;
+  nd_ctx *c = (nd_ctx *)ctx;
+  nd_grid G;
+  nd_box(c->h->dims, c->h->bd, b, &G);
+  for (int64_t k = 0; k < c->h->S; k++) {
+    int64_t i = nd_slot_index(c->h->dims, c->h->bd, &G, k);
+    if (i >= 0) c->out[i] = c->add_mean ? head + p[k] : p[k];
+  }
+}
+static int decode_nd(const uint8_t *s, int64_t bytes, int32_t *out, int add_mean) {
+  orc_header h;
+  int st = parse(s, bytes, &h);
+  if (st) return st;
+  nd_ctx c = {&h, out, add_mean};
+  return walk(s, bytes, put_nd, &c, NULL);
+}
+
 int orc_decode_p(const uint8_t *s, int64_t bytes, int32_t *dp) {
+  orc_header h;
+  int st = parse(s, bytes, &h);
+  if (st) return st;
+  if (h.pred == 4) return decode_nd(s, bytes, dp, 0);
   return walk(s, bytes, put_p, dp, NULL);
 }
 
@@ -678,6 +919,7 @@ int orc_decode_q(const uint8_t *s, int64_t bytes, int32_t *dq) {
   orc_header h;
   int st = parse(s, bytes, &h);
   if (st) return st;
+  if (h.pred == 4) return decode_nd(s, bytes, dq, 1);
   if (h.pred < 2) return walk(s, bytes, put_q, dq, NULL);
   st = walk(s, bytes, put_p, dq, NULL);
   if (st) return st;
@@ -701,7 +943,7 @@ int orc_decode_m(const uint8_t *s, int64_t bytes, int32_t *heads) {
   int st = parse(s, bytes, &h);
   if (st) return st;
   /* the global predictors keep no block metadata (Table 2: stages 2-4) */
-  if (h.pred >= 2) return ORC_ERR_UNSUPPORTED;
+  if (h.pred == 2 || h.pred == 3) return ORC_ERR_UNSUPPORTED;
   return walk(s, bytes, put_m, heads, NULL);
 }
 
@@ -1043,6 +1285,122 @@ int orc_lorenzo_lap_p(const int32_t *dp, const int64_t *dims3, int64_t *Lout) {
     for (int64_t i = 0; i < n; i++) Lout[i] += t[i];
   }
   free(t);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* HSZx-nd operations (Sections V-A and V-B) on D_p in field order and   */
+/* the box means M (row-major over the box grid).  bd = (b0, b1, b2).    */
+/* ------------------------------------------------------------------ */
+
+/* Stage 1 mean (Eq. mean_m): T = sum_b M_b S_b with the true box sizes. */
+int orc_xnd_mean_m(const int32_t *M, const int64_t *dims3, const int64_t *bd, int64_t *T) {
+  int64_t nb = grid_blocks(dims3, bd), t = 0;
+  for (int64_t b = 0; b < nb; b++) t += (int64_t)M[b] * nd_box_size(dims3, bd, b);
+  *T = t;
+  return ORC_OK;
+}
+
+/* Stage 2 mean (Section V-A): sum q = sum_b (sum_{p in B_b} p + M_b S_b). */
+int orc_xnd_mean_p(const int32_t *dp, const int32_t *M, const int64_t *dims3, const int64_t *bd, int64_t *s1) {
+  int64_t t = 0;
+  orc_xnd_mean_m(M, dims3, bd, &t);
+  int64_t n = dims3[0] * dims3[1] * dims3[2];
+  for (int64_t i = 0; i < n; i++) t += dp[i];
+  *s1 = t;
+  return ORC_OK;
+}
+
+/* Stage 2 standard deviation (Section V-A): about the integer mean
+ * mu~ = round(T / N) of stage 1 (nearest, ties toward zero),
+ * sigma = sqrt(sum (p + M_b - mu~)^2 / (N - 1)) 2 eps; the exact 128-bit
+ * sum of squares is returned too. */
+int orc_xnd_std_p(const int32_t *dp, const int32_t *M, const int64_t *dims3, const int64_t *bd, double eps,
+                  int64_t *mu_tilde, uint64_t *s2_lo, uint64_t *s2_hi, double *sigma) {
+  int64_t n = dims3[0] * dims3[1] * dims3[2];
+  int64_t T;
+  orc_xnd_mean_m(M, dims3, bd, &T);
+  int64_t mu = nearest_ratio(T, n);
+  u128 acc = 0;
+  for (int64_t z = 0; z < dims3[0]; z++)
+    for (int64_t y = 0; y < dims3[1]; y++)
+      for (int64_t x = 0; x < dims3[2]; x++) {
+        int64_t i = (z * dims3[1] + y) * dims3[2] + x;
+        int64_t d = (int64_t)dp[i] + M[nd_box_of(dims3, bd, z, y, x)] - mu;
+        acc += (u128)(d * d);
+      }
+  *mu_tilde = mu;
+  *s2_lo = (uint64_t)acc;
+  *s2_hi = (uint64_t)(acc >> 64);
+  double v = n >= 2 ? (double)acc / (double)(n - 1) : NAN;
+  *sigma = sqrt(v) * 2.0 * eps;
+  return ORC_OK;
+}
+
+static int64_t xnd_p(const int32_t *dp, const int64_t *d, const int64_t *c) {
+  return dp[(c[0] * d[1] + c[1]) * d[2] + c[2]];
+}
+static int64_t xnd_m(const int32_t *M, const int64_t *d, const int64_t *bd, const int64_t *c) {
+  return M[nd_box_of(d, bd, c[0], c[1], c[2])];
+}
+
+/* Stage 2 derivative numerators of HSZx-nd (Section V-B, "Operation with
+ * D_p", HSZx-2d, written for every axis of a 3-D field): inside a box
+ * D = p[i+e] - p[i-e]; where a neighbour lies in another box the difference
+ * of the box means is added, D = p[i+e] - p[i-e] + (M_{box(i+e)} -
+ * M_{box(i-e)}).  Domain edges as at stage 3: one-sided and doubled, 0 on an
+ * axis of length 1. */
+int orc_xnd_deriv_p(const int32_t *dp, const int32_t *M, const int64_t *dims3, const int64_t *bd, int axis,
+                    int64_t *D) {
+  const int64_t *d = dims3;
+  for (int64_t z = 0; z < d[0]; z++)
+    for (int64_t y = 0; y < d[1]; y++)
+      for (int64_t x = 0; x < d[2]; x++) {
+        int64_t c[3] = {z, y, x}, lo[3] = {z, y, x}, hi[3] = {z, y, x};
+        int64_t len = d[axis], k = c[axis], e = 1;
+        if (len == 1) {
+          D[(z * d[1] + y) * d[2] + x] = 0;
+          continue;
+        }
+        if (k == 0) {
+          hi[axis] = 1;
+          e = 2;
+        } else if (k == len - 1) {
+          lo[axis] = k - 1;
+          e = 2;
+        } else {
+          lo[axis] = k - 1;
+          hi[axis] = k + 1;
+        }
+        int64_t v = xnd_p(dp, d, hi) - xnd_p(dp, d, lo);
+        if (nd_box_of(d, bd, hi[0], hi[1], hi[2]) != nd_box_of(d, bd, lo[0], lo[1], lo[2]))
+          v += xnd_m(M, d, bd, hi) - xnd_m(M, d, bd, lo); /* border: the box means' difference */
+        D[(z * d[1] + y) * d[2] + x] = v * e;
+      }
+  return ORC_OK;
+}
+
+/* Stage 2 Laplacian numerators of HSZx-nd (Section V-B, HSZx-2d: the
+ * neighbours' p minus 2 ndim p, corrected at box borders by the neighbour
+ * box's mean minus the centre box's), with replicated edges: a missing
+ * neighbour repeats the centre (its term is 0). */
+int orc_xnd_lap_p(const int32_t *dp, const int32_t *M, const int64_t *dims3, const int64_t *bd, int64_t *L) {
+  const int64_t *d = dims3;
+  for (int64_t z = 0; z < d[0]; z++)
+    for (int64_t y = 0; y < d[1]; y++)
+      for (int64_t x = 0; x < d[2]; x++) {
+        int64_t c[3] = {z, y, x};
+        int64_t pc = xnd_p(dp, d, c), mc = xnd_m(M, d, bd, c), v = 0;
+        for (int a = 0; a < 3; a++)
+          for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int64_t nb[3] = {z, y, x};
+            nb[a] += sgn;
+            if (nb[a] < 0 || nb[a] >= d[a]) continue; /* replicated edge: term 0 */
+            v += xnd_p(dp, d, nb) - pc;
+            if (nd_box_of(d, bd, nb[0], nb[1], nb[2]) != nd_box_of(d, bd, z, y, x)) v += xnd_m(M, d, bd, nb) - mc;
+          }
+        L[(z * d[1] + y) * d[2] + x] = v;
+      }
   return ORC_OK;
 }
 

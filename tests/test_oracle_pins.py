@@ -144,14 +144,19 @@ def _py_decode(stream):
     payload = s[op:op + 4 * pw].view("<u4").astype(np.uint64)
     bits = ((payload[:, None] >> np.arange(32, dtype=np.uint64)) & 1).reshape(-1)
     q = np.empty(N, np.int64)
+    qs = np.zeros((nb, S), np.int64)  # every slot of every block (predictor 4)
     for b in range(nb):
         first = b * S
         Sb = min(S, N - first)
         w = int(widths[b])
-        if w == 0:  # every p is 0: q = head (delta) or q = M_b (block mean)
+        if pred == 4:
+            if w == 0:
+                qs[b] = heads[b]
+                continue
+        elif w == 0:  # every p is 0: q = head (delta) or q = M_b (block mean)
             q[first:first + Sb] = heads[b]
             continue
-        if pred >= 2:
+        if pred in (2, 3):
             assert heads[b] == 0
         base = int(offs[b]) * 32
         k = np.arange(S)
@@ -159,6 +164,9 @@ def _py_decode(stream):
         mb = base + nsw * 32 + (k[:, None] * w + np.arange(w)[None, :])
         mag = (bits[mb] << np.arange(w, dtype=np.uint64)).sum(axis=1).astype(np.int64)
         p = np.where(sign == 1, -mag, mag)
+        if pred == 4:
+            qs[b] = heads[b] + p
+            continue
         assert np.all(p[Sb:] == 0)
         if pred >= 2:  # global predictors: the slots hold residuals, no heads
             q[first:first + Sb] = p[:Sb]
@@ -170,6 +178,18 @@ def _py_decode(stream):
     chunk_g = max(1, 4096 // S)
     chunks = s[oc:oc + 8 * (-(-nb // chunk_g) + 1)].view("<u8").astype(np.int64)
     np.testing.assert_array_equal(chunks, offs[::chunk_g].tolist() + ([offs[-1]] if nb % chunk_g else []))
+    if pred == 4:  # HSZx-nd: box slots back to field positions (outside slots dropped)
+        d = (u64(8), u64(16), u64(24))
+        bd = (u32(144), u32(148), u32(152))
+        g = [-(-d[a] // bd[a]) for a in range(3)]
+        field = np.empty(d, np.int64)
+        for b in range(nb):
+            k = (b // (g[1] * g[2]), (b // g[2]) % g[1], b % g[2])
+            box = qs[b].reshape(bd)
+            sl = tuple(slice(k[a] * bd[a], min(d[a], (k[a] + 1) * bd[a])) for a in range(3))
+            ext = tuple(sl[a].stop - sl[a].start for a in range(3))
+            field[sl] = box[: ext[0], : ext[1], : ext[2]]
+        q = field.reshape(-1)
     if pred == 3:  # HSZp: q is the running sum over the flattened field
         q = np.cumsum(q)
     elif pred == 2:  # HSZp-nd: q is the running sum along every axis
@@ -717,3 +737,119 @@ def test_lorenzo_stage2_laplacian_equals_library(orc, rng, shape):
     ref = ndimage.laplace(q.astype(np.float64), mode="nearest")
     np.testing.assert_array_equal(L, ref.astype(np.int64))
     np.testing.assert_array_equal(L, orc.lap_q(q))
+
+
+# ------------------------------------------------------- HSZx-nd (boxes of codes)
+def test_hszx_nd_worked_example(orc):
+    """Section IV's HSZx-nd example as printed: the 2x4 codes Y_q in 2x2 boxes
+    give the box means M = 5, -1 and the printed 2x4 Y_p; Section V-A's
+    stage-2 standard deviation about round(16/8) = 2 is 2.000."""
+    g = read_golden_table("worked_example.txt")
+    Yq = np.array([int(v) for v in g["Yq"]], np.int32).reshape(2, 4)
+    Yp = np.array([int(v) for v in g["Yp"]], np.int64).reshape(2, 4)
+    M = [int(v) for v in g["M"]]
+    s = orc.compress_codes_nd(Yq, (2, 2), 0.1, np.float64)
+    h = orc.read_header(s)
+    assert (h["pred"], h["block"], h["nb"], h["S"]) == (4, (2, 2), 2, 4)
+    np.testing.assert_array_equal(orc.decode(s, "m"), M)
+    np.testing.assert_array_equal(orc.decode(s, "p"), Yp)
+    np.testing.assert_array_equal(orc.decode(s, "q"), Yq)
+    dp, Mv = orc.decode(s, "p"), orc.decode(s, "m")
+    assert orc.xnd_mean_m(Mv, (2, 4), (2, 2)) == 5 * 4 + (-1) * 4
+    assert orc.xnd_mean_p(dp, Mv, (2, 2)) == int(Yq.sum()) == 18
+    mt, ss, sigma = orc.xnd_std_p(dp, Mv, (2, 2), 0.1)
+    assert (mt, ss) == (2, 700)
+    assert f"{sigma:.3f}" == g["sigma_p_hszx"][0]
+    q_py, _ = _py_decode(s)
+    np.testing.assert_array_equal(q_py.reshape(2, 4), Yq)
+
+
+ND_CASES = [((7, 10), (2, 3)), ((5, 6, 7), (2, 2, 4)), ((9,), (4,)), ((3, 8, 9), (1, 4, 8)),
+            ((4, 5, 6), (8, 8, 8)), ((13, 17, 19), (4, 4, 4)), ((1, 33, 40), (1, 8, 8)), ((50, 3), (16, 4))]
+
+
+@pytest.mark.parametrize("shape,block", ND_CASES)
+def test_hszx_nd_roundtrip_and_reader(orc, rng, shape, block):
+    """Boxes cut by the field's end: D_q is the codes, the independent reader
+    (box slots back to field positions) agrees, each box mean follows the
+    rounding rule over the true box size, each width is the bit length of
+    the box's largest |q - M_b|."""
+    q = _smooth_codes(rng, shape, scale=900)
+    s = orc.compress_codes_nd(q, block, 0.01)
+    np.testing.assert_array_equal(orc.decode(s, "q"), q)
+    q_py, widths = _py_decode(s)
+    np.testing.assert_array_equal(q_py.reshape(shape), q)
+    M = orc.decode(s, "m")
+    d = (1,) * (3 - len(shape)) + shape
+    bd = (1,) * (3 - len(block)) + block
+    q3 = q.reshape(d).astype(np.int64)
+    g = [-(-d[a] // bd[a]) for a in range(3)]
+    assert M.size == widths.size == g[0] * g[1] * g[2]
+    b = 0
+    for k0 in range(g[0]):
+        for k1 in range(g[1]):
+            for k2 in range(g[2]):
+                box = q3[k0 * bd[0]:(k0 + 1) * bd[0], k1 * bd[1]:(k1 + 1) * bd[1], k2 * bd[2]:(k2 + 1) * bd[2]]
+                assert M[b] == _nearest_tie_zero(int(box.sum()), box.size)
+                assert widths[b] == int(np.abs(box - M[b]).max()).bit_length()
+                b += 1
+    np.testing.assert_array_equal(orc.decode(s, "p").reshape(d),
+                                  q3 - np.repeat(np.repeat(np.repeat(M.reshape(g), bd[0], 0), bd[1], 1), bd[2], 2)
+                                  [: d[0], : d[1], : d[2]])
+
+
+@pytest.mark.parametrize("S", [1, 7, 32, 100])
+def test_hszx_nd_one_axis_equals_hszx(orc, rng, S):
+    """Boxes along one axis are HSZx's 1-D blocks: the same widths, means
+    and payload; only the predictor byte and the box extents differ."""
+    q = _smooth_codes(rng, (1000,), scale=700)
+    a = orc.compress_codes(q, 0.01, S, pred=1)
+    b = orc.compress_codes_nd(q, (S,), 0.01)
+    assert a.size == b.size
+    diff = np.nonzero(a != b)[0]
+    assert diff.size and diff.min() >= 140 and diff.max() < 156
+
+
+@pytest.mark.parametrize("shape,block", ND_CASES)
+def test_hszx_nd_statistics(orc, rng, shape, block):
+    """Section V-A on boxes: the stage-1 sum uses the true box sizes (brute
+    force), the stage-2 sum is sum q exactly, the stage-2 deviation is the
+    exact sum of (q - mu~)^2 (numpy), and the stage-1 mean is within eps of
+    the exact mean (Section V-D)."""
+    q = _smooth_codes(rng, shape, scale=5000)
+    eps = 0.01
+    s = orc.compress_codes_nd(q, block, eps)
+    dp, M = orc.decode(s, "p"), orc.decode(s, "m")
+    d = (1,) * (3 - len(shape)) + shape
+    bd = (1,) * (3 - len(block)) + block
+    g = [-(-d[a] // bd[a]) for a in range(3)]
+    sizes = [min(bd[0], d[0] - k0 * bd[0]) * min(bd[1], d[1] - k1 * bd[1]) * min(bd[2], d[2] - k2 * bd[2])
+             for k0 in range(g[0]) for k1 in range(g[1]) for k2 in range(g[2])]
+    T = orc.xnd_mean_m(M, shape, block)
+    assert T == sum(int(m) * n for m, n in zip(M, sizes))
+    assert orc.xnd_mean_p(dp, M, block) == int(q.astype(np.int64).sum())
+    mt, ss, sigma = orc.xnd_std_p(dp, M, block, eps)
+    assert mt == _nearest_tie_zero(T, q.size)
+    assert ss == sum((int(v) - mt) ** 2 for v in q.ravel())
+    assert abs(T / q.size - q.astype(np.int64).sum() / q.size) * 2 * eps <= eps
+
+
+@pytest.mark.parametrize("shape,block", ND_CASES)
+def test_hszx_nd_stage2_stencils_equal_library(orc, rng, shape, block):
+    """Section V-B's HSZx-2d stage-2 formulas (p differences plus the box
+    means' difference at box borders), for every axis: the derivative
+    numerators equal 2 numpy.gradient of the codes and the Laplacian
+    numerators scipy.ndimage.laplace with replicated edges."""
+    from scipy import ndimage
+
+    q = _smooth_codes(rng, shape, scale=3000)
+    s = orc.compress_codes_nd(q, block, 0.01)
+    dp, M = orc.decode(s, "p"), orc.decode(s, "m")
+    for a in range(q.ndim):
+        D = orc.xnd_deriv_p(dp, M, block, a)
+        if shape[a] == 1:
+            assert not D.any()
+            continue
+        np.testing.assert_array_equal(D, (2 * np.gradient(q.astype(np.float64), axis=a)).astype(np.int64))
+    L = orc.xnd_lap_p(dp, M, block)
+    np.testing.assert_array_equal(L, ndimage.laplace(q.astype(np.float64), mode="nearest").astype(np.int64))
