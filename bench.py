@@ -986,6 +986,93 @@ def run_lorenzo(args):
     return 0
 
 
+def run_boxes(args):
+    """HSZx-nd (block means over boxes of codes) on the paper-like workload:
+    the five fields in 4x4x4 boxes (8x8 for the 2-D field), eb 1e-3 value-range
+    relative.  Per field: the stream size beside 1-D HSZx (block 64) and the
+    block-head stream; the mean at stages 1, 2 and 3, the standard deviation
+    at stages 2 and 3, the derivative along the first axis and the Laplacian
+    at stages 2 and 3, against the plain path (decompress to float32, then the
+    operation).  Median CUDA-event time over 5 runs with an L2 flush before
+    each; GB/s counts the field's original bytes.  The roofline line is the
+    stage-3 variance kernel (k_stats_box) at its algorithmic bytes, the
+    compressed stream."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peak, peak_src = measured_peaks()
+    rows, tot = [], {}
+    var_bytes = 0
+    for shape, x in make_fields():
+        block = (4, 4, 4) if len(shape) == 3 else (8, 8)
+        xd = torch.from_numpy(x).to(dev)
+        cb = hc._trim(hc.compress(xd, EB, rel=True, predictor="mean-nd", block=block))
+        cx = hc._trim(hc.compress(xd, EB, rel=True, S=64, predictor="mean"))
+        cd = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK))
+        del xd
+        n = int(np.prod(shape))
+        scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
+        df = torch.empty(shape, dtype=torch.float32, device=dev)
+        fo = torch.empty(shape, dtype=torch.float32, device=dev)
+        sf = hc.as_stage(cb, "f", df)
+
+        def plain(op):
+            hc.decompress(cb, "f", out=df)
+            op()
+
+        t = {
+            "mean_stage1": time_call(torch, dev, lambda: hc.mean(cb, level="m", out=scal)),
+            "mean_stage2": time_call(torch, dev, lambda: hc.mean(cb, level="p", out=scal)),
+            "mean_plain": time_call(torch, dev, lambda: plain(lambda: hc.mean(sf, out=scal))),
+            "std_stage2": time_call(torch, dev, lambda: hc.variance(cb, level="p", out=scal)),
+            "std_stage3": time_call(torch, dev, lambda: hc.variance(cb, level="q", out=scal)),
+            "std_plain": time_call(torch, dev, lambda: plain(lambda: hc.variance(sf, out=scal))),
+            "deriv0_stage2": time_call(torch, dev, lambda: hc.derivative(cb, 0, level="p", out=fo)),
+            "deriv0_stage3": time_call(torch, dev, lambda: hc.derivative(cb, 0, level="q", out=fo)),
+            "deriv0_plain": time_call(torch, dev, lambda: plain(lambda: hc.derivative(sf, 0, out=fo))),
+            "lap_stage2": time_call(torch, dev, lambda: hc.laplacian(cb, level="p", out=fo)),
+            "lap_stage3": time_call(torch, dev, lambda: hc.laplacian(cb, level="q", out=fo)),
+            "lap_plain": time_call(torch, dev, lambda: plain(lambda: hc.laplacian(sf, out=fo))),
+        }
+        var_bytes += cb.nbytes + 64
+        sp = lambda a, b: round(t[a] / t[b], 2)  # noqa: E731
+        rows.append({"field": "x".join(map(str, shape)), "block": list(block), "box_bytes": cb.nbytes,
+                     "hszx_s64_bytes": cx.nbytes, "delta_bytes": cd.nbytes,
+                     "ms": {k: round(v, 4) for k, v in t.items()},
+                     "gbs_orig": {k: round(n * 4 / v / 1e6, 1) for k, v in t.items()},
+                     "speedup_vs_plain": {"mean_stage1": sp("mean_plain", "mean_stage1"),
+                                          "mean_stage2": sp("mean_plain", "mean_stage2"),
+                                          "std_stage2": sp("std_plain", "std_stage2"),
+                                          "std_stage3": sp("std_plain", "std_stage3"),
+                                          "deriv0_stage2": sp("deriv0_plain", "deriv0_stage2"),
+                                          "deriv0_stage3": sp("deriv0_plain", "deriv0_stage3"),
+                                          "lap_stage2": sp("lap_plain", "lap_stage2"),
+                                          "lap_stage3": sp("lap_plain", "lap_stage3")}})
+        for k, v in t.items():
+            tot[k] = tot.get(k, 0.0) + v
+        del cb, cx, cd, df, fo
+    orig = sum(int(np.prod(sh)) * 4 for sh in synth_shapes())
+    achieved = var_bytes / (tot["std_stage3"] * 1e-3) / 1e9
+    line = {"metric": "HSZx-nd (box means): GB/s of original data per stage, vs the plain path",
+            "unit": "GB/s", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("block 32;", "boxes of 4x4x4 (8x8 in 2-D), box-mean predictor "
+                                                                 "(HSZx-nd);"),
+                       "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
+            "roofline": {"kernel": "k_stats_box", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                         "algorithmic_bytes": "compressed stream + 64 B per field"},
+            "totals_ms": {k: round(v, 4) for k, v in tot.items()},
+            "totals_gbs_orig": {k: round(orig / v / 1e6, 1) for k, v in tot.items()},
+            "per_field": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def run_profile_lorenzo():
     """Small case for ncu captures of the global-predictor kernels: one
     256x384x384 float32 field as HSZp-nd (compressed ~40 MB, D_q 151 MB), the
@@ -1157,6 +1244,7 @@ def main(argv=None):
     ap.add_argument("--lorenzo", action="store_true",
                     help="the global predictors (HSZp-nd, HSZp) on the paper-like workload")
     ap.add_argument("--profile-lorenzo", action="store_true", help="run the small global-predictor ncu case")
+    ap.add_argument("--boxes", action="store_true", help="HSZx-nd (box means) on the paper-like workload")
     ap.add_argument("--fields", type=int, default=200)
     ap.add_argument("--qps", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=30.0)
@@ -1175,6 +1263,8 @@ def main(argv=None):
         return run_lorenzo(args)
     if args.profile_lorenzo:
         return run_profile_lorenzo()
+    if args.boxes:
+        return run_boxes(args)
     if args.batched:
         if args.warmup < 3:
             args.warmup = 3

@@ -83,7 +83,8 @@ typedef enum {
   HC_PRED_DELTA = 0,
   HC_PRED_MEAN = 1,
   HC_PRED_LORENZO = 2,
-  HC_PRED_GLOBAL_DELTA = 3
+  HC_PRED_GLOBAL_DELTA = 3,
+  HC_PRED_MEAN_ND = 4 /* HSZx-nd: block means over boxes of codes (hc_compress_nd) */
 } hc_predictor;
 typedef enum {
   HC_STAGE_COMPRESSED = 0, /* the stream itself (operations fuse decoding in) */
@@ -111,6 +112,8 @@ typedef struct hc_header {
   int64_t off_widths, off_heads, off_chunks, off_payload, total_bytes;
   uint32_t wmax;     /* largest block width */
   uint32_t pred;     /* hc_predictor the stream was written with */
+  uint32_t block[3]; /* HC_PRED_MEAN_ND: box extents (b0, b1, b2) along (n0, n1, n2), leading ones;
+                        S = b0 b1 b2.  0 for the other predictors */
 } hc_header;
 
 /* An input of an operation: the stream (fused decode + operation) or a
@@ -160,7 +163,9 @@ HC_API size_t hc_workspace_bytes(void);
 /* Workspace of any call on the stream `hdr` describes: hc_workspace_bytes()
  * for DELTA and MEAN streams; for the global predictors (LORENZO,
  * GLOBAL_DELTA) hc_workspace_bytes() plus scratch for a rebuilt D_q and the
- * prefix sums (about 12.3 bytes per element).  0 for a NULL header. */
+ * prefix sums (about 12.3 bytes per element); for MEAN_ND streams
+ * hc_workspace_bytes() plus 4 bytes per element (a stage in field order).
+ * 0 for a NULL header. */
 HC_API size_t hc_workspace_bytes_for(const hc_header* hdr);
 /* Bytes of a materialized stage (M, P, Q or F; F in the header's dtype). */
 HC_API size_t hc_stage_bytes(const hc_header* hdr, int kind);
@@ -199,6 +204,24 @@ HC_API int hc_compress_codes_ex(const int32_t* d_q, int dtype, int ndim, const i
                                 int eb_mode, int S, int predictor, void* d_stream, size_t cap, void* d_ws,
                                 size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, void* stream);
 
+/* HSZx-nd (Section IV, "HSZx-nd"): the field is partitioned into boxes of
+ * block[0] x ... x block[ndim-1] codes (one extent per axis, product S <=
+ * 4096) and each box is decorrelated by its integer mean, p = q - M_b (M_b the
+ * nearest integer to the box's code sum over its true size, ties toward zero;
+ * a box cut by the end of the field has the true size of its clipped extents
+ * and zero in the slots outside the field).  Boxes are stored in row-major
+ * order of the box grid ceil(n_a / b_a), the S slots of a box row-major inside
+ * it; header byte 140 = HC_PRED_MEAN_ND and bytes 144..155 the extents.
+ * Sizing: hc_compress_bound_nd / hc_compress_workspace_bytes_nd.  SYNC. */
+HC_API size_t hc_compress_bound_nd(int ndim, const int64_t* dims, const int32_t* block);
+HC_API size_t hc_compress_workspace_bytes_nd(int ndim, const int64_t* dims, const int32_t* block);
+HC_API int hc_compress_nd(const void* d_x, int dtype, int ndim, const int64_t* dims, const int32_t* block, double eb,
+                          int eb_mode, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
+                          hc_header* hdr_out, void* stream);
+HC_API int hc_compress_codes_nd(const int32_t* d_q, int dtype, int ndim, const int64_t* dims, const int32_t* block,
+                                double eps, double eb, int eb_mode, void* d_stream, size_t cap, void* d_ws,
+                                size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, void* stream);
+
 /* Copy the 256-byte header of a device-resident stream to the host and
  * validate it (magic, version, shape, section offsets, total size against
  * `bytes`).  SYNC. */
@@ -206,8 +229,9 @@ HC_API int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out
 
 /* ---------------------------------------------------------- decompression */
 /* D_i ... D_1 (Algorithm 2): decode the whole stream to stage `kind`:
- *   HC_STAGE_M -> int32 heads[nb] (HC_PRED_MEAN: the block means; the
- *   global predictors have no stage 1: HC_ERR_UNSUPPORTED);
+ *   HC_STAGE_M -> int32 heads[nb] (HC_PRED_MEAN / MEAN_ND: the block or box
+ *   means, boxes in grid order; the global predictors have no stage 1:
+ *   HC_ERR_UNSUPPORTED); MEAN_ND stages 2-4 are in field order;
  *   HC_STAGE_P -> int32[N] (HC_PRED_DELTA: head in each block's first slot,
  *   so q is the in-block prefix sum; HC_PRED_MEAN: p = q - M_b; the global
  *   predictors: their residuals); HC_STAGE_Q -> int32[N] (global
@@ -242,6 +266,9 @@ HC_API int hc_workspace_status(void* d_ws, void* stream);
  *     S and n set): the mean of Eq. mean_m, (T / N) 2 eps, from the block
  *     means alone; s1 = T, exact = 0; mean only (the variance needs the codes).
  *     HC_PRED_DELTA heads support no statistic (HC_ERR_UNSUPPORTED).
+ *   MEAN_ND streams: as MEAN with the true box sizes S_b (stage 1: Eq.
+ *     mean_m; stage 2: the exact mean and the deviation about mu~; stage 3:
+ *     exact), fused with the decode.
  *   Global predictors (stream inputs; ws_bytes >= hc_workspace_bytes_for):
  *     level P mean: sum q = sum_i p_i (L0 - z)(L1 - y)(L2 - x), (z, y, x)
  *     the position of p_i in the prediction shape L (the field's shape for
@@ -289,7 +316,11 @@ HC_API int hc_op_variance_noalloc(const hc_stage* in, double eps, int ndim, cons
  * the sum form above it), the Laplacian the sum over axes of differences of
  * such box sums (Eq. laplacian_Dp), computed from D_p by prefix sums over
  * the other axes only, never forming D_q; the gradient magnitude is not
- * offered there (HC_ERR_UNSUPPORTED).  Global-predictor streams at level Q
+ * offered there (HC_ERR_UNSUPPORTED) -- and for HC_PRED_MEAN_ND (HSZx-nd)
+ * streams at level P: Section V-B's HSZx-2d formulas on every axis, the
+ * differences of D_p plus the box means' difference where a neighbour lies
+ * in another box (derivative, gradient magnitude and Laplacian; D_p in field
+ * order is formed in the workspace, D_q never).  Global-predictor streams at level Q
  * rebuild D_q in the workspace and take the stage-3 operation on it
  * (ws_bytes >= hc_workspace_bytes_for).  `axis` is a user axis in
  * [0, ndim), 0 the slowest.  d_out: N elements of out_dtype:

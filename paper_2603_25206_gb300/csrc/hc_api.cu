@@ -34,6 +34,7 @@ int make_layout(int ndim, const int64_t* dims, int S, Layout* L) {
   }
   L->N = n;
   L->S = S;
+  L->bd[0] = L->bd[1] = L->bd[2] = 0;
   L->nb = (n + S - 1) / S;
   L->G = std::max(1, kChunkElems / S);
   L->nchunks = (L->nb + L->G - 1) / L->G;
@@ -43,6 +44,32 @@ int make_layout(int ndim, const int64_t* dims, int S, Layout* L) {
   L->off_payload = align16(L->off_chunks + 8 * (L->nchunks + 1));
   const int64_t nseg = (S + 31) / 32;
   const int64_t wmax_words = nseg + ((int64_t)S * 31 + 31) / 32;
+  L->bound = (size_t)align16(L->off_payload + 4 * L->nb * wmax_words + 16);
+  return HC_OK;
+}
+
+int make_layout_nd(int ndim, const int64_t* dims, const int32_t* block, Layout* L) {
+  if (ndim < 1 || ndim > 3 || !dims || !block) return fail(HC_ERR_INVALID_ARG, "ndim must be 1..3 with dims and block");
+  int64_t S = 1;
+  for (int a = 0; a < ndim; ++a) {
+    if (block[a] < 1 || block[a] > kMaxS) return fail(HC_ERR_INVALID_ARG, "box extents must be >= 1");
+    S *= block[a];
+    if (S > kMaxS) return fail(HC_ERR_INVALID_ARG, "box size (product of the extents) must be <= 4096");
+  }
+  int rc = make_layout(ndim, dims, (int)S, L);
+  if (rc) return rc;
+  int64_t nb = 1;
+  for (int a = 0; a < 3; ++a) {
+    L->bd[a] = a < 3 - ndim ? 1 : block[a - (3 - ndim)];
+    nb *= (L->dims[a] + L->bd[a] - 1) / L->bd[a];
+  }
+  L->nb = nb;
+  L->nchunks = (L->nb + L->G - 1) / L->G;
+  L->off_heads = align16(L->off_widths + L->nb);
+  L->off_chunks = align16(L->off_heads + 4 * L->nb);
+  L->off_payload = align16(L->off_chunks + 8 * (L->nchunks + 1));
+  const int64_t nseg = (S + 31) / 32;
+  const int64_t wmax_words = nseg + (S * 31 + 31) / 32;
   L->bound = (size_t)align16(L->off_payload + 4 * L->nb * wmax_words + 16);
   return HC_OK;
 }
@@ -129,7 +156,17 @@ int check_header(const hc_header& h) {
   Layout L;
   int64_t d[3];
   for (int a = 0; a < h.ndim; ++a) d[a] = h.dims[3 - h.ndim + a];
-  if (make_layout(h.ndim, d, h.S, &L) != HC_OK) return fail(HC_ERR_CORRUPT, "bad shape or block size");
+  if (h.pred == HC_PRED_MEAN_ND) {
+    int32_t bl[3];
+    for (int a = 0; a < 3 - h.ndim; ++a)
+      if (h.block[a] != 1) return fail(HC_ERR_CORRUPT, "leading box extents must be 1");
+    for (int a = 0; a < h.ndim; ++a) bl[a] = (int32_t)h.block[3 - h.ndim + a];
+    if ((int64_t)h.block[0] * h.block[1] * h.block[2] != h.S) return fail(HC_ERR_CORRUPT, "box extents and S disagree");
+    if (make_layout_nd(h.ndim, d, bl, &L) != HC_OK) return fail(HC_ERR_CORRUPT, "bad shape or box extents");
+  } else {
+    if (h.block[0] || h.block[1] || h.block[2]) return fail(HC_ERR_CORRUPT, "box extents on a 1-D block stream");
+    if (make_layout(h.ndim, d, h.S, &L) != HC_OK) return fail(HC_ERR_CORRUPT, "bad shape or block size");
+  }
   if (L.N != h.N || L.nb != h.nb || L.G != h.G || L.nchunks != h.nchunks || L.off_widths != h.off_widths ||
       L.off_heads != h.off_heads || L.off_chunks != h.off_chunks || L.off_payload != h.off_payload)
     return fail(HC_ERR_CORRUPT, "section offsets do not follow from the shape");
@@ -137,7 +174,7 @@ int check_header(const hc_header& h) {
     return fail(HC_ERR_CORRUPT, "payload size and total size disagree");
   if ((size_t)h.total_bytes > L.bound) return fail(HC_ERR_CORRUPT, "payload larger than any valid stream");
   if (h.wmax > 31) return fail(HC_ERR_CORRUPT, "max width above 31");
-  if (h.pred > HC_PRED_GLOBAL_DELTA) return fail(HC_ERR_CORRUPT, "unknown predictor");
+  if (h.pred > HC_PRED_MEAN_ND) return fail(HC_ERR_CORRUPT, "unknown predictor");
   if (!(h.eps > 0.0) || !std::isfinite(h.eps)) return fail(HC_ERR_CORRUPT, "bad eps");
   if (h.qmax >= (1u << 30)) return fail(HC_ERR_CORRUPT, "max |q| out of range");
   return HC_OK;
@@ -174,6 +211,7 @@ int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStr
   h.total_bytes = (int64_t)le(b, 128, 8);
   h.wmax = (uint32_t)le(b, 136, 4);
   h.pred = (uint32_t)le(b, 140, 4);
+  for (int a = 0; a < 3; ++a) h.block[a] = (uint32_t)le(b, 144 + 4 * a, 4);
   int rc = check_header(h);
   if (rc) return rc;
   if ((size_t)h.total_bytes > bytes) return fail(HC_ERR_CORRUPT, "stream truncated");
@@ -218,7 +256,7 @@ static int check_op(const hc_stage* in, double eps, int ndim, const int64_t* dim
   if (in->kind == HC_STAGE_P && in->pred == HC_PRED_MEAN)
     return fail(HC_ERR_UNSUPPORTED, "a block-mean D_p array needs its block means: operate on the stream");
   if ((in->kind == HC_STAGE_P || in->kind == HC_STAGE_M) && in->pred >= HC_PRED_LORENZO)
-    return fail(HC_ERR_UNSUPPORTED, "a global-predictor D_p array: operate on the stream");
+    return fail(HC_ERR_UNSUPPORTED, "a global-predictor or box D_p array: operate on the stream");
   if (in->kind < HC_STAGE_M || in->kind > HC_STAGE_F) return fail(HC_ERR_INVALID_ARG, "unknown stage kind");
   return HC_OK;
 }
@@ -268,6 +306,7 @@ size_t hc_workspace_bytes(void) { return kOpWsBytes; }
 
 size_t hc_workspace_bytes_for(const hc_header* hdr) {
   if (!hdr) return 0;
+  if (hdr->pred == HC_PRED_MEAN_ND) return xnd_workspace_bytes(hdr);
   return global_workspace_bytes(hdr);
 }
 
@@ -291,7 +330,8 @@ size_t hc_stage_bytes(const hc_header* hdr, int kind) {
 int hc_compress_ex(const void* d_x, int dtype, int ndim, const int64_t* dims, double eb, int eb_mode, int S,
                    int predictor, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
                    hc_header* hdr_out, void* stream) {
-  return compress_impl(d_x, dtype == HC_F64 ? 1 : 0, dtype, ndim, dims, eb, 0.0, eb_mode, S, predictor, d_stream,
+  if (predictor == HC_PRED_MEAN_ND) return fail(HC_ERR_INVALID_ARG, "HSZx-nd streams are written by hc_compress_nd");
+  return compress_impl(d_x, dtype == HC_F64 ? 1 : 0, dtype, ndim, dims, eb, 0.0, eb_mode, S, predictor, nullptr, d_stream,
                        cap, d_ws, ws_bytes, out_bytes, hdr_out, as_stream(stream));
 }
 
@@ -306,7 +346,8 @@ int hc_compress_codes_ex(const int32_t* d_q, int dtype, int ndim, const int64_t*
                          int eb_mode, int S, int predictor, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
                          size_t* out_bytes, hc_header* hdr_out, void* stream) {
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HC_ERR_INVALID_ARG, "eps must be positive and finite");
-  return compress_impl(d_q, 2, dtype, ndim, dims, eb, eps, eb_mode, S, predictor, d_stream, cap, d_ws, ws_bytes,
+  if (predictor == HC_PRED_MEAN_ND) return fail(HC_ERR_INVALID_ARG, "HSZx-nd streams are written by hc_compress_codes_nd");
+  return compress_impl(d_q, 2, dtype, ndim, dims, eb, eps, eb_mode, S, predictor, nullptr, d_stream, cap, d_ws, ws_bytes,
                        out_bytes, hdr_out, as_stream(stream));
 }
 
@@ -315,6 +356,33 @@ int hc_compress_codes(const int32_t* d_q, int dtype, int ndim, const int64_t* di
                       hc_header* hdr_out, void* stream) {
   return hc_compress_codes_ex(d_q, dtype, ndim, dims, eps, eb, eb_mode, S, HC_PRED_DELTA, d_stream, cap, d_ws,
                               ws_bytes, out_bytes, hdr_out, stream);
+}
+
+size_t hc_compress_bound_nd(int ndim, const int64_t* dims, const int32_t* block) {
+  Layout L;
+  if (make_layout_nd(ndim, dims, block, &L) != HC_OK) return 0;
+  return L.bound;
+}
+
+size_t hc_compress_workspace_bytes_nd(int ndim, const int64_t* dims, const int32_t* block) {
+  Layout L;
+  if (make_layout_nd(ndim, dims, block, &L) != HC_OK) return 0;
+  return compress_ws_bytes(L);
+}
+
+int hc_compress_nd(const void* d_x, int dtype, int ndim, const int64_t* dims, const int32_t* block, double eb,
+                   int eb_mode, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes, size_t* out_bytes,
+                   hc_header* hdr_out, void* stream) {
+  return compress_impl(d_x, dtype == HC_F64 ? 1 : 0, dtype, ndim, dims, eb, 0.0, eb_mode, 0, HC_PRED_MEAN_ND, block,
+                       d_stream, cap, d_ws, ws_bytes, out_bytes, hdr_out, as_stream(stream));
+}
+
+int hc_compress_codes_nd(const int32_t* d_q, int dtype, int ndim, const int64_t* dims, const int32_t* block,
+                         double eps, double eb, int eb_mode, void* d_stream, size_t cap, void* d_ws, size_t ws_bytes,
+                         size_t* out_bytes, hc_header* hdr_out, void* stream) {
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HC_ERR_INVALID_ARG, "eps must be positive and finite");
+  return compress_impl(d_q, 2, dtype, ndim, dims, eb, eps, eb_mode, 0, HC_PRED_MEAN_ND, block, d_stream, cap, d_ws,
+                       ws_bytes, out_bytes, hdr_out, as_stream(stream));
 }
 
 int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out, void* stream) {
@@ -330,6 +398,8 @@ int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, int kind,
   if (kind < HC_STAGE_M || kind > HC_STAGE_F) return fail(HC_ERR_INVALID_ARG, "kind must be M, P, Q or F");
   if (kind == HC_STAGE_F && out_dtype != HC_F32 && out_dtype != HC_F64)
     return fail(HC_ERR_INVALID_ARG, "F output is HC_F32 or HC_F64");
+  if (hdr->pred == HC_PRED_MEAN_ND)
+    return xnd_decode_impl(hdr, d_stream, kind, d_out, out_dtype, d_ws, ws_bytes, as_stream(stream));
   if (hdr->pred >= HC_PRED_LORENZO)
     return global_decode_impl(hdr, d_stream, kind, d_out, out_dtype, d_ws, ws_bytes, as_stream(stream));
   return decode_impl(hdr, d_stream, kind, d_out, out_dtype, d_ws, as_stream(stream));
@@ -353,6 +423,8 @@ static int stats(const hc_stage* in, double eps, int ndim, const int64_t* dims, 
   if (rc) return rc;
   if (!d_out) return fail(HC_ERR_INVALID_ARG, "null output");
   if (in->kind == HC_STAGE_COMPRESSED) {
+    if (in->hdr->pred == HC_PRED_MEAN_ND)
+      return xnd_stats_impl(in->hdr, in->d_data, in->level, what, d_out, d_ws, ws_bytes, as_stream(stream));
     if (in->hdr->pred >= HC_PRED_LORENZO)
       return global_stats_impl(in->hdr, in->d_data, in->level, what, d_out, d_ws, ws_bytes, as_stream(stream));
     return reduce_stream_impl(in->hdr, in->d_data, in->level, what, d_out, d_ws, as_stream(stream));
@@ -391,6 +463,9 @@ static int stencil(const hc_stage* in, double eps, int ndim, const int64_t* dims
   const int axis3 = axis + 3 - ndim;
   if (in->kind == HC_STAGE_COMPRESSED) {
     if (in->level == HC_STAGE_M) return fail(HC_ERR_UNSUPPORTED, "stage 1 holds no point values to differentiate");
+    if (in->hdr->pred == HC_PRED_MEAN_ND)
+      return xnd_stencil_impl(in->hdr, in->d_data, in->level, op, axis3, d_out, out_dtype, d_ws, ws_bytes,
+                              as_stream(stream));
     if (in->hdr->pred >= HC_PRED_LORENZO)
       return global_stencil_impl(in->hdr, in->d_data, in->level, op, axis3, d_out, out_dtype, d_ws, ws_bytes,
                                  as_stream(stream));

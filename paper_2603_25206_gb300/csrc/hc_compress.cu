@@ -154,7 +154,21 @@ struct OutStream {
   int S, G, nseg;
   int pred;      // hc_predictor
   int64_t L[3];  // prediction shape of the global predictors: (n0, n1, n2), or (1, 1, N) for HSZp
+  int64_t bd[3];  // HSZx-nd: box extents along (n0, n1, n2)
+  int64_t gd[3];  // HSZx-nd: box grid ceil(n_a / b_a)
 };
+
+// HSZx-nd: field index of slot k of box b (row-major inside the box, boxes
+// row-major over the grid), or -1 for a slot outside the field.
+__device__ __forceinline__ int64_t box_slot_index(const OutStream& o, int64_t b, int64_t k) {
+  const int64_t k2 = b % o.gd[2], r = b / o.gd[2];
+  const int64_t k1 = r % o.gd[1], k0 = r / o.gd[1];
+  const int64_t s2 = k % o.bd[2], t = k / o.bd[2];
+  const int64_t s1 = t % o.bd[1], s0 = t / o.bd[1];
+  const int64_t z = k0 * o.bd[0] + s0, y = k1 * o.bd[1] + s1, x = k2 * o.bd[2] + s2;
+  if (z >= o.L[0] || y >= o.L[1] || x >= o.L[2]) return -1;
+  return (z * o.L[1] + y) * o.L[2] + x;
+}
 
 // Residual of the global predictors at flat index i (Section IV, HSZp and
 // HSZp-nd): the Lorenzo residual over the prediction shape L, with codes
@@ -218,7 +232,31 @@ __global__ void __launch_bounds__(kThreads) k_blocks(Src src, OutStream o, CompW
     int32_t prev = 0, q;
     uint32_t maxmag = 0, qm = 0;
     bool ok = true;
-    if (o.pred >= HC_PRED_LORENZO) {
+    if (o.pred == HC_PRED_MEAN_ND) {
+      // HSZx-nd: the box mean over the slots inside the field, then the
+      // widest |q - M_b| over them
+      long long sum = 0;
+      int64_t nin = 0;
+      for (int64_t k = 0; k < o.S; ++k) {
+        const int64_t i = box_slot_index(o, b, k);
+        if (i < 0) continue;
+        ok &= quantize_at(src, i, two_eps, q);
+        sum += q;
+        ++nin;
+        const uint32_t aq = (uint32_t)(q < 0 ? -q : q);
+        qm = aq > qm ? aq : qm;
+      }
+      const int32_t mb = ok ? nearest_ratio(sum, nin) : 0;
+      o.heads[b] = mb;
+      for (int64_t k = 0; k < o.S && ok; ++k) {
+        const int64_t i = box_slot_index(o, b, k);
+        if (i < 0) continue;
+        quantize_at(src, i, two_eps, q);
+        const int32_t p = q - mb;
+        const uint32_t m = (uint32_t)(p < 0 ? -(long long)p : (long long)p);
+        maxmag = m > maxmag ? m : maxmag;
+      }
+    } else if (o.pred >= HC_PRED_LORENZO) {
       // global predictors: no block metadata, the widest residual
       o.heads[b] = 0;
       for (int64_t k = 0; k < Sb; ++k) {
@@ -351,11 +389,18 @@ __global__ void __launch_bounds__(kThreads) k_pack(Src src, OutStream o, CompWs*
     uint32_t nbits = 0;
     int32_t prev = 0, q;
     const bool mean_pred = o.pred == HC_PRED_MEAN;
-    const bool global_pred = o.pred >= HC_PRED_LORENZO;
+    const bool box_pred = o.pred == HC_PRED_MEAN_ND;
+    const bool global_pred = o.pred == HC_PRED_LORENZO || o.pred == HC_PRED_GLOBAL_DELTA;
     const int32_t mb = mean_pred ? o.heads[b] : 0;
     for (int64_t k = 0; k < o.S; ++k) {
       int32_t p = 0;
-      if (k < Sb) {
+      if (box_pred) {
+        const int64_t i = box_slot_index(o, b, k);
+        if (i >= 0) {
+          quantize_at(src, i, two_eps, q);
+          p = q - o.heads[b];
+        }
+      } else if (k < Sb) {
         if (global_pred) {
           global_residual(src, o, first + k, two_eps, p);
         } else {
@@ -384,6 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_pack(Src src, OutStream o, CompWs*
 
 struct HeaderArgs {
   int dtype, ndim, S, G, eb_mode, pred;
+  int64_t bd[3];  // HSZx-nd box extents (0 otherwise)
   int64_t dims[3];
   double eb;
   int64_t N, nb, nchunks, off_widths, off_heads, off_chunks, off_payload;
@@ -421,6 +467,7 @@ __global__ void k_header(HeaderArgs a, uint8_t* stream, CompWs* ws) {
   put_le(stream, 128, (unsigned long long)total, 8);
   put_le(stream, 136, ws->wmax, 4);
   put_le(stream, 140, (unsigned long long)a.pred, 4);
+  for (int d = 0; d < 3; ++d) put_le(stream, 144 + 4 * d, (unsigned long long)a.bd[d], 4);
   for (int64_t i = a.off_widths + a.nb; i < a.off_heads; ++i) stream[i] = 0;
   for (int64_t i = a.off_heads + 4 * a.nb; i < a.off_chunks; ++i) stream[i] = 0;
   for (int64_t i = a.off_chunks + 8 * (a.nchunks + 1); i < a.off_payload; ++i) stream[i] = 0;
@@ -429,16 +476,17 @@ __global__ void k_header(HeaderArgs a, uint8_t* stream, CompWs* ws) {
 
 // ------------------------------------------------------------------ host
 int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int64_t* dims, double eb,
-                  double eps_given, int eb_mode, int S, int pred, void* d_stream, size_t cap, void* d_ws,
-                  size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, cudaStream_t st) {
+                  double eps_given, int eb_mode, int S, int pred, const int32_t* block, void* d_stream, size_t cap,
+                  void* d_ws, size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, cudaStream_t st) {
   Layout L;
-  int rc = make_layout(ndim, dims, S, &L);
+  int rc = pred == HC_PRED_MEAN_ND ? make_layout_nd(ndim, dims, block, &L) : make_layout(ndim, dims, S, &L);
   if (rc) return rc;
+  S = L.S;
   if (!d_x || !d_stream || !d_ws || !out_bytes) return fail(HC_ERR_INVALID_ARG, "null pointer");
   if (!aligned16(d_stream) || !aligned16(d_ws) || !aligned16(d_x)) return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
   if (dtype != HC_F32 && dtype != HC_F64) return fail(HC_ERR_INVALID_ARG, "dtype must be HC_F32 or HC_F64");
   if (eb_mode != HC_EB_ABS && eb_mode != HC_EB_REL) return fail(HC_ERR_INVALID_ARG, "eb_mode");
-  if (pred < HC_PRED_DELTA || pred > HC_PRED_GLOBAL_DELTA) return fail(HC_ERR_INVALID_ARG, "predictor");
+  if (pred < HC_PRED_DELTA || pred > HC_PRED_MEAN_ND) return fail(HC_ERR_INVALID_ARG, "predictor");
   if (!(eb > 0.0) || !std::isfinite(eb)) return fail(HC_ERR_INVALID_ARG, "eb must be positive and finite");
   if (cap < L.bound) return fail(HC_ERR_NOMEM, "stream buffer smaller than hc_compress_bound");
   if (ws_bytes < compress_ws_bytes(L)) return fail(HC_ERR_NOMEM, "workspace smaller than hc_compress_workspace_bytes");
@@ -458,7 +506,11 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   o.G = L.G;
   o.nseg = (S + 31) / 32;
   o.pred = pred;
-  for (int d = 0; d < 3; ++d) o.L[d] = pred == HC_PRED_GLOBAL_DELTA ? (d == 2 ? L.N : 1) : L.dims[d];
+  for (int d = 0; d < 3; ++d) {
+    o.L[d] = pred == HC_PRED_GLOBAL_DELTA ? (d == 2 ? L.N : 1) : L.dims[d];
+    o.bd[d] = L.bd[d] ? L.bd[d] : 1;
+    o.gd[d] = (L.dims[d] + o.bd[d] - 1) / o.bd[d];
+  }
 
   const int sms = device_sms();
   k_ws_init<<<(unsigned)std::min<int64_t>(ceil_div(L.nchunks, kThreads) + 1, 4096), kThreads, 0, st>>>(ws, L.nchunks);
@@ -495,7 +547,10 @@ int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int6
   a.G = L.G;
   a.eb_mode = eb_mode;
   a.pred = pred;
-  for (int d = 0; d < 3; ++d) a.dims[d] = L.dims[d];
+  for (int d = 0; d < 3; ++d) {
+    a.dims[d] = L.dims[d];
+    a.bd[d] = L.bd[d];
+  }
   a.eb = eb;
   a.N = L.N;
   a.nb = L.nb;

@@ -237,18 +237,22 @@ int decode_residuals_impl(const hc_header* h, const void* d_stream, void* d_out,
   return launch_decode_sp<HC_STAGE_P, int32_t, HC_PRED_MEAN>(h, d_stream, d_out, err, st);
 }
 
+// Stage 1: the heads section as it is (first codes, block means or box means).
+int decode_heads_impl(const hc_header* h, const void* d_stream, void* d_out, cudaStream_t st) {
+  const uint8_t* b = reinterpret_cast<const uint8_t*>(d_stream);
+  const int grid = (int)std::min<int64_t>(ceil_div(h->nb, kThreads), 4096);
+  k_copy_heads<<<grid, kThreads, 0, st>>>(reinterpret_cast<const int32_t*>(b + h->off_heads),
+                                          reinterpret_cast<int32_t*>(d_out), h->nb);
+  return check_launch("decompress_to_stage(M)");
+}
+
 int decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,
                 cudaStream_t st) {
   if (h->pred >= HC_PRED_LORENZO) return fail(HC_ERR_INVALID_ARG, "global-predictor stream on the block decoder");
   int* err = &reinterpret_cast<OpWs*>(d_ws)->status;
   switch (kind) {
-    case HC_STAGE_M: {
-      const uint8_t* b = reinterpret_cast<const uint8_t*>(d_stream);
-      const int grid = (int)std::min<int64_t>(ceil_div(h->nb, kThreads), 4096);
-      k_copy_heads<<<grid, kThreads, 0, st>>>(reinterpret_cast<const int32_t*>(b + h->off_heads),
-                                              reinterpret_cast<int32_t*>(d_out), h->nb);
-      return check_launch("decompress_to_stage(M)");
-    }
+    case HC_STAGE_M:
+      return decode_heads_impl(h, d_stream, d_out, st);
     case HC_STAGE_P:
       return launch_decode_s<HC_STAGE_P, int32_t>(h, d_stream, d_out, err, st);
     case HC_STAGE_Q:

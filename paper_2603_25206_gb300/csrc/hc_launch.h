@@ -21,6 +21,7 @@ struct Layout {
   int S, G;
   int64_t off_widths, off_heads, off_chunks, off_payload;
   size_t bound;  // stream bytes with every block at width 31
+  int64_t bd[3];  // HSZx-nd box extents (leading ones); 0 for 1-D blocks
 };
 
 // Record a failure message (thread-local) and return `code`.
@@ -28,6 +29,9 @@ int fail(int code, const char* msg);
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int make_layout(int ndim, const int64_t* dims, int S, Layout* L);
+// Layout of an HSZx-nd stream: boxes of block[0..ndim) codes, S their product,
+// nb the box grid.
+int make_layout_nd(int ndim, const int64_t* dims, const int32_t* block, Layout* L);
 size_t compress_ws_bytes(const Layout& L);
 
 int device_sms();
@@ -41,9 +45,10 @@ int ensure_smem(const void* kernel, int bytes);
 int check_header(const hc_header& h);
 int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st);
 
+// block: the box extents of an HSZx-nd stream (pred HC_PRED_MEAN_ND), else NULL
 int compress_impl(const void* d_x, int src_kind, int dtype, int ndim, const int64_t* dims, double eb,
-                  double eps_given, int eb_mode, int S, int pred, void* d_stream, size_t cap, void* d_ws,
-                  size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, cudaStream_t st);
+                  double eps_given, int eb_mode, int S, int pred, const int32_t* block, void* d_stream, size_t cap,
+                  void* d_ws, size_t ws_bytes, size_t* out_bytes, hc_header* hdr_out, cudaStream_t st);
 
 // Workspace of decompression and operations: a status word, the
 // last-block ticket of the reductions and the per-CTA partial results.
@@ -71,6 +76,8 @@ int decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out,
 // The residuals D_p of every slot (block-mean and global-predictor streams),
 // int32[N] into d_out (hc_decode.cu).
 int decode_residuals_impl(const hc_header* h, const void* d_stream, void* d_out, void* d_ws, cudaStream_t st);
+// Stage 1: a copy of the heads section (hc_decode.cu).
+int decode_heads_impl(const hc_header* h, const void* d_stream, void* d_out, cudaStream_t st);
 
 // Global-predictor streams (hc_global.cu): workspace they need (any call),
 // decompression, statistics and stencils at a level.
@@ -81,6 +88,15 @@ int global_stats_impl(const hc_header* h, const void* d_stream, int level, int w
                       size_t ws_bytes, cudaStream_t st);
 int global_stencil_impl(const hc_header* h, const void* d_stream, int level, int op, int axis3, void* d_out,
                         int out_dtype, void* d_ws, size_t ws_bytes, cudaStream_t st);
+
+// HSZx-nd streams (hc_xnd.cu): the same four entry points.
+size_t xnd_workspace_bytes(const hc_header* h);
+int xnd_decode_impl(const hc_header* h, const void* d_stream, int kind, void* d_out, int out_dtype, void* d_ws,
+                    size_t ws_bytes, cudaStream_t st);
+int xnd_stats_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, void* d_ws,
+                   size_t ws_bytes, cudaStream_t st);
+int xnd_stencil_impl(const hc_header* h, const void* d_stream, int level, int op, int axis3, void* d_out,
+                     int out_dtype, void* d_ws, size_t ws_bytes, cudaStream_t st);
 
 enum ReduceWhat { RED_MEAN = 0, RED_VAR = 1 };
 int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out,

@@ -43,13 +43,15 @@ ABI_FUNCTIONS = (
     "hc_op_derivative", "hc_op_gradmag", "hc_op_laplacian", "hc_op_variance_noalloc", "hc_autotune",
     "hc_batch_plan_bytes", "hc_batch_workspace_bytes", "hc_batch_plan", "hc_batch_run", "hc_batch_graph_create",
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
-    "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for",
+    "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for", "hc_compress_bound_nd",
+    "hc_compress_workspace_bytes_nd", "hc_compress_nd", "hc_compress_codes_nd",
 )
-HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA = 0, 1, 2, 3
+HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA, HC_PRED_MEAN_ND = 0, 1, 2, 3, 4
 # "delta": HSZp with block heads; "mean": HSZx; "lorenzo": HSZp-nd (Lorenzo over
-# the field's axes); "global": HSZp (delta across blocks, flattened field)
+# the field's axes); "global": HSZp (delta across blocks, flattened field);
+# "mean-nd": HSZx-nd (box means, boxes given by `block`)
 PREDICTORS = {"delta": HC_PRED_DELTA, "mean": HC_PRED_MEAN, "lorenzo": HC_PRED_LORENZO,
-              "global": HC_PRED_GLOBAL_DELTA}
+              "global": HC_PRED_GLOBAL_DELTA, "mean-nd": HC_PRED_MEAN_ND}
 HC_BATCH_MEAN, HC_BATCH_VARIANCE, HC_BATCH_DERIVATIVE, HC_BATCH_GRADMAG, HC_BATCH_LAPLACIAN = 1, 2, 4, 8, 16
 BATCH_OPS = {"mean": HC_BATCH_MEAN, "variance": HC_BATCH_VARIANCE, "derivative": HC_BATCH_DERIVATIVE,
              "gradmag": HC_BATCH_GRADMAG, "laplacian": HC_BATCH_LAPLACIAN}
@@ -68,7 +70,7 @@ class HcHeader(ctypes.Structure):
                 ("nb", ctypes.c_int64), ("nchunks", ctypes.c_int64), ("payload_words", ctypes.c_int64),
                 ("off_widths", ctypes.c_int64), ("off_heads", ctypes.c_int64), ("off_chunks", ctypes.c_int64),
                 ("off_payload", ctypes.c_int64), ("total_bytes", ctypes.c_int64), ("wmax", ctypes.c_uint32),
-                ("pred", ctypes.c_uint32)]
+                ("pred", ctypes.c_uint32), ("block", ctypes.c_uint32 * 3)]
 
     @property
     def shape(self):
@@ -128,6 +130,12 @@ def lib():
             "hc_compress_workspace_bytes": ([i64, i32], sz),
             "hc_workspace_bytes": ([], sz),
             "hc_workspace_bytes_for": ([P(HcHeader)], sz),
+            "hc_compress_bound_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
+            "hc_compress_workspace_bytes_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
+            "hc_compress_nd": ([vp, i32, i32, P(ctypes.c_int64), P(ctypes.c_int32), dbl, i32, vp, sz, vp, sz, P(sz),
+                                P(HcHeader), vp], i32),
+            "hc_compress_codes_nd": ([vp, i32, i32, P(ctypes.c_int64), P(ctypes.c_int32), dbl, dbl, i32, vp, sz, vp,
+                                      sz, P(sz), P(HcHeader), vp], i32),
             "hc_stage_bytes": ([P(HcHeader), i32], sz),
             "hc_compress": ([vp, i32, i32, P(ctypes.c_int64), dbl, i32, i32, vp, sz, vp, sz, P(sz), P(HcHeader), vp],
                             i32),
@@ -272,11 +280,24 @@ class StageArray:
         return st
 
 
-def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None, predictor: str = "delta") -> Compressed:
+def _block(block, ndim):
+    if block is None or len(block) != ndim:
+        raise ValueError("predictor 'mean-nd' needs block: one box extent per axis")
+    arr = (ctypes.c_int32 * 3)()
+    for i, b in enumerate(block):
+        arr[i] = int(b)
+    return arr
+
+
+def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None, predictor: str = "delta",
+             block=None) -> Compressed:
     """C (Algorithm 1) of a float32/float64 CUDA tensor.  predictor "delta"
-    (HSZp with block heads), "mean" (HSZx: block means), "lorenzo" (HSZp-nd)
-    or "global" (HSZp, delta across blocks)."""
+    (HSZp with block heads), "mean" (HSZx: block means), "lorenzo" (HSZp-nd),
+    "global" (HSZp, delta across blocks) or "mean-nd" (HSZx-nd: box means,
+    boxes of `block` codes, one extent per axis; S is then their product)."""
     torch = _torch()
+    if predictor == "mean-nd":
+        return _compress_nd(x, None, eb, rel, block, stream)
     if not x.is_cuda:
         raise ValueError("compress expects a CUDA tensor")
     x = x.contiguous()
@@ -296,10 +317,41 @@ def compress(x, eb: float, rel: bool = True, S: int = 32, stream=None, predictor
     return Compressed(out, hdr, nbytes.value)
 
 
+def _compress_nd(x, codes_eps, eb, rel, block, stream, dtype="float32"):
+    torch = _torch()
+    src = x.contiguous()
+    shape = tuple(src.shape)
+    L = lib()
+    bl = _block(block, len(shape))
+    cap = int(L.hc_compress_bound_nd(len(shape), _dims(shape), bl))
+    wsn = int(L.hc_compress_workspace_bytes_nd(len(shape), _dims(shape), bl))
+    if not cap or not wsn:
+        raise HcError(HC_ERR_INVALID_ARG, "bad shape or box extents")
+    out = torch.empty(cap, dtype=torch.uint8, device=src.device)
+    ws = torch.empty(wsn, dtype=torch.uint8, device=src.device)
+    nbytes = ctypes.c_size_t()
+    hdr = HcHeader()
+    if codes_eps is None:
+        dt = HC_F64 if src.dtype == torch.float64 else HC_F32
+        _check(L.hc_compress_nd(ctypes.c_void_p(src.data_ptr()), dt, len(shape), _dims(shape), bl, eb,
+                                HC_EB_REL if rel else HC_EB_ABS, ctypes.c_void_p(out.data_ptr()), cap,
+                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(nbytes), ctypes.byref(hdr),
+                                _stream_ptr(stream)))
+    else:
+        _check(L.hc_compress_codes_nd(ctypes.c_void_p(src.data_ptr()), HC_F64 if dtype == "float64" else HC_F32,
+                                      len(shape), _dims(shape), bl, codes_eps, codes_eps if eb is None else eb,
+                                      HC_EB_REL if rel else HC_EB_ABS, ctypes.c_void_p(out.data_ptr()), cap,
+                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(nbytes),
+                                      ctypes.byref(hdr), _stream_ptr(stream)))
+    return Compressed(out, hdr, nbytes.value)
+
+
 def compress_codes(q, eps: float, S: int = 32, dtype: str = "float32", eb=None, rel=False, stream=None,
-                   predictor: str = "delta") -> Compressed:
+                   predictor: str = "delta", block=None) -> Compressed:
     """Encode given int32 codes (CUDA tensor)."""
     torch = _torch()
+    if predictor == "mean-nd":
+        return _compress_nd(q, eps, eb, rel, block, stream, dtype)
     q = q.contiguous()
     L = lib()
     cap = int(L.hc_compress_bound(q.numel(), S))
