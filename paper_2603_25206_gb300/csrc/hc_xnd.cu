@@ -254,32 +254,41 @@ __global__ void __launch_bounds__(kThreads) k_stats_box(DevStream s, BoxGeo bg, 
 // axis, D = W[hi] - W[lo] + (M[box hi] - M[box lo] when the two neighbours
 // lie in different boxes), one-sided and doubled at a domain edge, 0 on an
 // axis of length 1; the Laplacian adds, per existing neighbour,
-// W[nb] - W[c] + (M[box nb] - M[box c] across a box border).
+// W[nb] - W[c] + (M[box nb] - M[box c] across a box border).  A CTA takes a
+// run of kThreads points of one row: the box coordinates of the row are
+// formed once, and a neighbour crosses into the next box along an axis only
+// from the box's first or last layer, so no neighbour needs a division.
 template <int OP, int OUT>
 __global__ void __launch_bounds__(kThreads) k_box_stencil(const int32_t* __restrict__ W, const int32_t* __restrict__ M,
                                                            BoxGeo bg, Geo g, typename OutType<OUT>::T* __restrict__ out) {
-  const int64_t n = bg.n[0] * bg.n[1] * bg.n[2];
-  const int64_t st[3] = {bg.n[1] * bg.n[2], bg.n[2], 1};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c[3] = {i / st[0], (i / st[1]) % bg.n[1], i % bg.n[2]};
-    auto box_of = [&](int64_t z, int64_t y, int64_t x) -> int64_t {
-      return ((z / bg.b[0]) * bg.g[1] + y / bg.b[1]) * bg.g[2] + x / bg.b[2];
-    };
-    const int64_t bc = box_of(c[0], c[1], c[2]);
+  const int64_t rows = bg.n[0] * bg.n[1];
+  const int n2 = (int)bg.n[2];
+  const int64_t nxc = (n2 + kThreads - 1) / kThreads;
+  const int64_t st[3] = {bg.n[1] * bg.n[2], bg.n[2], 1};   // element strides
+  const int64_t gs[3] = {bg.g[1] * bg.g[2], bg.g[2], 1};   // box-index strides
+  for (int64_t t = blockIdx.x; t < rows * nxc; t += gridDim.x) {
+    const int64_t row = t / nxc;
+    const int x = (int)(t - row * nxc) * kThreads + threadIdx.x;
+    if (x >= n2) continue;
+    const int64_t z = row / bg.n[1], y = row - z * bg.n[1];
+    const int64_t kz = z / bg.b[0], ky = y / bg.b[1];
+    const int kx = x / bg.b[2];
+    const int64_t c[3] = {z, y, x};
+    const int r[3] = {(int)(z - kz * bg.b[0]), (int)(y - ky * bg.b[1]), x - kx * bg.b[2]};
+    const int64_t bc = kz * gs[0] + ky * gs[1] + kx;
+    const int64_t i = row * n2 + x;
     if constexpr (OP == ST_LAPLACIAN) {
       const long long wc = __ldg(W + i), mc = __ldg(M + bc);
       long long v = 0;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int sg = -1; sg <= 1; sg += 2) {
-          const int64_t k = c[a] + sg;
-          if (k < 0 || k >= bg.n[a]) continue;  // replicated edge: term 0
-          int64_t nbc[3] = {c[0], c[1], c[2]};
-          nbc[a] = k;
-          v += (long long)__ldg(W + i + sg * st[a]) - wc;
-          const int64_t bn = box_of(nbc[0], nbc[1], nbc[2]);
-          if (bn != bc) v += (long long)__ldg(M + bn) - mc;
+        if (c[a] > 0) {  // lower neighbour (a missing one replicates the edge: term 0)
+          v += (long long)__ldg(W + i - st[a]) - wc;
+          if (r[a] == 0) v += (long long)__ldg(M + bc - gs[a]) - mc;
+        }
+        if (c[a] + 1 < bg.n[a]) {
+          v += (long long)__ldg(W + i + st[a]) - wc;
+          if (r[a] == bg.b[a] - 1) v += (long long)__ldg(M + bc + gs[a]) - mc;
         }
       }
       out[i] = emit<OP, OUT>(v, 0, 0, g);
@@ -288,17 +297,14 @@ __global__ void __launch_bounds__(kThreads) k_box_stencil(const int32_t* __restr
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (OP == ST_DERIV && a != g.axis) continue;
-        const int64_t len = bg.n[a];
+        const int64_t len = bg.n[a], k = c[a];
         if (len == 1) continue;
-        const int64_t k = c[a];
-        const int64_t lo = k == 0 ? 0 : k - 1, hi = k == len - 1 ? k : k + 1;
-        int64_t cl[3] = {c[0], c[1], c[2]}, ch[3] = {c[0], c[1], c[2]};
-        cl[a] = lo;
-        ch[a] = hi;
-        long long v = (long long)__ldg(W + i + (hi - k) * st[a]) - __ldg(W + i + (lo - k) * st[a]);
-        const int64_t bh = box_of(ch[0], ch[1], ch[2]), bl = box_of(cl[0], cl[1], cl[2]);
-        if (bh != bl) v += (long long)__ldg(M + bh) - __ldg(M + bl);
-        d[a] = (k == 0 || k == len - 1) ? 2 * v : v;
+        const bool lo_step = k > 0, hi_step = k + 1 < len;  // one-sided at an edge
+        long long v = (long long)__ldg(W + i + (hi_step ? st[a] : 0)) - __ldg(W + i - (lo_step ? st[a] : 0));
+        const bool lo_cross = lo_step && r[a] == 0, hi_cross = hi_step && r[a] == bg.b[a] - 1;
+        if (lo_cross || hi_cross)
+          v += (long long)__ldg(M + bc + (hi_cross ? gs[a] : 0)) - __ldg(M + bc - (lo_cross ? gs[a] : 0));
+        d[a] = (lo_step && hi_step) ? v : 2 * v;
       }
       if constexpr (OP == ST_DERIV)
         out[i] = emit<OP, OUT>(d[g.axis], 0, 0, g);
@@ -382,6 +388,7 @@ int launch_box_stencil(const hc_header* h, const int32_t* W, const int32_t* M, i
                        cudaStream_t st) {
   const Geo g = stencil_base_geo(h->dims, h->eps, axis3);
   const BoxGeo bg = box_geo(h);
+  if (h->dims[2] > 0x7fffffff) return fail(HC_ERR_UNSUPPORTED, "rows longer than 2^31 codes");
   switch (out_dtype) {
     case HC_F32:
       k_box_stencil<OP, HC_F32><<<elem_grid(h->N), kThreads, 0, st>>>(W, M, bg, g, reinterpret_cast<float*>(d_out));
