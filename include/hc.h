@@ -347,9 +347,20 @@ HC_API int hc_op_laplacian(const hc_stage* in, double eps, int ndim, const int64
  * an edge).  Components quantized with different eps are scaled one by one,
  * sum_c eps_c D_c in double (the paper assumes one eps); an HC_I64 output
  * (the exact integer numerator) needs one eps for all components.
- *   comps: ncomp HC_STAGE_COMPRESSED stages at level HC_STAGE_Q.
+ *   comps: ncomp HC_STAGE_COMPRESSED stages, all at level HC_STAGE_Q (or all
+ *   at HC_STAGE_P for HSZp-nd / HSZx-nd components, see below).
  *   d_out: N outputs of out_dtype (HC_F32, HC_F64 or HC_I64), 16-byte aligned.
  * Rows longer than about a million codes are HC_ERR_UNSUPPORTED.  ASYNC. */
+/* Components of other predictors, of different block sizes, or at level P
+ * (HSZp-nd and HSZx-nd: Section V-C's stage-2 divergence and curl, each
+ * component's derivative taken by its stage-2 path -- Eq. derivative_Dp for
+ * HSZp-nd, the box-border form for HSZx-nd -- then added): each component's
+ * integer derivative numerators are formed in turn in the workspace, summed
+ * exactly, and scaled as above (the same values as the fused kernel).  Then
+ * ws_bytes >= hc_vector_workspace_bytes(comps, ncomp) (the largest
+ * component workspace + 16 bytes per element); otherwise hc_workspace_bytes()
+ * suffices. */
+HC_API size_t hc_vector_workspace_bytes(const hc_stage* comps, int ncomp);
 HC_API int hc_op_divergence(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out,
                             int out_dtype, void* d_ws, size_t ws_bytes, void* stream);
 HC_API int hc_op_curl(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out, int out_dtype,

@@ -582,22 +582,36 @@ static int vector_op(const hc_stage* comps, int ncomp, int ndim, const int64_t* 
   if (out_dtype != HC_F32 && out_dtype != HC_F64 && out_dtype != HC_I64) return fail(HC_ERR_INVALID_ARG, "out_dtype");
   const hc_header* hs[3];
   const void* ds[3];
+  const int level = comps[0].level;
+  bool fused = level == HC_STAGE_Q;  // 1-D block streams of one block size at stage Q: one fused kernel
   for (int c = 0; c < ncomp; ++c) {
     const hc_stage& in = comps[c];
     if (in.kind != HC_STAGE_COMPRESSED || !in.hdr)
       return fail(HC_ERR_UNSUPPORTED, "vector operations take compressed streams");
-    if (in.level != HC_STAGE_Q)
-      return fail(HC_ERR_UNSUPPORTED, "vector operations on a 1-D block partition run at stage Q (Section V-C)");
-    if (in.hdr->pred >= HC_PRED_LORENZO)
-      return fail(HC_ERR_UNSUPPORTED, "vector operations take block-coded streams: decompress global ones to stage Q");
+    if (in.level != level) return fail(HC_ERR_INVALID_ARG, "every component at the same level");
+    if (level != HC_STAGE_P && level != HC_STAGE_Q)
+      return fail(HC_ERR_UNSUPPORTED, "vector operations run at stage P or Q (Section V-C)");
     int64_t dims3[3];
     int rc = check_op(&in, in.hdr->eps, ndim, dims, d_ws, ws_bytes, dims3);
     if (rc) return rc;
-    if (in.hdr->S != comps[0].hdr->S) return fail(HC_ERR_UNSUPPORTED, "components must share the block size");
+    if (in.hdr->pred >= HC_PRED_LORENZO || in.hdr->S != comps[0].hdr->S) fused = false;
     hs[c] = in.hdr;
     ds[c] = in.d_data;
   }
-  return vector_stream_impl(hs, ds, ncomp, op, d_out, out_dtype, d_ws, as_stream(stream));
+  if (fused) return vector_stream_impl(hs, ds, ncomp, op, d_out, out_dtype, d_ws, as_stream(stream));
+  return vector_any_impl(hs, ds, ncomp, op, level, d_out, out_dtype, d_ws, ws_bytes, as_stream(stream));
+}
+
+size_t hc_vector_workspace_bytes(const hc_stage* comps, int ncomp) {
+  if (!comps || ncomp < 1 || ncomp > 3) return 0;
+  const hc_header* hs[3];
+  bool fused = comps[0].level == HC_STAGE_Q;
+  for (int c = 0; c < ncomp; ++c) {
+    if (comps[c].kind != HC_STAGE_COMPRESSED || !comps[c].hdr) return 0;
+    hs[c] = comps[c].hdr;
+    if (hs[c]->pred >= HC_PRED_LORENZO || hs[c]->S != hs[0]->S || comps[c].level != HC_STAGE_Q) fused = false;
+  }
+  return fused ? kOpWsBytes : vector_any_workspace_bytes(hs, ncomp);
 }
 
 int hc_op_divergence(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, void* d_out, int out_dtype,

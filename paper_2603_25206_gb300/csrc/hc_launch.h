@@ -125,6 +125,11 @@ int stencil_multi_impl(const hc_header* h, const void* d_stream, void* const der
 // Divergence (op 0) or 2-D curl (op 1) of nc component streams (hc_vector.cu).
 int vector_stream_impl(const hc_header* const* hs, const void* const* streams, int nc, int op, void* d_out,
                        int out_dtype, void* d_ws, cudaStream_t st);
+// The same on streams of any predictor and at stage 2 or 3, component by
+// component (each component's own derivative path, exact integer sums).
+size_t vector_any_workspace_bytes(const hc_header* const* hs, int nc);
+int vector_any_impl(const hc_header* const* hs, const void* const* streams, int nc, int op, int level, void* d_out,
+                    int out_dtype, void* d_ws, size_t ws_bytes, cudaStream_t st);
 // Shape the fused stencils walk: a 2-D field (1, n1, n2) is walked as (n1, 1, n2).
 void stencil_walk_dims(const hc_header* h, int64_t d3[3], int* axis3);
 // Time the pipelined kernel's tile heights for this field/op and cache the best.

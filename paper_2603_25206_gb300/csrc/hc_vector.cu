@@ -184,6 +184,113 @@ int launch_vector_s(const VArgs& va, const Geo& g, int smem, void* d_out, int* e
 
 }  // namespace
 
+namespace {
+
+// acc (first component: =) += sign * T, integer numerators (one eps)
+__global__ void __launch_bounds__(kThreads) k_vec_acc(const long long* __restrict__ T, long long* __restrict__ acc,
+                                                       int64_t n, int sign, int first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc[i] = (first ? 0ll : acc[i]) + sign * T[i];
+}
+
+// accd = accd + (sign * T) * eps_c in double, in component order (several eps)
+__global__ void __launch_bounds__(kThreads) k_vec_acc_d(const long long* __restrict__ T, double* __restrict__ accd,
+                                                         int64_t n, int sign, double eps, int first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    accd[i] = __dadd_rn(first ? 0.0 : accd[i], __dmul_rn(__ll2double_rn(sign * T[i]), eps));
+}
+
+// the scaled output: num * eps (one eps), or the double sum (several)
+template <int OUT>
+__global__ void __launch_bounds__(kThreads) k_vec_emit(const long long* __restrict__ acc, int64_t n, double eps,
+                                                        int same_eps, typename OutType<OUT>::T* __restrict__ out) {
+  const double* accd = reinterpret_cast<const double*>(acc);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (OUT == HC_I64) {
+      out[i] = acc[i];
+    } else if (same_eps) {
+      if constexpr (OUT == HC_F32)
+        out[i] = __fmul_rn(__ll2float_rn(acc[i]), (float)eps);
+      else
+        out[i] = __dmul_rn(__ll2double_rn(acc[i]), eps);
+    } else {
+      out[i] = (typename OutType<OUT>::T)accd[i];
+    }
+  }
+}
+
+unsigned vec_grid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), (int64_t)device_sms() * 16));
+}
+
+// derivative numerators of one component along internal axis axis3, at
+// `level`, by its own predictor's path, into T (int64)
+int component_derivative(const hc_header* h, const void* d_stream, int level, int axis3, long long* T, void* d_ws,
+                         size_t ws_bytes, cudaStream_t st) {
+  if (h->pred == HC_PRED_MEAN_ND)
+    return xnd_stencil_impl(h, d_stream, level, ST_DERIV, axis3, T, HC_I64, d_ws, ws_bytes, st);
+  if (h->pred >= HC_PRED_LORENZO)
+    return global_stencil_impl(h, d_stream, level, ST_DERIV, axis3, T, HC_I64, d_ws, ws_bytes, st);
+  if (level != HC_STAGE_Q)
+    return fail(HC_ERR_UNSUPPORTED, "stage-2 differentiation is not defined for a 1-D block partition (Section V-B)");
+  return stencil_stream_impl(h, d_stream, ST_DERIV, axis3, T, HC_I64, d_ws, st);
+}
+
+}  // namespace
+
+size_t vector_any_workspace_bytes(const hc_header* const* hs, int nc) {
+  size_t w = kOpWsBytes;
+  for (int c = 0; c < nc; ++c) w = std::max(w, hc_workspace_bytes_for(hs[c]));
+  return ((w + 15) & ~(size_t)15) + 16 * (size_t)hs[0]->N;
+}
+
+// Divergence / curl on streams of any predictor, component by component:
+// each component's derivative numerators (its predictor's stage-2 or stage-3
+// path) are summed exactly, then scaled as the fused kernel scales them.
+int vector_any_impl(const hc_header* const* hs, const void* const* streams, int nc, int op, int level, void* d_out,
+                    int out_dtype, void* d_ws, size_t ws_bytes, cudaStream_t st) {
+  if (ws_bytes < vector_any_workspace_bytes(hs, nc))
+    return fail(HC_ERR_NOMEM, "workspace smaller than hc_vector_workspace_bytes");
+  size_t wsp = kOpWsBytes;
+  for (int c = 0; c < nc; ++c) wsp = std::max(wsp, hc_workspace_bytes_for(hs[c]));
+  wsp = (wsp + 15) & ~(size_t)15;
+  const int64_t n = hs[0]->N;
+  long long* T = reinterpret_cast<long long*>(reinterpret_cast<char*>(d_ws) + wsp);
+  long long* acc = T + n;
+  int same_eps = 1;
+  for (int c = 1; c < nc; ++c) same_eps &= hs[c]->eps == hs[0]->eps;
+  if (out_dtype == HC_I64 && !same_eps)
+    return fail(HC_ERR_UNSUPPORTED, "an integer numerator needs one eps for every component");
+  const int ndim = hs[0]->ndim;
+  for (int c = 0; c < nc; ++c) {
+    // divergence: component c along user axis c; curl: u along j, v along i (minus)
+    const int user_axis = op == VEC_DIV ? c : (c == 0 ? 1 : 0);
+    const int sign = (op == VEC_CURL && c == 1) ? -1 : 1;
+    int rc = component_derivative(hs[c], streams[c], level, user_axis + 3 - ndim, T, d_ws, wsp, st);
+    if (rc) return rc;
+    if (same_eps)
+      k_vec_acc<<<vec_grid(n), kThreads, 0, st>>>(T, acc, n, sign, c == 0);
+    else
+      k_vec_acc_d<<<vec_grid(n), kThreads, 0, st>>>(T, reinterpret_cast<double*>(acc), n, sign, hs[c]->eps, c == 0);
+    if ((rc = check_launch("vector operation (sum)"))) return rc;
+  }
+  switch (out_dtype) {
+    case HC_F32:
+      k_vec_emit<HC_F32><<<vec_grid(n), kThreads, 0, st>>>(acc, n, hs[0]->eps, same_eps, reinterpret_cast<float*>(d_out));
+      break;
+    case HC_F64:
+      k_vec_emit<HC_F64><<<vec_grid(n), kThreads, 0, st>>>(acc, n, hs[0]->eps, same_eps, reinterpret_cast<double*>(d_out));
+      break;
+    case HC_I64:
+      k_vec_emit<HC_I64><<<vec_grid(n), kThreads, 0, st>>>(acc, n, hs[0]->eps, same_eps,
+                                                           reinterpret_cast<long long*>(d_out));
+      break;
+    default:
+      return fail(HC_ERR_INVALID_ARG, "out_dtype");
+  }
+  return check_launch("vector operation (scale)");
+}
+
 // comps: nc stream headers and device streams of the same shape and block
 // size; op 0 divergence, 1 curl (2-D, two components).
 int vector_stream_impl(const hc_header* const* hs, const void* const* streams, int nc, int op, void* d_out,

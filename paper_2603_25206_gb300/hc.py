@@ -44,7 +44,7 @@ ABI_FUNCTIONS = (
     "hc_batch_plan_bytes", "hc_batch_workspace_bytes", "hc_batch_plan", "hc_batch_run", "hc_batch_graph_create",
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
     "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for", "hc_compress_bound_nd",
-    "hc_compress_workspace_bytes_nd", "hc_compress_nd", "hc_compress_codes_nd",
+    "hc_compress_workspace_bytes_nd", "hc_compress_nd", "hc_compress_codes_nd", "hc_vector_workspace_bytes",
 )
 HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA, HC_PRED_MEAN_ND = 0, 1, 2, 3, 4
 # "delta": HSZp with block heads; "mean": HSZx; "lorenzo": HSZp-nd (Lorenzo over
@@ -131,6 +131,7 @@ def lib():
             "hc_workspace_bytes": ([], sz),
             "hc_workspace_bytes_for": ([P(HcHeader)], sz),
             "hc_compress_bound_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
+            "hc_vector_workspace_bytes": ([P(HcStage), i32], sz),
             "hc_compress_workspace_bytes_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
             "hc_compress_nd": ([vp, i32, i32, P(ctypes.c_int64), P(ctypes.c_int32), dbl, i32, vp, sz, vp, sz, P(sz),
                                 P(HcHeader), vp], i32),
@@ -524,29 +525,31 @@ def multi(inp, derivative=True, gradmag=True, laplacian=True, stats=True, out_dt
     return outs
 
 
-def _vector(fn, comps, out_dtype, out, stream):
+def _vector(fn, comps, out_dtype, out, stream, level="q"):
     torch = _torch()
     arr = (HcStage * len(comps))()
     for k, c in enumerate(comps):
-        arr[k] = c.stage("q")
+        arr[k] = c.stage(level)
     shape = comps[0].shape
     dev = comps[0].stream.device
     out = _field_out(shape, out_dtype, dev, out)
-    ws = workspace(dev, stream)
+    ws = workspace(dev, stream, int(lib().hc_vector_workspace_bytes(arr, len(comps))))
     _check(getattr(lib(), fn)(arr, len(comps), len(shape), _dims(shape), ctypes.c_void_p(out.data_ptr()),
                               _OUT[out_dtype], ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return out
 
 
-def divergence(comps, out_dtype: str = "float32", out=None, stream=None):
+def divergence(comps, out_dtype: str = "float32", out=None, stream=None, level: str = "q"):
     """Divergence of the vector field whose components are the compressed
-    fields `comps` (one per axis, same shape and block size)."""
-    return _vector("hc_op_divergence", comps, out_dtype, out, stream)
+    fields `comps` (one per axis, same shape); level "p" for HSZp-nd and
+    HSZx-nd components (Section V-C's stage-2 form)."""
+    return _vector("hc_op_divergence", comps, out_dtype, out, stream, level)
 
 
-def curl(comps, out_dtype: str = "float32", out=None, stream=None):
-    """Curl of a 2-D vector field (u, v) given as two compressed fields."""
-    return _vector("hc_op_curl", comps, out_dtype, out, stream)
+def curl(comps, out_dtype: str = "float32", out=None, stream=None, level: str = "q"):
+    """Curl of a 2-D vector field (u, v) given as two compressed fields;
+    level "p" for HSZp-nd and HSZx-nd components."""
+    return _vector("hc_op_curl", comps, out_dtype, out, stream, level)
 
 
 def workspace_status(stream=None) -> int:

@@ -148,8 +148,9 @@ def test_global_stream_stencils(env, orc, pred, name, x, eb, rel, S):
 def test_global_refusals(env, orc):
     """What the global predictors do not offer is refused, nothing runs: stage
     1, the stage-2 gradient magnitude, stage-2 differentiation of HSZp (a 1-D
-    partition), D_p arrays, vector operations, the batch, the allocation-free
-    variance, and a workspace smaller than hc_workspace_bytes_for."""
+    partition, also inside a divergence), D_p arrays, the batch, the
+    allocation-free variance, and a workspace smaller than
+    hc_workspace_bytes_for."""
     import ctypes
 
     import synth
@@ -161,7 +162,7 @@ def test_global_refusals(env, orc):
     U = hc.HC_ERR_UNSUPPORTED
     for fn in (lambda: hc.gradmag(cl, level="p"), lambda: hc.derivative(cg, 0, level="p"),
                lambda: hc.laplacian(cg, level="p"), lambda: hc.mean(cl, level="m"),
-               lambda: hc.variance_noalloc(cl), lambda: hc.divergence([cl, cl, cl]),
+               lambda: hc.variance_noalloc(cl), lambda: hc.divergence([cg, cg, cg], level="p"),
                lambda: hc.mean(hc.as_stage(cl, "p", hc.decompress(cl, "p")))):
         with pytest.raises(hc.HcError) as e:
             fn()
