@@ -638,12 +638,13 @@ def run_ours(args):
         # both ways must deliver the same bytes to the host
         same = all(torch.equal(a_, b_) for hs_a, hs_b in zip(copied, host_out) for a_, b_ in zip(hs_a, hs_b))
     except hc.HcError:  # a host buffer the library does not accept (alignment): copies only
-        direct_ms, same = float("inf"), False
+        direct_ms, same = None, False
     del copied
     e2e_ms = min(copy_ms, direct_ms) if same else copy_ms
+    direct_won = same and direct_ms < copy_ms
     e2e = {"value": weak_value(bytes_step, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": comp_bytes,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-           "mode": "kernel writes to pinned host memory" if (same and direct_ms < copy_ms)
+           "mode": "kernel writes to pinned host memory" if direct_won
            else "device outputs copied back on four copy streams",
            "copy_engines_ms_per_step": copy_ms, "direct_host_write_ms_per_step": direct_ms,
            "direct_equals_copied": same}
