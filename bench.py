@@ -1129,6 +1129,36 @@ def run_profile_boxes():
     return 0
 
 
+def run_hbm_probe():
+    """Context for the roofline: HBM write, read and copy bandwidth of plain
+    torch operations (fill, sum, copy) on a 4 GiB float32 buffer, CUDA-event
+    time over 10 repetitions after 3 warm-ups.  Not a roofline denominator
+    (that stays MEASURED_PEAKS.json's copy bandwidth)."""
+    import torch
+
+    n = 1 << 30
+    x = torch.empty(n, dtype=torch.float32, device="cuda")
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+
+    def t(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    w, r, c = t(lambda: x.fill_(1.0)), t(lambda: x.sum()), t(lambda: y.copy_(x))
+    print(json.dumps({"hbm_probe": {"write_gbs": round(4 * n / w / 1e6, 1), "read_gbs": round(4 * n / r / 1e6, 1),
+                                    "copy_gbs": round(8 * n / c / 1e6, 1), "buffer_bytes": 4 * n}}))
+    return 0
+
+
 def run_profile_lorenzo():
     """Small case for ncu captures of the global-predictor kernels: one
     256x384x384 float32 field as HSZp-nd (compressed ~40 MB, D_q 151 MB), the
@@ -1302,6 +1332,7 @@ def main(argv=None):
     ap.add_argument("--profile-lorenzo", action="store_true", help="run the small global-predictor ncu case")
     ap.add_argument("--boxes", action="store_true", help="HSZx-nd (box means) on the paper-like workload")
     ap.add_argument("--profile-boxes", action="store_true", help="run the small HSZx-nd ncu case")
+    ap.add_argument("--hbm-probe", action="store_true", help="HBM write/read/copy bandwidth of plain torch ops")
     ap.add_argument("--fields", type=int, default=200)
     ap.add_argument("--qps", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=30.0)
@@ -1324,6 +1355,8 @@ def main(argv=None):
         return run_boxes(args)
     if args.profile_boxes:
         return run_profile_boxes()
+    if args.hbm_probe:
+        return run_hbm_probe()
     if args.batched:
         if args.warmup < 3:
             args.warmup = 3

@@ -254,62 +254,65 @@ __global__ void __launch_bounds__(kThreads) k_stats_box(DevStream s, BoxGeo bg, 
 // axis, D = W[hi] - W[lo] + (M[box hi] - M[box lo] when the two neighbours
 // lie in different boxes), one-sided and doubled at a domain edge, 0 on an
 // axis of length 1; the Laplacian adds, per existing neighbour,
-// W[nb] - W[c] + (M[box nb] - M[box c] across a box border).  A CTA takes a
-// run of kThreads points of one row: the box coordinates of the row are
-// formed once, and a neighbour crosses into the next box along an axis only
-// from the box's first or last layer, so no neighbour needs a division.
+// W[nb] - W[c] + (M[box nb] - M[box c] across a box border).  A CTA walks
+// whole rows (its threads along x): the row's box coordinates are formed once
+// per row, the box along x by a shift when its extent is a power of two, and
+// a neighbour crosses into the next box only from a box's first or last
+// layer, so no neighbour needs a division.
 template <int OP, int OUT>
 __global__ void __launch_bounds__(kThreads) k_box_stencil(const int32_t* __restrict__ W, const int32_t* __restrict__ M,
-                                                           BoxGeo bg, Geo g, typename OutType<OUT>::T* __restrict__ out) {
+                                                           BoxGeo bg, Geo g, int xshift,
+                                                           typename OutType<OUT>::T* __restrict__ out) {
   const int64_t rows = bg.n[0] * bg.n[1];
   const int n2 = (int)bg.n[2];
-  const int64_t nxc = (n2 + kThreads - 1) / kThreads;
   const int64_t st[3] = {bg.n[1] * bg.n[2], bg.n[2], 1};   // element strides
   const int64_t gs[3] = {bg.g[1] * bg.g[2], bg.g[2], 1};   // box-index strides
-  for (int64_t t = blockIdx.x; t < rows * nxc; t += gridDim.x) {
-    const int64_t row = t / nxc;
-    const int x = (int)(t - row * nxc) * kThreads + threadIdx.x;
-    if (x >= n2) continue;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
     const int64_t z = row / bg.n[1], y = row - z * bg.n[1];
     const int64_t kz = z / bg.b[0], ky = y / bg.b[1];
-    const int kx = x / bg.b[2];
-    const int64_t c[3] = {z, y, x};
-    const int r[3] = {(int)(z - kz * bg.b[0]), (int)(y - ky * bg.b[1]), x - kx * bg.b[2]};
-    const int64_t bc = kz * gs[0] + ky * gs[1] + kx;
-    const int64_t i = row * n2 + x;
-    if constexpr (OP == ST_LAPLACIAN) {
-      const long long wc = __ldg(W + i), mc = __ldg(M + bc);
-      long long v = 0;
+    const int rz = (int)(z - kz * bg.b[0]), ry = (int)(y - ky * bg.b[1]);
+    const int64_t brow = kz * gs[0] + ky * gs[1];
+    const int64_t i0 = row * n2;
+    for (int x = threadIdx.x; x < n2; x += blockDim.x) {
+      const int kx = xshift >= 0 ? (x >> xshift) : x / bg.b[2];
+      const int64_t c[3] = {z, y, x};
+      const int r[3] = {rz, ry, x - kx * bg.b[2]};
+      const int64_t bc = brow + kx;
+      const int64_t i = i0 + x;
+      if constexpr (OP == ST_LAPLACIAN) {
+        const long long wc = __ldg(W + i), mc = __ldg(M + bc);
+        long long v = 0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (c[a] > 0) {  // lower neighbour (a missing one replicates the edge: term 0)
-          v += (long long)__ldg(W + i - st[a]) - wc;
-          if (r[a] == 0) v += (long long)__ldg(M + bc - gs[a]) - mc;
+        for (int a = 0; a < 3; ++a) {
+          if (c[a] > 0) {  // lower neighbour (a missing one replicates the edge: term 0)
+            v += (long long)__ldg(W + i - st[a]) - wc;
+            if (r[a] == 0) v += (long long)__ldg(M + bc - gs[a]) - mc;
+          }
+          if (c[a] + 1 < bg.n[a]) {
+            v += (long long)__ldg(W + i + st[a]) - wc;
+            if (r[a] == bg.b[a] - 1) v += (long long)__ldg(M + bc + gs[a]) - mc;
+          }
         }
-        if (c[a] + 1 < bg.n[a]) {
-          v += (long long)__ldg(W + i + st[a]) - wc;
-          if (r[a] == bg.b[a] - 1) v += (long long)__ldg(M + bc + gs[a]) - mc;
-        }
-      }
-      out[i] = emit<OP, OUT>(v, 0, 0, g);
-    } else {
-      long long d[3] = {0, 0, 0};
+        out[i] = emit<OP, OUT>(v, 0, 0, g);
+      } else {
+        long long d[3] = {0, 0, 0};
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (OP == ST_DERIV && a != g.axis) continue;
-        const int64_t len = bg.n[a], k = c[a];
-        if (len == 1) continue;
-        const bool lo_step = k > 0, hi_step = k + 1 < len;  // one-sided at an edge
-        long long v = (long long)__ldg(W + i + (hi_step ? st[a] : 0)) - __ldg(W + i - (lo_step ? st[a] : 0));
-        const bool lo_cross = lo_step && r[a] == 0, hi_cross = hi_step && r[a] == bg.b[a] - 1;
-        if (lo_cross || hi_cross)
-          v += (long long)__ldg(M + bc + (hi_cross ? gs[a] : 0)) - __ldg(M + bc - (lo_cross ? gs[a] : 0));
-        d[a] = (lo_step && hi_step) ? v : 2 * v;
+        for (int a = 0; a < 3; ++a) {
+          if (OP == ST_DERIV && a != g.axis) continue;
+          const int64_t len = bg.n[a], k = c[a];
+          if (len == 1) continue;
+          const bool lo_step = k > 0, hi_step = k + 1 < len;  // one-sided at an edge
+          long long v = (long long)__ldg(W + i + (hi_step ? st[a] : 0)) - __ldg(W + i - (lo_step ? st[a] : 0));
+          const bool lo_cross = lo_step && r[a] == 0, hi_cross = hi_step && r[a] == bg.b[a] - 1;
+          if (lo_cross || hi_cross)
+            v += (long long)__ldg(M + bc + (hi_cross ? gs[a] : 0)) - __ldg(M + bc - (lo_cross ? gs[a] : 0));
+          d[a] = (lo_step && hi_step) ? v : 2 * v;
+        }
+        if constexpr (OP == ST_DERIV)
+          out[i] = emit<OP, OUT>(d[g.axis], 0, 0, g);
+        else
+          out[i] = emit<OP, OUT>(d[0], d[1], d[2], g);
       }
-      if constexpr (OP == ST_DERIV)
-        out[i] = emit<OP, OUT>(d[g.axis], 0, 0, g);
-      else
-        out[i] = emit<OP, OUT>(d[0], d[1], d[2], g);
     }
   }
 }
@@ -379,27 +382,26 @@ int launch_mean_m_box(const hc_header* h, const void* d_stream, hc_scalar* d_out
   return check_launch("mean (stage 1, boxes)");
 }
 
-unsigned elem_grid(int64_t n) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), (int64_t)device_sms() * 16));
-}
-
 template <int OP>
 int launch_box_stencil(const hc_header* h, const int32_t* W, const int32_t* M, int axis3, void* d_out, int out_dtype,
                        cudaStream_t st) {
   const Geo g = stencil_base_geo(h->dims, h->eps, axis3);
   const BoxGeo bg = box_geo(h);
   if (h->dims[2] > 0x7fffffff) return fail(HC_ERR_UNSUPPORTED, "rows longer than 2^31 codes");
+  const int xshift = (bg.b[2] & (bg.b[2] - 1)) == 0 ? __builtin_ctz((unsigned)bg.b[2]) : -1;
+  const unsigned grid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(bg.n[0] * bg.n[1], (int64_t)device_sms() * 16));
   switch (out_dtype) {
     case HC_F32:
-      k_box_stencil<OP, HC_F32><<<elem_grid(h->N), kThreads, 0, st>>>(W, M, bg, g, reinterpret_cast<float*>(d_out));
+      k_box_stencil<OP, HC_F32><<<grid, kThreads, 0, st>>>(W, M, bg, g, xshift, reinterpret_cast<float*>(d_out));
       break;
     case HC_F64:
-      k_box_stencil<OP, HC_F64><<<elem_grid(h->N), kThreads, 0, st>>>(W, M, bg, g, reinterpret_cast<double*>(d_out));
+      k_box_stencil<OP, HC_F64><<<grid, kThreads, 0, st>>>(W, M, bg, g, xshift, reinterpret_cast<double*>(d_out));
       break;
     case HC_I64:
       if (OP == ST_GRADMAG) return fail(HC_ERR_UNSUPPORTED, "the gradient magnitude has no integer form");
-      k_box_stencil<OP, HC_I64><<<elem_grid(h->N), kThreads, 0, st>>>(W, M, bg, g,
-                                                                       reinterpret_cast<long long*>(d_out));
+      k_box_stencil<OP, HC_I64><<<grid, kThreads, 0, st>>>(W, M, bg, g, xshift,
+                                                           reinterpret_cast<long long*>(d_out));
       break;
     default:
       return fail(HC_ERR_INVALID_ARG, "out_dtype");
