@@ -265,6 +265,12 @@ __global__ void __launch_bounds__(kThreads) k_global_mean(DevStream s, int64_t L
 }
 
 // ---------------------------------------------- stage-2 stencils on D_p
+// Both kernels walk whole rows (CTA per row, threads along x), so a point's
+// position along the axis is the row's z or y, or x: no division per point.
+__device__ __forceinline__ int64_t axis_pos(int ax, int64_t z, int64_t y, int x) {
+  return ax == 0 ? z : (ax == 1 ? y : (int64_t)x);
+}
+
 // Derivative along internal axis ax from u = prefix sums of D_p over the
 // other axes (u(i) = q(i) - q(i - e_ax) for i_ax > 0, q(i) at i_ax = 0):
 // interior u(i) + u(i + e), first slice 2 u(i + e), last slice 2 u(i), an
@@ -273,22 +279,26 @@ template <int OUT>
 __global__ void __launch_bounds__(kThreads) k_deriv_from_u(const uint32_t* __restrict__ u,
                                                             typename OutType<OUT>::T* __restrict__ out, Geo g,
                                                             int ax) {
-  const int64_t n = g.n0 * g.n1 * g.n2;
+  const int64_t rows = g.n0 * g.n1;
+  const int n2 = (int)g.n2;
   const int64_t len = ax == 0 ? g.n0 : (ax == 1 ? g.n1 : g.n2);
   const int64_t stride = ax == 2 ? 1 : (ax == 1 ? g.n2 : g.n1 * g.n2);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = (i / stride) % len;
-    long long d = 0;
-    if (len > 1) {
-      const long long here = (int32_t)__ldg(u + i);
-      if (k == 0)
-        d = 2ll * (int32_t)__ldg(u + i + stride);
-      else if (k == len - 1)
-        d = 2ll * here;
-      else
-        d = here + (int32_t)__ldg(u + i + stride);
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int64_t z = row / g.n1, y = row - z * g.n1;
+    for (int x = threadIdx.x; x < n2; x += blockDim.x) {
+      const int64_t i = row * n2 + x, k = axis_pos(ax, z, y, x);
+      long long d = 0;
+      if (len > 1) {
+        const long long here = (int32_t)__ldg(u + i);
+        if (k == 0)
+          d = 2ll * (int32_t)__ldg(u + i + stride);
+        else if (k == len - 1)
+          d = 2ll * here;
+        else
+          d = here + (int32_t)__ldg(u + i + stride);
+      }
+      out[i] = emit<ST_DERIV, OUT>(d, 0, 0, g);
     }
-    out[i] = emit<ST_DERIV, OUT>(d, 0, 0, g);
   }
 }
 
@@ -298,18 +308,22 @@ __global__ void __launch_bounds__(kThreads) k_deriv_from_u(const uint32_t* __res
 template <int OUT, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kThreads) k_lap_from_u(const uint32_t* __restrict__ u, long long* __restrict__ acc,
                                                           typename OutType<OUT>::T* __restrict__ out, Geo g, int ax) {
-  const int64_t n = g.n0 * g.n1 * g.n2;
+  const int64_t rows = g.n0 * g.n1;
+  const int n2 = (int)g.n2;
   const int64_t len = ax == 0 ? g.n0 : (ax == 1 ? g.n1 : g.n2);
   const int64_t stride = ax == 2 ? 1 : (ax == 1 ? g.n2 : g.n1 * g.n2);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = (i / stride) % len;
-    long long v = FIRST ? 0ll : acc[i];
-    if (k < len - 1) v += (int32_t)__ldg(u + i + stride);
-    if (k > 0) v -= (int32_t)__ldg(u + i);
-    if (LAST)
-      out[i] = emit<ST_LAPLACIAN, OUT>(v, 0, 0, g);
-    else
-      acc[i] = v;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int64_t z = row / g.n1, y = row - z * g.n1;
+    for (int x = threadIdx.x; x < n2; x += blockDim.x) {
+      const int64_t i = row * n2 + x, k = axis_pos(ax, z, y, x);
+      long long v = FIRST ? 0ll : acc[i];
+      if (k < len - 1) v += (int32_t)__ldg(u + i + stride);
+      if (k > 0) v -= (int32_t)__ldg(u + i);
+      if (LAST)
+        out[i] = emit<ST_LAPLACIAN, OUT>(v, 0, 0, g);
+      else
+        acc[i] = v;
+    }
   }
 }
 
@@ -359,6 +373,11 @@ unsigned elem_grid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), (int64_t)device_sms() * 16));
 }
 
+// one CTA per row (grid-stride), for the row-walking kernels
+unsigned row_grid(const Geo& g) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g.n0 * g.n1, (int64_t)device_sms() * 16));
+}
+
 template <int OUT>
 int stencil_p_typed(const hc_header* h, const void* d_stream, int op, int axis3, void* d_out, const GlobalWs& gw,
                     void* d_ws, cudaStream_t st) {
@@ -369,7 +388,7 @@ int stencil_p_typed(const hc_header* h, const void* d_stream, int op, int axis3,
   int rc;
   if (op == ST_DERIV) {
     if ((rc = partial_sums(h, d_stream, axis3, gw, d_ws, st))) return rc;
-    k_deriv_from_u<OUT><<<elem_grid(n), kThreads, 0, st>>>(gw.W, out, g, axis3);
+    k_deriv_from_u<OUT><<<row_grid(g), kThreads, 0, st>>>(gw.W, out, g, axis3);
     return check_launch("stage-2 derivative");
   }
   // Laplacian: one term per axis longer than 1
@@ -385,13 +404,13 @@ int stencil_p_typed(const hc_header* h, const void* d_stream, int op, int axis3,
     if ((rc = partial_sums(h, d_stream, ax, gw, d_ws, st))) return rc;
     const bool first = k == 0, last = k == na - 1;
     if (first && last)
-      k_lap_from_u<OUT, true, true><<<elem_grid(n), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
+      k_lap_from_u<OUT, true, true><<<row_grid(g), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
     else if (first)
-      k_lap_from_u<OUT, true, false><<<elem_grid(n), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
+      k_lap_from_u<OUT, true, false><<<row_grid(g), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
     else if (last)
-      k_lap_from_u<OUT, false, true><<<elem_grid(n), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
+      k_lap_from_u<OUT, false, true><<<row_grid(g), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
     else
-      k_lap_from_u<OUT, false, false><<<elem_grid(n), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
+      k_lap_from_u<OUT, false, false><<<row_grid(g), kThreads, 0, st>>>(gw.W, gw.acc, out, g, ax);
     if ((rc = check_launch("stage-2 Laplacian"))) return rc;
   }
   return HC_OK;
