@@ -265,8 +265,19 @@ __global__ void __launch_bounds__(kThreads) k_global_mean(DevStream s, int64_t L
 }
 
 // ---------------------------------------------- stage-2 stencils on D_p
-// Both kernels walk whole rows (CTA per row, threads along x), so a point's
-// position along the axis is the row's z or y, or x: no division per point.
+// Both kernels walk whole rows (CTA per row, threads along x): one thread
+// splits the row index into (z, y) and shares it, so a point's position along
+// the axis is the row's z or y, or x, with no division per point.
+__device__ __forceinline__ void row_zy(const Geo& g, int64_t row, long long* s_zy, int64_t& z, int64_t& y) {
+  if (threadIdx.x == 0) {
+    s_zy[0] = row / g.n1;
+    s_zy[1] = row - s_zy[0] * g.n1;
+  }
+  __syncthreads();
+  z = s_zy[0];
+  y = s_zy[1];
+  __syncthreads();
+}
 __device__ __forceinline__ int64_t axis_pos(int ax, int64_t z, int64_t y, int x) {
   return ax == 0 ? z : (ax == 1 ? y : (int64_t)x);
 }
@@ -283,8 +294,10 @@ __global__ void __launch_bounds__(kThreads) k_deriv_from_u(const uint32_t* __res
   const int n2 = (int)g.n2;
   const int64_t len = ax == 0 ? g.n0 : (ax == 1 ? g.n1 : g.n2);
   const int64_t stride = ax == 2 ? 1 : (ax == 1 ? g.n2 : g.n1 * g.n2);
+  __shared__ long long s_zy[2];
   for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int64_t z = row / g.n1, y = row - z * g.n1;
+    int64_t z, y;
+    row_zy(g, row, s_zy, z, y);
     for (int x = threadIdx.x; x < n2; x += blockDim.x) {
       const int64_t i = row * n2 + x, k = axis_pos(ax, z, y, x);
       long long d = 0;
@@ -312,8 +325,10 @@ __global__ void __launch_bounds__(kThreads) k_lap_from_u(const uint32_t* __restr
   const int n2 = (int)g.n2;
   const int64_t len = ax == 0 ? g.n0 : (ax == 1 ? g.n1 : g.n2);
   const int64_t stride = ax == 2 ? 1 : (ax == 1 ? g.n2 : g.n1 * g.n2);
+  __shared__ long long s_zy[2];
   for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int64_t z = row / g.n1, y = row - z * g.n1;
+    int64_t z, y;
+    row_zy(g, row, s_zy, z, y);
     for (int x = threadIdx.x; x < n2; x += blockDim.x) {
       const int64_t i = row * n2 + x, k = axis_pos(ax, z, y, x);
       long long v = FIRST ? 0ll : acc[i];

@@ -255,10 +255,11 @@ __global__ void __launch_bounds__(kThreads) k_stats_box(DevStream s, BoxGeo bg, 
 // lie in different boxes), one-sided and doubled at a domain edge, 0 on an
 // axis of length 1; the Laplacian adds, per existing neighbour,
 // W[nb] - W[c] + (M[box nb] - M[box c] across a box border).  A CTA walks
-// whole rows (its threads along x): the row's box coordinates are formed once
-// per row, the box along x by a shift when its extent is a power of two, and
-// a neighbour crosses into the next box only from a box's first or last
-// layer, so no neighbour needs a division.
+// whole rows (its threads along x): one thread forms the row's coordinates and
+// box coordinates once per row and shares them, the box along x comes from a
+// shift when its extent is a power of two, and a neighbour crosses into the
+// next box only from a box's first or last layer, so no neighbour needs a
+// division.
 template <int OP, int OUT>
 __global__ void __launch_bounds__(kThreads) k_box_stencil(const int32_t* __restrict__ W, const int32_t* __restrict__ M,
                                                            BoxGeo bg, Geo g, int xshift,
@@ -267,11 +268,20 @@ __global__ void __launch_bounds__(kThreads) k_box_stencil(const int32_t* __restr
   const int n2 = (int)bg.n[2];
   const int64_t st[3] = {bg.n[1] * bg.n[2], bg.n[2], 1};   // element strides
   const int64_t gs[3] = {bg.g[1] * bg.g[2], bg.g[2], 1};   // box-index strides
+  __shared__ long long s_row[4];  // z, y, box index of x = 0, (ry << 32) | rz
   for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int64_t z = row / bg.n[1], y = row - z * bg.n[1];
-    const int64_t kz = z / bg.b[0], ky = y / bg.b[1];
-    const int rz = (int)(z - kz * bg.b[0]), ry = (int)(y - ky * bg.b[1]);
-    const int64_t brow = kz * gs[0] + ky * gs[1];
+    if (threadIdx.x == 0) {
+      const int64_t zz = row / bg.n[1], yy = row - zz * bg.n[1];
+      const int64_t kz = zz / bg.b[0], ky = yy / bg.b[1];
+      s_row[0] = zz;
+      s_row[1] = yy;
+      s_row[2] = kz * gs[0] + ky * gs[1];
+      s_row[3] = ((long long)(yy - ky * bg.b[1]) << 32) | (long long)(zz - kz * bg.b[0]);
+    }
+    __syncthreads();
+    const int64_t z = s_row[0], y = s_row[1], brow = s_row[2];
+    const int rz = (int)(s_row[3] & 0xffffffffll), ry = (int)(s_row[3] >> 32);
+    __syncthreads();  // every thread has read the row before thread 0 moves on
     const int64_t i0 = row * n2;
     for (int x = threadIdx.x; x < n2; x += blockDim.x) {
       const int kx = xshift >= 0 ? (x >> xshift) : x / bg.b[2];
