@@ -226,3 +226,26 @@ def test_global_paper_size_field(env, orc):
     num, _ = orc.stencil_at(q, orc.KIND_LAPLACIAN, eps, idx)
     np.testing.assert_array_equal(lap.cpu().numpy(), num)
     assert hc.workspace_status() == 0
+
+
+@pytest.mark.parametrize("pred", [LORENZO, GLOBAL])
+def test_global_corrupt_stream_reported_not_faulting(env, orc, pred):
+    """A width byte above the header's max width in a global-predictor stream:
+    the residual decoder and the fused stage-2 mean flag the tile and skip it
+    (every read stays inside the stream); the status comes back on the host."""
+    import synth
+
+    hc, torch, dev = env
+    x = synth.grf_field((16, 16, 64), 4)
+    ref, eps = orc.compress(x, 1e-3, True, 32, pred=pred)
+    bad = ref.copy()
+    bad[256 + 100] = 31
+    c = hc.from_stream(torch.from_numpy(bad).to(dev))
+    assert hc.parse_scalar(hc.mean(c, level="p"))["status"] == hc.HC_ERR_CORRUPT
+    assert hc.workspace_status() == hc.HC_ERR_CORRUPT
+    hc.decompress(c, "q")
+    assert hc.workspace_status() == hc.HC_ERR_CORRUPT
+    if pred == LORENZO:
+        hc.laplacian(c, level="p")
+        assert hc.workspace_status() == hc.HC_ERR_CORRUPT
+    assert hc.workspace_status() == 0

@@ -179,3 +179,24 @@ def test_box_paper_size_field(env, orc):
     num, _ = orc.stencil_at(q, orc.KIND_LAPLACIAN, eps, idx)
     np.testing.assert_array_equal(got, num)
     assert hc.workspace_status() == 0
+
+
+def test_box_corrupt_stream_reported_not_faulting(env, orc):
+    """A width byte above the header's max width in a box stream: the box
+    decoder and the statistics flag the tile and skip it; the status comes
+    back on the host."""
+    import synth
+
+    hc, torch, dev = env
+    x = synth.grf_field((16, 16, 64), 4)
+    ref, eps = orc.compress_nd(x, (4, 4, 4), 1e-3, True)
+    bad = ref.copy()
+    bad[256 + 100] = 31
+    c = hc.from_stream(torch.from_numpy(bad).to(dev))
+    assert hc.parse_scalar(hc.variance(c, level="q"))["status"] == hc.HC_ERR_CORRUPT
+    assert hc.workspace_status() == hc.HC_ERR_CORRUPT
+    hc.decompress(c, "q")
+    assert hc.workspace_status() == hc.HC_ERR_CORRUPT
+    hc.laplacian(c, level="p")
+    assert hc.workspace_status() == hc.HC_ERR_CORRUPT
+    assert hc.workspace_status() == 0
