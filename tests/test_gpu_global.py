@@ -241,8 +241,8 @@ def test_global_corrupt_stream_reported_not_faulting(env, orc, pred):
     bad = ref.copy()
     bad[256 + 100] = 31
     c = hc.from_stream(torch.from_numpy(bad).to(dev))
+    # a statistic reports in its result; decoders in the workspace status word
     assert hc.parse_scalar(hc.mean(c, level="p"))["status"] == hc.HC_ERR_CORRUPT
-    assert hc.workspace_status() == hc.HC_ERR_CORRUPT
     hc.decompress(c, "q")
     assert hc.workspace_status() == hc.HC_ERR_CORRUPT
     if pred == LORENZO:

@@ -193,8 +193,8 @@ def test_box_corrupt_stream_reported_not_faulting(env, orc):
     bad = ref.copy()
     bad[256 + 100] = 31
     c = hc.from_stream(torch.from_numpy(bad).to(dev))
+    # a statistic reports in its result; decoders in the workspace status word
     assert hc.parse_scalar(hc.variance(c, level="q"))["status"] == hc.HC_ERR_CORRUPT
-    assert hc.workspace_status() == hc.HC_ERR_CORRUPT
     hc.decompress(c, "q")
     assert hc.workspace_status() == hc.HC_ERR_CORRUPT
     hc.laplacian(c, level="p")
