@@ -14,10 +14,10 @@
 //                      u(i+e_a) - u(i) accumulated (Eq. laplacian_Dp)
 //   stages 3 and 4     D_q rebuilt by prefix sums along every axis
 //
-// The prefix sums are a chunked scan along one axis of an array seen as
-// (A, L, B): element (a, l, b) at (a L + l) B + b, chunks of kScanChunk along
-// l, the chunk totals scanned by the same routine (recursion), then each
-// chunk rescanned from its carry.  No kernel waits on another CTA.  The
+// The prefix sums run along one axis of an array seen as (A, L, B): element
+// (a, l, b) at (a L + l) B + b -- one pass per column or per row where the
+// shape allows, else chunk totals scanned by the same routine (recursion)
+// and each chunk rescanned from its carry.  No kernel waits on another CTA.  The
 // arithmetic is unsigned (wrapping): every value a caller reads back -- a
 // code, a difference of codes -- fits 32 bits, and a wrapping sum of exact
 // terms is exact modulo 2^32 whatever the intermediate sums are.
@@ -54,16 +54,77 @@ unsigned scan_grid(int64_t threads) {
 }
 
 // ------------------------------------------------------------------ scans
-// axis of length <= kScanChunk: one thread per (a, b) walks l
-__global__ void __launch_bounds__(kThreads) k_scan_short(uint32_t* x, int64_t A, int L, int64_t B) {
+// Plans, by the shape (A, L, B) of the scan:
+//   L <= 32, or B > 1 with many columns: one thread per column (a, b) walks
+//     l, loads coalesced across b -- one pass;
+//   B == 1 (rows): one warp per chunk of 1024 codes of a row, coalesced
+//     loads and a warp-shuffle scan; a row of up to 1024 codes is one pass,
+//     longer rows first sum their chunks (then the same scan on the totals);
+//   otherwise (few long columns): chunks of 32 along l, totals, recursion,
+//     rescan from the carries.
+constexpr int kRowChunk = 1024;
+constexpr int64_t kColumnThreads = 152 * 256;
+enum { SCAN_NONE, SCAN_COLUMN, SCAN_ROWS, SCAN_CHUNKED };
+
+int scan_mode(int64_t A, int64_t L, int64_t B) {
+  if (L <= 1 || A * B == 0) return SCAN_NONE;
+  if (B == 1) return L <= kScanChunk ? SCAN_COLUMN : SCAN_ROWS;
+  if (L <= kScanChunk || A * B >= kColumnThreads) return SCAN_COLUMN;
+  return SCAN_CHUNKED;
+}
+
+// one thread per column (a, b) walks l
+__global__ void __launch_bounds__(kThreads) k_scan_column(uint32_t* x, int64_t A, int64_t L, int64_t B) {
   const int64_t n = A * B;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = t / B, b = t - a * B;
     uint32_t* p = x + a * L * B + b;
     uint32_t run = 0;
-    for (int l = 0; l < L; ++l) {
+    for (int64_t l = 0; l < L; ++l) {
       run += p[l * B];
       p[l * B] = run;
+    }
+  }
+}
+
+// rows: totals of the 1024-code chunks, one warp per chunk
+__global__ void __launch_bounds__(kThreads) k_row_sums(const uint32_t* __restrict__ x, uint32_t* __restrict__ cs,
+                                                        int64_t A, int64_t L, int64_t nc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < A * nc; t += nw) {
+    const int64_t a = t / nc, c = t - a * nc;
+    const uint32_t* p = x + a * L + c * kRowChunk;
+    const int len = (int)min((int64_t)kRowChunk, L - c * kRowChunk);
+    uint32_t v = 0;
+    for (int l = lane; l < len; l += 32) v += __ldg(p + l);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) cs[t] = v;
+  }
+}
+
+// rows: each chunk scanned 32 codes at a time with warp shuffles, from the
+// inclusive total of the chunks before it (cs NULL: one chunk per row)
+__global__ void __launch_bounds__(kThreads) k_row_apply(uint32_t* __restrict__ x, const uint32_t* __restrict__ cs,
+                                                         int64_t A, int64_t L, int64_t nc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < A * nc; t += nw) {
+    const int64_t a = t / nc, c = t - a * nc;
+    uint32_t* p = x + a * L + c * kRowChunk;
+    const int len = (int)min((int64_t)kRowChunk, L - c * kRowChunk);
+    uint32_t carry = (cs && c > 0) ? cs[t - 1] : 0u;
+    for (int j = 0; j < len; j += 32) {
+      const int l = j + lane;
+      uint32_t v = l < len ? p[l] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      if (l < len) p[l] = v + carry;
+      carry += __shfl_sync(0xffffffffu, v, 31);
     }
   }
 }
@@ -102,28 +163,59 @@ __global__ void __launch_bounds__(kThreads) k_chunk_apply(uint32_t* __restrict__
 
 // elements of scratch a scan of (A, L, B) uses (every level rounded to 4)
 int64_t scan_scratch_elems(int64_t A, int64_t L, int64_t B) {
-  if (L <= kScanChunk) return 0;
-  const int64_t nc = ceil_div(L, kScanChunk);
-  return ((A * nc * B + 3) & ~(int64_t)3) + scan_scratch_elems(A, nc, B);
+  switch (scan_mode(A, L, B)) {
+    case SCAN_ROWS: {
+      const int64_t nc = ceil_div(L, kRowChunk);
+      return nc == 1 ? 0 : ((A * nc + 3) & ~(int64_t)3) + scan_scratch_elems(A, nc, 1);
+    }
+    case SCAN_CHUNKED: {
+      const int64_t nc = ceil_div(L, kScanChunk);
+      return ((A * nc * B + 3) & ~(int64_t)3) + scan_scratch_elems(A, nc, B);
+    }
+    default:
+      return 0;
+  }
+}
+
+unsigned warp_grid(int64_t warps) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps * 32, kThreads), kScanGridCap));
 }
 
 // inclusive prefix sums along l of x seen as (A, L, B), in place
 int scan_axis(uint32_t* x, int64_t A, int64_t L, int64_t B, uint32_t* scratch, cudaStream_t st) {
-  if (L <= 1 || A * B == 0) return HC_OK;
-  if (L <= kScanChunk) {
-    k_scan_short<<<scan_grid(A * B), kThreads, 0, st>>>(x, A, (int)L, B);
-    return check_launch("prefix sum");
+  switch (scan_mode(A, L, B)) {
+    case SCAN_NONE:
+      return HC_OK;
+    case SCAN_COLUMN:
+      k_scan_column<<<scan_grid(A * B), kThreads, 0, st>>>(x, A, L, B);
+      return check_launch("prefix sum (columns)");
+    case SCAN_ROWS: {
+      const int64_t nc = ceil_div(L, kRowChunk);
+      if (nc == 1) {
+        k_row_apply<<<warp_grid(A), kThreads, 0, st>>>(x, nullptr, A, L, 1);
+        return check_launch("prefix sum (rows)");
+      }
+      uint32_t* cs = scratch;
+      uint32_t* next = scratch + ((A * nc + 3) & ~(int64_t)3);
+      k_row_sums<<<warp_grid(A * nc), kThreads, 0, st>>>(x, cs, A, L, nc);
+      int rc = check_launch("prefix sum (row chunk totals)");
+      if (rc) return rc;
+      if ((rc = scan_axis(cs, A, nc, 1, next, st))) return rc;
+      k_row_apply<<<warp_grid(A * nc), kThreads, 0, st>>>(x, cs, A, L, nc);
+      return check_launch("prefix sum (row chunks)");
+    }
+    default: {
+      const int64_t nc = ceil_div(L, kScanChunk);
+      uint32_t* cs = scratch;
+      uint32_t* next = scratch + ((A * nc * B + 3) & ~(int64_t)3);
+      k_chunk_sums<<<scan_grid(A * nc * B), kThreads, 0, st>>>(x, cs, A, L, B, nc);
+      int rc = check_launch("prefix sum (chunk totals)");
+      if (rc) return rc;
+      if ((rc = scan_axis(cs, A, nc, B, next, st))) return rc;
+      k_chunk_apply<<<scan_grid(A * nc * B), kThreads, 0, st>>>(x, cs, A, L, B, nc);
+      return check_launch("prefix sum (chunks)");
+    }
   }
-  const int64_t nc = ceil_div(L, kScanChunk);
-  uint32_t* cs = scratch;
-  uint32_t* next = scratch + ((A * nc * B + 3) & ~(int64_t)3);
-  k_chunk_sums<<<scan_grid(A * nc * B), kThreads, 0, st>>>(x, cs, A, L, B, nc);
-  int rc = check_launch("prefix sum (chunk totals)");
-  if (rc) return rc;
-  rc = scan_axis(cs, A, nc, B, next, st);
-  if (rc) return rc;
-  k_chunk_apply<<<scan_grid(A * nc * B), kThreads, 0, st>>>(x, cs, A, L, B, nc);
-  return check_launch("prefix sum (chunks)");
 }
 
 // prefix sums along internal axis ax of an array of shape L
