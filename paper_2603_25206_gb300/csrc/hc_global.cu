@@ -73,17 +73,33 @@ int scan_mode(int64_t A, int64_t L, int64_t B) {
   return SCAN_CHUNKED;
 }
 
+// Walk codes [l0, l1) of one column with stride B from `run`, eight loads
+// issued before their stores (the loads are independent of the running sum,
+// and B >= 1 keeps every address distinct).
+__device__ __forceinline__ void scan_walk(uint32_t* p, int64_t l0, int64_t l1, int64_t B, uint32_t run) {
+  int64_t l = l0;
+  for (; l + 8 <= l1; l += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = p[(l + k) * B];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      run += v[k];
+      p[(l + k) * B] = run;
+    }
+  }
+  for (; l < l1; ++l) {
+    run += p[l * B];
+    p[l * B] = run;
+  }
+}
+
 // one thread per column (a, b) walks l
 __global__ void __launch_bounds__(kThreads) k_scan_column(uint32_t* x, int64_t A, int64_t L, int64_t B) {
   const int64_t n = A * B;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = t / B, b = t - a * B;
-    uint32_t* p = x + a * L * B + b;
-    uint32_t run = 0;
-    for (int64_t l = 0; l < L; ++l) {
-      run += p[l * B];
-      p[l * B] = run;
-    }
+    scan_walk(x + a * L * B + b, 0, L, B, 0u);
   }
 }
 
@@ -152,12 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_chunk_apply(uint32_t* __restrict__
     const int64_t b = t % B, r = t / B;
     const int64_t c = r % nc, a = r / nc;
     const int64_t l0 = c * kScanChunk, l1 = min(L, l0 + kScanChunk);
-    uint32_t* p = x + (a * L + l0) * B + b;
-    uint32_t run = c > 0 ? cs[t - B] : 0u;
-    for (int64_t l = l0; l < l1; ++l, p += B) {
-      run += *p;
-      *p = run;
-    }
+    scan_walk(x + a * L * B + b, l0, l1, B, c > 0 ? cs[t - B] : 0u);
   }
 }
 
