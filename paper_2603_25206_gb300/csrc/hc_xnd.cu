@@ -3,9 +3,9 @@
 // (the S = b0 b1 b2 slots of a box row-major inside it), each decorrelated by
 // its integer mean, p = q - M_b; slots of a box outside the field hold 0.
 //
-//   k_decode_box     stages 2-4 in field order: each 32-slot segment of a
-//                    box is unpacked and its slots written to their field
-//                    positions (p, M_b + p, or the dequantized value)
+//   k_decode_box     stages 2-4 in field order: a tile's boxes are unpacked
+//                    into shared memory, then written out row by row along
+//                    runs of boxes (p, M_b + p, or the dequantized value)
 //   k_mean_m_box     stage 1: sum_b M_b S_b with the true box sizes (Eq. mean_m)
 //   k_stats_box      stages 2 and 3: per segment sum p and sum p^2, per box
 //                    the S_b terms -- s1 = sum p + S_b M_b, and about a shift
@@ -163,26 +163,103 @@ int box_tile_smem(const hc_header* h, int* stage) {
   return 4 * pipe_tile_smem(kTileChunks * h->G, *stage, 0).total;
 }
 
+// Stages 2-4 in field order.  A tile's boxes are decoded into a staging
+// buffer in shared memory (box by box, slot order, one pad word per box), then
+// written out row by row: the tile's boxes form runs along x of one box row
+// (k0, k1), and for each layer (s0, s1) of such a run the field codes are one
+// contiguous segment, so consecutive threads store consecutive codes.
 template <int KIND, class OutT, bool SMALL>
 __global__ void __launch_bounds__(kThreads) k_decode_box(DevStream s, BoxGeo bg, OutT* __restrict__ out, float te_f,
-                                                          double te, int64_t ntiles, int stage_words, int* err) {
-  box_tiles<SMALL>(s, ntiles, stage_words, err,
-                   [&](int64_t b, int j, int cnt, uint32_t w, const uint32_t* blk, int32_t head) {
-                     SlotWalk sw(bg, b, 32 * j);
-                     if (w == 0) {
-                       for (int i = 0; i < cnt; ++i) {
-                         const int64_t idx = sw.index(bg);
-                         if (idx >= 0) out[idx] = box_value<KIND, OutT>(head, 0, te_f, te);
-                         sw.next(bg);
-                       }
-                       return;
-                     }
-                     unpack_any(blk + s.nseg + j * w, blk[j], w, cnt, [&](int, int32_t p) {
-                       const int64_t idx = sw.index(bg);
-                       if (idx >= 0) out[idx] = box_value<KIND, OutT>(head, p, te_f, te);
-                       sw.next(bg);
-                     });
-                   });
+                                                          double te, int64_t ntiles, int stage_words, int xshift,
+                                                          int* err) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_warp[32];
+  __shared__ int s_flag;
+  const int tb = kTileChunks * s.G;
+  const PipeTileSmem Lm = pipe_tile_smem(tb, stage_words, tb * (s.S + 1));
+  uint32_t* s_off = smem + Lm.off;
+  int32_t* stg = reinterpret_cast<int32_t*>(smem + Lm.extra);  // box bl, slot k at bl (S + 1) + k
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int S1 = s.S + 1;
+  int64_t t = blockIdx.x;
+  int bi = 0;
+  TileCopy cur{}, nxt{};
+  bool cur_ok = false, have_nxt = false;
+  if (t < ntiles) {
+    cur = tile_bounds(s, t, tb);
+    cur_ok = tile_issue(s, cur, stage_words, Lm.w(smem, 0), Lm.h(smem, 0), Lm.words(smem, 0));
+  }
+  if (t + gridDim.x < ntiles) {
+    nxt = tile_bounds(s, t + gridDim.x, tb);
+    have_nxt = true;
+  }
+  for (; t < ntiles; t += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();
+    bool nxt_ok = false;
+    if (have_nxt)
+      nxt_ok = tile_issue(s, nxt, stage_words, Lm.w(smem, bi ^ 1), Lm.h(smem, bi ^ 1), Lm.words(smem, bi ^ 1));
+    TileCopy nn{};
+    const bool have_nn = t + 2 * (int64_t)gridDim.x < ntiles;
+    if (have_nn) nn = tile_bounds(s, t + 2 * (int64_t)gridDim.x, tb);
+    const int64_t b0 = cur.b0;
+    const int nblk = cur.nblk;
+    const int32_t* hb = Lm.h(smem, bi) + (int)(b0 & 3);
+    TileView tv;
+    const bool ok = tile_ready(s, cur, cur_ok, Lm.w(smem, bi), s_off, Lm.words(smem, bi), s_warp, &s_flag, err, tv);
+    cur = nxt;
+    cur_ok = nxt_ok;
+    nxt = nn;
+    have_nxt = have_nn;
+    bi ^= 1;
+    if (!ok) continue;
+    // decode into the staging buffer
+    const int nsegs = SMALL ? nblk : nblk * s.nseg;
+    for (int sg = tid; sg < nsegs; sg += nt) {
+      const int bl = SMALL ? sg : sg / s.nseg;
+      const int j = SMALL ? 0 : sg - bl * s.nseg;
+      const int cnt = min(32, s.S - 32 * j);
+      const uint32_t w = tv.w[bl];
+      const int32_t head = hb[bl];
+      int32_t* dst = stg + bl * S1 + 32 * j;
+      if (w == 0) {
+        for (int i = 0; i < cnt; ++i) dst[i] = KIND == HC_STAGE_P ? 0 : head;
+      } else {
+        const uint32_t* blk = tv.words + tv.off[bl];
+        unpack_any(blk + s.nseg + j * w, blk[j], w, cnt,
+                   [&](int i, int32_t p) { dst[i] = KIND == HC_STAGE_P ? p : head + p; });
+      }
+    }
+    __syncthreads();
+    // write out: runs of boxes along x within one box row
+    int64_t b = b0;
+    const int64_t bend = b0 + nblk;
+    while (b < bend) {
+      const int64_t k2 = b % bg.g[2], r = b / bg.g[2];
+      const int64_t k1 = r % bg.g[1], k0 = r / bg.g[1];
+      const int64_t run = min(bg.g[2] - k2, bend - b);  // boxes in this run
+      const int64_t x0 = k2 * bg.b[2];
+      const int xlen = (int)(min(bg.n[2], (k2 + run) * bg.b[2]) - x0);
+      const int blr = (int)(b - b0);
+      for (int s0 = 0; s0 < bg.b[0]; ++s0) {
+        const int64_t z = k0 * bg.b[0] + s0;
+        if (z >= bg.n[0]) break;
+        for (int s1 = 0; s1 < bg.b[1]; ++s1) {
+          const int64_t y = k1 * bg.b[1] + s1;
+          if (y >= bg.n[1]) break;
+          OutT* row = out + (z * bg.n[1] + y) * bg.n[2] + x0;
+          const int lrow = (s0 * bg.b[1] + s1) * bg.b[2];
+          for (int xo = tid; xo < xlen; xo += nt) {
+            const int kb = xshift >= 0 ? (xo >> xshift) : xo / bg.b[2];
+            const int32_t v = stg[(blr + kb) * S1 + lrow + (xo - kb * bg.b[2])];
+            row[xo] = box_value<KIND == HC_STAGE_P ? HC_STAGE_Q : KIND, OutT>(0, v, te_f, te);
+          }
+        }
+      }
+      b += run;
+    }
+  }
+  cp_async_wait_all();
 }
 
 // stage 1: T = sum_b M_b S_b; mean (T / N) 2 eps (exact = 0); mu~ = nearest(T / N)
@@ -337,8 +414,10 @@ int tile_grid(const void* kern, int smem, int64_t ntiles) {
 
 template <int KIND, class OutT, bool SMALL>
 int launch_decode_box(const hc_header* h, const void* d_stream, void* d_out, int* err, cudaStream_t st) {
-  int stage = 0;
-  const int smem = box_tile_smem<SMALL>(h, &stage);
+  const int stage = stage_words_for(kTileChunks * h->G, h->S, (int)h->wmax);
+  const int tb = kTileChunks * h->G;
+  const int smem = 4 * pipe_tile_smem(tb, stage, tb * (h->S + 1)).total;
+  const int xshift = (h->block[2] & (h->block[2] - 1)) == 0 ? __builtin_ctz(h->block[2]) : -1;
   auto kern = k_decode_box<KIND, OutT, SMALL>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (rc) return rc;
@@ -346,7 +425,7 @@ int launch_decode_box(const hc_header* h, const void* d_stream, void* d_out, int
   const int grid = tile_grid(reinterpret_cast<const void*>(kern), smem, ntiles);
   const double te = 2.0 * h->eps;
   kern<<<grid, kThreads, smem, st>>>(dev_stream(h, d_stream), box_geo(h), reinterpret_cast<OutT*>(d_out),
-                                     (float)te, te, ntiles, stage, err);
+                                     (float)te, te, ntiles, stage, xshift, err);
   return check_launch_cfg("decompress_to_stage (boxes)", reinterpret_cast<const void*>(kern), grid, smem);
 }
 
