@@ -83,28 +83,19 @@ struct OT<HC_I64> {
   using T = long long;
 };
 
-// Exact int -> float for |a| < 2^22 without the conversion unit: the bit
-// pattern of 1.5 * 2^23 plus a is the float 1.5 * 2^23 + a (one unit in the
-// last place is 1 at that exponent), and subtracting 1.5 * 2^23 is exact.
-// The pipelined kernels hold |q| < 2^15, so every numerator they convert
-// (|D| < 2^17, |L| < 2^19) is in range; the result equals __int2float_rn(a).
-__device__ __forceinline__ float small_int_to_float(int a) {
-  return __fsub_rn(__int_as_float(0x4B400000 + a), 12582912.0f);
-}
-
 template <int OP, int OUT>
 __device__ __forceinline__ typename OT<OUT>::T emit1(int a, int b, int c, const PGeo& g) {
   if constexpr (OP == ST_DERIV) {
-    if constexpr (OUT == HC_F32) return __fmul_rn(small_int_to_float(a), g.eps_f);
+    if constexpr (OUT == HC_F32) return __fmul_rn(__int2float_rn(a), g.eps_f);
     if constexpr (OUT == HC_F64) return __dmul_rn((double)a, g.eps);
     if constexpr (OUT == HC_I64) return (long long)a;
   } else if constexpr (OP == ST_LAPLACIAN) {
-    if constexpr (OUT == HC_F32) return __fmul_rn(small_int_to_float(a), g.te_f);
+    if constexpr (OUT == HC_F32) return __fmul_rn(__int2float_rn(a), g.te_f);
     if constexpr (OUT == HC_F64) return __dmul_rn((double)a, g.te);
     if constexpr (OUT == HC_I64) return (long long)a;
   } else {
     if constexpr (OUT == HC_F32) {
-      const float x = small_int_to_float(a), y = small_int_to_float(b), z = small_int_to_float(c);
+      const float x = __int2float_rn(a), y = __int2float_rn(b), z = __int2float_rn(c);
       return __fmul_rn(__fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z))), g.eps_f);
     } else {
       // explicit roundings: the same value from every kernel (no contraction)
