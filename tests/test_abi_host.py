@@ -239,3 +239,83 @@ def test_vector_argument_errors_before_any_cuda_call(hc):
     comps[0].kind = comps[1].kind = hc.HC_STAGE_Q
     assert L.hc_op_divergence(comps, 2, 2, dims, ctypes.c_void_p(16), hc.HC_F32, ws, L.hc_workspace_bytes(),
                               None) == hc.HC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape,block", [((7, 10), (2, 3)), ((5, 6, 7), (2, 2, 4)), ((9,), (4,)),
+                                         ((13, 17, 19), (4, 4, 4)), ((3, 5, 6), (8, 8, 8))])
+def test_box_compress_bound_matches_oracle_layout(hc, orc, shape, block):
+    """HSZx-nd sizing: the stream bound follows the box grid exactly as the
+    oracle lays it out; bad extents give 0."""
+    import numpy as np
+
+    L = hc.lib()
+    d = (ctypes.c_int64 * 3)(*shape)
+    b = (ctypes.c_int32 * 3)(*block)
+    want = int(orc.lib().orc_compress_bound_nd(len(shape), orc._ptr(np.array(shape, np.int64)),
+                                               orc._ptr(np.array(block, np.int64))))
+    assert int(L.hc_compress_bound_nd(len(shape), d, b)) == want
+    assert int(L.hc_compress_workspace_bytes_nd(len(shape), d, b)) > 64
+    for bad in ((0,) * len(shape), (4096,) + (2,) * (len(shape) - 1)):
+        if len(bad) == len(shape) and (0 in bad or np.prod(bad) > 4096):
+            assert int(L.hc_compress_bound_nd(len(shape), d, (ctypes.c_int32 * 3)(*bad))) == 0
+
+
+def _fake_header(hc, shape, pred, S=32, block=(0, 0, 0)):
+    h = hc.HcHeader()
+    h.ndim = len(shape)
+    dims = (1,) * (3 - len(shape)) + tuple(shape)
+    for a in range(3):
+        h.dims[a] = dims[a]
+        h.block[a] = block[a]
+    h.N = int(dims[0] * dims[1] * dims[2])
+    h.S = S
+    h.pred = pred
+    return h
+
+
+def test_workspace_sizes_per_predictor(hc):
+    """hc_workspace_bytes_for: the common size for block streams; + 4 bytes
+    per element for HSZx-nd; + a rebuilt D_q (4), an int64 accumulator (8)
+    and the scan totals for the global predictors (the totals vanish when no
+    axis is longer than 32 and grow with a long flattened row)."""
+    L = hc.lib()
+    base = int(L.hc_workspace_bytes())
+    r16 = lambda v: (v + 15) & ~15  # noqa: E731
+    for pred in (hc.HC_PRED_DELTA, hc.HC_PRED_MEAN):
+        assert int(L.hc_workspace_bytes_for(ctypes.byref(_fake_header(hc, (64, 64, 64), pred)))) == base
+    hb = _fake_header(hc, (20, 33, 64), hc.HC_PRED_MEAN_ND, 64, (4, 4, 4))
+    assert int(L.hc_workspace_bytes_for(ctypes.byref(hb))) == r16(base) + r16(4 * hb.N)
+    small = _fake_header(hc, (8, 20, 24), hc.HC_PRED_LORENZO)
+    assert int(L.hc_workspace_bytes_for(ctypes.byref(small))) == r16(base) + 12 * small.N
+    big = _fake_header(hc, (256, 384, 384), hc.HC_PRED_LORENZO)
+    flat = _fake_header(hc, (256, 384, 384), hc.HC_PRED_GLOBAL_DELTA)
+    nb = int(L.hc_workspace_bytes_for(ctypes.byref(big)))
+    nf = int(L.hc_workspace_bytes_for(ctypes.byref(flat)))
+    assert r16(base) + 12 * big.N <= nb < r16(base) + 13 * big.N
+    assert nf > r16(base) + 12 * flat.N  # one long row: chunk totals
+    assert int(L.hc_workspace_bytes_for(None)) == 0
+
+
+def test_vector_workspace_sizes(hc):
+    """hc_vector_workspace_bytes: the common size when one fused kernel
+    applies (block streams of one block size at stage Q), else the largest
+    component workspace plus 16 bytes per element."""
+    L = hc.lib()
+    base = int(L.hc_workspace_bytes())
+    heads = [_fake_header(hc, (8, 20, 24), hc.HC_PRED_DELTA) for _ in range(3)]
+    arr = (hc.HcStage * 3)()
+    for k in range(3):
+        arr[k].kind = hc.HC_STAGE_COMPRESSED
+        arr[k].level = hc.HC_STAGE_Q
+        arr[k].hdr = ctypes.pointer(heads[k])
+    assert int(L.hc_vector_workspace_bytes(arr, 3)) == base
+    heads[1].pred = hc.HC_PRED_LORENZO
+    arr[1].hdr = ctypes.pointer(heads[1])
+    comp = int(L.hc_workspace_bytes_for(ctypes.byref(heads[1])))
+    assert int(L.hc_vector_workspace_bytes(arr, 3)) == ((comp + 15) & ~15) + 16 * heads[0].N
+    for k in range(3):
+        arr[k].level = hc.HC_STAGE_P
+    heads[1].pred = hc.HC_PRED_DELTA
+    arr[1].hdr = ctypes.pointer(heads[1])
+    assert int(L.hc_vector_workspace_bytes(arr, 3)) == ((base + 15) & ~15) + 16 * heads[0].N
+    assert int(L.hc_vector_workspace_bytes(arr, 0)) == 0
