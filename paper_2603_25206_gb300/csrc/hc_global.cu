@@ -5,9 +5,9 @@
 // in the prediction shape L = (L0, L1, L2): the field's (n0, n1, n2) for the
 // Lorenzo predictor (HSZp-nd), (1, 1, N) for the delta across blocks (HSZp).
 //
-//   stage 2 mean       k_global_mean: sum q = sum p (L0-z)(L1-y)(L2-x), the
-//                      weights formed per element while the stream is
-//                      decoded (Section V-A's weighted sums); no prefix sum
+//   stage 2 mean       k_global_mean: sum q = sum p (L0-z)(L1-y)(L2-x) while
+//                      the stream is decoded (Section V-A's weighted sums),
+//                      from running sums of each segment; no prefix sum
 //   stage 2 derivative prefix sums of D_p over the axes other than a, then
 //                      D = u(i) + u(i+e_a) (Eq. derivative_Dp as a box sum)
 //   stage 2 Laplacian  per axis the same prefix sums, then the difference

@@ -48,37 +48,6 @@ BoxGeo box_geo(const hc_header* h) {
   return bg;
 }
 
-// Walks the slots of one box from slot s on: field index of the current
-// slot, or -1 outside the field.
-struct SlotWalk {
-  int64_t o0, o1, o2;  // box origin
-  int c0, c1, c2;      // slot coordinates inside the box
-  __device__ SlotWalk(const BoxGeo& bg, int64_t box, int s) {
-    const int64_t k2 = box % bg.g[2], r = box / bg.g[2];
-    o2 = k2 * bg.b[2];
-    o1 = (r % bg.g[1]) * bg.b[1];
-    o0 = (r / bg.g[1]) * bg.b[0];
-    c2 = s % bg.b[2];
-    const int t = s / bg.b[2];
-    c1 = t % bg.b[1];
-    c0 = t / bg.b[1];
-  }
-  __device__ __forceinline__ int64_t index(const BoxGeo& bg) const {
-    const int64_t z = o0 + c0, y = o1 + c1, x = o2 + c2;
-    if (z >= bg.n[0] || y >= bg.n[1] || x >= bg.n[2]) return -1;
-    return (z * bg.n[1] + y) * bg.n[2] + x;
-  }
-  __device__ __forceinline__ void next(const BoxGeo& bg) {
-    if (++c2 == bg.b[2]) {
-      c2 = 0;
-      if (++c1 == bg.b[1]) {
-        c1 = 0;
-        ++c0;
-      }
-    }
-  }
-};
-
 __device__ __forceinline__ int64_t box_true_size(const BoxGeo& bg, int64_t box) {
   const int64_t k2 = box % bg.g[2], r = box / bg.g[2];
   const int64_t k1 = r % bg.g[1], k0 = r / bg.g[1];
