@@ -249,3 +249,27 @@ def test_global_corrupt_stream_reported_not_faulting(env, orc, pred):
         hc.laplacian(c, level="p")
         assert hc.workspace_status() == hc.HC_ERR_CORRUPT
     assert hc.workspace_status() == 0
+
+
+def test_global_multi_equals_one_operation_calls(env):
+    """hc_op_multi on global-predictor streams takes the one-operation paths:
+    the same bytes as the separate calls, at stage 3 and (HSZp-nd, without the
+    gradient magnitude) at stage 2."""
+    import synth
+
+    hc, torch, dev = env
+    x = synth.grf_field((9, 20, 36), 72)
+    for pred in ("lorenzo", "global"):
+        c = hc.compress(torch.from_numpy(x).to(dev), 1e-3, predictor=pred)
+        r = hc.multi(c, level="q")
+        for a in range(3):
+            assert torch.equal(r["derivative"][a], hc.derivative(c, a, level="q"))
+        assert torch.equal(r["gradmag"], hc.gradmag(c, level="q"))
+        assert torch.equal(r["laplacian"], hc.laplacian(c, level="q"))
+        assert hc.parse_scalar(r["stats"]) == hc.parse_scalar(hc.variance(c, level="q"))
+    c = hc.compress(torch.from_numpy(x).to(dev), 1e-3, predictor="lorenzo")
+    r = hc.multi(c, level="p", gradmag=False)
+    for a in range(3):
+        assert torch.equal(r["derivative"][a], hc.derivative(c, a, level="q"))
+    assert torch.equal(r["laplacian"], hc.laplacian(c, level="q"))
+    assert hc.workspace_status() == 0

@@ -200,3 +200,20 @@ def test_box_corrupt_stream_reported_not_faulting(env, orc):
     hc.laplacian(c, level="p")
     assert hc.workspace_status() == hc.HC_ERR_CORRUPT
     assert hc.workspace_status() == 0
+
+
+def test_box_multi_equals_one_operation_calls(env):
+    """hc_op_multi on a box stream takes the one-operation paths: the same
+    bytes as the separate calls at stages 2 and 3 (stage 2 equals stage 3)."""
+    import synth
+
+    hc, torch, dev = env
+    x = synth.grf_field((9, 20, 36), 73)
+    c = hc.compress(torch.from_numpy(x).to(dev), 1e-3, predictor="mean-nd", block=(2, 4, 4))
+    for level in ("p", "q"):
+        r = hc.multi(c, level=level)
+        for a in range(3):
+            assert torch.equal(r["derivative"][a], hc.derivative(c, a, level="q"))
+        assert torch.equal(r["gradmag"], hc.gradmag(c, level="q"))
+        assert torch.equal(r["laplacian"], hc.laplacian(c, level="q"))
+    assert hc.workspace_status() == 0
