@@ -51,7 +51,10 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        # HC_ORACLE_LIB: a build of a modified copy of hc_oracle.c, loaded in
+        # place of oracle/liboracle.so (the planted-mistake runs of
+        # tests/test_oracle_mutants.py)
+        L = ctypes.CDLL(os.environ.get("HC_ORACLE_LIB") or build())
         i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
         P = ctypes.POINTER
         L.orc_eps.argtypes = [vp, i32, i64, dbl, i32, P(dbl)]

@@ -449,6 +449,7 @@ def test_sampled_stencils_equal_whole_field(orc, rng):
         np.testing.assert_array_equal(val, orc.stencil_q(q, orc.KIND_DERIV, eps, ax).reshape(-1)[idx])
     num, val = orc.stencil_at(q, orc.KIND_LAPLACIAN, eps, idx)
     np.testing.assert_array_equal(num, orc.lap_q(q).reshape(-1)[idx])
+    np.testing.assert_array_equal(val, orc.stencil_q(q, orc.KIND_LAPLACIAN, eps).reshape(-1)[idx])
     _, val = orc.stencil_at(q, orc.KIND_GRADMAG, eps, idx)
     np.testing.assert_array_equal(val, orc.stencil_q(q, orc.KIND_GRADMAG, eps).reshape(-1)[idx])
 
@@ -500,6 +501,30 @@ def test_hszx_block_mean_rounding(orc):
     for b, (lo, hi) in enumerate([(0, 4), (4, 8), (8, 12), (12, 16), (16, 18)]):
         assert M[b] == _nearest_tie_zero(int(q[lo:hi].astype(np.int64).sum()), hi - lo)
     np.testing.assert_array_equal(orc.decode(s, "p"), q - np.repeat(M, [4, 4, 4, 4, 2]))
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+def test_hszx_mu_tilde_rounds_to_nearest(orc, sign):
+    """The integer mean mu~ of Section V-A's stage-2 deviation is the nearest
+    integer to T / N (T = sum M_b S_b), not its truncation: block means
+    3, 3, 2 over 12 codes give T / N = 32 / 12 = 2.67 -> mu~ = 3 and
+    sum (q - 3)^2 = 4 (truncation would give mu~ = 2 and 8).  The same
+    codes as one 3x4 field in 1x4 boxes give the same under HSZx-nd."""
+    q = (sign * np.array([3, 3, 3, 3, 3, 3, 3, 3, 2, 2, 2, 2])).astype(np.int32)
+    eps = 0.5
+    s = orc.compress_codes(q, eps, 4, np.float64, pred=1)
+    dp, M = orc.decode(s, "p"), orc.decode(s, "m")
+    np.testing.assert_array_equal(M, sign * np.array([3, 3, 2]))
+    assert orc.mean_m_sum(M, 4, 12) == sign * 32
+    mt, ss, sigma = orc.std_p_x(dp, M, 4, eps)
+    assert (mt, ss) == (sign * 3, 4)
+    assert abs(sigma - math.sqrt(4 / 11)) <= 1e-15
+    q2 = q.reshape(3, 4)
+    s2 = orc.compress_codes_nd(q2, (1, 4), eps)
+    dp2, M2 = orc.decode(s2, "p"), orc.decode(s2, "m")
+    mt2, ss2, sigma2 = orc.xnd_std_p(dp2, M2, (1, 4), eps)
+    assert (mt2, ss2) == (sign * 3, 4)
+    assert abs(sigma2 - math.sqrt(4 / 11)) <= 1e-15
 
 
 @pytest.mark.parametrize("S", SIZES_S)
