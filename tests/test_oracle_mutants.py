@@ -185,6 +185,38 @@ MUTANTS = [
      [("g[a] = vp - vm; /* one-sided", "g[a] = (vp - vm) / 2.0; /* one-sided")]),
     ("plain_lap_centre", "generic-flow Laplacian centre weight 1",
      [("lap += vm + vp - 2.0 * center;", "lap += vm + vp - center;")]),
+    # second batch: bounds of mixed components, edges, carried state, box order
+    ('div_mixed_eps', 'divergence of mixed bounds scales every term by the first eps',
+     [('v += (double)D * eps[c];', 'v += (double)D * eps[0];')]),
+    ('curl_mixed_eps', 'curl of mixed bounds with the bounds swapped',
+     [('(double)du * eps_u - (double)dv * eps_v', '(double)du * eps_v - (double)dv * eps_u')]),
+    ('plain_gradmag_2d', 'generic-flow gradient magnitude without the last axis',
+     [('r = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);', 'r = sqrt(g[0] * g[0] + g[1] * g[1] + 0 * g[2]);')]),
+    ('lorenzo_lap_hi_edge', 'stage-2 Laplacian drops the neighbour next to the high edge',
+     [('if (c[a] < L[a] - 1) v += dp_at(dp, L, nx[0], nx[1], nx[2]);', 'if (c[a] < L[a] - 2) v += dp_at(dp, L, nx[0], nx[1], nx[2]);')]),
+    ('lorenzo_deriv_hi_edge', 'stage-2 derivative high edge not doubled',
+     [('r = 2 * dp_at(dp, L, z, y, x);', 'r = dp_at(dp, L, z, y, x);')]),
+    ('eta_no_restart', 'eta carried across blocks',
+     [('int64_t eta = 0;', 'static int64_t eta; eta = first ? eta : 0;')]),
+    ('eta_s2', "eta's square taken from p",
+     [('b += (u128)(eta * eta);', 'b += (u128)(eta * dp[first + i]);')]),
+    ('hszp_as_nd', "HSZp predicts over the field's axes",
+     [('if (pred == 3) {', 'if (pred == 99) {')]),
+    ('nd_box_order', 'boxes stored with axes 1 and 2 transposed',
+     [('G->k[2] = b % G->g[2];', 'G->k[2] = (b / G->g[1]) % G->g[2];'),
+      ('G->k[1] = (b / G->g[2]) % G->g[1];', 'G->k[1] = b % G->g[1];')]),
+    ('nd_mean_m_unweighted', 'HSZx-nd Eq. mean_m without the box sizes',
+     [('t += (int64_t)M[b] * nd_box_size(dims3, bd, b);', 't += (int64_t)M[b] * 1 + 0 * nd_box_size(dims3, bd, b);')]),
+    ('nd_deriv_lo_edge', 'HSZx-nd derivative low edge not doubled',
+     [('          hi[axis] = 1;\n          e = 2;', '          hi[axis] = 1;\n          e = 1;')]),
+    ('header_eps_eb', 'header stores eb in place of eps',
+     [('put_f64(out, 40, eps);', 'put_f64(out, 40, eb);')]),
+    ('rel_min_first', 'value range from the first element',
+     [('if (v < mn) mn = v;', 'if (v < mn) mn = mn;')]),
+    ('sd_is_var', 'standard deviation without the root',
+     [('*sd = sqrt(*var);', '*sd = *var;')]),
+    ('lorenzo_var_s2', "Algorithm 4's s2 from the column buffer",
+     [('b += (u128)(qv * qv);', 'b += (u128)(qv * col[x]);')]),
 ]
 
 
