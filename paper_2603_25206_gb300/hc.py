@@ -10,6 +10,13 @@ Two layers:
   (``hc_compress``, ``hc_decompress_to_stage``, ``hc_op_mean`` ...).
 * ``compress`` / ``decompress`` / ``mean`` / ``variance`` / ``derivative`` /
   ``gradmag`` / ``laplacian`` allocate outputs with torch and call them.
+
+Streams: every call takes ``stream=`` (default: torch's current stream) and
+queues its kernels there.  The operation workspace is allocated and zeroed on
+that stream.  Outputs are allocated the torch way, on the current stream: a
+caller that passes another stream runs the call inside
+``torch.cuda.stream(s)``, or orders the streams itself, as with any torch
+tensor that is used on a side stream.
 """
 from __future__ import annotations
 
@@ -217,7 +224,11 @@ def workspace(device=None, stream=None, nbytes: int = 0):
     if ws is None or ws.numel() < need:
         if ws is not None:
             s.synchronize()  # the old buffer may still be in use by queued work
-        ws = torch.zeros(need, dtype=torch.uint8, device=dev)
+        # allocated and zero-filled on the stream it serves, so the fill is
+        # ordered before the first kernel that reads it even when that stream
+        # is not torch's current one
+        with torch.cuda.stream(s):
+            ws = torch.zeros(need, dtype=torch.uint8, device=dev)
         _ws_cache[key] = ws
     return ws
 
