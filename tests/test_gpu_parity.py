@@ -254,6 +254,29 @@ def test_repeat_calls_deterministic(env):
         assert torch.equal(fn(), fn())
 
 
+def test_side_stream_not_current(env, orc):
+    """Operations queued on fresh side streams that are never made torch's
+    current stream: each stream's workspace is allocated and zeroed on that
+    stream, and the results equal the oracle's exactly."""
+    hc, torch, dev = env
+    import synth
+
+    x = synth.grf_field((20, 30, 40), 31)
+    ref, eps = orc.compress(x, 1e-3, True, 32)
+    c = hc.compress(torch.from_numpy(x).to(dev), 1e-3)
+    q = orc.decode(ref, "q")
+    lap_ref = orc.lap_q(q)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        s = torch.cuda.Stream(device=dev)
+        r = hc.variance(c, stream=s)
+        lap = hc.laplacian(c, out_dtype="int64", stream=s)
+        s.synchronize()
+        rs = hc.parse_scalar(r)
+        assert (rs["s1"], rs["s2"]) == orc.sums_q(q) and rs["status"] == 0
+        assert np.array_equal(lap.cpu().numpy(), lap_ref)
+
+
 def test_kernel_reuse_across_tile_sizes(env, orc):
     """One kernel launched with large, small, then large shared-memory tiles
     (fields of different row lengths) stays valid and exact."""
