@@ -75,3 +75,37 @@ def test_single_rank_helpers_identity():
     assert bench.timed_max(4.0, 1) == 4.0
     assert bench.weak_value(2e9, 1, 1.0) == pytest.approx(2000.0)
     json.dumps({"x": bench.weak_value(1.0, 1, 1.0)})
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    """The reference arm (the oracle timed on host cores) prints one JSON line
+    with the keys of the bench contract: impl, metric, unit, value, the
+    steps and warm-up asked for, its own cpu_baseline, and an e2e entry with
+    no host-device copies.  Run on a small stand-in for the 512^3 field."""
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+    import synth
+
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    shapes = list(synth.PAPER_SHAPES)
+    shapes[1] = (20, 24, 32)
+    monkeypatch.setattr(synth, "PAPER_SHAPES", tuple(shapes))
+    args = argparse.Namespace(gpus=1, steps=2, warmup=3)
+    assert bench.run_reference(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference"
+    assert (line["metric"], line["unit"]) == (bench.METRIC, bench.UNIT)
+    assert (line["n_gpus"], line["steps"], line["warmup"]) == (1, 2, 3)
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == bench.WORKLOAD
