@@ -239,6 +239,8 @@ static int check_op(const hc_stage* in, double eps, int ndim, const int64_t* dim
   if (in->kind == HC_STAGE_COMPRESSED) {
     const hc_header* h = in->hdr;
     if (!h) return fail(HC_ERR_INVALID_ARG, "a stream input needs its header (hc_read_header)");
+    rc = check_header(*h);  // the caller's host copy: its sections must follow from its shape
+    if (rc) return rc;
     if (h->ndim != ndim || h->eps != eps) return fail(HC_ERR_INVALID_ARG, "eps / ndim differ from the stream header");
     for (int a = 0; a < 3; ++a)
       if (h->dims[a] != dims3[a]) return fail(HC_ERR_INVALID_ARG, "dims differ from the stream header");
@@ -392,6 +394,8 @@ int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out, void*
 int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, int kind, void* d_out, int out_dtype,
                            void* d_ws, size_t ws_bytes, void* stream) {
   if (!hdr || !d_stream || !d_out) return fail(HC_ERR_INVALID_ARG, "null pointer");
+  int rc = check_header(*hdr);
+  if (rc) return rc;
   if (!d_ws || ws_bytes < kOpWsBytes) return fail(HC_ERR_NOMEM, "workspace smaller than hc_workspace_bytes()");
   if (!aligned16(d_stream) || !aligned16(d_out) || !aligned16(d_ws))
     return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
@@ -498,6 +502,7 @@ int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_
   *chosen = 0;
   if (in->kind != HC_STAGE_COMPRESSED || !in->hdr || !in->d_data)
     return fail(HC_ERR_INVALID_ARG, "hc_autotune takes a compressed stream with its header");
+  if (int rc = check_header(*in->hdr)) return rc;
   if (!d_ws || ws_bytes < kOpWsBytes) return fail(HC_ERR_NOMEM, "workspace smaller than hc_workspace_bytes()");
   if (!d_out || !aligned16(d_out) || !aligned16(in->d_data) || !aligned16(d_ws))
     return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");

@@ -56,6 +56,7 @@ extern "C" HC_API int hc_op_variance_noalloc(const hc_stage* in, double eps, int
   if (in->kind != HC_STAGE_COMPRESSED)
     return fail(HC_ERR_UNSUPPORTED, "hc_op_variance_noalloc takes a compressed stream (HC_STAGE_COMPRESSED)");
   if (!in->d_data || !in->hdr) return fail(HC_ERR_INVALID_ARG, "a stream input needs its data and header");
+  if (int hrc = check_header(*in->hdr)) return hrc;
   if (in->level != HC_STAGE_P && in->level != HC_STAGE_Q)
     return fail(HC_ERR_INVALID_ARG, "fused level must be HC_STAGE_P or HC_STAGE_Q");
   if (in->hdr && in->hdr->pred == HC_PRED_MEAN && in->level == HC_STAGE_P)

@@ -319,3 +319,110 @@ def test_vector_workspace_sizes(hc):
     arr[1].hdr = ctypes.pointer(heads[1])
     assert int(L.hc_vector_workspace_bytes(arr, 3)) == ((base + 15) & ~15) + 16 * heads[0].N
     assert int(L.hc_vector_workspace_bytes(arr, 0)) == 0
+
+
+def _header_from_oracle_stream(hc, orc, s):
+    """A host hc_header filled from an oracle stream's header (the section
+    offsets follow the stream layout: widths at 256, heads and the chunk
+    index each on the next 16-byte boundary)."""
+    g = orc.read_header(s)
+    r16 = lambda v: (v + 15) & ~15  # noqa: E731
+    h = hc.HcHeader()
+    h.dtype, h.ndim = g["dtype"], g["ndim"]
+    for a, k in enumerate(("n0", "n1", "n2")):
+        h.dims[a] = g[k]
+    for a, k in enumerate(("b0", "b1", "b2")):
+        h.block[a] = g[k]
+    h.S, h.G, h.eps, h.eb, h.eb_mode, h.qmax = g["S"], g["G"], g["eps"], g["eb"], g["eb_mode"], g["qmax"]
+    h.N, h.nb, h.nchunks, h.payload_words = g["N"], g["nb"], g["nchunks"], g["payload_words"]
+    h.off_widths = 256
+    h.off_heads = r16(256 + g["nb"])
+    h.off_chunks = r16(h.off_heads + 4 * g["nb"])
+    h.off_payload, h.total_bytes, h.wmax, h.pred = g["off_payload"], g["total_bytes"], g["wmax"], g["pred"]
+    assert h.off_payload == r16(h.off_chunks + 8 * (g["nchunks"] + 1))
+    return h
+
+
+def _copy_header(hc, h):
+    c = hc.HcHeader()
+    ctypes.memmove(ctypes.byref(c), ctypes.byref(h), ctypes.sizeof(h))
+    return c
+
+
+def test_host_header_checked_before_any_cuda_call(hc, orc, rng):
+    """Every entry point that takes the caller's host copy of a header checks
+    it on the host first: a header whose fields contradict one another is
+    refused with HC_ERR_CORRUPT before anything reaches the GPU.  The
+    unmodified header passes that check; each call with it is stopped by a
+    later argument check instead (an invalid stage kind, a null output, an
+    invalid level), so no kernel is launched."""
+    import numpy as np
+
+    L = hc.lib()
+    p16 = ctypes.c_void_p(16)
+    wsn = L.hc_workspace_bytes()
+    x = rng.standard_normal((6, 10, 40)).astype(np.float32)
+    s0, _ = orc.compress(x, 1e-3, True, 32)
+    x2 = rng.standard_normal((12, 20)).astype(np.float32)
+    s4, _ = orc.compress_nd(x2, (4, 4), 1e-3, True)
+
+    def entries(h, base):
+        # the call's own ndim, dims and eps are the valid stream's: only the header differs
+        dims = (ctypes.c_int64 * 3)(*[int(v) for v in base.dims][3 - base.ndim:])
+        nd, eps = base.ndim, base.eps
+        st = hc.HcStage()
+        st.kind, st.level, st.d_data, st.hdr = hc.HC_STAGE_COMPRESSED, hc.HC_STAGE_Q, 16, ctypes.pointer(h)
+        st.n = h.N
+        bad_level = hc.HcStage()
+        ctypes.memmove(ctypes.byref(bad_level), ctypes.byref(st), ctypes.sizeof(st))
+        bad_level.level = hc.HC_STAGE_F
+        chosen = ctypes.c_int()
+        return {
+            "decompress": lambda: L.hc_decompress_to_stage(ctypes.byref(h), p16, 99, p16, 0, p16, wsn, None),
+            "mean": lambda: L.hc_op_mean(ctypes.byref(st), eps, nd, dims, None, p16, wsn, None),
+            "laplacian": lambda: L.hc_op_laplacian(ctypes.byref(st), eps, nd, dims, None, 0, p16, wsn, None),
+            "multi": lambda: L.hc_op_multi(ctypes.byref(st), eps, nd, dims, None, p16, wsn, None),
+            "noalloc": lambda: L.hc_op_variance_noalloc(ctypes.byref(bad_level), eps, nd, dims, p16, None),
+            "autotune": lambda: L.hc_autotune(ctypes.byref(st), hc.HC_OP_LAPLACIAN, 0, None, p16, wsn, None,
+                                              ctypes.byref(chosen)),
+        }
+
+    corruptions = [
+        ("dtype", lambda h: setattr(h, "dtype", 2), b"bad dtype"),
+        ("ndim", lambda h: setattr(h, "ndim", 0), b"bad ndim"),
+        ("N", lambda h: setattr(h, "N", h.N + 1), b"section offsets"),
+        ("nb", lambda h: setattr(h, "nb", h.nb + 1), b"section offsets"),
+        ("off_payload", lambda h: setattr(h, "off_payload", h.off_payload + 16), b"section offsets"),
+        ("total_bytes", lambda h: setattr(h, "total_bytes", h.total_bytes + 16), b"total size"),
+        ("payload_words", lambda h: (setattr(h, "payload_words", h.payload_words + (1 << 30)),
+                                     setattr(h, "total_bytes", h.total_bytes + (4 << 30))), b"larger than any"),
+        ("wmax", lambda h: setattr(h, "wmax", 32), b"max width"),
+        ("pred", lambda h: setattr(h, "pred", 5), (b"unknown predictor", b"box extents on")),
+        ("eps_zero", lambda h: setattr(h, "eps", 0.0), b"bad eps"),
+        ("eps_inf", lambda h: setattr(h, "eps", float("inf")), b"bad eps"),
+        ("qmax", lambda h: setattr(h, "qmax", 1 << 30), b"max |q|"),
+    ]
+    h0 = _header_from_oracle_stream(hc, orc, s0)
+    h4 = _header_from_oracle_stream(hc, orc, s4)
+    assert (h0.pred, h4.pred, tuple(h4.block), tuple(h0.block)) == (0, 4, (1, 4, 4), (0, 0, 0))
+    after_check = {"decompress": b"kind must be", "mean": b"null output", "laplacian": b"output must be",
+                   "multi": b"null output set", "noalloc": b"fused level", "autotune": b"16-byte aligned"}
+    for h in (h0, h4):
+        for name, call in entries(h, h).items():
+            assert call() == hc.HC_ERR_INVALID_ARG, name
+            assert after_check[name] in L.hc_last_error(), (name, L.hc_last_error())
+    box_corruptions = [
+        ("block_on_delta", h0, lambda h: setattr(h, "block", (ctypes.c_uint32 * 3)(0, 0, 4)), b"box extents on"),
+        ("box_product", h4, lambda h: setattr(h, "block", (ctypes.c_uint32 * 3)(1, 4, 8)), b"box extents and S"),
+        ("box_leading", h4, lambda h: setattr(h, "block", (ctypes.c_uint32 * 3)(2, 4, 2)), b"leading box"),
+        ("leading_dim", h4, lambda h: h.dims.__setitem__(0, 2), b"leading dims"),
+    ]
+    cases = [(n, base, f, m) for base in (h0, h4) for n, f, m in corruptions] + box_corruptions
+    for name, base, corrupt, msg in cases:
+        h = _copy_header(hc, base)
+        corrupt(h)
+        for entry, call in entries(h, base).items():
+            rc = call()
+            assert rc == hc.HC_ERR_CORRUPT, (name, entry, rc, L.hc_last_error())
+            msgs = msg if isinstance(msg, tuple) else (msg,)
+            assert any(m in L.hc_last_error() for m in msgs), (name, entry, L.hc_last_error())
