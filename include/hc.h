@@ -25,6 +25,13 @@
  *    hc_scalar result, or the first int32 of the workspace for field results
  *    (read it with hc_workspace_status).  Kernels never read outside the
  *    stream, whatever its content.
+ *  - A host hc_header passed by the caller (hc_decompress_to_stage, an
+ *    hc_stage of kind HC_STAGE_COMPRESSED, hc_autotune, hc_batch_plan) is
+ *    checked on the host before anything is enqueued: its section offsets,
+ *    sizes, block or box extents, width, eps and max |q| must follow from
+ *    its shape and block size, else HC_ERR_CORRUPT.  The header must still
+ *    describe the device stream passed with it (hc_read_header of that
+ *    stream, or the one hc_compress returned).
  *  - No C++ exception crosses this interface.
  */
 #ifndef HC_H
