@@ -172,7 +172,8 @@ HC_API size_t hc_workspace_bytes(void);
  * GLOBAL_DELTA) hc_workspace_bytes() plus scratch for a rebuilt D_q and the
  * prefix sums (about 12.3 bytes per element); for MEAN_ND streams
  * hc_workspace_bytes() plus 4 bytes per element (a stage in field order).
- * 0 for a NULL header. */
+ * 0 for a NULL header, or one whose ndim, extents (>= 1, product N), box
+ * extents or predictor are invalid. */
 HC_API size_t hc_workspace_bytes_for(const hc_header* hdr);
 /* Bytes of a materialized stage (M, P, Q or F; F in the header's dtype). */
 HC_API size_t hc_stage_bytes(const hc_header* hdr, int kind);

@@ -307,7 +307,15 @@ size_t hc_compress_workspace_bytes(int64_t n, int S) {
 size_t hc_workspace_bytes(void) { return kOpWsBytes; }
 
 size_t hc_workspace_bytes_for(const hc_header* hdr) {
-  if (!hdr) return 0;
+  if (!hdr || hdr->ndim < 1 || hdr->ndim > 3 || hdr->pred > HC_PRED_MEAN_ND) return 0;
+  // the fields the size depends on must agree: extents >= 1 whose product is N
+  __int128 n = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (hdr->dims[a] < 1 || (hdr->pred == HC_PRED_MEAN_ND && hdr->block[a] < 1)) return 0;
+    n *= hdr->dims[a];
+    if (n > ((__int128)1 << 40)) return 0;
+  }
+  if (n != hdr->N) return 0;
   if (hdr->pred == HC_PRED_MEAN_ND) return xnd_workspace_bytes(hdr);
   return global_workspace_bytes(hdr);
 }
@@ -612,7 +620,7 @@ size_t hc_vector_workspace_bytes(const hc_stage* comps, int ncomp) {
   const hc_header* hs[3];
   bool fused = comps[0].level == HC_STAGE_Q;
   for (int c = 0; c < ncomp; ++c) {
-    if (comps[c].kind != HC_STAGE_COMPRESSED || !comps[c].hdr) return 0;
+    if (comps[c].kind != HC_STAGE_COMPRESSED || !comps[c].hdr || !hc_workspace_bytes_for(comps[c].hdr)) return 0;
     hs[c] = comps[c].hdr;
     if (hs[c]->pred >= HC_PRED_LORENZO || hs[c]->S != hs[0]->S || comps[c].level != HC_STAGE_Q) fused = false;
   }

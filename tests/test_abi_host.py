@@ -426,3 +426,54 @@ def test_host_header_checked_before_any_cuda_call(hc, orc, rng):
             assert rc == hc.HC_ERR_CORRUPT, (name, entry, rc, L.hc_last_error())
             msgs = msg if isinstance(msg, tuple) else (msg,)
             assert any(m in L.hc_last_error() for m in msgs), (name, entry, L.hc_last_error())
+
+
+def test_workspace_size_of_real_and_invalid_headers(hc, orc, rng):
+    """hc_workspace_bytes_for on the headers of real streams of every
+    predictor (1-D, 2-D and 3-D fields, ragged boxes) gives the documented
+    size; a header whose ndim, extents, N, box extents or predictor are
+    invalid gives 0, and so does a vector of components holding one."""
+    import numpy as np
+
+    L = hc.lib()
+    base = int(L.hc_workspace_bytes())
+    r16 = lambda v: (v + 15) & ~15  # noqa: E731
+    for shape in ((300,), (17, 23), (5, 9, 40)):
+        x = rng.standard_normal(shape).astype(np.float32)
+        for pred in (0, 1, 2, 3):
+            s, _ = orc.compress(x, 1e-3, True, 16, pred=pred)
+            h = _header_from_oracle_stream(hc, orc, s)
+            got = int(L.hc_workspace_bytes_for(ctypes.byref(h)))
+            if pred < 2:
+                assert got == base
+            else:
+                assert r16(base) + 12 * h.N <= got < r16(base) + 13 * h.N + 4096, (shape, pred)
+        block = (7,) * len(shape) if len(shape) < 3 else (2, 3, 8)
+        s4, _ = orc.compress_nd(x, block, 1e-3, True)
+        h4 = _header_from_oracle_stream(hc, orc, s4)
+        assert int(L.hc_workspace_bytes_for(ctypes.byref(h4))) == r16(base) + r16(4 * h4.N)
+    s, _ = orc.compress(rng.standard_normal((6, 8, 10)).astype(np.float32), 1e-3, True, 32, pred=2)
+    good = _header_from_oracle_stream(hc, orc, s)
+    s4, _ = orc.compress_nd(rng.standard_normal((6, 8, 10)).astype(np.float32), (2, 2, 4), 1e-3, True)
+    good4 = _header_from_oracle_stream(hc, orc, s4)
+    bad = [
+        (good, lambda h: setattr(h, "ndim", 0)),
+        (good, lambda h: setattr(h, "ndim", 4)),
+        (good, lambda h: h.dims.__setitem__(1, 0)),
+        (good, lambda h: h.dims.__setitem__(2, -8)),
+        (good, lambda h: setattr(h, "N", h.N + 1)),
+        (good, lambda h: setattr(h, "pred", 5)),
+        (good, lambda h: (h.dims.__setitem__(0, 1 << 20), h.dims.__setitem__(1, 1 << 20),
+                          setattr(h, "N", (1 << 40) * h.dims[2]))),
+        (good4, lambda h: h.block.__setitem__(2, 0)),
+    ]
+    for base_h, corrupt in bad:
+        h = _copy_header(hc, base_h)
+        corrupt(h)
+        assert int(L.hc_workspace_bytes_for(ctypes.byref(h))) == 0
+        st = hc.HcStage()
+        st.kind, st.level, st.d_data, st.hdr = hc.HC_STAGE_COMPRESSED, hc.HC_STAGE_Q, 16, ctypes.pointer(h)
+        assert int(L.hc_vector_workspace_bytes(ctypes.byref(st), 1)) == 0
+    st = hc.HcStage()
+    st.kind, st.level, st.d_data, st.hdr = hc.HC_STAGE_COMPRESSED, hc.HC_STAGE_Q, 16, ctypes.pointer(good)
+    assert int(L.hc_vector_workspace_bytes(ctypes.byref(st), 1)) >= int(L.hc_workspace_bytes_for(ctypes.byref(good)))
