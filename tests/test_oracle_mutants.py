@@ -217,6 +217,35 @@ MUTANTS = [
      [('*sd = sqrt(*var);', '*sd = *var;')]),
     ('lorenzo_var_s2', "Algorithm 4's s2 from the column buffer",
      [('b += (u128)(qv * qv);', 'b += (u128)(qv * col[x]);')]),
+    # third batch: header fields, limits and the reader's structural checks (none that
+    # guards memory is dropped)
+    ('header_wmax', 'header max width one too high',
+     [('put_u32(out, 136, (uint32_t)wmax);', 'put_u32(out, 136, (uint32_t)wmax + 1u);')]),
+    ('header_qmax', 'header max |q| one too high',
+     [('put_u32(out, 60, (uint32_t)qmax);', 'put_u32(out, 60, (uint32_t)qmax + 1u);')]),
+    ('header_eb_mode', 'header bound mode always absolute',
+     [('put_u32(out, 56, (uint32_t)eb_mode);', 'put_u32(out, 56, 0u * (uint32_t)eb_mode);')]),
+    ('header_eb_is_eps', 'header stores eps in place of eb',
+     [('put_f64(out, 48, eb);', 'put_f64(out, 48, eps);')]),
+    ('header_ndim_3', 'header ndim always 3',
+     [('put_u8(out, 7, (uint32_t)ndim);', 'put_u8(out, 7, 3u + 0u * (uint32_t)ndim);')]),
+    ('stats_f_mean_n1', 'generic-flow mean over N + 1',
+     [('double mu = (s + c) / (double)n;', 'double mu = (s + c) / (double)(n + 1);')]),
+    ('qlimit_2x', 'codes accepted up to 2^31',
+     [('if (!(fabs(r) < (double)ORC_QLIMIT)) return ORC_ERR_RANGE;', 'if (!(fabs(r) < 2.0 * (double)ORC_QLIMIT)) return ORC_ERR_RANGE;')]),
+    ('resid_range_30', 'global residuals limited to 2^30',
+     [('if (v <= -((int64_t)1 << 31) || v >= ((int64_t)1 << 31)) {', 'if (v <= -((int64_t)1 << 30) || v >= ((int64_t)1 << 30)) {')]),
+    ('chunk_check_dropped', 'reader ignores the chunk index',
+     [('if (b % h.G == 0 && (int64_t)get_u64(s, h.off_chunks + 8 * (b / h.G)) != word) {', 'if (b % h.G == 0 && (int64_t)get_u64(s, h.off_chunks + 8 * (b / h.G)) != word && 0) {')]),
+    ('magic_check_dropped', 'reader ignores magic and version',
+     [('if (get_u32(s, 0) != ORC_MAGIC || get_u16(s, 4) != ORC_VERSION) return ORC_ERR_CORRUPT;', 'if (0 && (get_u32(s, 0) != ORC_MAGIC || get_u16(s, 4) != ORC_VERSION)) return ORC_ERR_CORRUPT;')]),
+    ('payload_total_check', 'reader ignores the payload total of the walk',
+     [('if (word != h.payload_words ||', 'if (0 * (word != h.payload_words) ||')]),
+    ('global_heads_allowed', 'stage 1 of a global-predictor stream not refused',
+     [('if (h.pred == 2 || h.pred == 3) return ORC_ERR_UNSUPPORTED;', 'if (0 * h.pred) return ORC_ERR_UNSUPPORTED;')]),
+    ('msb_in_byte_both', 'bits taken most-significant first inside each byte, writer and reader alike',
+     [('out[byte] |= (uint8_t)(1u << (bit % 8));', 'out[byte] |= (uint8_t)(1u << (7 - bit % 8));'),
+      ('if ((s[byte] >> (bit % 8)) & 1u) m |= 1u << j;', 'if ((s[byte] >> (7 - bit % 8)) & 1u) m |= 1u << j;')]),
 ]
 
 

@@ -91,6 +91,30 @@ def test_range_and_argument_errors(orc):
     assert orc.eps_for(np.full(10, 3.0, np.float32), 1e-3, True) == 1e-3
 
 
+def test_quantize_limit_is_two_to_the_thirty(orc):
+    """Codes satisfy |q| < 2^30 (the stream's code range): with 2 eps = 1,
+    x = +-(2^30 - 1) quantises and x = +-2^30, or 2^30 - 1/2 (which rounds up
+    to 2^30), is refused as out of range."""
+    ok = orc.quantize(np.array([2.0**30 - 1, -(2.0**30 - 1), 2.0**30 - 0.75], np.float64), 0.5)
+    assert [int(v) for v in ok] == [2**30 - 1, -(2**30 - 1), 2**30 - 1]
+    for v in (2.0**30, -(2.0**30), 2.0**30 - 0.5):
+        with pytest.raises(orc.OracleError) as e:
+            orc.quantize(np.array([v], np.float64), 0.5)
+        assert e.value.status == 2
+
+
+def test_header_records_the_bound_as_given(orc, rng):
+    """The header keeps the bound as the caller gave it (eb and its mode)
+    beside the absolute eps it used: eps = eb (max - min) for a value-range
+    relative bound (Section VI-B), eps = eb for an absolute one."""
+    x = rng.normal(size=(10, 20)).astype(np.float32)
+    for eb, rel in ((1e-3, True), (0.01, False)):
+        s, eps = orc.compress(x, eb, rel, 32)
+        h = orc.read_header(s)
+        assert (h["eb"], h["eb_mode"]) == (eb, 1 if rel else 0)
+        assert h["eps"] == eps == (eb * (float(x.max()) - float(x.min())) if rel else eb)
+
+
 # ---------------------------------------------------------------- the stream
 def _golden_stream_bytes():
     out = None
@@ -272,6 +296,42 @@ def test_corrupt_streams_are_rejected(orc, rng):
     with pytest.raises(orc.OracleError):
         orc.decode(bad, "q")
     assert h["N"] == 1000
+
+
+def test_reader_checks_chunk_index_and_walk_total(orc, rng):
+    """The reader checks each chunk's stored base against the running sum of
+    the block sizes, and the walk's total against the header.  Two streams
+    must be refused as corrupt: one with the base of chunk 1 moved by a word,
+    and one whose header and chunk-index end both claim 4 more payload words
+    than the blocks hold."""
+    x = rng.normal(size=20000).astype(np.float32)
+    s, _ = orc.compress(x, 1e-3, True, 32)
+    h = orc.read_header(s)
+    assert h["nchunks"] >= 3 and s.size == h["total_bytes"]
+    r16 = lambda v: (v + 15) & ~15  # noqa: E731
+    off_chunks = r16(r16(256 + h["nb"]) + 4 * h["nb"])
+
+    def put_u64(buf, off, v):
+        buf[off:off + 8] = np.frombuffer(struct.pack("<Q", v), np.uint8)
+
+    def get_u64(buf, off):
+        return struct.unpack("<Q", bytes(buf[off:off + 8]))[0]
+
+    bad = s.copy()
+    put_u64(bad, off_chunks + 8, get_u64(bad, off_chunks + 8) + 1)
+    with pytest.raises(orc.OracleError) as e:
+        orc.decode(bad, "q")
+    assert e.value.status == 3
+    grown = np.zeros(s.size + 16, np.uint8)
+    grown[: s.size] = s
+    put_u64(grown, 88, h["payload_words"] + 4)
+    put_u64(grown, 128, h["total_bytes"] + 16)
+    end = off_chunks + 8 * h["nchunks"]
+    put_u64(grown, end, get_u64(grown, end) + 4)
+    with pytest.raises(orc.OracleError) as e:
+        orc.decode(grown, "q")
+    assert e.value.status == 3
+    np.testing.assert_array_equal(orc.decode(s, "q"), orc.quantize(x, h["eps"]))
 
 
 # ------------------------------------------------------------------- statistics
