@@ -62,6 +62,7 @@ int main(void) {
          offsetof(hc_batch_item, d_scalar), offsetof(hc_batch_item, field_dtype));
   printf("%zu %zu %zu\n", sizeof(hc_batch_tune), offsetof(hc_batch_tune, unit_elems), offsetof(hc_batch_tune, ctas_per_sm));
   printf("%zu %zu %zu\n", sizeof(hc_multi_out), offsetof(hc_multi_out, d_stats), offsetof(hc_multi_out, out_dtype));
+  printf("%zu %zu %zu\n", offsetof(hc_header, pred), offsetof(hc_header, block), offsetof(hc_stage, pred));
   return 0;
 }
 """
@@ -83,6 +84,52 @@ int main(void) {
     assert vals[19:22] == [ctypes.sizeof(T), T.unit_elems.offset, T.ctas_per_sm.offset]
     M = hc.HcMultiOut
     assert vals[22:25] == [ctypes.sizeof(M), M.d_stats.offset, M.out_dtype.offset]
+    assert vals[25:28] == [H.pred.offset, H.block.offset, St.pred.offset]
+
+
+def test_plain_c_program_links_and_calls_the_library(hc, orc):
+    """A C11 program that includes only hc.h links libhc.so and calls its host
+    entry points: version, status strings, the size queries of a stream and of
+    a box stream (the same values as the oracle's layout), and a refused call
+    whose message comes back through hc_last_error.  No GPU is touched."""
+    src = r"""
+#include <stdio.h>
+#include <string.h>
+#include "hc.h"
+int main(void) {
+  int64_t dims[3] = {20, 24, 32};
+  int32_t block[3] = {4, 4, 8};
+  printf("%d\n", hc_version());
+  printf("%s|%s\n", hc_status_str(HC_ERR_CORRUPT), hc_status_str(HC_ERR_UNSUPPORTED));
+  printf("%zu %zu\n", hc_compress_bound(1000, 32), hc_compress_bound_nd(3, dims, block));
+  printf("%zu\n", hc_workspace_bytes());
+  hc_header h;
+  memset(&h, 0, sizeof h);
+  int rc = hc_decompress_to_stage(&h, (const void*)16, HC_STAGE_Q, (void*)16, HC_F32, (void*)16,
+                                  hc_workspace_bytes(), NULL);
+  printf("%d %s\n", rc, hc_last_error());
+  return 0;
+}
+"""
+    lib_dir = os.path.dirname(hc.LIB_PATH)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.dirname(HC_H), c, "-o", exe,
+                               "-L", lib_dir, "-lhc", "-Wl,-rpath," + lib_dir])
+        lines = subprocess.check_output([exe]).decode().splitlines()
+    assert int(lines[0]) == hc.lib().hc_version()
+    assert lines[1] == "corrupt stream|unsupported"
+    bound, bound_nd = (int(v) for v in lines[2].split())
+    assert bound == orc.compress_bound(1000, 32)
+    import numpy as np
+
+    assert bound_nd == int(orc.lib().orc_compress_bound_nd(3, orc._ptr(np.array((20, 24, 32), np.int64)),
+                                                           orc._ptr(np.array((4, 4, 8), np.int64))))
+    assert int(lines[3]) == int(hc.lib().hc_workspace_bytes())
+    rc, msg = lines[4].split(" ", 1)
+    assert int(rc) == hc.HC_ERR_CORRUPT and msg == "bad ndim"
 
 
 @pytest.mark.parametrize("S", [1, 2, 3, 16, 32, 33, 64, 100, 128, 4096])
