@@ -524,3 +524,37 @@ def test_workspace_size_of_real_and_invalid_headers(hc, orc, rng):
     st = hc.HcStage()
     st.kind, st.level, st.d_data, st.hdr = hc.HC_STAGE_COMPRESSED, hc.HC_STAGE_Q, 16, ctypes.pointer(good)
     assert int(L.hc_vector_workspace_bytes(ctypes.byref(st), 1)) >= int(L.hc_workspace_bytes_for(ctypes.byref(good)))
+
+
+def test_empty_and_oversized_fields_refused_on_the_host(hc):
+    """An empty field (an axis of length 0), a negative extent, more than
+    2^40 elements, or an empty or oversized box is refused with
+    HC_ERR_INVALID_ARG before any device memory is touched, by compression,
+    box compression, the size queries and an operation on a stage array."""
+    L = hc.lib()
+    p16 = ctypes.c_void_p(16)
+    n = ctypes.c_size_t()
+    big = 1 << 21
+    for nd, dims, msg in ((1, (0,), b"every dimension"), (2, (7, 0), b"every dimension"),
+                          (3, (4, -2, 9), b"every dimension"), (3, (big, big, 2), b"too large")):
+        d = (ctypes.c_int64 * 3)(*dims, *([1] * (3 - len(dims))))
+        rc = L.hc_compress(p16, 0, nd, d, 1e-3, 1, 32, p16, 1 << 30, p16, 1 << 30, ctypes.byref(n), None, None)
+        assert rc == hc.HC_ERR_INVALID_ARG and msg in L.hc_last_error(), dims
+        rc = L.hc_compress_codes_ex(p16, 0, nd, d, 0.5, 1e-3, 0, 32, 0, p16, 1 << 30, p16, 1 << 30,
+                                    ctypes.byref(n), None, None)
+        assert rc == hc.HC_ERR_INVALID_ARG and msg in L.hc_last_error(), dims
+        blk = (ctypes.c_int32 * 3)(4, 4, 4)
+        rc = L.hc_compress_nd(p16, 0, nd, d, blk, 1e-3, 1, p16, 1 << 30, p16, 1 << 30, ctypes.byref(n), None, None)
+        assert rc == hc.HC_ERR_INVALID_ARG and msg in L.hc_last_error(), dims
+        assert int(L.hc_compress_bound_nd(nd, d, blk)) == 0
+        st = hc.HcStage()
+        st.kind, st.d_data, st.n = hc.HC_STAGE_Q, 16, 0
+        rc = L.hc_op_mean(ctypes.byref(st), 1e-3, nd, d, p16, p16, L.hc_workspace_bytes(), None)
+        assert rc == hc.HC_ERR_INVALID_ARG and msg in L.hc_last_error(), dims
+    d = (ctypes.c_int64 * 3)(8, 8, 8)
+    for blk, msg in (((0, 4, 4), b"box extents"), ((16, 16, 32), b"box size")):
+        rc = L.hc_compress_nd(p16, 0, 3, d, (ctypes.c_int32 * 3)(*blk), 1e-3, 1, p16, 1 << 30, p16, 1 << 30,
+                              ctypes.byref(n), None, None)
+        assert rc == hc.HC_ERR_INVALID_ARG and msg in L.hc_last_error(), blk
+    assert int(L.hc_compress_bound(0, 32)) == 0 and int(L.hc_compress_bound(-5, 32)) == 0
+    assert int(L.hc_compress_bound(1 << 41, 32)) == 0
