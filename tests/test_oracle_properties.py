@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 pytest.importorskip("hypothesis")
-from hypothesis import HealthCheck, given, settings  # noqa: E402
+from hypothesis import HealthCheck, assume, given, settings  # noqa: E402
 from hypothesis import strategies as st  # noqa: E402
 
 SETTINGS = settings(max_examples=200, deadline=None, derandomize=True,
@@ -114,6 +114,8 @@ def test_hszx_nd_stages_sums_and_stencils(orc, data, q):
        rel=st.booleans(), pred=st.integers(0, 3), S=st.sampled_from([3, 32, 64]))
 def test_error_bound_holds(orc, q, dtype, eb, rel, pred, S):
     x = (q.astype(np.float64) * 1e-4 + np.sin(np.arange(q.size)).reshape(q.shape)).astype(dtype)
+    # codes below 2^27 keep every predictor's residual inside the encoder's 31 bits
+    assume(int(np.abs(orc.quantize(x, orc.eps_for(x, eb, rel)).astype(np.int64)).max()) < (1 << 27))
     s, eps = orc.compress(x, eb, rel, S, pred=pred)
     f = orc.decode(s, "f")
     err = np.abs(f.astype(np.float64) - x.astype(np.float64))
