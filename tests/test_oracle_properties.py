@@ -121,3 +121,26 @@ def test_error_bound_holds(orc, q, dtype, eb, rel, pred, S):
     err = np.abs(f.astype(np.float64) - x.astype(np.float64))
     slack = 0.0 if dtype == np.float64 else np.spacing(np.abs(f)).astype(np.float64)
     assert np.all(err <= eps * (1 + 1e-12) + slack)
+
+
+@SETTINGS
+@given(q=codes(), eps=st.sampled_from([1e-6, 1e-3, 0.5, 7.0]))
+def test_homomorphic_equals_generic_flow(orc, q, eps):
+    """Section V-D: on the same codes, the homomorphic results (integer sums
+    and numerators, scaled once) equal the generic flow on D_f = 2 eps q in
+    float64 up to rounding: a few units in the last place of the field's
+    scale 2 eps max|q| (its square for the variance)."""
+    f = orc.dequantize(q, eps, np.float64)
+    ulp = 2.0**-52 * 2 * eps * max(1, int(np.abs(q.astype(np.int64)).max()))
+    for a in range(q.ndim):
+        np.testing.assert_allclose(orc.stencil_q(q, orc.KIND_DERIV, eps, a), orc.stencil_f(f, orc.KIND_DERIV, a),
+                                   rtol=0, atol=8 * ulp)
+    np.testing.assert_allclose(orc.stencil_q(q, orc.KIND_GRADMAG, eps), orc.stencil_f(f, orc.KIND_GRADMAG),
+                               rtol=0, atol=16 * ulp)
+    np.testing.assert_allclose(orc.stencil_q(q, orc.KIND_LAPLACIAN, eps), orc.stencil_f(f, orc.KIND_LAPLACIAN),
+                               rtol=0, atol=32 * q.ndim * ulp)
+    mean, var, _ = orc.finalize(q.size, *orc.sums_q(q), eps)
+    mf, vf = orc.stats_f(f)
+    assert abs(mean - mf) <= 4 * ulp
+    if q.size > 1:
+        assert abs(var - vf) <= 16 * ulp * ulp / 2.0**-52 + 1e-12 * vf
