@@ -159,22 +159,29 @@ class ClockSampler:
         if not inside and self.lines:
             mid = (t0 + self.t1) / 2
             inside = [min(self.lines, key=lambda tl: abs(tl[0] - mid))[1]]
-        sm, smax, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in inside:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm), "period_ms": 50}
+        return summarize_clock_samples(inside)
+
+
+def summarize_clock_samples(lines) -> dict:
+    """Median SM clock, maximum SM clock and the throttle reasons seen, from
+    nvidia-smi CSV lines (ClockSampler.FIELDS, noheader, nounits); lines that
+    do not parse are skipped."""
+    sm, smax, reasons = [], [], set()
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm), "period_ms": 50}
 
 
 def smi_index(local: int) -> str:

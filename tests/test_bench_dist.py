@@ -109,3 +109,69 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"] == bench.WORKLOAD
+
+
+def test_clock_samples_summarized():
+    """The clock record of the timed region: median and maximum SM clock and
+    the throttle reasons that were active; lines that do not parse are
+    skipped (nvidia-smi CSV, noheader, nounits)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    idle = "0, 2070, 2070, 812.35, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1965, 2070, 1398.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    slow = "0, 1500, 2070, 1200.00, 0x0000000000000008, Active, Not Active, Not Active, Not Active"
+    r = bench.summarize_clock_samples([idle, idle, capped, "garbage", "0, [N/A], 2070, 1, 0, a, b, c, d", idle])
+    assert (r["sm_mhz"], r["sm_max_mhz"], r["reasons"], r["samples"]) == (2070.0, 2070.0, ["sw_power_cap"], 4)
+    r = bench.summarize_clock_samples([slow, capped, idle])
+    assert r["sm_mhz"] == 1965.0 and r["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    r = bench.summarize_clock_samples([])
+    assert r["sm_mhz"] is None and r["sm_max_mhz"] is None and r["reasons"] == []
+
+
+def test_profile_traffic_and_peaks(monkeypatch, tmp_path):
+    """The roofline's inputs: the headline profile's DRAM traffic per element
+    is used while the kernel sources hash as at its capture, and dropped
+    (None) once they differ; the HBM peak is the measured one when
+    MEASURED_PEAKS.json is present, else the fallback, and says which."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    per_elem = bench.read_profile_traffic("stencil_multi_256x384x384")
+    assert per_elem is not None and 4 * 5 * 0.9 < per_elem < 4 * 5 * 1.2  # five float32 outputs dominate
+    monkeypatch.setattr(bench, "csrc_hash", lambda: "0" * 64)
+    assert bench.read_profile_traffic("stencil_multi_256x384x384") is None
+    assert bench.read_profile_traffic("no_such_profile") is None
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7012.5, "bf16_tflops": 1900}))
+    assert bench.measured_peaks() == (7012.5, "measured")
+
+
+def test_clock_sampler_keeps_the_timed_region():
+    """ClockSampler.stop keeps the samples taken inside the marked region
+    (with a stand-in for the nvidia-smi process) and summarizes those."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    class _Thread:
+        def join(self, timeout=None):
+            pass
+
+    s = bench.ClockSampler(0)
+    s.proc, s.thread = _Proc(), _Thread()
+    row = "0, {}, 2070, 900.0, 0x0, Not Active, Not Active, {}, Not Active"
+    s.lines = [(0.0, row.format(1000, "Active")),  # before the region
+               (10.0, row.format(2070, "Not Active")), (10.5, row.format(2055, "Not Active")),
+               (11.0, row.format(2070, "Not Active")),
+               (99.0, row.format(900, "Active"))]  # after it
+    s.t0, s.t1 = 9.9, 11.0
+    r = s.stop()
+    assert (r["sm_mhz"], r["sm_max_mhz"], r["reasons"], r["samples"]) == (2070.0, 2070.0, [], 3)
