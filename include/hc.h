@@ -474,6 +474,43 @@ HC_API int hc_batch_graph_destroy(void* graph_exec);
  * launch since the last call).  SYNC on `stream`. */
 HC_API int hc_batch_status(void* d_ws, void* stream);
 
+/* ---------------------------------------------------------------- shards */
+/* A contiguous range of whole chunks of a stream as a stream of its own, so
+ * that ranks can each reduce a part of one field (no counterpart in the
+ * paper: with block heads (HC_PRED_DELTA) or block means (HC_PRED_MEAN) every
+ * block decodes alone, so the exact sums of Section V-A add over any
+ * partition of the blocks).  The shard of chunks [c0, c1) is a 1-D field of
+ * the elements those blocks hold, in row-major order from element `first`;
+ * every statistic of hc_op_mean / hc_op_variance runs on it unchanged, and
+ * the ranks' exact s1 and s2 add up to the whole field's.  Stencils need
+ * neighbours across the range and are not offered on shards.
+ *
+ * hc_shard_plan (host only, no device access) takes the full stream's
+ * header and a host copy of its chunk index (nchunks + 1 uint64 words, from
+ * byte hdr->off_chunks of the stream) and fills `out`: the shard's header,
+ * its 256-byte image, the three byte ranges to copy from the full stream
+ * (widths, heads, payload) and where they go, and in chunks_out (c1 - c0 + 1
+ * uint64) the shard's chunk index, rebased to its first payload word.  The
+ * caller builds the shard in a zeroed device buffer of hdr.total_bytes:
+ * header_bytes at 0, the three copies, chunks_out at chunks_off.
+ * The shard keeps the full stream's max width and max |q| as upper bounds.
+ * Errors: HC_ERR_INVALID_ARG (null pointer, c0 < 0, c1 <= c0 or c1 >
+ * nchunks), HC_ERR_CORRUPT (an inconsistent header, or a chunk index that
+ * is not ascending or does not end at the payload size), HC_ERR_UNSUPPORTED
+ * (a global-predictor or HSZx-nd stream: their blocks do not decode
+ * alone). */
+typedef struct hc_shard {
+  hc_header hdr;            /* the shard's header (ndim 1, N = its elements) */
+  uint8_t header_bytes[256];/* its image: the first 256 bytes of the shard */
+  int64_t src_off[3];       /* byte offsets in the full stream of the widths, heads and payload copied */
+  int64_t dst_off[3];       /* their byte offsets in the shard */
+  int64_t nbytes[3];        /* their sizes in bytes */
+  int64_t chunks_off;       /* byte offset of the shard's chunk index */
+  int64_t first;            /* the shard's first element in the full field (row-major) */
+} hc_shard;
+HC_API int hc_shard_plan(const hc_header* full, const uint64_t* h_chunks, int64_t c0, int64_t c1, hc_shard* out,
+                         uint64_t* chunks_out);
+
 /* ---------------------------------------------------------------- tuning */
 /* Autotuner of the fused stencil kernel (no counterpart in the paper: a GPU
  * tiling choice).  For a compressed-stream input and op (HC_OP_DERIVATIVE,

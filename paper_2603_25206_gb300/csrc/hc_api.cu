@@ -637,6 +637,94 @@ int hc_op_curl(const hc_stage* comps, int ncomp, int ndim, const int64_t* dims, 
   return vector_op(comps, ncomp, ndim, dims, d_out, out_dtype, d_ws, ws_bytes, stream, 1);
 }
 
+// ------------------------------------------------------------------ shards
+static void put_le(uint8_t* b, int off, uint64_t v, int n) {
+  for (int i = 0; i < n; ++i) b[off + i] = (uint8_t)(v >> (8 * i));
+}
+// The 256-byte image of a header, field by field as read_header_impl reads it.
+static void header_image(const hc_header& h, uint8_t* b) {
+  std::memset(b, 0, kHeaderBytes);
+  put_le(b, 0, kMagic, 4);
+  put_le(b, 4, (uint64_t)kVersion, 2);
+  put_le(b, 6, (uint64_t)h.dtype, 1);
+  put_le(b, 7, (uint64_t)h.ndim, 1);
+  for (int a = 0; a < 3; ++a) put_le(b, 8 + 8 * a, (uint64_t)h.dims[a], 8);
+  put_le(b, 32, (uint64_t)h.S, 4);
+  put_le(b, 36, (uint64_t)h.G, 4);
+  uint64_t u;
+  std::memcpy(&u, &h.eps, 8);
+  put_le(b, 40, u, 8);
+  std::memcpy(&u, &h.eb, 8);
+  put_le(b, 48, u, 8);
+  put_le(b, 56, (uint64_t)h.eb_mode, 4);
+  put_le(b, 60, h.qmax, 4);
+  put_le(b, 64, (uint64_t)h.N, 8);
+  put_le(b, 72, (uint64_t)h.nb, 8);
+  put_le(b, 80, (uint64_t)h.nchunks, 8);
+  put_le(b, 88, (uint64_t)h.payload_words, 8);
+  put_le(b, 96, (uint64_t)h.off_widths, 8);
+  put_le(b, 104, (uint64_t)h.off_heads, 8);
+  put_le(b, 112, (uint64_t)h.off_chunks, 8);
+  put_le(b, 120, (uint64_t)h.off_payload, 8);
+  put_le(b, 128, (uint64_t)h.total_bytes, 8);
+  put_le(b, 136, h.wmax, 4);
+  put_le(b, 140, h.pred, 4);
+  for (int a = 0; a < 3; ++a) put_le(b, 144 + 4 * a, h.block[a], 4);
+}
+
+int hc_shard_plan(const hc_header* full, const uint64_t* h_chunks, int64_t c0, int64_t c1, hc_shard* out,
+                  uint64_t* chunks_out) {
+  if (!full || !h_chunks || !out || !chunks_out) return fail(HC_ERR_INVALID_ARG, "null pointer");
+  int rc = check_header(*full);
+  if (rc) return rc;
+  if (full->pred != HC_PRED_DELTA && full->pred != HC_PRED_MEAN)
+    return fail(HC_ERR_UNSUPPORTED, "only block-head and block-mean streams shard: their blocks decode alone");
+  if (c0 < 0 || c1 <= c0 || c1 > full->nchunks) return fail(HC_ERR_INVALID_ARG, "chunk range must be 0 <= c0 < c1 <= nchunks");
+  if (h_chunks[0] != 0 || h_chunks[full->nchunks] != (uint64_t)full->payload_words)
+    return fail(HC_ERR_CORRUPT, "chunk index does not run from 0 to the payload size");
+  for (int64_t c = 0; c < full->nchunks; ++c)
+    if (h_chunks[c] > h_chunks[c + 1]) return fail(HC_ERR_CORRUPT, "chunk index not ascending");
+  const int64_t G = full->G, S = full->S;
+  const int64_t b0 = c0 * G, b1 = std::min<int64_t>(c1 * G, full->nb);
+  const int64_t first = b0 * S, n = std::min<int64_t>(b1 * S, full->N) - first;
+  Layout L;
+  rc = make_layout(1, &n, (int)S, &L);
+  if (rc) return rc;
+  if (L.nb != b1 - b0 || L.nchunks != c1 - c0 || L.G != G) return fail(HC_ERR_CORRUPT, "shard layout mismatch");
+  const uint64_t w0 = h_chunks[c0], w1 = h_chunks[c1];
+  hc_header h = *full;
+  h.ndim = 1;
+  h.dims[0] = h.dims[1] = 1;
+  h.dims[2] = n;
+  h.N = n;
+  h.nb = L.nb;
+  h.nchunks = L.nchunks;
+  h.off_widths = L.off_widths;
+  h.off_heads = L.off_heads;
+  h.off_chunks = L.off_chunks;
+  h.off_payload = L.off_payload;
+  h.payload_words = (int64_t)(w1 - w0);
+  h.total_bytes = align16(L.off_payload + 4 * h.payload_words + 16);
+  h.block[0] = h.block[1] = h.block[2] = 0;
+  rc = check_header(h);
+  if (rc) return rc;
+  out->hdr = h;
+  header_image(h, out->header_bytes);
+  out->src_off[0] = full->off_widths + b0;
+  out->dst_off[0] = h.off_widths;
+  out->nbytes[0] = b1 - b0;
+  out->src_off[1] = full->off_heads + 4 * b0;
+  out->dst_off[1] = h.off_heads;
+  out->nbytes[1] = 4 * (b1 - b0);
+  out->src_off[2] = full->off_payload + 4 * (int64_t)w0;
+  out->dst_off[2] = h.off_payload;
+  out->nbytes[2] = 4 * h.payload_words;
+  out->chunks_off = h.off_chunks;
+  out->first = first;
+  for (int64_t k = 0; k <= c1 - c0; ++k) chunks_out[k] = h_chunks[c0 + k] - w0;
+  return HC_OK;
+}
+
 size_t hc_batch_plan_bytes(int n_items) { return (size_t)batch_plan_bytes(n_items); }
 size_t hc_batch_workspace_bytes(int n_items) { return (size_t)batch_ws_bytes(n_items); }
 int hc_batch_plan(const hc_batch_item* items, int n_items, const hc_batch_tune* tune, void* h_plan, size_t cap,

@@ -52,6 +52,7 @@ ABI_FUNCTIONS = (
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
     "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for", "hc_compress_bound_nd",
     "hc_compress_workspace_bytes_nd", "hc_compress_nd", "hc_compress_codes_nd", "hc_vector_workspace_bytes",
+    "hc_shard_plan",
 )
 HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA, HC_PRED_MEAN_ND = 0, 1, 2, 3, 4
 # "delta": HSZp with block heads; "mean": HSZx; "lorenzo": HSZp-nd (Lorenzo over
@@ -102,6 +103,12 @@ class HcMultiOut(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class HcShard(ctypes.Structure):
+    _fields_ = [("hdr", HcHeader), ("header_bytes", ctypes.c_uint8 * 256), ("src_off", ctypes.c_int64 * 3),
+                ("dst_off", ctypes.c_int64 * 3), ("nbytes", ctypes.c_int64 * 3), ("chunks_off", ctypes.c_int64),
+                ("first", ctypes.c_int64)]
+
+
 class HcBatchTune(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ty", ctypes.c_int32), ("unit_elems", ctypes.c_int64),
                 ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -139,6 +146,7 @@ def lib():
             "hc_workspace_bytes_for": ([P(HcHeader)], sz),
             "hc_compress_bound_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
             "hc_vector_workspace_bytes": ([P(HcStage), i32], sz),
+            "hc_shard_plan": ([P(HcHeader), vp, i64, i64, P(HcShard), vp], i32),
             "hc_compress_workspace_bytes_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
             "hc_compress_nd": ([vp, i32, i32, P(ctypes.c_int64), P(ctypes.c_int32), dbl, i32, vp, sz, vp, sz, P(sz),
                                 P(HcHeader), vp], i32),
@@ -385,6 +393,58 @@ def from_stream(stream_tensor, stream=None) -> Compressed:
     _check(lib().hc_read_header(ctypes.c_void_p(stream_tensor.data_ptr()), stream_tensor.numel(),
                                 ctypes.byref(hdr), _stream_ptr(stream)))
     return Compressed(stream_tensor, hdr, int(hdr.total_bytes))
+
+
+def shard_range(nchunks: int, rank: int, world: int):
+    """Chunks [c0, c1) of rank `rank` of `world`: contiguous, balanced, in
+    rank order (empty when there are more ranks than chunks)."""
+    if not (0 <= rank < world):
+        raise ValueError("rank must be in [0, world)")
+    return rank * nchunks // world, (rank + 1) * nchunks // world
+
+
+def shard_plan(header: HcHeader, chunks, c0: int, c1: int):
+    """hc_shard_plan on a host copy of the chunk index (uint64 array of
+    nchunks + 1 words): the shard's HcShard and its rebased chunk index."""
+    chunks = np.ascontiguousarray(chunks, dtype=np.uint64)
+    if chunks.size != int(header.nchunks) + 1:
+        raise ValueError("the chunk index has nchunks + 1 words")
+    plan = HcShard()
+    out = np.empty(c1 - c0 + 1 if c1 > c0 else 1, np.uint64)
+    _check(lib().hc_shard_plan(ctypes.byref(header), ctypes.c_void_p(chunks.ctypes.data), int(c0), int(c1),
+                               ctypes.byref(plan), ctypes.c_void_p(out.ctypes.data)))
+    return plan, out
+
+
+def shard(c: Compressed, rank: int, world: int, stream=None):
+    """The part of c that rank `rank` of `world` reduces: a stream of its own
+    made of contiguous whole chunks (hc_shard_plan), built on c's device with
+    copies only.  None when the rank has no chunk.  The statistics of the
+    ranks' shards add up exactly to those of c (paper_2603_25206_gb300.shard
+    combines them across ranks)."""
+    torch = _torch()
+    c0, c1 = shard_range(int(c.header.nchunks), rank, world)
+    if c1 <= c0:
+        return None
+    off = int(c.header.off_chunks)
+    n_idx = int(c.header.nchunks) + 1
+    s = torch.cuda.current_stream(c.stream.device) if stream is None else stream
+    with torch.cuda.stream(s):
+        chunks = c.stream[off:off + 8 * n_idx].cpu().numpy().view(np.uint64)
+        plan, rebased = shard_plan(c.header, chunks, c0, c1)
+        total = int(plan.hdr.total_bytes)
+        out = torch.zeros(total, dtype=torch.uint8, device=c.stream.device)
+        out[:256] = torch.from_numpy(np.frombuffer(bytes(plan.header_bytes), np.uint8).copy()).to(out.device)
+        for k in range(3):
+            n = int(plan.nbytes[k])
+            if n:
+                so, do = int(plan.src_off[k]), int(plan.dst_off[k])
+                out[do:do + n].copy_(c.stream[so:so + n])
+        co = int(plan.chunks_off)
+        out[co:co + 8 * rebased.size] = torch.from_numpy(rebased.view(np.uint8).copy()).to(out.device)
+    hdr = HcHeader()
+    ctypes.memmove(ctypes.byref(hdr), ctypes.byref(plan.hdr), ctypes.sizeof(HcHeader))
+    return Compressed(out, hdr, total)
 
 
 def decompress(c: Compressed, stage: str = "f", out=None, out_dtype=None, stream=None):

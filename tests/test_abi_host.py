@@ -63,6 +63,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(hc_batch_tune), offsetof(hc_batch_tune, unit_elems), offsetof(hc_batch_tune, ctas_per_sm));
   printf("%zu %zu %zu\n", sizeof(hc_multi_out), offsetof(hc_multi_out, d_stats), offsetof(hc_multi_out, out_dtype));
   printf("%zu %zu %zu\n", offsetof(hc_header, pred), offsetof(hc_header, block), offsetof(hc_stage, pred));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(hc_shard), offsetof(hc_shard, header_bytes), offsetof(hc_shard, src_off),
+         offsetof(hc_shard, nbytes), offsetof(hc_shard, chunks_off), offsetof(hc_shard, first));
   return 0;
 }
 """
@@ -85,6 +87,9 @@ int main(void) {
     M = hc.HcMultiOut
     assert vals[22:25] == [ctypes.sizeof(M), M.d_stats.offset, M.out_dtype.offset]
     assert vals[25:28] == [H.pred.offset, H.block.offset, St.pred.offset]
+    Sh = hc.HcShard
+    assert vals[28:34] == [ctypes.sizeof(Sh), Sh.header_bytes.offset, Sh.src_off.offset, Sh.nbytes.offset,
+                           Sh.chunks_off.offset, Sh.first.offset]
 
 
 def test_plain_c_program_links_and_calls_the_library(hc, orc):
