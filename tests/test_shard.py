@@ -223,3 +223,51 @@ def test_gloo_ranks_combine_to_the_whole_field(hc, orc, rng):
     for rank, tot, stats in got:
         assert tot == (s1, s2, q.size)
         assert stats[:2] == want_stats[:2]
+
+
+def test_binding_shard_builds_the_planned_streams(hc, orc, rng, monkeypatch):
+    """hc.shard, run on CPU tensors (a stand-in replaces torch.cuda's stream
+    calls), builds for every rank the stream the plan describes: the oracle
+    decodes each to its slice of the codes, the slices tile the field in rank
+    order, and a rank without chunks gets None."""
+    import contextlib
+
+    import torch
+
+    class _Cuda:
+        @staticmethod
+        def current_stream(device=None):
+            return None
+
+        @staticmethod
+        def stream(s):
+            return contextlib.nullcontext()
+
+    class _Torch:
+        cuda = _Cuda
+
+        def __getattr__(self, name):
+            return getattr(torch, name)
+
+    monkeypatch.setattr(hc, "_torch", lambda: _Torch())
+    for pred in (0, 1):
+        x = _field(rng, 4096 * 5 + 300, np.float32)
+        s, eps = orc.compress(x, 1e-3, True, 32, pred=pred)
+        h = _header_from_oracle_stream(hc, orc, s)
+        c = hc.Compressed(torch.from_numpy(np.concatenate([s, np.zeros(64, np.uint8)])), h, int(s.size))
+        q = orc.decode(s, "q").reshape(-1)
+        for world in (1, 2, 4, 9):
+            pos = 0
+            for rank in range(world):
+                sh = hc.shard(c, rank, world)
+                c0, c1 = hc.shard_range(int(h.nchunks), rank, world)
+                if c1 <= c0:
+                    assert sh is None
+                    continue
+                b = sh.stream.numpy()
+                assert b.size == sh.nbytes == int(sh.header.total_bytes)
+                assert orc.read_header(b)["N"] == int(sh.header.N)
+                qs = orc.decode(b, "q")
+                np.testing.assert_array_equal(qs, q[pos:pos + qs.size])
+                pos += qs.size
+            assert pos == q.size
