@@ -26,7 +26,8 @@
  *    (read it with hc_workspace_status).  Kernels never read outside the
  *    stream, whatever its content.
  *  - A host hc_header passed by the caller (hc_decompress_to_stage, an
- *    hc_stage of kind HC_STAGE_COMPRESSED, hc_autotune, hc_batch_plan) is
+ *    hc_stage of kind HC_STAGE_COMPRESSED, hc_autotune, hc_batch_plan,
+ *    hc_shard_plan) is
  *    checked on the host before anything is enqueued: its section offsets,
  *    sizes, block or box extents, width, eps and max |q| must follow from
  *    its shape and block size, else HC_ERR_CORRUPT.  The header must still
