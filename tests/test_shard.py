@@ -10,7 +10,6 @@ decodes every shard to exactly its slice; the ranks' exact sums add up to
 the whole field's, and the combined mean / variance / std equal the
 oracle's bit for bit.
 """
-import ctypes
 import os
 import sys
 
@@ -165,7 +164,7 @@ def test_finalize_matches_the_oracle_bit_for_bit(orc, rng):
         assert shard.finalize(n, s1, s2, eps)[:2] == orc.finalize(n, s1, s2, eps)[:2] or n < 2
 
 
-def _rank_worker(rank, world, port, streams, q_all, eps, out):
+def _rank_worker(rank, world, port, streams, eps, out):
     os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
     sys.path.insert(0, ROOT)
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -213,7 +212,7 @@ def test_gloo_ranks_combine_to_the_whole_field(hc, orc, rng):
     sock.close()
     ctx = mp.get_context("spawn")
     out = ctx.Queue()
-    ps = [ctx.Process(target=_rank_worker, args=(r, world, port, streams, None, eps, out)) for r in range(world)]
+    ps = [ctx.Process(target=_rank_worker, args=(r, world, port, streams, eps, out)) for r in range(world)]
     for p in ps:
         p.start()
     for p in ps:
