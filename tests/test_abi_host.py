@@ -26,8 +26,6 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def hc():
-    import __graft_entry__
-
     from paper_2603_25206_gb300 import build as b
 
     b.build()

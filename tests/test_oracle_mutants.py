@@ -18,8 +18,6 @@ import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
 
-import pytest
-
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "hc_oracle.c")
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")

@@ -11,7 +11,6 @@ GPU tests.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
