@@ -235,6 +235,13 @@ HC_API int hc_compress_codes_nd(const int32_t* d_q, int dtype, int ndim, const i
  * validate it (magic, version, shape, section offsets, total size against
  * `bytes`).  SYNC. */
 HC_API int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out, void* stream);
+/* The same checks on a stream held in HOST memory (a file read back, a
+ * buffer received from another process): h_stream holds `bytes` bytes of the
+ * stream, at least its 256-byte header.  No device access; the stream is the
+ * persistent form of the compressed field (Section III-A: c = C(d, eps)),
+ * so saving it is writing its total_bytes and loading it is this check
+ * followed by a copy to the device.  Errors as hc_read_header. */
+HC_API int hc_read_header_host(const void* h_stream, size_t bytes, hc_header* hdr_out);
 
 /* ---------------------------------------------------------- decompression */
 /* D_i ... D_1 (Algorithm 2): decode the whole stream to stage `kind`:

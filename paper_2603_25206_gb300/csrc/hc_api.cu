@@ -180,13 +180,10 @@ int check_header(const hc_header& h) {
   return HC_OK;
 }
 
-int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st) {
-  if (!d_stream || !out) return fail(HC_ERR_INVALID_ARG, "null pointer");
-  if (bytes < (size_t)kHeaderBytes) return fail(HC_ERR_CORRUPT, "stream shorter than its header");
-  uint8_t b[kHeaderBytes];
-  if (cudaMemcpyAsync(b, d_stream, kHeaderBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+// The header image b (kHeaderBytes bytes, host memory) of a stream of `bytes`
+// bytes: parsed field by field, checked, and refused if the stream is shorter
+// than the header says.
+static int parse_header_image(const uint8_t* b, size_t bytes, hc_header* out) {
   if (le(b, 0, 4) != kMagic || le(b, 4, 2) != (uint64_t)kVersion) return fail(HC_ERR_CORRUPT, "bad magic or version");
   hc_header h;
   std::memset(&h, 0, sizeof h);
@@ -217,6 +214,22 @@ int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStr
   if ((size_t)h.total_bytes > bytes) return fail(HC_ERR_CORRUPT, "stream truncated");
   *out = h;
   return HC_OK;
+}
+
+int read_header_impl(const void* d_stream, size_t bytes, hc_header* out, cudaStream_t st) {
+  if (!d_stream || !out) return fail(HC_ERR_INVALID_ARG, "null pointer");
+  if (bytes < (size_t)kHeaderBytes) return fail(HC_ERR_CORRUPT, "stream shorter than its header");
+  uint8_t b[kHeaderBytes];
+  if (cudaMemcpyAsync(b, d_stream, kHeaderBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(HC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  return parse_header_image(b, bytes, out);
+}
+
+static int read_header_host_impl(const void* h_stream, size_t bytes, hc_header* out) {
+  if (!h_stream || !out) return fail(HC_ERR_INVALID_ARG, "null pointer");
+  if (bytes < (size_t)kHeaderBytes) return fail(HC_ERR_CORRUPT, "stream shorter than its header");
+  return parse_header_image(reinterpret_cast<const uint8_t*>(h_stream), bytes, out);
 }
 
 }  // namespace hc
@@ -397,6 +410,10 @@ int hc_compress_codes_nd(const int32_t* d_q, int dtype, int ndim, const int64_t*
 
 int hc_read_header(const void* d_stream, size_t bytes, hc_header* hdr_out, void* stream) {
   return read_header_impl(d_stream, bytes, hdr_out, as_stream(stream));
+}
+
+int hc_read_header_host(const void* h_stream, size_t bytes, hc_header* hdr_out) {
+  return read_header_host_impl(h_stream, bytes, hdr_out);
 }
 
 int hc_decompress_to_stage(const hc_header* hdr, const void* d_stream, int kind, void* d_out, int out_dtype,

@@ -52,7 +52,7 @@ ABI_FUNCTIONS = (
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
     "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for", "hc_compress_bound_nd",
     "hc_compress_workspace_bytes_nd", "hc_compress_nd", "hc_compress_codes_nd", "hc_vector_workspace_bytes",
-    "hc_shard_plan",
+    "hc_shard_plan", "hc_read_header_host",
 )
 HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA, HC_PRED_MEAN_ND = 0, 1, 2, 3, 4
 # "delta": HSZp with block heads; "mean": HSZx; "lorenzo": HSZp-nd (Lorenzo over
@@ -147,6 +147,7 @@ def lib():
             "hc_compress_bound_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
             "hc_vector_workspace_bytes": ([P(HcStage), i32], sz),
             "hc_shard_plan": ([P(HcHeader), vp, i64, i64, P(HcShard), vp], i32),
+            "hc_read_header_host": ([vp, sz, P(HcHeader)], i32),
             "hc_compress_workspace_bytes_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
             "hc_compress_nd": ([vp, i32, i32, P(ctypes.c_int64), P(ctypes.c_int32), dbl, i32, vp, sz, vp, sz, P(sz),
                                 P(HcHeader), vp], i32),
@@ -393,6 +394,39 @@ def from_stream(stream_tensor, stream=None) -> Compressed:
     _check(lib().hc_read_header(ctypes.c_void_p(stream_tensor.data_ptr()), stream_tensor.numel(),
                                 ctypes.byref(hdr), _stream_ptr(stream)))
     return Compressed(stream_tensor, hdr, int(hdr.total_bytes))
+
+
+def header_of(data) -> HcHeader:
+    """The checked header of a stream held in host memory (bytes, bytearray
+    or a uint8 numpy array holding the whole stream): hc_read_header_host."""
+    arr = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
+                               dtype=np.uint8)
+    hdr = HcHeader()
+    _check(lib().hc_read_header_host(ctypes.c_void_p(arr.ctypes.data), arr.size, ctypes.byref(hdr)))
+    return hdr
+
+
+def save(c: Compressed, path: str) -> int:
+    """Write the stream of c (its total_bytes, header first) to `path`; the
+    file is the persistent form of the compressed field.  Returns the bytes
+    written."""
+    data = c.stream[: c.nbytes].cpu().numpy()
+    with open(path, "wb") as f:
+        f.write(data.tobytes())
+    return int(data.size)
+
+
+def load(path: str, device=None) -> Compressed:
+    """Read a stream written by save (or by any producer of the same format),
+    check its header on the host, and put it on `device` (default: the current
+    CUDA device)."""
+    torch = _torch()
+    data = np.fromfile(path, dtype=np.uint8)
+    hdr = header_of(data)
+    n = int(hdr.total_bytes)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    t = torch.from_numpy(data[:n].copy()).to(dev)
+    return Compressed(t, hdr, n)
 
 
 def shard_range(nchunks: int, rank: int, world: int):

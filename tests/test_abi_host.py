@@ -561,3 +561,53 @@ def test_empty_and_oversized_fields_refused_on_the_host(hc):
         assert rc == hc.HC_ERR_INVALID_ARG and msg in L.hc_last_error(), blk
     assert int(L.hc_compress_bound(0, 32)) == 0 and int(L.hc_compress_bound(-5, 32)) == 0
     assert int(L.hc_compress_bound(1 << 41, 32)) == 0
+
+
+def test_host_header_reader_and_save_load(hc, orc, rng, tmp_path):
+    """hc_read_header_host (the parser hc_read_header shares) reads every
+    predictor's stream header as the oracle writes it, refuses corrupt and
+    truncated images, and save / load round-trip a stream through a file
+    (here on CPU tensors: the file format is the stream itself)."""
+    import numpy as np
+    import torch
+
+    x = rng.standard_normal((9, 20, 48)).astype(np.float32)
+    streams = [orc.compress(x, 1e-3, True, 32, pred=p)[0] for p in (0, 1, 2, 3)]
+    streams.append(orc.compress_nd(x, (3, 4, 8), 1e-3, True)[0])
+    streams.append(orc.compress(x.astype(np.float64).reshape(-1), 1e-4, False, 100)[0])
+    for s in streams:
+        want = _header_from_oracle_stream(hc, orc, s)
+        got = hc.header_of(s)
+        for name, _ in hc.HcHeader._fields_:
+            a, b = getattr(got, name), getattr(want, name)
+            if hasattr(a, "_length_"):
+                a, b = list(a), list(b)
+            assert a == b, name
+        assert hc.header_of(bytes(s)).total_bytes == s.size
+        for bad, why in ((s[:255], "shorter than its header"), (s[:-16], "truncated")):
+            with pytest.raises(hc.HcError) as e:
+                hc.header_of(bad)
+            assert e.value.status == hc.HC_ERR_CORRUPT and why in str(e.value)
+        for off in (0, 72, 128):  # magic, nb, total size
+            bad = s.copy()
+            bad[off] ^= 0x01
+            with pytest.raises(hc.HcError) as e:
+                hc.header_of(bad)
+            assert e.value.status == hc.HC_ERR_CORRUPT
+        c = hc.Compressed(torch.from_numpy(np.concatenate([s, np.zeros(48, np.uint8)])), got, int(s.size))
+        path = str(tmp_path / "field.hcz")
+        assert hc.save(c, path) == s.size
+        assert open(path, "rb").read() == s.tobytes()
+        back = hc.load(path, device="cpu")
+        assert back.nbytes == s.size and np.array_equal(back.stream.numpy(), s)
+        assert bytes(back.header) == bytes(got)
+    # a shard's header image is a stream header the library itself accepts
+    s = streams[0]
+    h = hc.header_of(s)
+    r16 = lambda v: (v + 15) & ~15  # noqa: E731
+    off = r16(r16(256 + h.nb) + 4 * h.nb)
+    chunks = np.frombuffer(s[off:off + 8 * (h.nchunks + 1)].tobytes(), np.uint64)
+    plan, _ = hc.shard_plan(h, chunks, 0, int(h.nchunks))
+    img = np.zeros(int(plan.hdr.total_bytes), np.uint8)
+    img[:256] = np.frombuffer(bytes(plan.header_bytes), np.uint8)
+    assert bytes(hc.header_of(img)) == bytes(plan.hdr)
