@@ -131,12 +131,24 @@ class Scheduler:
         self.in_flight -= 1
 
 
-def serve(queries, executor, scheduler: Scheduler, clock=time.perf_counter, idle=None):
+class StepTimeout(RuntimeError):
+    """A step stayed in flight longer than serve's step_timeout.  Its memory
+    and slot stay reserved (the device may still be using them); the caller
+    decides whether to wait longer or to abandon the device."""
+
+    def __init__(self, step: int, qids, waited: float):
+        super().__init__(f"step {step} (queries {list(qids)}) still in flight after {waited:.3f} s")
+        self.step, self.qids, self.waited = step, list(qids), waited
+
+
+def serve(queries, executor, scheduler: Scheduler, clock=time.perf_counter, idle=None, step_timeout=None):
     """Run the arrival stream through the scheduler and executor.  Returns
     the records of the completed queries in completion order.
 
     executor.launch(batch) -> handle; executor.done(handle) -> bool;
-    executor.results(handle) -> list of per-query results (or Nones)."""
+    executor.results(handle) -> list of per-query results (or Nones).
+    Every wait for a step is a poll; with step_timeout (seconds) a step still
+    in flight that long raises StepTimeout instead of being polled forever."""
     queries = sorted(queries, key=lambda q: q.t_arrive)
     n = len(queries)
     t0 = clock()
@@ -158,6 +170,9 @@ def serve(queries, executor, scheduler: Scheduler, clock=time.perf_counter, idle
                     records.append(Record(q.qid, q.t_arrive, t_admit, t_done, k, r))
                 scheduler.finish(mem)
             else:
+                waited = clock() - t0 - t_admit
+                if step_timeout is not None and waited > step_timeout:
+                    raise StepTimeout(k, [q.qid for q in batch], waited)
                 keep.append((h, batch, mem, t_admit, k))
         inflight = keep
         while True:

@@ -112,3 +112,23 @@ def test_summary_percentiles():
     assert s["qps"] == pytest.approx(100 / 0.1)
     assert s["orig_gbs"] == pytest.approx((50 * 4000 + 50 * 8000) / 0.1 / 1e9)
     assert s["steps"] == 10 and s["mean_batch"] == 10
+
+
+def test_step_timeout_raises_instead_of_polling_forever():
+    """A step whose completion never comes (its event never fires) ends the
+    loop with StepTimeout after step_timeout seconds, naming the step and its
+    queries; without a timeout nothing changes for steps that finish."""
+    class Stuck(FakeExecutor):
+        def done(self, h):
+            return False if h == 1 else super().done(h)
+
+    qs = [serving.Query(i, 1e-3 * i, 0, "mean", "q") for i in range(3)]
+    clk = FakeClock(tick=1e-4)
+    ex = Stuck(clk, base=1e-4, per_query=0.0)
+    sch = serving.Scheduler(10_000, 4, 1, lambda q: 100)
+    with pytest.raises(serving.StepTimeout) as e:
+        serving.serve(qs, ex, sch, clock=clk, step_timeout=0.05)
+    assert e.value.step == 1 and e.value.qids == [1] and 0.05 < e.value.waited < 0.06
+    assert sch.in_flight >= 1  # the stuck step keeps its slot and memory
+    recs, sch2, _ = _run(qs)
+    assert sorted(r.qid for r in recs) == [0, 1, 2]
