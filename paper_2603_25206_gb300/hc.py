@@ -397,10 +397,13 @@ def from_stream(stream_tensor, stream=None) -> Compressed:
 
 
 def header_of(data) -> HcHeader:
-    """The checked header of a stream held in host memory (bytes, bytearray
-    or a uint8 numpy array holding the whole stream): hc_read_header_host."""
-    arr = np.ascontiguousarray(np.frombuffer(data, np.uint8) if isinstance(data, (bytes, bytearray)) else data,
-                               dtype=np.uint8)
+    """The checked header of a stream held in host memory (bytes, bytearray,
+    memoryview or a numpy array holding the whole stream, read as its raw
+    bytes whatever its dtype): hc_read_header_host."""
+    if isinstance(data, np.ndarray):
+        arr = np.ascontiguousarray(data).reshape(-1).view(np.uint8)
+    else:
+        arr = np.frombuffer(memoryview(data).cast("B"), np.uint8)
     hdr = HcHeader()
     _check(lib().hc_read_header_host(ctypes.c_void_p(arr.ctypes.data), arr.size, ctypes.byref(hdr)))
     return hdr

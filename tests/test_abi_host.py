@@ -584,6 +584,9 @@ def test_host_header_reader_and_save_load(hc, orc, rng, tmp_path):
                 a, b = list(a), list(b)
             assert a == b, name
         assert hc.header_of(bytes(s)).total_bytes == s.size
+        assert hc.header_of(memoryview(bytearray(s))).total_bytes == s.size
+        padded = np.concatenate([s, np.zeros((-s.size) % 8, np.uint8)])
+        assert bytes(hc.header_of(padded.view(np.uint64))) == bytes(got)  # raw bytes, not converted values
         for bad, why in ((s[:255], "shorter than its header"), (s[:-16], "truncated")):
             with pytest.raises(hc.HcError) as e:
                 hc.header_of(bad)
