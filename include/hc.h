@@ -304,9 +304,10 @@ HC_API int hc_op_std(const hc_stage* in, double eps, int ndim, const int64_t* di
 
 /* Allocation-free fused variance (the paper has no counterpart: this is an
  * interface for callers, not a method step).  For callers that cannot
- * allocate device memory when they need the statistic -- code inside a CUDA
- * graph capture, allocation-free real-time loops, plugins handed only a stream
- * and pointers by a host application that owns all memory -- it computes what
+ * allocate device memory when they need the statistic -- allocation-free
+ * real-time loops, whose latency budget leaves no room for an allocator call,
+ * and plugins handed only a stream and pointers by a host application that
+ * owns all device memory and gives out no allocator -- it computes what
  * hc_op_variance computes for a compressed-stream input (level P or Q), but
  * takes no workspace: its scratch is a static device array inside libhc.so of
  * 64 KiB + 256 bytes (one ticket counter and 2048 per-CTA partial sums), held
@@ -518,6 +519,21 @@ typedef struct hc_shard {
 } hc_shard;
 HC_API int hc_shard_plan(const hc_header* full, const uint64_t* h_chunks, int64_t c0, int64_t c1, hc_shard* out,
                          uint64_t* chunks_out);
+
+/* The final scaling of Eq. var_q (Section V-A) on the host, from exact sums:
+ * s1 = sum q (int64) and s2 = sum q^2 (128 bits: s2_hi * 2^64 + s2_lo) over
+ * n codes quantized with bound eps -- for example the totals of several
+ * shards' hc_scalar results, added exactly.  Fills *out (HOST memory) as a
+ * fused statistic's device finish does, with the same integer arithmetic and
+ * the same roundings, so the values are bit-equal to a one-launch result:
+ *   mean = ((double)s1 / N) * 2 eps,
+ *   variance = ((double)(N s2 - s1^2) / (N (N - 1))) * (2 eps)^2, the
+ *     128-bit numerator converted once (round to nearest even),
+ *   std = sqrt(variance); variance and std are NaN for N = 1;
+ *   n, s1, s2_lo, s2_hi copied; status = HC_OK; exact = 1.
+ * No device access.  Errors: HC_ERR_INVALID_ARG for out == NULL, n < 1, or
+ * eps not positive and finite (nothing written then). */
+HC_API int hc_finalize(int64_t n, int64_t s1, uint64_t s2_lo, uint64_t s2_hi, double eps, hc_scalar* out);
 
 /* ---------------------------------------------------------------- tuning */
 /* Autotuner of the fused stencil kernel (no counterpart in the paper: a GPU

@@ -742,6 +742,38 @@ int hc_shard_plan(const hc_header* full, const uint64_t* h_chunks, int64_t c0, i
   return HC_OK;
 }
 
+// Eq. var_q on the host: the same integer arithmetic and the same rounding
+// steps as finalize_int, the device finish of every exact statistic (each
+// integer converted to double once, round to nearest even; the 128-bit
+// numerator N s2 - s1^2 formed with the same wrapping 128-bit products).
+int hc_finalize(int64_t n, int64_t s1, uint64_t s2_lo, uint64_t s2_hi, double eps, hc_scalar* out) {
+  if (!out) return fail(HC_ERR_INVALID_ARG, "null output");
+  if (n < 1) return fail(HC_ERR_INVALID_ARG, "N must be at least 1");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(HC_ERR_INVALID_ARG, "eps must be positive and finite");
+  typedef unsigned __int128 u128h;
+  typedef __int128 i128h;
+  const u128h s2 = ((u128h)s2_hi << 64) | (u128h)s2_lo;
+  const double two_eps = 2.0 * eps;
+  hc_scalar r;
+  r.n = n;
+  r.s1 = s1;
+  r.s2_lo = s2_lo;
+  r.s2_hi = s2_hi;
+  r.status = HC_OK;
+  r.exact = 1;
+  r.mean = ((double)s1 / (double)n) * two_eps;
+  double v = std::nan("");
+  if (n >= 2) {
+    const i128h num = (i128h)((u128h)(i128h)n * s2 - (u128h)((i128h)s1 * (i128h)s1));
+    const double den = (double)n * (double)(n - 1);
+    v = ((double)num / den) * (two_eps * two_eps);
+  }
+  r.variance = v;
+  r.std = std::sqrt(v);
+  *out = r;
+  return HC_OK;
+}
+
 size_t hc_batch_plan_bytes(int n_items) { return (size_t)batch_plan_bytes(n_items); }
 size_t hc_batch_workspace_bytes(int n_items) { return (size_t)batch_ws_bytes(n_items); }
 int hc_batch_plan(const hc_batch_item* items, int n_items, const hc_batch_tune* tune, void* h_plan, size_t cap,

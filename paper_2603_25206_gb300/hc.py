@@ -52,7 +52,7 @@ ABI_FUNCTIONS = (
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
     "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for", "hc_compress_bound_nd",
     "hc_compress_workspace_bytes_nd", "hc_compress_nd", "hc_compress_codes_nd", "hc_vector_workspace_bytes",
-    "hc_shard_plan", "hc_read_header_host",
+    "hc_shard_plan", "hc_read_header_host", "hc_finalize",
 )
 HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA, HC_PRED_MEAN_ND = 0, 1, 2, 3, 4
 # "delta": HSZp with block heads; "mean": HSZx; "lorenzo": HSZp-nd (Lorenzo over
@@ -148,6 +148,7 @@ def lib():
             "hc_vector_workspace_bytes": ([P(HcStage), i32], sz),
             "hc_shard_plan": ([P(HcHeader), vp, i64, i64, P(HcShard), vp], i32),
             "hc_read_header_host": ([vp, sz, P(HcHeader)], i32),
+            "hc_finalize": ([i64, i64, ctypes.c_uint64, ctypes.c_uint64, dbl, vp], i32),
             "hc_compress_workspace_bytes_nd": ([i32, P(ctypes.c_int64), P(ctypes.c_int32)], sz),
             "hc_compress_nd": ([vp, i32, i32, P(ctypes.c_int64), P(ctypes.c_int32), dbl, i32, vp, sz, vp, sz, P(sz),
                                 P(HcHeader), vp], i32),
@@ -523,6 +524,19 @@ def parse_scalar(buf) -> dict:
     d = {k: raw[k].item() for k in _SCALAR_DTYPE.names}
     d["s2"] = (int(d.pop("s2_hi")) << 64) | int(d.pop("s2_lo"))
     return d
+
+
+def finalize(n: int, s1: int, s2: int, eps: float) -> dict:
+    """Eq. var_q's final scaling of exact sums (s1 = sum q, s2 = sum q^2 as a
+    Python int below 2^128) over n codes, computed by the library on the host
+    (hc_finalize: the device finish's arithmetic and roundings); returns the
+    parsed hc_scalar."""
+    if not (0 <= s2 < (1 << 128)):
+        raise ValueError("s2 must be a non-negative 128-bit integer")
+    buf = ctypes.create_string_buffer(SCALAR_BYTES)
+    _check(lib().hc_finalize(int(n), int(s1), s2 & ((1 << 64) - 1), s2 >> 64, float(eps),
+                             ctypes.cast(buf, ctypes.c_void_p)))
+    return parse_scalar(buf.raw)
 
 
 def _stat(fn_name, inp, level, out, stream):

@@ -9,12 +9,11 @@ unsigned 32-bit limbs, each rank's limbs are summed as int64 (no overflow for
 fewer than 2^31 ranks), and the carries are resolved in Python integers.  The
 result does not depend on the order of the ranks, the backend or the
 partition: every rank gets the whole field's s1 and s2 bit for bit, and
-`finalize` scales them with the same rounding steps as the library's own
-last-CTA finish, so the mean, variance and std equal a one-GPU reduction's.
+`finalize` has the library scale them (hc_finalize: the arithmetic of its
+own last-CTA finish), so the mean, variance and std equal a one-GPU
+reduction's.
 """
 from __future__ import annotations
-
-import math
 
 LIMB = 32
 _MASK = (1 << LIMB) - 1
@@ -51,13 +50,11 @@ def allreduce_exact(s1: int, s2: int, n: int, group=None, device=None) -> tuple:
 
 
 def finalize(n: int, s1: int, s2: int, eps: float) -> tuple:
-    """(mean, variance, std) from the exact sums (Eq. var_q):
-    mean = (s1 / N) * 2 eps, variance = ((N s2 - s1^2) / (N (N - 1))) * (2 eps)^2,
-    each integer converted to double once with round-to-nearest, as the
-    library's finish does.  N < 2 gives NaN variance and std."""
-    two_eps = 2.0 * eps
-    mean = (float(s1) / float(n)) * two_eps
-    if n < 2:
-        return mean, math.nan, math.nan
-    var = (float(n * s2 - s1 * s1) / (float(n) * float(n - 1))) * (two_eps * two_eps)
-    return mean, var, math.sqrt(var)
+    """(mean, variance, std) from the exact sums (Eq. var_q), scaled by the
+    library (hc_finalize, host code with the device finish's arithmetic and
+    roundings), so they equal a one-launch reduction's bit for bit.  N < 2
+    gives NaN variance and std."""
+    from . import hc
+
+    r = hc.finalize(n, s1, s2, eps)
+    return r["mean"], r["variance"], r["std"]

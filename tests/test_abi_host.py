@@ -614,3 +614,40 @@ def test_host_header_reader_and_save_load(hc, orc, rng, tmp_path):
     img = np.zeros(int(plan.hdr.total_bytes), np.uint8)
     img[:256] = np.frombuffer(bytes(plan.header_bytes), np.uint8)
     assert bytes(hc.header_of(img)) == bytes(plan.hdr)
+
+
+def test_finalize_on_the_host_matches_the_oracle(hc, orc):
+    """hc_finalize (host code, no device access) applies Eq. var_q's final
+    scaling to exact sums: bit-equal to the oracle's finish for s2 below and
+    above 2^64, NaN variance for N = 1, the sums copied through; null output,
+    N < 1 and a non-positive or non-finite eps are refused."""
+    import math
+
+    import numpy as np
+
+    rng = np.random.default_rng(2026)
+    cases = [(1, 7, 49, 0.25), (2, -3, 5, 1e-3), (8, 18, 740, 0.1)]
+    for _ in range(40):
+        k = int(rng.integers(2, 64))
+        q = [int(v) for v in rng.integers(-(1 << 29), 1 << 29, size=k)]
+        rep = int(rng.choice([1, 1 << 10, 1 << 20]))
+        cases.append((k * rep, sum(q) * rep, sum(v * v for v in q) * rep, float(rng.choice([1e-6, 3.3e-3, 17.0]))))
+    saw_wide = False
+    for n, s1, s2, eps in cases:
+        r = hc.finalize(n, s1, s2, eps)
+        m, v, sd = orc.finalize(n, s1, s2, eps)
+        assert r["n"] == n and r["s1"] == s1 and r["s2"] == s2 and r["exact"] == 1 and r["status"] == 0
+        assert r["mean"] == m
+        if n < 2:
+            assert math.isnan(r["variance"]) and math.isnan(r["std"])
+        else:
+            assert r["variance"] == v and r["std"] == sd
+        saw_wide |= s2 >= (1 << 64)
+    assert saw_wide
+    L = hc.lib()
+    buf = ctypes.create_string_buffer(hc.SCALAR_BYTES)
+    out = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.hc_finalize(4, 1, 1, 0, 1e-3, None) == hc.HC_ERR_INVALID_ARG
+    assert L.hc_finalize(0, 1, 1, 0, 1e-3, out) == hc.HC_ERR_INVALID_ARG
+    for eps in (0.0, -1.0, float("inf"), float("nan")):
+        assert L.hc_finalize(4, 1, 1, 0, eps, out) == hc.HC_ERR_INVALID_ARG
