@@ -2,9 +2,10 @@
 // compressed stream for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc (or a framework allocator) at the point
-// where they need a statistic: code running inside a CUDA graph capture,
-// allocation-free real-time or embedded loops, and plugins that are handed a
-// stream and a few pointers by a host application that owns all memory.  For
+// where they need a statistic: allocation-free real-time or embedded loops,
+// whose latency budget leaves no room for an allocator call, and plugins that
+// are handed a stream and a few pointers by a host application that owns all
+// device memory and gives out no allocator.  For
 // them this entry point needs no workspace argument: the kernel's scratch
 // (one ticket counter and up to kNoAllocParts per-CTA partial sums) lives in a
 // file-scope static device array of fixed size, which every GPU that loads
@@ -21,6 +22,9 @@ namespace hc {
 constexpr int kNoAllocParts = 2048;
 constexpr size_t kNoAllocHead = 256;
 constexpr size_t kNoAllocBytes = kNoAllocHead + sizeof(Partial) * kNoAllocParts;  // 64 KiB + 256 B
+// the launch caps its grid at kMaxGrid like the workspace launch, so both
+// launches use the same grid whenever it fits the slots
+static_assert(kNoAllocParts <= kMaxGrid, "the static partial slots must not exceed the workspace launch's grid cap");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 

@@ -243,17 +243,26 @@ class GpuExecutor:
             for d in c.shape:
                 n *= int(d)
             self.sizes.append(n)
+        # the operation workspace each one-field call allocates on the slot
+        # stream (the field's own size: global predictors need scratch)
+        self.ws_bytes = [int(hc.lib().hc_workspace_bytes_for(ctypes.byref(c.header))) for c in fields]
+        self.op_ws_bytes = int(hc.lib().hc_workspace_bytes())
 
     def need_bytes(self, q: Query) -> int:
         c = self.fields[q.field]
         n = 1
         for d in c.shape:
             n *= int(d)
-        need = 64
+        # the 64-byte statistic, the field output of a gradient query (the
+        # batched path allocates it too), the float array of the plain path and
+        # the workspace of every one-field call the query makes (a batched
+        # query uses the slot's preallocated batch workspace; counting a
+        # workspace for it as well keeps the bound an upper bound)
+        need = 64 + self.ws_bytes[q.field]
         if q.op == "gradmag":
             need += 4 * n
         if q.stage == "f":
-            need += (8 if c.dtype == "float64" else 4) * n
+            need += (8 if c.dtype == "float64" else 4) * n + self.op_ws_bytes
         return need
 
     def launch(self, batch):

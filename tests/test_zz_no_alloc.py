@@ -39,6 +39,13 @@ def _noalloc(hc, torch, c, level):
     return hc.parse_scalar(out)
 
 
+def _same(got, ref):
+    assert got["status"] == 0 and got["exact"] == 1
+    assert (got["n"], got["s1"], got["s2"]) == (ref["n"], ref["s1"], ref["s2"])
+    for k in ("mean", "variance", "std"):
+        assert abs(got[k] - ref[k]) <= 1e-12 * abs(ref[k])
+
+
 @pytest.mark.parametrize("shape,S,eb", [((64, 64, 64), 32, 1e-3), ((13, 17, 19), 16, 1e-2), ((5, 6, 70), 64, 1e-4),
                                         ((512, 512), 32, 1e-3)])
 def test_noalloc_matches_workspace_variance(env, shape, S, eb):
@@ -49,11 +56,27 @@ def test_noalloc_matches_workspace_variance(env, shape, S, eb):
     for level in ("q", "p"):
         ref = hc.parse_scalar(hc.variance(c, level=level))
         for _ in range(2):
-            got = _noalloc(hc, torch, c, level)
-            assert got["status"] == 0 and got["exact"] == 1
-            assert (got["n"], got["s1"], got["s2"]) == (ref["n"], ref["s1"], ref["s2"])
-            for k in ("mean", "variance", "std"):
-                assert abs(got[k] - ref[k]) <= 1e-12 * abs(ref[k])
+            _same(_noalloc(hc, torch, c, level), ref)
+
+
+@pytest.mark.parametrize("shape,S,eb", [((64, 64, 64), 32, 1e-3), ((5, 6, 70), 64, 1e-4)])
+def test_noalloc_block_mean_streams(env, shape, S, eb):
+    """Block-mean (HSZx) streams at level q: the same exact sums as the
+    workspace path, twice in a row; through the Python wrapper as well.  Their
+    stage-2 deviation needs a workspace and is refused."""
+    hc, torch, dev = env
+    import synth
+
+    c = hc.compress(torch.from_numpy(synth.grf_field(shape, 78)).to(dev), eb, S=S, predictor="mean")
+    ref = hc.parse_scalar(hc.variance(c, level="q"))
+    for _ in range(2):
+        _same(_noalloc(hc, torch, c, "q"), ref)
+        _same(hc.parse_scalar(hc.variance_noalloc(c, level="q")), ref)
+    out = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
+    st = c.stage("p")
+    rc = hc.lib().hc_op_variance_noalloc(ctypes.byref(st), c.eps, len(c.shape), hc._dims(c.shape),
+                                         ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == hc.HC_ERR_UNSUPPORTED
 
 
 def test_noalloc_rejects_array_inputs(env):
