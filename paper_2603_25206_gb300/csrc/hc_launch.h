@@ -105,6 +105,13 @@ int reduce_array_impl(const hc_stage* in, double eps, int what, hc_scalar* d_out
 // Stage-1 mean of HSZx from a block-means array (Eq. mean_m).
 int mean_m_array_impl(const int32_t* means, int64_t nb, int S, int64_t n, double eps, hc_scalar* d_out, void* d_ws,
                       cudaStream_t st);
+// Fused statistics of block-size-32 streams (block heads or block means,
+// widths <= 16, |q| < 2^26; hc_reduce32.cu): warp-autonomous chunks with bulk
+// copies.  reduce32_applies says whether a stream qualifies; max_parts bounds
+// the grid (partial slots); shift: the stage-2 HSZx deviation's integer mean.
+bool reduce32_applies(const hc_header* h);
+int reduce32_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, Partial* parts,
+                  unsigned* ticket, int max_parts, const long long* shift, cudaStream_t st);
 // Fused stage-3 variance with its scratch (per-CTA partials + ticket) at given device addresses.
 int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
                                  unsigned* ticket, int max_parts, cudaStream_t st);

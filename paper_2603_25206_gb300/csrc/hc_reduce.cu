@@ -604,6 +604,17 @@ int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int 
     if (what != RED_MEAN) return fail(HC_ERR_UNSUPPORTED, "stage 1 gives the mean only (Eq. mean_m)");
     return launch_mean_m(means, h->nb, h->S, h->N, h->eps, d_out, d_ws, nullptr, st);
   }
+  if (reduce32_applies(h)) {
+    OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
+    long long* mu = nullptr;
+    if (hszx && level == HC_STAGE_P && what == RED_VAR) {
+      // Section V-A: the deviations about the integer mean mu~ of stage 1
+      mu = reinterpret_cast<long long*>(&ws->pad[0]);
+      int rc = launch_mean_m(means, h->nb, h->S, h->N, h->eps, d_out, d_ws, mu, st);
+      if (rc) return rc;
+    }
+    return reduce32_impl(h, d_stream, level, what, d_out, ws_partials(d_ws), &ws->ticket, kMaxGrid, mu, st);
+  }
   if (hszx && level == HC_STAGE_P && what == RED_VAR) {
     // Section V-A: the deviations about the integer mean mu~ of stage 1
     long long* mu = reinterpret_cast<long long*>(&reinterpret_cast<OpWs*>(d_ws)->pad[0]);
@@ -728,7 +739,7 @@ static int launch_var_scratch_p(const hc_header* h, const void* d_stream, hc_sca
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, bytes);
   per_sm = std::max(per_sm, 1);
   const int64_t ntiles = ceil_div(h->nchunks, kRedTileChunks);
-  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm);
+  const int64_t grid = std::min<int64_t>(std::min<int64_t>(ntiles, (int64_t)device_sms() * per_sm), kMaxGrid);
   if (grid > max_parts) return fail(HC_ERR_NOMEM, "the static scratch of hc_op_variance_noalloc has too few partial slots for this GPU");
   kern<<<(unsigned)grid, kThreads, bytes, st>>>(s, ntiles, stage, parts, ticket, d_out, 2.0 * h->eps, nullptr);
   return check_launch_cfg("variance (static scratch)", reinterpret_cast<const void*>(kern), grid, bytes);
@@ -746,6 +757,8 @@ static int launch_var_scratch(const hc_header* h, const void* d_stream, hc_scala
 int variance_stream_scratch_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
                                  unsigned* ticket, int max_parts, cudaStream_t st) {
   if (h->pred >= HC_PRED_LORENZO) return fail(HC_ERR_INVALID_ARG, "global-predictor stream on the block reducer");
+  if (reduce32_applies(h))
+    return reduce32_impl(h, d_stream, HC_STAGE_Q, RED_VAR, d_out, parts, ticket, max_parts, nullptr, st);
   const bool small = h->S <= 32;
   switch (acc_class(h->qmax)) {
     case 0:

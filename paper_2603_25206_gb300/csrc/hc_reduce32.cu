@@ -1,0 +1,320 @@
+// hc_reduce32.cu -- fused homomorphic statistics (Section V-A) for the common
+// stream shape: block size 32, block widths <= 16, codes |q| < 2^26.
+//
+// Same results as k_reduce_stream (exact s1 = sum q, s2 = sum q^2 and the
+// final scaling of Eq. var_q); a different schedule:
+//  * every warp works alone on whole chunks (128 blocks, 4096 codes): the
+//    chunk index gives the chunk's payload range, so no warp waits for
+//    another and there is no CTA barrier until the final sum;
+//  * one lane copies the next chunk's payload into the warp's other shared
+//    buffer with a 1-D bulk copy (TMA) completing on an mbarrier, while the
+//    warp decodes the current chunk; widths and heads come straight into
+//    registers (one coalesced 4-byte and one 16-byte load per lane);
+//  * lane l decodes blocks 4l .. 4l+3 of the chunk with the grouped unpacker
+//    (hc_group.cuh: G codes per window step, G = 4, 3 or 2 from the stream's
+//    largest width).
+// Per code: stage 2 ("Operation with D_p") is one multiply-add of the
+// block-weighted sum sum_k (32 - k) p_k, no prefix sum; stage 3 ("Operation
+// with D_q") rebuilds q with the running (eta) accumulator and adds q (mean)
+// and q^2 (variance).  Block-mean (HSZx) streams: q = M_b + p, so the sums
+// follow from sum p and sum p^2 per block.
+#include <cstdint>
+#include <type_traits>
+
+#include "hc_finish.cuh"
+#include "hc_group.cuh"
+#include "hc_internal.cuh"
+#include "hc_launch.h"
+
+namespace hc {
+
+DevStream dev_stream(const hc_header* h, const void* d_stream);
+
+namespace {
+
+constexpr int kWarps = 4;          // warps per CTA
+constexpr int kChunkBlocks = 128;  // blocks per chunk at S = 32 (4096 / 32)
+constexpr unsigned kWaitPolls = 1u << 22;
+
+// What a launch sums: the stage-2 weighted sum (mean), the stage-3 sum
+// (mean), or the stage-3 sums of q and q^2 (variance).
+enum Op { OP_MEAN_P = 0, OP_MEAN_Q = 1, OP_VAR = 2 };
+
+// Words of one chunk buffer: 128 blocks of at most wmax + 1 words, the
+// copy's 16-byte alignment on both ends and the decoder's read-ahead.
+__host__ __device__ inline int chunk_buf_words(int wmax) { return round4(kChunkBlocks * (wmax + 1) + 3 + 3 + 8); }
+__host__ __device__ inline int smem_bytes(int buf_words) { return 128 + kWarps * 2 * buf_words * 4; }
+
+struct ChunkMeta {
+  uint32_t w4;  // widths of the lane's four blocks (byte j: block 4 lane + j)
+  int4 h4;      // their heads
+  uint64_t p0, p1;  // payload words of the chunk
+};
+
+__device__ __forceinline__ ChunkMeta load_meta(const DevStream& s, int64_t c, int lane) {
+  ChunkMeta m;
+  const int64_t b = c * kChunkBlocks + 4 * lane;
+  m.w4 = 0;
+  m.h4 = make_int4(0, 0, 0, 0);
+  if (b < s.nb) {
+    // b is a multiple of 4: 4-byte aligned widths, 16-byte aligned heads; a
+    // lane whose last blocks lie past nb reads at most 3 bytes / 12 bytes
+    // beyond the sections' ends, inside their 16-byte padding
+    m.w4 = __ldg(reinterpret_cast<const uint32_t*>(s.widths + b));
+    m.h4 = __ldg(reinterpret_cast<const int4*>(s.heads + b));
+  }
+  m.p0 = __ldg(s.chunks + c);
+  m.p1 = __ldg(s.chunks + c + 1);
+  return m;
+}
+
+template <int G, int OP, int ACC, int PRED>
+__global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_words, Partial* parts,
+                                                          unsigned* ticket, hc_scalar* out, double two_eps,
+                                                          const long long* shift) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm) + 2 * warp;
+  uint32_t* bufs = reinterpret_cast<uint32_t*>(sm + 128) + (size_t)(2 * warp) * buf_words;
+  const long long c0 = shift ? __ldcg(shift) : 0ll;
+  const int64_t stride = (int64_t)gridDim.x * kWarps;
+  int err = 0;
+  long long S1 = 0;
+  u128 S2 = 0;
+
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+
+  // Copy of chunk c's payload into buffer b by lane 0: words [a0, end) with
+  // a0 = p0 rounded down and end = p1 rounded up to 16 bytes (the stream keeps
+  // >= 16 zero bytes after the payload).  False (nothing issued) when the
+  // chunk index is inconsistent or the chunk holds no payload words.
+  auto issue = [&](const ChunkMeta& m, int b) -> bool {
+    if (m.p1 < m.p0 || m.p1 > (uint64_t)s.payload_words) return false;
+    const uint64_t a0 = m.p0 & ~(uint64_t)3, end = (m.p1 + 3) & ~(uint64_t)3;
+    if ((int64_t)(end - a0) + 8 > (int64_t)buf_words || end == a0) return false;
+    if (lane == 0) {
+      const unsigned bytes = (unsigned)((end - a0) * 4);
+      mbar_expect_tx(bar + b, bytes);
+      bulk_g2s(bufs + (size_t)b * buf_words, s.payload + a0, bytes, bar + b);
+    }
+    return true;
+  };
+
+  int64_t c = (int64_t)blockIdx.x * kWarps + warp;
+  ChunkMeta cur{};
+  bool cur_issued = false;
+  unsigned phase = 0;  // bit b: parity of buffer b's next completion
+  if (c < s.nchunks) {
+    cur = load_meta(s, c, lane);
+    cur_issued = issue(cur, 0);
+  }
+  for (int i = 0; c < s.nchunks; c += stride, ++i) {
+    const int b = i & 1;
+    const int64_t cn = c + stride;
+    ChunkMeta nxt{};
+    bool nxt_issued = false;
+    if (cn < s.nchunks) {
+      nxt = load_meta(s, cn, lane);
+      // every lane is done with buffer b ^ 1 (chunk c - stride) before the
+      // bulk copy overwrites it
+      __syncwarp();
+      if (lane == 0) fence_proxy_async_smem();
+      nxt_issued = issue(nxt, b ^ 1);
+    }
+    // block offsets inside the chunk: exclusive scan of the block sizes
+    // (1 sign word + w magnitude words, 0 for width 0)
+    const int64_t bb = c * kChunkBlocks + 4 * lane;
+    uint32_t wj[4], oj[4];
+    uint32_t lsum = 0;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t w = (cur.w4 >> (8 * j)) & 0xffu;
+      if (bb + j >= s.nb) w = 0;
+      if (w > (uint32_t)s.wmax) {
+        bad = true;
+        w = 0;
+      }
+      wj[j] = w;
+      oj[j] = lsum;
+      lsum += w ? w + 1u : 0u;
+    }
+    uint32_t incl = lsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    bad = __any_sync(0xffffffffu, bad) || (!cur_issued && total != 0) || (uint64_t)total != cur.p1 - cur.p0;
+    if (cur_issued) {
+      // every lane waits (each observes the copy's completion itself); the
+      // outcome is made warp-uniform so the warp leaves together on a timeout
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar + b, (phase >> b) & 1u, kWaitPolls))) {
+        err = HC_ERR_TIMEOUT;
+        if (nxt_issued) mbar_wait_bounded(bar + (b ^ 1), (phase >> (b ^ 1)) & 1u, kWaitPolls);
+        break;
+      }
+      phase ^= 1u << b;
+    }
+    if (bad) {
+      err = HC_ERR_CORRUPT;
+    } else {
+      const uint32_t* base = bufs + (size_t)b * buf_words + (uint32_t)(cur.p0 & 3) + (incl - lsum);
+      const int32_t hj[4] = {cur.h4.x, cur.h4.y, cur.h4.z, cur.h4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t blk = bb + j;
+        if (blk >= s.nb) break;
+        const uint32_t w = wj[j];
+        const int32_t head = hj[j];
+        const uint32_t* bw = base + oj[j];
+        const int cnt = (int)min((int64_t)32, s.N - blk * 32);
+        if constexpr (PRED == HC_PRED_MEAN) {
+          // q = M_b + p for every slot (HSZx): sums from sum p and sum p^2
+          long long sp = 0;
+          unsigned long long sp2 = 0;
+          if (w) {
+            if (cnt == 32) {
+              int32_t a = 0;
+              unsigned long long a2 = 0;
+              decode32<G>(bw + 1, bw[0], w, [&](int, int32_t x, int32_t neg) {
+                const int32_t p = x - neg;
+                a += p;
+                if (OP == OP_VAR) a2 += (unsigned long long)((long long)p * p);
+              });
+              sp = a;
+              sp2 = a2;
+            } else {
+              unpack_segment<false>(bw + 1, bw[0], w, cnt, [&](int, int32_t p) {
+                sp += p;
+                if (OP == OP_VAR) sp2 += (unsigned long long)((long long)p * p);
+              });
+            }
+          }
+          S1 += (long long)cnt * head + sp;
+          if (OP == OP_VAR) {
+            const long long cc = (long long)head - c0;
+            S2 += (u128)((i128)cnt * cc * cc + (i128)2 * cc * sp + (i128)sp2);
+          }
+        } else if constexpr (OP == OP_MEAN_P) {
+          // Section V-A, stage 2: S_b head + sum_k (S_b - k) p_k (p_0 = 0)
+          long long c1 = (long long)cnt * head;
+          if (w) {
+            if (cnt == 32) {
+              int32_t a = 0;
+              decode32<G>(bw + 1, bw[0], w, [&](int k, int32_t x, int32_t) { a += (32 - k) * x; });
+              c1 += (long long)a + weighted_sign_count(bw[0]);
+            } else {
+              long long a = 0;
+              unpack_segment<false>(bw + 1, bw[0], w, cnt, [&](int k, int32_t p) { a += (long long)(cnt - k) * p; });
+              c1 += a;
+            }
+          }
+          S1 += c1;
+        } else {
+          // Section V-A, stage 3: q rebuilt from the head (eta accumulator)
+          if (w == 0) {
+            S1 += (long long)cnt * head;
+            if (OP == OP_VAR) S2 += (u128)((unsigned long long)cnt * (unsigned long long)((long long)head * head));
+          } else if (cnt == 32) {
+            int32_t q = head, a1 = 0;
+            using A2 = typename std::conditional<ACC == 0, uint32_t, unsigned long long>::type;
+            A2 a2 = 0;
+            decode32<G>(bw + 1, bw[0], w, [&](int, int32_t x, int32_t neg) {
+              q = q + x - neg;
+              a1 += q;
+              if (OP == OP_VAR) {
+                if constexpr (ACC == 0)
+                  a2 += (uint32_t)(q * q);
+                else
+                  a2 += (unsigned long long)((long long)q * q);
+              }
+            });
+            S1 += a1;
+            if (OP == OP_VAR) S2 += (u128)a2;
+          } else {
+            int32_t q = head;
+            long long a1 = 0;
+            unsigned long long a2 = 0;
+            unpack_segment<false>(bw + 1, bw[0], w, cnt, [&](int, int32_t p) {
+              q += p;
+              a1 += q;
+              if (OP == OP_VAR) a2 += (unsigned long long)((long long)q * q);
+            });
+            S1 += a1;
+            if (OP == OP_VAR) S2 += (u128)a2;
+          }
+        }
+      }
+    }
+    cur = nxt;
+    cur_issued = nxt_issued;
+  }
+  reduce_and_finish(S1, S2, err, parts, ticket, [&](long long a, u128 b2, int e) {
+    if (shift)
+      finalize_about(out, s.N, a, b2, c0, two_eps, e);
+    else
+      finalize_int(out, s.N, a, b2, OP == OP_VAR, two_eps, e);
+  });
+}
+
+template <int G, int OP, int ACC, int PRED>
+int launch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts, unsigned* ticket,
+           int max_parts, const long long* shift, cudaStream_t st) {
+  const DevStream s = dev_stream(h, d_stream);
+  const int bw = chunk_buf_words((int)h->wmax);
+  const int bytes = smem_bytes(bw);
+  auto kern = k_reduce32<G, OP, ACC, PRED>;
+  int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
+  if (rc) return rc;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, bytes);
+  per_sm = std::max(per_sm, 1);
+  int64_t grid = std::min<int64_t>((int64_t)device_sms() * per_sm, ceil_div(h->nchunks, kWarps));
+  grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::min<int64_t>(kMaxGrid, max_parts)));
+  kern<<<(unsigned)grid, kWarps * 32, bytes, st>>>(s, bw, parts, ticket, d_out, 2.0 * h->eps, shift);
+  return check_launch_cfg("reduce (block size 32)", reinterpret_cast<const void*>(kern), grid, bytes);
+}
+
+template <int OP, int ACC, int PRED>
+int launch_g(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts, unsigned* ticket,
+             int max_parts, const long long* shift, cudaStream_t st) {
+  if (h->wmax <= 8) return launch<4, OP, ACC, PRED>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+  if (h->wmax <= 10) return launch<3, OP, ACC, PRED>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+  return launch<2, OP, ACC, PRED>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+}
+
+}  // namespace
+
+bool reduce32_applies(const hc_header* h) {
+  return h->S == 32 && (h->pred == HC_PRED_DELTA || h->pred == HC_PRED_MEAN) && h->wmax <= 16 && h->qmax > 0 &&
+         h->qmax < (1u << 26);
+}
+
+int reduce32_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, Partial* parts,
+                  unsigned* ticket, int max_parts, const long long* shift, cudaStream_t st) {
+  const bool narrow = h->qmax < (1u << 12);
+  if (h->pred == HC_PRED_MEAN) {
+    // stages 2 and 3 have the same sums (sum q = sum p + M_b S_b); with
+    // `shift` the squares are taken about the integer mean (stage-2 std)
+    if (what == RED_MEAN) return launch_g<OP_MEAN_Q, 1, HC_PRED_MEAN>(h, d_stream, d_out, parts, ticket, max_parts, nullptr, st);
+    return narrow ? launch_g<OP_VAR, 0, HC_PRED_MEAN>(h, d_stream, d_out, parts, ticket, max_parts, shift, st)
+                  : launch_g<OP_VAR, 1, HC_PRED_MEAN>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+  }
+  if (what == RED_MEAN) {
+    if (level == HC_STAGE_P)
+      return launch_g<OP_MEAN_P, 1, HC_PRED_DELTA>(h, d_stream, d_out, parts, ticket, max_parts, nullptr, st);
+    return launch_g<OP_MEAN_Q, 1, HC_PRED_DELTA>(h, d_stream, d_out, parts, ticket, max_parts, nullptr, st);
+  }
+  // the variance at stage 2 rebuilds q with the eta accumulator: stage 3's arithmetic
+  return narrow ? launch_g<OP_VAR, 0, HC_PRED_DELTA>(h, d_stream, d_out, parts, ticket, max_parts, nullptr, st)
+                : launch_g<OP_VAR, 1, HC_PRED_DELTA>(h, d_stream, d_out, parts, ticket, max_parts, nullptr, st);
+}
+
+}  // namespace hc
