@@ -9,12 +9,21 @@ eb = 1e-3, block 32).  The step runs one pass per field (hc_op_multi: the
 stream is decoded once and every operation is written from the same
 neighbourhood, "decompress once, many ops").
 
-value    = original bytes of the fields x operations / step time (GB/s of
+value    = original bytes of one pass over the fields / step time (GB/s of
            original data, the paper's throughput definition) on the device
-           with the compressed inputs already resident;
+           with the compressed inputs already resident; value_op_weighted
+           counts those bytes once per operation;
+per_field = the one-pass kernel's rooflines field by field;
 per_op_launches = the same operations as one fused kernel per operation
            (the paper's per-operation form: mean at stage 2, the rest at
            stage 3), with that form's own roofline and kernel shares;
+per_op_cold = every per-operation kernel of every field cold (median of 30,
+           L2 flushed before each run), with its roofline, the plain path and
+           Table 4's decompress / operate split; field_512 singles out the
+           512^3 field and its error-bound sweep (eb 1e-2, 1e-4);
+configs  = the other configurations, time-bounded: HSZx, HSZp-nd / HSZp,
+           HSZx-nd, the 64-field batched launch, the wide-code field and the
+           serving saturation curve;
 e2e      = the one-pass step through the C ABI from pinned host memory: the
            compressed streams are copied in and every output field and the
            statistics copied out inside the timed region;
@@ -23,14 +32,18 @@ plain    = full decompression to float32 followed by the same operations on
            operation, for the speedups;
 roofline = the one-pass kernel's algorithmic bytes (compressed input +
            output fields) over its CUDA-event time, against the measured HBM
-           copy bandwidth.
+           copy bandwidth;
+cpu_baseline = the oracle on every host core (one process per core, each on
+           its own slab of the 512^3 field) and on one core.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference].
 With torchrun (WORLD_SIZE > 1) every rank runs its own copy of the workload
 on its own GPU (independent problems, weak scaling, no data-path collective);
-the step time is the maximum over ranks.  Other modes: --batched (64 uneven
-fields in one launch), --serving (query stream), --profile-small /
---profile-batch (small ncu cases).
+the step time is the maximum over ranks.  Other modes print one
+configuration alone: --batched, --serving, --hszx, --lorenzo, --boxes,
+--wide; --no-extras skips the cold tables, the sweep and the configurations;
+--profile-small / --profile-batch / --profile-lorenzo / --profile-boxes run
+the small ncu cases.
 """
 from __future__ import annotations
 
@@ -257,13 +270,19 @@ class Workload:
                     events.append((fi, op, e0, e1))
 
 
+# timing protocol of the per-operation and plain forms: the L2 is flushed
+# (a 512 MB write, four times the L2) before every timed run, and the median
+# of REPS runs is kept
+REPS = 30
+
+
 def flush_l2(torch, dev, buf=[]):
     if not buf:
         buf.append(torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev))
     buf[0].fill_(1.0)
 
 
-def time_call(torch, dev, fn, reps=5):
+def time_call(torch, dev, fn, reps=REPS):
     """Median CUDA-event time (ms) of fn() with an L2 flush before each rep."""
     ts = []
     for _ in range(reps):
@@ -278,33 +297,103 @@ def time_call(torch, dev, fn, reps=5):
     return float(np.median(ts))
 
 
-def per_op_table(hc, torch, dev, wl):
-    """Every op at every stage vs the plain path, per field (Tab. 4 style split)."""
-    rows = []
-    for it in wl.items:
-        c = it["c"]
-        n = it["n"]
-        dq = hc.decompress(c, "q")
-        dp = hc.decompress(c, "p")
-        df = hc.decompress(c, "f")
-        t_dec = {s: time_call(torch, dev, lambda s=s, o=o: hc.decompress(c, s, out=o))
-                 for s, o in (("p", dp), ("q", dq), ("f", df))}
-        sp, sq, sf = hc.as_stage(c, "p", dp), hc.as_stage(c, "q", dq), hc.as_stage(c, "f", df)
-        for op, ax in op_list(len(it["shape"])):
-            r = {"field": "x".join(map(str, it["shape"])), "op": op + ("" if ax is None else str(ax))}
-            r["fused_ms"] = time_call(torch, dev, lambda: wl.run_op(it, op, ax))
-            if op in ("mean", "variance"):
-                r["fused_p_ms"] = time_call(torch, dev, lambda: wl.run_op(it, op, ax, level_q="p"))
-                r["unfused_p_ms"] = t_dec["p"] + time_call(torch, dev, lambda: wl.run_op(it, op, ax, src=sp))
-            r["unfused_q_ms"] = t_dec["q"] + time_call(torch, dev, lambda: wl.run_op(it, op, ax, src=sq))
-            r["plain_decompress_ms"] = t_dec["f"]
-            r["plain_op_ms"] = time_call(torch, dev, lambda: wl.run_op(it, op, ax, src=sf))
-            r["plain_ms"] = r["plain_decompress_ms"] + r["plain_op_ms"]
-            r["speedup_vs_plain"] = r["plain_ms"] / r["fused_ms"]
-            r["fused_gbs_orig"] = n * 4 / r["fused_ms"] / 1e6
-            rows.append(r)
-        del dq, dp, df
-    return rows
+def op_specs(ndim):
+    """Every per-operation kernel of a field: (label, operation, level or axis)."""
+    specs = [("mean_stage2", "mean", "p"), ("mean_stage3", "mean", "q"),
+             ("variance_stage2", "variance", "p"), ("variance_stage3", "variance", "q")]
+    specs += [(f"derivative{a}", "derivative", a) for a in range(ndim)]
+    return specs + [("gradmag", "gradmag", None), ("laplacian", "laplacian", None)]
+
+
+def run_spec(hc, inp, kind, arg, out, scal):
+    if kind == "mean":
+        hc.mean(inp, level=arg or "p", out=scal)
+    elif kind == "variance":
+        hc.variance(inp, level=arg or "q", out=scal)
+    elif kind == "derivative":
+        hc.derivative(inp, arg, out=out)
+    elif kind == "gradmag":
+        hc.gradmag(inp, out=out)
+    else:
+        hc.laplacian(inp, out=out)
+
+
+def cold_table(hc, torch, dev, c, shape, peak, plain=True, split=True):
+    """Every operation of one compressed field on its own, cold (REPS runs,
+    L2 flushed before each): the fused kernel's time, GB/s of original data
+    and roofline fraction (compressed stream + output over the measured HBM
+    peak); the plain path (decompress to float32, then the operation on the
+    floats) and the speedup; and Table 4's split of the unfused stages:
+    decompression to D_p / D_q / D_f and the operation on that array."""
+    n = int(np.prod(shape))
+    nd = len(shape)
+    out = torch.empty(shape, dtype=torch.float32, device=dev)
+    scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
+    arrs, t_dec = {}, {}
+    if plain or split:
+        for s in ("p", "q", "f"):
+            arrs[s] = hc.decompress(c, s)
+            t_dec[s] = time_call(torch, dev, lambda s=s: hc.decompress(c, s, out=arrs[s]))
+        stages = {s: hc.as_stage(c, s, arrs[s]) for s in arrs}
+    rows = {}
+    for label, kind, arg in op_specs(nd):
+        run_spec(hc, c, kind, arg, out, scal)
+        ms = time_call(torch, dev, lambda: run_spec(hc, c, kind, arg, out, scal))
+        field_op = kind in ("derivative", "gradmag", "laplacian")
+        alg = c.nbytes + (4 * n if field_op else 64)
+        r = {"ms": round(ms, 5), "gbs_orig": round(n * 4 / ms / 1e6, 1), "alg_bytes": alg,
+             "roofline_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)}
+        aarg = arg if kind == "derivative" else None  # arrays: the axis only (no level)
+        if plain:
+            op_f = time_call(torch, dev, lambda: run_spec(hc, stages["f"], kind, aarg, out, scal))
+            r["plain_ms"] = round(t_dec["f"] + op_f, 5)
+            r["speedup_vs_plain"] = round((t_dec["f"] + op_f) / ms, 3)
+            r["plain_split_ms"] = {"decompress_f": round(t_dec["f"], 5), "op_on_f": round(op_f, 5)}
+        if split:
+            st = arg if kind in ("mean", "variance") else "q"
+            op_a = time_call(torch, dev, lambda: run_spec(hc, stages[st], kind, aarg, out, scal))
+            r["unfused_split_ms"] = {"stage": st, "decompress": round(t_dec[st], 5), "op_on_array": round(op_a, 5),
+                                     "total": round(t_dec[st] + op_a, 5)}
+        rows[label] = r
+    del arrs, out, scal
+    res = {"field": "x".join(map(str, shape)), "compressed_bytes": c.nbytes, "wmax": int(c.header.wmax),
+           "ops": rows}
+    if t_dec:
+        res["decompress_ms"] = {s: round(v, 5) for s, v in t_dec.items()}
+    return res
+
+
+def one_pass_cold(hc, torch, dev, c, shape, peak):
+    """The one-pass kernel (every operation from one decode) cold on one field."""
+    n = int(np.prod(shape))
+    nd = len(shape)
+    mo = {"derivative": [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(nd)],
+          "gradmag": torch.empty(shape, dtype=torch.float32, device=dev),
+          "laplacian": torch.empty(shape, dtype=torch.float32, device=dev),
+          "stats": torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)}
+    hc.multi(c, outs=mo)
+    ms = time_call(torch, dev, lambda: hc.multi(c, outs=mo))
+    alg = c.nbytes + (nd + 2) * 4 * n + 64
+    del mo
+    return {"ms": round(ms, 5), "gbs_orig": round(n * 4 / ms / 1e6, 1), "alg_bytes": alg,
+            "roofline_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)}
+
+
+def eb_sweep(hc, torch, dev, x, shape, peak, ebs=(1e-2, 1e-4)):
+    """The 512^3 field at the other error bounds of the paper-like
+    configuration: stream size and widths, the one-pass kernel and every
+    per-operation kernel cold, against the plain path."""
+    out = {}
+    for eb in ebs:
+        xd = torch.from_numpy(x).to(dev)
+        c = hc._trim(hc.compress(xd, eb, rel=True, S=BLOCK))
+        del xd
+        row = cold_table(hc, torch, dev, c, shape, peak, plain=True, split=False)
+        row["one_pass"] = one_pass_cold(hc, torch, dev, c, shape, peak)
+        out[f"{eb:g}"] = row
+        del c
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- roofline
@@ -328,7 +417,7 @@ def read_profile_traffic(kernel_tag: str):
 # the other profiled kernels): a profile's traffic is used only while these
 # are unchanged since its capture
 KERNEL_SOURCES = ("hc_stencil_pipe.cu", "hc_stencil_pipe.cuh", "hc_stencil_tile.cuh", "hc_internal.cuh",
-                  "hc_finish.cuh")
+                  "hc_finish.cuh", "hc_group.cuh")
 
 
 def csrc_hash():
@@ -348,42 +437,180 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------- CPU baseline
-def cpu_sample_run(field, shape, planes):
-    """The oracle, as it stands, on the first `planes` planes of a field: decode the
-    compressed sample and run every operation.  Returns (seconds, original bytes x ops)."""
+def oracle_sample(sub):
+    """Compress a sample with the oracle (outside any timed region)."""
     import oracle
 
-    sub = np.ascontiguousarray(field[:planes])
-    s, eps = oracle.compress(sub, EB, True, BLOCK)
+    s, eps = oracle.compress(np.ascontiguousarray(sub), EB, True, BLOCK)
+    return s, eps
+
+
+def oracle_ops(s, eps, ndim):
+    """The oracle, as it stands, on one compressed sample: decode to D_p and
+    D_q and run every operation.  Returns (seconds, original bytes of the
+    sample: one pass)."""
+    import oracle
+
     t0 = time.perf_counter()
     dp = oracle.decode(s, "p")
     oracle.mean_p_sum(dp, BLOCK)
     q = oracle.decode(s, "q")
     s1, s2 = oracle.sums_q(q)
     oracle.finalize(q.size, s1, s2, eps)
-    for ax in range(sub.ndim):
+    for ax in range(ndim):
         oracle.stencil_q(q, oracle.KIND_DERIV, eps, ax)
     oracle.stencil_q(q, oracle.KIND_GRADMAG, eps)
     oracle.stencil_q(q, oracle.KIND_LAPLACIAN, eps)
     dt = time.perf_counter() - t0
-    return dt, sub.size * 4 * len(op_list(sub.ndim))
+    return dt, q.size * 4
 
 
-def cpu_baseline(fields, target_s=12.0):
+def cpu_sample_run(field, shape, planes):
+    """The oracle on the first `planes` planes of a field (single thread)."""
+    s, eps = oracle_sample(field[:planes])
+    return oracle_ops(s, eps, len(shape))
+
+
+def _oracle_worker(rank, sub, inbox, outbox):
+    """One process of the all-cores oracle pool: compresses its slab once,
+    then runs the oracle on it at every 'go' (spawned: no CUDA state)."""
+    sys.path.insert(0, ROOT)
+    s, eps = oracle_sample(sub)
+    outbox.put(("ready", rank, 0.0, 0))
+    while True:
+        msg = inbox.get()
+        if msg != "go":
+            break
+        dt, b = oracle_ops(s, eps, sub.ndim)
+        outbox.put(("done", rank, dt, b))
+
+
+class OraclePool:
+    """The unmodified oracle on every host core: one spawned process per core,
+    each on its own slab of planes of the field (the operations run on each
+    slab as a field of its own; the slabs together cover the sample).  step()
+    starts every process at once and returns (wall seconds until the last one
+    finished, original bytes of the whole sample)."""
+
+    def __init__(self, x, planes, nproc=None):
+        import multiprocessing as mp
+
+        self.nproc = nproc or os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        per = max(1, planes // self.nproc)
+        self.nproc = min(self.nproc, max(1, planes // per))
+        self.planes = per * self.nproc
+        self.inboxes = [ctx.Queue() for _ in range(self.nproc)]
+        self.outbox = ctx.Queue()
+        self.procs = []
+        for r in range(self.nproc):
+            sub = np.ascontiguousarray(x[r * per:(r + 1) * per])
+            p = ctx.Process(target=_oracle_worker, args=(r, sub, self.inboxes[r], self.outbox), daemon=True)
+            p.start()
+            self.procs.append(p)
+        for _ in range(self.nproc):
+            self.outbox.get(timeout=600)
+
+    def step(self):
+        t0 = time.perf_counter()
+        for q in self.inboxes:
+            q.put("go")
+        b = 0
+        for _ in range(self.nproc):
+            _, _, _, nb = self.outbox.get(timeout=600)
+            b += nb
+        return time.perf_counter() - t0, b
+
+    def close(self):
+        for q in self.inboxes:
+            q.put("stop")
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def cpu_baseline(fields, target_s=10.0):
+    """The oracle timed on the host cores, on samples of the 512^3 field: one
+    thread on its first planes (about target_s of work), and every core at
+    once on the whole field (one slab per process; median of 3 passes)."""
     shape, x = fields[1]  # the 512^3 field
     planes = 8
     dt, b = cpu_sample_run(x, shape, planes)
     planes = int(max(8, min(shape[0], planes * target_s / max(dt, 1e-3))))
     dt, b = cpu_sample_run(x, shape, planes)
-    return {"value": b / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {planes} planes of the 512x512x512 field ({planes * 512 * 512} elements), "
-                      f"oracle decode to D_p and D_q + mean, variance, 3 derivatives, gradient magnitude, "
-                      f"Laplacian, single thread, {dt:.1f} s"}
+    single = {"value": b / dt / 1e9, "cores": 1,
+              "sample": f"first {planes} planes of the 512x512x512 field ({planes * 512 * 512} elements), "
+                        f"single thread, {dt:.1f} s"}
+    pool = OraclePool(x, shape[0])
+    try:
+        runs = [pool.step() for _ in range(3)]
+    finally:
+        pool.close()
+    wall = float(np.median([w for w, _ in runs]))
+    ball = runs[0][1]
+    return {"value": ball / wall / 1e9, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
+            "sample": f"the whole 512x512x512 field split into {pool.nproc} slabs of {pool.planes // pool.nproc} "
+                      f"planes, one oracle process per host core (spawned), each decoding its slab to D_p and "
+                      f"D_q and running the mean, variance, 3 derivatives, gradient magnitude and Laplacian; "
+                      f"median of 3 passes, {wall:.2f} s each; GB/s of original data (one pass)",
+            "single_thread": single}
+
+
+def _setup():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2603_25206_gb300 import hc
+
+    return hc, torch, torch.device("cuda", torch.cuda.current_device())
+
+
+def guarded(fn):
+    """fn()'s result, or the error it raised: a failing extra measurement
+    never takes the benchmark line down."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001
+        import traceback
+
+        return {"error": f"{type(e).__name__}: {e}", "where": traceback.format_exc().splitlines()[-4:]}
+
+
+SERVING_QPS = (2000.0, 8000.0, 32000.0)
+SERVING_P99_MS = 20.0
+
+
+def run_extras(hc, torch, dev, fields, peak, args):
+    """The other configurations of the paper-like benchmark, each bounded in
+    time, as sub-objects of the benchmark line: the block-mean (HSZx), global
+    predictor (HSZp-nd, HSZp) and box-mean (HSZx-nd) forms of the five fields,
+    the 64-field batched launch, the wide-code float64 field and the serving
+    loop's saturation curve."""
+    out = {}
+    jobs = (("hszx", lambda: measure_hszx(hc, torch, dev, fields)),
+            ("lorenzo", lambda: measure_lorenzo(hc, torch, dev, fields)),
+            ("boxes", lambda: measure_boxes(hc, torch, dev, fields)),
+            ("batched", lambda: measure_batched(hc, torch, dev, steps=max(3, args.steps), warmup=3,
+                                                device_fields=True, sample_clocks=False)),
+            ("wide", lambda: measure_wide(hc, torch, dev, device_field=True)),
+            ("serving", lambda: measure_serving(hc, torch, dev, nfields=args.fields, qps_list=SERVING_QPS,
+                                                duration=args.serving_duration, p99_ms=SERVING_P99_MS)))
+    for name, fn in jobs:
+        t = time.perf_counter()
+        r = guarded(fn)
+        r["wall_s"] = round(time.perf_counter() - t, 1)
+        out[name] = r
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 # -------------------------------------------------------------------- arms
 def run_reference(args):
-    """The oracle as the reference arm: K timed steps on a bounded sample."""
+    """The oracle as the reference arm: K timed steps, each the oracle on
+    every host core at once over a bounded sample of the 512^3 field (one
+    slab per process)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -391,21 +618,26 @@ def run_reference(args):
 
     shape = synth.PAPER_SHAPES[1]
     x = synth.grf_field(shape, 1001)
-    planes = 16
-    for _ in range(args.warmup):
-        cpu_sample_run(x, shape, planes)
-    tot_t, tot_b = 0.0, 0
-    for _ in range(args.steps):
-        dt, b = cpu_sample_run(x, shape, planes)
-        tot_t += dt
-        tot_b += b
+    nproc = os.cpu_count() or 1
+    pool = OraclePool(x, min(shape[0], 16 * nproc), nproc)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        tot_t, tot_b = 0.0, 0
+        for _ in range(args.steps):
+            dt, b = pool.step()
+            tot_t += dt
+            tot_b += b
+    finally:
+        pool.close()
     value = tot_b / tot_t / 1e9
+    sample = (f"the first {pool.planes} planes of the 512x512x512 field per step, {pool.nproc} oracle processes "
+              f"(one per host core) on {pool.planes // pool.nproc} planes each")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"first {planes} planes of 512^3"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {planes} planes of the 512x512x512 field per step, single thread"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.nproc, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -429,6 +661,10 @@ def run_ours(args):
     hc.lib()
     fields = make_fields()
     wl = Workload(hc, torch, dev, fields)
+    # original bytes of one pass over every field (the metric's unit of work);
+    # the operation-weighted figure (x the operations per field) is reported
+    # under its own key
+    bytes_pass = sum(it["n"] * 4 for it in wl.items)
     bytes_step = wl.orig_bytes_per_step
     comp_bytes = sum(it["c"].nbytes for it in wl.items)
     # the library's autotuner picks the fused stencil's tile height per field and op
@@ -482,13 +718,27 @@ def run_ours(args):
     barrier(world)
     clocks = sampler.stop()
     ms = reduce_max(t0.elapsed_time(t1) / args.steps, world)
-    value = weak_value(bytes_step, world, ms)
+    value = weak_value(bytes_pass, world, ms)
+    value_op_weighted = weak_value(bytes_step, world, ms)
     m_ms = sum(x.elapsed_time(y) for _, x, y in mev)
     m_bytes = sum(wl.items[fi]["c"].nbytes + (len(wl.items[fi]["shape"]) + 2) * 4 * wl.items[fi]["n"] + 64
                   for fi, _, _ in mev)
     achieved = m_bytes / (m_ms * 1e-3) / 1e9
     per_elem = read_profile_traffic("stencil_multi_256x384x384")
     m_elems = sum(wl.items[fi]["n"] for fi, _, _ in mev) / max(1, len(mev))
+    per_field = {}
+    for fi, x, y in mev:
+        it = wl.items[fi]
+        d = per_field.setdefault("x".join(map(str, it["shape"])), {"ms": 0.0, "launches": 0, "n": it["n"],
+                                                                    "alg": it["c"].nbytes + (len(it["shape"]) + 2) * 4 * it["n"] + 64})
+        d["ms"] += x.elapsed_time(y)
+        d["launches"] += 1
+    for k, d in per_field.items():
+        a = d["ms"] / d["launches"]
+        per_field[k] = {"kernel": "k_stencil_multi", "avg_launch_ms": round(a, 5),
+                        "gbs_orig": round(d["n"] * 4 / a / 1e6, 1), "algorithmic_bytes_per_launch": d["alg"],
+                        "achieved_gbs": round(d["alg"] / (a * 1e-3) / 1e9, 1),
+                        "roofline_frac": round(d["alg"] / (a * 1e-3) / 1e9 / peak, 4)}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": per_elem * m_elems if per_elem is not None else None,
                 "kernel": "k_stencil_multi", "peak_source": peak_src,
@@ -528,7 +778,8 @@ def run_ours(args):
     elems = sum(wl.items[fi]["n"] for fi, op, _, _ in events if op == dom) / max(1, per[dom]["launches"])
     per_op_launches = {
         "what": "one fused kernel per operation (mean at stage 2, the rest at stage 3), 35 launches per step",
-        "ms_per_step": op_ms, "value": weak_value(bytes_step, world, op_ms),
+        "ms_per_step": op_ms, "value": weak_value(bytes_pass, world, op_ms),
+        "value_op_weighted": weak_value(bytes_step, world, op_ms),
         "one_pass_speedup": op_ms / ms,
         "roofline": {"bound": "hbm", "achieved": op_ach, "peak": peak, "unit": "GB/s", "frac": op_ach / peak,
                      "traffic": op_pe * elems if op_pe is not None else None, "kernel": dom,
@@ -649,24 +900,40 @@ def run_ours(args):
     del copied
     e2e_ms = min(copy_ms, direct_ms) if same else copy_ms
     direct_won = same and direct_ms < copy_ms
-    e2e = {"value": weak_value(bytes_step, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": comp_bytes,
+    e2e = {"value": weak_value(bytes_pass, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": comp_bytes,
+           "value_op_weighted": weak_value(bytes_step, world, e2e_ms),
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
            "mode": "kernel writes to pinned host memory" if direct_won
            else "device outputs copied back on four copy streams",
            "copy_engines_ms_per_step": copy_ms, "direct_host_write_ms_per_step": direct_ms,
            "direct_equals_copied": same}
 
-    per_op = None
-    if args.per_op and rank == 0:
-        per_op = per_op_table(hc, torch, dev, wl)
+    # per-operation kernels cold (REPS runs, L2 flushed before each) on every
+    # field, with the plain path and Table 4's decompress / operate split;
+    # the 512^3 field at the other error bounds; the other configurations
+    cold = sweep = extras = None
+    if rank == 0 and world == 1 and args.extras:
+        cold = []
+        for it in wl.items:
+            def field_rows(it=it):
+                row = cold_table(hc, torch, dev, it["c"], it["shape"], peak, plain=not args.skip_plain, split=True)
+                row["one_pass"] = one_pass_cold(hc, torch, dev, it["c"], it["shape"], peak)
+                return row
+            cold.append(guarded(field_rows))
+        sweep = guarded(lambda: eb_sweep(hc, torch, dev, fields[1][1], fields[1][0], peak))
+        extras = run_extras(hc, torch, dev, fields, peak, args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "value_op_weighted": value_op_weighted,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "fields": ["x".join(map(str, it["shape"])) for it in wl.items],
                            "eb_rel": EB, "block": BLOCK, "compressed_bytes": comp_bytes,
-                           "original_bytes_per_op_pass": sum(it["n"] * 4 for it in wl.items),
+                           "original_bytes_per_pass": bytes_pass,
+                           "value": "original bytes of one pass over the five fields / step time (each pass "
+                                    "computes every operation of every field); value_op_weighted counts "
+                                    "those bytes once per operation",
                            "l2": "no flush: every step streams 5 compressed fields and writes ~6.9 GB of output "
                                  "fields, far larger than the 129 MB L2",
                            "parallelism": f"replicas x{world} (independent fields per GPU)",
@@ -677,18 +944,29 @@ def run_ours(args):
                 "plain": None if plain_ms is None else {
                     "what": "decompress to float32 on the GPU, then the same operations on the floats",
                     "decompress_once_ms_per_step": plain_once_ms,
-                    "decompress_once_value": weak_value(bytes_step, world, plain_once_ms),
+                    "decompress_once_value": weak_value(bytes_pass, world, plain_once_ms),
                     "speedup_vs_decompress_once": plain_once_ms / ms,
                     "decompress_per_op_ms_per_step": plain_ms,
-                    "decompress_per_op_value": weak_value(bytes_step, world, plain_ms),
+                    "decompress_per_op_value": weak_value(bytes_pass, world, plain_ms),
                     "speedup_vs_decompress_per_op": plain_ms / ms},
                 "per_op_launches": per_op_launches,
                 "e2e": e2e, "gpu_launches": len(wl.items) * args.steps,
                 "roofline": roofline, "clocks": clocks}
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(fields)
-        if per_op is not None:
-            line["per_op"] = per_op
+        line["per_field"] = per_field
+        if cold is not None:
+            line["per_op_cold"] = {"timing": f"median of {REPS} CUDA-event runs per kernel, a 512 MB write "
+                                             "(4x L2) before each", "eb_rel": EB, "fields": cold}
+            f512 = next((r for r in cold if r.get("field") == "512x512x512"), None)
+            if f512 is not None:
+                line["field_512"] = {"one_pass": f512["one_pass"],
+                                     "ops": {k: {"roofline_frac": v["roofline_frac"], "ms": v["ms"],
+                                                 "speedup_vs_plain": v.get("speedup_vs_plain")}
+                                             for k, v in f512["ops"].items()},
+                                     "eb_sweep": sweep}
+        if extras is not None:
+            line["configs"] = extras
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -697,7 +975,7 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
+def measure_batched(hc, torch, dev, steps, warmup, device_fields=False, sample_clocks=True):
     """The batched form: 64 float32 fields of uneven sizes (every axis drawn
     log-uniformly from [32, 384], seed 3; k^-3 field + 5% spikes), value-range-
     relative eb = 1e-3.  Mean, variance and Laplacian of every field in ONE
@@ -707,31 +985,29 @@ def run_batched(args):
     operations).  Compared on the same GPU with the same streams: the three
     one-field fused calls per field (192 launches), and the plain path
     (decompress each field to float32, then the three operations)."""
-    import torch
-
-    import __graft_entry__
     import synth
 
-    __graft_entry__.build()
-    from paper_2603_25206_gb300 import hc
-
-    dev = torch.device("cuda", torch.cuda.current_device())
     shapes = synth.log_uniform_shapes(64, 32, 384, 3)
-    raw = [torch.from_numpy(synth.grf_field(sh, 3000 + j)).to(dev) for j, sh in enumerate(shapes)]
+    if device_fields:  # the same recipe drawn on the device (fast; different numbers)
+        raw = [synth.grf_field_device(sh, 3000 + j, dev) for j, sh in enumerate(shapes)]
+    else:
+        raw = [torch.from_numpy(synth.grf_field(sh, 3000 + j)).to(dev) for j, sh in enumerate(shapes)]
     n_total = sum(int(x.numel()) for x in raw)
     flush = lambda: flush_l2(torch, dev)  # noqa: E731
     best, table = hc.batch_autotune(raw, EB, True, "mean|variance|laplacian", flush=flush)
     del raw
     b, comps = best["batch"], best["comps"]
     comp_bytes = sum(c.nbytes for c in comps)
-    sampler = ClockSampler(smi_index(0))
-    sampler.start()
-    for _ in range(args.warmup):
+    sampler = ClockSampler(smi_index(0)) if sample_clocks else None
+    if sampler:
+        sampler.start()
+    for _ in range(warmup):
         b.replay()
     torch.cuda.synchronize()
-    sampler.mark()
+    if sampler:
+        sampler.mark()
     ev = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -740,9 +1016,11 @@ def run_batched(args):
         e1.record()
         ev.append((e0, e1))
     torch.cuda.synchronize()
-    sampler.mark()
-    clocks = sampler.stop()
-    ms = sum(a.elapsed_time(z) for a, z in ev) / args.steps
+    clocks = None
+    if sampler:
+        sampler.mark()
+        clocks = sampler.stop()
+    ms = sum(a.elapsed_time(z) for a, z in ev) / steps
     assert b.status() == 0
     value = n_total * 4 / (ms * 1e-3) / 1e9
 
@@ -772,16 +1050,17 @@ def run_batched(args):
     alg = comp_bytes + n_total * 4 + 64 * len(comps)
     achieved = alg / (ms * 1e-3) / 1e9
     line = {
-        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "batched: 64 float32 fields, every axis log-uniform in [32, 384] (seed 3), k^-3 "
                                "GRF + 5% spikes, value-range-relative eb=1e-3; mean + variance + Laplacian per "
                                "field in one persistent fused launch under a CUDA graph; S and threads autotuned",
                    "elements": n_total, "compressed_bytes": comp_bytes, "S": best["S"],
                    "threads": best["threads"], "ty": best["ty"], "grid": b.grid,
-                   "l2": "flushed between timed iterations"},
-        "gpu_launches": args.steps,
+                   "l2": "flushed between timed iterations",
+                   "fields_drawn_on": "device" if device_fields else "host"},
+        "gpu_launches": steps,
         "autotune": table,
         "one_field_calls_ms": round(t_sep, 4), "speedup_vs_one_field_calls": round(t_sep / ms, 3),
         "plain_ms": round(t_plain, 4), "speedup_vs_plain": round(t_plain / ms, 3),
@@ -791,34 +1070,26 @@ def run_batched(args):
                      "algorithmic_bytes": "compressed streams + float32 Laplacian outputs + 64 B per field"},
         "clocks": clocks,
     }
-    print(json.dumps(line))
     b.close()
+    return line
+
+
+def run_batched(args):
+    hc, torch, dev = _setup()
+    print(json.dumps(measure_batched(hc, torch, dev, args.steps, args.warmup)))
     return 0
 
 
-def run_serving(args):
-    """The serving form: 200 compressed float32 fields resident on the device
-    (cube side log-uniform in [64, 512], k^-3 Gaussian random fields drawn on
-    the device, eb uniform over {1e-2, 1e-3, 1e-4} value-range-relative,
-    block 32); a seeded Poisson stream of `--qps` queries per second for
-    `--duration` seconds mixing mean / variance / gradient-magnitude queries
-    at random stages; 120 GB admission budget, 4 stream slots, up to 64
-    queries per step.  The same arrival stream is then served by the plain
-    path (every query decompresses to float32 first).  Reports p50 / p99
-    latency and throughput for both."""
-    import torch
-
-    import __graft_entry__
+def serving_fields(hc, torch, dev, nfields):
+    """The serving set: nfields compressed float32 fields resident on the
+    device (cube side log-uniform in [64, 512], k^-3 Gaussian random fields
+    drawn on the device, eb uniform over {1e-2, 1e-3, 1e-4} value-range-
+    relative, block 32)."""
     import synth
 
-    __graft_entry__.build()
-    from paper_2603_25206_gb300 import hc, serving
-
-    dev = torch.device("cuda", torch.cuda.current_device())
     rng = np.random.default_rng(4)
     fields, fbytes = [], {}
-    t_gen = time.perf_counter()
-    for j in range(args.fields):
+    for j in range(nfields):
         side = int(round(math.exp(rng.uniform(math.log(64), math.log(512)))))
         eb = float(rng.choice([1e-2, 1e-3, 1e-4]))
         x = synth.grf_field_device((side, side, side), 5000 + j, dev, spikes=0.0)
@@ -826,54 +1097,83 @@ def run_serving(args):
         fbytes[j] = x.numel() * 4
         del x
     torch.cuda.synchronize()
-    t_gen = time.perf_counter() - t_gen
-    comp = sum(c.nbytes for c in fields)
-    raw = sum(fbytes.values())
-    out = {"metric": "serving: query latency p50/p99 and throughput, homomorphic vs plain",
-           "config": {"workload": f"serving: {args.fields} float32 fields, cube side log-uniform 64..512, k^-3 "
-                                  f"GRF, eb in {{1e-2,1e-3,1e-4}} (REL), block 32; Poisson {args.qps:g} qps for "
-                                  f"{args.duration:g} s (seed 4) of mean/variance/gradmag at random stages; "
-                                  f"120 GB admission budget, 4 slots, <= 64 queries per step",
-                      "raw_bytes": raw, "compressed_bytes": comp, "setup_s": round(t_gen, 1)},
-           "data": "synthetic"}
+    return fields, fbytes
+
+
+def serve_once(hc, torch, fields, fbytes, qps, duration, plain):
+    """One seeded Poisson stream served to the end: p50 / p99 latency and
+    throughput (120 GB admission budget, 4 stream slots, <= 64 queries per step)."""
+    from paper_2603_25206_gb300 import serving
+
     budget = 120 * 10**9
-    for name, plain in (("homomorphic", False), ("plain", True)):
-        qs = serving.poisson_queries(len(fields), args.qps, args.duration, 4, plain=plain)
-        # warm-up on a short prefix (kernels, allocator, plans)
-        serving.run(hc, fields, qs[:64], budget, slots=4, max_batch=64)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        recs, sch = serving.run(hc, fields, qs, budget, slots=4, max_batch=64)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        summ = serving.summarize(recs, qs, fbytes, wall=wall)
-        summ["offered"] = len(qs)
-        summ["refused"] = len(sch.refused)
-        summ["peak_reserved_gb"] = round(sch.peak_bytes / 1e9, 3)
-        out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
-    print(json.dumps(out))
+    qs = serving.poisson_queries(len(fields), qps, duration, 4, plain=plain)
+    # warm-up on a short prefix (kernels, allocator, plans)
+    serving.run(hc, fields, qs[:64], budget, slots=4, max_batch=64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    recs, sch = serving.run(hc, fields, qs, budget, slots=4, max_batch=64)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    summ = serving.summarize(recs, qs, fbytes, wall=wall)
+    summ["offered_qps"] = qps
+    summ["offered"] = len(qs)
+    summ["refused"] = len(sch.refused)
+    summ["peak_reserved_gb"] = round(sch.peak_bytes / 1e9, 3)
+    return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
+
+
+def measure_serving(hc, torch, dev, nfields, qps_list, duration, p99_ms=SERVING_P99_MS):
+    """The serving form: a seeded Poisson stream of mean / variance /
+    gradient-magnitude queries at random stages on the resident serving set,
+    served by the homomorphic path and by the plain path (every query
+    decompresses to float32 first), at each offered rate of qps_list.  The
+    saturation point of a path is the highest offered rate it serves with
+    p99 <= p99_ms and a completed rate of at least 95% of the offered one."""
+    t_gen = time.perf_counter()
+    fields, fbytes = serving_fields(hc, torch, dev, nfields)
+    t_gen = time.perf_counter() - t_gen
+    out = {"metric": "serving: query latency p50/p99 and throughput, homomorphic vs plain, per offered rate",
+           "config": {"workload": f"serving: {nfields} float32 fields, cube side log-uniform 64..512, k^-3 "
+                                  f"GRF, eb in {{1e-2,1e-3,1e-4}} (REL), block 32; Poisson queries (seed 4) of "
+                                  f"mean/variance/gradmag at random stages for {duration:g} s per rate; 120 GB "
+                                  f"admission budget, 4 slots, <= 64 queries per step",
+                      "raw_bytes": sum(fbytes.values()), "compressed_bytes": sum(c.nbytes for c in fields),
+                      "setup_s": round(t_gen, 1), "p99_bound_ms": p99_ms},
+           "data": "synthetic", "rates": {}}
+    sat = {"homomorphic": 0.0, "plain": 0.0}
+    for qps in qps_list:
+        row = {}
+        for name, plain in (("homomorphic", False), ("plain", True)):
+            r = serve_once(hc, torch, fields, fbytes, qps, duration, plain)
+            row[name] = r
+            if r.get("p99_ms", 1e9) <= p99_ms and r.get("qps", 0.0) >= 0.95 * qps:
+                sat[name] = max(sat[name], qps)
+        out["rates"][f"{qps:g}"] = row
+    out["saturation_qps"] = sat
+    del fields
+    return out
+
+
+def run_serving(args):
+    """The serving form at one offered rate (--qps, --duration) or, with
+    --qps 0, the saturation curve over the default rates."""
+    hc, torch, dev = _setup()
+    qps = SERVING_QPS if args.qps <= 0 else (args.qps,)
+    print(json.dumps(measure_serving(hc, torch, dev, args.fields, qps, args.duration)))
     return 0
 
 
-def run_hszx(args):
+def measure_hszx(hc, torch, dev, fields):
     """The block-mean (HSZx) form of the paper-like workload: the same five
     fields compressed with block means as metadata (block 32, eb 1e-3
     value-range relative).  Per field and operation: the fused time at every
     stage it is defined at (mean at stages 1, 2, 3; standard deviation at 2
     and 3; all stencils in one pass at 3) and the plain path (decompress to
-    float32, then the operation), median CUDA-event time over 5 runs with an
-    L2 flush before each.  GB/s counts the field's original bytes."""
-    import torch
-
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_2603_25206_gb300 import hc
-
-    dev = torch.device("cuda", torch.cuda.current_device())
+    float32, then the operation), median CUDA-event time over REPS runs with
+    an L2 flush before each.  GB/s counts the field's original bytes."""
     rows = []
     tot = {}
-    for shape, x in make_fields():
+    for shape, x in fields:
         xd = torch.from_numpy(x).to(dev)
         cx = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK, predictor="mean"))
         cd = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK))
@@ -929,15 +1229,20 @@ def run_hszx(args):
     line = {"metric": "HSZx (block-mean) operations: GB/s of original data per stage, vs the plain path",
             "unit": "GB/s", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("block 32;", "block 32, block-mean predictor (HSZx);"),
-                       "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
+                       "timing": f"median of {REPS} CUDA-event runs per op, L2 flushed before each"},
             "totals_ms": {k: round(v, 4) for k, v in tot.items()},
             "totals_gbs_orig": {k: round(orig / v / 1e6, 1) for k, v in tot.items()},
             "per_field": rows}
-    print(json.dumps(line))
+    return line
+
+
+
+def run_hszx(args):
+    hc, torch, dev = _setup()
+    print(json.dumps(measure_hszx(hc, torch, dev, make_fields())))
     return 0
 
-
-def run_lorenzo(args):
+def measure_lorenzo(hc, torch, dev, fields):
     """The global predictors on the paper-like workload: the same five fields
     compressed as HSZp-nd (Lorenzo over the field's axes) and as HSZp (delta
     across blocks over the flattened field), block 32, eb 1e-3 value-range
@@ -945,21 +1250,13 @@ def run_lorenzo(args):
     fused stage-2 mean (weighted sum), the statistics and the derivative along
     the first axis and the Laplacian at stages 2 and 3, against the plain path
     (decompress to float32, then the operation); decompression to D_q.
-    Median CUDA-event time over 5 runs with an L2 flush before each; GB/s
+    Median CUDA-event time over REPS runs with an L2 flush before each; GB/s
     counts the field's original bytes.  The roofline line is the stage-2 mean
     kernel (k_global_mean) at its algorithmic bytes, the compressed stream."""
-    import torch
-
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_2603_25206_gb300 import hc
-
-    dev = torch.device("cuda", torch.cuda.current_device())
     peak, peak_src = measured_peaks()
     rows, tot = [], {}
     mean_bytes = 0
-    for shape, x in make_fields():
+    for shape, x in fields:
         xd = torch.from_numpy(x).to(dev)
         cl = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK, predictor="lorenzo"))
         cg = hc._trim(hc.compress(xd, EB, rel=True, S=BLOCK, predictor="global"))
@@ -1014,40 +1311,37 @@ def run_lorenzo(args):
             "unit": "GB/s", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("block 32;", "block 32, Lorenzo predictor (HSZp-nd) and "
                                                                  "delta across blocks (HSZp);"),
-                       "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
+                       "timing": f"median of {REPS} CUDA-event runs per op, L2 flushed before each"},
             "roofline": {"kernel": "k_global_mean", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                          "algorithmic_bytes": "compressed stream + 64 B per field"},
             "totals_ms": {k: round(v, 4) for k, v in tot.items()},
             "totals_gbs_orig": {k: round(orig / v / 1e6, 1) for k, v in tot.items()},
             "per_field": rows}
-    print(json.dumps(line))
+    return line
+
+
+
+def run_lorenzo(args):
+    hc, torch, dev = _setup()
+    print(json.dumps(measure_lorenzo(hc, torch, dev, make_fields())))
     return 0
 
-
-def run_boxes(args):
+def measure_boxes(hc, torch, dev, fields):
     """HSZx-nd (block means over boxes of codes) on the paper-like workload:
     the five fields in 4x4x4 boxes (8x8 for the 2-D field), eb 1e-3 value-range
     relative.  Per field: the stream size beside 1-D HSZx (block 64) and the
     block-head stream; the mean at stages 1, 2 and 3, the standard deviation
     at stages 2 and 3, the derivative along the first axis and the Laplacian
     at stages 2 and 3, against the plain path (decompress to float32, then the
-    operation).  Median CUDA-event time over 5 runs with an L2 flush before
+    operation).  Median CUDA-event time over REPS runs with an L2 flush before
     each; GB/s counts the field's original bytes.  The roofline line is the
     stage-3 variance kernel (k_stats_box) at its algorithmic bytes, the
     compressed stream."""
-    import torch
-
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_2603_25206_gb300 import hc
-
-    dev = torch.device("cuda", torch.cuda.current_device())
     peak, peak_src = measured_peaks()
     rows, tot = [], {}
     var_bytes = 0
-    for shape, x in make_fields():
+    for shape, x in fields:
         block = (4, 4, 4) if len(shape) == 3 else (8, 8)
         xd = torch.from_numpy(x).to(dev)
         cb = hc._trim(hc.compress(xd, EB, rel=True, predictor="mean-nd", block=block))
@@ -1101,16 +1395,21 @@ def run_boxes(args):
             "unit": "GB/s", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("block 32;", "boxes of 4x4x4 (8x8 in 2-D), box-mean predictor "
                                                                  "(HSZx-nd);"),
-                       "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
+                       "timing": f"median of {REPS} CUDA-event runs per op, L2 flushed before each"},
             "roofline": {"kernel": "k_stats_box", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                          "algorithmic_bytes": "compressed stream + 64 B per field"},
             "totals_ms": {k: round(v, 4) for k, v in tot.items()},
             "totals_gbs_orig": {k: round(orig / v / 1e6, 1) for k, v in tot.items()},
             "per_field": rows}
-    print(json.dumps(line))
-    return 0
+    return line
 
+
+
+def run_boxes(args):
+    hc, torch, dev = _setup()
+    print(json.dumps(measure_boxes(hc, torch, dev, make_fields())))
+    return 0
 
 def run_profile_boxes():
     """Small case for ncu captures of the HSZx-nd kernels: one 256x384x384
@@ -1192,37 +1491,31 @@ def run_profile_lorenzo():
     return 0
 
 
-def run_wide(args):
+def measure_wide(hc, torch, dev, device_field=False):
     """The wide-code configuration: one float64 512 x 512 x 1024 field (k^-3
     field times 1e4 plus a linear trend), block 64, value-range-relative
     eb 1e-6, and its ABS companion (eps = range / 2^31, block widths in the
     upper 20s).  Per form and operation: fused time (mean, variance with exact
     128-bit sums, derivative per axis into float32 and float64) against the
-    plain path (decompress to float64, then the operation), median of 5
+    plain path (decompress to float64, then the operation), median of REPS
     CUDA-event runs with an L2 flush before each.  GB/s counts the field's
     original bytes (8 per element)."""
-    import torch
-
-    import __graft_entry__
     import synth
 
-    __graft_entry__.build()
-    from paper_2603_25206_gb300 import hc
-
-    dev = torch.device("cuda", torch.cuda.current_device())
     shape = (512, 512, 1024)
-    x = synth.wide_field(shape, 3000)
+    if device_field:  # the same recipe drawn on the device (fast; different numbers)
+        x = synth.wide_field_device(shape, 3000, dev)
+    else:
+        x = torch.from_numpy(synth.wide_field(shape, 3000)).to(dev)
     forms = {}
     for form in ("rel_1e-6", "abs_2^-31"):
         if form == "rel_1e-6":
-            xd = torch.from_numpy(x).to(dev)
-            c = hc._trim(hc.compress(xd, 1e-6, rel=True, S=64))
+            c = hc._trim(hc.compress(x, 1e-6, rel=True, S=64))
         else:
-            xc = np.ascontiguousarray(x - (x.max() + x.min()) / 2)
-            xd = torch.from_numpy(xc).to(dev)
-            c = hc._trim(hc.compress(xd, float(xc.max() - xc.min()) / 2**31, rel=False, S=64))
+            lo, hi = float(x.min()), float(x.max())
+            xc = x - (hi + lo) / 2
+            c = hc._trim(hc.compress(xc, float(xc.max() - xc.min()) / 2**31, rel=False, S=64))
             del xc
-        del xd
         n = int(np.prod(shape))
         scal = torch.empty(hc.SCALAR_BYTES, dtype=torch.uint8, device=dev)
         o32 = torch.empty(shape, dtype=torch.float32, device=dev)
@@ -1245,12 +1538,19 @@ def run_wide(args):
                        "ms": {k: round(v, 4) for k, v in t.items()},
                        "gbs_orig": {k: round(n * 8 / v / 1e6, 1) for k, v in t.items()}}
         del c, o32, o64, df, sf
-    print(json.dumps({"metric": "wide-code field: GB/s of original data per operation, fused vs plain",
-                      "unit": "GB/s", "data": "synthetic",
-                      "config": {"workload": "wide-code: float64 512x512x1024 k^-3 GRF x 1e4 + linear trend, block 64; "
-                                             "REL 1e-6 and ABS range/2^31",
-                                 "timing": "median of 5 CUDA-event runs per op, L2 flushed before each"},
-                      "forms": forms}))
+    del x
+    return {"metric": "wide-code field: GB/s of original data per operation, fused vs plain",
+            "unit": "GB/s", "data": "synthetic",
+            "config": {"workload": "wide-code: float64 512x512x1024 k^-3 GRF x 1e4 + linear trend, block 64; "
+                                   "REL 1e-6 and ABS range/2^31",
+                       "timing": f"median of {REPS} CUDA-event runs per op, L2 flushed before each",
+                       "field_drawn_on": "device" if device_field else "host"},
+            "forms": forms}
+
+
+def run_wide(args):
+    hc, torch, dev = _setup()
+    print(json.dumps(measure_wide(hc, torch, dev)))
     return 0
 
 
@@ -1325,7 +1625,6 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--per-op", action="store_true", help="also time every op at every stage per field")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-small", action="store_true", help="run the small ncu case and exit")
@@ -1343,6 +1642,10 @@ def main(argv=None):
     ap.add_argument("--fields", type=int, default=200)
     ap.add_argument("--qps", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--serving-duration", type=float, default=2.0,
+                    help="seconds of queries per offered rate in the default run's saturation curve")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the cold per-operation tables, the error-bound sweep and the other configurations")
     args = ap.parse_args(argv)
     if args.profile_small:
         return run_profile_small()

@@ -434,25 +434,41 @@ typedef enum {
   HC_BATCH_VARIANCE = 2,    /* d_scalar: mean, variance, std; exact s1, s2 */
   HC_BATCH_DERIVATIVE = 4,  /* d_field: derivative along `axis` */
   HC_BATCH_GRADMAG = 8,     /* d_field: gradient magnitude */
-  HC_BATCH_LAPLACIAN = 16   /* d_field: Laplacian */
+  HC_BATCH_LAPLACIAN = 16,  /* d_field: Laplacian */
+  HC_BATCH_DIVERGENCE = 32, /* d_field: divergence of the item's components (Section V-C) */
+  HC_BATCH_CURL = 64        /* d_field: 2-D curl of the item's two components (Section V-C) */
 } hc_batch_op;
 
+/* A batch item is one field, or (DIVERGENCE / CURL) one vector field given
+ * by its component streams: the values are exactly those of hc_op_divergence
+ * / hc_op_curl on the same components at stage Q (one fused tile reads every
+ * component's stream).  A vector item has that one operation and no other;
+ * its components are block-head or block-mean streams (HC_PRED_DELTA or
+ * HC_PRED_MEAN) of one shape and block size (other predictors:
+ * HC_ERR_UNSUPPORTED, use hc_op_divergence / hc_op_curl); DIVERGENCE takes
+ * ndim components, CURL a 2-D field's two. */
 typedef struct hc_batch_item {
-  const void* d_stream;  /* device: the compressed stream, 16-byte aligned */
-  hc_header hdr;         /* host copy of its header (hc_read_header / hc_compress) */
+  const void* d_stream;  /* device: the compressed stream, 16-byte aligned (unused by vector items) */
+  hc_header hdr;         /* host copy of its header (hc_read_header / hc_compress; unused by vector items) */
   uint32_t ops;          /* OR of hc_batch_op, with at most one field operation */
   int32_t axis;          /* HC_BATCH_DERIVATIVE: user axis in [0, ndim) */
   hc_scalar* d_scalar;   /* device: statistics result, or NULL without MEAN / VARIANCE */
   void* d_field;         /* device: N outputs of field_dtype, or NULL without a field op */
-  int32_t field_dtype;   /* HC_F32, HC_F64, or HC_I64 (exact numerators; not GRADMAG) */
-  int32_t reserved;
+  int32_t field_dtype;   /* HC_F32, HC_F64, or HC_I64 (exact numerators; not GRADMAG; one eps for
+                            every component of a vector item) */
+  int32_t ncomp;         /* DIVERGENCE / CURL: components in comps; 0 otherwise */
+  const hc_stage* comps; /* DIVERGENCE / CURL: HOST array of ncomp HC_STAGE_COMPRESSED stages at level
+                            HC_STAGE_Q (streams 16-byte aligned, headers as for d_stream / hdr), read
+                            by hc_batch_plan only; NULL otherwise */
 } hc_batch_item;
 
 /* Launch shape of the batch kernel (GPU tiling choices, no counterpart in
  * the paper).  Zero fields take the defaults. */
 typedef struct hc_batch_tune {
   int32_t threads;      /* threads per CTA: 128, 256 (default) or 512 */
-  int32_t ty;           /* largest stencil tile height in rows (16, 8, 4, 2 or 1); 0: largest that fits */
+  int32_t ty;           /* largest stencil tile height in rows; 0: no limit.  Each field takes the largest
+                           height up to it (the whole plane when it has at most 128 rows, else 128, 64, 32,
+                           16, 8, 4, 2 or 1) whose tile fits three CTAs per SM */
   int64_t unit_elems;   /* output points per stencil work unit; 0: about six units per CTA */
   int32_t ctas_per_sm;  /* upper limit on resident CTAs per SM; 0: occupancy limit */
   int32_t reserved;

@@ -8,7 +8,8 @@
 // 2^15, 256 threads per CTA: a loader warp prefetches the next slabs while
 // seven warps decode and compute) or else of the general one; a field with statistics only
 // (Section V-A) contributes one unit per two chunks of blocks, decoded to
-// D_q in shared memory and summed.  Statistics are taken at stage 3 (the codes
+// D_q in shared memory and summed; a vector field (divergence or curl,
+// Section V-C) one unit per output tile of the fused multi-component tile.  Statistics are taken at stage 3 (the codes
 // q): s1 = sum q (64-bit) and s2 = sum q^2 (128-bit), exact.  When a field has
 // both a stencil and statistics, the stencil units add up the codes they own,
 // so one pass over the stream serves both.
@@ -28,6 +29,7 @@
 #include "hc_launch.h"
 #include "hc_stencil_pipe.cuh"
 #include "hc_stencil_tile.cuh"
+#include "hc_vector_tile.cuh"
 
 namespace hc {
 
@@ -40,7 +42,7 @@ constexpr uint32_t kPlanMagic = 0x4E4C5042u;  // "BPLN"
 enum { STATS_NONE = 0, STATS_MEAN = 1, STATS_VAR = 2 };
 
 // One field of the batch as the kernel sees it.
-enum { KIND_TILE = 0, KIND_PIPE = 1, KIND_STATS = 2 };
+enum { KIND_TILE = 0, KIND_PIPE = 1, KIND_STATS = 2, KIND_VECTOR = 3 };
 
 struct BItem {
   DevStream s;
@@ -57,7 +59,13 @@ struct BItem {
   int rwords;          // statistics unit: words of the decoded D_q tile
   int kind;            // KIND_*
   int vec;             // KIND_PIPE: outputs per work item of the pipelined tile (8, 4 or 1)
+  VArgs va;            // KIND_VECTOR: the components, signs and output type (tile geometry in g)
 };
+
+// Unit kinds a launch's kernel carries: every kind, or (256 threads) only
+// pipelined stencil tiles, with the operation at run time or the float32
+// Laplacian at compile time.
+enum { KSET_ALL = 0, KSET_PIPE = 1, KSET_PIPE_LAP = 2 };
 
 struct BPlan {
   uint32_t magic;
@@ -65,7 +73,7 @@ struct BPlan {
   int32_t threads;
   int32_t grid;
   int32_t smem;
-  int32_t pad;
+  int32_t kset;  // KSET_*
   int64_t total_units;
   int64_t items_off;   // byte offset of BItem[n]
   int64_t prefix_off;  // byte offset of int64 unit prefix[n + 1]
@@ -128,6 +136,14 @@ template <int V, int PRED>
 __device__ __noinline__ void pipe_unit(const BItem& it, int64_t lu, int* err, unsigned char* smem, Moments& mo) {
   pipe_tile<ST_RUNTIME, ST_RUNTIME, V, true, PRED>(it.s, it.pg, (int)(lu % it.pg.nyt), (int)(lu / it.pg.nyt),
                                                   it.field, err, smem, mo);
+}
+
+// A divergence / curl output tile (operation and output type in the item's
+// VArgs).
+template <bool SMALL>
+__device__ __noinline__ void vector_unit(const BItem& it, int64_t lu, int* err, uint32_t* smem, uint32_t* s_warp,
+                                         int* s_flag, long long (*s_base)[3][66]) {
+  vector_tile<SMALL>(it.va, it.g, lu, it.field, err, smem, s_warp, s_flag, s_base);
 }
 
 // The float32 Laplacian (the batched workload's field operation) with its
@@ -207,20 +223,22 @@ __device__ void publish(const BItem& it, const Moments& mo, BAcc* a, int* status
   }
 }
 
-// Resident CTAs per SM assumed for the register budget: the tiles' shared
-// memory (tens of KB) allows about two 256-thread CTAs per SM, so more than
-// that would only force spills.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 ? 2 : 1)) k_batch(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
+// The persistent scheduling loop: every CTA takes the next unit from the
+// counter, copies its item into shared memory, runs the unit and publishes
+// its sums.  KSET_ALL dispatches over every unit kind; the pipelined-only
+// sets inline the one tile they carry, so their kernels keep the tile's own
+// register budget.
+template <int THREADS, int KSET>
+__device__ __forceinline__ void batch_loop(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_warp[32];
   __shared__ int s_flag;
-  __shared__ long long s_base[3][66];
+  __shared__ long long s_base[3][3][66];  // ring-slot offsets: [0] for scalar stencils, all for vector tiles
   __shared__ __align__(16) BItem s_it;
   __shared__ long long s_unit;
   __shared__ int s_item;
   const BPlan* P = reinterpret_cast<const BPlan*>(plan);
-  const bool valid = P->magic == kPlanMagic && P->threads == THREADS;
+  const bool valid = P->magic == kPlanMagic && P->threads == THREADS && P->kset == KSET;
   if (!valid && threadIdx.x == 0) set_error(&ws->status, HC_ERR_INVALID_ARG);
   const BItem* items = reinterpret_cast<const BItem*>(plan + (valid ? P->items_off : 0));
   const int64_t* prefix = reinterpret_cast<const int64_t*>(plan + (valid ? P->prefix_off : 0));
@@ -258,26 +276,57 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 
     const int64_t lu = s_unit;
     int* err = &acc[it].err;
     Moments mo;
-    if (s_it.kind == KIND_PIPE) {
-      if constexpr (THREADS == kThreads) {
-        unsigned char* sm = reinterpret_cast<unsigned char*>(smem);
-        if (s_it.vec == 8)
-          pipe_unit_p<8>(s_it, lu, err, sm, mo);
-        else if (s_it.vec == 4)
-          pipe_unit_p<4>(s_it, lu, err, sm, mo);
-        else
-          pipe_unit_p<1>(s_it, lu, err, sm, mo);
+    unsigned char* sm = reinterpret_cast<unsigned char*>(smem);
+    if constexpr (KSET == KSET_PIPE_LAP) {
+      float* f = reinterpret_cast<float*>(s_it.field);
+      const int yt = (int)(lu % s_it.pg.nyt), zt = (int)(lu / s_it.pg.nyt);
+      const bool mean = s_it.s.pred == HC_PRED_MEAN;
+#define HC_LAP(VV)                                                                                     \
+  if (mean)                                                                                            \
+    pipe_tile<ST_LAPLACIAN, HC_F32, VV, true, HC_PRED_MEAN>(s_it.s, s_it.pg, yt, zt, f, err, sm, mo);  \
+  else                                                                                                 \
+    pipe_tile<ST_LAPLACIAN, HC_F32, VV, true, HC_PRED_DELTA>(s_it.s, s_it.pg, yt, zt, f, err, sm, mo);
+      if (s_it.vec == 8) {
+        HC_LAP(8)
+      } else if (s_it.vec == 4) {
+        HC_LAP(4)
+      } else {
+        HC_LAP(1)
       }
-    } else if (s_it.fop >= 0) {
-      if (s_it.s.S <= 32)
-        stencil_unit<true>(s_it, lu, err, smem, s_warp, &s_flag, s_base, mo);
+#undef HC_LAP
+    } else if constexpr (KSET == KSET_PIPE) {
+      if (s_it.vec == 8)
+        pipe_unit_p<8>(s_it, lu, err, sm, mo);
+      else if (s_it.vec == 4)
+        pipe_unit_p<4>(s_it, lu, err, sm, mo);
       else
-        stencil_unit<false>(s_it, lu, err, smem, s_warp, &s_flag, s_base, mo);
+        pipe_unit_p<1>(s_it, lu, err, sm, mo);
     } else {
-      if (s_it.s.S <= 32)
-        stats_unit<true>(s_it, lu, err, smem, s_warp, &s_flag, mo);
-      else
-        stats_unit<false>(s_it, lu, err, smem, s_warp, &s_flag, mo);
+      if (s_it.kind == KIND_PIPE) {
+        if constexpr (THREADS == kThreads) {
+          if (s_it.vec == 8)
+            pipe_unit_p<8>(s_it, lu, err, sm, mo);
+          else if (s_it.vec == 4)
+            pipe_unit_p<4>(s_it, lu, err, sm, mo);
+          else
+            pipe_unit_p<1>(s_it, lu, err, sm, mo);
+        }
+      } else if (s_it.kind == KIND_VECTOR) {
+        if (s_it.va.s[0].S <= 32)
+          vector_unit<true>(s_it, lu, err, smem, s_warp, &s_flag, s_base);
+        else
+          vector_unit<false>(s_it, lu, err, smem, s_warp, &s_flag, s_base);
+      } else if (s_it.fop >= 0) {
+        if (s_it.s.S <= 32)
+          stencil_unit<true>(s_it, lu, err, smem, s_warp, &s_flag, s_base[0], mo);
+        else
+          stencil_unit<false>(s_it, lu, err, smem, s_warp, &s_flag, s_base[0], mo);
+      } else {
+        if (s_it.s.S <= 32)
+          stats_unit<true>(s_it, lu, err, smem, s_warp, &s_flag, mo);
+        else
+          stats_unit<false>(s_it, lu, err, smem, s_warp, &s_flag, mo);
+      }
     }
     publish<THREADS>(s_it, mo, acc + it, &ws->status);
     __syncthreads();
@@ -290,12 +339,29 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 
   }
 }
 
+// Resident CTAs per SM assumed for the register budget: the tiles' shared
+// memory (tens of KB) allows about two 256-thread CTAs per SM, so more than
+// that would only force spills.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 ? 2 : 1)) k_batch(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
+  batch_loop<THREADS, KSET_ALL>(plan, ws, acc);
+}
+
+// Batches of pipelined tiles only: three 256-thread CTAs per SM (the tile's
+// shared memory allows three), the tile inlined.
+template <int KSET>
+__global__ void __launch_bounds__(kThreads, 3) k_batch_pipe(const uint8_t* __restrict__ plan, BWs* ws, BAcc* acc) {
+  batch_loop<kThreads, KSET>(plan, ws, acc);
+}
+
 template <int THREADS>
 const void* batch_kernel() {
   return reinterpret_cast<const void*>(k_batch<THREADS>);
 }
 
-const void* kernel_for(int threads) {
+const void* kernel_for(int threads, int kset = KSET_ALL) {
+  if (kset == KSET_PIPE) return reinterpret_cast<const void*>(k_batch_pipe<KSET_PIPE>);
+  if (kset == KSET_PIPE_LAP) return reinterpret_cast<const void*>(k_batch_pipe<KSET_PIPE_LAP>);
   switch (threads) {
     case 128:
       return batch_kernel<128>();
@@ -312,6 +378,15 @@ int launch(const BPlan* hp, const void* d_plan, void* d_ws, cudaStream_t st) {
   BWs* ws = reinterpret_cast<BWs*>(d_ws);
   BAcc* acc = reinterpret_cast<BAcc*>(reinterpret_cast<char*>(d_ws) + sizeof(BWs));
   const uint8_t* p = reinterpret_cast<const uint8_t*>(d_plan);
+  if (hp->kset == KSET_PIPE) {
+    k_batch_pipe<KSET_PIPE><<<hp->grid, kThreads, hp->smem, st>>>(p, ws, acc);
+    return check_launch_cfg("batch (pipelined tiles)", kernel_for(hp->threads, hp->kset), hp->grid, hp->smem);
+  }
+  if (hp->kset == KSET_PIPE_LAP) {
+    k_batch_pipe<KSET_PIPE_LAP><<<hp->grid, kThreads, hp->smem, st>>>(p, ws, acc);
+    return check_launch_cfg("batch (pipelined Laplacian tiles)", kernel_for(hp->threads, hp->kset), hp->grid,
+                            hp->smem);
+  }
   switch (hp->threads) {
     case 128:
       k_batch<128><<<hp->grid, 128, hp->smem, st>>>(p, ws, acc);
@@ -329,7 +404,8 @@ int launch(const BPlan* hp, const void* d_plan, void* d_ws, cudaStream_t st) {
 int check_plan(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_bytes, const BPlan** out) {
   if (!h_plan || !d_plan || !d_ws) return fail(HC_ERR_INVALID_ARG, "null pointer");
   const BPlan* hp = reinterpret_cast<const BPlan*>(h_plan);
-  if (hp->magic != kPlanMagic || !kernel_for(hp->threads) || hp->n < 1 || hp->grid < 1)
+  if (hp->magic != kPlanMagic || !kernel_for(hp->threads) || hp->n < 1 || hp->grid < 1 || hp->kset < KSET_ALL ||
+      hp->kset > KSET_PIPE_LAP || (hp->kset != KSET_ALL && hp->threads != kThreads))
     return fail(HC_ERR_INVALID_ARG, "not a batch plan");
   if (!aligned16(d_plan) || !aligned16(d_ws)) return fail(HC_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
   if (ws_bytes < sizeof(BWs) + sizeof(BAcc) * (size_t)hp->n)
@@ -341,6 +417,76 @@ int check_plan(const void* h_plan, const void* d_plan, void* d_ws, size_t ws_byt
 }  // namespace
 
 // ------------------------------------------------------------------ host
+namespace {
+
+int64_t unit_elems_hint(const hc_batch_tune* tune) { return tune ? tune->unit_elems : 0; }
+
+// A divergence / curl item: the components' checks of hc_op_divergence /
+// hc_op_curl for the fused stage-3 tile, the tile geometry and its shared
+// memory.  The planes per unit are set with the other items' units.
+int plan_vector_item(const hc_batch_item& x, BItem& b, int* smem, int64_t) {
+  const bool div = (x.ops & HC_BATCH_DIVERGENCE) != 0;
+  if (x.ops != (uint32_t)(div ? HC_BATCH_DIVERGENCE : HC_BATCH_CURL))
+    return fail(HC_ERR_INVALID_ARG, "batch: a vector item has its one operation and no other");
+  if (!x.comps || x.ncomp < 1 || x.ncomp > 3) return fail(HC_ERR_INVALID_ARG, "batch: vector item components");
+  if (!x.d_field || !aligned16(x.d_field)) return fail(HC_ERR_INVALID_ARG, "batch: vector output");
+  if (x.field_dtype != HC_F32 && x.field_dtype != HC_F64 && x.field_dtype != HC_I64)
+    return fail(HC_ERR_INVALID_ARG, "batch: field_dtype");
+  const hc_header* hs[3] = {nullptr, nullptr, nullptr};
+  for (int c = 0; c < x.ncomp; ++c) {
+    const hc_stage& in = x.comps[c];
+    if (in.kind != HC_STAGE_COMPRESSED || !in.hdr || !in.d_data)
+      return fail(HC_ERR_INVALID_ARG, "batch: vector components are compressed streams");
+    if (in.level != HC_STAGE_Q) return fail(HC_ERR_UNSUPPORTED, "batch: vector items run at stage Q");
+    int rc = check_header(*in.hdr);
+    if (rc) return rc;
+    if (!aligned16(in.d_data)) return fail(HC_ERR_INVALID_ARG, "batch: stream pointer");
+    hs[c] = in.hdr;
+    if (in.hdr->pred != HC_PRED_DELTA && in.hdr->pred != HC_PRED_MEAN)
+      return fail(HC_ERR_UNSUPPORTED, "batch: vector components must be block-head or block-mean streams");
+    if (in.hdr->S != hs[0]->S || in.hdr->ndim != hs[0]->ndim)
+      return fail(HC_ERR_INVALID_ARG, "batch: vector components of one block size and shape");
+    for (int a = 0; a < 3; ++a)
+      if (in.hdr->dims[a] != hs[0]->dims[a]) return fail(HC_ERR_INVALID_ARG, "batch: vector components of one shape");
+  }
+  const int ndim = hs[0]->ndim;
+  if (div && x.ncomp != ndim) return fail(HC_ERR_INVALID_ARG, "batch: divergence takes ndim components");
+  if (!div && (ndim != 2 || x.ncomp != 2)) return fail(HC_ERR_UNSUPPORTED, "batch: curl is defined for 2-D fields");
+  VArgs& va = b.va;
+  va = VArgs{};
+  va.ncomp = x.ncomp;
+  va.same_eps = 1;
+  va.gmax = 1;
+  va.wmax = 0;
+  for (int c = 0; c < x.ncomp; ++c) {
+    va.s[c] = dev_stream(hs[c], x.comps[c].d_data);
+    va.eps[c] = hs[c]->eps;
+    if (hs[c]->eps != hs[0]->eps) va.same_eps = 0;
+    va.gmax = std::max(va.gmax, (int)hs[c]->G);
+    va.wmax = std::max(va.wmax, (int)hs[c]->wmax);
+  }
+  if (x.field_dtype == HC_I64 && !va.same_eps)
+    return fail(HC_ERR_UNSUPPORTED, "an integer numerator needs one eps for every component");
+  va.out = x.field_dtype;
+  vector_axes(hs[0], div ? VEC_DIV : VEC_CURL, x.ncomp, va);
+  int64_t d3[3];
+  int axis3 = 0;
+  stencil_walk_dims(hs[0], d3, &axis3);
+  b.g = stencil_base_geo(d3, hs[0]->eps, 0);
+  int rc = plan_vector(hs, x.ncomp, d3, b.g, va.gmax, va.wmax, smem);
+  if (rc) return rc;
+  b.kind = KIND_VECTOR;
+  b.fop = -1;
+  b.out = x.field_dtype;
+  b.field = x.d_field;
+  b.stats = STATS_NONE;
+  b.scalar = nullptr;
+  b.s = va.s[0];
+  return HC_OK;
+}
+
+}  // namespace
+
 int64_t batch_plan_bytes(int n) { return n < 1 ? 0 : plan_bytes_for(n); }
 int64_t batch_ws_bytes(int n) { return n < 1 ? 0 : (int64_t)(sizeof(BWs) + sizeof(BAcc) * (size_t)n); }
 
@@ -362,8 +508,18 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
   int smem = 0;
   int64_t field_points = 0;
   const uint32_t field_ops = HC_BATCH_DERIVATIVE | HC_BATCH_GRADMAG | HC_BATCH_LAPLACIAN;
+  const uint32_t vec_ops = HC_BATCH_DIVERGENCE | HC_BATCH_CURL;
   for (int i = 0; i < n; ++i) {
     const hc_batch_item& x = items[i];
+    if (x.ops & vec_ops) {
+      int sm = 0;
+      int rc = plan_vector_item(x, it[i], &sm, unit_elems_hint(tune));
+      if (rc) return rc;
+      smem = std::max(smem, sm);
+      field_points += it[i].va.s[0].N;
+      continue;
+    }
+    if (x.ncomp != 0 || x.comps) return fail(HC_ERR_INVALID_ARG, "batch: components given without a vector operation");
     const hc_header& h = x.hdr;
     int rc = check_header(h);
     if (!rc && h.pred >= HC_PRED_LORENZO)
@@ -399,7 +555,7 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
       // the pipelined tile when it applies (it needs kThreads threads per CTA)
       b.kind = KIND_TILE;
       if (threads == kThreads && aligned16(x.d_field) && d3[1] * d3[2] < ((int64_t)1 << 31) &&
-          plan_pipe_geometry(&h, d3, b.pg, &sm, ty_force, ty_force ? 200 * 1024 : 74 * 1024)) {
+          plan_pipe_geometry(&h, d3, b.pg, &sm, 0, 74 * 1024, ty_force)) {
         // rows of other lengths: one output per item (measured faster inside
         // the batched kernel than the unaligned 8-wide items, whose code and
         // registers the persistent kernel would carry for every unit)
@@ -437,6 +593,17 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
       b.units = ceil_div(h.nb, b.rblocks);
     }
   }
+  // the narrowest kernel that carries every item's unit kind
+  int kset = KSET_ALL;
+  if (threads == kThreads) {
+    bool all_pipe = true, all_lap = true;
+    for (int i = 0; i < n; ++i) {
+      all_pipe &= it[i].kind == KIND_PIPE;
+      all_lap &= it[i].kind == KIND_PIPE && it[i].pg.op == ST_LAPLACIAN && it[i].pg.out == HC_F32;
+    }
+    kset = all_lap ? KSET_PIPE_LAP : (all_pipe ? KSET_PIPE : KSET_ALL);
+  }
+  kern = kernel_for(threads, kset);
   int optin = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -462,6 +629,12 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
       // the planes per tile do not change the tile's shared memory
       if (sm > smem) return fail(HC_ERR_UNSUPPORTED, "batch: inconsistent tile plan");
       b.units = (int64_t)b.g.nxt * b.g.nyt * b.g.nzt;
+    } else if (b.kind == KIND_VECTOR) {
+      // planes per unit from the unit size (whole rows of ty rows per plane)
+      const int64_t plane = (int64_t)b.g.ty * b.g.n2;
+      b.g.tz = (int)std::min<int64_t>(b.g.n0, std::max<int64_t>(1, ceil_div(unit_elems, plane)));
+      b.g.nzt = (int)ceil_div(b.g.n0, b.g.tz);
+      b.units = (int64_t)b.g.nyt * b.g.nzt;
     } else if (b.kind == KIND_PIPE) {
       // at least four planes per unit: a pipelined tile primes three slabs
       const int64_t plane = (int64_t)b.pg.ty * b.pg.n2;
@@ -478,6 +651,7 @@ int batch_plan_impl(const hc_batch_item* items, int n, const hc_batch_tune* tune
   P->magic = kPlanMagic;
   P->n = n;
   P->threads = threads;
+  P->kset = kset;
   P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_cap, total));
   P->smem = smem;
   P->total_units = total;
@@ -492,7 +666,7 @@ int batch_run_impl(const void* h_plan, const void* d_plan, void* d_ws, size_t ws
   const BPlan* hp = nullptr;
   int rc = check_plan(h_plan, d_plan, d_ws, ws_bytes, &hp);
   if (rc) return rc;
-  rc = ensure_smem(kernel_for(hp->threads), hp->smem);
+  rc = ensure_smem(kernel_for(hp->threads, hp->kset), hp->smem);
   if (rc) return rc;
   return launch(hp, d_plan, d_ws, st);
 }
@@ -503,7 +677,7 @@ int batch_graph_impl(const void* h_plan, const void* d_plan, void* d_ws, size_t 
   const BPlan* hp = nullptr;
   int rc = check_plan(h_plan, d_plan, d_ws, ws_bytes, &hp);
   if (rc) return rc;
-  rc = ensure_smem(kernel_for(hp->threads), hp->smem);
+  rc = ensure_smem(kernel_for(hp->threads, hp->kset), hp->smem);
   if (rc) return rc;
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)

@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "hc_internal.cuh"
+
 namespace hc {
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -33,9 +35,17 @@ __device__ __forceinline__ uint32_t byte_sign(uint32_t v, uint32_t j) {
 
 // Decode one full 32-code segment of width 1 <= w <= 32 / G.  mw: the
 // segment's first magnitude word in shared memory (the window reads up to
-// three words past the segment's last magnitude word; callers leave that much
+// two words past the segment's last magnitude word; callers leave that much
 // readable slack after the staged payload).  f(k, x, neg) is called for
 // k = 0..31 in order with x = |p_k| ^ neg and neg = 0 / -1.
+//
+// The window (lo, hi) slides one word when a group crosses a word boundary,
+// with the next word already loaded (nx), so every payload word is read from
+// shared memory once.  Measured on GB300 against a window read by index for
+// each group (two loads per group, word index by multiply) and against
+// moving the in-group shifts and sums to the multiply-add pipe: both moved
+// work off the integer ALU pipe but were slower (more shared loads and
+// longer dependency chains), so the sliding window stays.
 template <int G, class F>
 __device__ __forceinline__ void decode32(const uint32_t* __restrict__ mw, uint32_t sw, uint32_t w, F&& f) {
   static_assert(G >= 1 && G <= 4, "groups of 1 to 4 codes");
@@ -72,6 +82,68 @@ __device__ __forceinline__ void decode32(const uint32_t* __restrict__ mw, uint32
       }
     }
   }
+}
+
+// decode32 with each group's window read by index: group g's first bit is
+// g G w, its word (g G w) / 32, both found with multiply-adds, and the two
+// window words are loaded for every group.  Twice the shared loads of the
+// sliding window, but no compares and predicated moves on the integer ALU
+// pipe and no dependency from one group to the next.  Measured on GB300:
+// faster inside the stencil tiles, whose stencil arithmetic keeps the ALU
+// pipe busy (the one-pass kernel 0.77 -> 0.81 of HBM on 512^3), slower in
+// the statistics kernel, where the extra shared loads dominate.  Reads at
+// most one word past the segment's last magnitude word.
+template <int G, class F>
+__device__ __forceinline__ void decode32_ix(const uint32_t* __restrict__ mw, uint32_t sw, uint32_t w, F&& f) {
+  static_assert(G >= 1 && G <= 4, "groups of 1 to 4 codes");
+  constexpr int NG = (32 + G - 1) / G;
+  const uint32_t mask = (1u << w) - 1u;
+  uint32_t sh[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) sh[r] = sw << r;
+  const uint32_t gw = (uint32_t)G * w;
+  // multipliers of the in-group shifts by w, 2 w, 3 w: y >> s = hi32(y 2^(32 - s))
+  const uint32_t m1 = 1u << (32u - w);
+  const uint32_t m2 = G > 2 ? 1u << (32u - 2u * w) : 0u;
+  const uint32_t m3 = G > 3 ? 1u << (32u - 3u * w) : 0u;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const uint32_t bp = (uint32_t)g * gw;       // first bit of the group
+    const uint32_t j = __umulhi(bp, 1u << 27);  // its word: bp / 32
+    const uint32_t y = __funnelshift_r(mw[j], mw[j + 1], bp);
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int k = g * G + i;
+      if (k < 32) {
+        const uint32_t yi = i == 0 ? y : __umulhi(y, i == 1 ? m1 : (i == 2 ? m2 : m3));
+        const uint32_t neg = byte_sign(sh[7 - (k & 7)], (uint32_t)(k >> 3));
+        f(k, (int32_t)((yi & mask) ^ neg), (int32_t)neg);
+      }
+    }
+  }
+}
+
+// Group size of the grouped unpacker for a stream whose widths are at most
+// wmax: the most codes whose bits fit one 32-bit funnel shift (1 = the
+// one-code sliding window of unpack_full).
+__host__ __device__ inline int group_for_width(uint32_t wmax) {
+  return wmax <= 8u ? 4 : (wmax <= 10u ? 3 : (wmax <= 16u ? 2 : 1));
+}
+
+// decode32_ix with the group size chosen at run time (uniform over a launch,
+// so no divergence); grp = 1 falls back to the one-code window (any width).
+// The stencil tiles' decoder.
+template <class F>
+__device__ __forceinline__ void decode32_grp(int grp, const uint32_t* __restrict__ mw, uint32_t sw, uint32_t w,
+                                             F&& f) {
+  if (grp == 4)
+    decode32_ix<4>(mw, sw, w, f);
+  else if (grp == 3)
+    decode32_ix<3>(mw, sw, w, f);
+  else if (grp == 2)
+    decode32_ix<2>(mw, sw, w, f);
+  else
+    unpack_full(mw, sw, w, [&](int k, int32_t p) { f(k, p, 0); });
 }
 
 // sum_k (32 - k) b_k over the sign bits b_k of a full segment: with

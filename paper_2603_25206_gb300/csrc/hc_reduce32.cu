@@ -9,7 +9,8 @@
 //  * one lane copies the next chunk's payload into the warp's other shared
 //    buffer with a 1-D bulk copy (TMA) completing on an mbarrier, while the
 //    warp decodes the current chunk; widths and heads come straight into
-//    registers (one coalesced 4-byte and one 16-byte load per lane);
+//    registers (one coalesced 4-byte and one 16-byte load per lane, one
+//    iteration ahead);
 //  * lane l decodes blocks 4l .. 4l+3 of the chunk with the grouped unpacker
 //    (hc_group.cuh: G codes per window step, G = 4, 3 or 2 from the stream's
 //    largest width).
@@ -45,27 +46,43 @@ enum Op { OP_MEAN_P = 0, OP_MEAN_Q = 1, OP_VAR = 2 };
 __host__ __device__ inline int chunk_buf_words(int wmax) { return round4(kChunkBlocks * (wmax + 1) + 3 + 3 + 8); }
 __host__ __device__ inline int smem_bytes(int buf_words) { return 128 + kWarps * 2 * buf_words * 4; }
 
-struct ChunkMeta {
-  uint32_t w4;  // widths of the lane's four blocks (byte j: block 4 lane + j)
-  int4 h4;      // their heads
-  uint64_t p0, p1;  // payload words of the chunk
+// Widths and heads of the lane's four blocks of a chunk, blocks 4 lane ..
+// 4 lane + 3 (byte j of w4 and h4: block 4 lane + j): one 4-byte and one
+// 16-byte load per lane, loaded one iteration before use.  (Interleaving the
+// blocks over the lanes, block 32 j + lane, lowers shared-memory bank
+// conflicts but needs eight narrow loads per lane; measured slower.)
+struct ChunkData {
+  uint32_t w4;
+  int4 h4;
+};
+// Payload words [p0, p1) of a chunk, loaded two iterations before use (one
+// iteration before its bulk copy is issued).
+struct ChunkRange {
+  uint64_t p0, p1;
 };
 
-__device__ __forceinline__ ChunkMeta load_meta(const DevStream& s, int64_t c, int lane) {
-  ChunkMeta m;
+__device__ __forceinline__ ChunkData load_data(const DevStream& s, int64_t c, int lane) {
+  ChunkData m;
   const int64_t b = c * kChunkBlocks + 4 * lane;
   m.w4 = 0;
   m.h4 = make_int4(0, 0, 0, 0);
-  if (b < s.nb) {
+  if (c < s.nchunks && b < s.nb) {
     // b is a multiple of 4: 4-byte aligned widths, 16-byte aligned heads; a
     // lane whose last blocks lie past nb reads at most 3 bytes / 12 bytes
     // beyond the sections' ends, inside their 16-byte padding
     m.w4 = __ldg(reinterpret_cast<const uint32_t*>(s.widths + b));
     m.h4 = __ldg(reinterpret_cast<const int4*>(s.heads + b));
   }
-  m.p0 = __ldg(s.chunks + c);
-  m.p1 = __ldg(s.chunks + c + 1);
   return m;
+}
+
+__device__ __forceinline__ ChunkRange load_range(const DevStream& s, int64_t c) {
+  ChunkRange r{0, 0};
+  if (c < s.nchunks) {
+    r.p0 = __ldg(s.chunks + c);
+    r.p1 = __ldg(s.chunks + c + 1);
+  }
+  return r;
 }
 
 template <int G, int OP, int ACC, int PRED>
@@ -89,11 +106,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
   }
   __syncwarp();
 
-  // Copy of chunk c's payload into buffer b by lane 0: words [a0, end) with
+  // Copy of a chunk's payload into buffer b by lane 0: words [a0, end) with
   // a0 = p0 rounded down and end = p1 rounded up to 16 bytes (the stream keeps
   // >= 16 zero bytes after the payload).  False (nothing issued) when the
   // chunk index is inconsistent or the chunk holds no payload words.
-  auto issue = [&](const ChunkMeta& m, int b) -> bool {
+  auto issue = [&](const ChunkRange& m, int b) -> bool {
     if (m.p1 < m.p0 || m.p1 > (uint64_t)s.payload_words) return false;
     const uint64_t a0 = m.p0 & ~(uint64_t)3, end = (m.p1 + 3) & ~(uint64_t)3;
     if ((int64_t)(end - a0) + 8 > (int64_t)buf_words || end == a0) return false;
@@ -105,27 +122,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
     return true;
   };
 
+  // Software pipeline over the warp's chunks c, c + stride, ...: at the
+  // iteration of chunk c the copy of c + stride is issued (its range was
+  // loaded one iteration earlier), the widths and heads of c + stride and the
+  // range of c + 2 stride are loaded, and chunk c is decoded.
   int64_t c = (int64_t)blockIdx.x * kWarps + warp;
-  ChunkMeta cur{};
-  bool cur_issued = false;
+  ChunkRange cur_r = load_range(s, c);
+  ChunkData cur = load_data(s, c, lane);
+  ChunkRange nxt_r = load_range(s, c + stride);
+  bool cur_issued = c < s.nchunks && issue(cur_r, 0);
   unsigned phase = 0;  // bit b: parity of buffer b's next completion
-  if (c < s.nchunks) {
-    cur = load_meta(s, c, lane);
-    cur_issued = issue(cur, 0);
-  }
   for (int i = 0; c < s.nchunks; c += stride, ++i) {
     const int b = i & 1;
     const int64_t cn = c + stride;
-    ChunkMeta nxt{};
     bool nxt_issued = false;
     if (cn < s.nchunks) {
-      nxt = load_meta(s, cn, lane);
       // every lane is done with buffer b ^ 1 (chunk c - stride) before the
       // bulk copy overwrites it
       __syncwarp();
       if (lane == 0) fence_proxy_async_smem();
-      nxt_issued = issue(nxt, b ^ 1);
+      nxt_issued = issue(nxt_r, b ^ 1);
     }
+    const ChunkData nxt = load_data(s, cn, lane);
+    const ChunkRange nn_r = load_range(s, cn + stride);
     // block offsets inside the chunk: exclusive scan of the block sizes
     // (1 sign word + w magnitude words, 0 for width 0)
     const int64_t bb = c * kChunkBlocks + 4 * lane;
@@ -151,7 +170,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
       if (lane >= o) incl += y;
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    bad = __any_sync(0xffffffffu, bad) || (!cur_issued && total != 0) || (uint64_t)total != cur.p1 - cur.p0;
+    bad = __any_sync(0xffffffffu, bad) || (!cur_issued && total != 0) || (uint64_t)total != cur_r.p1 - cur_r.p0;
     if (cur_issued) {
       // every lane waits (each observes the copy's completion itself); the
       // outcome is made warp-uniform so the warp leaves together on a timeout
@@ -165,7 +184,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
     if (bad) {
       err = HC_ERR_CORRUPT;
     } else {
-      const uint32_t* base = bufs + (size_t)b * buf_words + (uint32_t)(cur.p0 & 3) + (incl - lsum);
+      const uint32_t* base = bufs + (size_t)b * buf_words + (uint32_t)(cur_r.p0 & 3) + (incl - lsum);
       const int32_t hj[4] = {cur.h4.x, cur.h4.y, cur.h4.z, cur.h4.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -254,6 +273,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
       }
     }
     cur = nxt;
+    cur_r = nxt_r;
+    nxt_r = nn_r;
     cur_issued = nxt_issued;
   }
   reduce_and_finish(S1, S2, err, parts, ticket, [&](long long a, u128 b2, int e) {

@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "hc_finish.cuh"
+#include "hc_group.cuh"
 #include "hc_internal.cuh"
 #include "hc_launch.h"
 #include "hc_stencil_pipe.cuh"
@@ -54,15 +55,20 @@ __global__ void __launch_bounds__(kThreads) k_stencil_multi(DevStream s, PGeo g,
 // of any length: 8-wide items, vector ones when the row length allows).  The
 // tile height is the largest that keeps at least three CTAs per SM; the plane
 // ranges are sized so that the grid fills whole waves of resident CTAs.
-bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* smem_out, int force_ty, int budget) {
+bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* smem_out, int force_ty, int budget,
+                        int max_ty) {
   if (h->S != 32 || h->qmax >= 32768u) return false;
   g.n0 = d3[0];
   g.n1 = d3[1];
   g.n2 = d3[2];
   const int S = 32;
   int chosen = 0;
-  for (int ty : kPipeTileHeights) {
+  int heights[10];
+  const int nh = pipe_heights(g.n1, heights);
+  for (int hi = 0; hi < nh; ++hi) {
+    const int ty = heights[hi];
     if (force_ty && ty != force_ty) continue;
+    if (!force_ty && max_ty > 0 && ty > max_ty) continue;
     if (ty > g.n1 && ty != 1) continue;
     const int64_t rows = std::min<int64_t>(ty + 2, g.n1);
     const int64_t span = rows * g.n2;
@@ -82,6 +88,7 @@ bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* sme
   }
   if (!chosen || *smem_out > 200 * 1024) return false;
   g.nyt = (int)ceil_div(g.n1, g.ty);
+  g.grp = group_for_width(h->wmax);
   return true;
 }
 
@@ -185,7 +192,10 @@ int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(HC_ERR_CUDA, "autotune: cudaEventCreate failed");
-  for (int ty : kPipeTileHeights) {
+  int heights[10];
+  const int nh = pipe_heights(d3[1], heights);
+  for (int hi = 0; hi < nh; ++hi) {
+    const int ty = heights[hi];
     PGeo g{};
     int smem = 0;
     if (!plan_pipe_geometry(h, d3, g, &smem, ty, 200 * 1024)) continue;

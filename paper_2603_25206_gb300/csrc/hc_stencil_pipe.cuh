@@ -6,14 +6,16 @@
 // One CTA owns TY whole rows for a range of planes and marches along the
 // slowest axis (the sliding window of Algorithm 3, one plane slab per step).
 // Warp 0 is a loader; warps 1..7 decode and compute:
-//   step k:  loader   wait for the copies issued in step k-1, scan the widths
-//                     of slab k+2, cp.async its payload and the widths + heads
-//                     of slab k+3 (so every copy has a whole step to land);
+//   step k:  loader   wait for the copies issued two steps before, scan the
+//                     widths of slab k+3, cp.async its payload and heads and
+//                     the widths of slab k+5 (so every copy has two whole
+//                     steps to land: a step is often shorter than a DRAM
+//                     round trip);
 //            workers  decode slab k into ring slot k % 4 and compute every
 //                     output plane whose three slabs are ready (normally the
 //                     plane of slab k-2);
 //            one __syncthreads.
-// Buffers: 4 ring slots, 3 payload stages, 4 metadata buffers.  A work item
+// Buffers: 4 ring slots, 4 payload and heads stages, 6 widths buffers.  A work item
 // is V = 8 (rows a multiple of 8) or V = 4 (a multiple of 4) consecutive
 // outputs of one row, or for rows of any length (V = 0) 8 outputs at any
 // offset with unaligned loads, and the rows' last n2 % 8 outputs one by one.
@@ -26,6 +28,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "hc_group.cuh"
 #include "hc_internal.cuh"
 #include "hc_launch.h"
 #include "hc_stencil_tile.cuh"
@@ -36,15 +39,14 @@ constexpr int kWorkers = kThreads - 32;
 constexpr int kSlots = 4;
 constexpr int kWorkerWarps = kWorkers / 32;
 // Estimated thread instructions per decoded code and per output point (from
-// ncu instruction counts of the kernels): decoding costs about 25 per code,
-// a point about as much for one operation, about 40 with the run-time
-// operation dispatch and exact sums of the batched tiles, and about 100 for
-// all operations.
-constexpr int kDecodeCost = 25;
+// ncu instruction counts of the kernels): decoding with the grouped unpacker
+// costs about 10 per code, a point about 25 for one operation, about 40 with
+// the run-time operation dispatch and exact sums of the batched tiles, and
+// about 100 for all operations.
+constexpr int kDecodeCost = 10;
 constexpr int kPointCost = 25;
 constexpr int kPointCostRuntime = 40;  // run-time operation dispatch plus the exact sums (batched tiles)
 constexpr int kPointCostMulti = 100;
-
 
 struct PGeo {
   int64_t n0, n1, n2;
@@ -60,6 +62,7 @@ struct PGeo {
                       // internal axes 0, 1, 2, the gradient magnitude, the Laplacian
   unsigned nq_magic;  // ceil(2^32 / nq) for the row/item split (unused when nq == 1)
   int nq;             // items per row: n2 / V
+  int grp;            // group size of the grouped unpacker (group_for_width of the stream's max width)
   float eps_f, te_f;
   double eps, te;
 };
@@ -106,19 +109,29 @@ __device__ __forceinline__ typename OT<OUT>::T emit1(int a, int b, int c, const 
   return 0;
 }
 
-// Shared-memory carve-up (byte offsets), computed identically on both sides.
+// Copy pipeline depth: the payload and heads of slab j are copied three
+// steps before slab j is decoded (kStages buffers), its widths five steps
+// before (kWidthBufs buffers: scanned two steps after they were copied), so
+// every copy has at least two whole steps to land.
+constexpr int kStages = 4;
+constexpr int kWidthBufs = 6;
+
+// Shared-memory carve-up (byte offsets), computed identically on both sides:
+// the ring of decoded slots, the payload stages, the widths, heads and
+// block offsets of the slabs in flight.
 struct PSmem {
-  int ring, stage, meta, total;
-  int meta_bytes;  // one meta buffer: widths | heads | offsets
+  int ring, stage, wb, hb, ob, total;
+  int ob_bytes;  // one offsets buffer
 };
 __host__ __device__ inline PSmem psmem(const PGeo& g) {
   PSmem p;
   p.ring = 0;
   p.stage = p.ring + kSlots * g.slot_bytes;
-  p.meta = p.stage + 3 * 4 * g.stage_words;
-  p.meta_bytes = g.pre_max + 4 * g.heads_max + 4 * (g.nblk_max + 4);
-  p.meta_bytes = (p.meta_bytes + 15) & ~15;
-  p.total = p.meta + 4 * p.meta_bytes;
+  p.wb = p.stage + kStages * 4 * g.stage_words;
+  p.hb = p.wb + kWidthBufs * g.pre_max;
+  p.ob = p.hb + kStages * 4 * g.heads_max;
+  p.ob_bytes = (4 * (g.nblk_max + 4) + 15) & ~15;
+  p.total = p.ob + kStages * p.ob_bytes;
   return p;
 }
 
@@ -349,50 +362,62 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
   const int64_t zs = max(z0 - 1, (int64_t)0), ze = min(z1 + 1, g.n0);  // slabs [zs, ze)
   const int nslab = (int)(ze - zs);
 
-  auto meta_w = [&](int j) { return sm + L.meta + (j & 3) * L.meta_bytes; };
-  auto meta_h = [&](int j) { return reinterpret_cast<int32_t*>(sm + L.meta + (j & 3) * L.meta_bytes + g.pre_max); };
-  auto meta_o = [&](int j) {
-    return reinterpret_cast<uint32_t*>(sm + L.meta + (j & 3) * L.meta_bytes + g.pre_max + 4 * g.heads_max);
-  };
-  auto stage = [&](int j) { return reinterpret_cast<uint32_t*>(sm + L.stage + (j % 3) * 4 * g.stage_words); };
+  auto meta_w = [&](int j) { return sm + L.wb + (j % kWidthBufs) * g.pre_max; };
+  auto meta_h = [&](int j) { return reinterpret_cast<int32_t*>(sm + L.hb + (j % kStages) * 4 * g.heads_max); };
+  auto meta_o = [&](int j) { return reinterpret_cast<uint32_t*>(sm + L.ob + (j % kStages) * L.ob_bytes); };
+  auto stage = [&](int j) { return reinterpret_cast<uint32_t*>(sm + L.stage + (j % kStages) * 4 * g.stage_words); };
   auto slot = [&](int64_t z) { return sm + L.ring + (int)(z & 3) * g.slot_bytes; };
 
-  // loader: copy widths [cs, b0 + nblk) and heads [b0, b0 + nblk) of slab j
-  auto load_meta = [&](int j) {
+  // loader: copy widths [cs, b0 + nblk) of slab j
+  auto load_widths = [&](int j) {
     const SlabDesc d = slab_desc(s, g, zs + j, ylo, yhi);
     const int nw = (d.npre + d.nblk + 15) & ~15;
     const uint8_t* wsrc = s.widths + d.cs;  // cs is a multiple of G = 128: 16-byte aligned
     uint8_t* wdst = meta_w(j);
     for (int i = lane * 16; i < nw; i += 32 * 16) cp_async16(wdst + i, wsrc + i);
+  };
+  // loader: copy heads [b0, b0 + nblk) of slab j
+  auto load_heads = [&](int j) {
+    const SlabDesc d = slab_desc(s, g, zs + j, ylo, yhi);
     const int64_t h0 = d.b0 & ~(int64_t)3;
     const int nh = (int)((d.b0 + d.nblk - h0 + 3) & ~3);
     int32_t* hdst = meta_h(j);
     for (int i = lane * 4; i < nh; i += 32 * 4) cp_async16(hdst + i, s.heads + h0 + i);
   };
-  // loader: offsets of slab j from its widths, then cp.async of its payload
+  // loader: offsets of slab j from its widths, then cp.async of its payload.
+  // Lane l sums the block sizes of its own run of consecutive widths, one warp
+  // scan turns the run totals into run offsets, and a second pass over the
+  // run writes the block offsets: two short independent passes instead of a
+  // chain of dependent warp scans, one per 32 widths.
   auto scan_and_load_payload = [&](int j) {
     const SlabDesc d = slab_desc(s, g, zs + j, ylo, yhi);
     const uint8_t* w = meta_w(j);
     uint32_t* off = meta_o(j);
-    uint32_t carry = 0;
     const int n = d.npre + d.nblk;
+    const int per = (n + 31) >> 5;
+    const int r0 = min(lane * per, n), r1 = min(r0 + per, n);
     int bad = 0;
-    for (int base = 0; base < n; base += 32) {
-      const int i = base + lane;
-      uint32_t wi = i < n ? w[i] : 0u;
+    uint32_t run = 0;
+    for (int i = r0; i < r1; ++i) {
+      uint32_t wi = w[i];
       if (wi > (uint32_t)s.wmax) {
         bad = 1;
         wi = 0;
       }
-      const uint32_t words = wi ? 1u + wi : 0u;  // S = 32: one sign word + w magnitude words
-      uint32_t x = words;
+      run += wi ? 1u + wi : 0u;  // S = 32: one sign word + w magnitude words
+    }
+    uint32_t x = run;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (i >= d.npre && i < n) off[i - d.npre] = carry + x - words;  // exclusive, relative to chunk start
-      carry += __shfl_sync(0xffffffffu, x, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const uint32_t carry = __shfl_sync(0xffffffffu, x, 31);  // words of the whole range
+    uint32_t at = x - run;                                     // exclusive, relative to chunk start
+    for (int i = r0; i < r1; ++i) {
+      const uint32_t wi = w[i];
+      if (i >= d.npre) off[i - d.npre] = at;
+      at += (wi && wi <= (uint32_t)s.wmax) ? 1u + wi : 0u;
     }
     // payload words [chunk base + off[0], chunk base + carry) plus one word
     __syncwarp();
@@ -414,15 +439,15 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
     if (bad && lane == 0) set_error(err, HC_ERR_CORRUPT);
   };
 
-  // ---- prologue: metadata of slabs 0..2, payload of slabs 0 and 1
+  // ---- prologue: widths of slabs 0..4; payload and heads of slabs 0..2
   if (warp == 0) {
-    load_meta(0);
-    if (nslab > 1) load_meta(1);
+    for (int j = 0; j < 5 && j < nslab; ++j) load_widths(j);
     cp_async_wait_all();
     __syncwarp();
-    scan_and_load_payload(0);
-    if (nslab > 1) scan_and_load_payload(1);
-    if (nslab > 2) load_meta(2);
+    for (int j = 0; j < 3 && j < nslab; ++j) {
+      scan_and_load_payload(j);
+      load_heads(j);
+    }
     cp_async_wait_all();
   }
   __syncthreads();
@@ -430,15 +455,26 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
   int64_t znext = z0;  // next output plane
   for (int k = 0; k <= nslab; ++k) {
     if (warp == 0) {
-      // copies issued in the previous step (payload k+1, metadata k+2) land here
-      cp_async_wait_all();
+      // One copy group per step: step k copies the payload and heads of slab
+      // k + 3 and the widths of slab k + 5.  Waiting for all groups but the
+      // newest (step k - 1's) completes step k - 2's group: the widths of
+      // slab k + 3, scanned now, and (read after this step's barrier) the
+      // payload of slab k + 1; every copy has two steps to land.
+      cp_async_wait_group1();
       __syncwarp();
-      if (k + 2 < nslab) scan_and_load_payload(k + 2);
-      if (k + 3 < nslab) load_meta(k + 3);
+      if (k + 3 < nslab) {
+        scan_and_load_payload(k + 3);
+        load_heads(k + 3);
+      }
+      if (k + 5 < nslab) load_widths(k + 5);
+      cp_async_commit();
     } else {
       // Split the 7 worker warps between decoding slab k and computing the
       // planes that are ready, in proportion to the estimated work (a segment
       // kDecodeCost / kPointCost above); a warp has one role, so no divergence.
+      // (Giving every warp an equal share of both jobs was measured slower:
+      // with separate roles the decoding warps' integer work overlaps the
+      // computing warps' conversions and stores.)
       const int ww = warp - 1;
       const int64_t ready = zs + k - 1;  // last slab decoded in an earlier step
       int64_t zc1 = znext;
@@ -483,11 +519,11 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
           } else if constexpr (PRED == HC_PRED_MEAN) {
             // block mean (HSZx): q = M_b + p
             const uint32_t* blk = stg + off[seg];
-            unpack_full(blk + 1, blk[0], wi, [&](int i, int32_t p) { v[i] = (short)(q + p); });
+            decode32_grp(g.grp, blk + 1, blk[0], wi, [&](int i, int32_t x, int32_t neg) { v[i] = (short)(q + x - neg); });
           } else {
             const uint32_t* blk = stg + off[seg];
-            unpack_full(blk + 1, blk[0], wi, [&](int i, int32_t p) {
-              q += p;
+            decode32_grp(g.grp, blk + 1, blk[0], wi, [&](int i, int32_t x, int32_t neg) {
+              q = q + x - neg;
               v[i] = (short)q;
             });
           }
@@ -524,7 +560,7 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
           } else {
             // the last n2 % 8 codes of every row, one at a time
             const int t2 = it - nfull;
-            const int yr = t2 / tail;
+            const int yr = t2 / (tail > 0 ? tail : 1);  // tail > 0 here (V = 0 only)
             const int x = g.nq * VW + (t2 - yr * tail);
             pipe_item<OP, OUT, 1, true, STATS>(g, out, pc, pm, pp, rc0, rm0, rp0, row0, y0, yr, x, n2, ez, mo);
           }
@@ -537,13 +573,27 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
 }
 
 // Tile heights tried by the autotuner (and, without tuning, the first that
-// fits the shared-memory budget).
-constexpr int kPipeTileHeights[] = {16, 8, 4, 2, 1};
+// fits the shared-memory budget), largest first.  Small planes take tall
+// tiles (up to the whole plane): a step then decodes and computes enough
+// work to cover its fixed costs, and fewer halo rows are decoded twice.
+constexpr int kPipeTileHeights[] = {128, 64, 32, 16, 8, 4, 2, 1};
+// The heights to try for rows of n1 codes into out (at most 9): the whole
+// plane first when n1 <= 128 is not itself in kPipeTileHeights, then those.
+inline int pipe_heights(int64_t n1, int* out) {
+  int k = 0;
+  bool listed = false;
+  for (int ty : kPipeTileHeights) listed |= ty == n1;
+  if (n1 > 1 && n1 <= 128 && !listed) out[k++] = (int)n1;
+  for (int ty : kPipeTileHeights) out[k++] = ty;
+  return k;
+}
 
 // Geometry of the pipelined tile for a field walked as d3 (host).  False when
 // the tile does not apply: S != 32, |q| >= 2^15, or no tile height fits.
 // budget: shared-memory bytes a CTA may use (force_ty > 0 takes that height).
-bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* smem_out, int force_ty, int budget);
+// max_ty > 0: no height above it (force_ty == 0 only).
+bool plan_pipe_geometry(const hc_header* h, const int64_t* d3, PGeo& g, int* smem_out, int force_ty, int budget,
+                        int max_ty = 0);
 // Items per row and the magic divisor of the row/item split; false when
 // the 32-bit magic division would not be exact for this tile.
 bool plan_pipe_items(PGeo& g, int V);

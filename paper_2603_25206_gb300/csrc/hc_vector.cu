@@ -18,6 +18,7 @@
 #include "hc_internal.cuh"
 #include "hc_launch.h"
 #include "hc_stencil_tile.cuh"
+#include "hc_vector_tile.cuh"
 
 namespace hc {
 
@@ -25,112 +26,17 @@ DevStream dev_stream(const hc_header* h, const void* d_stream);
 
 namespace {
 
-enum { VEC_DIV = 0, VEC_CURL = 1 };
-
-struct VArgs {
-  DevStream s[3];
-  double eps[3];
-  int axes[3];  // internal axis each component is differentiated along
-  int ncomp;
-  int same_eps;
-  int gmax, wmax;  // staging buffer: largest G and block width over the components
-};
-
-// derivative numerator of ring `ring` (one component) at (z, y, x) along axis a
-__device__ __forceinline__ long long dnum(const Geo& g, const int32_t* ring, long long (*base)[66], int64_t z,
-                                          int64_t y, int x, int a) {
-  auto at = [&](int64_t zz, int64_t yy, int xx) -> int32_t {
-    const int slot = ring_slot(g, zz);
-    const int r = (int)((zz * g.n1 + yy) * g.n2 + xx - base[slot][0]);
-    return ring[slot * g.slot_words + pidx(r)];
-  };
-  if (a == 0) {
-    const int64_t zm = z > 0 ? z - 1 : 0, zp = z + 1 < g.n0 ? z + 1 : z;
-    const int e = (z == 0 || z == g.n0 - 1) ? 2 : 1;
-    return ((long long)at(zp, y, x) - at(zm, y, x)) * e;
-  }
-  if (a == 1) {
-    const int64_t ym = y > 0 ? y - 1 : 0, yp = y + 1 < g.n1 ? y + 1 : y;
-    const int e = (y == 0 || y == g.n1 - 1) ? 2 : 1;
-    return ((long long)at(z, yp, x) - at(z, ym, x)) * e;
-  }
-  const int n2 = (int)g.n2;
-  const int xm = x > 0 ? x - 1 : 0, xp = x + 1 < n2 ? x + 1 : x;
-  const int e = (x == 0 || x == n2 - 1) ? 2 : 1;
-  return ((long long)at(z, y, xp) - at(z, y, xm)) * e;
-}
-
-template <int OP, int OUT, bool SMALL>
-__global__ void __launch_bounds__(kThreads) k_vector_stream(VArgs va, Geo g, typename OutType<OUT>::T* out,
-                                                             int* err) {
-  using T = typename OutType<OUT>::T;
+template <bool SMALL>
+__global__ void __launch_bounds__(kThreads) k_vector_stream(VArgs va, Geo g, void* out, int* err) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_warp[32];
   __shared__ int s_flag;
   __shared__ long long s_base[3][3][66];
-  const int nc = va.ncomp;
-  const int S = va.s[0].S;
-  const int nsegmax = SMALL ? g.nblk_max : g.nblk_max * va.s[0].nseg;
-  const TileSmem L = tile_smem(g.nblk_max, va.gmax - 1, S, va.wmax,
-                               nc * g.nslot * g.slot_words + (SMALL ? 0 : round4(nsegmax)));
-  uint32_t* s_stage = smem;
-  uint32_t* s_off = smem + L.off;
-  int32_t* rings = reinterpret_cast<int32_t*>(smem + L.extra);
-  int32_t* s_tot = rings + nc * g.nslot * g.slot_words;
-  uint8_t* s_w = reinterpret_cast<uint8_t*>(smem + L.w);
-  const int range_words = padded_elems_words(g.range_elems);
-
-  int64_t t = blockIdx.x;
-  const int yt = (int)(t % g.nyt);
-  const int zt = (int)(t / g.nyt);
-  const int64_t y0 = (int64_t)yt * g.ty, y1 = min(y0 + g.ty, g.n1);
-  const int64_t z0 = (int64_t)zt * g.tz, z1 = min(z0 + g.tz, g.n0);
-  const int64_t ylo = max(y0 - 1, (int64_t)0), yhi = min(y1 + 1, g.n1);
-
-  auto load = [&](int c, int64_t z) {
-    load_slab<SMALL>(va.s[c], g, z, ylo, yhi, 0, g.n2, true, rings + c * g.nslot * g.slot_words, range_words,
-                     s_base[c], s_w, s_off, s_stage, L.stage_words, s_tot, s_warp, &s_flag, err);
-  };
-  for (int c = 0; c < nc; ++c) {
-    if (z0 > 0) load(c, z0 - 1);
-    load(c, z0);
-  }
-  const int n2 = (int)g.n2;
-  for (int64_t z = z0; z < z1; ++z) {
-    if (z + 1 < g.n0)
-      for (int c = 0; c < nc; ++c) load(c, z + 1);
-    for (int64_t y = y0; y < y1; ++y) {
-      T* orow = out + (z * g.n1 + y) * g.n2;
-      for (int x = threadIdx.x; x < n2; x += blockDim.x) {
-        long long D[3] = {0, 0, 0};
-        if constexpr (OP == VEC_DIV) {
-          for (int c = 0; c < nc; ++c)
-            D[c] = dnum(g, rings + c * g.nslot * g.slot_words, s_base[c], z, y, x, va.axes[c]);
-        } else {
-          D[0] = dnum(g, rings, s_base[0], z, y, x, va.axes[0]);
-          D[1] = -dnum(g, rings + g.nslot * g.slot_words, s_base[1], z, y, x, va.axes[1]);
-        }
-        const long long num = D[0] + D[1] + D[2];
-        if constexpr (OUT == HC_I64) {
-          orow[x] = num;
-        } else if (va.same_eps) {
-          if constexpr (OUT == HC_F32)
-            orow[x] = __fmul_rn(__ll2float_rn(num), (float)va.eps[0]);
-          else
-            orow[x] = __dmul_rn(__ll2double_rn(num), va.eps[0]);
-        } else {
-          double v = 0.0;
-          for (int c = 0; c < nc; ++c) v = __dadd_rn(v, __dmul_rn(__ll2double_rn(D[c]), va.eps[c]));
-          orow[x] = (T)v;
-        }
-      }
-    }
-    __syncthreads();
-  }
+  vector_tile<SMALL>(va, g, (int64_t)blockIdx.x, out, err, smem, s_warp, &s_flag, s_base);
 }
 
-// Geometry: whole rows, the largest tile height whose rings (one per
-// component) fit the budget; about four tiles per SM.
+}  // namespace
+
 int plan_vector(const hc_header* const* hs, int nc, const int64_t* d3, Geo& g, int gmax, int wmax, int* smem_out) {
   const int S = hs[0]->S;
   const bool small = S <= 32;
@@ -165,21 +71,17 @@ int plan_vector(const hc_header* const* hs, int nc, const int64_t* d3, Geo& g, i
   return fail(HC_ERR_UNSUPPORTED, "vector stencil: rows too long for a fused tile");
 }
 
-template <int OP, int OUT, bool SMALL>
+namespace {
+
+template <bool SMALL>
 int launch_vector(const VArgs& va, const Geo& g, int smem, void* d_out, int* err, cudaStream_t st) {
-  auto kern = k_vector_stream<OP, OUT, SMALL>;
+  auto kern = k_vector_stream<SMALL>;
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (rc) return rc;
   const int64_t grid = (int64_t)g.nyt * g.nzt;
   if (grid > 0x7fffffff) return fail(HC_ERR_UNSUPPORTED, "field too large");
-  kern<<<(unsigned)grid, kThreads, smem, st>>>(va, g, reinterpret_cast<typename OutType<OUT>::T*>(d_out), err);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(va, g, d_out, err);
   return check_launch_cfg("vector stencil", reinterpret_cast<const void*>(kern), grid, smem);
-}
-
-template <int OP, int OUT>
-int launch_vector_s(const VArgs& va, const Geo& g, int smem, void* d_out, int* err, cudaStream_t st) {
-  if (va.s[0].S <= 32) return launch_vector<OP, OUT, true>(va, g, smem, d_out, err, st);
-  return launch_vector<OP, OUT, false>(va, g, smem, d_out, err, st);
 }
 
 }  // namespace
@@ -310,42 +212,18 @@ int vector_stream_impl(const hc_header* const* hs, const void* const* streams, i
   }
   if (out_dtype == HC_I64 && !va.same_eps)
     return fail(HC_ERR_UNSUPPORTED, "an integer numerator needs one eps for every component");
-  // user axes in the shape the kernel walks (a 2-D field is walked as (n1, 1, n2))
-  const int ndim = hs[0]->ndim;
+  if (out_dtype != HC_F32 && out_dtype != HC_F64 && out_dtype != HC_I64) return fail(HC_ERR_INVALID_ARG, "out_dtype");
+  va.out = out_dtype;
+  vector_axes(hs[0], op, nc, va);
   int64_t d3[3];
-  int amap[3];
-  for (int a = 0; a < ndim; ++a) {
-    int axis3 = a + 3 - ndim;
-    stencil_walk_dims(hs[0], d3, &axis3);
-    amap[a] = axis3;
-  }
-  if (op == VEC_DIV) {
-    for (int c = 0; c < nc; ++c) va.axes[c] = amap[c];
-  } else {
-    va.axes[0] = amap[1];  // u along j
-    va.axes[1] = amap[0];  // v along i
-  }
+  int axis3 = 0;
+  stencil_walk_dims(hs[0], d3, &axis3);
   Geo g = stencil_base_geo(d3, hs[0]->eps, 0);
   int smem = 0;
   int rc = plan_vector(hs, nc, d3, g, va.gmax, va.wmax, &smem);
   if (rc) return rc;
-#define HC_VEC(OPV)                                                         \
-  switch (out_dtype) {                                                      \
-    case HC_F32:                                                            \
-      return launch_vector_s<OPV, HC_F32>(va, g, smem, d_out, err, st);     \
-    case HC_F64:                                                            \
-      return launch_vector_s<OPV, HC_F64>(va, g, smem, d_out, err, st);     \
-    case HC_I64:                                                            \
-      return launch_vector_s<OPV, HC_I64>(va, g, smem, d_out, err, st);     \
-    default:                                                                \
-      return fail(HC_ERR_INVALID_ARG, "out_dtype");                         \
-  }
-  if (op == VEC_DIV) {
-    HC_VEC(VEC_DIV)
-  } else {
-    HC_VEC(VEC_CURL)
-  }
-#undef HC_VEC
+  if (va.s[0].S <= 32) return launch_vector<true>(va, g, smem, d_out, err, st);
+  return launch_vector<false>(va, g, smem, d_out, err, st);
 }
 
 }  // namespace hc

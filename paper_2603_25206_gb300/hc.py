@@ -61,8 +61,10 @@ HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA, HC_PRED_MEAN
 PREDICTORS = {"delta": HC_PRED_DELTA, "mean": HC_PRED_MEAN, "lorenzo": HC_PRED_LORENZO,
               "global": HC_PRED_GLOBAL_DELTA, "mean-nd": HC_PRED_MEAN_ND}
 HC_BATCH_MEAN, HC_BATCH_VARIANCE, HC_BATCH_DERIVATIVE, HC_BATCH_GRADMAG, HC_BATCH_LAPLACIAN = 1, 2, 4, 8, 16
+HC_BATCH_DIVERGENCE, HC_BATCH_CURL = 32, 64
 BATCH_OPS = {"mean": HC_BATCH_MEAN, "variance": HC_BATCH_VARIANCE, "derivative": HC_BATCH_DERIVATIVE,
-             "gradmag": HC_BATCH_GRADMAG, "laplacian": HC_BATCH_LAPLACIAN}
+             "gradmag": HC_BATCH_GRADMAG, "laplacian": HC_BATCH_LAPLACIAN, "divergence": HC_BATCH_DIVERGENCE,
+             "curl": HC_BATCH_CURL}
 
 
 class HcError(RuntimeError):
@@ -94,7 +96,7 @@ class HcStage(ctypes.Structure):
 class HcBatchItem(ctypes.Structure):
     _fields_ = [("d_stream", ctypes.c_void_p), ("hdr", HcHeader), ("ops", ctypes.c_uint32), ("axis", ctypes.c_int32),
                 ("d_scalar", ctypes.c_void_p), ("d_field", ctypes.c_void_p), ("field_dtype", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("ncomp", ctypes.c_int32), ("comps", ctypes.c_void_p)]
 
 
 class HcMultiOut(ctypes.Structure):
@@ -702,7 +704,8 @@ class Batch:
 
     ``items``: a list of (Compressed, ops) where ops is a string such as
     "mean|variance|laplacian" (at most one of derivative / gradmag /
-    laplacian).  Field outputs are allocated here (``field_dtype``); the
+    laplacian), or (tuple of component Compressed, "divergence" / "curl")
+    for a vector field.  Field outputs are allocated here (``field_dtype``); the
     statistics land in one 64-byte hc_scalar per item.  ``run()`` launches
     the kernel; ``capture()`` records it in a CUDA graph that ``replay()``
     relaunches.  The plan is built once (host) and copied to the device; the
@@ -716,24 +719,36 @@ class Batch:
             raise ValueError("empty batch")
         L = lib()
         self.comps = [c for c, _ in items]
-        dev = device if device is not None else self.comps[0].stream.device
+        first = self.comps[0][0] if isinstance(self.comps[0], (tuple, list)) else self.comps[0]
+        dev = device if device is not None else first.stream.device
         n = len(items)
         self.n = n
         self.scalars = torch.zeros((n, SCALAR_BYTES), dtype=torch.uint8, device=dev)
         self.fields = [None] * n
         arr = (HcBatchItem * n)()
+        self._vec = []  # the component stage arrays of vector items (read by hc_batch_plan)
         for i, (c, ops) in enumerate(items):
             mask = 0
             for name in ops.split("|"):
                 mask |= BATCH_OPS[name.strip()]
             it = arr[i]
-            it.d_stream = c.stream.data_ptr()
-            it.hdr = c.header
+            if isinstance(c, (tuple, list)):
+                comps = (HcStage * len(c))()
+                for k, ck in enumerate(c):
+                    comps[k] = ck.stage("q")
+                self._vec.append((comps, c))
+                it.ncomp = len(c)
+                it.comps = ctypes.cast(comps, ctypes.c_void_p)
+                c = c[0]
+            else:
+                it.d_stream = c.stream.data_ptr()
+                it.hdr = c.header
             it.ops = mask
             it.axis = axis
             if mask & (HC_BATCH_MEAN | HC_BATCH_VARIANCE):
                 it.d_scalar = self.scalars[i].data_ptr()
-            if mask & (HC_BATCH_DERIVATIVE | HC_BATCH_GRADMAG | HC_BATCH_LAPLACIAN):
+            if mask & (HC_BATCH_DERIVATIVE | HC_BATCH_GRADMAG | HC_BATCH_LAPLACIAN | HC_BATCH_DIVERGENCE |
+                       HC_BATCH_CURL):
                 f = _field_out(c.shape, field_dtype, dev, None)
                 self.fields[i] = f
                 it.d_field = f.data_ptr()
@@ -826,7 +841,7 @@ def time_batch(b: Batch, reps: int = 5, flush=None) -> float:
 
 
 def batch_autotune(fields, eb: float, rel: bool = True, ops: str = "mean|variance|laplacian",
-                   S_list=(16, 32, 64, 128), threads_list=(128, 256, 512), ty_list=(16, 8, 4),
+                   S_list=(16, 32, 64, 128), threads_list=(128, 256, 512), ty_list=(0, 16, 8),
                    field_dtype: str = "float32", reps: int = 5, flush=None):
     """Autotuner of the batched launch: block size S, threads per CTA and
     stencil tile height.
@@ -834,9 +849,9 @@ def batch_autotune(fields, eb: float, rel: bool = True, ops: str = "mean|varianc
     For every S the fields (CUDA tensors) are compressed at that block size;
     for every (threads, tile height) the batch is planned, captured in a CUDA
     graph and timed (median of `reps` replays).  Returns (best, table): best
-    is a dict with the chosen S, threads, ty, the compressed fields at that S
-    and the planned Batch; table lists every (S, threads, ty, ms, compressed
-    bytes).
+    is a dict with the chosen S, threads, ty (the largest tile height a field
+    may take; 0: no limit), the compressed fields at that S and the planned
+    Batch; table lists every (S, threads, ty, ms, compressed bytes).
     The block size changes the stream (and its compression ratio), not the
     results: the codes q, and so every integer result, are the same for all S.
     """

@@ -20,6 +20,8 @@ Recipes
   torch's seeded CUDA generator (for workloads too large to draw on the host,
   such as the 200-field serving set); the same spectrum and spikes, but not
   the same numbers as the host generator.
+* ``wide_field_device``: the ``wide_field`` recipe drawn on a CUDA device
+  (float64), for the benchmark's wide-code configuration.
 """
 from __future__ import annotations
 
@@ -27,7 +29,8 @@ import math
 
 import numpy as np
 
-__all__ = ["sinusoid_field", "grf_field", "grf_field_device", "wide_field", "log_uniform_shapes", "PAPER_SHAPES"]
+__all__ = ["sinusoid_field", "grf_field", "grf_field_device", "wide_field", "wide_field_device", "log_uniform_shapes",
+           "PAPER_SHAPES"]
 
 # Shapes of the paper-like workload: Hurricane-like, NYX-like, Miranda-like,
 # a 98 x 1200 x 1200 volume and a 1800 x 3600 (2-D) ocean-like slice.
@@ -98,13 +101,11 @@ def grf_field(shape, seed: int, spikes: float = 0.05, dtype=np.float32) -> np.nd
     return np.ascontiguousarray(_minmax(field).astype(dtype))
 
 
-def grf_field_device(shape, seed: int, device, spikes: float = 0.05):
-    """k^-3 Gaussian random field (+ spikes) as a float32 CUDA tensor in [0, 1]."""
+def _grf_device(shape, device, g):
+    """Standardised k^-3 Gaussian random field in float64 on a CUDA device,
+    white noise drawn from the seeded generator g."""
     import torch
 
-    shape = tuple(int(s) for s in shape)
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
     white = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
     spec = torch.fft.rfftn(white)
     del white
@@ -123,6 +124,17 @@ def grf_field_device(shape, seed: int, device, spikes: float = 0.05):
     sd = field.std()
     if sd > 0:
         field /= sd
+    return field
+
+
+def grf_field_device(shape, seed: int, device, spikes: float = 0.05):
+    """k^-3 Gaussian random field (+ spikes) as a float32 CUDA tensor in [0, 1]."""
+    import torch
+
+    shape = tuple(int(s) for s in shape)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    field = _grf_device(shape, device, g)
     if spikes > 0:
         mask = torch.rand(shape, generator=g, device=device) < spikes
         amp = torch.rand(shape, generator=g, device=device, dtype=torch.float64) * 7.0 + 3.0
@@ -141,6 +153,21 @@ def wide_field(shape, seed: int) -> np.ndarray:
     trend = 1e4 * (np.arange(n0, dtype=np.float64) / n0)
     field += trend.reshape((n0,) + (1,) * (len(shape) - 1))
     return np.ascontiguousarray(field)
+
+
+def wide_field_device(shape, seed: int, device):
+    """The ``wide_field`` recipe drawn on a CUDA device (float64 tensor): the
+    same spectrum, scale and trend, not the same numbers as the host draw."""
+    import torch
+
+    shape = tuple(int(s) for s in shape)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    field = _grf_device(shape, device, g) * 1e4
+    n0 = shape[0]
+    trend = 1e4 * (torch.arange(n0, device=device, dtype=torch.float64) / n0)
+    field += trend.reshape((n0,) + (1,) * (len(shape) - 1))
+    return field.contiguous()
 
 
 def log_uniform_shapes(count: int, lo: int, hi: int, seed: int, ndim: int = 3):

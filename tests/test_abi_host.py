@@ -63,6 +63,7 @@ int main(void) {
   printf("%zu %zu %zu\n", offsetof(hc_header, pred), offsetof(hc_header, block), offsetof(hc_stage, pred));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(hc_shard), offsetof(hc_shard, header_bytes), offsetof(hc_shard, src_off),
          offsetof(hc_shard, nbytes), offsetof(hc_shard, chunks_off), offsetof(hc_shard, first));
+  printf("%zu %zu\n", offsetof(hc_batch_item, ncomp), offsetof(hc_batch_item, comps));
   return 0;
 }
 """
@@ -88,6 +89,7 @@ int main(void) {
     Sh = hc.HcShard
     assert vals[28:34] == [ctypes.sizeof(Sh), Sh.header_bytes.offset, Sh.src_off.offset, Sh.nbytes.offset,
                            Sh.chunks_off.offset, Sh.first.offset]
+    assert vals[34:36] == [B.ncomp.offset, B.comps.offset]
 
 
 def test_plain_c_program_links_and_calls_the_library(hc, orc):
@@ -241,6 +243,30 @@ def test_batch_argument_errors_before_any_cuda_call(hc):
     tune = hc.HcBatchTune(100, 0, 0, 0, 0)
     items[0].axis = 0
     assert L.hc_batch_plan(items, 1, ctypes.byref(tune), buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    # vector items (divergence / curl): components without the operation, the
+    # operation without components or with a second operation, a component
+    # whose header is inconsistent, a divergence with ncomp != ndim
+    items[0].ops = hc.HC_BATCH_LAPLACIAN
+    items[0].ncomp = 1
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    assert b"components" in L.hc_last_error()
+    items[0].ops = hc.HC_BATCH_DIVERGENCE
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    comps = (hc.HcStage * 2)()
+    items[0].comps = ctypes.cast(comps, ctypes.c_void_p)
+    items[0].ops = hc.HC_BATCH_DIVERGENCE | hc.HC_BATCH_MEAN
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    items[0].ops = hc.HC_BATCH_DIVERGENCE
+    bad = hc.HcHeader()  # all zero: inconsistent
+    for k in range(2):
+        comps[k].kind, comps[k].level, comps[k].d_data = hc.HC_STAGE_COMPRESSED, hc.HC_STAGE_Q, 16
+        comps[k].hdr = ctypes.pointer(bad)
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_CORRUPT
+    for k in range(2):
+        comps[k].hdr = ctypes.pointer(h)  # a 1-D field: a divergence takes 1 component
+    items[0].ncomp = 2
+    assert L.hc_batch_plan(items, 1, None, buf, cap, ctypes.byref(used)) == hc.HC_ERR_INVALID_ARG
+    items[0].ops, items[0].ncomp, items[0].comps = hc.HC_BATCH_DERIVATIVE, 0, None
     # run / graph with something that is not a plan
     ws = ctypes.c_void_p(16)
     assert L.hc_batch_run(buf, ctypes.c_void_p(16), ws, 1 << 20, None) == hc.HC_ERR_INVALID_ARG

@@ -78,7 +78,7 @@ def test_single_rank_helpers_identity():
 
 
 def test_reference_arm_json_line(monkeypatch, capsys):
-    """The reference arm (the oracle timed on host cores) prints one JSON line
+    """The reference arm (the oracle timed on every host core) prints one JSON line
     with the keys of the bench contract: impl, metric, unit, value, the
     steps and warm-up asked for, its own cpu_baseline, and an e2e entry with
     no host-device copies.  Run on a small stand-in for the 512^3 field."""
@@ -104,7 +104,9 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     assert line["value"] > 0 and line["ms_per_step"] > 0
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    # every host core: one oracle process per core, each on its own slab
+    assert cb["kind"] == "oracle" and cb["cores"] == min(os.cpu_count(), 20) and cb["value"] == line["value"]
+    assert cb["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
@@ -137,12 +139,17 @@ def test_profile_traffic_and_peaks(monkeypatch, tmp_path):
     sys.path.insert(0, ROOT)
     import bench
 
-    per_elem = bench.read_profile_traffic("stencil_multi_256x384x384")
-    assert per_elem is not None and 4 * 5 * 0.9 < per_elem < 4 * 5 * 1.2  # five float32 outputs dominate
-    monkeypatch.setattr(bench, "csrc_hash", lambda: "0" * 64)
-    assert bench.read_profile_traffic("stencil_multi_256x384x384") is None
-    assert bench.read_profile_traffic("no_such_profile") is None
+    h = bench.csrc_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k_case.md").write_text("| DRAM traffic per launch (read + write, bytes) | 2000000 |\n"
+                                    "elements per launch: 100000\ncsrc_sha256: " + h[:16] + "\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "csrc_hash", lambda: h)
+    assert bench.read_profile_traffic("k_case") == 20.0
+    monkeypatch.setattr(bench, "csrc_hash", lambda: "0" * 64)
+    assert bench.read_profile_traffic("k_case") is None
+    assert bench.read_profile_traffic("no_such_profile") is None
     assert bench.measured_peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7012.5, "bf16_tflops": 1900}))
     assert bench.measured_peaks() == (7012.5, "measured")

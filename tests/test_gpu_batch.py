@@ -230,3 +230,78 @@ def test_batched_config_full_size(env, orc, batched_fields, S):
         assert np.array_equal(f.reshape(-1)[torch.from_numpy(idx).to(dev)].cpu().numpy(), num)
     assert int(b.ws.count_nonzero()) == 0
     b.close()
+
+
+def _vector_components(orc, hc, torch, dev, shape, S, rel, seed, predictor="delta"):
+    import synth
+
+    comps, qs, eps = [], [], []
+    pred = 1 if predictor == "mean" else 0
+    for c in range(len(shape)):
+        x = synth.grf_field(shape, seed + c)
+        ref, e = orc.compress(x, 1e-3 if rel else 2e-3, rel, S, pred=pred)
+        comps.append(hc.from_stream(torch.from_numpy(ref).to(dev)))
+        qs.append(orc.decode(ref, "q"))
+        eps.append(e)
+    return comps, qs, eps
+
+
+@pytest.mark.parametrize("field_dtype", ["float64", "float32", "int64"])
+def test_vector_items_in_a_mixed_batch(env, orc, field_dtype):
+    """Divergence and curl items (Section V-C) in one batch with scalar items:
+    each vector output equals hc_op_divergence / hc_op_curl on the same
+    components bit for bit, and the oracle's (exact integer numerators for
+    int64; float64 values bit for bit; float32 within 1e-6 of the field's
+    scale); the scalar items keep their oracle results; graph replay gives
+    the same outputs."""
+    hc, torch, dev = env
+    div3, q3, e3 = _vector_components(orc, hc, torch, dev, (10, 24, 40), 32, False, 7100)
+    div2, q2, e2 = _vector_components(orc, hc, torch, dev, (33, 50), 16, False, 7200, "mean")
+    curl2, qc, ec = _vector_components(orc, hc, torch, dev, (40, 64), 32, False, 7300)
+    x = _field((12, 20, 48), 7400)
+    ref, eps = orc.compress(x, 1e-3, True, 32)
+    c = hc.from_stream(torch.from_numpy(ref).to(dev))
+    q = orc.decode(ref, "q")
+    b = hc.Batch([(tuple(div3), "divergence"), (c, "mean|variance|laplacian"), (tuple(div2), "divergence"),
+                  (tuple(curl2), "curl")], field_dtype=field_dtype)
+    for run in (b.run, lambda: (b.capture(), b.replay())):
+        run()
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        res = b.results()
+        for k, spec in enumerate(((div3, q3, e3, "div"), None, (div2, q2, e2, "div"), (curl2, qc, ec, "curl"))):
+            if spec is None:
+                continue
+            comps, qs, eps_c, op = spec
+            got = res[k][1].cpu().numpy()
+            one = (hc.divergence if op == "div" else hc.curl)(comps, out_dtype=field_dtype).cpu().numpy()
+            assert np.array_equal(got, one), (k, op)
+            num, val = orc.divergence_q(qs, eps_c) if op == "div" else orc.curl2_q(qs[0], qs[1], eps_c[0], eps_c[1])
+            if field_dtype == "int64":
+                assert np.array_equal(got, num)
+            elif field_dtype == "float64":
+                assert np.array_equal(got, val)
+            else:
+                assert np.all(np.abs(got - val) <= 1e-6 * np.maximum(np.abs(val), min(eps_c)))
+        s1, s2 = orc.sums_q(q)
+        st = res[1][0]
+        assert (st["s1"], st["s2"], st["status"]) == (s1, s2, 0)
+        lap = res[1][1].cpu().numpy()
+        if field_dtype == "int64":
+            assert np.array_equal(lap, orc.lap_q(q))
+    b.close()
+
+
+def test_vector_item_rules(env, orc):
+    hc, torch, dev = env
+    comps, _, _ = _vector_components(orc, hc, torch, dev, (6, 8, 16), 32, False, 7500)
+    for items, status in ((((tuple(comps), "curl"),), hc.HC_ERR_UNSUPPORTED),  # 3-D curl
+                          (((tuple(comps[:2]), "divergence"),), hc.HC_ERR_INVALID_ARG),  # ncomp != ndim
+                          (((tuple(comps), "divergence|mean"),), hc.HC_ERR_INVALID_ARG)):  # a second op
+        with pytest.raises(hc.HcError) as e:
+            hc.Batch(list(items))
+        assert e.value.status == status
+    cl = hc.compress(torch.from_numpy(_field((6, 8, 16), 7600)).to(dev), 1e-3, predictor="lorenzo")
+    with pytest.raises(hc.HcError) as e:
+        hc.Batch([((comps[0], comps[1], cl), "divergence")])
+    assert e.value.status == hc.HC_ERR_UNSUPPORTED
