@@ -486,17 +486,20 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
       const int nfull = (int)(y1 - y0) * g.nq;
       const int tail = V == 0 ? (int)g.n2 - g.nq * VW : 0;
       const int items = nfull + (int)(y1 - y0) * tail;
-      const long long dec_cost = (long long)kDecodeCost * 32 * nseg_k;
-      const int point_cost = OP == ST_MULTI ? kPointCostMulti : (OP == ST_RUNTIME || STATS ? kPointCostRuntime : kPointCost);
-      const long long comp_cost = (long long)point_cost * nplanes * (int)(y1 - y0) * g.n2;
+      // (single-precision estimates: every worker warp forms the split once
+      // per step, so it stays a handful of instructions)
+      constexpr int point_cost =
+          OP == ST_MULTI ? kPointCostMulti : (OP == ST_RUNTIME || STATS ? kPointCostRuntime : kPointCost);
+      const float dec_cost = (float)(kDecodeCost * 32) * (float)nseg_k;
+      const float comp_cost = (float)point_cost * (float)nplanes * (float)((int)(y1 - y0) * (int)g.n2);
       int ndw = kWorkerWarps;
-      if (comp_cost == 0)
+      if (nplanes == 0)
         ndw = kWorkerWarps;
-      else if (dec_cost == 0)
+      else if (nseg_k == 0)
         ndw = 0;
       else
         ndw = min(kWorkerWarps - 1,
-                  max(1, (int)((kWorkerWarps * dec_cost + (dec_cost + comp_cost) / 2) / (dec_cost + comp_cost))));
+                  max(1, __float2int_rn(__fdividef((float)kWorkerWarps * dec_cost, dec_cost + comp_cost))));
       const bool decoder = ww < ndw;
       const int wt = decoder ? ww * 32 + lane : (ww - ndw) * 32 + lane;
       const int wstride = decoder ? ndw * 32 : (kWorkerWarps - ndw) * 32;
@@ -547,10 +550,15 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
         const short* pp = reinterpret_cast<const short*>(slot(zp));
         // element offsets (inside each slot) of row y0 of planes z, z-1, z+1
         const int64_t row0 = (z * g.n1 + y0) * g.n2;
-        const int rc0 = (int)(row0 - (slab_desc(s, g, z, ylo, yhi).b0 << 5));
-        const int rm0 = (int)((zm * g.n1 + y0) * g.n2 - (slab_desc(s, g, zm, ylo, yhi).b0 << 5));
-        const int rp0 = (int)((zp * g.n1 + y0) * g.n2 - (slab_desc(s, g, zp, ylo, yhi).b0 << 5));
+        // a slot starts at block (e0 >> 5) of its slab's first element e0 =
+        // (z n1 + ylo) n2, so row y0 sits at (y0 - ylo) n2 + (e0 mod 32) in
+        // it; e0 mod 32 needs only the low 32 bits of the product
         const int n2 = (int)g.n2;
+        const int dy = (int)(y0 - ylo) * n2;
+        const uint32_t pl = (uint32_t)g.n1 * (uint32_t)g.n2, yl = (uint32_t)ylo * (uint32_t)g.n2;
+        const int rc0 = dy + (int)(((uint32_t)z * pl + yl) & 31u);
+        const int rm0 = dy + (int)(((uint32_t)zm * pl + yl) & 31u);
+        const int rp0 = dy + (int)(((uint32_t)zp * pl + yl) & 31u);
         const int ez = (z == 0 || z == g.n0 - 1) ? 2 : 1;
         for (int it = wt; it < items; it += wstride) {
           if (V != 0 || it < nfull) {
