@@ -1413,9 +1413,9 @@ def run_boxes(args):
 
 def run_profile_boxes():
     """Small case for ncu captures of the HSZx-nd kernels: one 256x384x384
-    float32 field in 4x4x4 boxes (compressed ~44 MB, D_p 151 MB), the stage-3
-    variance three times, then the stage-2 Laplacian (D_p decode, then the
-    border-corrected stencil)."""
+    float32 field in 4x4x4 boxes (compressed ~44 MB, float32 output 151 MB),
+    the stage-3 variance three times, then the one-pass Laplacian at stage 2
+    (border-corrected) and at stage 3."""
     import torch
 
     import __graft_entry__
@@ -1430,6 +1430,7 @@ def run_profile_boxes():
     for _ in range(3):
         hc.variance(c, level="q")
     hc.laplacian(c, level="p", out=out)
+    hc.laplacian(c, level="q", out=out)
     torch.cuda.synchronize()
     print(json.dumps({"profile_boxes": "ok", "compressed_bytes": c.nbytes, "wmax": int(c.header.wmax)}))
     return 0

@@ -97,6 +97,11 @@ int xnd_stats_impl(const hc_header* h, const void* d_stream, int level, int what
                    size_t ws_bytes, cudaStream_t st);
 int xnd_stencil_impl(const hc_header* h, const void* d_stream, int level, int op, int axis3, void* d_out,
                      int out_dtype, void* d_ws, size_t ws_bytes, cudaStream_t st);
+// One-pass HSZx-nd stencils at stage 2 or 3 (hc_xnd_march.cu): d_scratch
+// holds the box offsets (4 nb bytes).  HC_ERR_UNSUPPORTED (nothing recorded)
+// when the tile plan does not apply.
+int xnd_march_impl(const hc_header* h, const void* d_stream, int level, int op, int axis3, void* d_out, int out_dtype,
+                   void* d_ws, void* d_scratch, size_t scratch_bytes, cudaStream_t st);
 
 enum ReduceWhat { RED_MEAN = 0, RED_VAR = 1 };
 int reduce_stream_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out,

@@ -517,6 +517,10 @@ int xnd_stencil_impl(const hc_header* h, const void* d_stream, int level, int op
   if (ws_bytes < xnd_workspace_bytes(h)) return fail(HC_ERR_NOMEM, "workspace smaller than hc_workspace_bytes_for");
   int32_t* W = box_scratch(d_ws);
   int* err = &reinterpret_cast<OpWs*>(d_ws)->status;
+  // one pass when the march tile applies; else decode to an array, then the stencil
+  const int rc1 = xnd_march_impl(h, d_stream, level, op, axis3, d_out, out_dtype, d_ws, W,
+                                 ws_bytes - align16z(kOpWsBytes), st);
+  if (rc1 != HC_ERR_UNSUPPORTED) return rc1;
   if (level == HC_STAGE_Q) {
     int rc = launch_decode_box_s<HC_STAGE_Q, int32_t>(h, d_stream, W, err, st);
     if (rc) return rc;

@@ -39,6 +39,15 @@ def _cases():
     yield "leading_len1", synth.grf_field((1, 24, 40), 90), 1e-3, True, (1, 8, 8)
     yield "constant", np.full((5, 6, 7), 2.5, np.float32), 1e-3, True, (2, 2, 2)
     yield "single", np.array([3.25], np.float32), 0.1, False, (4,)
+    # one-pass box stencil tiles: boxes of odd extent (divisions, not
+    # shifts) with a tile width that is not a multiple of 4 codes; a row of
+    # several tiles with a ragged last one; tall fields whose tiles march
+    # through more than one box layer (b0 = 1 and b0 = 4)
+    yield "grf_3d_333_odd", synth.grf_field((7, 11, 13), 91), 1e-3, True, (3, 3, 3)
+    yield "grf_3d_222_odd_cols", synth.grf_field((6, 10, 10), 92), 1e-3, True, (2, 2, 2)
+    yield "grf_3d_wide_x", synth.grf_field((12, 20, 300), 93), 1e-3, True, (4, 4, 4)
+    yield "grf_3d_tall_144", synth.grf_field((700, 8, 16), 94), 1e-3, True, (1, 4, 4)
+    yield "grf_3d_tall_444", synth.grf_field((2500, 8, 8), 95), 1e-3, True, (4, 4, 4)
 
 
 CASES = list(_cases())
