@@ -413,11 +413,11 @@ def read_profile_traffic(kernel_tag: str):
     return float(m.group(1)) / float(n.group(1))
 
 
-# device sources of the one-pass kernel (and of the tile helpers it shares with
-# the other profiled kernels): a profile's traffic is used only while these
-# are unchanged since its capture
+# device sources of the profiled kernels (the one-pass and single-operation
+# stencils, their tile helpers, and the block-size-32 statistics): a
+# profile's traffic is used only while these are unchanged since its capture
 KERNEL_SOURCES = ("hc_stencil_pipe.cu", "hc_stencil_pipe.cuh", "hc_stencil_tile.cuh", "hc_internal.cuh",
-                  "hc_finish.cuh", "hc_group.cuh")
+                  "hc_finish.cuh", "hc_group.cuh", "hc_reduce32.cu")
 
 
 def csrc_hash():
@@ -773,7 +773,7 @@ def run_ours(args):
     # ncu capture on the 256x384x384 case, scaled to this launch's elements
     tag = {"derivative": "stencil_pipe_derivative_256x384x384", "gradmag": "stencil_pipe_gradmag_256x384x384",
            "laplacian": "stencil_pipe_laplacian_256x384x384",
-           "variance": "reduce_stream_variance_256x384x384"}.get(dom, "")
+           "variance": "reduce32_variance_256x384x384", "mean": "reduce32_mean_stage2_256x384x384"}.get(dom, "")
     op_pe = read_profile_traffic(tag) if tag else None
     elems = sum(wl.items[fi]["n"] for fi, op, _, _ in events if op == dom) / max(1, per[dom]["launches"])
     per_op_launches = {

@@ -555,8 +555,9 @@ HC_API int hc_finalize(int64_t n, int64_t s1, uint64_t s2_lo, uint64_t s2_hi, do
 /* Autotuner of the fused stencil kernel (no counterpart in the paper: a GPU
  * tiling choice).  For a compressed-stream input and op (HC_OP_DERIVATIVE,
  * HC_OP_GRADMAG or HC_OP_LAPLACIAN) and output type, times every tile height
- * the kernel can use on this field (each 1 warm-up + 3 runs, writing d_out,
- * which must hold the op's output) and keeps the fastest for all later calls
+ * the kernel can use on this field, each with the grid sized for one and for
+ * two waves of resident CTAs (each 1 warm-up + 3 runs, writing d_out, which
+ * must hold the op's output) and keeps the fastest pair for all later calls
  * on fields of the same shape, max width, op and output type in this
  * process.  *chosen receives the tile height (0: the general kernel applies
  * and nothing was tuned; statistics ops have nothing to tune).  HC_OP_MULTI

@@ -112,8 +112,9 @@ bool plan_pipe_items(PGeo& g, int V) {
 }
 
 static void plan_pipe_grid(PGeo& g, int per_sm) {
-  const int64_t capacity = (int64_t)device_sms() * std::max(per_sm, 1);
-  // one wave when the rows allow it; never fewer than 4 planes per CTA
+  const int64_t capacity = (int64_t)device_sms() * std::max(per_sm, 1) * std::max(g.waves, 1);
+  // g.waves waves of resident CTAs when the rows allow it; never fewer than
+  // 4 planes per CTA
   int64_t nzt = std::max<int64_t>(1, capacity / g.nyt);
   nzt = std::min<int64_t>(nzt, std::max<int64_t>(1, g.n0 / 4));
   g.tz = (int)ceil_div(g.n0, nzt);
@@ -153,7 +154,8 @@ static int launch_pipe_v(const hc_header* h, const void* d_stream, const PGeo& g
 
 // Returns HC_ERR_UNSUPPORTED (without recording an error) when the fast path
 // does not apply.
-// Tile heights picked by hc_autotune, per (shape, max width, op, output type).
+// Tile heights and grid waves picked by hc_autotune, per (shape, max width,
+// op, output type); a choice is coded as ty | waves << 8 (0: untuned).
 namespace {
 struct TuneKey {
   int64_t n0, n1, n2;
@@ -166,25 +168,28 @@ std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
 }  // namespace
 
-static int tuned_ty(const hc_header* h, const int64_t* d3, int op, int out_dtype) {
+static int tuned_choice(const hc_header* h, const int64_t* d3, int op, int out_dtype) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tuned.find(TuneKey{d3[0], d3[1], d3[2], (int)h->wmax, op, out_dtype});
   return it == g_tuned.end() ? 0 : it->second;
 }
 
 static int stencil_pipe_launch(const hc_header* h, const void* d_stream, const int64_t* d3, int op, int axis3,
-                               void* d_out, int out_dtype, void* d_ws, cudaStream_t st, int force_ty);
+                               void* d_out, int out_dtype, void* d_ws, cudaStream_t st, int tune);
 
 int stencil_pipe_impl(const hc_header* h, const void* d_stream, const int64_t* d3, int op, int axis3, void* d_out,
                       int out_dtype, void* d_ws, cudaStream_t st) {
-  return stencil_pipe_launch(h, d_stream, d3, op, axis3, d_out, out_dtype, d_ws, st, tuned_ty(h, d3, op, out_dtype));
+  return stencil_pipe_launch(h, d_stream, d3, op, axis3, d_out, out_dtype, d_ws, st,
+                             tuned_choice(h, d3, op, out_dtype));
 }
 
 static int stencil_multi_launch(const hc_header* h, const void* d_stream, void* const outs[5], hc_scalar* d_stats,
-                                int out_dtype, void* d_ws, cudaStream_t st, int force_ty);
+                                int out_dtype, void* d_ws, cudaStream_t st, int tune);
 
-// Time every tile height that fits on this field and remember the fastest.
-// Returns the chosen height (0 when the pipelined kernel does not apply).
+// Time every tile height that fits on this field, each with the plane
+// ranges sized for one and for two waves of resident CTAs, and remember the
+// fastest pair.  *chosen: the chosen height (0 when the pipelined kernel
+// does not apply).
 int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_t* d3, int op, void* d_out,
                           int out_dtype, void* d_ws, cudaStream_t st, int* chosen) {
   *chosen = 0;
@@ -193,9 +198,11 @@ int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(HC_ERR_CUDA, "autotune: cudaEventCreate failed");
   int heights[10];
+  int pick = 0;
   const int nh = pipe_heights(d3[1], heights);
-  for (int hi = 0; hi < nh; ++hi) {
-    const int ty = heights[hi];
+  for (int hw = 0; hw < 2 * nh; ++hw) {
+    const int ty = heights[hw >> 1], waves = 1 + (hw & 1);
+    const int tune = ty | (waves << 8);
     PGeo g{};
     int smem = 0;
     if (!plan_pipe_geometry(h, d3, g, &smem, ty, 200 * 1024)) continue;
@@ -219,9 +226,9 @@ int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_
         }
         outs[3] = o + (k++) * nb;
         outs[4] = o + (k++) * nb;
-        rc = stencil_multi_launch(h, d_stream, outs, nullptr, out_dtype, d_ws, st, ty);
+        rc = stencil_multi_launch(h, d_stream, outs, nullptr, out_dtype, d_ws, st, tune);
       } else {
-        rc = stencil_pipe_launch(h, d_stream, d3, op, 0, d_out, out_dtype, d_ws, st, ty);
+        rc = stencil_pipe_launch(h, d_stream, d3, op, 0, d_out, out_dtype, d_ws, st, tune);
       }
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = HC_ERR_CUDA;
@@ -229,27 +236,30 @@ int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_
     }
     if (rc != HC_OK) continue;
     std::sort(times, times + 3);
-    if (*chosen == 0 || times[1] < best) {
+    if (pick == 0 || times[1] < best) {
       best = times[1];
-      *chosen = ty;
+      pick = tune;
     }
   }
+  *chosen = pick & 0xff;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGetLastError();
   if (*chosen) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned[TuneKey{d3[0], d3[1], d3[2], (int)h->wmax, op, out_dtype}] = *chosen;
+    g_tuned[TuneKey{d3[0], d3[1], d3[2], (int)h->wmax, op, out_dtype}] = pick;
   }
   return HC_OK;
 }
 
 static int stencil_pipe_launch(const hc_header* h, const void* d_stream, const int64_t* d3, int op, int axis3,
-                               void* d_out, int out_dtype, void* d_ws, cudaStream_t st, int force_ty) {
+                               void* d_out, int out_dtype, void* d_ws, cudaStream_t st, int tune) {
   PGeo g{};
   int smem = 0;
+  const int force_ty = tune & 0xff;
   if (!aligned16(d_out) || !plan_pipe_geometry(h, d3, g, &smem, force_ty, force_ty ? 200 * 1024 : 74 * 1024))
     return HC_ERR_UNSUPPORTED;
+  g.waves = std::max(1, tune >> 8);
   if (g.n1 * g.n2 >= ((int64_t)1 << 31)) return HC_ERR_UNSUPPORTED;
   g.axis = axis3;
   g.eps = h->eps;
@@ -315,11 +325,13 @@ int stencil_multi_impl(const hc_header* h, const void* d_stream, void* const der
   int64_t d3[3];
   stencil_walk_dims(h, d3, nullptr);
   void* outs[5] = {deriv3[0], deriv3[1], deriv3[2], d_grad, d_lap};
-  return stencil_multi_launch(h, d_stream, outs, d_stats, out_dtype, d_ws, st, tuned_ty(h, d3, ST_MULTI, out_dtype));
+  return stencil_multi_launch(h, d_stream, outs, d_stats, out_dtype, d_ws, st,
+                              tuned_choice(h, d3, ST_MULTI, out_dtype));
 }
 
 static int stencil_multi_launch(const hc_header* h, const void* d_stream, void* const outs_in[5], hc_scalar* d_stats,
-                                int out_dtype, void* d_ws, cudaStream_t st, int force_ty) {
+                                int out_dtype, void* d_ws, cudaStream_t st, int tune) {
+  const int force_ty = tune & 0xff;
   if (out_dtype != HC_F32 && out_dtype != HC_F64) return HC_ERR_UNSUPPORTED;
   void* outs[5] = {outs_in[0], outs_in[1], outs_in[2], outs_in[3], outs_in[4]};
   for (void* o : outs)
@@ -330,6 +342,7 @@ static int stencil_multi_launch(const hc_header* h, const void* d_stream, void* 
   int smem = 0;
   if (!plan_pipe_geometry(h, d3, g, &smem, force_ty, force_ty ? 200 * 1024 : 74 * 1024)) return HC_ERR_UNSUPPORTED;
   if (g.n1 * g.n2 >= ((int64_t)1 << 31)) return HC_ERR_UNSUPPORTED;
+  g.waves = std::max(1, tune >> 8);
   g.axis = 0;
   g.op = ST_MULTI;
   g.out = out_dtype;

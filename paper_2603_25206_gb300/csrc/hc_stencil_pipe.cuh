@@ -63,6 +63,7 @@ struct PGeo {
   unsigned nq_magic;  // ceil(2^32 / nq) for the row/item split (unused when nq == 1)
   int nq;             // items per row: n2 / V
   int grp;            // group size of the grouped unpacker (group_for_width of the stream's max width)
+  int waves;          // plane ranges for about this many waves of resident CTAs (1 or 2, tuned)
   float eps_f, te_f;
   double eps, te;
 };

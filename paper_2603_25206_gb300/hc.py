@@ -682,9 +682,10 @@ def workspace_status(stream=None) -> int:
 
 
 def autotune(c: Compressed, op: str, out_dtype: str = "float32", out=None, stream=None) -> int:
-    """Time the fused stencil's tile heights for this field and op ("derivative",
-    "gradmag", "laplacian", or "multi" for hc_op_multi's one-pass kernel);
-    later calls use the fastest."""
+    """Time the fused stencil's tile heights, each with a one- and a two-wave
+    grid, for this field and op ("derivative", "gradmag", "laplacian", or
+    "multi" for hc_op_multi's one-pass kernel); later calls use the fastest.
+    Returns the chosen tile height."""
     torch = _torch()
     st = c.stage("q")
     if op == "multi" and out is None:
