@@ -1336,8 +1336,8 @@ def measure_boxes(hc, torch, dev, fields):
     at stages 2 and 3, against the plain path (decompress to float32, then the
     operation).  Median CUDA-event time over REPS runs with an L2 flush before
     each; GB/s counts the field's original bytes.  The roofline line is the
-    stage-3 variance kernel (k_stats_box) at its algorithmic bytes, the
-    compressed stream."""
+    stage-3 variance kernel (k_reduce32 on 64-slot boxes) at its algorithmic
+    bytes, the compressed stream."""
     peak, peak_src = measured_peaks()
     rows, tot = [], {}
     var_bytes = 0
@@ -1396,8 +1396,8 @@ def measure_boxes(hc, torch, dev, fields):
             "config": {"workload": WORKLOAD.replace("block 32;", "boxes of 4x4x4 (8x8 in 2-D), box-mean predictor "
                                                                  "(HSZx-nd);"),
                        "timing": f"median of {REPS} CUDA-event runs per op, L2 flushed before each"},
-            "roofline": {"kernel": "k_stats_box", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+            "roofline": {"kernel": "k_reduce32 (64-slot boxes)", "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                          "algorithmic_bytes": "compressed stream + 64 B per field"},
             "totals_ms": {k: round(v, 4) for k, v in tot.items()},
             "totals_gbs_orig": {k: round(orig / v / 1e6, 1) for k, v in tot.items()},

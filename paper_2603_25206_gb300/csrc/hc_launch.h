@@ -115,6 +115,12 @@ int mean_m_array_impl(const int32_t* means, int64_t nb, int S, int64_t n, double
 // copies.  reduce32_applies says whether a stream qualifies; max_parts bounds
 // the grid (partial slots); shift: the stage-2 HSZx deviation's integer mean.
 bool reduce32_applies(const hc_header* h);
+// The same kernel on HSZx-nd streams of 64- or 128-slot boxes (widths <= 16,
+// |q| < 2^26): the mean (what RED_MEAN) and the sums about `shift` (NULL:
+// the exact stage-3 variance).
+bool reduce32_box_applies(const hc_header* h);
+int reduce32_box_impl(const hc_header* h, const void* d_stream, int what, hc_scalar* d_out, Partial* parts,
+                      unsigned* ticket, int max_parts, const long long* shift, cudaStream_t st);
 int reduce32_impl(const hc_header* h, const void* d_stream, int level, int what, hc_scalar* d_out, Partial* parts,
                   unsigned* ticket, int max_parts, const long long* shift, cudaStream_t st);
 // Fused stage-3 variance with its scratch (per-CTA partials + ticket) at given device addresses.

@@ -18,7 +18,10 @@
 // block-weighted sum sum_k (32 - k) p_k, no prefix sum; stage 3 ("Operation
 // with D_q") rebuilds q with the running (eta) accumulator and adds q (mean)
 // and q^2 (variance).  Block-mean (HSZx) streams: q = M_b + p, so the sums
-// follow from sum p and sum p^2 per block.
+// follow from sum p and sum p^2 per block.  HSZx-nd streams of boxes of 64
+// or 128 slots (BPL = 2 or 1 boxes per lane of a 4096-code chunk) take the
+// same path: a box is 2 or 4 consecutive 32-slot segments, its mean M_b
+// weighted by the box's true size S_b (padding slots hold p = 0).
 #include <cstdint>
 #include <type_traits>
 
@@ -34,7 +37,7 @@ DevStream dev_stream(const hc_header* h, const void* d_stream);
 namespace {
 
 constexpr int kWarps = 4;          // warps per CTA
-constexpr int kChunkBlocks = 128;  // blocks per chunk at S = 32 (4096 / 32)
+constexpr int kChunkSegs = 128;    // 32-slot segments per chunk (4096 codes)
 constexpr unsigned kWaitPolls = 1u << 22;
 
 // What a launch sums: the stage-2 weighted sum (mean), the stage-3 sum
@@ -43,14 +46,15 @@ enum Op { OP_MEAN_P = 0, OP_MEAN_Q = 1, OP_VAR = 2 };
 
 // Words of one chunk buffer: 128 blocks of at most wmax + 1 words, the
 // copy's 16-byte alignment on both ends and the decoder's read-ahead.
-__host__ __device__ inline int chunk_buf_words(int wmax) { return round4(kChunkBlocks * (wmax + 1) + 3 + 3 + 8); }
+__host__ __device__ inline int chunk_buf_words(int wmax) { return round4(kChunkSegs * (wmax + 1) + 3 + 3 + 8); }
 __host__ __device__ inline int smem_bytes(int buf_words) { return 128 + kWarps * 2 * buf_words * 4; }
 
-// Widths and heads of the lane's four blocks of a chunk, blocks 4 lane ..
-// 4 lane + 3 (byte j of w4 and h4: block 4 lane + j): one 4-byte and one
-// 16-byte load per lane, loaded one iteration before use.  (Interleaving the
-// blocks over the lanes, block 32 j + lane, lowers shared-memory bank
-// conflicts but needs eight narrow loads per lane; measured slower.)
+// Widths and heads of the lane's BPL blocks (boxes) of a chunk, blocks
+// BPL lane .. BPL lane + BPL - 1 (byte j of w4 and lane j of h4: block
+// BPL lane + j): one load of widths and one of heads per lane, loaded one
+// iteration before use.  (Interleaving the blocks over the lanes, block 32 j
+// + lane, lowers shared-memory bank conflicts but needs eight narrow loads
+// per lane; measured slower.)
 struct ChunkData {
   uint32_t w4;
   int4 h4;
@@ -61,19 +65,45 @@ struct ChunkRange {
   uint64_t p0, p1;
 };
 
+template <int BPL>
 __device__ __forceinline__ ChunkData load_data(const DevStream& s, int64_t c, int lane) {
   ChunkData m;
-  const int64_t b = c * kChunkBlocks + 4 * lane;
+  const int64_t b = c * (32 * BPL) + BPL * lane;
   m.w4 = 0;
   m.h4 = make_int4(0, 0, 0, 0);
   if (c < s.nchunks && b < s.nb) {
-    // b is a multiple of 4: 4-byte aligned widths, 16-byte aligned heads; a
-    // lane whose last blocks lie past nb reads at most 3 bytes / 12 bytes
+    // b is a multiple of BPL: aligned widths and heads; a lane whose last
+    // blocks lie past nb reads at most BPL - 1 bytes / 4 (BPL - 1) bytes
     // beyond the sections' ends, inside their 16-byte padding
-    m.w4 = __ldg(reinterpret_cast<const uint32_t*>(s.widths + b));
-    m.h4 = __ldg(reinterpret_cast<const int4*>(s.heads + b));
+    if constexpr (BPL == 4) {
+      m.w4 = __ldg(reinterpret_cast<const uint32_t*>(s.widths + b));
+      m.h4 = __ldg(reinterpret_cast<const int4*>(s.heads + b));
+    } else if constexpr (BPL == 2) {
+      m.w4 = __ldg(reinterpret_cast<const uint16_t*>(s.widths + b));
+      const int2 h2 = __ldg(reinterpret_cast<const int2*>(s.heads + b));
+      m.h4.x = h2.x;
+      m.h4.y = h2.y;
+    } else {
+      m.w4 = __ldg(s.widths + b);
+      m.h4.x = __ldg(s.heads + b);
+    }
   }
   return m;
+}
+
+// Box geometry of an HSZx-nd stream, for the true sizes of ragged boxes at
+// the field's far faces (unused for 1-D blocks and when every box is full).
+struct BoxDims {
+  int64_t n0, n1, n2, g1, g2;
+  int b0, b1, b2;
+  int ragged;
+};
+__device__ __forceinline__ long long box_size(const BoxDims& d, int64_t b, int S) {
+  if (!d.ragged) return S;
+  const int64_t k2 = b % d.g2, r = b / d.g2;
+  const int64_t k1 = r % d.g1, k0 = r / d.g1;
+  return min((int64_t)d.b0, d.n0 - k0 * d.b0) * min((int64_t)d.b1, d.n1 - k1 * d.b1) *
+         min((int64_t)d.b2, d.n2 - k2 * d.b2);
 }
 
 __device__ __forceinline__ ChunkRange load_range(const DevStream& s, int64_t c) {
@@ -85,10 +115,11 @@ __device__ __forceinline__ ChunkRange load_range(const DevStream& s, int64_t c) 
   return r;
 }
 
-template <int G, int OP, int ACC, int PRED>
+template <int G, int OP, int ACC, int PRED, int BPL>
 __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_words, Partial* parts,
                                                           unsigned* ticket, hc_scalar* out, double two_eps,
-                                                          const long long* shift) {
+                                                          const long long* shift, BoxDims bd) {
+  constexpr int SEGS = 4 / BPL;  // 32-slot segments per block (box)
   extern __shared__ __align__(128) unsigned char sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm) + 2 * warp;
@@ -128,7 +159,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
   // range of c + 2 stride are loaded, and chunk c is decoded.
   int64_t c = (int64_t)blockIdx.x * kWarps + warp;
   ChunkRange cur_r = load_range(s, c);
-  ChunkData cur = load_data(s, c, lane);
+  ChunkData cur = load_data<BPL>(s, c, lane);
   ChunkRange nxt_r = load_range(s, c + stride);
   bool cur_issued = c < s.nchunks && issue(cur_r, 0);
   unsigned phase = 0;  // bit b: parity of buffer b's next completion
@@ -143,16 +174,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
       if (lane == 0) fence_proxy_async_smem();
       nxt_issued = issue(nxt_r, b ^ 1);
     }
-    const ChunkData nxt = load_data(s, cn, lane);
+    const ChunkData nxt = load_data<BPL>(s, cn, lane);
     const ChunkRange nn_r = load_range(s, cn + stride);
     // block offsets inside the chunk: exclusive scan of the block sizes
-    // (1 sign word + w magnitude words, 0 for width 0)
-    const int64_t bb = c * kChunkBlocks + 4 * lane;
-    uint32_t wj[4], oj[4];
+    // (SEGS sign words + SEGS w magnitude words, 0 for width 0)
+    const int64_t bb = c * (32 * BPL) + BPL * lane;
+    uint32_t wj[BPL], oj[BPL];
     uint32_t lsum = 0;
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < BPL; ++j) {
       uint32_t w = (cur.w4 >> (8 * j)) & 0xffu;
       if (bb + j >= s.nb) w = 0;
       if (w > (uint32_t)s.wmax) {
@@ -161,7 +192,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
       }
       wj[j] = w;
       oj[j] = lsum;
-      lsum += w ? w + 1u : 0u;
+      lsum += w ? SEGS * (w + 1u) : 0u;
     }
     uint32_t incl = lsum;
 #pragma unroll
@@ -187,14 +218,39 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
       const uint32_t* base = bufs + (size_t)b * buf_words + (uint32_t)(cur_r.p0 & 3) + (incl - lsum);
       const int32_t hj[4] = {cur.h4.x, cur.h4.y, cur.h4.z, cur.h4.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < BPL; ++j) {
         const int64_t blk = bb + j;
         if (blk >= s.nb) break;
         const uint32_t w = wj[j];
         const int32_t head = hj[j];
         const uint32_t* bw = base + oj[j];
         const int cnt = (int)min((int64_t)32, s.N - blk * 32);
-        if constexpr (PRED == HC_PRED_MEAN) {
+        if constexpr (PRED == HC_PRED_MEAN_ND) {
+          // q = M_b + p for every slot of the box's true size S_b (HSZx-nd;
+          // padding slots hold p = 0): sums from sum p and sum p^2
+          const long long sb = box_size(bd, blk, 32 * SEGS);
+          long long sp = 0;
+          unsigned long long sp2 = 0;
+          if (w) {
+#pragma unroll
+            for (int t = 0; t < SEGS; ++t) {
+              int32_t a = 0;
+              unsigned long long a2 = 0;
+              decode32<G>(bw + SEGS + t * w, bw[t], w, [&](int, int32_t x, int32_t neg) {
+                const int32_t p = x - neg;
+                a += p;
+                if (OP == OP_VAR) a2 += (unsigned long long)((long long)p * p);
+              });
+              sp += a;
+              sp2 += a2;
+            }
+          }
+          S1 += sb * head + sp;
+          if (OP == OP_VAR) {
+            const long long cc = (long long)head - c0;
+            S2 += (u128)((i128)sb * cc * cc + (i128)2 * cc * sp + (i128)sp2);
+          }
+        } else if constexpr (PRED == HC_PRED_MEAN) {
           // q = M_b + p for every slot (HSZx): sums from sum p and sum p^2
           long long sp = 0;
           unsigned long long sp2 = 0;
@@ -285,13 +341,25 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
   });
 }
 
-template <int G, int OP, int ACC, int PRED>
+template <int G, int OP, int ACC, int PRED, int BPL>
 int launch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts, unsigned* ticket,
            int max_parts, const long long* shift, cudaStream_t st) {
   const DevStream s = dev_stream(h, d_stream);
   const int bw = chunk_buf_words((int)h->wmax);
   const int bytes = smem_bytes(bw);
-  auto kern = k_reduce32<G, OP, ACC, PRED>;
+  auto kern = k_reduce32<G, OP, ACC, PRED, BPL>;
+  BoxDims bd{};
+  if (PRED == HC_PRED_MEAN_ND) {
+    bd.n0 = h->dims[0];
+    bd.n1 = h->dims[1];
+    bd.n2 = h->dims[2];
+    bd.b0 = (int)h->block[0];
+    bd.b1 = (int)h->block[1];
+    bd.b2 = (int)h->block[2];
+    bd.g1 = ceil_div(bd.n1, bd.b1);
+    bd.g2 = ceil_div(bd.n2, bd.b2);
+    bd.ragged = bd.n0 % bd.b0 || bd.n1 % bd.b1 || bd.n2 % bd.b2;
+  }
   int rc = ensure_smem(reinterpret_cast<const void*>(kern), bytes);
   if (rc) return rc;
   int per_sm = 0;
@@ -299,19 +367,42 @@ int launch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* 
   per_sm = std::max(per_sm, 1);
   int64_t grid = std::min<int64_t>((int64_t)device_sms() * per_sm, ceil_div(h->nchunks, kWarps));
   grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::min<int64_t>(kMaxGrid, max_parts)));
-  kern<<<(unsigned)grid, kWarps * 32, bytes, st>>>(s, bw, parts, ticket, d_out, 2.0 * h->eps, shift);
+  kern<<<(unsigned)grid, kWarps * 32, bytes, st>>>(s, bw, parts, ticket, d_out, 2.0 * h->eps, shift, bd);
   return check_launch_cfg("reduce (block size 32)", reinterpret_cast<const void*>(kern), grid, bytes);
 }
 
-template <int OP, int ACC, int PRED>
+template <int OP, int ACC, int PRED, int BPL = 4>
 int launch_g(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts, unsigned* ticket,
              int max_parts, const long long* shift, cudaStream_t st) {
-  if (h->wmax <= 8) return launch<4, OP, ACC, PRED>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
-  if (h->wmax <= 10) return launch<3, OP, ACC, PRED>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
-  return launch<2, OP, ACC, PRED>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+  if (h->wmax <= 8)
+    return launch<4, OP, ACC, PRED, BPL>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+  if (h->wmax <= 10)
+    return launch<3, OP, ACC, PRED, BPL>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+  return launch<2, OP, ACC, PRED, BPL>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
+}
+
+template <int BPL>
+int box_dispatch(const hc_header* h, const void* d_stream, int what, hc_scalar* d_out, Partial* parts,
+                 unsigned* ticket, int max_parts, const long long* shift, cudaStream_t st) {
+  if (what == RED_MEAN)
+    return launch_g<OP_MEAN_Q, 1, HC_PRED_MEAN_ND, BPL>(h, d_stream, d_out, parts, ticket, max_parts, nullptr, st);
+  return launch_g<OP_VAR, 1, HC_PRED_MEAN_ND, BPL>(h, d_stream, d_out, parts, ticket, max_parts, shift, st);
 }
 
 }  // namespace
+
+bool reduce32_box_applies(const hc_header* h) {
+  return h->pred == HC_PRED_MEAN_ND && (h->S == 64 || h->S == 128) && h->wmax <= 16 && h->qmax > 0 &&
+         h->qmax < (1u << 26);
+}
+
+int reduce32_box_impl(const hc_header* h, const void* d_stream, int what, hc_scalar* d_out, Partial* parts,
+                      unsigned* ticket, int max_parts, const long long* shift, cudaStream_t st) {
+  // stages 2 and 3 have the same sums (sum q = sum p + M_b S_b); with
+  // `shift` the squares are taken about the integer mean (stage-2 std)
+  if (h->S == 64) return box_dispatch<2>(h, d_stream, what, d_out, parts, ticket, max_parts, shift, st);
+  return box_dispatch<1>(h, d_stream, what, d_out, parts, ticket, max_parts, shift, st);
+}
 
 bool reduce32_applies(const hc_header* h) {
   return h->S == 32 && (h->pred == HC_PRED_DELTA || h->pred == HC_PRED_MEAN) && h->wmax <= 16 && h->qmax > 0 &&

@@ -500,15 +500,24 @@ int xnd_stats_impl(const hc_header* h, const void* d_stream, int level, int what
     if (what != RED_MEAN) return fail(HC_ERR_UNSUPPORTED, "stage 1 gives the mean only (Eq. mean_m)");
     return launch_mean_m_box(h, d_stream, d_out, d_ws, nullptr, st);
   }
-  if (what == RED_MEAN) return launch_stats_box_m<0>(h, d_stream, d_out, d_ws, nullptr, st);
+  // boxes of 64 or 128 slots with narrow widths: the warp-autonomous
+  // statistics kernel of hc_reduce32.cu; else the tile kernel k_stats_box
+  OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
+  const bool r32 = reduce32_box_applies(h);
+  Partial* parts = ws_partials(d_ws);
+  if (what == RED_MEAN)
+    return r32 ? reduce32_box_impl(h, d_stream, RED_MEAN, d_out, parts, &ws->ticket, kMaxGrid, nullptr, st)
+               : launch_stats_box_m<0>(h, d_stream, d_out, d_ws, nullptr, st);
   if (level == HC_STAGE_P) {
     // Section V-A: the deviations about the integer mean mu~ of stage 1
-    long long* mu = reinterpret_cast<long long*>(&reinterpret_cast<OpWs*>(d_ws)->pad[0]);
+    long long* mu = reinterpret_cast<long long*>(&ws->pad[0]);
     int rc = launch_mean_m_box(h, d_stream, d_out, d_ws, mu, st);
     if (rc) return rc;
-    return launch_stats_box_m<2>(h, d_stream, d_out, d_ws, mu, st);
+    return r32 ? reduce32_box_impl(h, d_stream, RED_VAR, d_out, parts, &ws->ticket, kMaxGrid, mu, st)
+               : launch_stats_box_m<2>(h, d_stream, d_out, d_ws, mu, st);
   }
-  return launch_stats_box_m<1>(h, d_stream, d_out, d_ws, nullptr, st);
+  return r32 ? reduce32_box_impl(h, d_stream, RED_VAR, d_out, parts, &ws->ticket, kMaxGrid, nullptr, st)
+             : launch_stats_box_m<1>(h, d_stream, d_out, d_ws, nullptr, st);
 }
 
 int xnd_stencil_impl(const hc_header* h, const void* d_stream, int level, int op, int axis3, void* d_out,
