@@ -331,8 +331,20 @@ __global__ void __launch_bounds__(kThreads) k_global_mean(DevStream s, int64_t L
       const uint32_t w = tv.w[bl];
       if (cnt <= 0 || w == 0) continue;
       const int64_t e0 = b * s.S + 32 * j;
-      int64_t x = e0 % L2, r = e0 / L2;
-      int64_t y = r % L1, z = r / L1;
+      int64_t x, y, z;
+      if (s.N <= 0xffffffffll) {
+        // 32-bit divisions (the 64-bit ones cost several times more per segment)
+        const uint32_t e = (uint32_t)e0, l2 = (uint32_t)L2, l1 = (uint32_t)L1;
+        const uint32_t r = e / l2, zz = r / l1;
+        x = e - r * l2;
+        y = r - zz * l1;
+        z = zz;
+      } else {
+        const int64_t r = e0 / L2;
+        x = e0 - r * L2;
+        y = r % L1;
+        z = r / L1;
+      }
       unsigned long long wzy = (unsigned long long)(L0 - z) * (unsigned long long)(L1 - y);
       const uint32_t* blk = tv.words + tv.off[bl];
       if (L2 - x >= cnt) {
@@ -564,6 +576,8 @@ int global_stats_impl(const hc_header* h, const void* d_stream, int level, int w
                       size_t ws_bytes, cudaStream_t st) {
   if (level == HC_STAGE_M) return fail(HC_ERR_UNSUPPORTED, "a global-predictor stream keeps no block metadata");
   OpWs* ws = reinterpret_cast<OpWs*>(d_ws);
+  if (level == HC_STAGE_P && what == RED_MEAN && reduce32_global_mean_applies(h))
+    return reduce32_global_mean_impl(h, d_stream, d_out, ws_partials(d_ws), &ws->ticket, kMaxGrid, st);
   if (level == HC_STAGE_P && what == RED_MEAN) {
     const DevStream s = dev_stream(h, d_stream);
     int64_t L[3];

@@ -42,7 +42,13 @@ constexpr unsigned kWaitPolls = 1u << 22;
 
 // What a launch sums: the stage-2 weighted sum (mean), the stage-3 sum
 // (mean), or the stage-3 sums of q and q^2 (variance).
-enum Op { OP_MEAN_P = 0, OP_MEAN_Q = 1, OP_VAR = 2 };
+enum Op { OP_MEAN_P = 0, OP_MEAN_Q = 1, OP_VAR = 2, OP_MEAN_G = 3 };
+// OP_MEAN_G: the stage-2 mean of a global-predictor stream (HSZp-nd Lorenzo
+// residuals, or HSZp's delta across blocks), sum q = sum_i p_i (L0 - z)(L1 -
+// y)(L2 - x) over the prediction shape L, modulo 2^64 (exact: sum q fits
+// 63 bits).  For a block of 32 codes inside one row starting at x0, sum_k p_k
+// (L2 - x0 - k) = (L2 - x0 - 32) sum_k p_k + sum_k (32 - k) p_k: two sums per
+// block, the second the stage-2 weighted sum of the block-head streams.
 
 // Words of one chunk buffer: 128 blocks of at most wmax + 1 words, the
 // copy's 16-byte alignment on both ends and the decoder's read-ahead.
@@ -92,7 +98,8 @@ __device__ __forceinline__ ChunkData load_data(const DevStream& s, int64_t c, in
 }
 
 // Box geometry of an HSZx-nd stream, for the true sizes of ragged boxes at
-// the field's far faces (unused for 1-D blocks and when every box is full).
+// the field's far faces (unused for 1-D blocks and when every box is full);
+// for OP_MEAN_G, (n0, n1, n2) is the prediction shape L.
 struct BoxDims {
   int64_t n0, n1, n2, g1, g2;
   int b0, b1, b2;
@@ -129,6 +136,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
   int err = 0;
   long long S1 = 0;
   u128 S2 = 0;
+  unsigned long long G1 = 0;  // OP_MEAN_G: sum q modulo 2^64
 
   if (lane == 0) {
     mbar_init(bar, 1);
@@ -225,7 +233,41 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
         const int32_t head = hj[j];
         const uint32_t* bw = base + oj[j];
         const int cnt = (int)min((int64_t)32, s.N - blk * 32);
-        if constexpr (PRED == HC_PRED_MEAN_ND) {
+        if constexpr (OP == OP_MEAN_G) {
+          // position of the block's first code in the prediction shape
+          // (32-bit when N < 2^32, as the launch requires)
+          const uint32_t e0 = (uint32_t)blk * 32u, l2 = (uint32_t)bd.n2, l1 = (uint32_t)bd.n1;
+          const uint32_t r = e0 / l2, x0 = e0 - r * l2, zz = r / l1, yy = r - zz * l1;
+          const unsigned long long wzy =
+              (unsigned long long)((uint64_t)bd.n0 - zz) * (unsigned long long)((uint64_t)l1 - yy);
+          if (w == 0 || cnt <= 0) continue;
+          if (cnt == 32 && x0 + 32u <= l2) {
+            // inside one row: sum p and sum (32 - k) p from the grouped unpacker
+            int32_t a = 0, aw = 0;
+            decode32<G>(bw + 1, bw[0], w, [&](int k, int32_t x, int32_t) {
+              a += x;
+              aw += (32 - k) * x;
+            });
+            const long long P = (long long)a + __popc(bw[0]);
+            const long long R = (long long)aw + weighted_sign_count(bw[0]);
+            G1 += wzy * ((unsigned long long)(l2 - x0 - 32u) * (unsigned long long)P + (unsigned long long)R);
+          } else {
+            // a block that crosses a row end (or the field's last one): code by code
+            unsigned long long wz = wzy;
+            uint32_t x = x0, y = yy, z = zz;
+            unpack_segment<false>(bw + 1, bw[0], w, cnt, [&](int, int32_t p) {
+              G1 += wz * (unsigned long long)(l2 - x) * (unsigned long long)(long long)p;
+              if (++x == l2) {
+                x = 0;
+                if (++y == l1) {
+                  y = 0;
+                  ++z;
+                }
+                wz = (unsigned long long)((uint64_t)bd.n0 - z) * (unsigned long long)((uint64_t)l1 - y);
+              }
+            });
+          }
+        } else if constexpr (PRED == HC_PRED_MEAN_ND) {
           // q = M_b + p for every slot of the box's true size S_b (HSZx-nd;
           // padding slots hold p = 0): sums from sum p and sum p^2
           const long long sb = box_size(bd, blk, 32 * SEGS);
@@ -333,6 +375,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
     nxt_r = nn_r;
     cur_issued = nxt_issued;
   }
+  if constexpr (OP == OP_MEAN_G) S1 = (long long)G1;
   reduce_and_finish(S1, S2, err, parts, ticket, [&](long long a, u128 b2, int e) {
     if (shift)
       finalize_about(out, s.N, a, b2, c0, two_eps, e);
@@ -349,7 +392,13 @@ int launch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* 
   const int bytes = smem_bytes(bw);
   auto kern = k_reduce32<G, OP, ACC, PRED, BPL>;
   BoxDims bd{};
-  if (PRED == HC_PRED_MEAN_ND) {
+  if (OP == OP_MEAN_G) {
+    // the prediction shape: the field's for HSZp-nd, (1, 1, N) for HSZp
+    const bool flat = h->pred == HC_PRED_GLOBAL_DELTA;
+    bd.n0 = flat ? 1 : h->dims[0];
+    bd.n1 = flat ? 1 : h->dims[1];
+    bd.n2 = flat ? h->N : h->dims[2];
+  } else if (PRED == HC_PRED_MEAN_ND) {
     bd.n0 = h->dims[0];
     bd.n1 = h->dims[1];
     bd.n2 = h->dims[2];
@@ -402,6 +451,21 @@ int reduce32_box_impl(const hc_header* h, const void* d_stream, int what, hc_sca
   // `shift` the squares are taken about the integer mean (stage-2 std)
   if (h->S == 64) return box_dispatch<2>(h, d_stream, what, d_out, parts, ticket, max_parts, shift, st);
   return box_dispatch<1>(h, d_stream, what, d_out, parts, ticket, max_parts, shift, st);
+}
+
+bool reduce32_global_mean_applies(const hc_header* h) {
+  // rows a multiple of 32 codes (or HSZp's single row): a block crossing a
+  // row end takes the code-by-code path, and with such blocks in most
+  // chunks the warps would wait on those lanes (the tile kernel
+  // k_global_mean is faster there)
+  const bool rows32 = h->pred == HC_PRED_GLOBAL_DELTA || h->dims[2] % 32 == 0;
+  return h->S == 32 && (h->pred == HC_PRED_LORENZO || h->pred == HC_PRED_GLOBAL_DELTA) && h->wmax <= 16 &&
+         h->N < 0xffffff00ll && rows32;
+}
+
+int reduce32_global_mean_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,
+                              unsigned* ticket, int max_parts, cudaStream_t st) {
+  return launch_g<OP_MEAN_G, 1, HC_PRED_LORENZO>(h, d_stream, d_out, parts, ticket, max_parts, nullptr, st);
 }
 
 bool reduce32_applies(const hc_header* h) {
