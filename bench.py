@@ -585,8 +585,8 @@ def run_extras(hc, torch, dev, fields, peak, args):
     """The other configurations of the paper-like benchmark, each bounded in
     time, as sub-objects of the benchmark line: the block-mean (HSZx), global
     predictor (HSZp-nd, HSZp) and box-mean (HSZx-nd) forms of the five fields,
-    the 64-field batched launch, the wide-code float64 field and the serving
-    loop's saturation curve."""
+    the 64-field batched launch, the wide-code float64 field, the serving
+    loop's saturation curve and the small PR1 reference field."""
     out = {}
     jobs = (("hszx", lambda: measure_hszx(hc, torch, dev, fields)),
             ("lorenzo", lambda: measure_lorenzo(hc, torch, dev, fields)),
@@ -594,6 +594,7 @@ def run_extras(hc, torch, dev, fields, peak, args):
             ("batched", lambda: measure_batched(hc, torch, dev, steps=max(3, args.steps), warmup=3,
                                                 device_fields=True, sample_clocks=False)),
             ("wide", lambda: measure_wide(hc, torch, dev, device_field=True)),
+            ("pr1", lambda: measure_pr1(hc, torch, dev)),
             ("serving", lambda: measure_serving(hc, torch, dev, nfields=args.fields, qps_list=SERVING_QPS,
                                                 duration=args.serving_duration, p99_ms=SERVING_P99_MS)))
     for name, fn in jobs:
@@ -1491,6 +1492,31 @@ def run_profile_lorenzo():
     torch.cuda.synchronize()
     print(json.dumps({"profile_lorenzo": "ok", "compressed_bytes": c.nbytes, "wmax": int(c.header.wmax)}))
     return 0
+
+
+def measure_pr1(hc, torch, dev):
+    """The small reference configuration: one 64^3 float32 field, the sum of
+    8 seeded plane sinusoids plus N(0, 0.01^2) noise, min-max normalised,
+    value-range-relative eb 1e-3, block 32.  Every operation fused at stages
+    2 and 3, on a materialised stage-3 array, and on the plain path (stage 4),
+    each the median of REPS runs with an L2 flush before each.  The field
+    (1 MB) fits in L2, so the line is reported for completeness and is not a
+    roofline figure."""
+    import synth
+
+    peak, _ = measured_peaks()
+    shape = (64, 64, 64)
+    x = torch.from_numpy(synth.sinusoid_field(shape)).to(dev)
+    c = hc._trim(hc.compress(x, EB, rel=True, S=BLOCK))
+    del x
+    row = cold_table(hc, torch, dev, c, shape, peak, plain=True, split=True)
+    return {"metric": "PR1 reference field: ms per operation, fused at stages 2 / 3, on the stage-3 array, "
+                      "and on the plain path",
+            "config": {"workload": "PR1: 64x64x64 float32, 8 seeded plane sinusoids + N(0, 0.01^2) noise, "
+                                   "min-max normalised; value-range-relative eb=1e-3; block 32",
+                       "timing": f"median of {REPS} CUDA-event runs per op, L2 flushed before each",
+                       "note": "the 1 MB field fits in L2: not a roofline figure"},
+            "data": "synthetic", "field": row}
 
 
 def measure_wide(hc, torch, dev, device_field=False):

@@ -359,8 +359,12 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
 
   const int64_t y0 = (int64_t)yt * g.ty, y1 = min(y0 + g.ty, g.n1);
   const int64_t z0 = (int64_t)zt * g.tz, z1 = min(z0 + g.tz, g.n0);
-  const int64_t ylo = max(y0 - 1, (int64_t)0), yhi = min(y1 + 1, g.n1);
-  const int64_t zs = max(z0 - 1, (int64_t)0), ze = min(z1 + 1, g.n0);  // slabs [zs, ze)
+  // halo rows and planes: a derivative reads neighbours along its own axis
+  // only, so the rows above and below the tile are decoded for axis 1 alone
+  // and the planes around its range for axis 0 alone
+  const bool hy = OP != ST_DERIV || g.axis == 1, hz = OP != ST_DERIV || g.axis == 0;
+  const int64_t ylo = hy ? max(y0 - 1, (int64_t)0) : y0, yhi = hy ? min(y1 + 1, g.n1) : y1;
+  const int64_t zs = hz ? max(z0 - 1, (int64_t)0) : z0, ze = hz ? min(z1 + 1, g.n0) : z1;  // slabs [zs, ze)
   const int nslab = (int)(ze - zs);
 
   auto meta_w = [&](int j) { return sm + L.wb + (j % kWidthBufs) * g.pre_max; };
@@ -479,7 +483,9 @@ __device__ inline void pipe_tile(const DevStream& s, const PGeo& g, int yt, int 
       const int ww = warp - 1;
       const int64_t ready = zs + k - 1;  // last slab decoded in an earlier step
       int64_t zc1 = znext;
-      while (zc1 < z1 && min(zc1 + 1, g.n0 - 1) <= ready) ++zc1;
+      // a plane is ready once its own slab (and, when planes are neighbours,
+      // the next one) is decoded
+      while (zc1 < z1 && min(zc1 + (hz ? 1 : 0), g.n0 - 1) <= ready) ++zc1;
       const int nplanes = (int)(zc1 - znext);
       const int nseg_k = k < nslab ? slab_desc(s, g, zs + k, ylo, yhi).nblk : 0;
       // full items of VW outputs, then (V = 0: rows of any length) the
