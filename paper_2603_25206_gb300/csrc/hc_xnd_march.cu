@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(kThreads) k_box_offsets(DevStream s, uint32_t*
 // kOX - 1 / kOX + nx), the slot table (slot -> (s0 << 20) | s1 pitch + s2)
 // and, at stage 2, the box means of three layers around the tile.
 template <int OP, int OUT, bool ST2, int AX>
-__global__ void __launch_bounds__(kThreads, 3) k_box_march(DevStream s, MGeo m, Geo g, const uint32_t* __restrict__ boff,
-                                                       typename OutType<OUT>::T* __restrict__ out, int* err) {
+__global__ void __launch_bounds__(kThreads, 3)
+    k_box_march(DevStream s, MGeo m, Geo g, const uint32_t* __restrict__ boff,
+                typename OutType<OUT>::T* __restrict__ out, int* err) {
   using T = typename OutType<OUT>::T;
   extern __shared__ __align__(16) int32_t sm[];
   int32_t* ring = sm;
@@ -162,11 +163,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_box_march(DevStream s, MGeo m, 
   __syncthreads();
 
   int64_t znext = z0;  // next output plane
+  // halos: a derivative reads neighbours along its own axis only (no plane
+  // below / above the range unless AX = 0, no row / column halo unless AX =
+  // 1 / 2); a plane is then ready once its own layer is decoded
+  constexpr bool HZ = OP != ST_DERIV || AX == 0, HY = OP != ST_DERIV || AX == 1, HX = OP != ST_DERIV || AX == 2;
+  const int64_t kfirst = HZ ? max(ka - 1, (int64_t)0) : ka;
   // (k b0) mod P and k mod 3 of the first layer the loop visits, then
   // advanced by one layer per iteration
-  const int64_t kfirst = max(ka - 1, (int64_t)0);
   int zb = (int)((kfirst * m.b0) % m.P), k3 = (int)(kfirst % 3);
-  for (int64_t k = kfirst; k <= kb; ++k) {
+  for (int64_t k = kfirst; k <= (HZ ? kb : kb - 1); ++k) {
     if (k >= m.g0) break;  // uniform over the CTA
     // planes of layer k to decode: the whole layer inside the range, the
     // last plane of the layer below it, the first plane of the layer above
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_box_march(DevStream s, MGeo m, 
     // the thread's staging slot with every load in flight together.
     {
       const int nown = Rt * Xt * nj;
-      const bool hy0 = y0 > 0, hy1 = y1 < m.n1, hx0 = x0 > 0, hx1 = x1 < m.n2;
+      const bool hy0 = HY && y0 > 0, hy1 = HY && y1 < m.n1, hx0 = HX && x0 > 0, hx1 = HX && x1 < m.n2;
       const int runs = (hy0 + hy1) * Xt + (hx0 + hx1) * Rt;
       const int nhalo = (k != ka - 1 && k != kb) ? (int)(zhi - zlo + 1) * runs : 0;
       uint32_t* sb = stg + tid * m.sw;
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_box_march(DevStream s, MGeo m, 
 
     // every output plane whose neighbours are decoded: up to zhi - 1, or
     // up to the field's last plane once it is decoded
-    const int64_t zc_end = min(z1, zhi >= m.n0 - 1 ? m.n0 : zhi);
+    const int64_t zc_end = min(z1, (zhi >= m.n0 - 1 || !HZ) ? zhi + 1 : zhi);
     for (; znext < zc_end; ++znext) {
       const int64_t z = znext;
       const int64_t zm = z > 0 ? z - 1 : z, zp = z + 1 < m.n0 ? z + 1 : z;
