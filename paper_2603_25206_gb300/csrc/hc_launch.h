@@ -119,8 +119,8 @@ bool reduce32_applies(const hc_header* h);
 // |q| < 2^26): the mean (what RED_MEAN) and the sums about `shift` (NULL:
 // the exact stage-3 variance).
 bool reduce32_box_applies(const hc_header* h);
-// The stage-2 mean of a global-predictor stream (HSZp-nd with rows of a
-// multiple of 32 codes, HSZp) of block size 32, widths <= 16 and N below
+// The stage-2 mean of a global-predictor stream (HSZp-nd with rows of at
+// least 32 codes, HSZp) of block size 32, widths <= 16 and N below
 // 2^32 - 256, on the same kernel.
 bool reduce32_global_mean_applies(const hc_header* h);
 int reduce32_global_mean_impl(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* parts,

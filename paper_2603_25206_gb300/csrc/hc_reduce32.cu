@@ -99,7 +99,8 @@ __device__ __forceinline__ ChunkData load_data(const DevStream& s, int64_t c, in
 
 // Box geometry of an HSZx-nd stream, for the true sizes of ragged boxes at
 // the field's far faces (unused for 1-D blocks and when every box is full);
-// for OP_MEAN_G, (n0, n1, n2) is the prediction shape L.
+// for OP_MEAN_G, (n0, n1, n2) is the prediction shape L and `ragged` says
+// that blocks cross row ends.
 struct BoxDims {
   int64_t n0, n1, n2, g1, g2;
   int b0, b1, b2;
@@ -251,6 +252,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
             const long long P = (long long)a + __popc(bw[0]);
             const long long R = (long long)aw + weighted_sign_count(bw[0]);
             G1 += wzy * ((unsigned long long)(l2 - x0 - 32u) * (unsigned long long)P + (unsigned long long)R);
+          } else if (cnt == 32 && bd.ragged) {
+            // across one row end (rows of at least 32 codes): codes k < kb end
+            // row A, codes k >= kb start row B at x = k - kb; the same two sums
+            // over each part (row B's from a predicated second pair), with
+            // weights (L2 - x0 - 32) for A and (L2 + kb - 32) for B, modulo 2^64
+            const uint32_t kb = l2 - x0;
+            int32_t a = 0, aw = 0, b = 0, bw2 = 0;
+            decode32<G>(bw + 1, bw[0], w, [&](int k, int32_t x, int32_t) {
+              a += x;
+              aw += (32 - k) * x;
+              const int32_t xb = (uint32_t)k >= kb ? x : 0;
+              b += xb;
+              bw2 += (32 - k) * xb;
+            });
+            const uint32_t mb = ~0u << kb, sw = bw[0];
+            const long long PB = (long long)b + __popc(sw & mb), RB = (long long)bw2 + weighted_sign_count(sw & mb);
+            const long long PA = (long long)a + __popc(sw) - PB, RA = (long long)aw + weighted_sign_count(sw) - RB;
+            const uint32_t yb = yy + 1u == l1 ? 0u : yy + 1u, zb = yy + 1u == l1 ? zz + 1u : zz;
+            const unsigned long long wzyb =
+                (unsigned long long)((uint64_t)bd.n0 - zb) * (unsigned long long)((uint64_t)l1 - yb);
+            const unsigned long long wa = (unsigned long long)((long long)l2 - x0 - 32);  // negative: wraps
+            G1 += wzy * (wa * (unsigned long long)PA + (unsigned long long)RA);
+            G1 += wzyb * ((unsigned long long)(l2 + kb - 32u) * (unsigned long long)PB + (unsigned long long)RB);
           } else {
             // a block that crosses a row end (or the field's last one): code by code
             unsigned long long wz = wzy;
@@ -398,6 +422,7 @@ int launch(const hc_header* h, const void* d_stream, hc_scalar* d_out, Partial* 
     bd.n0 = flat ? 1 : h->dims[0];
     bd.n1 = flat ? 1 : h->dims[1];
     bd.n2 = flat ? h->N : h->dims[2];
+    bd.ragged = bd.n2 % 32 != 0;  // blocks across row ends (rows of >= 32 codes)
   } else if (PRED == HC_PRED_MEAN_ND) {
     bd.n0 = h->dims[0];
     bd.n1 = h->dims[1];
@@ -454,11 +479,10 @@ int reduce32_box_impl(const hc_header* h, const void* d_stream, int what, hc_sca
 }
 
 bool reduce32_global_mean_applies(const hc_header* h) {
-  // rows a multiple of 32 codes (or HSZp's single row): a block crossing a
-  // row end takes the code-by-code path, and with such blocks in most
-  // chunks the warps would wait on those lanes (the tile kernel
-  // k_global_mean is faster there)
-  const bool rows32 = h->pred == HC_PRED_GLOBAL_DELTA || h->dims[2] % 32 == 0;
+  // rows of at least 32 codes (or HSZp's single row): a block then crosses
+  // at most one row end, which the two-part sums handle without leaving
+  // the grouped unpacker
+  const bool rows32 = h->pred == HC_PRED_GLOBAL_DELTA || h->dims[2] >= 32;
   return h->S == 32 && (h->pred == HC_PRED_LORENZO || h->pred == HC_PRED_GLOBAL_DELTA) && h->wmax <= 16 &&
          h->N < 0xffffff00ll && rows32;
 }
