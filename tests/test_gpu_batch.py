@@ -137,6 +137,51 @@ def test_other_field_ops(env, orc):
                     (orc.sums_q(q)[0], orc.sums_q(q)[1] if "variance" in ops else 0)
 
 
+# Rows whose length is not a multiple of 4 (block 32) take the padded ring:
+# one to several 8-wide items per row, the last one partial; tiles of one row
+# up to the whole plane (ty caps the height); 3-D, 2-D and 1-D fields.
+PADDED_3D = [(3, 4, 7), (5, 9, 9), (4, 6, 15), (3, 17, 23), (6, 5, 33), (2, 3, 63), (7, 2, 2), (2, 1, 129),
+             (9, 13, 37), (30, 70, 131), (1, 1, 1), (1, 6, 5)]
+PADDED_LOW = [(7, 13), (11, 3), (5,), (3001,), (40, 257)]
+
+
+@pytest.mark.parametrize("ty", [0, 1, 2])
+def test_padded_rows_every_operation(env, orc, ty):
+    hc, torch, dev = env
+    tune = {"ty": ty} if ty else {}
+    shapes = PADDED_3D + PADDED_LOW
+    specs = [(sh, 32, "laplacian|variance", 1e-3, True, 60 + j) for j, sh in enumerate(shapes)]
+    for fd in ("int64", "float32", "float64"):
+        b, refs = _make(env, orc, specs, field_dtype=fd, **tune)
+        b.run()
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        _check(orc, b, refs, fd)
+        for c, (sc, f) in zip(b.comps, b.results()):
+            assert torch.equal(hc.laplacian(c, out_dtype=fd), f), (fd, c.shape)
+    specs = [(sh, 32, "gradmag|mean", 1e-3, True, 90 + j) for j, sh in enumerate(shapes)]
+    b, refs = _make(env, orc, specs, field_dtype="float64", **tune)
+    b.run()
+    for (sc, f), (q, eps, ops) in zip(b.results(), refs):
+        assert sc["s1"] == orc.sums_q(q)[0]
+        val = orc.stencil_q(q, orc.KIND_GRADMAG, eps)
+        assert np.all(np.abs(f.cpu().numpy() - val) <= 1e-12 * np.maximum(np.abs(val), eps))
+    for ax in range(3):
+        specs = [(sh, 32, "derivative|variance", 1e-3, True, 120 + j) for j, sh in enumerate(PADDED_3D)]
+        b, refs = _make(env, orc, specs, field_dtype="int64", axis=ax, **tune)
+        b.run()
+        for (sc, f), (q, eps, ops) in zip(b.results(), refs):
+            assert np.array_equal(f.cpu().numpy(), orc.deriv_q(q, ax)), (ax, q.shape)
+            assert (sc["s1"], sc["s2"]) == orc.sums_q(q)
+    for ax in range(2):
+        specs = [(sh, 32, "derivative", 1e-3, True, 150 + j) for j, sh in enumerate(PADDED_LOW) if len(sh) == 2]
+        b, refs = _make(env, orc, specs, field_dtype="float32", axis=ax, **tune)
+        b.run()
+        for (sc, f), (q, eps, ops) in zip(b.results(), refs):
+            val = orc.stencil_q(q, orc.KIND_DERIV, eps, axis=ax)
+            assert np.all(np.abs(f.cpu().numpy() - val) <= 1e-6 * np.maximum(np.abs(val), eps)), (ax, q.shape)
+
+
 def test_graph_replay_and_launch_shapes_identical(env, orc):
     hc, torch, dev = env
     b, refs = _make(env, orc, MIXED, field_dtype="float32")
