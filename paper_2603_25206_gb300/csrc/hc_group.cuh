@@ -84,6 +84,67 @@ __device__ __forceinline__ void decode32(const uint32_t* __restrict__ mw, uint32
   }
 }
 
+// decode32 over two independent segments (a, b) side by side: the same
+// sliding windows, one per segment, advanced in the same unrolled loop, so
+// the two dependency chains (window moves, running sums in the callbacks)
+// interleave instead of running one after the other.  fa(k, x, neg) and
+// fb(k, x, neg) are called for k = 0..31 in order, as in decode32.  A
+// segment of width 0 decodes to x = neg (p = 0); its sign word and window
+// words are then whatever follows in shared memory, which callers must
+// keep readable (three words past the segment's start).
+template <int G, class FA, class FB>
+__device__ __forceinline__ void decode32x2(const uint32_t* __restrict__ ma, uint32_t sa, uint32_t wa,
+                                           const uint32_t* __restrict__ mb, uint32_t sb, uint32_t wb, FA&& fa,
+                                           FB&& fb) {
+  static_assert(G >= 1 && G <= 4, "groups of 1 to 4 codes");
+  constexpr int NG = (32 + G - 1) / G;
+  const uint32_t mska = (1u << wa) - 1u, mskb = (1u << wb) - 1u;
+  uint32_t sha[8], shb[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    sha[r] = sa << r;
+    shb[r] = sb << r;
+  }
+  uint32_t loa = ma[0], hia = ma[1], nxa = ma[2];
+  uint32_t lob = mb[0], hib = mb[1], nxb = mb[2];
+  const uint32_t* pa = ma + 3;
+  const uint32_t* pb = mb + 3;
+  const uint32_t gwa = (uint32_t)G * wa, gwb = (uint32_t)G * wb;
+  uint32_t oa = 0, ob = 0;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const uint32_t ya = __funnelshift_r(loa, hia, oa);
+    const uint32_t yb = __funnelshift_r(lob, hib, ob);
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int k = g * G + i;
+      if (k < 32) {
+        const uint32_t yia = ya >> (i * wa), yib = yb >> (i * wb);
+        const uint32_t nega = byte_sign(sha[7 - (k & 7)], (uint32_t)(k >> 3));
+        const uint32_t negb = byte_sign(shb[7 - (k & 7)], (uint32_t)(k >> 3));
+        fa(k, (int32_t)((yia & mska) ^ nega), (int32_t)nega);
+        fb(k, (int32_t)((yib & mskb) ^ negb), (int32_t)negb);
+      }
+    }
+    if (g + 1 < NG) {
+      oa += gwa;
+      if (oa >= 32u) {
+        oa -= 32u;
+        loa = hia;
+        hia = nxa;
+        nxa = *pa++;
+      }
+      ob += gwb;
+      if (ob >= 32u) {
+        ob -= 32u;
+        lob = hib;
+        hib = nxb;
+        nxb = *pb++;
+      }
+    }
+  }
+}
+
 // decode32 with each group's window read by index: group g's first bit is
 // g G w, its word (g G w) / 32, both found with multiply-adds, and the two
 // window words are loaded for every group.  Twice the shared loads of the

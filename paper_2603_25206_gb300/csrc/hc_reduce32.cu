@@ -124,7 +124,7 @@ __device__ __forceinline__ ChunkRange load_range(const DevStream& s, int64_t c) 
 }
 
 template <int G, int OP, int ACC, int PRED, int BPL>
-__global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_words, Partial* parts,
+__global__ void __launch_bounds__(kWarps * 32, 5) k_reduce32(DevStream s, int buf_words, Partial* parts,
                                                           unsigned* ticket, hc_scalar* out, double two_eps,
                                                           const long long* shift, BoxDims bd) {
   constexpr int SEGS = 4 / BPL;  // 32-slot segments per block (box)
@@ -226,8 +226,61 @@ __global__ void __launch_bounds__(kWarps * 32) k_reduce32(DevStream s, int buf_w
     } else {
       const uint32_t* base = bufs + (size_t)b * buf_words + (uint32_t)(cur_r.p0 & 3) + (incl - lsum);
       const int32_t hj[4] = {cur.h4.x, cur.h4.y, cur.h4.z, cur.h4.w};
+      constexpr bool kPairs = BPL == 4 && PRED == HC_PRED_DELTA && (OP == OP_MEAN_P || OP == OP_MEAN_Q);
+      // the lane's four blocks all full (every lane but the one holding the
+      // stream's last blocks): decoded two at a time, side by side; a block
+      // of width 0 goes through the same arithmetic (it decodes to p = 0)
+      const bool pairs = kPairs && (bb + 4) * 32 <= s.N;
+      if constexpr (kPairs) {
+        if (pairs) {
+#pragma unroll
+          for (int j = 0; j < 4; j += 2) {
+            const uint32_t* ba = base + oj[j];
+            const uint32_t* bq = base + oj[j + 1];
+            if constexpr (OP == OP_MEAN_P) {
+              // Section V-A, stage 2: 32 head + sum_k (32 - k) p_k per block
+              int32_t a = 0, c = 0;
+              decode32x2<G>(
+                  ba + 1, ba[0], wj[j], bq + 1, bq[0], wj[j + 1], [&](int k, int32_t x, int32_t) { a += (32 - k) * x; },
+                  [&](int k, int32_t x, int32_t) { c += (32 - k) * x; });
+              S1 += 32ll * ((long long)hj[j] + hj[j + 1]) + (long long)a + c + weighted_sign_count(ba[0]) +
+                    weighted_sign_count(bq[0]);
+            } else {
+              // Section V-A, stage 3: q rebuilt from each block's head
+              int32_t qa = hj[j], qc = hj[j + 1], a1 = 0, c1 = 0;
+              using A2 = typename std::conditional<ACC == 0, uint32_t, unsigned long long>::type;
+              A2 a2 = 0, c2 = 0;
+              decode32x2<G>(
+                  ba + 1, ba[0], wj[j], bq + 1, bq[0], wj[j + 1],
+                  [&](int, int32_t x, int32_t neg) {
+                    qa = qa + x - neg;
+                    a1 += qa;
+                    if (OP == OP_VAR) {
+                      if constexpr (ACC == 0)
+                        a2 += (uint32_t)(qa * qa);
+                      else
+                        a2 += (unsigned long long)((long long)qa * qa);
+                    }
+                  },
+                  [&](int, int32_t x, int32_t neg) {
+                    qc = qc + x - neg;
+                    c1 += qc;
+                    if (OP == OP_VAR) {
+                      if constexpr (ACC == 0)
+                        c2 += (uint32_t)(qc * qc);
+                      else
+                        c2 += (unsigned long long)((long long)qc * qc);
+                    }
+                  });
+              S1 += (long long)a1 + c1;
+              if (OP == OP_VAR) S2 += (u128)a2 + (u128)c2;
+            }
+          }
+        }
+      }
 #pragma unroll
       for (int j = 0; j < BPL; ++j) {
+        if (pairs) break;
         const int64_t blk = bb + j;
         if (blk >= s.nb) break;
         const uint32_t w = wj[j];
