@@ -568,6 +568,40 @@ HC_API int hc_finalize(int64_t n, int64_t s1, uint64_t s2_lo, uint64_t s2_hi, do
 HC_API int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_ws, size_t ws_bytes,
                        void* stream, int* chosen);
 
+/* The autotuner's choices as text, so that a later process (a server that
+ * restarts, a job on another GPU of the same kind) can reuse them instead of
+ * timing every tile again (no counterpart in the paper: a GPU tiling choice).
+ * The text is JSON:
+ *   {"format": "hc-autotune", "version": 1, "entries": [
+ *     {"n0": 512, "n1": 512, "n2": 512, "wmax": 9, "op": "multi", "out": "float32",
+ *      "tile_rows": 8, "waves": 1}, ...]}
+ * one entry per choice hc_autotune kept in this process: (n0, n1, n2) the shape
+ * the fused stencils walk (a 2-D field (n1, n2) is walked as (n1, 1, n2)), wmax
+ * the stream's largest block width, op one of "derivative", "gradmag",
+ * "laplacian", "multi", out one of "float32", "float64", "int64", tile_rows
+ * the tile height and waves the plane ranges (1 or 2 waves of resident CTAs).
+ * A choice is a launch shape only: every choice gives the same results, and a
+ * tile that does not fit a later field of the same key falls back to another
+ * kernel of the same results.
+ *
+ * hc_autotune_export: writes the text, NUL-terminated, into buf (cap bytes)
+ * and its length without the NUL into *len.  buf == NULL: only *len is set
+ * (a size query).  Errors: HC_ERR_INVALID_ARG for len == NULL; HC_ERR_NOMEM
+ * when cap <= *len (nothing written to buf).  Host only, no device access. */
+HC_API int hc_autotune_export(char* buf, size_t cap, size_t* len);
+
+/* hc_autotune_import: reads text in the export format (NUL-terminated; keys in
+ * any order, whitespace anywhere between tokens) and keeps its choices for the
+ * later calls of this process, replacing a kept choice of the same key;
+ * *count receives the number of entries read.  Errors (nothing kept then,
+ * *count = 0): HC_ERR_INVALID_ARG for a NULL argument, text that is not in the
+ * format (an unknown, missing or repeated key, another format name or
+ * version, trailing characters, string escapes, negative or over-long
+ * numbers), or an entry out of range (a dimension outside 1..2^40, wmax
+ * above 32, tile_rows outside 1..255, waves outside 1..2, an int64 gradient
+ * magnitude or one-pass entry).  Host only, no device access. */
+HC_API int hc_autotune_import(const char* text, int* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -556,6 +556,10 @@ int hc_autotune(const hc_stage* in, int op, int out_dtype, void* d_out, void* d_
   return stencil_pipe_autotune(in->hdr, in->d_data, d3, sop, d_out, out_dtype, d_ws, as_stream(stream), chosen);
 }
 
+int hc_autotune_export(char* buf, size_t cap, size_t* len) { return autotune_export_impl(buf, cap, len); }
+
+int hc_autotune_import(const char* text, int* count) { return autotune_import_impl(text, count); }
+
 int hc_op_multi(const hc_stage* in, double eps, int ndim, const int64_t* dims, const hc_multi_out* out, void* d_ws,
                 size_t ws_bytes, void* stream) {
   int64_t dims3[3];

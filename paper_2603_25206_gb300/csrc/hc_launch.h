@@ -159,6 +159,9 @@ void stencil_walk_dims(const hc_header* h, int64_t d3[3], int* axis3);
 // Time the pipelined kernel's tile heights for this field/op and cache the best.
 int stencil_pipe_autotune(const hc_header* h, const void* d_stream, const int64_t* d3, int op, void* d_out,
                           int out_dtype, void* d_ws, cudaStream_t st, int* chosen);
+// The tuner's choices as JSON text (hc_autotune_export / hc_autotune_import).
+int autotune_export_impl(char* buf, size_t cap, size_t* len);
+int autotune_import_impl(const char* text, int* count);
 int stencil_array_impl(const hc_stage* in, const int64_t* dims3, double eps, int op, int axis3, void* d_out,
                        int out_dtype, void* d_ws, cudaStream_t st);
 

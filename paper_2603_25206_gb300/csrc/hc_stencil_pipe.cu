@@ -3,10 +3,14 @@
 // autotuner and the dispatch over operation, output type and row width.
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <type_traits>
+#include <vector>
 
 #include "hc_finish.cuh"
 #include "hc_group.cuh"
@@ -172,6 +176,180 @@ static int tuned_choice(const hc_header* h, const int64_t* d3, int op, int out_d
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tuned.find(TuneKey{d3[0], d3[1], d3[2], (int)h->wmax, op, out_dtype});
   return it == g_tuned.end() ? 0 : it->second;
+}
+
+// ---------------------------------------------- the choices as JSON text
+// {"format": "hc-autotune", "version": 1, "entries": [{"n0": .., "n1": ..,
+// "n2": .., "wmax": .., "op": "derivative" | "gradmag" | "laplacian" |
+// "multi", "out": "float32" | "float64" | "int64", "tile_rows": ..,
+// "waves": ..}, ...]}: (n0, n1, n2) the shape the fused stencils walk.
+namespace {
+const char* const kTuneOps[] = {"derivative", "gradmag", "laplacian", "multi"};  // ST_DERIV .. ST_MULTI
+const char* tune_out_name(int out) { return out == HC_F32 ? "float32" : (out == HC_F64 ? "float64" : "int64"); }
+
+// A reader of exactly the export format: objects, arrays, strings without
+// escapes, non-negative integers of at most 15 digits.
+struct JsonIn {
+  const char* p;
+  void ws() {
+    while (*p == ' ' || *p == '\n' || *p == '\t' || *p == '\r') ++p;
+  }
+  bool eat(char c) {
+    ws();
+    if (*p != c) return false;
+    ++p;
+    return true;
+  }
+  bool str(std::string& out) {
+    ws();
+    if (*p != '"') return false;
+    ++p;
+    out.clear();
+    while (*p && *p != '"') {
+      if (*p == '\\' || (unsigned char)*p < 0x20) return false;
+      out += *p++;
+    }
+    if (*p != '"') return false;
+    ++p;
+    return true;
+  }
+  bool num(int64_t& v) {
+    ws();
+    if (*p < '0' || *p > '9') return false;
+    v = 0;
+    int digits = 0;
+    while (*p >= '0' && *p <= '9') {
+      if (++digits > 15) return false;
+      v = v * 10 + (*p++ - '0');
+    }
+    return true;
+  }
+};
+
+// One entry object; false when a key is missing, unknown or repeated, or a
+// value is out of range.
+bool read_entry(JsonIn& in, TuneKey& key, int& choice) {
+  if (!in.eat('{')) return false;
+  int64_t v[6] = {0, 0, 0, 0, 0, 0};  // n0, n1, n2, wmax, tile_rows, waves
+  const char* names[6] = {"n0", "n1", "n2", "wmax", "tile_rows", "waves"};
+  int op = -1, out = -1;
+  unsigned seen = 0;
+  for (;;) {
+    std::string k;
+    if (!in.str(k) || !in.eat(':')) return false;
+    int slot = -1;
+    for (int i = 0; i < 6; ++i)
+      if (k == names[i]) slot = i;
+    if (slot >= 0) {
+      if (seen & (1u << slot) || !in.num(v[slot])) return false;
+      seen |= 1u << slot;
+    } else if (k == "op" || k == "out") {
+      const unsigned bit = k == "op" ? 1u << 6 : 1u << 7;
+      std::string val;
+      if (seen & bit || !in.str(val)) return false;
+      seen |= bit;
+      if (k == "op") {
+        for (int i = 0; i < 4; ++i)
+          if (val == kTuneOps[i]) op = i;
+        if (op < 0) return false;
+      } else {
+        out = val == "float32" ? HC_F32 : (val == "float64" ? HC_F64 : (val == "int64" ? HC_I64 : -1));
+        if (out < 0) return false;
+      }
+    } else {
+      return false;
+    }
+    if (in.eat(',')) continue;
+    if (in.eat('}')) break;
+    return false;
+  }
+  if (seen != 0xffu) return false;
+  const int64_t kMaxDim = (int64_t)1 << 40;
+  for (int i = 0; i < 3; ++i)
+    if (v[i] < 1 || v[i] > kMaxDim) return false;
+  if (v[3] > 32 || v[4] < 1 || v[4] > 255 || v[5] < 1 || v[5] > 2) return false;
+  // combinations the tuner never records: no integer gradient magnitude, and
+  // the one-pass kernel writes floating-point outputs only
+  if (out == HC_I64 && (op == ST_GRADMAG || op == ST_MULTI)) return false;
+  key = TuneKey{v[0], v[1], v[2], (int)v[3], op, out};
+  choice = (int)v[4] | (int)(v[5] << 8);
+  return true;
+}
+}  // namespace
+
+int autotune_export_impl(char* buf, size_t cap, size_t* len) {
+  if (!len) return fail(HC_ERR_INVALID_ARG, "null length");
+  std::string t = "{\"format\": \"hc-autotune\", \"version\": 1, \"entries\": [";
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    bool first = true;
+    for (const auto& kv : g_tuned) {
+      char e[320];
+      const TuneKey& k = kv.first;
+      std::snprintf(e, sizeof(e),
+                    "%s\n  {\"n0\": %lld, \"n1\": %lld, \"n2\": %lld, \"wmax\": %d, \"op\": \"%s\", \"out\": \"%s\", "
+                    "\"tile_rows\": %d, \"waves\": %d}",
+                    first ? "" : ",", (long long)k.n0, (long long)k.n1, (long long)k.n2, k.wmax,
+                    kTuneOps[k.op], tune_out_name(k.out), kv.second & 0xff, std::max(1, kv.second >> 8));
+      t += e;
+      first = false;
+    }
+  }
+  t += "]}\n";
+  *len = t.size();
+  if (!buf) return HC_OK;  // size query
+  if (cap <= t.size()) return fail(HC_ERR_NOMEM, "buffer too small for the autotune text");
+  std::memcpy(buf, t.c_str(), t.size() + 1);
+  return HC_OK;
+}
+
+int autotune_import_impl(const char* text, int* count) {
+  if (!text || !count) return fail(HC_ERR_INVALID_ARG, "null argument");
+  *count = 0;
+  JsonIn in{text};
+  std::vector<std::pair<TuneKey, int>> got;
+  bool fmt = false, ver = false, ents = false;
+  auto bad = [](const char* why) { return fail(HC_ERR_INVALID_ARG, why); };
+  if (!in.eat('{')) return bad("autotune text: not an object");
+  for (;;) {
+    std::string k;
+    if (!in.str(k) || !in.eat(':')) return bad("autotune text: expected a key");
+    if (k == "format" && !fmt) {
+      std::string v;
+      if (!in.str(v) || v != "hc-autotune") return bad("autotune text: format is not hc-autotune");
+      fmt = true;
+    } else if (k == "version" && !ver) {
+      int64_t v;
+      if (!in.num(v) || v != 1) return bad("autotune text: unsupported version");
+      ver = true;
+    } else if (k == "entries" && !ents) {
+      if (!in.eat('[')) return bad("autotune text: entries is not an array");
+      if (!in.eat(']')) {
+        for (;;) {
+          TuneKey key{};
+          int choice = 0;
+          if (!read_entry(in, key, choice)) return bad("autotune text: malformed or out-of-range entry");
+          got.emplace_back(key, choice);
+          if (in.eat(',')) continue;
+          if (in.eat(']')) break;
+          return bad("autotune text: expected , or ] in entries");
+        }
+      }
+      ents = true;
+    } else {
+      return bad("autotune text: unknown or repeated key");
+    }
+    if (in.eat(',')) continue;
+    if (in.eat('}')) break;
+    return bad("autotune text: expected , or }");
+  }
+  in.ws();
+  if (*in.p != '\0') return bad("autotune text: trailing characters");
+  if (!fmt || !ver || !ents) return bad("autotune text: format, version and entries are required");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto& e : got) g_tuned[e.first] = e.second;
+  *count = (int)got.size();
+  return HC_OK;
 }
 
 static int stencil_pipe_launch(const hc_header* h, const void* d_stream, const int64_t* d3, int op, int axis3,

@@ -52,7 +52,7 @@ ABI_FUNCTIONS = (
     "hc_batch_graph_launch", "hc_batch_graph_destroy", "hc_batch_status", "hc_op_multi", "hc_compress_ex",
     "hc_compress_codes_ex", "hc_op_divergence", "hc_op_curl", "hc_workspace_bytes_for", "hc_compress_bound_nd",
     "hc_compress_workspace_bytes_nd", "hc_compress_nd", "hc_compress_codes_nd", "hc_vector_workspace_bytes",
-    "hc_shard_plan", "hc_read_header_host", "hc_finalize",
+    "hc_shard_plan", "hc_read_header_host", "hc_finalize", "hc_autotune_export", "hc_autotune_import",
 )
 HC_PRED_DELTA, HC_PRED_MEAN, HC_PRED_LORENZO, HC_PRED_GLOBAL_DELTA, HC_PRED_MEAN_ND = 0, 1, 2, 3, 4
 # "delta": HSZp with block heads; "mean": HSZx; "lorenzo": HSZp-nd (Lorenzo over
@@ -176,6 +176,8 @@ def lib():
             "hc_op_gradmag": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_op_laplacian": ([P(HcStage), dbl, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_autotune": ([P(HcStage), i32, i32, vp, vp, sz, vp, P(ctypes.c_int)], i32),
+            "hc_autotune_export": ([ctypes.c_char_p, sz, P(sz)], i32),
+            "hc_autotune_import": ([ctypes.c_char_p, P(ctypes.c_int)], i32),
             "hc_op_multi": ([P(HcStage), dbl, i32, P(ctypes.c_int64), P(HcMultiOut), vp, sz, vp], i32),
             "hc_op_divergence": ([P(HcStage), i32, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
             "hc_op_curl": ([P(HcStage), i32, i32, P(ctypes.c_int64), vp, i32, vp, sz, vp], i32),
@@ -696,6 +698,35 @@ def autotune(c: Compressed, op: str, out_dtype: str = "float32", out=None, strea
     _check(lib().hc_autotune(ctypes.byref(st), OPS[op], _OUT[out_dtype], ctypes.c_void_p(out.data_ptr()),
                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream), ctypes.byref(chosen)))
     return chosen.value
+
+
+def autotune_export() -> str:
+    """The autotuner's kept choices as JSON text (hc_autotune_export)."""
+    n = ctypes.c_size_t()
+    _check(lib().hc_autotune_export(None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib().hc_autotune_export(buf, n.value + 1, ctypes.byref(n)))
+    return buf.value.decode("ascii")
+
+
+def autotune_import(text: str) -> int:
+    """Keep the choices of an exported text for later calls of this process
+    (hc_autotune_import); returns the number of entries read."""
+    count = ctypes.c_int()
+    _check(lib().hc_autotune_import(text.encode("ascii"), ctypes.byref(count)))
+    return count.value
+
+
+def save_autotune(path) -> None:
+    """Write the autotuner's kept choices to a JSON file."""
+    with open(path, "w") as f:
+        f.write(autotune_export())
+
+
+def load_autotune(path) -> int:
+    """Read a file written by save_autotune; returns the number of choices read."""
+    with open(path) as f:
+        return autotune_import(f.read())
 
 
 # ------------------------------------------------------------ batched launch
