@@ -119,3 +119,29 @@ def test_save_and_load_a_file(hc, tmp_path):
     saved = json.loads(p.read_text())
     assert saved["format"] == "hc-autotune" and _entry(n0=11, tile_rows=2) in saved["entries"]
     assert hc.load_autotune(p) == len(saved["entries"])
+
+
+def test_any_valid_table_round_trips(hc):
+    """Drawn tables of valid entries read back as the same entries."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    entry = st.fixed_dictionaries({
+        "n0": st.integers(1, 1 << 40), "n1": st.integers(1, 1 << 40), "n2": st.integers(100000, 1 << 40),
+        "wmax": st.integers(0, 32), "op": st.sampled_from(["derivative", "laplacian"]),
+        "out": st.sampled_from(["float32", "float64", "int64"]), "tile_rows": st.integers(1, 255),
+        "waves": st.integers(1, 2)})
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(st.lists(entry, max_size=6))
+    def check(es):
+        assert hc.autotune_import(_text(es)) == len(es)
+        kept = _kept(hc)
+        for e in es:
+            key = {k: e[k] for k in ("n0", "n1", "n2", "wmax", "op", "out")}
+            mine = [k for k in kept if {x: k[x] for x in key} == key]
+            # a later entry of the same key replaces an earlier one
+            last = [x for x in es if {k: x[k] for k in key} == key][-1]
+            assert mine == [last]
+
+    check()
